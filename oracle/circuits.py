@@ -1,0 +1,597 @@
+"""Slot layout, public constants and the homomorphic circuits (test oracle).
+
+Two circuits are restated here, step by step, on top of ``ckks``:
+
+* ``fir_dft``: the small instance -- a 64-tap bandpass FIR (K5, Eq. for
+  I_f = T I) followed by the windowed, fftshifted D-point DFT of Eq. (K3)
+  (d_re = C v_re - S v_im, d_im = S v_re + C v_im), both as BSGS diagonal
+  matrix-vector products, applied to every range bin of a window.
+* ``vital``: the vital-sign chain of Sec. "Example Pipelines"
+  (K1 -> K2 -> K4 -> K5 -> K7 -> K3 -> K1 -> K2) with the level schedule of
+  Table 1 (depth 11 with the third-order Taylor arctan, 9 with first order).
+
+Slot layout (batched packing, Sec. "Packing"): frames are packed frame-major,
+slot(t, r) = t * R_c + r with F_pad = 2^ceil(log2 F) frame positions and
+R_c = (N/2) / F_pad range bins per ciphertext; a window's R bins fill
+G = ceil(R / R_c) ciphertexts per real/imaginary part; padding is zero.
+
+Readings of passages the paper leaves open (each restated in the design
+notes): constants are encoded at scale q_l of the level they multiply so the
+rescale returns the ciphertext scale; BSGS baby steps are hoisted, giant steps
+are ordinary rotations, one rescale follows each matrix product; products that
+are summed share one relinearization (lazy relinearization); the 1/3 of the
+third-order Taylor term is realised as 3 x^2 - y^2 (exact integer multiply)
+with the 1/3 folded into the DFT constants; the DFT of the vital chain keeps
+the band rows only (narrowband), placed at position k of frequency k fs / F,
+scaled by 1/F; FIR taps are a Hamming-windowed-sinc bandpass normalised to
+unit gain at the band centre.
+"""
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import ckks as ck
+
+
+# ----------------------------------------------------------------------------
+# configuration and slot layout (A0)
+# ----------------------------------------------------------------------------
+def next_pow2(x):
+    return 1 << max(0, math.ceil(math.log2(x)))
+
+
+@dataclass
+class Layout:
+    slots: int
+    bins: int           # R
+    frames: int         # F
+
+    @property
+    def f_pad(self):
+        return next_pow2(self.frames)
+
+    @property
+    def r_c(self):
+        return self.slots // self.f_pad
+
+    @property
+    def groups(self):
+        return -(-self.bins // self.r_c)
+
+    def slot(self, t, r):
+        return t * self.r_c + r
+
+    def pack(self, values):
+        """values [F, R] real -> G slot vectors (frame-major, zero padded)."""
+        F, R = values.shape
+        assert F == self.frames and R == self.bins
+        out = np.zeros((self.groups, self.slots))
+        for c in range(self.groups):
+            r0, r1 = c * self.r_c, min((c + 1) * self.r_c, R)
+            blk = np.zeros((self.f_pad, self.r_c))
+            blk[:F, : r1 - r0] = values[:, r0:r1]
+            out[c] = blk.reshape(-1)
+        return out
+
+
+@dataclass
+class FirDftConfig:
+    bins: int = 64
+    frames: int = 200
+    fs_mhz: int = 20000
+    taps: int = 64
+    band_mhz: tuple = (800, 2500)
+
+
+@dataclass
+class VitalConfig:
+    bins: int = 256
+    frames: int = 200
+    fs_mhz: int = 20000
+    taps: int = 64
+    bands_mhz: tuple = ((100, 600), (800, 2500))     # respiration, heart (Sec. "Example Pipelines")
+    taylor_order: int = 3
+    # public per-band spectral gains g_b of the narrowband DFT
+    # X_b[k] = g_b * sum_t w[t] dphi[t] exp(-j 2 pi k t / F) (None = defaults)
+    dft_gains: tuple = None
+
+    def gains(self):
+        """Default gains put the median DFT magnitude of the synthetic
+        workload near 0.5 so that |X|^2 and its square stay inside the
+        precision window of Delta = 2^40 and below q_0 / (2 Delta) at the
+        last level."""
+        if self.dft_gains is not None:
+            return self.dft_gains
+        return (30.0, 1.0) if self.taylor_order == 3 else (1.5, 0.2)
+
+
+# ----------------------------------------------------------------------------
+# public DSP constants (FP64)
+# ----------------------------------------------------------------------------
+def fir_bandpass(taps, f_lo_hz, f_hi_hz, fs_hz):
+    """Hamming-windowed-sinc bandpass, unit gain at the band centre."""
+    M = (taps - 1) / 2.0
+    m = np.arange(taps) - M
+    a, b = f_lo_hz / fs_hz, f_hi_hz / fs_hz                  # cycles / sample
+    h = 2 * b * np.sinc(2 * b * m) - 2 * a * np.sinc(2 * a * m)
+    h = h * (0.54 - 0.46 * np.cos(2 * np.pi * np.arange(taps) / (taps - 1)))
+    fc = 0.5 * (a + b)
+    return h / np.sum(h * np.cos(2 * np.pi * fc * m))
+
+
+def hann(n):
+    """Symmetric Hann ('Hanning') window w[k] = 0.5 - 0.5 cos(2 pi k / (n-1))."""
+    return 0.5 - 0.5 * np.cos(2 * np.pi * np.arange(n) / (n - 1))
+
+
+def dft_kernel(D):
+    """W[d, n] = w[n] exp(-j 2 pi sigma(d) n / D), sigma(d) = (d + D/2) mod D
+    (Eq. K3)."""
+    d = np.arange(D)[:, None]
+    n = np.arange(D)[None, :]
+    sig = (d + D // 2) % D
+    return hann(D)[None, :] * np.exp(-2j * np.pi * sig * n / D)
+
+
+def band_bins(frames, fs_mhz, band_mhz):
+    """Frequency bins k with f_lo <= k fs / F <= f_hi (exact integer test)."""
+    lo, hi = band_mhz
+    return [k for k in range(frames // 2 + 1) if lo * frames <= k * fs_mhz <= hi * frames]
+
+
+# ----------------------------------------------------------------------------
+# BSGS diagonal matrix-vector product (A9) and rotate-and-sum (A10)
+# ----------------------------------------------------------------------------
+def bsgs_split(num_diag):
+    """n1 = 2^ceil(log2(D)/2) baby steps, n2 = D / n1 giant steps."""
+    D = next_pow2(num_diag)
+    n1 = 1 << math.ceil(math.log2(D) / 2)
+    return n1, D // n1
+
+
+def rotate_slots(v, k):
+    """Rot(v, k)[j] = v[(j + k) mod n]."""
+    return np.roll(v, -k)
+
+
+def matrix_diagonals(M_time, lay, row_offset=0, col_offset=0):
+    """Diagonals of a time-axis matrix (rows = output positions, columns =
+    input positions over F_pad) in the frame-major layout.
+
+    Output slot(t, row_offset) receives sum_u M[t, u] x[slot(u, col_offset)],
+    realised as sum_delta diag_delta (.) Rot(x, delta * R_c) with
+    diag_delta[slot(t, row_offset)] = M[t, (t + delta) mod F_pad] (requires
+    row_offset == col_offset since the rotation keeps the in-frame offset).
+    Returns {delta: slot vector}; structurally absent diagonals are omitted.
+    """
+    assert row_offset == col_offset
+    Fp = lay.f_pad
+    out = {}
+    present = np.zeros(Fp, dtype=bool)
+    rows, cols = np.nonzero(M_time["support"])
+    present[(cols - rows) % Fp] = True
+    for delta in np.nonzero(present)[0]:
+        v = np.zeros(lay.slots)
+        t = np.arange(Fp)
+        v[t * lay.r_c + row_offset] = M_time["values"][t, (t + delta) % Fp]
+        out[int(delta)] = v
+    return out
+
+
+def prerotate(diag, g, n1, stride):
+    """D'_{g,b} = Rot(D_delta, -g n1 stride)."""
+    return rotate_slots(diag, -g * n1 * stride)
+
+
+class Evaluator:
+    """Evaluation context: parameters, keys and the op trace (for the
+    data-obliviousness check of Theorem 2)."""
+
+    def __init__(self, P, rlk, gks, trace=False):
+        self.P, self.rlk, self.gks = P, rlk, gks
+        self.trace = [] if trace else None
+
+    def _t(self, *rec):
+        if self.trace is not None:
+            self.trace.append(rec)
+
+    # thin wrappers that record the trace
+    def tensor(self, a, b):
+        self._t("tensor", a.level)
+        return ck.tensor(self.P, a, b)
+
+    def relin(self, t):
+        self._t("relin", t.level)
+        return ck.relinearize(self.P, t, self.rlk)
+
+    def rescale(self, a):
+        self._t("rescale", a.level)
+        return ck.rescale(self.P, a)
+
+    def rotate(self, a, k):
+        self._t("rotate", a.level, k)
+        return ck.rotate(self.P, a, k, self.gks)
+
+    def hoisted(self, a, ks):
+        self._t("hoisted", a.level, tuple(ks))
+        return ck.rotate_hoisted(self.P, a, ks, self.gks)
+
+    def add(self, a, b):
+        self._t("add", a.level)
+        return ck.add(self.P, a, b)
+
+    def mul_plain(self, a, pt):
+        self._t("mul_plain", a.level)
+        return ck.mul_plain(self.P, a, pt)
+
+    def rotsum(self, a, stride, span):
+        """x <- x + Rot(x, stride 2^i), i < log2(span): slot j then holds
+        sum_{m < span} x[j + m stride]."""
+        for i in range(int(math.log2(span))):
+            a = self.add(a, self.rotate(a, stride << i))
+        return a
+
+    def square_sum(self, xs):
+        """relin(sum_i x_i (x) x_i), not rescaled (lazy relinearization)."""
+        t = self.tensor(xs[0], xs[0])
+        for x in xs[1:]:
+            t = ck.tensor_add(self.P, t, self.tensor(x, x))
+        return self.relin(t)
+
+    def bsgs(self, babies, consts, n1, stride, level):
+        """Giant-step half of the BSGS product (A9).
+
+        ``babies[name][b]`` = Rot(x_name, b stride) (b < n1, from a hoisted
+        set); ``consts[(name, delta)]`` = encoded pre-rotated diagonal
+        D'_{g,b} with delta = g n1 + b.  Returns
+        sum_g Rot( sum_{name,b} D'_{g,b} (.) babies[name][b], g n1 stride ),
+        not rescaled.  Absent diagonals / giant groups are skipped.
+        """
+        groups = {}
+        for (name, delta) in consts:
+            groups.setdefault(delta // n1, []).append((name, delta))
+        acc = None
+        for g in sorted(groups):
+            pairs = []
+            for (name, delta) in sorted(groups[g]):
+                pairs.append((babies[name][delta % n1], consts[(name, delta)]))
+                self._t("mul_plain", level, name, delta)
+            inner = ck.mul_plain_sum(self.P, pairs)
+            if g:
+                inner = self.rotate(inner, g * n1 * stride)
+            acc = inner if acc is None else self.add(acc, inner)
+        return acc
+
+
+# ----------------------------------------------------------------------------
+# FIR + DFT circuit (small instance)
+# ----------------------------------------------------------------------------
+class FirDftCircuit:
+    """Bandpass FIR along time for every range bin, then the D = F point
+    windowed fftshifted DFT (Eq. K3), on G groups x (Re, Im) ciphertexts."""
+
+    def __init__(self, P, cfg=FirDftConfig()):
+        self.P, self.cfg = P, cfg
+        self.lay = Layout(P.slots, cfg.bins, cfg.frames)
+        self.n1_fir, self.n2_fir = bsgs_split(cfg.taps)
+        self.n1_dft, self.n2_dft = bsgs_split(self.lay.f_pad)
+
+    def fir_matrix(self):
+        cfg, Fp = self.cfg, self.lay.f_pad
+        h = fir_bandpass(cfg.taps, cfg.band_mhz[0] / 1000, cfg.band_mhz[1] / 1000, cfg.fs_mhz / 1000)
+        return fir_toeplitz(h, cfg.frames, Fp)
+
+    def dft_matrices(self):
+        D, Fp = self.cfg.frames, self.lay.f_pad
+        W = dft_kernel(D)
+        sup = np.zeros((Fp, Fp), dtype=bool)
+        sup[:D, :D] = True
+        out = {}
+        for name, vals in (("c", W.real), ("s", W.imag), ("ms", -W.imag)):
+            M = np.zeros((Fp, Fp))
+            M[:D, :D] = vals
+            out[name] = {"support": sup, "values": M}
+        return out
+
+    def fir_diagonals(self):
+        """FIR as diagonals over negative rotations: Rot(x, -k R_c), k < taps."""
+        M = self.fir_matrix()
+        lay, Fp = self.lay, self.lay.f_pad
+        out = {}
+        for k in range(self.cfg.taps):
+            v = np.zeros(lay.slots)
+            t = np.arange(Fp)
+            for r in range(lay.r_c):
+                v[t * lay.r_c + r] = M["values"][t, (t - k) % Fp] * M["support"][t, (t - k) % Fp]
+            out[k] = v
+        return out
+
+    def rotations(self):
+        lay = self.lay
+        ks = set()
+        ks |= {-b * lay.r_c for b in range(1, self.n1_fir)}
+        ks |= {-g * self.n1_fir * lay.r_c for g in range(1, self.n2_fir)}
+        ks |= {b * lay.r_c for b in range(1, self.n1_dft)}
+        ks |= {g * self.n1_dft * lay.r_c for g in range(1, self.n2_dft)}
+        return sorted({k % self.P.slots for k in ks})
+
+    def constants(self):
+        """Encoded constants keyed (name, delta) -> Plaintext."""
+        P, lay = self.P, self.lay
+        L = P.L
+        out = {}
+        n1 = self.n1_fir
+        for k, v in self.fir_diagonals().items():
+            out[("fir", k)] = ck.encode(P, prerotate(v, k // n1, n1, -lay.r_c), P.q[L], L)
+        n1 = self.n1_dft
+        for name, M in self.dft_matrices().items():
+            for delta, v in matrix_diagonals_all_offsets(M, lay).items():
+                out[("dft_" + name, delta)] = ck.encode(P, prerotate(v, delta // n1, n1, lay.r_c), P.q[L - 1], L - 1)
+        return out
+
+    def run(self, ev, consts, cts):
+        """cts: list of G (re, im) ciphertext pairs at level L.  Returns the
+        list of G (d_re, d_im) pairs at level L - 2."""
+        lay = self.lay
+        fir = {("x", k): consts[("fir", k)] for k in range(self.cfg.taps)}
+        out = []
+        for re, im in cts:
+            vf = []
+            for x in (re, im):
+                babies = {"x": ev.hoisted(x, [-b * lay.r_c for b in range(self.n1_fir)])}
+                vf.append(ev.rescale(ev.bsgs(babies, fir, self.n1_fir, -lay.r_c, x.level)))
+            n1 = self.n1_dft
+            babies = {
+                "re": ev.hoisted(vf[0], [b * lay.r_c for b in range(n1)]),
+                "im": ev.hoisted(vf[1], [b * lay.r_c for b in range(n1)]),
+            }
+            keys = [k for k in consts if k[0].startswith("dft_")]
+            c_re = {("re", d): consts[(n, d)] for (n, d) in keys if n == "dft_c"}
+            c_re.update({("im", d): consts[(n, d)] for (n, d) in keys if n == "dft_ms"})
+            c_im = {("re", d): consts[(n, d)] for (n, d) in keys if n == "dft_s"}
+            c_im.update({("im", d): consts[(n, d)] for (n, d) in keys if n == "dft_c"})
+            lvl = vf[0].level
+            d_re = ev.rescale(ev.bsgs(babies, c_re, n1, lay.r_c, lvl))
+            d_im = ev.rescale(ev.bsgs(babies, c_im, n1, lay.r_c, lvl))
+            out.append((d_re, d_im))
+        return out
+
+
+def fir_toeplitz(h, frames, f_pad):
+    """Causal FIR with zero initial state as a time-axis matrix:
+    y[t] = sum_k h[k] x[t - k], t < F, t - k >= 0."""
+    M = np.zeros((f_pad, f_pad))
+    sup = np.zeros((f_pad, f_pad), dtype=bool)
+    for t in range(frames):
+        for k in range(len(h)):
+            if t - k >= 0:
+                M[t, t - k] = h[k]
+                sup[t, t - k] = True
+    return {"support": sup, "values": M}
+
+
+def matrix_diagonals_all_offsets(M_time, lay):
+    """Like matrix_diagonals but the same time-axis matrix acts on every
+    in-frame offset r (every range bin of the group)."""
+    Fp = lay.f_pad
+    present = np.zeros(Fp, dtype=bool)
+    rows, cols = np.nonzero(M_time["support"])
+    present[(cols - rows) % Fp] = True
+    out = {}
+    t = np.arange(Fp)
+    for delta in np.nonzero(present)[0]:
+        blk = np.repeat(M_time["values"][t, (t + delta) % Fp][:, None], lay.r_c, axis=1)
+        out[int(delta)] = blk.reshape(-1)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# vital-sign chain (A11)
+# ----------------------------------------------------------------------------
+class VitalCircuit:
+    """K1 -> K2 side branch (target bin num/den) and the HR/RR main chain
+    K4 -> K5 -> K7 -> K3 -> |X|^2 -> merge + square -> weighted frequency
+    average, on a window of 2 streams x G groups x (Re, Im) ciphertexts.
+
+    Level schedule (Table 1), L0 = top level:
+      side: K1 p (L0-1), rotate-sum over frames; K2 w = E^2 (L0-2);
+            index / one vectors (L0-3), rotate-sum over bins -> num_r, den_r.
+      main: K4 p (L0-1), m = p^2 (L0-2), I, Q = sum m Re, m Im (L0-3),
+            rotate-sum over bins; K5 FIR per band (L0-4); K7 y, x (L0-5),
+            third order: u = 3x^2 - y^2 (L0-6), dphi3 = y u (L0-7);
+            K3 narrowband DFT (+1); |X|^2 (+2); merge RR+HR, square (+3);
+            x f_k and x 1 per band (+4), rotate-sum -> num_b, den_b.
+    Outputs: [num_r, den_r, num_RR, den_RR, num_HR, den_HR].
+    """
+
+    def __init__(self, P, cfg=VitalConfig()):
+        self.P, self.cfg = P, cfg
+        self.lay = Layout(P.slots, cfg.bins, cfg.frames)
+        self.n1_fir, self.n2_fir = bsgs_split(cfg.taps)
+        self.n1_dft, self.n2_dft = bsgs_split(self.lay.f_pad)
+        self.bands = [band_bins(cfg.frames, cfg.fs_mhz, b) for b in cfg.bands_mhz]
+        L0 = P.L
+        self.lv_side_const = L0 - 2
+        self.lv_fir = L0 - 3
+        self.lv_dphi = L0 - 7 if cfg.taylor_order == 3 else L0 - 5
+        self.lv_final_const = self.lv_dphi - 3
+        assert self.lv_final_const >= 1, "not enough levels for the chain"
+
+    # -- public constants ----------------------------------------------------
+    def taps(self, b):
+        lo, hi = self.cfg.bands_mhz[b]
+        return fir_bandpass(self.cfg.taps, lo / 1000, hi / 1000, self.cfg.fs_mhz / 1000)
+
+    def dft_gain(self, b):
+        """g_b, times 1/3 for the third-order chain (which carries 3 dphi)."""
+        return self.cfg.gains()[b] * (1.0 / 3.0 if self.cfg.taylor_order == 3 else 1.0)
+
+    def dft_time_matrices(self, b):
+        F, Fp = self.cfg.frames, self.lay.f_pad
+        w = hann(F)
+        t = np.arange(F)
+        out = {}
+        for name in ("dre", "dim"):
+            M = np.zeros((Fp, Fp))
+            sup = np.zeros((Fp, Fp), dtype=bool)
+            for k in self.bands[b]:
+                ang = 2 * np.pi * k * t / F
+                M[k, :F] = self.dft_gain(b) * w * (np.cos(ang) if name == "dre" else -np.sin(ang))
+                sup[k, :F] = True
+            out[name] = {"support": sup, "values": M}
+        return out
+
+    def span(self, b):
+        return next_pow2(max(self.bands[b]) + 1)
+
+    def fir_diagonals(self, b):
+        lay, F = self.lay, self.cfg.frames
+        h = self.taps(b)
+        out = {}
+        for k in range(self.cfg.taps):
+            v = np.zeros(lay.slots)
+            for t in range(k, F):
+                v[lay.slot(t, 0)] = h[k]
+            out[k] = v
+        return out
+
+    def rotations(self):
+        lay, cfg = self.lay, self.cfg
+        ks = set()
+        ks |= {lay.r_c << i for i in range(int(math.log2(lay.f_pad)))}
+        ks |= {1 << i for i in range(int(math.log2(lay.r_c)))}
+        ks |= {-b * lay.r_c for b in range(1, self.n1_fir)}
+        ks |= {-g * self.n1_fir * lay.r_c for g in range(1, self.n2_fir)}
+        ks.add(-lay.r_c)
+        for b in range(len(self.bands)):
+            for name, M in self.dft_time_matrices(b).items():
+                for delta in matrix_diagonals(M, lay):
+                    if delta % self.n1_dft:
+                        ks.add((delta % self.n1_dft) * lay.r_c)
+                    if delta // self.n1_dft:
+                        ks.add((delta // self.n1_dft) * self.n1_dft * lay.r_c)
+            ks |= {lay.r_c << i for i in range(int(math.log2(self.span(b))))}
+        return sorted({k % self.P.slots for k in ks})
+
+    def constants(self):
+        P, lay, cfg = self.P, self.lay, self.cfg
+        out = {}
+        lv = self.lv_side_const
+        for c in range(lay.groups):
+            idx, one = np.zeros(lay.slots), np.zeros(lay.slots)
+            for r in range(lay.r_c):
+                gbin = c * lay.r_c + r
+                if gbin < cfg.bins:
+                    idx[lay.slot(0, r)] = gbin
+                    one[lay.slot(0, r)] = 1.0
+            out[("idx", c)] = ck.encode(P, idx, P.q[lv], lv)
+            out[("one", c)] = ck.encode(P, one, P.q[lv], lv)
+        lv = self.lv_fir
+        for b in range(len(self.bands)):
+            for k, v in self.fir_diagonals(b).items():
+                v = prerotate(v, k // self.n1_fir, self.n1_fir, -lay.r_c)
+                out[("fir", b, k)] = ck.encode(P, v, P.q[lv], lv)
+        lv = self.lv_dphi
+        for b in range(len(self.bands)):
+            for name, M in self.dft_time_matrices(b).items():
+                for delta, v in matrix_diagonals(M, lay).items():
+                    v = prerotate(v, delta // self.n1_dft, self.n1_dft, lay.r_c)
+                    out[(name, b, delta)] = ck.encode(P, v, P.q[lv], lv)
+        lv = self.lv_final_const
+        fs_hz = cfg.fs_mhz / 1000
+        for b, ks in enumerate(self.bands):
+            fw, fo = np.zeros(lay.slots), np.zeros(lay.slots)
+            for k in ks:
+                fw[lay.slot(k, 0)] = k * fs_hz / cfg.frames          # Hz; the client multiplies by 60
+                fo[lay.slot(k, 0)] = 1.0
+            out[("fw", b)] = ck.encode(P, fw, P.q[lv], lv)
+            out[("fone", b)] = ck.encode(P, fo, P.q[lv], lv)
+        return out
+
+    # -- the chain -----------------------------------------------------------
+    def run(self, ev, consts, s1, s2):
+        """s1, s2: lists of G (re, im) ciphertext pairs (stream 1 feeds K1,
+        stream 2 feeds K4), all at the top level.  Returns six ciphertexts."""
+        P, lay, cfg = self.P, self.lay, self.cfg
+        G = lay.groups
+        # side branch: K1 energy, K2 soft power attention (gamma = 2)
+        w = []
+        for re, im in s1:
+            p = ev.rescale(ev.square_sum([re, im]))
+            E = ev.rotsum(p, lay.r_c, lay.f_pad)
+            w.append(ev.rescale(ev.square_sum([E])))
+        num = den = None
+        for c in range(G):
+            tn = ev.mul_plain(w[c], consts[("idx", c)])
+            td = ev.mul_plain(w[c], consts[("one", c)])
+            num = tn if num is None else ev.add(num, tn)
+            den = td if den is None else ev.add(den, td)
+        num_r = ev.rotsum(ev.rescale(num), 1, lay.r_c)
+        den_r = ev.rotsum(ev.rescale(den), 1, lay.r_c)
+
+        # K4 soft I/Q extraction (P_phi = 2)
+        m = []
+        for re, im in s2:
+            p = ev.rescale(ev.square_sum([re, im]))
+            m.append(ev.rescale(ev.square_sum([p])))
+        lv = m[0].level
+        iq = []
+        for part in (0, 1):
+            t = None
+            for c in range(G):
+                x = ck.drop_level(P, s2[c][part], lv)
+                tc = ev.tensor(m[c], x)
+                t = tc if t is None else ck.tensor_add(P, t, tc)
+            iq.append(ev.rotsum(ev.rescale(ev.relin(t)), 1, lay.r_c))
+        I, Q = iq
+
+        # K5 FIR per band: babies of I and Q hoisted once, shared by both bands
+        n1 = self.n1_fir
+        bI = ev.hoisted(I, [-b * lay.r_c for b in range(n1)])
+        bQ = ev.hoisted(Q, [-b * lay.r_c for b in range(n1)])
+        dphis = []
+        for b in range(len(self.bands)):
+            fir = {("x", k): consts[("fir", b, k)] for k in range(cfg.taps)}
+            If = ev.rescale(ev.bsgs({"x": bI}, fir, n1, -lay.r_c, I.level))
+            Qf = ev.rescale(ev.bsgs({"x": bQ}, fir, n1, -lay.r_c, Q.level))
+            # K7 differential phase
+            If1 = ev.rotate(If, -lay.r_c)
+            Qf1 = ev.rotate(Qf, -lay.r_c)
+            y = ev.rescale(ev.relin(ck.tensor_sub(P, ev.tensor(Qf, If1), ev.tensor(If, Qf1))))
+            x = ev.rescale(ev.relin(ck.tensor_add(P, ev.tensor(If, If1), ev.tensor(Qf, Qf1))))
+            if cfg.taylor_order == 3:
+                u = ck.tensor_sub(P, ck.tensor_mul_int(P, ev.tensor(x, x), 3), ev.tensor(y, y))
+                u = ev.rescale(ev.relin(u))
+                yd = ck.drop_level(P, y, u.level)
+                dphis.append(ev.rescale(ev.relin(ev.tensor(yd, u))))
+            else:
+                dphis.append(y)
+
+        # K3 narrowband DFT, |X|^2
+        n1 = self.n1_dft
+        powers = []
+        for b, dphi in enumerate(dphis):
+            cre, cim = {}, {}
+            for key, pt in consts.items():
+                if key[0] in ("dre", "dim") and key[1] == b:
+                    (cre if key[0] == "dre" else cim)[("x", key[2])] = pt
+            need = sorted({d % n1 for (_, d) in list(cre) + list(cim)})
+            hs = ev.hoisted(dphi, [bb * lay.r_c for bb in need])
+            babies = {"x": dict(zip(need, hs))}
+            Xre = ev.rescale(ev.bsgs(babies, cre, n1, lay.r_c, dphi.level))
+            Xim = ev.rescale(ev.bsgs(babies, cim, n1, lay.r_c, dphi.level))
+            powers.append(ev.rescale(ev.square_sum([Xre, Xim])))
+
+        # merge (disjoint bins) and sharpen (gamma = 2), weighted frequency average
+        Mg = powers[0]
+        for pw in powers[1:]:
+            Mg = ev.add(Mg, pw)
+        S = ev.rescale(ev.square_sum([Mg]))
+        outs = [num_r, den_r]
+        for b in range(len(self.bands)):
+            nb = ev.rescale(ev.mul_plain(S, consts[("fw", b)]))
+            db = ev.rescale(ev.mul_plain(S, consts[("fone", b)]))
+            outs.append(ev.rotsum(nb, lay.r_c, self.span(b)))
+            outs.append(ev.rotsum(db, lay.r_c, self.span(b)))
+        return outs

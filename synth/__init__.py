@@ -1,0 +1,133 @@
+"""Seeded synthetic inputs shared by the oracle tests and the CUDA path.
+
+This module draws random numbers and builds synthetic radar windows; it holds
+none of the homomorphic scheme's arithmetic.  The randomness a CKKS client
+draws (ternary secret, discrete-Gaussian errors, uniform ring elements) is
+produced here and passed into whichever implementation consumes it.
+
+Radar windows follow the paper's vital-sign setup (Sec. "Processing
+configuration": R range bins x F frames, 20 Hz frame rate, 10 s window;
+Appendix A: a target bin whose phase follows 4 pi d(t) / lambda) with the
+workload recipe:
+
+* one target bin r* ~ U{8 .. R-9}; chest displacement
+  d(t) = a_h sin(2 pi f_h t + phi_h) + a_r sin(2 pi f_r t + phi_r),
+  a_h = 0.5 mm, a_r = 4 mm, carrier 77 GHz (lambda = c / 77 GHz);
+* fixed-rate workload: f_h = 1.2 Hz, f_r = 0.25 Hz; randomized workload:
+  f_h ~ U(0.8, 2.0) Hz, f_r ~ U(0.1, 0.5) Hz;
+* target amplitude 1 with a random static phase, every bin (target included)
+  gets N(0, sigma^2) noise per real component, sigma = 0.05.
+"""
+import numpy as np
+
+C_LIGHT = 299_792_458.0
+F_CARRIER = 77e9
+LAMBDA_M = C_LIGHT / F_CARRIER
+
+GAUSS_SIGMA = 3.19
+GAUSS_TAIL = 6.0
+
+
+def rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+# ---------------------------------------------------------------------------
+# randomness of the scheme's client (passed in as inputs)
+# ---------------------------------------------------------------------------
+def ternary(g, n):
+    """Uniform ternary coefficients in {-1, 0, 1}."""
+    return g.integers(-1, 2, size=n, dtype=np.int64)
+
+
+def gaussian(g, n, sigma=GAUSS_SIGMA, tail=GAUSS_TAIL):
+    """Rounded Gaussian integers, |x| <= tail*sigma (resampled outside)."""
+    x = np.rint(g.normal(0.0, sigma, size=n))
+    bound = np.floor(tail * sigma)
+    bad = np.abs(x) > bound
+    while bad.any():
+        x[bad] = np.rint(g.normal(0.0, sigma, size=int(bad.sum())))
+        bad = np.abs(x) > bound
+    return x.astype(np.int64)
+
+
+def uniform_residues(g, primes, n):
+    """Rows of uniform residues, row i in [0, primes[i])."""
+    out = np.empty((len(primes), n), dtype=np.uint64)
+    for i, q in enumerate(primes):
+        out[i] = g.integers(0, int(q), size=n, dtype=np.uint64)
+    return out
+
+
+class KeyDraws:
+    """All randomness of one client key generation for a given rotation list.
+
+    secret: ternary s; pk: (a over Q, e); rlk / gk[k]: (a [dnum][Q*P rows],
+    e [dnum]) per switching key.  Draw order is fixed (s, pk, rlk, then the
+    rotation keys in the order given) so every consumer sees the same values.
+    """
+
+    def __init__(self, seed, n, q_primes, p_primes, dnum, rotations):
+        g = rng(seed)
+        qp = list(q_primes) + list(p_primes)
+        self.secret = ternary(g, n)
+        self.pk_a = uniform_residues(g, q_primes, n)
+        self.pk_e = gaussian(g, n)
+        self.rlk_a = np.stack([uniform_residues(g, qp, n) for _ in range(dnum)])
+        self.rlk_e = np.stack([gaussian(g, n) for _ in range(dnum)])
+        self.gk = {}
+        for k in rotations:
+            a = np.stack([uniform_residues(g, qp, n) for _ in range(dnum)])
+            e = np.stack([gaussian(g, n) for _ in range(dnum)])
+            self.gk[k] = (a, e)
+
+
+def encryption_draws(seed, n):
+    """(v, e0, e1) for one public-key encryption."""
+    g = rng(seed)
+    return ternary(g, n), gaussian(g, n), gaussian(g, n)
+
+
+def uniform_ciphertexts(seed, q_primes, n, count):
+    """``count`` ciphertexts of uniform residues, layout [count][2][L+1][N].
+
+    Under the RLWE assumption a ciphertext is indistinguishable from such a
+    pair; the cloud's work is independent of the values (data-oblivious
+    circuit), so this is the cloud's view of a batch of encrypted windows.
+    """
+    g = rng(seed)
+    out = np.empty((count, 2, len(q_primes), n), dtype=np.uint64)
+    for c in range(count):
+        for h in range(2):
+            out[c, h] = uniform_residues(g, q_primes, n)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# synthetic radar windows
+# ---------------------------------------------------------------------------
+class VitalWindow:
+    """Complex range profiles z[t, r] (F frames x R bins) of one window."""
+
+    def __init__(self, z, fs, target_bin, f_heart, f_resp):
+        self.z = z
+        self.fs = fs
+        self.target_bin = target_bin
+        self.f_heart = f_heart
+        self.f_resp = f_resp
+
+
+def vital_window(seed, frames=200, bins=64, fs=20.0, randomize_rates=False, sigma=0.05):
+    g = rng(seed)
+    t = np.arange(frames) / fs
+    r_star = int(g.integers(8, bins - 8))
+    if randomize_rates:
+        f_h = float(g.uniform(0.8, 2.0))
+        f_r = float(g.uniform(0.1, 0.5))
+    else:
+        f_h, f_r = 1.2, 0.25
+    ph_h, ph_r, ph0 = g.uniform(0, 2 * np.pi, size=3)
+    d = 0.5e-3 * np.sin(2 * np.pi * f_h * t + ph_h) + 4e-3 * np.sin(2 * np.pi * f_r * t + ph_r)
+    z = sigma * (g.normal(size=(frames, bins)) + 1j * g.normal(size=(frames, bins)))
+    z[:, r_star] += np.exp(1j * (ph0 + 4 * np.pi * d / LAMBDA_M))
+    return VitalWindow(z, fs, r_star, f_h, f_r)
