@@ -1,0 +1,284 @@
+/*
+ * mmfhe.h -- C ABI of the B300 (sm_103a) homomorphic evaluation library for
+ * the mmFHE cloud side: CKKS (RNS, hybrid key switching) evaluation of the
+ * paper's data-oblivious radar DSP kernel chains on batches of ciphertext
+ * windows.
+ *
+ * Problem statement followed (paper Sec. "System Design"): the cloud receives
+ * ciphertexts plus the public evaluation keys (rlk, gk), chains the fixed
+ * kernels K1..K7 over the ciphertexts, and returns encrypted results; the
+ * client alone decrypts.  The calls below are exactly that: create a context
+ * for a parameter set, load evaluation keys, load a plan (the public
+ * constants of a circuit), evaluate a batch of windows, synchronise.
+ *
+ * Conventions (apply to every call unless stated otherwise)
+ * ---------------------------------------------------------
+ *  - Status: every call returns MMFHE_OK (0) or a negative MMFHE_ERR_* code;
+ *    no C++ exception crosses the ABI.  mmfhe_last_error() gives a message.
+ *  - Rings: R_q = Z_q[X]/(X^N + 1), N = 2^log_n.  Q = q_0 ... q_L ("level l"
+ *    uses q_0..q_l, i.e. l+1 limbs), P = p_0 ... p_{K-1} (special primes).
+ *  - Boundary form: every polynomial crossing the ABI is in COEFFICIENT form,
+ *    limb-major, little-endian uint64, limb i holding residues in [0, q_i).
+ *    A ciphertext at level l is uint64[2][l+1][N] (c0 then c1; decrypts as
+ *    c0 + c1*s).  A batch of B ciphertexts is uint64[B][2][l+1][N].
+ *    A plaintext at level l is uint64[l+1][N].
+ *    A switching key is uint64[dnum][2][L+1+K][N]: digit j holds (b_j, a_j)
+ *    over q_0..q_L then p_0..p_{K-1}, with b_j = -a_j*s + e_j + P*Qt_j*s'.
+ *  - Memory: pointers may be host or device memory of the context's device
+ *    (detected with cudaPointerGetAttributes).  The caller owns all buffers
+ *    it passes; inputs are not modified unless stated.  The library owns
+ *    contexts, keys and plans until the matching destroy/unload call; it
+ *    copies every blob it is given, so the caller may free them on return.
+ *  - Streams: `stream` is a cudaStream_t (NULL = legacy default stream).
+ *    Calls that take a stream only enqueue work, except that host buffers are
+ *    copied synchronously with respect to the call (the call returns after
+ *    host outputs are written).  Calls on one context must use one stream at
+ *    a time (the context's scratch pool is stream-ordered); synchronise
+ *    before switching streams.  Use mmfhe_sync for a bounded wait.
+ *  - Alignment: device pointers must be 16-byte aligned.
+ *  - Thread safety: one context may be used by one host thread at a time.
+ */
+#ifndef MMFHE_H
+#define MMFHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t mmfhe_status;
+
+#define MMFHE_OK 0
+#define MMFHE_ERR_BAD_ARG (-1)        /* null pointer, size or value out of range */
+#define MMFHE_ERR_BAD_BLOB (-2)       /* malformed parameter set / key / constant */
+#define MMFHE_ERR_PARAM_MISMATCH (-3) /* object built for another context */
+#define MMFHE_ERR_LEVEL_MISMATCH (-4) /* operand levels do not fit the operation */
+#define MMFHE_ERR_OUT_OF_MEMORY (-5)  /* device allocation failed */
+#define MMFHE_ERR_CUDA (-6)           /* a CUDA runtime call failed (no device, launch error) */
+#define MMFHE_ERR_TIMEOUT (-7)        /* bounded wait expired; work is still queued */
+#define MMFHE_ERR_NOT_FOUND (-8)      /* missing Galois key / constant */
+#define MMFHE_ERR_BUSY (-9)           /* object in use */
+
+#define MMFHE_MAX_Q 32
+#define MMFHE_MAX_P 8
+
+/* ------------------------------------------------------------------------
+ * Parameters (paper Table 7: CKKS, N = 32768, depth 11, 128-bit classical
+ * security per the HE Standard; Delta = 2^40 vital, 2^50 gesture).
+ * ---------------------------------------------------------------------- */
+typedef struct mmfhe_params {
+    uint32_t log_n;            /* ring dimension N = 2^log_n, 10 <= log_n <= 16 */
+    uint32_t num_q;            /* L + 1, 1..MMFHE_MAX_Q */
+    uint32_t num_p;            /* K, 1..MMFHE_MAX_P */
+    uint32_t dnum;             /* key-switching digits; alpha = ceil(num_q/dnum) <= num_p required */
+    uint64_t q[MMFHE_MAX_Q];   /* q_0..q_L: distinct primes = 1 mod 2N, 2^20 < q < 2^61 */
+    uint64_t p[MMFHE_MAX_P];   /* p_0..p_{K-1}: same conditions, distinct from q */
+} mmfhe_params;
+
+/* Deterministic prime selection (host only, needs no GPU):
+ * q_0 = largest prime < 2^q0_bits with q = 1 mod 2N; q_1..q_L alternate
+ * largest-unused-below / smallest-unused-above 2^q_bits (below first);
+ * p_k = largest unused primes < 2^p_bits.  Errors: BAD_ARG. */
+mmfhe_status mmfhe_params_select(uint32_t log_n, uint32_t num_q, uint32_t q0_bits, uint32_t q_bits,
+                                 uint32_t num_p, uint32_t p_bits, uint32_t dnum, mmfhe_params *out);
+
+/* ------------------------------------------------------------------------
+ * Context: one parameter set on one device.  Builds the NTT twiddle tables,
+ * basis-conversion and rescale constants in device memory.
+ * params_size must be sizeof(mmfhe_params).  Errors: BAD_ARG, BAD_BLOB
+ * (non-prime / not 1 mod 2N / duplicate / out of range), CUDA (no device),
+ * OUT_OF_MEMORY.
+ * ---------------------------------------------------------------------- */
+typedef struct mmfhe_ctx mmfhe_ctx;
+mmfhe_status mmfhe_ctx_create(const mmfhe_params *params, size_t params_size, int device, mmfhe_ctx **out);
+mmfhe_status mmfhe_ctx_destroy(mmfhe_ctx *ctx);
+/* Message of the last failing call on ctx (ctx may be NULL: last failure of
+ * the calling thread).  The string stays valid until the next call. */
+const char *mmfhe_last_error(const mmfhe_ctx *ctx);
+/* Bounded wait for all work on `stream`: polls, returns TIMEOUT after
+ * timeout_ms without blocking further (the work stays queued). */
+mmfhe_status mmfhe_sync(mmfhe_ctx *ctx, void *stream, uint32_t timeout_ms);
+/* Number of kernels this library has launched on ctx since creation. */
+mmfhe_status mmfhe_launch_count(const mmfhe_ctx *ctx, uint64_t *out);
+/* Launch trace for auditing data obliviousness (Theorem 2: the execution
+ * trace depends only on public parameters).  enable != 0 clears the trace and
+ * starts recording one line "kernel grid(x,y,z) block(x,y,z)" per launch;
+ * enable == 0 stops.  mmfhe_trace_get copies up to capacity-1 bytes of the
+ * newline-separated trace into buf (NUL-terminated) and sets *length to the
+ * full length. */
+mmfhe_status mmfhe_trace_enable(mmfhe_ctx *ctx, int enable);
+mmfhe_status mmfhe_trace_get(const mmfhe_ctx *ctx, char *buf, size_t capacity, size_t *length);
+/* Per-kernel CUDA-event profile.  enable != 0 clears the profile and records
+ * a start/stop event pair around every subsequent launch (on the launch's
+ * stream); enable == 0 stops recording.  mmfhe_profile_get synchronises the
+ * recorded events and aggregates them by kernel name: up to `capacity`
+ * entries are written (names NUL-terminated, truncated to 31 chars);
+ * *count is the number of distinct kernels.  bytes = the launches'
+ * algorithmic bytes (every distinct word a launch must read or write once). */
+typedef struct mmfhe_kernel_stat {
+    char name[32];
+    uint64_t launches;
+    double total_ms;
+    double bytes;
+} mmfhe_kernel_stat;
+mmfhe_status mmfhe_profile_enable(mmfhe_ctx *ctx, int enable);
+mmfhe_status mmfhe_profile_get(mmfhe_ctx *ctx, mmfhe_kernel_stat *out, uint32_t capacity, uint32_t *count);
+
+/* ------------------------------------------------------------------------
+ * Evaluation keys (paper: rlk after every ct x ct product, one Galois key
+ * per rotation amount).  Keys are converted to the library's evaluation
+ * domain and stay resident in device memory until unloaded.
+ * ---------------------------------------------------------------------- */
+typedef struct mmfhe_keys mmfhe_keys;
+mmfhe_status mmfhe_keys_create(mmfhe_ctx *ctx, uint64_t user_id, mmfhe_keys **out);
+/* words: switching key from s^2 to s, layout above.  Errors: BAD_ARG. */
+mmfhe_status mmfhe_keys_set_relin(mmfhe_keys *keys, const uint64_t *words);
+/* Galois key for the left rotation Rot(x, k)[j] = x[(j + k) mod N/2], i.e.
+ * the automorphism X -> X^g, g = 5^(k mod N/2) mod 2N; switches s(X^g) to s. */
+mmfhe_status mmfhe_keys_set_galois(mmfhe_keys *keys, int32_t rotation, const uint64_t *words);
+mmfhe_status mmfhe_keys_unload(mmfhe_keys *keys);
+
+/* ------------------------------------------------------------------------
+ * Primitive operations (for composition and testing).  All take and return
+ * coefficient-form buffers, batched over `batch` ciphertexts of one level.
+ * Each call converts to the evaluation domain, runs, and converts back.
+ * Level errors: LEVEL_MISMATCH.  Missing key: NOT_FOUND.
+ * ---------------------------------------------------------------------- */
+/* Negacyclic NTT of `rows` rows of N words in place; row r is reduced mod the
+ * prime with index prime_idx[r] (0..num_q-1 = q_i, num_q..num_q+K-1 = p_k;
+ * prime_idx is a host array).  Forward output order is the library's
+ * evaluation order (row j holds a(psi^(2 brv(j) + 1))); inverse takes that
+ * order back to coefficients. */
+mmfhe_status mmfhe_ntt(mmfhe_ctx *ctx, uint64_t *rows, const uint32_t *prime_idx, size_t num_rows, int inverse, void *stream);
+/* out[r] = a[r] * b[r] in Z_q[X]/(X^N+1), coefficient form (at most 64 rows). */
+mmfhe_status mmfhe_poly_mul(mmfhe_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b,
+                            const uint32_t *prime_idx, size_t num_rows, void *stream);
+/* out = a + b (slot-wise add, depth free). */
+mmfhe_status mmfhe_ct_add(mmfhe_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t batch,
+                          uint32_t level, void *stream);
+/* out = ct * pt (pt shared by the batch), not rescaled. */
+mmfhe_status mmfhe_ct_mul_plain(mmfhe_ctx *ctx, uint64_t *out, const uint64_t *ct, const uint64_t *pt, size_t batch,
+                                uint32_t level, void *stream);
+/* out = relinearize(a (x) b): tensor product + key switch with rlk; not rescaled. */
+mmfhe_status mmfhe_ct_mul_relin(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out, const uint64_t *a,
+                                const uint64_t *b, size_t batch, uint32_t level, void *stream);
+/* out (level-1) = rescale(in): c_i <- (c_i - [c]_{q_l}^centered) * q_l^-1. */
+mmfhe_status mmfhe_ct_rescale(mmfhe_ctx *ctx, uint64_t *out, const uint64_t *in, size_t batch, uint32_t level,
+                              void *stream);
+/* out = Rot(in, k). */
+mmfhe_status mmfhe_ct_rotate(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out, const uint64_t *in, size_t batch,
+                             uint32_t level, int32_t k, void *stream);
+/* outs[i] = Rot(in, ks[i]) sharing one ModUp (hoisting); k = 0 copies. */
+mmfhe_status mmfhe_ct_rotate_hoisted(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *const *outs,
+                                     const uint64_t *in, size_t batch, uint32_t level, const int32_t *ks,
+                                     size_t num_k, void *stream);
+/* Digit decomposition + ModUp of d (uint64[batch][level+1][N]):
+ * out uint64[batch][beta][level+1+K][N] (coefficient form), beta = number of
+ * digits at this level; row order q_0..q_level, p_0..p_{K-1}. */
+mmfhe_status mmfhe_modup(mmfhe_ctx *ctx, uint64_t *out, const uint64_t *d, size_t batch, uint32_t level, void *stream);
+/* Key switch of d (uint64[batch][level+1][N]): out = uint64[batch][2][level+1][N]
+ * = ModDown(ModUp(d) . key).  which = 0: relinearization key; which = 1:
+ * Galois key of `rotation` (no automorphism applied). */
+mmfhe_status mmfhe_keyswitch(mmfhe_ctx *ctx, const mmfhe_keys *keys, int which, int32_t rotation, uint64_t *out,
+                             const uint64_t *d, size_t batch, uint32_t level, void *stream);
+/* Rotate-and-sum: x <- x + Rot(x, stride * 2^i) for i < log2(span). */
+mmfhe_status mmfhe_ct_rotsum(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out, const uint64_t *in, size_t batch,
+                             uint32_t level, int32_t stride, uint32_t span, void *stream);
+/* BSGS diagonal product: out = sum_g Rot(sum_b D'_{g,b} (.) Rot(in, b*stride), g*n1*stride)
+ * over the given diagonals delta = g*n1 + b (deltas[i], diags[i] = encoded
+ * pre-rotated diagonal uint64[level+1][N]); baby steps hoisted; not rescaled. */
+mmfhe_status mmfhe_ct_bsgs(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out, const uint64_t *in, size_t batch,
+                           uint32_t level, int32_t stride, uint32_t n1, const uint32_t *deltas,
+                           const uint64_t *const *diags, size_t num_diags, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Circuits (plans).  A plan holds a circuit's public configuration
+ * (Sec. "Leakage Profile": R, F, filter order, Taylor order, ...) and its
+ * encoded public constants (FIR taps, DFT rows, masks) resident on device.
+ * ---------------------------------------------------------------------- */
+#define MMFHE_CIRCUIT_FIR_DFT 1 /* 64-tap bandpass FIR + windowed fftshifted DFT on every bin */
+#define MMFHE_CIRCUIT_VITAL 2   /* vital-sign chain K1->K2 | K4->K5->K7->K3->|X|^2->sharpen->avg */
+
+typedef struct mmfhe_circuit_config {
+    uint32_t kind;             /* MMFHE_CIRCUIT_* */
+    uint32_t bins;             /* R range bins */
+    uint32_t frames;           /* F frames per window */
+    uint32_t fs_mhz;           /* frame rate in mHz */
+    uint32_t taps;             /* FIR taps */
+    uint32_t taylor_order;     /* 1 or 3 (VITAL) */
+    uint32_t num_bands;        /* FIR_DFT: 1; VITAL: 2 (respiration, heart) */
+    uint32_t band_lo_mhz[2];
+    uint32_t band_hi_mhz[2];
+    double dft_gain[2];        /* VITAL: public per-band DFT gains (both 0: defaults
+                                  30, 1 for third order; 1.5, 0.2 for first order) */
+} mmfhe_circuit_config;
+
+/* Constant tags of mmfhe_const_key.tag */
+#define MMFHE_CONST_IDX 1   /* side branch: bin-index vector of group `index` */
+#define MMFHE_CONST_ONE 2   /* side branch: ones vector of group `index` */
+#define MMFHE_CONST_FIR 3   /* FIR diagonal delta=`index` of band `band` (pre-rotated) */
+#define MMFHE_CONST_DRE 4   /* VITAL DFT real rows, diagonal `index`, band `band` */
+#define MMFHE_CONST_DIM 5   /* VITAL DFT imaginary rows */
+#define MMFHE_CONST_FW 6    /* frequency weights f_k (Hz) of band `band` */
+#define MMFHE_CONST_FONE 7  /* band indicator of band `band` */
+#define MMFHE_CONST_DFT_C 8  /* FIR_DFT: C = Re W diagonal `index` */
+#define MMFHE_CONST_DFT_S 9  /* FIR_DFT: S = Im W */
+#define MMFHE_CONST_DFT_MS 10 /* FIR_DFT: -S */
+
+typedef struct mmfhe_const_key {
+    uint32_t tag, band, index, level;
+} mmfhe_const_key;
+
+typedef struct mmfhe_plan mmfhe_plan;
+mmfhe_status mmfhe_plan_create(mmfhe_ctx *ctx, const mmfhe_circuit_config *cfg, size_t cfg_size, mmfhe_plan **out);
+mmfhe_status mmfhe_plan_destroy(mmfhe_plan *plan);
+/* The constants the circuit needs, in a fixed order (index 0..count-1). */
+mmfhe_status mmfhe_plan_num_consts(const mmfhe_plan *plan, uint32_t *count);
+mmfhe_status mmfhe_plan_const_key(const mmfhe_plan *plan, uint32_t i, mmfhe_const_key *out);
+/* Install pre-encoded constant i (coefficient form, uint64[level+1][N]). */
+mmfhe_status mmfhe_plan_set_const(mmfhe_plan *plan, uint32_t i, const uint64_t *words);
+/* Copy constant i back in coefficient form (uint64[level+1][N]); NOT_FOUND if unset. */
+mmfhe_status mmfhe_plan_get_const(const mmfhe_plan *plan, uint32_t i, uint64_t *words);
+/* Design and encode every constant with the library's own FP64 design
+ * (Hamming-windowed-sinc taps, Hann-windowed DFT rows) and encoder. */
+mmfhe_status mmfhe_plan_encode_consts(mmfhe_plan *plan);
+/* Rotation amounts whose Galois keys the plan needs (ascending, in [0, N/2)). */
+mmfhe_status mmfhe_plan_rotations(const mmfhe_plan *plan, int32_t *out, uint32_t capacity, uint32_t *count);
+/* Input/output shape: ciphertexts per window in and out, and the level of
+ * every output ciphertext (levels capacity 16).  Window input layout:
+ * uint64[n_in][2][L+1][N]; output: the n_out ciphertexts back to back, each
+ * uint64[2][level_i+1][N]. */
+mmfhe_status mmfhe_plan_io(const mmfhe_plan *plan, uint32_t *n_in, uint32_t *n_out, uint32_t *out_levels);
+
+/* Evaluate the plan's circuit on `batch` windows.  keys[w], in_cts[w] and
+ * out_cts[w] belong to window w; windows with the same keys object are
+ * evaluated together, every launch covering all of them.  Errors: BAD_ARG,
+ * NOT_FOUND (missing key/constant), CUDA, OUT_OF_MEMORY.  batch = 0 is a
+ * no-op. */
+mmfhe_status mmfhe_eval(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *const *keys,
+                        const uint64_t *const *in_cts, size_t batch, uint64_t *const *out_cts, void *stream);
+/* mmfhe_eval restricted to MMFHE_CIRCUIT_VITAL plans (paper Sec. "Example
+ * Pipelines", Encrypted Vital Signs; depth per Table 1).  Window inputs:
+ * stream 1 (K1) G groups x (Re, Im), then stream 2 (K4) G x (Re, Im), at the
+ * top level.  Outputs: num_r, den_r (target bin), num_RR, den_RR, num_HR,
+ * den_HR (frequency-weighted sums in Hz; BPM = 60 num/den). */
+mmfhe_status mmfhe_eval_vital(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *const *keys,
+                              const uint64_t *const *in_cts, size_t batch, uint64_t *const *out_cts, void *stream);
+
+/* ------------------------------------------------------------------------
+ * Host-side helpers (no GPU needed).
+ * ---------------------------------------------------------------------- */
+/* Batched-packing layout (Sec. "Packing", batched): values[F][R] (real) ->
+ * G slot vectors of N/2 doubles, slot(t, r) = t*R_c + r, F_pad = 2^ceil(log2 F),
+ * R_c = (N/2)/F_pad, G = ceil(R/R_c).  out must hold G*N/2 doubles. */
+mmfhe_status mmfhe_pack_window(uint32_t log_n, uint32_t frames, uint32_t bins, const double *values, double *out);
+/* Encode a real slot vector (N/2 doubles) at `scale` into uint64[level+1][N]
+ * (m = round(scale * tau^-1(z)), slot j <-> zeta^(5^j)). */
+mmfhe_status mmfhe_encode(const mmfhe_params *params, const double *slots, double scale, uint32_t level, uint64_t *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MMFHE_H */

@@ -1,0 +1,281 @@
+"""B300 (sm_103a) homomorphic evaluation of the mmFHE cloud-side kernel chain.
+
+Python binding of libmmfhe (include/mmfhe.h): RNS-CKKS key switching
+(batched NTT, ModUp/ModDown basis conversion, Galois automorphisms, the dnum
+key inner product, rescale, hoisted BSGS rotations) and the paper's
+vital-sign circuit, evaluated on batches of ciphertext windows on one GPU.
+The binding only marshals arguments; every operation runs in the library.
+"""
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CONST_TAGS, CircuitConfig, ConstKey, MmfheError, Params, check,
+                   ptr, ptr_array, stream_ptr)
+
+__all__ = ["Context", "Keys", "Plan", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
+           "Params", "CIRCUIT_FIR_DFT", "CIRCUIT_VITAL", "vital_config", "fir_dft_config", "fir_dft_params",
+           "vital_params"]
+
+
+def params_select(log_n, num_q, q0_bits, q_bits, num_p, p_bits, dnum):
+    """Deterministic prime chain (host only)."""
+    p = Params()
+    check(_lib.lib().mmfhe_params_select(log_n, num_q, q0_bits, q_bits, num_p, p_bits, dnum, ctypes.byref(p)))
+    return p
+
+
+def params_from_primes(log_n, q, p, dnum):
+    out = Params()
+    out.log_n, out.num_q, out.num_p, out.dnum = log_n, len(q), len(p), dnum
+    for i, x in enumerate(q):
+        out.q[i] = int(x)
+    for i, x in enumerate(p):
+        out.p[i] = int(x)
+    return out
+
+
+def fir_dft_params():
+    """N = 2^13, q_0 ~ 2^44 + 3 x 2^40, one 44-bit special prime, dnum = 4."""
+    return params_select(13, 4, 44, 40, 1, 44, 4)
+
+
+def vital_params():
+    """N = 2^15, depth 11 (q_0 60 bits + 11 x 40 bits), K = 4 x 60 bits, dnum = 3."""
+    return params_select(15, 12, 60, 40, 4, 60, 3)
+
+
+def encode(params, slots, scale, level):
+    """Encode N/2 real slots at `scale` into uint64[level+1][N] (host)."""
+    slots = np.ascontiguousarray(slots, dtype=np.float64)
+    out = np.empty((level + 1, 1 << params.log_n), dtype=np.uint64)
+    check(_lib.lib().mmfhe_encode(ctypes.byref(params), ptr(slots), float(scale), level, ptr(out)))
+    return out
+
+
+def pack_window(log_n, values):
+    """Batched-packing layout of a [F, R] real array into G slot vectors."""
+    values = np.ascontiguousarray(values, dtype=np.float64)
+    F, R = values.shape
+    n = 1 << (log_n - 1)
+    fp = 1
+    while fp < F:
+        fp <<= 1
+    G = -(-R // (n // fp))
+    out = np.empty((G, n), dtype=np.float64)
+    check(_lib.lib().mmfhe_pack_window(log_n, F, R, ptr(values), ptr(out)))
+    return out
+
+
+def vital_config(bins=256, frames=200, fs_mhz=20000, taps=64, taylor_order=3,
+                 bands_mhz=((100, 600), (800, 2500)), dft_gains=(0.0, 0.0)):
+    c = CircuitConfig()
+    c.kind, c.bins, c.frames, c.fs_mhz, c.taps, c.taylor_order = CIRCUIT_VITAL, bins, frames, fs_mhz, taps, taylor_order
+    c.num_bands = 2
+    for b in range(2):
+        c.band_lo_mhz[b], c.band_hi_mhz[b] = bands_mhz[b]
+        c.dft_gain[b] = dft_gains[b]
+    return c
+
+
+def fir_dft_config(bins=64, frames=200, fs_mhz=20000, taps=64, band_mhz=(800, 2500)):
+    c = CircuitConfig()
+    c.kind, c.bins, c.frames, c.fs_mhz, c.taps = CIRCUIT_FIR_DFT, bins, frames, fs_mhz, taps
+    c.num_bands = 1
+    c.band_lo_mhz[0], c.band_hi_mhz[0] = band_mhz
+    return c
+
+
+class Context:
+    """One parameter set on one CUDA device."""
+
+    def __init__(self, params, device=0):
+        self.params = params
+        self.n = 1 << params.log_n
+        self.L = params.num_q - 1
+        h = ctypes.c_void_p()
+        check(_lib.lib().mmfhe_ctx_create(ctypes.byref(params), ctypes.sizeof(Params), device, ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.lib().mmfhe_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _c(self, status):
+        check(status, self.h)
+
+    def sync(self, stream=None, timeout_ms=60000):
+        self._c(_lib.lib().mmfhe_sync(self.h, stream_ptr(stream), timeout_ms))
+
+    def launch_count(self):
+        v = ctypes.c_uint64()
+        self._c(_lib.lib().mmfhe_launch_count(self.h, ctypes.byref(v)))
+        return v.value
+
+    def trace(self, enable=None):
+        """Enable/disable the launch trace, or (enable=None) return it."""
+        if enable is not None:
+            self._c(_lib.lib().mmfhe_trace_enable(self.h, int(enable)))
+            return None
+        n = ctypes.c_size_t()
+        self._c(_lib.lib().mmfhe_trace_get(self.h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value + 1)
+        self._c(_lib.lib().mmfhe_trace_get(self.h, buf, n.value + 1, ctypes.byref(n)))
+        return buf.value.decode().splitlines()
+
+    def profile(self, enable=None):
+        """Enable/disable per-kernel event profiling, or (enable=None) return
+        {kernel: (launches, total_ms, algorithmic_bytes)}."""
+        if enable is not None:
+            self._c(_lib.lib().mmfhe_profile_enable(self.h, int(enable)))
+            return None
+        n = ctypes.c_uint32()
+        self._c(_lib.lib().mmfhe_profile_get(self.h, None, 0, ctypes.byref(n)))
+        arr = (_lib.KernelStat * max(1, n.value))()
+        self._c(_lib.lib().mmfhe_profile_get(self.h, arr, n.value, ctypes.byref(n)))
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].bytes) for i in range(n.value)}
+
+    def keys(self, user_id=0):
+        return Keys(self, user_id)
+
+    def plan(self, cfg):
+        return Plan(self, cfg)
+
+    # --- primitives (coefficient-form buffers) -----------------------------
+    def ntt(self, rows, prime_idx, inverse=False, stream=None):
+        pid = np.ascontiguousarray(prime_idx, dtype=np.uint32)
+        self._c(_lib.lib().mmfhe_ntt(self.h, ptr(rows), ptr(pid), len(pid), int(inverse), stream_ptr(stream)))
+
+    def poly_mul(self, out, a, b, prime_idx, stream=None):
+        pid = np.ascontiguousarray(prime_idx, dtype=np.uint32)
+        self._c(_lib.lib().mmfhe_poly_mul(self.h, ptr(out), ptr(a), ptr(b), ptr(pid), len(pid), stream_ptr(stream)))
+
+    def ct_add(self, out, a, b, batch, level, stream=None):
+        self._c(_lib.lib().mmfhe_ct_add(self.h, ptr(out), ptr(a), ptr(b), batch, level, stream_ptr(stream)))
+
+    def ct_mul_plain(self, out, ct, pt, batch, level, stream=None):
+        self._c(_lib.lib().mmfhe_ct_mul_plain(self.h, ptr(out), ptr(ct), ptr(pt), batch, level, stream_ptr(stream)))
+
+    def ct_mul_relin(self, keys, out, a, b, batch, level, stream=None):
+        self._c(_lib.lib().mmfhe_ct_mul_relin(self.h, keys.h, ptr(out), ptr(a), ptr(b), batch, level,
+                                              stream_ptr(stream)))
+
+    def ct_rescale(self, out, a, batch, level, stream=None):
+        self._c(_lib.lib().mmfhe_ct_rescale(self.h, ptr(out), ptr(a), batch, level, stream_ptr(stream)))
+
+    def ct_rotate(self, keys, out, a, batch, level, k, stream=None):
+        self._c(_lib.lib().mmfhe_ct_rotate(self.h, keys.h, ptr(out), ptr(a), batch, level, k, stream_ptr(stream)))
+
+    def ct_rotate_hoisted(self, keys, outs, a, batch, level, ks, stream=None):
+        ka = (ctypes.c_int32 * len(ks))(*ks)
+        self._c(_lib.lib().mmfhe_ct_rotate_hoisted(self.h, keys.h, ptr_array(outs), ptr(a), batch, level, ka, len(ks),
+                                                   stream_ptr(stream)))
+
+    def modup(self, out, d, batch, level, stream=None):
+        self._c(_lib.lib().mmfhe_modup(self.h, ptr(out), ptr(d), batch, level, stream_ptr(stream)))
+
+    def keyswitch(self, keys, out, d, batch, level, rotation=None, stream=None):
+        which, rot = (0, 0) if rotation is None else (1, rotation)
+        self._c(_lib.lib().mmfhe_keyswitch(self.h, keys.h, which, rot, ptr(out), ptr(d), batch, level,
+                                           stream_ptr(stream)))
+
+    def ct_rotsum(self, keys, out, a, batch, level, stride, span, stream=None):
+        self._c(_lib.lib().mmfhe_ct_rotsum(self.h, keys.h, ptr(out), ptr(a), batch, level, stride, span,
+                                           stream_ptr(stream)))
+
+    def ct_bsgs(self, keys, out, a, batch, level, stride, n1, deltas, diags, stream=None):
+        da = np.ascontiguousarray(deltas, dtype=np.uint32)
+        self._c(_lib.lib().mmfhe_ct_bsgs(self.h, keys.h, ptr(out), ptr(a), batch, level, stride, n1, ptr(da),
+                                         ptr_array(diags), len(diags), stream_ptr(stream)))
+
+    # --- circuits -------------------------------------------------------------
+    def eval(self, plan, keys, ins, outs, stream=None, vital=False):
+        """Evaluate `plan` on len(ins) windows; keys is one Keys or a list."""
+        B = len(ins)
+        kl = keys if isinstance(keys, (list, tuple)) else [keys] * B
+        karr = (ctypes.c_void_p * B)(*[k.h.value for k in kl])
+        f = _lib.lib().mmfhe_eval_vital if vital else _lib.lib().mmfhe_eval
+        self._c(f(self.h, plan.h, karr, ptr_array(ins), B, ptr_array(outs), stream_ptr(stream)))
+
+
+class Keys:
+    """Evaluation keys of one user, resident in device memory."""
+
+    def __init__(self, ctx, user_id=0):
+        self.ctx = ctx
+        h = ctypes.c_void_p()
+        ctx._c(_lib.lib().mmfhe_keys_create(ctx.h, user_id, ctypes.byref(h)))
+        self.h = h
+
+    def set_relin(self, words):
+        self.ctx._c(_lib.lib().mmfhe_keys_set_relin(self.h, ptr(words)))
+
+    def set_galois(self, k, words):
+        self.ctx._c(_lib.lib().mmfhe_keys_set_galois(self.h, int(k), ptr(words)))
+
+    def unload(self):
+        if getattr(self, "h", None):
+            _lib.lib().mmfhe_keys_unload(self.h)
+            self.h = None
+
+
+class Plan:
+    """A circuit's public configuration and encoded constants."""
+
+    def __init__(self, ctx, cfg):
+        self.ctx = ctx
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        ctx._c(_lib.lib().mmfhe_plan_create(ctx.h, ctypes.byref(cfg), ctypes.sizeof(CircuitConfig), ctypes.byref(h)))
+        self.h = h
+
+    def num_consts(self):
+        v = ctypes.c_uint32()
+        self.ctx._c(_lib.lib().mmfhe_plan_num_consts(self.h, ctypes.byref(v)))
+        return v.value
+
+    def const_key(self, i):
+        k = ConstKey()
+        self.ctx._c(_lib.lib().mmfhe_plan_const_key(self.h, i, ctypes.byref(k)))
+        return (CONST_TAGS[k.tag], k.band, k.index, k.level)
+
+    def const_keys(self):
+        return [self.const_key(i) for i in range(self.num_consts())]
+
+    def set_const(self, i, words):
+        self.ctx._c(_lib.lib().mmfhe_plan_set_const(self.h, i, ptr(words)))
+
+    def get_const(self, i):
+        level = self.const_key(i)[3]
+        out = np.empty((level + 1, self.ctx.n), dtype=np.uint64)
+        self.ctx._c(_lib.lib().mmfhe_plan_get_const(self.h, i, ptr(out)))
+        return out
+
+    def encode_consts(self):
+        self.ctx._c(_lib.lib().mmfhe_plan_encode_consts(self.h))
+
+    def rotations(self):
+        n = ctypes.c_uint32()
+        self.ctx._c(_lib.lib().mmfhe_plan_rotations(self.h, None, 0, ctypes.byref(n)))
+        arr = (ctypes.c_int32 * max(1, n.value))()
+        self.ctx._c(_lib.lib().mmfhe_plan_rotations(self.h, arr, n.value, ctypes.byref(n)))
+        return [arr[i] for i in range(n.value)]
+
+    def io(self):
+        ni, no = ctypes.c_uint32(), ctypes.c_uint32()
+        lv = (ctypes.c_uint32 * 16)()
+        self.ctx._c(_lib.lib().mmfhe_plan_io(self.h, ctypes.byref(ni), ctypes.byref(no), lv))
+        return ni.value, no.value, [lv[i] for i in range(no.value)]
+
+    def destroy(self):
+        if getattr(self, "h", None):
+            _lib.lib().mmfhe_plan_destroy(self.h)
+            self.h = None

@@ -1,0 +1,163 @@
+"""ctypes binding of libmmfhe (argument marshalling only).
+
+Every function here forwards to the C ABI declared in include/mmfhe.h; all
+arithmetic runs in the library's CUDA kernels.  Buffers may be numpy arrays
+(host memory) or torch tensors (host or CUDA memory).  A missing shared
+object raises immediately: there is no fallback path.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+SO_PATH = os.path.join(_HERE, "libmmfhe.so")
+
+MAX_Q, MAX_P = 32, 8
+
+OK = 0
+ERRORS = {
+    -1: "BAD_ARG", -2: "BAD_BLOB", -3: "PARAM_MISMATCH", -4: "LEVEL_MISMATCH", -5: "OUT_OF_MEMORY",
+    -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "BUSY",
+}
+CIRCUIT_FIR_DFT, CIRCUIT_VITAL = 1, 2
+CONST_TAGS = {1: "idx", 2: "one", 3: "fir", 4: "dre", 5: "dim", 6: "fw", 7: "fone", 8: "dft_c", 9: "dft_s",
+              10: "dft_ms"}
+
+
+class MmfheError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+        self.name = ERRORS.get(code, "?")
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("log_n", ctypes.c_uint32), ("num_q", ctypes.c_uint32), ("num_p", ctypes.c_uint32),
+                ("dnum", ctypes.c_uint32), ("q", ctypes.c_uint64 * MAX_Q), ("p", ctypes.c_uint64 * MAX_P)]
+
+    @property
+    def primes_q(self):
+        return [int(self.q[i]) for i in range(self.num_q)]
+
+    @property
+    def primes_p(self):
+        return [int(self.p[i]) for i in range(self.num_p)]
+
+
+class CircuitConfig(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_uint32), ("bins", ctypes.c_uint32), ("frames", ctypes.c_uint32),
+                ("fs_mhz", ctypes.c_uint32), ("taps", ctypes.c_uint32), ("taylor_order", ctypes.c_uint32),
+                ("num_bands", ctypes.c_uint32), ("band_lo_mhz", ctypes.c_uint32 * 2),
+                ("band_hi_mhz", ctypes.c_uint32 * 2), ("dft_gain", ctypes.c_double * 2)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+class ConstKey(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint32), ("band", ctypes.c_uint32), ("index", ctypes.c_uint32),
+                ("level", ctypes.c_uint32)]
+
+
+_VP = ctypes.c_void_p
+_U32, _U64, _I32, _SZ, _INT = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int32, ctypes.c_size_t, ctypes.c_int
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+_SIGS = {
+    "mmfhe_params_select": [_U32, _U32, _U32, _U32, _U32, _U32, _U32, ctypes.POINTER(Params)],
+    "mmfhe_ctx_create": [ctypes.POINTER(Params), _SZ, _INT, _PP],
+    "mmfhe_ctx_destroy": [_VP],
+    "mmfhe_sync": [_VP, _VP, _U32],
+    "mmfhe_launch_count": [_VP, ctypes.POINTER(_U64)],
+    "mmfhe_trace_enable": [_VP, _INT],
+    "mmfhe_trace_get": [_VP, ctypes.c_char_p, _SZ, ctypes.POINTER(_SZ)],
+    "mmfhe_profile_enable": [_VP, _INT],
+    "mmfhe_profile_get": [_VP, _VP, _U32, ctypes.POINTER(_U32)],
+    "mmfhe_keys_create": [_VP, _U64, _PP],
+    "mmfhe_keys_set_relin": [_VP, _VP],
+    "mmfhe_keys_set_galois": [_VP, _I32, _VP],
+    "mmfhe_keys_unload": [_VP],
+    "mmfhe_ntt": [_VP, _VP, _VP, _SZ, _INT, _VP],
+    "mmfhe_poly_mul": [_VP, _VP, _VP, _VP, _VP, _SZ, _VP],
+    "mmfhe_ct_add": [_VP, _VP, _VP, _VP, _SZ, _U32, _VP],
+    "mmfhe_ct_mul_plain": [_VP, _VP, _VP, _VP, _SZ, _U32, _VP],
+    "mmfhe_ct_mul_relin": [_VP, _VP, _VP, _VP, _VP, _SZ, _U32, _VP],
+    "mmfhe_ct_rescale": [_VP, _VP, _VP, _SZ, _U32, _VP],
+    "mmfhe_ct_rotate": [_VP, _VP, _VP, _VP, _SZ, _U32, _I32, _VP],
+    "mmfhe_ct_rotate_hoisted": [_VP, _VP, _VP, _VP, _SZ, _U32, _VP, _SZ, _VP],
+    "mmfhe_modup": [_VP, _VP, _VP, _SZ, _U32, _VP],
+    "mmfhe_keyswitch": [_VP, _VP, _INT, _I32, _VP, _VP, _SZ, _U32, _VP],
+    "mmfhe_ct_rotsum": [_VP, _VP, _VP, _VP, _SZ, _U32, _I32, _U32, _VP],
+    "mmfhe_ct_bsgs": [_VP, _VP, _VP, _VP, _SZ, _U32, _I32, _U32, _VP, _VP, _SZ, _VP],
+    "mmfhe_plan_create": [_VP, ctypes.POINTER(CircuitConfig), _SZ, _PP],
+    "mmfhe_plan_destroy": [_VP],
+    "mmfhe_plan_num_consts": [_VP, ctypes.POINTER(_U32)],
+    "mmfhe_plan_const_key": [_VP, _U32, ctypes.POINTER(ConstKey)],
+    "mmfhe_plan_set_const": [_VP, _U32, _VP],
+    "mmfhe_plan_get_const": [_VP, _U32, _VP],
+    "mmfhe_plan_encode_consts": [_VP],
+    "mmfhe_plan_rotations": [_VP, _VP, _U32, ctypes.POINTER(_U32)],
+    "mmfhe_plan_io": [_VP, ctypes.POINTER(_U32), ctypes.POINTER(_U32), _VP],
+    "mmfhe_eval": [_VP, _VP, _VP, _VP, _SZ, _VP, _VP],
+    "mmfhe_eval_vital": [_VP, _VP, _VP, _VP, _SZ, _VP, _VP],
+    "mmfhe_pack_window": [_U32, _U32, _U32, _VP, _VP],
+    "mmfhe_encode": [ctypes.POINTER(Params), _VP, ctypes.c_double, _U32, _VP],
+}
+
+_lib = None
+
+
+def lib():
+    """Load libmmfhe.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(SO_PATH):
+            raise ImportError("libmmfhe.so not built: run paper_2603_22437_b300/build.py")
+        L = ctypes.CDLL(SO_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int32
+        L.mmfhe_last_error.argtypes = [_VP]
+        L.mmfhe_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def check(status, ctx=None):
+    if status != OK:
+        msg = lib().mmfhe_last_error(ctx)
+        raise MmfheError(status, msg.decode() if msg else "")
+
+
+def ptr(x):
+    """Data pointer of a numpy array or torch tensor (contiguous)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"], "array must be C-contiguous"
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "tensor must be contiguous"
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError("unsupported buffer type %r" % type(x))
+
+
+def ptr_array(xs):
+    arr = (ctypes.c_void_p * len(xs))()
+    for i, x in enumerate(xs):
+        arr[i] = ptr(x)
+    return arr
+
+
+def stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)

@@ -1,0 +1,500 @@
+// Plans (public circuit configuration + encoded constants) and the two
+// circuits: the small FIR+DFT instance and the vital-sign chain.
+//
+// Vital chain (paper Sec. "Example Pipelines", Encrypted Vital Signs, with the
+// depth accounting of Table 1), L0 = top level:
+//   side branch  K1: p = Re^2 + Im^2 (L0-1), E = rotate-sum over frames;
+//                K2: w = E^2 (L0-2); num = sum idx (.) w, den = sum 1 (.) w
+//                (L0-3), rotate-sum over the bins of a frame.
+//   main chain   K4: p (L0-1), m = p^2 (L0-2), I = sum_c m Re, Q = sum_c m Im
+//                (L0-3), rotate-sum over bins; K5: FIR per band, BSGS with
+//                hoisted baby steps shared by both bands (L0-4); K7:
+//                y = Qf If' - If Qf', x = If If' + Qf Qf' (L0-5), third order
+//                u = 3x^2 - y^2 (L0-6), 3 dphi = y u (L0-7); K3 narrowband
+//                DFT (+1); |X|^2 (+2); merge bands + square (+3); frequency
+//                weights and band indicator (+4), rotate-sum.
+// Slot layout: slot(t, r) = t R_c + r, F_pad = 2^ceil(log2 F), R_c = N/2 / F_pad.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <set>
+#include <tuple>
+
+#include "circuits.h"
+#include "engine.h"
+#include "hostmath.h"
+
+namespace mmfhe {
+
+static int next_pow2(int x) {
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+static int ilog2(int x) {
+    int r = 0;
+    while ((1 << r) < x) r++;
+    return r;
+}
+
+static std::pair<int, int> bsgs_split(int ndiag) {
+    int D = next_pow2(ndiag);
+    int lg = ilog2(D);
+    int n1 = 1 << ((lg + 1) / 2);
+    return {n1, D / n1};
+}
+
+std::vector<int> band_bins(int frames, int fs_mhz, int lo_mhz, int hi_mhz) {
+    std::vector<int> out;
+    for (int k = 0; k <= frames / 2; k++) {
+        long long kf = (long long)k * fs_mhz;
+        if ((long long)lo_mhz * frames <= kf && kf <= (long long)hi_mhz * frames) out.push_back(k);
+    }
+    return out;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 public constants (the library's own design)
+// ---------------------------------------------------------------------------
+static double sinc(double x) {
+    if (x == 0.0) return 1.0;
+    double px = M_PI * x;
+    return std::sin(px) / px;
+}
+
+// Hamming-windowed-sinc bandpass, unit gain at the band centre.
+std::vector<double> fir_bandpass(int taps, double f_lo, double f_hi, double fs) {
+    std::vector<double> h(taps);
+    double M = (taps - 1) / 2.0, a = f_lo / fs, b = f_hi / fs, fc = 0.5 * (a + b), g = 0.0;
+    for (int k = 0; k < taps; k++) {
+        double m = k - M;
+        double w = 0.54 - 0.46 * std::cos(2 * M_PI * k / (taps - 1));
+        h[k] = (2 * b * sinc(2 * b * m) - 2 * a * sinc(2 * a * m)) * w;
+        g += h[k] * std::cos(2 * M_PI * fc * m);
+    }
+    for (double &x : h) x /= g;
+    return h;
+}
+
+static double hann(int n, int N) { return 0.5 - 0.5 * std::cos(2 * M_PI * n / (N - 1)); }
+
+// ---------------------------------------------------------------------------
+// encoder: m = round_half_away(scale * tau^-1(z)), slot j <-> zeta^(5^j)
+// ---------------------------------------------------------------------------
+static void fft_inplace(std::vector<std::complex<double>> &a) {
+    const size_t n = a.size();
+    for (size_t i = 1, j = 0; i < n; i++) {
+        size_t bit = n >> 1;
+        for (; j & bit; bit >>= 1) j ^= bit;
+        j ^= bit;
+        if (i < j) std::swap(a[i], a[j]);
+    }
+    for (size_t len = 2; len <= n; len <<= 1) {
+        double ang = -2 * M_PI / (double)len;
+        for (size_t i = 0; i < n; i += len) {
+            for (size_t j = 0; j < len / 2; j++) {
+                std::complex<double> w(std::cos(ang * j), std::sin(ang * j));
+                std::complex<double> u = a[i + j], v = a[i + j + len / 2] * w;
+                a[i + j] = u + v;
+                a[i + j + len / 2] = u - v;
+            }
+        }
+    }
+}
+
+void encode_slots(const mmfhe_params &p, const double *slots, double scale, int level, uint64_t *out) {
+    const uint32_t N = 1u << p.log_n, n = N / 2;
+    std::vector<std::complex<double>> Z(N);
+    uint64_t e = 1;
+    for (uint32_t j = 0; j < n; j++) {
+        Z[(e - 1) / 2] = slots[j];
+        Z[(2 * N - e - 1) / 2] = slots[j];   // real slots: the conjugate equals the value
+        e = (e * 5) % (2 * N);
+    }
+    fft_inplace(Z);
+    for (uint32_t k = 0; k < N; k++) {
+        std::complex<double> tw(std::cos(-M_PI * k / N), std::sin(-M_PI * k / N));
+        double m = (tw * Z[k]).real() / N * scale;
+        double r = m >= 0 ? std::floor(m + 0.5) : -std::floor(-m + 0.5);
+        if (std::fabs(r) >= 9.2e18) throw Error(MMFHE_ERR_BAD_ARG, "encode: value too large for the scale");
+        int64_t c = (int64_t)r;
+        for (int i = 0; i <= level; i++) {
+            uint64_t q = p.q[i];
+            uint64_t a = c >= 0 ? (uint64_t)c % q : (q - ((uint64_t)(-(c + 1)) + 1) % q) % q;
+            out[(size_t)i * N + k] = a;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plan structure
+// ---------------------------------------------------------------------------
+static void check_cfg(const Context &c, const mmfhe_circuit_config &cfg) {
+    if (cfg.kind != MMFHE_CIRCUIT_FIR_DFT && cfg.kind != MMFHE_CIRCUIT_VITAL) throw Error(MMFHE_ERR_BAD_ARG, "unknown circuit kind");
+    if (cfg.frames < 2 || cfg.bins < 1 || cfg.taps < 1 || cfg.fs_mhz < 1) throw Error(MMFHE_ERR_BAD_ARG, "bad circuit sizes");
+    int fpad = next_pow2((int)cfg.frames);
+    if ((uint32_t)fpad > c.n / 2) throw Error(MMFHE_ERR_BAD_ARG, "window longer than the slot count");
+    if (cfg.taps > cfg.frames) throw Error(MMFHE_ERR_BAD_ARG, "more taps than frames");
+    if (cfg.kind == MMFHE_CIRCUIT_VITAL && !(cfg.taylor_order == 1 || cfg.taylor_order == 3))
+        throw Error(MMFHE_ERR_BAD_ARG, "taylor_order must be 1 or 3");
+    uint32_t nb = cfg.kind == MMFHE_CIRCUIT_VITAL ? 2 : 1;
+    if (cfg.num_bands != nb) throw Error(MMFHE_ERR_BAD_ARG, "wrong number of bands");
+}
+
+uint64_t key_of(const mmfhe_const_key &k) {
+    return ((uint64_t)k.tag << 48) | ((uint64_t)k.band << 40) | (uint64_t)k.index;
+}
+
+Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg) {
+    check_cfg(c, cfg);
+    std::unique_ptr<Plan> p(new Plan());
+    p->ctx = &c;
+    p->cfg = cfg;
+    p->f_pad = next_pow2((int)cfg.frames);
+    p->r_c = (int)(c.n / 2) / p->f_pad;
+    p->groups = ((int)cfg.bins + p->r_c - 1) / p->r_c;
+    std::tie(p->n1_fir, p->n2_fir) = bsgs_split((int)cfg.taps);
+    std::tie(p->n1_dft, p->n2_dft) = bsgs_split(p->f_pad);
+    const int L = c.L, Fp = p->f_pad, F = (int)cfg.frames;
+    auto add = [&](uint32_t tag, uint32_t band, uint32_t idx, int level) {
+        if (level < 0) throw Error(MMFHE_ERR_BAD_ARG, "not enough levels in the parameter set for this circuit");
+        p->keys.push_back(mmfhe_const_key{tag, band, idx, (uint32_t)level});
+    };
+    std::set<int32_t> rots;
+    auto rot = [&](int32_t k) { rots.insert(norm_rot(c, k)); };
+    if (cfg.kind == MMFHE_CIRCUIT_FIR_DFT) {
+        if (L < 2) throw Error(MMFHE_ERR_BAD_ARG, "FIR+DFT needs at least 3 Q primes");
+        for (uint32_t k = 0; k < cfg.taps; k++) add(MMFHE_CONST_FIR, 0, k, L);
+        std::set<int> present;
+        for (int d = 0; d < F; d++)
+            for (int n = 0; n < F; n++) present.insert(((n - d) % Fp + Fp) % Fp);
+        p->dft_deltas[0].assign(present.begin(), present.end());
+        for (uint32_t tag : {MMFHE_CONST_DFT_C, MMFHE_CONST_DFT_S, MMFHE_CONST_DFT_MS})
+            for (int d : p->dft_deltas[0]) add(tag, 0, d, L - 1);
+        for (int b = 1; b < p->n1_fir; b++) rot(-b * p->r_c);
+        for (int g = 1; g < p->n2_fir; g++) rot(-g * p->n1_fir * p->r_c);
+        for (int d : p->dft_deltas[0]) {
+            if (d % p->n1_dft) rot((d % p->n1_dft) * p->r_c);
+            if (d / p->n1_dft) rot((d / p->n1_dft) * p->n1_dft * p->r_c);
+        }
+        p->n_in = 2 * p->groups;
+        for (int g = 0; g < p->groups; g++) {
+            p->out_levels.push_back(L - 2);
+            p->out_levels.push_back(L - 2);
+        }
+    } else {
+        const int lv_side = L - 2, lv_fir = L - 3;
+        const int lv_dphi = cfg.taylor_order == 3 ? L - 7 : L - 5;
+        const int lv_final = lv_dphi - 3;
+        if (lv_final < 1) throw Error(MMFHE_ERR_BAD_ARG, "not enough levels for the vital chain");
+        p->lv_side = lv_side;
+        p->lv_fir = lv_fir;
+        p->lv_dphi = lv_dphi;
+        p->lv_final = lv_final;
+        for (int g = 0; g < p->groups; g++) {
+            add(MMFHE_CONST_IDX, 0, g, lv_side);
+            add(MMFHE_CONST_ONE, 0, g, lv_side);
+        }
+        for (int b = 0; b < 2; b++)
+            for (uint32_t k = 0; k < cfg.taps; k++) add(MMFHE_CONST_FIR, b, k, lv_fir);
+        for (int b = 0; b < 2; b++) {
+            p->bands[b] = band_bins(F, (int)cfg.fs_mhz, (int)cfg.band_lo_mhz[b], (int)cfg.band_hi_mhz[b]);
+            if (p->bands[b].empty()) throw Error(MMFHE_ERR_BAD_ARG, "empty frequency band");
+            if (p->bands[b].back() >= Fp) throw Error(MMFHE_ERR_BAD_ARG, "band beyond window");
+            std::set<int> present;
+            for (int k : p->bands[b])
+                for (int t = 0; t < F; t++) present.insert(((t - k) % Fp + Fp) % Fp);
+            p->dft_deltas[b].assign(present.begin(), present.end());
+        }
+        for (int b = 0; b < 2; b++)
+            for (uint32_t tag : {MMFHE_CONST_DRE, MMFHE_CONST_DIM})
+                for (int d : p->dft_deltas[b]) add(tag, b, d, lv_dphi);
+        for (int b = 0; b < 2; b++) {
+            add(MMFHE_CONST_FW, b, 0, lv_final);
+            add(MMFHE_CONST_FONE, b, 0, lv_final);
+        }
+        for (int i = 0; (1 << i) < Fp; i++) rot(p->r_c << i);
+        for (int i = 0; (1 << i) < p->r_c; i++) rot(1 << i);
+        for (int b = 1; b < p->n1_fir; b++) rot(-b * p->r_c);
+        for (int g = 1; g < p->n2_fir; g++) rot(-g * p->n1_fir * p->r_c);
+        rot(-p->r_c);
+        for (int b = 0; b < 2; b++) {
+            for (int d : p->dft_deltas[b]) {
+                if (d % p->n1_dft) rot((d % p->n1_dft) * p->r_c);
+                if (d / p->n1_dft) rot((d / p->n1_dft) * p->n1_dft * p->r_c);
+            }
+            p->span[b] = next_pow2(p->bands[b].back() + 1);
+            for (int i = 0; (1 << i) < p->span[b]; i++) rot(p->r_c << i);
+        }
+        p->n_in = 4 * p->groups;
+        p->out_levels = {lv_side - 1, lv_side - 1, lv_final - 1, lv_final - 1, lv_final - 1, lv_final - 1};
+    }
+    rots.erase(0);
+    p->rotations.assign(rots.begin(), rots.end());
+    p->consts.resize(p->keys.size());
+    for (size_t i = 0; i < p->keys.size(); i++) p->index[key_of(p->keys[i])] = (int)i;
+    return p.release();
+}
+
+const PtDev &plan_const(const Plan &p, uint32_t tag, uint32_t band, uint32_t idx) {
+    auto it = p.index.find(((uint64_t)tag << 48) | ((uint64_t)band << 40) | idx);
+    if (it == p.index.end()) throw Error(MMFHE_ERR_NOT_FOUND, "plan constant missing");
+    const PtDev &pt = p.consts[it->second];
+    if (!pt.buf.get()) throw Error(MMFHE_ERR_NOT_FOUND, "plan constant " + std::to_string(it->second) + " not set");
+    return pt;
+}
+
+void plan_set_const(Plan &p, uint32_t i, const uint64_t *words_host_or_dev, cudaStream_t st) {
+    Context &c = *p.ctx;
+    if (i >= p.keys.size()) throw Error(MMFHE_ERR_BAD_ARG, "constant index out of range");
+    const int level = (int)p.keys[i].level;
+    PtDev pt = pt_new(c, level, (double)c.primes[level]);
+    CK(cudaMemcpyAsync(pt.buf.get(), words_host_or_dev, (size_t)(level + 1) * c.n * 8, cudaMemcpyDefault, st));
+    ntt_q_blocks(c, pt.buf.get(), 1, level + 1, false, st);
+    p.consts[i] = std::move(pt);
+}
+
+// slot vector of constant k with the library's own FP64 design
+static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) {
+    const Context &c = *p.ctx;
+    const mmfhe_circuit_config &cfg = p.cfg;
+    const int n = (int)c.n / 2, Rc = p.r_c, Fp = p.f_pad, F = (int)cfg.frames;
+    std::vector<double> v(n, 0.0), out(n, 0.0);
+    auto slot = [&](int t, int r) { return t * Rc + r; };
+    auto prerot = [&](int g, int n1, int stride) {
+        // D' = Rot(D, -g n1 stride): out[j] = v[(j - g n1 stride) mod n]
+        long long sh = (long long)g * n1 * stride;
+        for (int j = 0; j < n; j++) out[j] = v[(int)((((j - sh) % n) + n) % n)];
+        return out;
+    };
+    const double fs = cfg.fs_mhz / 1000.0;
+    switch (k.tag) {
+    case MMFHE_CONST_IDX:
+    case MMFHE_CONST_ONE:
+        for (int r = 0; r < Rc; r++) {
+            int gb = (int)k.index * Rc + r;
+            if (gb < (int)cfg.bins) v[slot(0, r)] = k.tag == MMFHE_CONST_IDX ? (double)gb : 1.0;
+        }
+        return v;
+    case MMFHE_CONST_FIR: {
+        int b = (int)k.band, kk = (int)k.index;
+        std::vector<double> h = fir_bandpass((int)cfg.taps, cfg.band_lo_mhz[b] / 1000.0, cfg.band_hi_mhz[b] / 1000.0, fs);
+        int rmax = cfg.kind == MMFHE_CIRCUIT_VITAL ? 1 : Rc;
+        for (int t = kk; t < F; t++)
+            for (int r = 0; r < rmax; r++) v[slot(t, r)] = h[kk];
+        return prerot(kk / p.n1_fir, p.n1_fir, -Rc);
+    }
+    case MMFHE_CONST_DRE:
+    case MMFHE_CONST_DIM: {
+        int b = (int)k.band, d = (int)k.index;
+        double gain = cfg.dft_gain[b] * (cfg.taylor_order == 3 ? 1.0 / 3.0 : 1.0);
+        for (int kk : p.bands[b]) {
+            int t = (kk + d) % Fp;   // diag_d[row kk] = M[kk, kk + d]
+            if (t < F) {
+                double ang = 2 * M_PI * kk * t / F;
+                v[slot(kk, 0)] = gain * hann(t, F) * (k.tag == MMFHE_CONST_DRE ? std::cos(ang) : -std::sin(ang));
+            }
+        }
+        return prerot(d / p.n1_dft, p.n1_dft, Rc);
+    }
+    case MMFHE_CONST_DFT_C:
+    case MMFHE_CONST_DFT_S:
+    case MMFHE_CONST_DFT_MS: {
+        int d = (int)k.index, D = F;
+        for (int row = 0; row < D; row++) {
+            int col = (row + d) % Fp;
+            if (col >= D) continue;
+            int sig = (row + D / 2) % D;
+            double ang = -2 * M_PI * sig * col / D;
+            double w = hann(col, D);
+            double val = k.tag == MMFHE_CONST_DFT_C ? w * std::cos(ang) : w * std::sin(ang);
+            if (k.tag == MMFHE_CONST_DFT_MS) val = -val;
+            for (int r = 0; r < Rc; r++) v[slot(row, r)] = val;
+        }
+        return prerot(d / p.n1_dft, p.n1_dft, Rc);
+    }
+    case MMFHE_CONST_FW:
+    case MMFHE_CONST_FONE:
+        for (int kk : p.bands[k.band]) v[slot(kk, 0)] = k.tag == MMFHE_CONST_FW ? kk * fs / F : 1.0;
+        return v;
+    }
+    throw Error(MMFHE_ERR_BAD_ARG, "unknown constant tag");
+}
+
+void plan_encode_consts(Plan &p, cudaStream_t st) {
+    Context &c = *p.ctx;
+    std::vector<uint64_t> words;
+    for (size_t i = 0; i < p.keys.size(); i++) {
+        const mmfhe_const_key &k = p.keys[i];
+        std::vector<double> v = const_slots(p, k);
+        words.assign((size_t)(k.level + 1) * c.n, 0);
+        encode_slots(c.params, v.data(), (double)c.primes[k.level], (int)k.level, words.data());
+        plan_set_const(p, (uint32_t)i, words.data(), st);
+        CK(cudaStreamSynchronize(st));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// circuit executors (all windows of the batch in every launch)
+// ---------------------------------------------------------------------------
+static CtB square_sum(Context &c, const Keys &k, const std::vector<const CtB *> &xs, cudaStream_t st) {
+    TensorB t = tensor_new(c, xs[0]->B, xs[0]->level);
+    for (size_t i = 0; i < xs.size(); i++) tensor_acc(c, t, *xs[i], *xs[i], 1, i == 0, st);
+    return relin(c, k, t, st);
+}
+
+static std::vector<CtB> run_fir_dft(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st) {
+    const int Rc = p.r_c;
+    std::vector<CtB> out;
+    std::vector<int> all_fir(p.n1_fir), rot_fir(p.n1_fir);
+    for (int b = 0; b < p.n1_fir; b++) { all_fir[b] = b; rot_fir[b] = -b * Rc; }
+    BsgsTerm fir;
+    for (uint32_t kk = 0; kk < p.cfg.taps; kk++) fir.diags.push_back({(int)kk, &plan_const(p, MMFHE_CONST_FIR, 0, kk)});
+    fir.baby_idx = all_fir;
+    std::vector<int> all_dft(p.n1_dft), rot_dft(p.n1_dft);
+    for (int b = 0; b < p.n1_dft; b++) { all_dft[b] = b; rot_dft[b] = b * Rc; }
+    for (int g = 0; g < p.groups; g++) {
+        CtB vf[2];
+        for (int part = 0; part < 2; part++) {
+            std::vector<CtB> babies = rotate_hoisted(c, k, in[2 * g + part], rot_fir, st);
+            BsgsTerm t = fir;
+            t.baby = &babies;
+            vf[part] = rescale(c, bsgs(c, k, {t}, p.n1_fir, -Rc, st), st);
+        }
+        std::vector<CtB> bre = rotate_hoisted(c, k, vf[0], rot_dft, st);
+        std::vector<CtB> bim = rotate_hoisted(c, k, vf[1], rot_dft, st);
+        auto term = [&](const std::vector<CtB> *bb, uint32_t tag) {
+            BsgsTerm t;
+            t.baby = bb;
+            t.baby_idx = all_dft;
+            for (int d : p.dft_deltas[0]) t.diags.push_back({d, &plan_const(p, tag, 0, d)});
+            return t;
+        };
+        out.push_back(rescale(c, bsgs(c, k, {term(&bre, MMFHE_CONST_DFT_C), term(&bim, MMFHE_CONST_DFT_MS)}, p.n1_dft, Rc, st), st));
+        out.push_back(rescale(c, bsgs(c, k, {term(&bre, MMFHE_CONST_DFT_S), term(&bim, MMFHE_CONST_DFT_C)}, p.n1_dft, Rc, st), st));
+    }
+    return out;
+}
+
+static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st) {
+    const int G = p.groups, Rc = p.r_c, Fp = p.f_pad;
+    const int B = in[0].B;
+    // ---- side branch: K1, K2 ----
+    std::vector<CtB> w;
+    for (int g = 0; g < G; g++) {
+        CtB pp = rescale(c, square_sum(c, k, {&in[2 * g], &in[2 * g + 1]}, st), st);
+        CtB E = rotsum(c, k, pp, Rc, (uint32_t)Fp, st);
+        w.push_back(rescale(c, square_sum(c, k, {&E}, st), st));
+    }
+    const PtDev &idx0 = plan_const(p, MMFHE_CONST_IDX, 0, 0);
+    CtB num = ct_new(c, B, w[0].level, w[0].scale * idx0.scale);
+    CtB den = ct_new(c, B, w[0].level, w[0].scale * idx0.scale);
+    for (int g = 0; g < G; g++) {
+        ct_mul_plain(c, num, w[g], plan_const(p, MMFHE_CONST_IDX, 0, g), g > 0, st);
+        ct_mul_plain(c, den, w[g], plan_const(p, MMFHE_CONST_ONE, 0, g), g > 0, st);
+    }
+    w.clear();
+    CtB num_r = rotsum(c, k, rescale(c, num, st), 1, (uint32_t)Rc, st);
+    CtB den_r = rotsum(c, k, rescale(c, den, st), 1, (uint32_t)Rc, st);
+    // ---- K4 soft I/Q ----
+    std::vector<CtB> m;
+    for (int g = 0; g < G; g++) {
+        const CtB &re = in[2 * G + 2 * g], &im = in[2 * G + 2 * g + 1];
+        CtB pp = rescale(c, square_sum(c, k, {&re, &im}, st), st);
+        m.push_back(rescale(c, square_sum(c, k, {&pp}, st), st));
+    }
+    const int lv = m[0].level;
+    CtB iq[2];
+    for (int part = 0; part < 2; part++) {
+        TensorB t = tensor_new(c, B, lv);
+        for (int g = 0; g < G; g++) {
+            CtB x = ct_drop(c, in[2 * G + 2 * g + part], lv, st);
+            tensor_acc(c, t, m[g], x, 1, g == 0, st);
+        }
+        iq[part] = rotsum(c, k, rescale(c, relin(c, k, t, st), st), 1, (uint32_t)Rc, st);
+    }
+    m.clear();
+    // ---- K5 FIR (hoisted babies shared by both bands) + K7 ----
+    std::vector<int> idx_fir(p.n1_fir), rot_fir(p.n1_fir);
+    for (int b = 0; b < p.n1_fir; b++) { idx_fir[b] = b; rot_fir[b] = -b * Rc; }
+    std::vector<CtB> bI = rotate_hoisted(c, k, iq[0], rot_fir, st);
+    std::vector<CtB> bQ = rotate_hoisted(c, k, iq[1], rot_fir, st);
+    CtB dphi[2];
+    for (int band = 0; band < 2; band++) {
+        BsgsTerm t;
+        t.baby_idx = idx_fir;
+        for (uint32_t kk = 0; kk < p.cfg.taps; kk++) t.diags.push_back({(int)kk, &plan_const(p, MMFHE_CONST_FIR, band, kk)});
+        t.baby = &bI;
+        CtB If = rescale(c, bsgs(c, k, {t}, p.n1_fir, -Rc, st), st);
+        t.baby = &bQ;
+        CtB Qf = rescale(c, bsgs(c, k, {t}, p.n1_fir, -Rc, st), st);
+        CtB If1 = rotate(c, k, If, -Rc, st);
+        CtB Qf1 = rotate(c, k, Qf, -Rc, st);
+        TensorB ty = tensor_new(c, B, If.level);
+        tensor_acc(c, ty, Qf, If1, 1, true, st);
+        tensor_acc(c, ty, If, Qf1, -1, false, st);
+        CtB y = rescale(c, relin(c, k, ty, st), st);
+        TensorB tx = tensor_new(c, B, If.level);
+        tensor_acc(c, tx, If, If1, 1, true, st);
+        tensor_acc(c, tx, Qf, Qf1, 1, false, st);
+        CtB x = rescale(c, relin(c, k, tx, st), st);
+        if (p.cfg.taylor_order == 3) {
+            TensorB tu = tensor_new(c, B, x.level);
+            tensor_acc(c, tu, x, x, 3, true, st);
+            tensor_acc(c, tu, y, y, -1, false, st);
+            CtB u = rescale(c, relin(c, k, tu, st), st);
+            CtB yd = ct_drop(c, y, u.level, st);
+            TensorB tp = tensor_new(c, B, u.level);
+            tensor_acc(c, tp, yd, u, 1, true, st);
+            dphi[band] = rescale(c, relin(c, k, tp, st), st);
+        } else {
+            dphi[band] = std::move(y);
+        }
+    }
+    bI.clear();
+    bQ.clear();
+    // ---- K3 narrowband DFT, |X|^2 ----
+    CtB power[2];
+    for (int band = 0; band < 2; band++) {
+        std::set<int> need;
+        for (int d : p.dft_deltas[band]) need.insert(d % p.n1_dft);
+        std::vector<int> idx(need.begin(), need.end());
+        std::vector<int32_t> rr;
+        for (int b : idx) rr.push_back(b * Rc);
+        std::vector<CtB> hs = rotate_hoisted(c, k, dphi[band], rr, st);
+        CtB X[2];
+        for (int part = 0; part < 2; part++) {
+            BsgsTerm t;
+            t.baby = &hs;
+            t.baby_idx = idx;
+            uint32_t tag = part == 0 ? MMFHE_CONST_DRE : MMFHE_CONST_DIM;
+            for (int d : p.dft_deltas[band]) t.diags.push_back({d, &plan_const(p, tag, band, d)});
+            X[part] = rescale(c, bsgs(c, k, {t}, p.n1_dft, Rc, st), st);
+        }
+        power[band] = rescale(c, square_sum(c, k, {&X[0], &X[1]}, st), st);
+    }
+    // ---- merge + sharpen, weighted frequency average ----
+    ct_addsub(c, power[0], power[0], power[1], false, st);
+    CtB S = rescale(c, square_sum(c, k, {&power[0]}, st), st);
+    std::vector<CtB> out;
+    out.push_back(std::move(num_r));
+    out.push_back(std::move(den_r));
+    for (int band = 0; band < 2; band++) {
+        for (uint32_t tag : {MMFHE_CONST_FW, MMFHE_CONST_FONE}) {
+            const PtDev &pt = plan_const(p, tag, band, 0);
+            CtB t = ct_new(c, B, S.level, S.scale * pt.scale);
+            ct_mul_plain(c, t, S, pt, false, st);
+            out.push_back(rotsum(c, k, rescale(c, t, st), Rc, (uint32_t)p.span[band], st));
+        }
+    }
+    return out;
+}
+
+std::vector<CtB> run_plan(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st) {
+    if (p.cfg.kind == MMFHE_CIRCUIT_FIR_DFT) return run_fir_dft(c, p, k, in, st);
+    return run_vital(c, p, k, in, st);
+}
+
+}  // namespace mmfhe

@@ -1,0 +1,265 @@
+// Homomorphic operations on device ciphertext batches (evaluation domain).
+//
+// Key switching is hybrid (dnum digits of alpha primes): ModUp of the digit
+// (iNTT, FastBConv to the other Q_l * P primes, NTT), inner product with the
+// switching key, ModDown (iNTT of the P rows, centered FastBConv P -> Q, NTT,
+// subtract and multiply by P^-1).  A rotation is the hoisted schedule of a
+// one-element set: the Galois automorphism is applied to the ModUp digits
+// inside the key inner product and to c0 inside the ModDown combine.
+#include <algorithm>
+#include <map>
+
+#include "engine.h"
+#include "hostmath.h"
+
+namespace mmfhe {
+
+PidList pids_q(int nl) {
+    PidList p{};
+    for (int i = 0; i < nl && i < MAXROWMAP; i++) p.pid[i] = (uint8_t)i;
+    return p;
+}
+
+int32_t norm_rot(const Context &c, int32_t k) {
+    int32_t n2 = (int32_t)(c.n / 2);
+    int32_t r = k % n2;
+    return r < 0 ? r + n2 : r;
+}
+
+uint32_t galois_elt(const Context &c, int32_t k) {
+    return (uint32_t)hm::powmod(5, (uint64_t)norm_rot(c, k), 2ull * c.n);
+}
+
+CtB ct_new(Context &c, int B, int level, double scale) {
+    CtB r;
+    r.B = B;
+    r.level = level;
+    r.scale = scale;
+    r.buf = Buf(c.pool.get(), (size_t)B * c.ct_words(level));
+    return r;
+}
+
+PtDev pt_new(Context &c, int level, double scale) {
+    PtDev p;
+    p.level = level;
+    p.scale = scale;
+    p.buf = Buf(c.pool.get(), (size_t)(level + 1) * c.n);
+    return p;
+}
+
+static std::vector<int> iota_pids(int nl) {
+    std::vector<int> v(nl);
+    for (int i = 0; i < nl; i++) v[i] = i;
+    return v;
+}
+
+void ntt_q_blocks(Context &c, uint64_t *base, size_t blocks, int nl, bool inverse, cudaStream_t st) {
+    RowsView v{base, make_map(nl, nl, iota_pids(nl)), blocks * nl};
+    launch_ntt(c, v, v, inverse, st);
+}
+
+void ct_addsub(Context &c, CtB &out, const CtB &a, const CtB &b, bool sub, cudaStream_t st) {
+    if (a.level != b.level || a.B != b.B) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "add: operand levels differ");
+    k_launch_addsub(c, out.ptr(), a.ptr(), b.ptr(), (size_t)a.B * 2 * (a.level + 1), pids_q(a.level + 1),
+                    a.level + 1, sub, st);
+}
+
+void ct_mul_plain(Context &c, CtB &out, const CtB &a, const PtDev &pt, bool acc, cudaStream_t st) {
+    if (a.level != pt.level) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "mul_plain: level mismatch");
+    k_launch_mul_plain(c, out.ptr(), a.ptr(), pt.buf.get(), (size_t)a.B * 2 * (a.level + 1), pids_q(a.level + 1),
+                       a.level + 1, acc, st);
+}
+
+void ct_mul_int(Context &c, CtB &out, const CtB &a, long long k, cudaStream_t st) {
+    k_launch_mul_int(c, out.ptr(), a.ptr(), (size_t)a.B * 2 * (a.level + 1), pids_q(a.level + 1), a.level + 1, k, st);
+}
+
+CtB ct_copy(Context &c, const CtB &a, cudaStream_t st) {
+    CtB r = ct_new(c, a.B, a.level, a.scale);
+    CK(cudaMemcpyAsync(r.ptr(), a.ptr(), (size_t)a.B * c.ct_words(a.level) * 8, cudaMemcpyDeviceToDevice, st));
+    return r;
+}
+
+CtB ct_drop(Context &c, const CtB &a, int level, cudaStream_t st) {
+    if (level > a.level || level < 0) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "drop: bad level");
+    if (level == a.level) return ct_copy(c, a, st);
+    CtB r = ct_new(c, a.B, level, a.scale);
+    int nl = level + 1;
+    RowsView src{a.ptr(), make_map(nl, a.level + 1, iota_pids(nl)), (size_t)a.B * 2 * nl};
+    RowsView dst{r.ptr(), make_map(nl, nl, iota_pids(nl)), (size_t)a.B * 2 * nl};
+    launch_copy_rows(c, src, dst, st);
+    return r;
+}
+
+TensorB tensor_new(Context &c, int B, int level) {
+    TensorB t;
+    t.B = B;
+    t.level = level;
+    t.buf = Buf(c.pool.get(), (size_t)B * 3 * (level + 1) * c.n);
+    return t;
+}
+
+void tensor_acc(Context &c, TensorB &t, const CtB &a, const CtB &b, long long coef, bool init, cudaStream_t st) {
+    if (a.level != b.level || a.level != t.level || a.B != t.B || b.B != t.B)
+        throw Error(MMFHE_ERR_LEVEL_MISMATCH, "tensor: level mismatch");
+    if (init) t.scale = a.scale * b.scale;
+    k_launch_tensor(c, t.buf.get(), a.ptr(), b.ptr(), t.B, t.level, coef, !init, st);
+}
+
+DigitsB modup(Context &c, const uint64_t *d_eval, size_t block_stride_rows, int B, int level, cudaStream_t st) {
+    const int nl = level + 1, nre = level + 1 + c.num_p;
+    const LevelConsts &lc = c.lv[level];
+    DigitsB dg;
+    dg.B = B;
+    dg.level = level;
+    dg.beta = lc.beta;
+    dg.buf = Buf(c.pool.get(), (size_t)B * lc.beta * nre * c.n);
+    Buf coef(c.pool.get(), (size_t)B * nl * c.n);
+    RowsView src{const_cast<uint64_t *>(d_eval), make_map(nl, (uint32_t)block_stride_rows, iota_pids(nl)), (size_t)B * nl};
+    RowsView dst{coef.get(), make_map(nl, nl, iota_pids(nl)), (size_t)B * nl};
+    launch_ntt(c, src, dst, true, st);
+    k_launch_modup_bconv(c, dg.buf.get(), coef.get(), d_eval, block_stride_rows * c.n, B, level, modup_consts(c, level),
+                         st);
+    // forward NTT of the converted rows (a digit's own rows are already in the evaluation domain)
+    for (int j = 0; j < lc.beta; j++) {
+        std::vector<int> pids(nre);
+        for (int t = 0; t < nre; t++) {
+            bool own = t <= level && t >= lc.digits[j].front() && t <= lc.digits[j].back();
+            pids[t] = own ? -1 : (t <= level ? t : c.num_q + (t - level - 1));
+        }
+        RowsView v{dg.buf.get() + (size_t)j * nre * c.n, make_map(nre, lc.beta * nre, pids), (size_t)B * nre};
+        launch_ntt(c, v, v, false, st);
+    }
+    return dg;
+}
+
+CtB keyswitch_moddown(Context &c, const DigitsB &dg, const uint64_t *key, uint32_t galois, const uint64_t *add0,
+                      const uint64_t *add1, size_t add_stride_words, double scale, cudaStream_t st) {
+    const int level = dg.level, B = dg.B, nl = level + 1, nre = level + 1 + c.num_p;
+    Buf u(c.pool.get(), (size_t)B * 2 * nre * c.n);
+    k_launch_keyip(c, u.get(), dg.buf.get(), key, B, level, dg.beta, galois, st);
+    std::vector<int> pids(nre, -1);
+    for (int k = 0; k < c.num_p; k++) pids[nl + k] = c.num_q + k;
+    RowsView pv{u.get(), make_map(nre, nre, pids), (size_t)B * 2 * nre};
+    launch_ntt(c, pv, pv, true, st);
+    Buf v(c.pool.get(), (size_t)B * 2 * nl * c.n);
+    ModDownConsts dc = moddown_consts(c);
+    k_launch_moddown_bconv(c, v.get(), u.get(), B, level, dc, st);
+    ntt_q_blocks(c, v.get(), (size_t)B * 2, nl, false, st);
+    CtB out = ct_new(c, B, level, scale);
+    k_launch_moddown_combine(c, out.ptr(), u.get(), v.get(), add0, add1, add_stride_words, galois, B, level, dc, st);
+    return out;
+}
+
+CtB relin(Context &c, const Keys &k, const TensorB &t, cudaStream_t st) {
+    if (!k.rlk.get()) throw Error(MMFHE_ERR_NOT_FOUND, "relinearization key not loaded");
+    const int nl = t.level + 1;
+    const uint64_t *base = t.buf.get();
+    DigitsB dg = modup(c, base + (size_t)2 * nl * c.n, (size_t)3 * nl, t.B, t.level, st);
+    return keyswitch_moddown(c, dg, k.rlk.get(), 1, base, base + (size_t)nl * c.n, (size_t)3 * nl * c.n, t.scale, st);
+}
+
+CtB rescale(Context &c, const CtB &a, cudaStream_t st) {
+    const int l = a.level;
+    if (l < 1) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "rescale at level 0");
+    const int B = a.B;
+    Buf last(c.pool.get(), (size_t)B * 2 * c.n);
+    RowsView src{a.ptr() + (size_t)l * c.n, make_map(1, l + 1, {l}), (size_t)B * 2};
+    RowsView dst{last.get(), make_map(1, 1, {l}), (size_t)B * 2};
+    launch_ntt(c, src, dst, true, st);
+    Buf tmp(c.pool.get(), (size_t)B * 2 * l * c.n);
+    RescaleConsts rc = rescale_consts(c, l);
+    k_launch_rescale_spread(c, tmp.get(), last.get(), B, l, rc, st);
+    ntt_q_blocks(c, tmp.get(), (size_t)B * 2, l, false, st);
+    CtB out = ct_new(c, B, l - 1, a.scale / (double)c.primes[l]);
+    k_launch_rescale_combine(c, out.ptr(), a.ptr(), tmp.get(), B, l, rc, st);
+    return out;
+}
+
+const uint64_t *galois_key(const Keys &k, int32_t rot) {
+    auto it = k.gk.find(rot);
+    if (it == k.gk.end()) throw Error(MMFHE_ERR_NOT_FOUND, "Galois key for rotation " + std::to_string(rot) + " not loaded");
+    return it->second.get();
+}
+
+std::vector<CtB> rotate_hoisted(Context &c, const Keys &k, const CtB &a, const std::vector<int32_t> &rots,
+                                cudaStream_t st) {
+    std::vector<CtB> out;
+    out.reserve(rots.size());
+    bool any = false;
+    for (int32_t r : rots) {
+        int32_t nr = norm_rot(c, r);
+        if (nr) {
+            galois_key(k, nr);   // fail before any work if a key is missing
+            any = true;
+        }
+    }
+    DigitsB dg;
+    const int nl = a.level + 1;
+    if (any) dg = modup(c, a.ptr() + (size_t)nl * c.n, (size_t)2 * nl, a.B, a.level, st);
+    for (int32_t r : rots) {
+        int32_t nr = norm_rot(c, r);
+        if (nr == 0) {
+            out.push_back(ct_copy(c, a, st));
+            continue;
+        }
+        out.push_back(keyswitch_moddown(c, dg, galois_key(k, nr), galois_elt(c, nr), a.ptr(), nullptr,
+                                        (size_t)2 * nl * c.n, a.scale, st));
+    }
+    return out;
+}
+
+CtB rotate(Context &c, const Keys &k, const CtB &a, int32_t rot, cudaStream_t st) {
+    std::vector<CtB> v = rotate_hoisted(c, k, a, {rot}, st);
+    return std::move(v[0]);
+}
+
+CtB rotsum(Context &c, const Keys &k, const CtB &a, int32_t stride, uint32_t span, cudaStream_t st) {
+    CtB x = ct_copy(c, a, st);
+    for (uint32_t s = 1; s < span; s <<= 1) {
+        CtB r = rotate(c, k, x, stride * (int32_t)s, st);
+        ct_addsub(c, x, x, r, false, st);
+    }
+    return x;
+}
+
+CtB bsgs(Context &c, const Keys &k, const std::vector<BsgsTerm> &terms, int n1, int32_t stride, cudaStream_t st) {
+    struct Item { const CtB *baby; const PtDev *pt; };
+    std::map<int, std::vector<Item>> groups;   // giant step g = delta / n1 -> products
+    int level = -1, B = 0;
+    double scale = 0;
+    for (const BsgsTerm &t : terms) {
+        std::map<int, int> pos;
+        for (size_t i = 0; i < t.baby_idx.size(); i++) pos[t.baby_idx[i]] = (int)i;
+        for (const auto &d : t.diags) {
+            auto it = pos.find(d.first % n1);
+            if (it == pos.end()) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: missing baby step");
+            const CtB *bb = &(*t.baby)[it->second];
+            groups[d.first / n1].push_back(Item{bb, d.second});
+            level = bb->level;
+            B = bb->B;
+            scale = bb->scale * d.second->scale;
+        }
+    }
+    if (groups.empty()) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: no diagonals");
+    CtB acc;
+    bool have = false;
+    for (auto &kv : groups) {
+        CtB inner = ct_new(c, B, level, scale);
+        bool first = true;
+        for (const Item &it : kv.second) {
+            ct_mul_plain(c, inner, *it.baby, *it.pt, !first, st);
+            first = false;
+        }
+        if (kv.first != 0) inner = rotate(c, k, inner, kv.first * n1 * stride, st);
+        if (!have) {
+            acc = std::move(inner);
+            have = true;
+        } else {
+            ct_addsub(c, acc, acc, inner, false, st);
+        }
+    }
+    return acc;
+}
+
+}  // namespace mmfhe

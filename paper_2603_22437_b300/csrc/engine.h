@@ -1,0 +1,61 @@
+// Homomorphic operations on device ciphertext batches (evaluation domain).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "internal.h"
+#include "kernels.h"
+
+namespace mmfhe {
+
+ModUpConsts modup_consts(const Context &c, int level);
+ModDownConsts moddown_consts(const Context &c);
+RescaleConsts rescale_consts(const Context &c, int level);
+
+PidList pids_q(int nl);
+uint32_t galois_elt(const Context &c, int32_t k);
+int32_t norm_rot(const Context &c, int32_t k);
+
+CtB ct_new(Context &c, int B, int level, double scale);
+PtDev pt_new(Context &c, int level, double scale);
+// in-place NTT (inverse=false) / iNTT of `blocks` contiguous blocks of nl Q-limbs
+void ntt_q_blocks(Context &c, uint64_t *base, size_t blocks, int nl, bool inverse, cudaStream_t st);
+
+void ct_addsub(Context &c, CtB &out, const CtB &a, const CtB &b, bool sub, cudaStream_t st);
+void ct_mul_plain(Context &c, CtB &out, const CtB &a, const PtDev &pt, bool acc, cudaStream_t st);
+void ct_mul_int(Context &c, CtB &out, const CtB &a, long long k, cudaStream_t st);
+CtB ct_copy(Context &c, const CtB &a, cudaStream_t st);
+CtB ct_drop(Context &c, const CtB &a, int level, cudaStream_t st);
+
+TensorB tensor_new(Context &c, int B, int level);
+// t (+)= coef * (a (x) b); first call with init = true
+void tensor_acc(Context &c, TensorB &t, const CtB &a, const CtB &b, long long coef, bool init, cudaStream_t st);
+CtB relin(Context &c, const Keys &k, const TensorB &t, cudaStream_t st);
+CtB rescale(Context &c, const CtB &a, cudaStream_t st);
+
+// ModUp of d (B windows, rows q_0..q_level, window stride block_stride_rows):
+// digits in the evaluation domain.
+DigitsB modup(Context &c, const uint64_t *d_eval, size_t block_stride_rows, int B, int level, cudaStream_t st);
+// ModDown(digits . key); `key` = device key in evaluation domain; galois != 1
+// applies the automorphism to the digits; add0/add1 optional addends (add0
+// read through the same automorphism).
+CtB keyswitch_moddown(Context &c, const DigitsB &dg, const uint64_t *key, uint32_t galois, const uint64_t *add0,
+                      const uint64_t *add1, size_t add_stride_words, double scale, cudaStream_t st);
+const uint64_t *galois_key(const Keys &k, int32_t rot);
+
+CtB rotate(Context &c, const Keys &k, const CtB &a, int32_t rot, cudaStream_t st);
+std::vector<CtB> rotate_hoisted(Context &c, const Keys &k, const CtB &a, const std::vector<int32_t> &rots,
+                                cudaStream_t st);
+CtB rotsum(Context &c, const Keys &k, const CtB &a, int32_t stride, uint32_t span, cudaStream_t st);
+
+// One BSGS operand: baby rotations of an input (baby[i] = Rot(x, baby_idx[i] * stride))
+// and the diagonals it is multiplied with, keyed by delta = g*n1 + b.
+struct BsgsTerm {
+    const std::vector<CtB> *baby = nullptr;
+    std::vector<int> baby_idx;
+    std::vector<std::pair<int, const PtDev *>> diags;   // (delta, pre-rotated diagonal)
+};
+CtB bsgs(Context &c, const Keys &k, const std::vector<BsgsTerm> &terms, int n1, int32_t stride, cudaStream_t st);
+
+}  // namespace mmfhe

@@ -1,0 +1,212 @@
+// Internal structures of the mmfhe library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "mmfhe.h"
+
+namespace mmfhe {
+
+constexpr int MAXPRIMES = MMFHE_MAX_Q + MMFHE_MAX_P;   // prime ids: 0..num_q-1 = q_i, num_q.. = p_k
+constexpr int MAXROWMAP = 64;
+constexpr uint8_t SKIP = 0xFF;
+
+// Error carrying an ABI status code; caught at the ABI boundary.
+struct Error : std::runtime_error {
+    mmfhe_status code;
+    Error(mmfhe_status c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+void cuda_check(cudaError_t e, const char *what);
+#define CK(x) ::mmfhe::cuda_check((x), #x)
+
+// Moduli passed by value to kernels (constant-bank resident).
+struct ModTab {
+    uint64_t q[MAXPRIMES];
+    uint64_t mu[MAXPRIMES];
+    uint32_t k[MAXPRIMES];
+};
+
+// Row addressing of a launch: row r lives at base + (r / period * block_stride
+// + r % period) * N and is reduced mod prime pid[r % period] (SKIP = untouched).
+struct RowMap {
+    uint32_t period;
+    uint32_t block_stride;   // in rows
+    uint8_t pid[MAXROWMAP];
+};
+
+// Twiddle tables (device): [prime id][N], forward psi^brv(i) and inverse
+// psi^-brv(i) with Shoup companions; n_inv per prime with companion.
+struct Twiddles {
+    const uint64_t *fw, *fw_sh, *iw, *iw_sh;
+    const uint64_t *ninv, *ninv_sh;
+};
+
+// ---------------------------------------------------------------------------
+// device memory pool (caching, by exact size; stream-ordered reuse)
+// ---------------------------------------------------------------------------
+class Pool {
+public:
+    explicit Pool(int device) : device_(device) {}
+    ~Pool();
+    uint64_t *get(size_t words);
+    void put(uint64_t *p, size_t words);
+    size_t bytes_held() const { return held_; }
+    void trim();
+
+private:
+    int device_;
+    std::multimap<size_t, uint64_t *> free_;
+    size_t held_ = 0;
+};
+
+// Pooled device buffer (RAII).
+class Buf {
+public:
+    Buf() = default;
+    Buf(Pool *pool, size_t words) : pool_(pool), words_(words), p_(words ? pool->get(words) : nullptr) {}
+    ~Buf() { release(); }
+    Buf(Buf &&o) noexcept { *this = std::move(o); }
+    Buf &operator=(Buf &&o) noexcept {
+        if (this != &o) {
+            release();
+            pool_ = o.pool_; words_ = o.words_; p_ = o.p_;
+            o.p_ = nullptr; o.words_ = 0;
+        }
+        return *this;
+    }
+    Buf(const Buf &) = delete;
+    Buf &operator=(const Buf &) = delete;
+    uint64_t *get() const { return p_; }
+    size_t words() const { return words_; }
+    void release() {
+        if (p_ && pool_) pool_->put(p_, words_);
+        p_ = nullptr; words_ = 0;
+    }
+
+private:
+    Pool *pool_ = nullptr;
+    size_t words_ = 0;
+    uint64_t *p_ = nullptr;
+};
+
+// Per-level basis-conversion constants (device).
+struct LevelConsts {
+    int level;
+    int beta;                        // digits at this level
+    std::vector<std::vector<int>> digits;
+    // ModUp: for digit j, source u (< alpha), target row t (< level+1+K):
+    //  inv[j][u] = (Qhat_{j,u})^-1 mod q_{D_j[u]} (+ Shoup),
+    //  m[j][u][t] = Qhat_{j,u} mod prime(t) (+ Shoup)
+    uint64_t *d_up_inv = nullptr, *d_up_inv_sh = nullptr;
+    uint64_t *d_up_m = nullptr, *d_up_m_sh = nullptr;
+    // rescale by q_level: qinv[i] = q_level^-1 mod q_i, qmod[i] = q_level mod q_i
+    uint64_t *d_rs_qinv = nullptr, *d_rs_qinv_sh = nullptr, *d_rs_qmod = nullptr;
+};
+
+struct Context {
+    int device = 0;
+    mmfhe_params params{};
+    int logn = 0;
+    uint32_t n = 0;
+    int num_q = 0, num_p = 0, dnum = 0, alpha = 0;
+    int L = 0;
+    std::vector<uint64_t> primes;    // by prime id
+    ModTab mods{};
+    uint64_t *d_tw = nullptr;        // 4 * np * N words
+    uint64_t *d_ninv = nullptr;      // 2 * np words
+    Twiddles tw{};
+    // ModDown constants: pinv[k] = Phat_k^-1 mod p_k, phat[k][i] = Phat_k mod q_i,
+    // pmod[i] = P mod q_i, Pinv[i] = P^-1 mod q_i (with Shoup companions)
+    uint64_t *d_dn_pinv = nullptr, *d_dn_pinv_sh = nullptr;
+    uint64_t *d_dn_phat = nullptr, *d_dn_phat_sh = nullptr;
+    uint64_t *d_dn_pmod = nullptr, *d_dn_pmod_sh = nullptr, *d_dn_Pinv = nullptr, *d_dn_Pinv_sh = nullptr;
+    std::vector<LevelConsts> lv;     // per level 0..L
+    std::unique_ptr<Pool> pool;
+    uint64_t launches = 0;
+    std::string last_error;
+    std::vector<void *> owned;       // cudaMalloc'd tables
+    // optional launch trace (kernel name + shape) for the data-obliviousness test
+    bool tracing = false;
+    std::vector<std::string> trace;
+    // optional per-launch CUDA-event profile: (name, start, stop, algorithmic bytes)
+    bool profiling = false;
+    struct ProfRec {
+        const char *name;
+        cudaEvent_t start, stop;
+        double bytes;
+    };
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> event_pool;
+    size_t event_next = 0;
+
+    size_t ct_words(int level) const { return 2ull * (level + 1) * n; }
+};
+
+// ---------------------------------------------------------------------------
+// device ciphertext batch (evaluation domain), layout [B][2][level+1][N]
+// ---------------------------------------------------------------------------
+struct CtB {
+    Buf buf;
+    int B = 0;
+    int level = -1;
+    double scale = 0.0;
+    uint64_t *ptr() const { return buf.get(); }
+};
+
+// Degree-2 tensor batch: [B][3][level+1][N] (d0, d1, d2).
+struct TensorB {
+    Buf buf;
+    int B = 0;
+    int level = -1;
+    double scale = 0.0;
+};
+
+// ModUp digits [B][beta][level+1+K][N], evaluation domain.
+struct DigitsB {
+    Buf buf;
+    int B = 0;
+    int level = -1;
+    int beta = 0;
+};
+
+// Plaintext on device (evaluation domain), [level+1][N].
+struct PtDev {
+    Buf buf;
+    int level = -1;
+    double scale = 0.0;
+};
+
+struct Keys {
+    Context *ctx = nullptr;
+    uint64_t user = 0;
+    Buf rlk;                                   // [dnum][2][L+1+K][N] eval
+    std::map<int32_t, Buf> gk;                 // rotation (mod N/2) -> key
+};
+
+// ---------------------------------------------------------------------------
+// launchers (ntt.cu)
+// ---------------------------------------------------------------------------
+struct RowsView {
+    uint64_t *base;
+    RowMap map;
+    size_t rows;
+};
+
+RowMap make_map(uint32_t period, uint32_t block_stride, const std::vector<int> &pids);
+
+void launch_ntt(Context &c, const RowsView &src, const RowsView &dst, bool inverse, cudaStream_t s);
+void launch_copy_rows(Context &c, const RowsView &src, const RowsView &dst, cudaStream_t s);
+
+// Launch bookkeeping: kernel_begin before a launch, kernel_end after it
+// (launch count, optional trace line, optional event pair + algorithmic bytes).
+void kernel_begin(Context &c, cudaStream_t st);
+void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cudaStream_t st);
+
+}  // namespace mmfhe

@@ -1,0 +1,404 @@
+// Element-wise and key-switching kernels (evaluation domain unless stated).
+//
+// Layouts (N words per row, rows contiguous):
+//   ciphertext batch   [B][2][l+1][N]
+//   tensor batch       [B][3][l+1][N]            (d0, d1, d2)
+//   ModUp digits       [B][beta][l+1+K][N]        rows q_0..q_l, p_0..p_{K-1}
+//   key-switch output  [B][2][l+1+K][N]
+//   key                [dnum][2][L+1+K][N]        (device, evaluation domain)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+#include "kernels.h"
+#include "modarith.cuh"
+
+namespace mmfhe {
+
+namespace {
+
+constexpr int EW_THREADS = 256;
+
+inline dim3 grid_for(size_t work) {
+    size_t b = (work + EW_THREADS - 1) / EW_THREADS;
+    return dim3((unsigned)std::min<size_t>(b, 148 * 64));
+}
+
+__device__ __forceinline__ uint64_t mulq(uint64_t a, uint64_t b, const ModTab &mt, int pid) {
+    return mm::mul_barrett(a, b, mt.q[pid], mt.mu[pid], mt.k[pid]);
+}
+
+// out[r] = a[r] (op) b[r]; rows have prime pid[r % period].
+__global__ void k_addsub(uint64_t *out, const uint64_t *a, const uint64_t *b, size_t words, int logn, uint32_t period,
+                         ModTab mt, PidList pl, int sub) {
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < words; w += (size_t)gridDim.x * blockDim.x) {
+        int pid = pl.pid[(w >> logn) % period];
+        uint64_t q = mt.q[pid];
+        out[w] = sub ? mm::sub_mod(a[w], b[w], q) : mm::add_mod(a[w], b[w], q);
+    }
+}
+
+// out[r] = c * a[r] mod q (c a small signed integer).
+__global__ void k_mul_int(uint64_t *out, const uint64_t *a, size_t words, int logn, uint32_t period, ModTab mt,
+                          PidList pl, long long c) {
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < words; w += (size_t)gridDim.x * blockDim.x) {
+        int pid = pl.pid[(w >> logn) % period];
+        uint64_t q = mt.q[pid];
+        uint64_t cm = c >= 0 ? (uint64_t)c % q : (q - ((uint64_t)(-c) % q)) % q;
+        out[w] = mulq(a[w], cm, mt, pid);
+    }
+}
+
+// out[r] (+)= a[r] * pt[r % period]   (pt rows = one plaintext, shared by all blocks)
+__global__ void k_mul_plain(uint64_t *out, const uint64_t *a, const uint64_t *pt, size_t words, int logn,
+                            uint32_t period, ModTab mt, PidList pl, int accumulate) {
+    const uint32_t n = 1u << logn;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < words; w += (size_t)gridDim.x * blockDim.x) {
+        uint32_t row = (uint32_t)(w >> logn) % period;
+        int pid = pl.pid[row];
+        uint64_t v = mulq(a[w], pt[(size_t)row * n + (w & (n - 1))], mt, pid);
+        out[w] = accumulate ? mm::add_mod(out[w], v, mt.q[pid]) : v;
+    }
+}
+
+// Tensor product accumulated with a small integer coefficient:
+// d (+)= coef * (a0 b0, a0 b1 + a1 b0, a1 b1), per window b, limb i, word x.
+__global__ void k_tensor(uint64_t *d, const uint64_t *a, const uint64_t *b, int B, int nl, int logn, ModTab mt,
+                         long long coef, int accumulate) {
+    const size_t per = (size_t)nl << logn;
+    const size_t total = (size_t)B * per;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        size_t bb = w / per, rem = w - bb * per;
+        int i = (int)(rem >> logn);
+        uint64_t q = mt.q[i];
+        const uint64_t *A = a + bb * 2 * per;
+        const uint64_t *Bq = b + bb * 2 * per;
+        uint64_t a0 = A[rem], a1 = A[per + rem], b0 = Bq[rem], b1 = Bq[per + rem];
+        uint64_t t0 = mulq(a0, b0, mt, i);
+        uint64_t t1 = mm::add_mod(mulq(a0, b1, mt, i), mulq(a1, b0, mt, i), q);
+        uint64_t t2 = mulq(a1, b1, mt, i);
+        if (coef != 1) {
+            uint64_t cm = coef >= 0 ? (uint64_t)coef % q : (q - ((uint64_t)(-coef) % q)) % q;
+            t0 = mulq(t0, cm, mt, i);
+            t1 = mulq(t1, cm, mt, i);
+            t2 = mulq(t2, cm, mt, i);
+        }
+        uint64_t *D = d + bb * 3 * per;
+        if (accumulate) {
+            D[rem] = mm::add_mod(D[rem], t0, q);
+            D[per + rem] = mm::add_mod(D[per + rem], t1, q);
+            D[2 * per + rem] = mm::add_mod(D[2 * per + rem], t2, q);
+        } else {
+            D[rem] = t0;
+            D[per + rem] = t1;
+            D[2 * per + rem] = t2;
+        }
+    }
+}
+
+// ModUp FastBConv of one level: for window b, digit j, word x:
+//   y_u = [x_u * inv_{j,u}]_{q_u} (u over the digit's primes, coefficient form)
+//   out[b][j][t][x] = sum_u y_u * M_{j,u,t} mod prime(t)      (t not in the digit)
+//   out[b][j][t][x] = d_eval[b][t][x]                         (t in the digit)
+// coef: [B][l+1][N] coefficient form of d; deval: d in the evaluation domain,
+// window stride deval_stride words.
+__global__ void k_modup_bconv(uint64_t *out, const uint64_t *coef, const uint64_t *deval, size_t deval_stride, int B,
+                              int level, int beta, int alpha, int nrows_ext, int logn, ModTab mt, ModUpConsts mc) {
+    const uint32_t n = 1u << logn;
+    const size_t total = (size_t)B * beta * n;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)(w & (n - 1));
+        size_t bj = w >> logn;
+        int j = (int)(bj % beta);
+        size_t bb = bj / beta;
+        int i0 = j * alpha;
+        int cnt = min(alpha, level + 1 - i0);
+        uint64_t y[MAX_ALPHA];
+        const uint64_t *C = coef + (bb * (level + 1)) * n;
+        for (int u = 0; u < cnt; u++) {
+            int pi = i0 + u;
+            y[u] = mm::mul_shoup(C[(size_t)pi * n + x], mc.inv[j * MAX_ALPHA + u], mc.inv_sh[j * MAX_ALPHA + u], mt.q[pi]);
+        }
+        uint64_t *O = out + ((bb * beta + j) * (size_t)nrows_ext) * n;
+        const uint64_t *De = deval + bb * deval_stride;
+        for (int t = 0; t < nrows_ext; t++) {
+            if (t >= i0 && t < i0 + cnt) {
+                O[(size_t)t * n + x] = De[(size_t)t * n + x];
+                continue;
+            }
+            int pid = t <= level ? t : mc.pid_p0 + (t - level - 1);
+            uint64_t qt = mt.q[pid];
+            uint64_t acc = 0;
+            for (int u = 0; u < cnt; u++) {
+                size_t ci = ((size_t)j * MAX_ALPHA + u) * MAXROWMAP + t;
+                acc += mm::mul_shoup_lazy(y[u], mc.m[ci], mc.m_sh[ci], qt);   // < 2q each
+                acc = acc >= 2 * qt ? acc - 2 * qt : acc;
+            }
+            O[(size_t)t * n + x] = acc >= qt ? acc - qt : acc;
+        }
+    }
+}
+
+// Key inner product fused with the Galois permutation of the digits:
+//   u_h[b][t][x] = sum_j digits[b][j][t][pi(x)] * key[j][h][krow(t)][x]
+// Each thread owns (t, x) and loops over the windows, so every key word is
+// read once per launch.
+__global__ void k_keyip(uint64_t *u, const uint64_t *digits, const uint64_t *key, int B, int level, int beta,
+                        int nrows_ext, int key_rows, int L1, int logn, uint32_t galois, ModTab mt, int pid_p0) {
+    const uint32_t n = 1u << logn;
+    const size_t total = (size_t)nrows_ext * n;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)(w & (n - 1));
+        int t = (int)(w >> logn);
+        int pid = t <= level ? t : pid_p0 + (t - level - 1);
+        int krow = t <= level ? t : L1 + (t - level - 1);
+        uint32_t px = galois == 1 ? x : mm::galois_perm(x, galois, logn);
+        uint64_t kb[MAX_DNUM], ka[MAX_DNUM];
+        for (int j = 0; j < beta; j++) {
+            kb[j] = key[(((size_t)j * 2 + 0) * key_rows + krow) * n + x];
+            ka[j] = key[(((size_t)j * 2 + 1) * key_rows + krow) * n + x];
+        }
+        uint64_t q = mt.q[pid];
+        for (int bb = 0; bb < B; bb++) {
+            uint64_t a0 = 0, a1 = 0;
+            for (int j = 0; j < beta; j++) {
+                uint64_t dv = digits[(((size_t)bb * beta + j) * nrows_ext + t) * n + px];
+                a0 = mm::add_mod(a0, mulq(dv, kb[j], mt, pid), q);
+                a1 = mm::add_mod(a1, mulq(dv, ka[j], mt, pid), q);
+            }
+            uint64_t *U = u + ((size_t)bb * 2 * nrows_ext) * n;
+            U[(size_t)t * n + x] = a0;
+            U[((size_t)nrows_ext + t) * n + x] = a1;
+        }
+    }
+}
+
+// ModDown FastBConv P -> Q with centered representatives (coefficient form):
+//   z_k = [u_{p_k} * Phat_k^-1]_{p_k}, negative representative when z_k > p_k/2
+//   v_i = sum_k z_k * (Phat_k mod q_i) - c * (P mod q_i),  c = #negative z_k
+// u: [B][2][l+1+K][N] with its P rows in coefficient form; v: [B][2][l+1][N].
+__global__ void k_moddown_bconv(uint64_t *v, const uint64_t *u, int B, int level, int K, int logn, ModTab mt,
+                                ModDownConsts dc) {
+    const uint32_t n = 1u << logn;
+    const int nre = level + 1 + K;
+    const size_t total = (size_t)B * 2 * n;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)(w & (n - 1));
+        size_t bh = w >> logn;
+        const uint64_t *U = u + bh * nre * n;
+        uint64_t z[MMFHE_MAX_P];
+        uint32_t negc = 0;
+        for (int k = 0; k < K; k++) {
+            uint64_t pk = mt.q[dc.pid_p0 + k];
+            z[k] = mm::mul_shoup(U[(size_t)(level + 1 + k) * n + x], dc.pinv[k], dc.pinv_sh[k], pk);
+            negc += z[k] > (pk >> 1) ? 1u : 0u;
+        }
+        uint64_t *V = v + bh * (level + 1) * n;
+        for (int i = 0; i <= level; i++) {
+            uint64_t q = mt.q[i];
+            uint64_t acc = 0;
+            for (int k = 0; k < K; k++) {
+                size_t ci = (size_t)k * MMFHE_MAX_Q + i;
+                acc += mm::mul_shoup_lazy(z[k], dc.phat[ci], dc.phat_sh[ci], q);
+                acc = acc >= 2 * q ? acc - 2 * q : acc;
+            }
+            acc = acc >= q ? acc - q : acc;
+            uint64_t corr = mm::mul_shoup(negc, dc.pmod[i], dc.pmod_sh[i], q);
+            V[(size_t)i * n + x] = mm::sub_mod(acc, corr, q);
+        }
+    }
+}
+
+// out[b][h][i][x] = (u[b][h][i][x] - v[b][h][i][x]) * P^-1 mod q_i
+//                   + add_h[b][i][perm(x)]   (add_h optional; perm = galois map)
+__global__ void k_moddown_combine(uint64_t *out, const uint64_t *u, const uint64_t *v, const uint64_t *add0,
+                                  const uint64_t *add1, size_t add_stride, uint32_t add_galois, int B, int level,
+                                  int K, int logn, ModTab mt, ModDownConsts dc) {
+    const uint32_t n = 1u << logn;
+    const int nl = level + 1, nre = level + 1 + K;
+    const size_t total = (size_t)B * 2 * nl * n;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)(w & (n - 1));
+        size_t r = w >> logn;
+        int i = (int)(r % nl);
+        size_t bh = r / nl;
+        int h = (int)(bh & 1);
+        size_t bb = bh >> 1;
+        uint64_t q = mt.q[i];
+        uint64_t uv = u[(bh * nre + i) * n + x];
+        uint64_t vv = v[(bh * nl + i) * n + x];
+        uint64_t res = mm::mul_shoup(mm::sub_mod(uv, vv, q), dc.Pinv[i], dc.Pinv_sh[i], q);
+        const uint64_t *A = h == 0 ? add0 : add1;
+        if (A) {
+            uint32_t px = add_galois == 1 ? x : mm::galois_perm(x, add_galois, logn);
+            res = mm::add_mod(res, A[bb * add_stride + (size_t)i * n + px], q);
+        }
+        out[w] = res;
+    }
+}
+
+// Rescale, spread step: r = last limb (coefficient form, [B][2][N]) taken
+// centered mod q_l, written as residues mod q_i for i < l into tmp [B][2][l][N].
+__global__ void k_rescale_spread(uint64_t *tmp, const uint64_t *last, int B, int level, int logn, ModTab mt,
+                                 RescaleConsts rc) {
+    const uint32_t n = 1u << logn;
+    const size_t total = (size_t)B * 2 * n;
+    const uint64_t ql = mt.q[level];
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)(w & (n - 1));
+        size_t bh = w >> logn;
+        uint64_t r = last[bh * n + x];
+        bool neg = r > (ql >> 1);
+        uint64_t *T = tmp + bh * (size_t)level * n;
+        for (int i = 0; i < level; i++) {
+            uint64_t q = mt.q[i];
+            uint64_t ri = mm::reduce_barrett(r, q, mt.mu[i], mt.k[i]);
+            if (neg) ri = mm::sub_mod(ri, rc.qmod[i], q);   // r - q_l
+            T[(size_t)i * n + x] = ri;
+        }
+    }
+}
+
+// out[b][h][i][x] = (c[b][h][i][x] - tmp[b][h][i][x]) * q_l^-1 mod q_i, i < l.
+__global__ void k_rescale_combine(uint64_t *out, const uint64_t *c, const uint64_t *tmp, int B, int level, int logn,
+                                  ModTab mt, RescaleConsts rc) {
+    const uint32_t n = 1u << logn;
+    const size_t total = (size_t)B * 2 * level * n;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)(w & (n - 1));
+        size_t r = w >> logn;
+        int i = (int)(r % level);
+        size_t bh = r / level;
+        uint64_t q = mt.q[i];
+        uint64_t cv = c[(bh * (level + 1) + i) * n + x];
+        out[w] = mm::mul_shoup(mm::sub_mod(cv, tmp[w], q), rc.qinv[i], rc.qinv_sh[i], q);
+    }
+}
+
+// Automorphism of whole rows in the evaluation domain.
+__global__ void k_permute(uint64_t *out, const uint64_t *in, size_t rows, int logn, uint32_t galois) {
+    const uint32_t n = 1u << logn;
+    const size_t total = rows * n;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        uint32_t x = (uint32_t)(w & (n - 1));
+        out[w] = in[(w - x) + mm::galois_perm(x, galois, logn)];
+    }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+#define LAUNCH(c, name, bytes, g, kern, ...)                  \
+    do {                                                      \
+        kernel_begin(c, st);                                  \
+        kern<<<g, EW_THREADS, 0, st>>>(__VA_ARGS__);          \
+        kernel_end(c, name, g, dim3(EW_THREADS), bytes, st);  \
+        CK(cudaGetLastError());                               \
+    } while (0)
+
+// Algorithmic bytes: every distinct word a launch must read or write once.
+static inline double W8(size_t words) { return 8.0 * (double)words; }
+
+void k_launch_addsub(Context &c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t rows, const PidList &pl,
+                     uint32_t period, bool sub, cudaStream_t st) {
+    size_t words = rows << c.logn;
+    if (!words) return;
+    dim3 g = grid_for(words);
+    LAUNCH(c, sub ? "sub" : "add", W8(3 * words), g, k_addsub, out, a, b, words, c.logn, period, c.mods, pl,
+           sub ? 1 : 0);
+}
+
+void k_launch_mul_int(Context &c, uint64_t *out, const uint64_t *a, size_t rows, const PidList &pl, uint32_t period,
+                      long long k, cudaStream_t st) {
+    size_t words = rows << c.logn;
+    if (!words) return;
+    dim3 g = grid_for(words);
+    LAUNCH(c, "mul_int", W8(2 * words), g, k_mul_int, out, a, words, c.logn, period, c.mods, pl, k);
+}
+
+void k_launch_mul_plain(Context &c, uint64_t *out, const uint64_t *a, const uint64_t *pt, size_t rows,
+                        const PidList &pl, uint32_t period, bool acc, cudaStream_t st) {
+    size_t words = rows << c.logn;
+    if (!words) return;
+    dim3 g = grid_for(words);
+    double bytes = W8((acc ? 3 : 2) * words + ((size_t)period << c.logn));
+    LAUNCH(c, acc ? "mul_plain_acc" : "mul_plain", bytes, g, k_mul_plain, out, a, pt, words, c.logn, period, c.mods,
+           pl, acc ? 1 : 0);
+}
+
+void k_launch_tensor(Context &c, uint64_t *d, const uint64_t *a, const uint64_t *b, int B, int level, long long coef,
+                     bool acc, cudaStream_t st) {
+    size_t work = (size_t)B * (level + 1) * c.n;
+    if (!work) return;
+    dim3 g = grid_for(work);
+    LAUNCH(c, "tensor", W8(work * (4 + (acc ? 6 : 3))), g, k_tensor, d, a, b, B, level + 1, c.logn, c.mods, coef,
+           acc ? 1 : 0);
+}
+
+void k_launch_modup_bconv(Context &c, uint64_t *out, const uint64_t *coef, const uint64_t *deval, size_t deval_stride,
+                          int B, int level, const ModUpConsts &mc, cudaStream_t st) {
+    const LevelConsts &lc = c.lv[level];
+    size_t work = (size_t)B * lc.beta * c.n;
+    if (!work) return;
+    dim3 g = grid_for(work);
+    const size_t nl = level + 1, nre = nl + c.num_p;
+    // reads: coefficient rows + evaluation rows of d; writes: every digit row
+    double bytes = W8((size_t)B * c.n * (2 * nl + lc.beta * nre));
+    LAUNCH(c, "modup_bconv", bytes, g, k_modup_bconv, out, coef, deval, deval_stride, B, level, lc.beta, c.alpha,
+           level + 1 + c.num_p, c.logn, c.mods, mc);
+}
+
+void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint64_t *key, int B, int level, int beta,
+                    uint32_t galois, cudaStream_t st) {
+    int nre = level + 1 + c.num_p;
+    size_t work = (size_t)nre * c.n;
+    dim3 g = grid_for(work);
+    // reads: B*beta digit rows + beta*2 key rows; writes: B*2 output rows
+    double bytes = W8(work * ((size_t)B * beta + 2 * beta + 2 * B));
+    LAUNCH(c, "keyip", bytes, g, k_keyip, u, digits, key, B, level, beta, nre, c.num_q + c.num_p, c.num_q, c.logn,
+           galois, c.mods, c.num_q);
+}
+
+void k_launch_moddown_bconv(Context &c, uint64_t *v, const uint64_t *u, int B, int level, const ModDownConsts &dc,
+                            cudaStream_t st) {
+    size_t work = (size_t)B * 2 * c.n;
+    dim3 g = grid_for(work);
+    double bytes = W8(work * (c.num_p + level + 1));
+    LAUNCH(c, "moddown_bconv", bytes, g, k_moddown_bconv, v, u, B, level, c.num_p, c.logn, c.mods, dc);
+}
+
+void k_launch_moddown_combine(Context &c, uint64_t *out, const uint64_t *u, const uint64_t *v, const uint64_t *add0,
+                              const uint64_t *add1, size_t add_stride, uint32_t add_galois, int B, int level,
+                              const ModDownConsts &dc, cudaStream_t st) {
+    size_t work = (size_t)B * 2 * (level + 1) * c.n;
+    dim3 g = grid_for(work);
+    double bytes = W8(work * 3 + (add0 ? work / 2 : 0) + (add1 ? work / 2 : 0));
+    LAUNCH(c, "moddown_combine", bytes, g, k_moddown_combine, out, u, v, add0, add1, add_stride, add_galois, B, level,
+           c.num_p, c.logn, c.mods, dc);
+}
+
+void k_launch_rescale_spread(Context &c, uint64_t *tmp, const uint64_t *last, int B, int level,
+                             const RescaleConsts &rc, cudaStream_t st) {
+    size_t work = (size_t)B * 2 * c.n;
+    dim3 g = grid_for(work);
+    LAUNCH(c, "rescale_spread", W8(work * (1 + level)), g, k_rescale_spread, tmp, last, B, level, c.logn, c.mods, rc);
+}
+
+void k_launch_rescale_combine(Context &c, uint64_t *out, const uint64_t *cc, const uint64_t *tmp, int B, int level,
+                              const RescaleConsts &rc, cudaStream_t st) {
+    size_t work = (size_t)B * 2 * level * c.n;
+    dim3 g = grid_for(work);
+    LAUNCH(c, "rescale_combine", W8(3 * work), g, k_rescale_combine, out, cc, tmp, B, level, c.logn, c.mods, rc);
+}
+
+void k_launch_permute(Context &c, uint64_t *out, const uint64_t *in, size_t rows, uint32_t galois, cudaStream_t st) {
+    size_t work = rows * c.n;
+    if (!work) return;
+    dim3 g = grid_for(work);
+    LAUNCH(c, "permute", W8(2 * work), g, k_permute, out, in, rows, c.logn, galois);
+}
+
+}  // namespace mmfhe

@@ -1,0 +1,62 @@
+// Kernel parameter structs and launcher declarations (kernels.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace mmfhe {
+
+constexpr int MAX_ALPHA = 8;   // primes per key-switching digit
+constexpr int MAX_DNUM = 8;    // key-switching digits
+
+// Prime id of each row within a period (elementwise kernels).
+struct PidList {
+    uint8_t pid[MAXROWMAP];
+};
+
+// ModUp constants of one level (device pointers):
+//   inv[j*MAX_ALPHA + u]     = (Qhat_{j,u})^-1 mod q_{j*alpha+u}   (+ Shoup)
+//   m[(j*MAX_ALPHA + u)*MAXROWMAP + t] = Qhat_{j,u} mod prime(t)   (+ Shoup)
+struct ModUpConsts {
+    const uint64_t *inv, *inv_sh, *m, *m_sh;
+    int pid_p0;
+};
+
+// ModDown constants (device pointers):
+//   pinv[k] = Phat_k^-1 mod p_k; phat[k*MAX_Q + i] = Phat_k mod q_i;
+//   pmod[i] = P mod q_i; Pinv[i] = P^-1 mod q_i  (all with Shoup companions)
+struct ModDownConsts {
+    const uint64_t *pinv, *pinv_sh, *phat, *phat_sh, *pmod, *pmod_sh, *Pinv, *Pinv_sh;
+    int pid_p0;
+};
+
+// Rescale-by-q_l constants: qinv[i] = q_l^-1 mod q_i (+ Shoup), qmod[i] = q_l mod q_i.
+struct RescaleConsts {
+    const uint64_t *qinv, *qinv_sh, *qmod;
+};
+
+void k_launch_addsub(Context &c, uint64_t *out, const uint64_t *a, const uint64_t *b, size_t rows, const PidList &pl,
+                     uint32_t period, bool sub, cudaStream_t st);
+void k_launch_mul_int(Context &c, uint64_t *out, const uint64_t *a, size_t rows, const PidList &pl, uint32_t period,
+                      long long k, cudaStream_t st);
+void k_launch_mul_plain(Context &c, uint64_t *out, const uint64_t *a, const uint64_t *pt, size_t rows,
+                        const PidList &pl, uint32_t period, bool acc, cudaStream_t st);
+void k_launch_tensor(Context &c, uint64_t *d, const uint64_t *a, const uint64_t *b, int B, int level, long long coef,
+                     bool acc, cudaStream_t st);
+void k_launch_modup_bconv(Context &c, uint64_t *out, const uint64_t *coef, const uint64_t *deval, size_t deval_stride,
+                          int B, int level, const ModUpConsts &mc, cudaStream_t st);
+void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint64_t *key, int B, int level, int beta,
+                    uint32_t galois, cudaStream_t st);
+void k_launch_moddown_bconv(Context &c, uint64_t *v, const uint64_t *u, int B, int level, const ModDownConsts &dc,
+                            cudaStream_t st);
+void k_launch_moddown_combine(Context &c, uint64_t *out, const uint64_t *u, const uint64_t *v, const uint64_t *add0,
+                              const uint64_t *add1, size_t add_stride, uint32_t add_galois, int B, int level,
+                              const ModDownConsts &dc, cudaStream_t st);
+void k_launch_rescale_spread(Context &c, uint64_t *tmp, const uint64_t *last, int B, int level,
+                             const RescaleConsts &rc, cudaStream_t st);
+void k_launch_rescale_combine(Context &c, uint64_t *out, const uint64_t *cc, const uint64_t *tmp, int B, int level,
+                              const RescaleConsts &rc, cudaStream_t st);
+void k_launch_permute(Context &c, uint64_t *out, const uint64_t *in, size_t rows, uint32_t galois, cudaStream_t st);
+
+}  // namespace mmfhe
