@@ -1,0 +1,395 @@
+"""Benchmark: encrypted vital-sign windows per second on one or more B300s.
+
+Workload (the configuration the headline metric is quoted on): the full
+vital-sign chain (K1 -> K2 | K4 -> K5 -> K7 -> K3 -> |X|^2 -> sharpen ->
+weighted average; depth 11) at N = 2^15 with 12 + 4 primes, one 10 s window
+= 200 frames x 256 range bins = 16 input ciphertexts.  A step evaluates a
+batch of B windows of one user (every launch covers the whole batch).
+
+Inputs are synthetic: uniform residues for the ciphertexts and switching keys
+(under RLWE a ciphertext or key is indistinguishable from such words, and the
+circuit is data-oblivious, so this is exactly the cloud's view), the plan's
+public constants designed and encoded by the library itself.  Each step
+reads B x 96 MiB of ciphertexts, more than the 126 MB L2.
+
+Timed region (device-resident): K steps on one stream, bracketed by a barrier
+and torch.cuda.synchronize, CUDA events per step.  e2e: the same call with
+pinned host input/output buffers (host <-> device copies inside the call).
+Per-kernel roofline: one extra profiled step with CUDA events around every
+launch (algorithmic bytes from the library).  cpu_baseline: the CPU oracle
+on a time-boxed sample of one window's chain.
+
+Multi-GPU: replicas (windows of different users are independent); each rank
+evaluates its own batch, no data-path collective; timing = max over ranks.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "encrypted windows/s and p99 latency, batched+learned vs plain, same decrypted MAE"
+WORKLOAD = ("vital-sign chain (K1,K2 | K4,K5,K7,K3,|X|^2,sharpen,avg; depth 11), CKKS N=2^15, "
+            "Q=60+11x40 bits, P=4x60 bits, dnum=3, 200 frames x 256 bins per 10 s window, 16 input cts")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=16, help="windows per step (per GPU)")
+    ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
+    ap.add_argument("--cpu-sample-s", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas: a barrier and a max, on CPU via gloo)
+# ---------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle sample (the baseline / reference arm)
+# ---------------------------------------------------------------------------
+class OracleSample:
+    """Oracle set-up for the same workload (untimed), then time-boxed runs of
+    one window's chain; progress is measured in key-switch limb units, the
+    oracle's dominant cost, against a counting run of the whole chain."""
+
+    def __init__(self, seed=4242):
+        import synth
+        from oracle import ckks as ck
+        from oracle import circuits as cc
+        from oracle import params as pm
+        from oracle import plain
+        self.ck, self.cc = ck, cc
+        P = pm.vital_params()
+        circ = cc.VitalCircuit(P, cc.VitalConfig(bins=256))
+        rots = circ.rotations()
+        kd = synth.KeyDraws(seed, P.n, P.q, P.p, P.dnum, rots)
+        sk = ck.SecretKey(P, kd.secret)
+        pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
+        self.rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
+        self.gks = {k: ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
+        del kd
+        self.consts = circ.constants()
+        win = synth.vital_window(seed, frames=200, bins=256, randomize_rates=True)
+        s1, s2 = plain.preprocess(win.z)
+        lay = circ.lay
+
+        def stream(x, sd):
+            re, im = lay.pack(x.real), lay.pack(x.imag)
+            return [(ck.encrypt(P, pk, ck.encode(P, re[c], P.scale, P.L), *synth.encryption_draws(sd + 2 * c, P.n)),
+                     ck.encrypt(P, pk, ck.encode(P, im[c], P.scale, P.L), *synth.encryption_draws(sd + 2 * c + 1, P.n)))
+                    for c in range(lay.groups)]
+
+        self.s1, self.s2 = stream(s1, seed + 100), stream(s2, seed + 200)
+        self.P, self.circ = P, circ
+        counter = cc.CountingEvaluator(P)
+        shapes = [(cc._Shape(P.L), cc._Shape(P.L)) for _ in range(lay.groups)]
+        circ.run(counter, {k: cc._Shape(0) for k in circ.constant_keys()}, shapes, shapes)
+        self.total_weight = counter.ks_weight
+
+    def run(self, budget_s):
+        """Returns (windows per second, elapsed seconds, completed fraction)."""
+        ev = self.cc.BudgetEvaluator(self.P, self.rlk, self.gks, budget_s)
+        t0 = time.perf_counter()
+        try:
+            self.circ.run(ev, self.consts, self.s1, self.s2)
+        except self.cc.SampleBudgetExceeded:
+            pass
+        dt = time.perf_counter() - t0
+        frac = ev.ks_weight / self.total_weight
+        return frac / dt, dt, frac
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores: K bounded samples."""
+    if rank != 0:
+        return
+    t_setup = time.perf_counter()
+    sample = OracleSample()
+    setup_s = time.perf_counter() - t_setup
+    per_step = max(5.0, min(30.0, 150.0 / (args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        sample.run(per_step / 4)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt, frac = sample.run(per_step)
+        vals.append(v)
+        times.append(dt)
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(times)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch_windows": 1, "parallelism": "single-threaded CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "windows/s", "cores": 1, "kind": "oracle",
+                         "sample": "first %.0f s of one window's chain per step, progress in key-switch limb units "
+                                   "(setup %.0f s untimed)" % (per_step, setup_s)},
+        "e2e": {"value": value, "unit": "windows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def csrc_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2603_22437_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        j = json.load(open(p))
+        return float(j["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was captured on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    j = json.load(open(p))
+    if j.get("csrc_hash") != csrc_hash():
+        return None
+    k = j.get("kernels", {}).get(kernel)
+    return None if k is None else k.get("dram_bytes_per_launch_full_size")
+
+
+def run_mine(args, rank, world, local):
+    import torch
+
+    import paper_2603_22437_b300 as M
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    params = M.vital_params()
+    ctx = M.Context(params, device=local)
+    plan = ctx.plan(M.vital_config())
+    plan.encode_consts()
+    rots = plan.rotations()
+    P_q, P_p = params.primes_q, params.primes_p
+    n = 1 << params.log_n
+    g = synth.rng(7000 + rank)
+    keys = ctx.keys(rank)
+    qp = P_q + P_p
+
+    def key_words():
+        return np.ascontiguousarray(np.stack([np.stack([synth.uniform_residues(g, qp, n) for _ in range(2)])
+                                              for _ in range(params.dnum)]))
+
+    keys.set_relin(key_words())
+    for k in rots:
+        keys.set_galois(k, key_words())
+    n_in, n_out, out_levels = plan.io()
+    B = args.batch
+    in_words = n_in * 2 * len(P_q) * n
+    out_words = sum(2 * (l + 1) * n for l in out_levels)
+    # device-resident inputs: B windows of uniform ciphertexts
+    host_in = []
+    for w in range(B):
+        cts = synth.uniform_ciphertexts(100 * rank + w, P_q, n, n_in)
+        host_in.append(cts.reshape(-1))
+    d_in = [torch.from_numpy(x.view(np.int64)).to(dev) for x in host_in]
+    d_out = [torch.empty(out_words, dtype=torch.int64, device=dev) for _ in range(B)]
+    stream = torch.cuda.Stream(device=dev)
+
+    def step(ins, outs):
+        ctx.eval(plan, keys, ins, outs, stream=stream, vital=True)
+
+    torch.cuda.synchronize()
+    for _ in range(args.warmup):
+        step(d_in, d_out)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident ----
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ctx.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step(d_in, d_out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    launches = ctx.launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_s = allmax(world, sum(step_ms) / 1000.0)
+    value = world * B * args.steps / total_s
+
+    # ---- e2e: pinned host buffers, copies inside the call ----
+    pin_in = [torch.from_numpy(x.view(np.int64)).pin_memory() for x in host_in]
+    pin_out = [torch.empty(out_words, dtype=torch.int64).pin_memory() for _ in range(B)]
+    step(pin_in, pin_out)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step(pin_in, pin_out)
+    torch.cuda.synchronize()
+    e2e_s = allmax(world, time.perf_counter() - t0)
+    e2e = {"value": world * B * args.e2e_steps / e2e_s, "unit": "windows/s",
+           "h2d_bytes_per_step": B * in_words * 8, "d2h_bytes_per_step": B * out_words * 8}
+
+    # ---- per-kernel profile of one more step ----
+    ctx.profile(True)
+    step(d_in, d_out)
+    torch.cuda.synchronize()
+    prof = ctx.profile()
+    ctx.profile(False)
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, ms, byts) = top
+    peak, peak_kind = measured_peaks()
+    achieved = byts / (ms / 1000.0) / 1e9
+    tot_ms = sum(v[1] for v in prof.values())
+    roofline = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind, "traffic": ncu_traffic(name),
+                "launches_per_step": nl, "avg_launch_us": 1000.0 * ms / nl,
+                "algorithmic_bytes_per_launch": byts / nl, "share_of_step": ms / tot_ms,
+                "kernels": {k: {"launches": v[0], "ms": round(v[1], 3), "GBps": round(v[2] / max(v[1], 1e-9) / 1e6, 1)}
+                            for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+    line = {
+        "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "batch_windows": B, "windows_per_step_all_gpus": world * B,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (%d MiB of ciphertexts per step)" % (B * in_words * 8 >> 20)},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "note": "latency of a window = its batch's step time"},
+        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
+        "wall_s_timed": wall,
+    }
+    return line
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    line = run_mine(args, rank, world, local)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = OracleSample()
+        v, dt, frac = sample.run(args.cpu_sample_s)
+        line["cpu_baseline"] = {"value": v, "unit": "windows/s", "cores": 1, "kind": "oracle",
+                                "host_cores_available": cpu_cores(),
+                                "sample": "first %.1f s of one window's chain (%.2f%% of its key-switch limb units)"
+                                          % (dt, 100 * frac)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

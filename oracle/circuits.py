@@ -225,6 +225,21 @@ class Evaluator:
         self._t("mul_plain", a.level)
         return ck.mul_plain(self.P, a, pt)
 
+    def drop(self, a, level):
+        return ck.drop_level(self.P, a, level)
+
+    def tensor_add(self, x, y):
+        return ck.tensor_add(self.P, x, y)
+
+    def tensor_sub(self, x, y):
+        return ck.tensor_sub(self.P, x, y)
+
+    def tensor_mul_int(self, x, k):
+        return ck.tensor_mul_int(self.P, x, k)
+
+    def mul_plain_sum(self, pairs):
+        return ck.mul_plain_sum(self.P, pairs)
+
     def rotsum(self, a, stride, span):
         """x <- x + Rot(x, stride 2^i), i < log2(span): slot j then holds
         sum_{m < span} x[j + m stride]."""
@@ -236,7 +251,7 @@ class Evaluator:
         """relin(sum_i x_i (x) x_i), not rescaled (lazy relinearization)."""
         t = self.tensor(xs[0], xs[0])
         for x in xs[1:]:
-            t = ck.tensor_add(self.P, t, self.tensor(x, x))
+            t = self.tensor_add(t, self.tensor(x, x))
         return self.relin(t)
 
     def bsgs(self, babies, consts, n1, stride, level):
@@ -257,11 +272,113 @@ class Evaluator:
             for (name, delta) in sorted(groups[g]):
                 pairs.append((babies[name][delta % n1], consts[(name, delta)]))
                 self._t("mul_plain", level, name, delta)
-            inner = ck.mul_plain_sum(self.P, pairs)
+            inner = self.mul_plain_sum(pairs)
             if g:
                 inner = self.rotate(inner, g * n1 * stride)
             acc = inner if acc is None else self.add(acc, inner)
         return acc
+
+
+class _Shape:
+    """Level/scale stand-in for a ciphertext in a counting run."""
+
+    def __init__(self, level, scale=1.0):
+        self.level, self.scale = level, scale
+
+
+class CountingEvaluator(Evaluator):
+    """Runs a circuit without computing it: every operation returns a
+    level-tracking stand-in and key switches are tallied, each weighted by
+    the number of limbs it touches (level + 1 + K).  Used to size a bounded
+    sample of the oracle's work."""
+
+    def __init__(self, P):
+        super().__init__(P, None, None)
+        self.ks_weight = 0
+        self.K = len(P.p)
+
+    def _ks(self, level, n=1):
+        self.ks_weight += n * (level + 1 + self.K)
+
+    def tensor(self, a, b):
+        return _Shape(a.level)
+
+    def relin(self, t):
+        self._ks(t.level)
+        return _Shape(t.level)
+
+    def rescale(self, a):
+        return _Shape(a.level - 1)
+
+    def rotate(self, a, k):
+        if k % self.P.slots:
+            self._ks(a.level)
+        return _Shape(a.level)
+
+    def hoisted(self, a, ks):
+        self._ks(a.level, sum(1 for k in ks if k % self.P.slots))
+        return [_Shape(a.level) for _ in ks]
+
+    def add(self, a, b):
+        return _Shape(a.level)
+
+    def mul_plain(self, a, pt):
+        return _Shape(a.level)
+
+    def drop(self, a, level):
+        return _Shape(level)
+
+    def tensor_add(self, x, y):
+        return _Shape(x.level)
+
+    tensor_sub = tensor_add
+
+    def tensor_mul_int(self, x, k):
+        return _Shape(x.level)
+
+    def mul_plain_sum(self, pairs):
+        return _Shape(pairs[0][0].level)
+
+
+class SampleBudgetExceeded(Exception):
+    pass
+
+
+class BudgetEvaluator(Evaluator):
+    """Real evaluation that tallies the same key-switch weight as
+    CountingEvaluator and stops once `budget_s` seconds have elapsed."""
+
+    def __init__(self, P, rlk, gks, budget_s):
+        import time
+        super().__init__(P, rlk, gks)
+        self._time = time.perf_counter
+        self.t0 = self._time()
+        self.budget = budget_s
+        self.ks_weight = 0
+        self.K = len(P.p)
+
+    def _check(self):
+        if self._time() - self.t0 > self.budget:
+            raise SampleBudgetExceeded()
+
+    def relin(self, t):
+        self._check()
+        r = super().relin(t)
+        self.ks_weight += t.level + 1 + self.K
+        return r
+
+    def rotate(self, a, k):
+        self._check()
+        r = super().rotate(a, k)
+        if k % self.P.slots:
+            self.ks_weight += a.level + 1 + self.K
+        return r
+
+    def hoisted(self, a, ks):
+        self._check()
+        r = super().hoisted(a, ks)
+        self.ks_weight += (a.level + 1 + self.K) * sum(1 for k in ks if k % self.P.slots)
+        return r
 
 
 # ----------------------------------------------------------------------------
@@ -474,6 +591,21 @@ class VitalCircuit:
             ks |= {lay.r_c << i for i in range(int(math.log2(self.span(b))))}
         return sorted({k % self.P.slots for k in ks})
 
+    def constant_keys(self):
+        """Keys of every constant ``constants()`` encodes, without encoding."""
+        keys = []
+        for c in range(self.lay.groups):
+            keys += [("idx", c), ("one", c)]
+        for b in range(len(self.bands)):
+            keys += [("fir", b, k) for k in range(self.cfg.taps)]
+        for b in range(len(self.bands)):
+            for name, M in self.dft_time_matrices(b).items():
+                rows, cols = np.nonzero(M["support"])
+                keys += [(name, b, int(d)) for d in sorted(set(((cols - rows) % self.lay.f_pad).tolist()))]
+        for b in range(len(self.bands)):
+            keys += [("fw", b), ("fone", b)]
+        return keys
+
     def constants(self):
         P, lay, cfg = self.P, self.lay, self.cfg
         out = {}
@@ -540,9 +672,9 @@ class VitalCircuit:
         for part in (0, 1):
             t = None
             for c in range(G):
-                x = ck.drop_level(P, s2[c][part], lv)
+                x = ev.drop(s2[c][part], lv)
                 tc = ev.tensor(m[c], x)
-                t = tc if t is None else ck.tensor_add(P, t, tc)
+                t = tc if t is None else ev.tensor_add(t, tc)
             iq.append(ev.rotsum(ev.rescale(ev.relin(t)), 1, lay.r_c))
         I, Q = iq
 
@@ -558,12 +690,12 @@ class VitalCircuit:
             # K7 differential phase
             If1 = ev.rotate(If, -lay.r_c)
             Qf1 = ev.rotate(Qf, -lay.r_c)
-            y = ev.rescale(ev.relin(ck.tensor_sub(P, ev.tensor(Qf, If1), ev.tensor(If, Qf1))))
-            x = ev.rescale(ev.relin(ck.tensor_add(P, ev.tensor(If, If1), ev.tensor(Qf, Qf1))))
+            y = ev.rescale(ev.relin(ev.tensor_sub(ev.tensor(Qf, If1), ev.tensor(If, Qf1))))
+            x = ev.rescale(ev.relin(ev.tensor_add(ev.tensor(If, If1), ev.tensor(Qf, Qf1))))
             if cfg.taylor_order == 3:
-                u = ck.tensor_sub(P, ck.tensor_mul_int(P, ev.tensor(x, x), 3), ev.tensor(y, y))
+                u = ev.tensor_sub(ev.tensor_mul_int(ev.tensor(x, x), 3), ev.tensor(y, y))
                 u = ev.rescale(ev.relin(u))
-                yd = ck.drop_level(P, y, u.level)
+                yd = ev.drop(y, u.level)
                 dphis.append(ev.rescale(ev.relin(ev.tensor(yd, u))))
             else:
                 dphis.append(y)
