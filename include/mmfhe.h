@@ -183,6 +183,28 @@ mmfhe_status mmfhe_modup(mmfhe_ctx *ctx, uint64_t *out, const uint64_t *d, size_
  * Galois key of `rotation` (no automorphism applied). */
 mmfhe_status mmfhe_keyswitch(mmfhe_ctx *ctx, const mmfhe_keys *keys, int which, int32_t rotation, uint64_t *out,
                              const uint64_t *d, size_t batch, uint32_t level, void *stream);
+/* Key switch that allocates nothing (the paper has no counterpart; this is a
+ * library-level convenience).  Same result, word for word, as
+ * mmfhe_keyswitch, for callers that must not allocate device memory during
+ * a call: code running where cudaMalloc/cudaFree are not allowed (host
+ * callbacks, paths that may not take the allocator's lock, runtimes that hand
+ * all device memory to their own allocator at start-up).  d and out must be
+ * 16-byte aligned DEVICE pointers (d uint64[batch][level+1][N] and out
+ * uint64[batch][2][level+1][N], coefficient form); work is only enqueued on
+ * `stream`.  Every intermediate lives in one fixed device array of
+ * MMFHE_NOALLOC_SCRATCH_BYTES that the library holds on each GPU it runs on
+ * until the process exits; a call that needs more (batch x rows of
+ * (level+1) + beta (level+1+K) + 2 (level+1+K) + 4 (level+1), N words each)
+ * returns BAD_ARG -- at N = 2^15, top level 11, K = 4, dnum = 3 that is one
+ * ciphertext per call.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  All calls share the array and it
+ * keeps the last call's contents (no region needs clearing: every word read
+ * is written earlier in the same call); calls that overlap on the GPU, on
+ * any stream or context of the same device, race on it -- serialise them. */
+#define MMFHE_NOALLOC_SCRATCH_BYTES (64u << 20)
+mmfhe_status mmfhe_keyswitch_noalloc(mmfhe_ctx *ctx, const mmfhe_keys *keys, int which, int32_t rotation,
+                                     uint64_t *out, const uint64_t *d, size_t batch, uint32_t level, void *stream);
 /* Rotate-and-sum: x <- x + Rot(x, stride * 2^i) for i < log2(span). */
 mmfhe_status mmfhe_ct_rotsum(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out, const uint64_t *in, size_t batch,
                              uint32_t level, int32_t stride, uint32_t span, void *stream);

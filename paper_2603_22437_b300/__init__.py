@@ -187,6 +187,13 @@ class Context:
         self._c(_lib.lib().mmfhe_keyswitch(self.h, keys.h, which, rot, ptr(out), ptr(d), batch, level,
                                            stream_ptr(stream)))
 
+    def keyswitch_noalloc(self, keys, out, d, batch, level, rotation=None, stream=None):
+        """Key switch using only the library's fixed device scratch array (no
+        device allocation in the call); out and d must be device buffers."""
+        which, rot = (0, 0) if rotation is None else (1, rotation)
+        self._c(_lib.lib().mmfhe_keyswitch_noalloc(self.h, keys.h, which, rot, ptr(out), ptr(d), batch, level,
+                                                   stream_ptr(stream)))
+
     def ct_rotsum(self, keys, out, a, batch, level, stride, span, stream=None):
         self._c(_lib.lib().mmfhe_ct_rotsum(self.h, keys.h, ptr(out), ptr(a), batch, level, stride, span,
                                            stream_ptr(stream)))

@@ -90,6 +90,7 @@ _SIGS = {
     "mmfhe_ct_rotate_hoisted": [_VP, _VP, _VP, _VP, _SZ, _U32, _VP, _SZ, _VP],
     "mmfhe_modup": [_VP, _VP, _VP, _SZ, _U32, _VP],
     "mmfhe_keyswitch": [_VP, _VP, _INT, _I32, _VP, _VP, _SZ, _U32, _VP],
+    "mmfhe_keyswitch_noalloc": [_VP, _VP, _INT, _I32, _VP, _VP, _SZ, _U32, _VP],
     "mmfhe_ct_rotsum": [_VP, _VP, _VP, _VP, _SZ, _U32, _I32, _U32, _VP],
     "mmfhe_ct_bsgs": [_VP, _VP, _VP, _VP, _SZ, _U32, _I32, _U32, _VP, _VP, _SZ, _VP],
     "mmfhe_plan_create": [_VP, ctypes.POINTER(CircuitConfig), _SZ, _PP],
