@@ -245,11 +245,20 @@ CtB bsgs(Context &c, const Keys &k, const std::vector<BsgsTerm> &terms, int n1, 
     CtB acc;
     bool have = false;
     for (auto &kv : groups) {
+        // one fused launch per MAX_SUM_TERMS products of the giant step
         CtB inner = ct_new(c, B, level, scale);
-        bool first = true;
-        for (const Item &it : kv.second) {
-            ct_mul_plain(c, inner, *it.baby, *it.pt, !first, st);
-            first = false;
+        const auto &items = kv.second;
+        for (size_t k0 = 0; k0 < items.size(); k0 += MAX_SUM_TERMS) {
+            SumTerms terms{};
+            terms.n = (int)std::min<size_t>(MAX_SUM_TERMS, items.size() - k0);
+            for (int t = 0; t < terms.n; t++) {
+                const Item &it = items[k0 + t];
+                if (it.baby->level != level || it.pt->level != level || it.baby->B != B)
+                    throw Error(MMFHE_ERR_LEVEL_MISMATCH, "bsgs: operand levels differ");
+                terms.ct[t] = it.baby->ptr();
+                terms.pt[t] = it.pt->buf.get();
+            }
+            k_launch_mul_plain_sum(c, inner.ptr(), terms, B, level, k0 > 0, st);
         }
         if (kv.first != 0) inner = rotate(c, k, inner, kv.first * n1 * stride, st);
         if (!have) {

@@ -276,6 +276,26 @@ __global__ void k_rescale_combine(uint64_t *out, const uint64_t *c, const uint64
     }
 }
 
+// out[w] (+)= sum_k ct_k[w] * pt_k[row(w)][x]: one read of every term, one
+// write of the output (the BSGS inner sum of a giant step).
+__global__ void k_mul_plain_sum(uint64_t *out, SumTerms terms, size_t words, int logn, int nl, ModTab mt,
+                                int accumulate) {
+    const uint32_t n = 1u << logn;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < words; w += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(w & (n - 1));
+        const int i = (int)((w >> logn) % nl);
+        const size_t poff = ((size_t)i << logn) + x;
+        const uint64_t q = mt.q[i], mu = mt.mu[i];
+        const uint32_t k = mt.k[i];
+        uint64_t acc = accumulate ? out[w] : 0;
+        for (int t = 0; t < terms.n; t++) {
+            uint64_t v = mm::mul_barrett(__ldg(terms.ct[t] + w), __ldg(terms.pt[t] + poff), q, mu, k);
+            acc = mm::add_mod(acc, v, q);
+        }
+        out[w] = acc;
+    }
+}
+
 // Automorphism of whole rows in the evaluation domain.
 __global__ void k_permute(uint64_t *out, const uint64_t *in, size_t rows, int logn, uint32_t galois) {
     const uint32_t n = 1u << logn;
@@ -392,6 +412,17 @@ void k_launch_rescale_combine(Context &c, uint64_t *out, const uint64_t *cc, con
     size_t work = (size_t)B * 2 * level * c.n;
     dim3 g = grid_for(work);
     LAUNCH(c, "rescale_combine", W8(3 * work), g, k_rescale_combine, out, cc, tmp, B, level, c.logn, c.mods, rc);
+}
+
+void k_launch_mul_plain_sum(Context &c, uint64_t *out, const SumTerms &terms, int B, int level, bool acc,
+                            cudaStream_t st) {
+    const int nl = level + 1;
+    size_t words = (size_t)B * 2 * nl * c.n;
+    if (!words || terms.n == 0) return;
+    dim3 g = grid_for(words);
+    // reads every term once, its constant once, writes (and reads, when accumulating) the output
+    double bytes = W8(words * (terms.n + (acc ? 2 : 1)) + (size_t)terms.n * nl * c.n);
+    LAUNCH(c, "mul_plain_sum", bytes, g, k_mul_plain_sum, out, terms, words, c.logn, nl, c.mods, acc ? 1 : 0);
 }
 
 void k_launch_permute(Context &c, uint64_t *out, const uint64_t *in, size_t rows, uint32_t galois, cudaStream_t st) {

@@ -59,4 +59,15 @@ void k_launch_rescale_combine(Context &c, uint64_t *out, const uint64_t *cc, con
                               const RescaleConsts &rc, cudaStream_t st);
 void k_launch_permute(Context &c, uint64_t *out, const uint64_t *in, size_t rows, uint32_t galois, cudaStream_t st);
 
+// Fused sum of products: out (+)= sum_k ct_k (.) pt_k over a batch of
+// ciphertexts at one level (each ct_k [B][2][l+1][N], each pt_k [l+1][N]).
+constexpr int MAX_SUM_TERMS = 32;
+struct SumTerms {
+    const uint64_t *ct[MAX_SUM_TERMS];
+    const uint64_t *pt[MAX_SUM_TERMS];
+    int n;
+};
+void k_launch_mul_plain_sum(Context &c, uint64_t *out, const SumTerms &terms, int B, int level, bool acc,
+                            cudaStream_t st);
+
 }  // namespace mmfhe

@@ -3,15 +3,21 @@
 // Merged (twisted) Cooley-Tukey forward transform with bit-reversed output:
 // row j of the result holds a(psi^(2 brv(j) + 1)); the Gentleman-Sande inverse
 // takes that order back to coefficients and multiplies by N^-1.  Stage s
-// (m = 2^s butterfly groups, distance t = N / 2^(s+1)) uses twiddle
-// psi^brv(m + i) for group i.
+// (2^s butterfly groups, distance N / 2^(s+1)) uses twiddle psi^brv(2^s + i)
+// for group i.
 //
-// Two passes per transform, each staged through shared memory:
-//  * "cols": stages 0 .. s1-1 only couple elements with equal index mod
-//    T1 = N / 2^s1, so each CTA loads `cols` adjacent columns of H = 2^s1
-//    elements at stride T1 (128-byte row segments) and runs s1 stages;
-//  * "rows": stages s1 .. logN-1 stay inside contiguous blocks of T1
-//    elements, so each CTA loads whole blocks and runs the remaining stages.
+// Two passes per transform, each staged once through shared memory:
+//  * "cols": stages 0 .. S1-1 only couple elements with equal index mod
+//    T1 = N / 2^S1, so a CTA loads 16 adjacent columns of H = 2^S1 elements
+//    at stride T1 (128-byte row segments);
+//  * "rows": stages S1 .. logN-1 stay inside contiguous blocks of T1
+//    elements; a CTA loads whole blocks.
+// Inside a pass every thread owns 16 elements of one column / block and runs
+// the pass's stages in rounds of at most 4: load the 16 elements of its
+// butterfly groups from shared memory into registers, apply the round's
+// stages in registers, store back.  A 256-element column therefore costs two
+// shared-memory round trips for its 8 stages.  All index arithmetic is fixed
+// at compile time per ring dimension (template on log N).
 // Values stay lazily reduced (forward [0, 4q), inverse [0, 2q)) until the
 // last pass.  Launch: grid.y = row, grid.x = tile within the row.
 #include <cuda_runtime.h>
@@ -26,167 +32,169 @@ namespace mmfhe {
 
 namespace {
 
-constexpr int NTT_THREADS = 256;
-constexpr int TILE_WORDS = 4096;   // 32 KiB of shared memory per CTA
-
-struct NttShape {
-    int logn, s1, T1, H, cols, rows_per_cta;
-};
-
-NttShape shape_for(int logn) {
-    NttShape s;
-    s.logn = logn;
-    s.s1 = (logn + 1) / 2;
-    s.T1 = 1 << (logn - s.s1);
-    s.H = 1 << s.s1;
-    s.cols = std::min(16, s.T1);
-    s.rows_per_cta = std::min(s.H, TILE_WORDS / s.T1);
-    return s;
-}
+constexpr int COLS = 16;        // columns per CTA in the strided pass
 
 __device__ __forceinline__ size_t row_offset(const RowMap &m, uint32_t r, int logn) {
     return ((size_t)(r / m.period) * m.block_stride + (r % m.period)) << logn;
 }
 
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_cols(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst,
-                                                              RowMap md, ModTab mt, Twiddles tw, NttShape sh) {
-    extern __shared__ uint64_t sm[];
+// Position of register element (group g, index j) of a round covering local
+// stages [A, A+R) of a sub-transform of size 2^LOG, for thread t that owns
+// 16 >> R groups: j fills bits [POS, POS+R) with POS = LOG - A - R, the group
+// number o = t * (16 >> R) + g fills the other bits.
+template <int LOG, int A, int R>
+__device__ __forceinline__ int elem_index(int t, int g, int j) {
+    constexpr int POS = LOG - A - R;
+    const int o = t * (16 >> R) + g;
+    return ((o >> POS) << (POS + R)) | (j << POS) | (o & ((1 << POS) - 1));
+}
+
+// One round of R stages on 16 register-resident elements.
+//   ADDR(h) -> shared-memory address of local element h
+//   TWI(s, h) -> twiddle index of stage s (local stage, 0-based) for lower element h
+template <int LOG, int A, int R, bool FWD, typename Addr, typename Twi>
+__device__ __forceinline__ void ntt_round(uint64_t *sm, int t, uint64_t q, const uint64_t *__restrict__ W,
+                                          const uint64_t *__restrict__ Wp, Addr addr, Twi twi) {
+    constexpr int G = 16 >> R;
+    constexpr int M = 1 << R;
+    uint64_t x[16];
+#pragma unroll
+    for (int g = 0; g < G; g++)
+#pragma unroll
+        for (int j = 0; j < M; j++) x[g * M + j] = sm[addr(elem_index<LOG, A, R>(t, g, j))];
+#pragma unroll
+    for (int uu = 0; uu < R; uu++) {
+        const int u = FWD ? uu : R - 1 - uu;
+        const int dist = 1 << (R - 1 - u);
+#pragma unroll
+        for (int g = 0; g < G; g++) {
+#pragma unroll
+            for (int j = 0; j < M; j++) {
+                if (j & dist) continue;
+                const int widx = twi(A + u, elem_index<LOG, A, R>(t, g, j));
+                const uint64_t w = __ldg(W + widx), wp = __ldg(Wp + widx);
+                if (FWD)
+                    mm::ct_butterfly(x[g * M + j], x[g * M + j + dist], w, wp, q);
+                else
+                    mm::gs_butterfly(x[g * M + j], x[g * M + j + dist], w, wp, q);
+            }
+        }
+    }
+#pragma unroll
+    for (int g = 0; g < G; g++)
+#pragma unroll
+        for (int j = 0; j < M; j++) sm[addr(elem_index<LOG, A, R>(t, g, j))] = x[g * M + j];
+}
+
+template <int LOGN>
+struct Geo {
+    static constexpr int S1 = (LOGN + 1) / 2;       // stages of the strided pass
+    static constexpr int LOGT = LOGN - S1;          // stages of the contiguous pass
+    static constexpr int H = 1 << S1;               // column length
+    static constexpr int T1 = 1 << LOGT;            // block length
+    static constexpr int R1C = S1 < 4 ? S1 : 4;     // round split of the strided pass
+    static constexpr int R2C = S1 - R1C;
+    static constexpr int R1R = LOGT < 4 ? LOGT : 4; // round split of the contiguous pass
+    static constexpr int R2R = LOGT - R1R;
+    static constexpr int TPC = H / 16;              // threads per column
+    static constexpr int COLS_THREADS = COLS * TPC;
+    static constexpr int TPR = T1 / 16;             // threads per block
+    static constexpr int ROWS = (256 / TPR) < H ? (256 / TPR) : H;   // blocks per CTA
+    static constexpr int RS = T1 + T1 / 16;         // padded block stride in shared memory
+};
+
+// Strided pass. FWD: stages 0..S1-1 (reads src, writes dst); inverse: stages
+// S1-1..0 in place on dst, then the N^-1 factor.
+template <int LOGN, bool FWD>
+__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS)
+    k_ntt_cols(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst, RowMap md, ModTab mt, Twiddles tw) {
+    using Gm = Geo<LOGN>;
+    __shared__ uint64_t sm[Gm::H * COLS];
     const uint32_t r = blockIdx.y;
     const uint8_t pid = md.pid[r % md.period];
     if (pid == SKIP) return;
-    const uint64_t *S = src + row_offset(ms, r, sh.logn);
-    uint64_t *D = dst + row_offset(md, r, sh.logn);
-    const int cols = sh.cols, T1 = sh.T1, H = sh.H, s1 = sh.s1;
-    const int lo0 = blockIdx.x * cols;
+    const uint64_t *S = (FWD ? src + row_offset(ms, r, LOGN) : dst + row_offset(md, r, LOGN));
+    uint64_t *D = dst + row_offset(md, r, LOGN);
+    const int lo0 = blockIdx.x * COLS;
     const uint64_t q = mt.q[pid];
-    for (int e = threadIdx.x; e < H * cols; e += blockDim.x) {
-        int h = e / cols, c = e - h * cols;
-        sm[e] = S[(size_t)h * T1 + lo0 + c];
+    for (int e = threadIdx.x; e < Gm::H * COLS; e += blockDim.x) sm[e] = S[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)];
+    __syncthreads();
+    const int c = threadIdx.x % COLS, t = threadIdx.x / COLS;
+    const uint64_t *W = (FWD ? tw.fw : tw.iw) + ((size_t)pid << LOGN);
+    const uint64_t *Wp = (FWD ? tw.fw_sh : tw.iw_sh) + ((size_t)pid << LOGN);
+    auto addr = [c](int h) { return h * COLS + c; };
+    auto twi = [](int s, int h) { return (1 << s) + (h >> (Gm::S1 - s)); };
+    if (FWD) {
+        ntt_round<Gm::S1, 0, Gm::R1C, true>(sm, t, q, W, Wp, addr, twi);
+        if (Gm::R2C > 0) {
+            __syncthreads();
+            ntt_round<Gm::S1, Gm::R1C, (Gm::R2C > 0 ? Gm::R2C : 1), true>(sm, t, q, W, Wp, addr, twi);
+        }
+    } else {
+        if (Gm::R2C > 0) {
+            ntt_round<Gm::S1, Gm::R1C, (Gm::R2C > 0 ? Gm::R2C : 1), false>(sm, t, q, W, Wp, addr, twi);
+            __syncthreads();
+        }
+        ntt_round<Gm::S1, 0, Gm::R1C, false>(sm, t, q, W, Wp, addr, twi);
     }
     __syncthreads();
-    const uint64_t *W = tw.fw + ((size_t)pid << sh.logn);
-    const uint64_t *Wp = tw.fw_sh + ((size_t)pid << sh.logn);
-    for (int s = 0; s < s1; s++) {
-        const int ltt = s1 - s - 1;
-        for (int e = threadIdx.x; e < (H >> 1) * cols; e += blockDim.x) {
-            int hb = e / cols, c = e - hb * cols;
-            int h = ((hb >> ltt) << (ltt + 1)) + (hb & ((1 << ltt) - 1));
-            int widx = (1 << s) + (h >> (s1 - s));
-            uint64_t X = sm[h * cols + c], Y = sm[(h + (1 << ltt)) * cols + c];
-            mm::ct_butterfly(X, Y, W[widx], Wp[widx], q);
-            sm[h * cols + c] = X;
-            sm[(h + (1 << ltt)) * cols + c] = Y;
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < H * cols; e += blockDim.x) {
-        int h = e / cols, c = e - h * cols;
-        D[(size_t)h * T1 + lo0 + c] = sm[e];
+    if (FWD) {
+        for (int e = threadIdx.x; e < Gm::H * COLS; e += blockDim.x) D[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)] = sm[e];
+    } else {
+        const uint64_t ni = tw.ninv[pid], nip = tw.ninv_sh[pid];
+        for (int e = threadIdx.x; e < Gm::H * COLS; e += blockDim.x)
+            D[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)] = mm::mul_shoup(sm[e], ni, nip, q);
     }
 }
 
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_fwd_rows(uint64_t *dst, RowMap md, ModTab mt, Twiddles tw,
-                                                              NttShape sh) {
-    extern __shared__ uint64_t sm[];
+// Contiguous pass. FWD: stages S1..logN-1 in place on dst, final reduction to
+// [0, q); inverse: stages logN-1..S1 (reads src, writes dst).
+template <int LOGN, bool FWD>
+__global__ void __launch_bounds__(256)
+    k_ntt_rows(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst, RowMap md, ModTab mt, Twiddles tw) {
+    using Gm = Geo<LOGN>;
+    __shared__ uint64_t sm[Gm::ROWS * Gm::RS];
     const uint32_t r = blockIdx.y;
     const uint8_t pid = md.pid[r % md.period];
     if (pid == SKIP) return;
-    uint64_t *D = dst + row_offset(md, r, sh.logn);
-    const int T1 = sh.T1, R = sh.rows_per_cta, s1 = sh.s1, logn = sh.logn;
-    const int hi0 = blockIdx.x * R;
-    uint64_t *blk = D + (size_t)hi0 * T1;
+    const uint64_t *S = (FWD ? dst + row_offset(md, r, LOGN) : src + row_offset(ms, r, LOGN));
+    uint64_t *D = dst + row_offset(md, r, LOGN);
+    const int hi0 = blockIdx.x * Gm::ROWS;
     const uint64_t q = mt.q[pid];
-    for (int e = threadIdx.x; e < R * T1; e += blockDim.x) sm[e] = blk[e];
-    __syncthreads();
-    const uint64_t *W = tw.fw + ((size_t)pid << logn);
-    const uint64_t *Wp = tw.fw_sh + ((size_t)pid << logn);
-    const int half = T1 >> 1;
-    for (int s = s1; s < logn; s++) {
-        const int lt = logn - s - 1;   // t = 2^lt
-        for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
-            int row = e / half, k = e - row * half;
-            int l = ((k >> lt) << (lt + 1)) + (k & ((1 << lt) - 1));
-            int hi = hi0 + row;
-            int widx = (1 << s) + (hi << (s - s1)) + (l >> (logn - s));
-            uint64_t *x = sm + row * T1;
-            uint64_t X = x[l], Y = x[l + (1 << lt)];
-            mm::ct_butterfly(X, Y, W[widx], Wp[widx], q);
-            x[l] = X;
-            x[l + (1 << lt)] = Y;
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < R * T1; e += blockDim.x) blk[e] = mm::reduce_4q(sm[e], q);
-}
-
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_rows(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst,
-                                                              RowMap md, ModTab mt, Twiddles tw, NttShape sh) {
-    extern __shared__ uint64_t sm[];
-    const uint32_t r = blockIdx.y;
-    const uint8_t pid = md.pid[r % md.period];
-    if (pid == SKIP) return;
-    const uint64_t *S = src + row_offset(ms, r, sh.logn);
-    uint64_t *D = dst + row_offset(md, r, sh.logn);
-    const int T1 = sh.T1, R = sh.rows_per_cta, s1 = sh.s1, logn = sh.logn;
-    const int hi0 = blockIdx.x * R;
-    const uint64_t q = mt.q[pid];
-    for (int e = threadIdx.x; e < R * T1; e += blockDim.x) sm[e] = S[(size_t)hi0 * T1 + e];
-    __syncthreads();
-    const uint64_t *W = tw.iw + ((size_t)pid << logn);
-    const uint64_t *Wp = tw.iw_sh + ((size_t)pid << logn);
-    const int half = T1 >> 1;
-    for (int s = logn - 1; s >= s1; s--) {
-        const int lt = logn - s - 1;
-        for (int e = threadIdx.x; e < R * half; e += blockDim.x) {
-            int row = e / half, k = e - row * half;
-            int l = ((k >> lt) << (lt + 1)) + (k & ((1 << lt) - 1));
-            int hi = hi0 + row;
-            int widx = (1 << s) + (hi << (s - s1)) + (l >> (logn - s));
-            uint64_t *x = sm + row * T1;
-            uint64_t X = x[l], Y = x[l + (1 << lt)];
-            mm::gs_butterfly(X, Y, W[widx], Wp[widx], q);
-            x[l] = X;
-            x[l + (1 << lt)] = Y;
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < R * T1; e += blockDim.x) D[(size_t)hi0 * T1 + e] = sm[e];
-}
-
-__global__ void __launch_bounds__(NTT_THREADS) k_ntt_inv_cols(uint64_t *dst, RowMap md, ModTab mt, Twiddles tw,
-                                                              NttShape sh) {
-    extern __shared__ uint64_t sm[];
-    const uint32_t r = blockIdx.y;
-    const uint8_t pid = md.pid[r % md.period];
-    if (pid == SKIP) return;
-    uint64_t *D = dst + row_offset(md, r, sh.logn);
-    const int cols = sh.cols, T1 = sh.T1, H = sh.H, s1 = sh.s1;
-    const int lo0 = blockIdx.x * cols;
-    const uint64_t q = mt.q[pid];
-    for (int e = threadIdx.x; e < H * cols; e += blockDim.x) {
-        int h = e / cols, c = e - h * cols;
-        sm[e] = D[(size_t)h * T1 + lo0 + c];
+    const size_t base = (size_t)hi0 * Gm::T1;
+    for (int e = threadIdx.x; e < Gm::ROWS * Gm::T1; e += blockDim.x) {
+        int rr = e / Gm::T1, l = e % Gm::T1;
+        sm[rr * Gm::RS + l + (l >> 4)] = S[base + e];
     }
     __syncthreads();
-    const uint64_t *W = tw.iw + ((size_t)pid << sh.logn);
-    const uint64_t *Wp = tw.iw_sh + ((size_t)pid << sh.logn);
-    for (int s = s1 - 1; s >= 0; s--) {
-        const int ltt = s1 - s - 1;
-        for (int e = threadIdx.x; e < (H >> 1) * cols; e += blockDim.x) {
-            int hb = e / cols, c = e - hb * cols;
-            int h = ((hb >> ltt) << (ltt + 1)) + (hb & ((1 << ltt) - 1));
-            int widx = (1 << s) + (h >> (s1 - s));
-            uint64_t X = sm[h * cols + c], Y = sm[(h + (1 << ltt)) * cols + c];
-            mm::gs_butterfly(X, Y, W[widx], Wp[widx], q);
-            sm[h * cols + c] = X;
-            sm[(h + (1 << ltt)) * cols + c] = Y;
+    const int t = threadIdx.x % Gm::TPR, rr = threadIdx.x / Gm::TPR;
+    const int hi = hi0 + rr;
+    const uint64_t *W = (FWD ? tw.fw : tw.iw) + ((size_t)pid << LOGN);
+    const uint64_t *Wp = (FWD ? tw.fw_sh : tw.iw_sh) + ((size_t)pid << LOGN);
+    uint64_t *row = sm + rr * Gm::RS;
+    auto addr = [](int l) { return l + (l >> 4); };
+    auto twi = [hi](int u, int l) {
+        const int s = Gm::S1 + u;
+        return (1 << s) + (hi << u) + (l >> (Gm::LOGT - u));
+    };
+    if (FWD) {
+        ntt_round<Gm::LOGT, 0, Gm::R1R, true>(row, t, q, W, Wp, addr, twi);
+        if (Gm::R2R > 0) {
+            __syncthreads();
+            ntt_round<Gm::LOGT, Gm::R1R, (Gm::R2R > 0 ? Gm::R2R : 1), true>(row, t, q, W, Wp, addr, twi);
         }
-        __syncthreads();
+    } else {
+        if (Gm::R2R > 0) {
+            ntt_round<Gm::LOGT, Gm::R1R, (Gm::R2R > 0 ? Gm::R2R : 1), false>(row, t, q, W, Wp, addr, twi);
+            __syncthreads();
+        }
+        ntt_round<Gm::LOGT, 0, Gm::R1R, false>(row, t, q, W, Wp, addr, twi);
     }
-    const uint64_t ni = tw.ninv[pid], nip = tw.ninv_sh[pid];
-    for (int e = threadIdx.x; e < H * cols; e += blockDim.x) {
-        int h = e / cols, c = e - h * cols;
-        D[(size_t)h * T1 + lo0 + c] = mm::mul_shoup(sm[e], ni, nip, q);
+    __syncthreads();
+    for (int e = threadIdx.x; e < Gm::ROWS * Gm::T1; e += blockDim.x) {
+        int r2 = e / Gm::T1, l = e % Gm::T1;
+        uint64_t v = sm[r2 * Gm::RS + l + (l >> 4)];
+        D[base + e] = FWD ? mm::reduce_4q(v, q) : v;
     }
 }
 
@@ -242,10 +250,31 @@ void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cuda
     }
 }
 
+template <int LOGN>
+static void ntt_launch_t(Context &c, const uint64_t *sb, RowMap ms, uint64_t *db, RowMap md, size_t nr, bool inverse,
+                         double bytes, cudaStream_t st) {
+    using Gm = Geo<LOGN>;
+    dim3 gc(Gm::T1 / COLS, (unsigned)nr), bc(Gm::COLS_THREADS);
+    dim3 gr(Gm::H / Gm::ROWS, (unsigned)nr), br(Gm::ROWS * Gm::TPR);
+    if (!inverse) {
+        kernel_begin(c, st);
+        k_ntt_cols<LOGN, true><<<gc, bc, 0, st>>>(sb, ms, db, md, c.mods, c.tw);
+        kernel_end(c, "ntt_fwd_cols", gc, bc, bytes, st);
+        kernel_begin(c, st);
+        k_ntt_rows<LOGN, true><<<gr, br, 0, st>>>(db, md, db, md, c.mods, c.tw);
+        kernel_end(c, "ntt_fwd_rows", gr, br, bytes, st);
+    } else {
+        kernel_begin(c, st);
+        k_ntt_rows<LOGN, false><<<gr, br, 0, st>>>(sb, ms, db, md, c.mods, c.tw);
+        kernel_end(c, "ntt_inv_rows", gr, br, bytes, st);
+        kernel_begin(c, st);
+        k_ntt_cols<LOGN, false><<<gc, bc, 0, st>>>(db, md, db, md, c.mods, c.tw);
+        kernel_end(c, "ntt_inv_cols", gc, bc, bytes, st);
+    }
+}
+
 void launch_ntt(Context &c, const RowsView &src, const RowsView &dst, bool inverse, cudaStream_t st) {
     if (src.rows == 0) return;
-    const NttShape sh = shape_for(c.logn);
-    const size_t smem = TILE_WORDS * sizeof(uint64_t);
     // grid.y is limited to 65535 rows per launch: split on block boundaries
     const size_t chunk = (65535 / src.map.period) * src.map.period;
     for (size_t r0 = 0; r0 < src.rows; r0 += chunk) {
@@ -254,24 +283,18 @@ void launch_ntt(Context &c, const RowsView &src, const RowsView &dst, bool inver
         size_t blocks0 = r0 / ms.period;
         const uint64_t *sb = src.base + ((blocks0 * ms.block_stride) << c.logn);
         uint64_t *db = dst.base + ((blocks0 * md.block_stride) << c.logn);
-        dim3 gc(sh.T1 / sh.cols, (unsigned)nr), gr(sh.H / sh.rows_per_cta, (unsigned)nr), blk(NTT_THREADS);
         size_t live = 0;   // rows actually transformed (skipped rows move no data)
         for (size_t r = 0; r < nr; r++) live += md.pid[r % md.period] != SKIP;
         const double bytes = 2.0 * (double)live * c.n * 8;   // each pass reads and writes every live row once
-        if (!inverse) {
-            kernel_begin(c, st);
-            k_ntt_fwd_cols<<<gc, blk, smem, st>>>(sb, ms, db, md, c.mods, c.tw, sh);
-            kernel_end(c, "ntt_fwd_cols", gc, blk, bytes, st);
-            kernel_begin(c, st);
-            k_ntt_fwd_rows<<<gr, blk, smem, st>>>(db, md, c.mods, c.tw, sh);
-            kernel_end(c, "ntt_fwd_rows", gr, blk, bytes, st);
-        } else {
-            kernel_begin(c, st);
-            k_ntt_inv_rows<<<gr, blk, smem, st>>>(sb, ms, db, md, c.mods, c.tw, sh);
-            kernel_end(c, "ntt_inv_rows", gr, blk, bytes, st);
-            kernel_begin(c, st);
-            k_ntt_inv_cols<<<gc, blk, smem, st>>>(db, md, c.mods, c.tw, sh);
-            kernel_end(c, "ntt_inv_cols", gc, blk, bytes, st);
+        switch (c.logn) {
+        case 10: ntt_launch_t<10>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
+        case 11: ntt_launch_t<11>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
+        case 12: ntt_launch_t<12>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
+        case 13: ntt_launch_t<13>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
+        case 14: ntt_launch_t<14>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
+        case 15: ntt_launch_t<15>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
+        case 16: ntt_launch_t<16>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
+        default: throw Error(MMFHE_ERR_BAD_ARG, "unsupported ring dimension");
         }
     }
     CK(cudaGetLastError());
