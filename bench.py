@@ -83,6 +83,22 @@ def allmax(world, x):
     return float(t.item())
 
 
+def allsum(world, x):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(world, windows, seconds):
+    """Whole-job windows/s of replicas: every rank's windows over the slowest
+    rank's time (each rank evaluates its own users' windows; no exchange)."""
+    return allsum(world, windows) / allmax(world, seconds)
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -324,8 +340,7 @@ def run_mine(args, rank, world, local):
     launches = ctx.launch_count() - launches0
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_s = allmax(world, sum(step_ms) / 1000.0)
-    value = world * B * args.steps / total_s
+    value = job_throughput(world, B * args.steps, sum(step_ms) / 1000.0)
 
     # ---- e2e: pinned host buffers, copies inside the call ----
     pin_in = [torch.from_numpy(x.view(np.int64)).pin_memory() for x in host_in]
@@ -337,8 +352,7 @@ def run_mine(args, rank, world, local):
     for _ in range(args.e2e_steps):
         step(pin_in, pin_out)
     torch.cuda.synchronize()
-    e2e_s = allmax(world, time.perf_counter() - t0)
-    e2e = {"value": world * B * args.e2e_steps / e2e_s, "unit": "windows/s",
+    e2e = {"value": job_throughput(world, B * args.e2e_steps, time.perf_counter() - t0), "unit": "windows/s",
            "h2d_bytes_per_step": B * in_words * 8, "d2h_bytes_per_step": B * out_words * 8}
 
     # ---- per-kernel profile of one more step ----
