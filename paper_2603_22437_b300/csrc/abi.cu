@@ -263,6 +263,7 @@ static Buf load_key(Context &c, const uint64_t *words) {
     for (int i = 0; i < rows; i++) pids[i] = i;
     RowsView v{b.get(), make_map(rows, rows, pids), (size_t)c.dnum * 2 * rows};
     launch_ntt(c, v, v, false, 0);
+    k_launch_mont_convert(c, v, true, 0);   // keys are kept in Montgomery form (key inner product)
     CK(cudaStreamSynchronize(0));
     return b;
 }
@@ -529,6 +530,7 @@ mmfhe_status mmfhe_ct_bsgs(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out
         pts[i] = pt_new(*c, (int)level, 1.0);
         CK(cudaMemcpyAsync(pts[i].buf.get(), diags[i], (size_t)(level + 1) * c->n * 8, cudaMemcpyDefault, st));
         ntt_q_blocks(*c, pts[i].buf.get(), 1, (int)level + 1, false, st);
+        pt_to_mont(*c, pts[i], st);
         need.insert((int)(deltas[i] % n1));
     }
     BsgsTerm t;
@@ -613,9 +615,10 @@ mmfhe_status mmfhe_plan_get_const(const mmfhe_plan *plan, uint32_t i, uint64_t *
     Buf tmp(c->pool.get(), (size_t)nl * c->n);
     std::vector<int> pids(nl);
     for (int k = 0; k < nl; k++) pids[k] = k;
-    RowsView src{pt.buf.get(), make_map(nl, nl, pids), (size_t)nl};
-    RowsView dst{tmp.get(), make_map(nl, nl, pids), (size_t)nl};
-    launch_ntt(*c, src, dst, true, 0);
+    CK(cudaMemcpyAsync(tmp.get(), pt.buf.get(), (size_t)nl * c->n * 8, cudaMemcpyDeviceToDevice, 0));
+    RowsView tv{tmp.get(), make_map(nl, nl, pids), (size_t)nl};
+    if (pt.mont) k_launch_mont_convert(*c, tv, false, 0);
+    launch_ntt(*c, tv, tv, true, 0);
     CK(cudaMemcpy(words, tmp.get(), (size_t)nl * c->n * 8, cudaMemcpyDefault));
     ABI_CATCH(c)
 }

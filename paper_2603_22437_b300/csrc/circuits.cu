@@ -253,6 +253,7 @@ void plan_set_const(Plan &p, uint32_t i, const uint64_t *words_host_or_dev, cuda
     PtDev pt = pt_new(c, level, (double)c.primes[level]);
     CK(cudaMemcpyAsync(pt.buf.get(), words_host_or_dev, (size_t)(level + 1) * c.n * 8, cudaMemcpyDefault, st));
     ntt_q_blocks(c, pt.buf.get(), 1, level + 1, false, st);
+    pt_to_mont(c, pt, st);   // plan constants are kept in Montgomery form
     p.consts[i] = std::move(pt);
 }
 

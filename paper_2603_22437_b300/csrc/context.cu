@@ -269,7 +269,14 @@ Context *create_context(const mmfhe_params &p, int device) {
             c->mods.q[i] = c->primes[i];
             c->mods.mu[i] = hm::barrett_mu(c->primes[i]);
             c->mods.k[i] = hm::bitlen(c->primes[i]);
+            uint64_t inv = 1;
+            for (int it = 0; it < 7; it++) inv *= 2 - c->primes[i] * inv;   // Newton: q^-1 mod 2^64
+            c->mods.qinv[i] = inv;
+            c->mods.r64[i] = (uint64_t)(((hm::u128)1 << 64) % c->primes[i]);
         }
+        uint64_t qmax = 0;
+        for (int i = 0; i < c->num_q; i++) qmax = std::max(qmax, c->primes[i]);
+        c->sum_terms_max = (int)std::min<uint64_t>(16, (~0ull) / qmax);
         // twiddles: fw[i] = psi^brv(i), iw[i] = psi^-brv(i)
         const uint32_t n = c->n;
         std::vector<uint64_t> tw(4ull * np * n), ninv(2ull * np);

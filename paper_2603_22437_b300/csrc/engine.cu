@@ -67,7 +67,15 @@ void ct_addsub(Context &c, CtB &out, const CtB &a, const CtB &b, bool sub, cudaS
 void ct_mul_plain(Context &c, CtB &out, const CtB &a, const PtDev &pt, bool acc, cudaStream_t st) {
     if (a.level != pt.level) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "mul_plain: level mismatch");
     k_launch_mul_plain(c, out.ptr(), a.ptr(), pt.buf.get(), (size_t)a.B * 2 * (a.level + 1), pids_q(a.level + 1),
-                       a.level + 1, acc, st);
+                       a.level + 1, acc, st, pt.mont);
+}
+
+void pt_to_mont(Context &c, PtDev &pt, cudaStream_t st) {
+    if (pt.mont) return;
+    const int nl = pt.level + 1;
+    RowsView v{pt.buf.get(), make_map(nl, nl, iota_pids(nl)), (size_t)nl};
+    k_launch_mont_convert(c, v, true, st);
+    pt.mont = true;
 }
 
 void ct_mul_int(Context &c, CtB &out, const CtB &a, long long k, cudaStream_t st) {
@@ -134,7 +142,7 @@ DigitsB modup(Context &c, const uint64_t *d_eval, size_t block_stride_rows, int 
 }
 
 CtB keyswitch_moddown(Context &c, const DigitsB &dg, const uint64_t *key, uint32_t galois, const uint64_t *add0,
-                      const uint64_t *add1, size_t add_stride_words, double scale, cudaStream_t st) {
+                      const uint64_t *add1, size_t add_stride_words, double scale, cudaStream_t st, const CtB *plus) {
     const int level = dg.level, B = dg.B, nl = level + 1, nre = level + 1 + c.num_p;
     Buf u(c.pool.get(), (size_t)B * 2 * nre * c.n);
     k_launch_keyip(c, u.get(), dg.buf.get(), key, B, level, dg.beta, galois, st);
@@ -147,7 +155,9 @@ CtB keyswitch_moddown(Context &c, const DigitsB &dg, const uint64_t *key, uint32
     k_launch_moddown_bconv(c, v.get(), u.get(), B, level, dc, st);
     ntt_q_blocks(c, v.get(), (size_t)B * 2, nl, false, st);
     CtB out = ct_new(c, B, level, scale);
-    k_launch_moddown_combine(c, out.ptr(), u.get(), v.get(), add0, add1, add_stride_words, galois, B, level, dc, st);
+    if (plus && (plus->level != level || plus->B != B)) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "add: operand levels differ");
+    k_launch_moddown_combine(c, out.ptr(), u.get(), v.get(), add0, add1, add_stride_words, galois, B, level, dc, st,
+                             plus ? plus->ptr() : nullptr);
     return out;
 }
 
@@ -214,12 +224,25 @@ CtB rotate(Context &c, const Keys &k, const CtB &a, int32_t rot, cudaStream_t st
     return std::move(v[0]);
 }
 
-CtB rotsum(Context &c, const Keys &k, const CtB &a, int32_t stride, uint32_t span, cudaStream_t st) {
-    CtB x = ct_copy(c, a, st);
-    for (uint32_t s = 1; s < span; s <<= 1) {
-        CtB r = rotate(c, k, x, stride * (int32_t)s, st);
-        ct_addsub(c, x, x, r, false, st);
+CtB rotate_add(Context &c, const Keys &k, const CtB &a, int32_t rot, const CtB &plus, cudaStream_t st) {
+    int32_t nr = norm_rot(c, rot);
+    if (nr == 0) {
+        CtB r = ct_new(c, a.B, a.level, a.scale);
+        ct_addsub(c, r, a, plus, false, st);
+        return r;
     }
+    const int nl = a.level + 1;
+    const uint64_t *key = galois_key(k, nr);
+    DigitsB dg = modup(c, a.ptr() + (size_t)nl * c.n, (size_t)2 * nl, a.B, a.level, st);
+    return keyswitch_moddown(c, dg, key, galois_elt(c, nr), a.ptr(), nullptr, (size_t)2 * nl * c.n, a.scale, st,
+                             &plus);
+}
+
+CtB rotsum(Context &c, const Keys &k, const CtB &a, int32_t stride, uint32_t span, cudaStream_t st) {
+    if (span <= 1) return ct_copy(c, a, st);
+    // x <- x + Rot(x, stride s): the addition happens inside the key switch's last kernel
+    CtB x = rotate_add(c, k, a, stride, a, st);
+    for (uint32_t s = 2; s < span; s <<= 1) x = rotate_add(c, k, x, stride * (int32_t)s, x, st);
     return x;
 }
 
@@ -248,22 +271,25 @@ CtB bsgs(Context &c, const Keys &k, const std::vector<BsgsTerm> &terms, int n1, 
         // one fused launch per MAX_SUM_TERMS products of the giant step
         CtB inner = ct_new(c, B, level, scale);
         const auto &items = kv.second;
-        for (size_t k0 = 0; k0 < items.size(); k0 += MAX_SUM_TERMS) {
+        const size_t chunk = (size_t)std::min(MAX_SUM_TERMS, c.sum_terms_max);
+        for (size_t k0 = 0; k0 < items.size(); k0 += chunk) {
             SumTerms terms{};
-            terms.n = (int)std::min<size_t>(MAX_SUM_TERMS, items.size() - k0);
+            terms.n = (int)std::min<size_t>(chunk, items.size() - k0);
             for (int t = 0; t < terms.n; t++) {
                 const Item &it = items[k0 + t];
                 if (it.baby->level != level || it.pt->level != level || it.baby->B != B)
                     throw Error(MMFHE_ERR_LEVEL_MISMATCH, "bsgs: operand levels differ");
+                if (!it.pt->mont) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: diagonals must be in Montgomery form");
                 terms.ct[t] = it.baby->ptr();
                 terms.pt[t] = it.pt->buf.get();
             }
             k_launch_mul_plain_sum(c, inner.ptr(), terms, B, level, k0 > 0, st);
         }
-        if (kv.first != 0) inner = rotate(c, k, inner, kv.first * n1 * stride, st);
         if (!have) {
-            acc = std::move(inner);
+            acc = kv.first != 0 ? rotate(c, k, inner, kv.first * n1 * stride, st) : std::move(inner);
             have = true;
+        } else if (kv.first != 0) {
+            acc = rotate_add(c, k, inner, kv.first * n1 * stride, acc, st);   // acc + Rot(inner)
         } else {
             ct_addsub(c, acc, acc, inner, false, st);
         }

@@ -25,6 +25,8 @@ void ntt_q_blocks(Context &c, uint64_t *base, size_t blocks, int nl, bool invers
 void ct_addsub(Context &c, CtB &out, const CtB &a, const CtB &b, bool sub, cudaStream_t st);
 void ct_mul_plain(Context &c, CtB &out, const CtB &a, const PtDev &pt, bool acc, cudaStream_t st);
 void ct_mul_int(Context &c, CtB &out, const CtB &a, long long k, cudaStream_t st);
+// Convert a plaintext (evaluation domain) into Montgomery form, in place.
+void pt_to_mont(Context &c, PtDev &pt, cudaStream_t st);
 CtB ct_copy(Context &c, const CtB &a, cudaStream_t st);
 CtB ct_drop(Context &c, const CtB &a, int level, cudaStream_t st);
 
@@ -41,10 +43,13 @@ DigitsB modup(Context &c, const uint64_t *d_eval, size_t block_stride_rows, int 
 // applies the automorphism to the digits; add0/add1 optional addends (add0
 // read through the same automorphism).
 CtB keyswitch_moddown(Context &c, const DigitsB &dg, const uint64_t *key, uint32_t galois, const uint64_t *add0,
-                      const uint64_t *add1, size_t add_stride_words, double scale, cudaStream_t st);
+                      const uint64_t *add1, size_t add_stride_words, double scale, cudaStream_t st,
+                      const CtB *plus = nullptr);
 const uint64_t *galois_key(const Keys &k, int32_t rot);
 
 CtB rotate(Context &c, const Keys &k, const CtB &a, int32_t rot, cudaStream_t st);
+// Rot(a, rot) + plus, the addition fused into the key switch's last kernel.
+CtB rotate_add(Context &c, const Keys &k, const CtB &a, int32_t rot, const CtB &plus, cudaStream_t st);
 std::vector<CtB> rotate_hoisted(Context &c, const Keys &k, const CtB &a, const std::vector<int32_t> &rots,
                                 cudaStream_t st);
 CtB rotsum(Context &c, const Keys &k, const CtB &a, int32_t stride, uint32_t span, cudaStream_t st);

@@ -29,7 +29,9 @@ void cuda_check(cudaError_t e, const char *what);
 // Moduli passed by value to kernels (constant-bank resident).
 struct ModTab {
     uint64_t q[MAXPRIMES];
-    uint64_t mu[MAXPRIMES];
+    uint64_t mu[MAXPRIMES];     // Barrett constant floor(2^(2k) / q)
+    uint64_t qinv[MAXPRIMES];   // q^-1 mod 2^64 (Montgomery reduction)
+    uint64_t r64[MAXPRIMES];    // 2^64 mod q (conversion into Montgomery form)
     uint32_t k[MAXPRIMES];
 };
 
@@ -128,6 +130,7 @@ struct Context {
     uint64_t *d_dn_phat = nullptr, *d_dn_phat_sh = nullptr;
     uint64_t *d_dn_pmod = nullptr, *d_dn_pmod_sh = nullptr, *d_dn_Pinv = nullptr, *d_dn_Pinv_sh = nullptr;
     std::vector<LevelConsts> lv;     // per level 0..L
+    int sum_terms_max = 8;           // products one Montgomery reduction may absorb: n*q_max < 2^64
     std::unique_ptr<Pool> pool;
     uint64_t launches = 0;
     std::string last_error;
@@ -181,6 +184,7 @@ struct PtDev {
     Buf buf;
     int level = -1;
     double scale = 0.0;
+    bool mont = false;   // words stored as x * 2^64 mod q (Montgomery form)
 };
 
 struct Keys {

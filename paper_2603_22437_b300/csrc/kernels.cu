@@ -50,15 +50,30 @@ __global__ void k_mul_int(uint64_t *out, const uint64_t *a, size_t words, int lo
     }
 }
 
-// out[r] (+)= a[r] * pt[r % period]   (pt rows = one plaintext, shared by all blocks)
+// out[r] (+)= a[r] * pt[r % period]   (pt rows = one plaintext, shared by all
+// blocks; mont: pt is in Montgomery form)
 __global__ void k_mul_plain(uint64_t *out, const uint64_t *a, const uint64_t *pt, size_t words, int logn,
-                            uint32_t period, ModTab mt, PidList pl, int accumulate) {
+                            uint32_t period, ModTab mt, PidList pl, int accumulate, int mont) {
     const uint32_t n = 1u << logn;
     for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < words; w += (size_t)gridDim.x * blockDim.x) {
         uint32_t row = (uint32_t)(w >> logn) % period;
         int pid = pl.pid[row];
-        uint64_t v = mulq(a[w], pt[(size_t)row * n + (w & (n - 1))], mt, pid);
+        const uint64_t av = a[w], pv = pt[(size_t)row * n + (w & (n - 1))];
+        uint64_t v = mont ? mm::redc(mm::mulhi64(av, pv), av * pv, mt.q[pid], mt.qinv[pid]) : mulq(av, pv, mt, pid);
         out[w] = accumulate ? mm::add_mod(out[w], v, mt.q[pid]) : v;
+    }
+}
+
+// Rows into (to = 1) or out of (to = 0) Montgomery form, in place.
+__global__ void k_mont_convert(uint64_t *base, RowMap map, size_t rows, int logn, ModTab mt, int to) {
+    const uint32_t n = 1u << logn;
+    const size_t total = rows << logn;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t r = (uint32_t)(w >> logn);
+        const uint8_t pid = map.pid[r % map.period];
+        if (pid == SKIP) continue;
+        uint64_t *p = base + (((size_t)(r / map.period) * map.block_stride + (r % map.period)) << logn) + (w & (n - 1));
+        *p = to ? mulq(*p, mt.r64[pid], mt, pid) : mm::redc(0, *p, mt.q[pid], mt.qinv[pid]);
     }
 }
 
@@ -159,17 +174,19 @@ __global__ void k_keyip(uint64_t *u, const uint64_t *digits, const uint64_t *key
             kb[j] = key[(((size_t)j * 2 + 0) * key_rows + krow) * n + x];
             ka[j] = key[(((size_t)j * 2 + 1) * key_rows + krow) * n + x];
         }
-        uint64_t q = mt.q[pid];
+        const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
+        // keys are in Montgomery form: sum the 128-bit products of the digits
+        // (beta q^2 < q 2^64 because beta <= 8 and q < 2^61), reduce once
         for (int bb = 0; bb < B; bb++) {
-            uint64_t a0 = 0, a1 = 0;
+            uint64_t h0 = 0, l0 = 0, h1 = 0, l1 = 0;
             for (int j = 0; j < beta; j++) {
                 uint64_t dv = digits[(((size_t)bb * beta + j) * nrows_ext + t) * n + px];
-                a0 = mm::add_mod(a0, mulq(dv, kb[j], mt, pid), q);
-                a1 = mm::add_mod(a1, mulq(dv, ka[j], mt, pid), q);
+                mm::mac128(h0, l0, dv, kb[j]);
+                mm::mac128(h1, l1, dv, ka[j]);
             }
             uint64_t *U = u + ((size_t)bb * 2 * nrows_ext) * n;
-            U[(size_t)t * n + x] = a0;
-            U[((size_t)nrows_ext + t) * n + x] = a1;
+            U[(size_t)t * n + x] = mm::redc(h0, l0, q, qinv);
+            U[((size_t)nrows_ext + t) * n + x] = mm::redc(h1, l1, q, qinv);
         }
     }
 }
@@ -214,7 +231,7 @@ __global__ void k_moddown_bconv(uint64_t *v, const uint64_t *u, int B, int level
 //                   + add_h[b][i][perm(x)]   (add_h optional; perm = galois map)
 __global__ void k_moddown_combine(uint64_t *out, const uint64_t *u, const uint64_t *v, const uint64_t *add0,
                                   const uint64_t *add1, size_t add_stride, uint32_t add_galois, int B, int level,
-                                  int K, int logn, ModTab mt, ModDownConsts dc) {
+                                  int K, int logn, ModTab mt, ModDownConsts dc, const uint64_t *plus) {
     const uint32_t n = 1u << logn;
     const int nl = level + 1, nre = level + 1 + K;
     const size_t total = (size_t)B * 2 * nl * n;
@@ -234,6 +251,7 @@ __global__ void k_moddown_combine(uint64_t *out, const uint64_t *u, const uint64
             uint32_t px = add_galois == 1 ? x : mm::galois_perm(x, add_galois, logn);
             res = mm::add_mod(res, A[bb * add_stride + (size_t)i * n + px], q);
         }
+        if (plus) res = mm::add_mod(res, plus[w], q);   // same [B][2][l+1][N] layout as out
         out[w] = res;
     }
 }
@@ -285,14 +303,13 @@ __global__ void k_mul_plain_sum(uint64_t *out, SumTerms terms, size_t words, int
         const uint32_t x = (uint32_t)(w & (n - 1));
         const int i = (int)((w >> logn) % nl);
         const size_t poff = ((size_t)i << logn) + x;
-        const uint64_t q = mt.q[i], mu = mt.mu[i];
-        const uint32_t k = mt.k[i];
-        uint64_t acc = accumulate ? out[w] : 0;
-        for (int t = 0; t < terms.n; t++) {
-            uint64_t v = mm::mul_barrett(__ldg(terms.ct[t] + w), __ldg(terms.pt[t] + poff), q, mu, k);
-            acc = mm::add_mod(acc, v, q);
-        }
-        out[w] = acc;
+        const uint64_t q = mt.q[i], qinv = mt.qinv[i];
+        // constants are in Montgomery form: 128-bit sum of products, one reduction
+        // (the launcher keeps terms.n * q < 2^64)
+        uint64_t hi = 0, lo = 0;
+        for (int t = 0; t < terms.n; t++) mm::mac128(hi, lo, __ldg(terms.ct[t] + w), __ldg(terms.pt[t] + poff));
+        uint64_t v = mm::redc(hi, lo, q, qinv);
+        out[w] = accumulate ? mm::add_mod(out[w], v, q) : v;
     }
 }
 
@@ -340,13 +357,21 @@ void k_launch_mul_int(Context &c, uint64_t *out, const uint64_t *a, size_t rows,
 }
 
 void k_launch_mul_plain(Context &c, uint64_t *out, const uint64_t *a, const uint64_t *pt, size_t rows,
-                        const PidList &pl, uint32_t period, bool acc, cudaStream_t st) {
+                        const PidList &pl, uint32_t period, bool acc, cudaStream_t st, bool mont) {
     size_t words = rows << c.logn;
     if (!words) return;
     dim3 g = grid_for(words);
     double bytes = W8((acc ? 3 : 2) * words + ((size_t)period << c.logn));
     LAUNCH(c, acc ? "mul_plain_acc" : "mul_plain", bytes, g, k_mul_plain, out, a, pt, words, c.logn, period, c.mods,
-           pl, acc ? 1 : 0);
+           pl, acc ? 1 : 0, mont ? 1 : 0);
+}
+
+void k_launch_mont_convert(Context &c, const RowsView &v, bool to, cudaStream_t st) {
+    size_t words = v.rows << c.logn;
+    if (!words) return;
+    dim3 g = grid_for(words);
+    LAUNCH(c, to ? "to_mont" : "from_mont", W8(2 * words), g, k_mont_convert, v.base, v.map, v.rows, c.logn, c.mods,
+           to ? 1 : 0);
 }
 
 void k_launch_tensor(Context &c, uint64_t *d, const uint64_t *a, const uint64_t *b, int B, int level, long long coef,
@@ -392,12 +417,12 @@ void k_launch_moddown_bconv(Context &c, uint64_t *v, const uint64_t *u, int B, i
 
 void k_launch_moddown_combine(Context &c, uint64_t *out, const uint64_t *u, const uint64_t *v, const uint64_t *add0,
                               const uint64_t *add1, size_t add_stride, uint32_t add_galois, int B, int level,
-                              const ModDownConsts &dc, cudaStream_t st) {
+                              const ModDownConsts &dc, cudaStream_t st, const uint64_t *plus) {
     size_t work = (size_t)B * 2 * (level + 1) * c.n;
     dim3 g = grid_for(work);
-    double bytes = W8(work * 3 + (add0 ? work / 2 : 0) + (add1 ? work / 2 : 0));
+    double bytes = W8(work * 3 + (add0 ? work / 2 : 0) + (add1 ? work / 2 : 0) + (plus ? work : 0));
     LAUNCH(c, "moddown_combine", bytes, g, k_moddown_combine, out, u, v, add0, add1, add_stride, add_galois, B, level,
-           c.num_p, c.logn, c.mods, dc);
+           c.num_p, c.logn, c.mods, dc, plus);
 }
 
 void k_launch_rescale_spread(Context &c, uint64_t *tmp, const uint64_t *last, int B, int level,
@@ -419,6 +444,7 @@ void k_launch_mul_plain_sum(Context &c, uint64_t *out, const SumTerms &terms, in
     const int nl = level + 1;
     size_t words = (size_t)B * 2 * nl * c.n;
     if (!words || terms.n == 0) return;
+    if (terms.n > c.sum_terms_max) throw Error(MMFHE_ERR_BAD_ARG, "mul_plain_sum: too many terms for one reduction");
     dim3 g = grid_for(words);
     // reads every term once, its constant once, writes (and reads, when accumulating) the output
     double bytes = W8(words * (terms.n + (acc ? 2 : 1)) + (size_t)terms.n * nl * c.n);

@@ -41,7 +41,9 @@ void k_launch_addsub(Context &c, uint64_t *out, const uint64_t *a, const uint64_
 void k_launch_mul_int(Context &c, uint64_t *out, const uint64_t *a, size_t rows, const PidList &pl, uint32_t period,
                       long long k, cudaStream_t st);
 void k_launch_mul_plain(Context &c, uint64_t *out, const uint64_t *a, const uint64_t *pt, size_t rows,
-                        const PidList &pl, uint32_t period, bool acc, cudaStream_t st);
+                        const PidList &pl, uint32_t period, bool acc, cudaStream_t st, bool mont = false);
+// Convert rows of a view into (to) or out of Montgomery form, in place.
+void k_launch_mont_convert(Context &c, const RowsView &v, bool to, cudaStream_t st);
 void k_launch_tensor(Context &c, uint64_t *d, const uint64_t *a, const uint64_t *b, int B, int level, long long coef,
                      bool acc, cudaStream_t st);
 void k_launch_modup_bconv(Context &c, uint64_t *out, const uint64_t *coef, const uint64_t *deval, size_t deval_stride,
@@ -52,7 +54,7 @@ void k_launch_moddown_bconv(Context &c, uint64_t *v, const uint64_t *u, int B, i
                             cudaStream_t st);
 void k_launch_moddown_combine(Context &c, uint64_t *out, const uint64_t *u, const uint64_t *v, const uint64_t *add0,
                               const uint64_t *add1, size_t add_stride, uint32_t add_galois, int B, int level,
-                              const ModDownConsts &dc, cudaStream_t st);
+                              const ModDownConsts &dc, cudaStream_t st, const uint64_t *plus = nullptr);
 void k_launch_rescale_spread(Context &c, uint64_t *tmp, const uint64_t *last, int B, int level,
                              const RescaleConsts &rc, cudaStream_t st);
 void k_launch_rescale_combine(Context &c, uint64_t *out, const uint64_t *cc, const uint64_t *tmp, int B, int level,
@@ -60,8 +62,9 @@ void k_launch_rescale_combine(Context &c, uint64_t *out, const uint64_t *cc, con
 void k_launch_permute(Context &c, uint64_t *out, const uint64_t *in, size_t rows, uint32_t galois, cudaStream_t st);
 
 // Fused sum of products: out (+)= sum_k ct_k (.) pt_k over a batch of
-// ciphertexts at one level (each ct_k [B][2][l+1][N], each pt_k [l+1][N]).
-constexpr int MAX_SUM_TERMS = 32;
+// ciphertexts at one level (each ct_k [B][2][l+1][N], each pt_k [l+1][N] in
+// Montgomery form); at most Context::sum_terms_max terms per launch.
+constexpr int MAX_SUM_TERMS = 16;
 struct SumTerms {
     const uint64_t *ct[MAX_SUM_TERMS];
     const uint64_t *pt[MAX_SUM_TERMS];

@@ -72,6 +72,23 @@ MM_HD uint64_t sub_mod(uint64_t a, uint64_t b, uint64_t q) {
     return a >= b ? a - b : a + q - b;
 }
 
+// Montgomery reduction (R = 2^64): for T = hi*2^64 + lo < q*2^64, q odd,
+// qinv = q^-1 mod 2^64, returns T * 2^-64 mod q in [0, q).  With
+// m = lo*qinv, T - m*q is divisible by 2^64 and (T - m*q)/2^64 = hi - mulhi(m, q)
+// lies in (-q, q).
+MM_HD uint64_t redc(uint64_t hi, uint64_t lo, uint64_t q, uint64_t qinv) {
+    uint64_t m = lo * qinv;
+    uint64_t mh = mulhi64(m, q);
+    return hi >= mh ? hi - mh : hi - mh + q;
+}
+
+// 128-bit multiply-accumulate (hi:lo) += a*b.
+MM_HD void mac128(uint64_t &hi, uint64_t &lo, uint64_t a, uint64_t b) {
+    uint64_t pl = a * b, ph = mulhi64(a, b);
+    lo += pl;
+    hi += ph + (lo < pl ? 1 : 0);
+}
+
 // Reduce x in [0, 4q) to [0, q).
 MM_HD uint64_t reduce_4q(uint64_t x, uint64_t q) {
     uint64_t q2 = q << 1;
