@@ -466,6 +466,7 @@ mmfhe_status mmfhe_modup(mmfhe_ctx *ctx, uint64_t *out, const uint64_t *d, size_
     CK(cudaMemcpyAsync(dd.get(), d, batch * nl * c->n * 8, cudaMemcpyDefault, st));
     ntt_q_blocks(*c, dd.get(), batch, nl, false, st);
     DigitsB dg = modup(*c, dd.get(), (size_t)nl, (int)batch, (int)level, st);
+    digits_fill_own(*c, dg, st);
     std::vector<int> pids(nre);
     for (int t = 0; t < nre; t++) pids[t] = t <= (int)level ? t : c->num_q + (t - nl);
     RowsView v{dg.buf.get(), make_map(nre, nre, pids), batch * dg.beta * nre};

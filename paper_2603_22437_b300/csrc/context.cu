@@ -182,6 +182,34 @@ static void build_level_consts(Context &c) {
                 }
             }
         }
+        // fused ModUp: Montgomery-form conversion factors; the inverse NTT's final
+        // multiply by N^-1 (Qhat_{j,u})^-1 (q rows) or N^-1 Phat_k^-1 (p rows)
+        std::vector<uint64_t> m_mont(mm_.size(), 0), ks(MAXPRIMES, 0), ks_sh(MAXPRIMES, 0);
+        for (int j = 0; j < lc.beta; j++)
+            for (size_t u = 0; u < lc.digits[j].size(); u++) {
+                const int i = lc.digits[j][u];
+                const uint64_t qi = c.primes[i];
+                ks[i] = hm::mulmod(hm::invmod(c.n % qi, qi), inv[j * MAX_ALPHA + u], qi);
+                ks_sh[i] = hm::shoup(ks[i], qi);
+                for (int t = 0; t < nre; t++) {
+                    const int pid = t <= l ? t : c.num_q + (t - l - 1);
+                    const uint64_t pt = c.primes[pid];
+                    const size_t ci = ((size_t)j * MAX_ALPHA + u) * MAXROWMAP + t;
+                    m_mont[ci] = hm::mulmod(mm_[ci], c.mods.r64[pid], pt);
+                }
+            }
+        for (int k = 0; k < K; k++) {
+            const int pid = c.num_q + k;
+            const uint64_t pk = c.primes[pid];
+            uint64_t ph = 1;
+            for (int m = 0; m < K; m++)
+                if (m != k) ph = hm::mulmod(ph, c.primes[c.num_q + m] % pk, pk);
+            ks[pid] = hm::mulmod(hm::invmod(c.n % pk, pk), hm::invmod(ph, pk), pk);
+            ks_sh[pid] = hm::shoup(ks[pid], pk);
+        }
+        lc.d_up_mm = upload(c, m_mont);
+        lc.d_ks_scale = upload(c, ks);
+        lc.d_ks_scale_sh = upload(c, ks_sh);
         lc.d_up_inv = upload(c, inv);
         lc.d_up_inv_sh = upload(c, inv_sh);
         lc.d_up_m = upload(c, mm_);
@@ -228,6 +256,15 @@ static void build_level_consts(Context &c) {
         Pinv[i] = hm::invmod(P, qi);
         Pinv_sh[i] = hm::shoup(Pinv[i], qi);
     }
+    std::vector<uint64_t> phat_mont(phat.size(), 0), negp_mont(MMFHE_MAX_Q, 0);
+    for (int i = 0; i < c.num_q; i++) {
+        const uint64_t qi = c.primes[i];
+        for (int k = 0; k < K; k++)
+            phat_mont[k * MMFHE_MAX_Q + i] = hm::mulmod(phat[k * MMFHE_MAX_Q + i], c.mods.r64[i], qi);
+        negp_mont[i] = hm::mulmod((qi - pmod[i]) % qi, c.mods.r64[i], qi);
+    }
+    c.d_dn_phat_mont = upload(c, phat_mont);
+    c.d_dn_negp_mont = upload(c, negp_mont);
     c.d_dn_pinv = upload(c, pinv);
     c.d_dn_pinv_sh = upload(c, pinv_sh);
     c.d_dn_phat = upload(c, phat);

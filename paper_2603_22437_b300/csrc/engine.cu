@@ -121,43 +121,52 @@ DigitsB modup(Context &c, const uint64_t *d_eval, size_t block_stride_rows, int 
     dg.B = B;
     dg.level = level;
     dg.beta = lc.beta;
+    dg.own = d_eval;
+    dg.own_stride = block_stride_rows * c.n;
     dg.buf = Buf(c.pool.get(), (size_t)B * lc.beta * nre * c.n);
-    Buf coef(c.pool.get(), (size_t)B * nl * c.n);
+    // y = [x (Qhat_{j,u})^-1]_{q_i} in coefficient form: the inverse NTT's last multiply
+    Buf y(c.pool.get(), (size_t)B * nl * c.n);
     RowsView src{const_cast<uint64_t *>(d_eval), make_map(nl, (uint32_t)block_stride_rows, iota_pids(nl)), (size_t)B * nl};
-    RowsView dst{coef.get(), make_map(nl, nl, iota_pids(nl)), (size_t)B * nl};
-    launch_ntt(c, src, dst, true, st);
-    k_launch_modup_bconv(c, dg.buf.get(), coef.get(), d_eval, block_stride_rows * c.n, B, level, modup_consts(c, level),
-                         st);
-    // forward NTT of the converted rows (a digit's own rows are already in the evaluation domain)
-    for (int j = 0; j < lc.beta; j++) {
-        std::vector<int> pids(nre);
-        for (int t = 0; t < nre; t++) {
-            bool own = t <= level && t >= lc.digits[j].front() && t <= lc.digits[j].back();
-            pids[t] = own ? -1 : (t <= level ? t : c.num_q + (t - level - 1));
-        }
-        RowsView v{dg.buf.get() + (size_t)j * nre * c.n, make_map(nre, lc.beta * nre, pids), (size_t)B * nre};
-        launch_ntt(c, v, v, false, st);
-    }
+    RowsView dst{y.get(), make_map(nl, nl, iota_pids(nl)), (size_t)B * nl};
+    launch_ntt(c, src, dst, true, st, lc.d_ks_scale, lc.d_ks_scale_sh);
+    // FastBConv to every other prime inside the forward NTT of each digit row
+    launch_modup_ntt(c, dg.buf.get(), y.get(), B, level, st);
     return dg;
+}
+
+void digits_fill_own(Context &c, DigitsB &dg, cudaStream_t st) {
+    const int nl = dg.level + 1, nre = nl + c.num_p;
+    const LevelConsts &lc = c.lv[dg.level];
+    for (int j = 0; j < dg.beta; j++) {
+        std::vector<int> pids(nre, -1);
+        for (int t : lc.digits[j]) pids[t] = t;
+        RowsView src{const_cast<uint64_t *>(dg.own), make_map(nre, (uint32_t)(dg.own_stride / c.n), pids),
+                     (size_t)dg.B * nre};
+        RowsView dst{dg.buf.get() + (size_t)j * nre * c.n, make_map(nre, dg.beta * nre, pids), (size_t)dg.B * nre};
+        launch_copy_rows(c, src, dst, st);
+    }
 }
 
 CtB keyswitch_moddown(Context &c, const DigitsB &dg, const uint64_t *key, uint32_t galois, const uint64_t *add0,
                       const uint64_t *add1, size_t add_stride_words, double scale, cudaStream_t st, const CtB *plus) {
-    const int level = dg.level, B = dg.B, nl = level + 1, nre = level + 1 + c.num_p;
-    Buf u(c.pool.get(), (size_t)B * 2 * nre * c.n);
-    k_launch_keyip(c, u.get(), dg.buf.get(), key, B, level, dg.beta, galois, st);
-    std::vector<int> pids(nre, -1);
-    for (int k = 0; k < c.num_p; k++) pids[nl + k] = c.num_q + k;
-    RowsView pv{u.get(), make_map(nre, nre, pids), (size_t)B * 2 * nre};
-    launch_ntt(c, pv, pv, true, st);
-    Buf v(c.pool.get(), (size_t)B * 2 * nl * c.n);
-    ModDownConsts dc = moddown_consts(c);
-    k_launch_moddown_bconv(c, v.get(), u.get(), B, level, dc, st);
-    ntt_q_blocks(c, v.get(), (size_t)B * 2, nl, false, st);
-    CtB out = ct_new(c, B, level, scale);
+    const int level = dg.level, B = dg.B, nl = level + 1, nre = level + 1 + c.num_p, K = c.num_p;
     if (plus && (plus->level != level || plus->B != B)) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "add: operand levels differ");
-    k_launch_moddown_combine(c, out.ptr(), u.get(), v.get(), add0, add1, add_stride_words, galois, B, level, dc, st,
-                             plus ? plus->ptr() : nullptr);
+    Buf u(c.pool.get(), (size_t)B * 2 * nre * c.n);
+    k_launch_keyip(c, u.get(), dg.buf.get(), dg.own, dg.own_stride, 0, key, B, level, dg.beta, galois, st);
+    // z = [u_P Phat^-1]_P in coefficient form, [B*2][K][N]
+    Buf z(c.pool.get(), (size_t)B * 2 * K * c.n);
+    std::vector<int> pids(nre, -1);
+    for (int k = 0; k < K; k++) pids[nl + k] = c.num_q + k;
+    RowsView pv{u.get(), make_map(nre, nre, pids), (size_t)B * 2 * nre};
+    RowMap zm = make_map(nre, K, pids);
+    zm.row0 = nl;
+    RowsView zv{z.get(), zm, (size_t)B * 2 * nre};
+    launch_ntt(c, pv, zv, true, st, c.lv[level].d_ks_scale, c.lv[level].d_ks_scale_sh);
+    // centered FastBConv P -> Q inside v's forward NTT; the combine inside its last pass
+    Buf v(c.pool.get(), (size_t)B * 2 * nl * c.n);
+    CtB out = ct_new(c, B, level, scale);
+    CombineArgs a{out.ptr(), u.get(), add0, add1, add_stride_words, galois, plus ? plus->ptr() : nullptr};
+    launch_moddown_ntt(c, v.get(), z.get(), a, B, level, st);
     return out;
 }
 

@@ -39,6 +39,8 @@ CtB rescale(Context &c, const CtB &a, cudaStream_t st);
 // ModUp of d (B windows, rows q_0..q_level, window stride block_stride_rows):
 // digits in the evaluation domain.
 DigitsB modup(Context &c, const uint64_t *d_eval, size_t block_stride_rows, int B, int level, cudaStream_t st);
+// Write the digits' own rows (copies of the input rows) into the digit buffer.
+void digits_fill_own(Context &c, DigitsB &dg, cudaStream_t st);
 // ModDown(digits . key); `key` = device key in evaluation domain; galois != 1
 // applies the automorphism to the digits; add0/add1 optional addends (add0
 // read through the same automorphism).

@@ -35,12 +35,17 @@ struct ModTab {
     uint32_t k[MAXPRIMES];
 };
 
-// Row addressing of a launch: row r lives at base + (r / period * block_stride
-// + r % period) * N and is reduced mod prime pid[r % period] (SKIP = untouched).
+// Row addressing of a launch over blocks of `period` rows: period row p of
+// block b lives at base + (b * block_stride + p - row0) * N and is reduced mod
+// prime pid[p] (SKIP = untouched).  The launcher fills act[0..nact) with the
+// non-SKIP period rows, so a grid covers only the rows it transforms.
 struct RowMap {
     uint32_t period;
     uint32_t block_stride;   // in rows
+    uint32_t row0;           // first stored period row (0 unless the buffer holds a tail of each block)
+    uint32_t nact;
     uint8_t pid[MAXROWMAP];
+    uint8_t act[MAXROWMAP];
 };
 
 // Twiddle tables (device): [prime id][N], forward psi^brv(i) and inverse
@@ -108,6 +113,11 @@ struct LevelConsts {
     //  m[j][u][t] = Qhat_{j,u} mod prime(t) (+ Shoup)
     uint64_t *d_up_inv = nullptr, *d_up_inv_sh = nullptr;
     uint64_t *d_up_m = nullptr, *d_up_m_sh = nullptr;
+    // fused ModUp (Montgomery form): m_mont[j][u][t] = Qhat_{j,u} * 2^64 mod prime(t)
+    uint64_t *d_up_mm = nullptr;
+    // last multiply of the key switch's inverse NTTs, by prime id: N^-1 (Qhat_{j,u})^-1
+    // for q_i (ModUp input rows) and N^-1 Phat_k^-1 for p_k (ModDown P rows) (+ Shoup)
+    uint64_t *d_ks_scale = nullptr, *d_ks_scale_sh = nullptr;
     // rescale by q_level: qinv[i] = q_level^-1 mod q_i, qmod[i] = q_level mod q_i
     uint64_t *d_rs_qinv = nullptr, *d_rs_qinv_sh = nullptr, *d_rs_qmod = nullptr;
 };
@@ -129,6 +139,9 @@ struct Context {
     uint64_t *d_dn_pinv = nullptr, *d_dn_pinv_sh = nullptr;
     uint64_t *d_dn_phat = nullptr, *d_dn_phat_sh = nullptr;
     uint64_t *d_dn_pmod = nullptr, *d_dn_pmod_sh = nullptr, *d_dn_Pinv = nullptr, *d_dn_Pinv_sh = nullptr;
+    // Montgomery forms for the fused ModDown: phat_mont[k][i] = Phat_k 2^64 mod q_i,
+    // negp_mont[i] = (-P) 2^64 mod q_i
+    uint64_t *d_dn_phat_mont = nullptr, *d_dn_negp_mont = nullptr;
     std::vector<LevelConsts> lv;     // per level 0..L
     int sum_terms_max = 8;           // products one Montgomery reduction may absorb: n*q_max < 2^64
     std::unique_ptr<Pool> pool;
@@ -171,12 +184,17 @@ struct TensorB {
     double scale = 0.0;
 };
 
-// ModUp digits [B][beta][level+1+K][N], evaluation domain.
+// ModUp digits [B][beta][level+1+K][N], evaluation domain.  Row t of digit j
+// for t inside digit j's own primes is not stored: it equals the input row,
+// read from `own` (window b at own + b * own_stride, row t at + t * N), which
+// must outlive the digits.
 struct DigitsB {
     Buf buf;
     int B = 0;
     int level = -1;
     int beta = 0;
+    const uint64_t *own = nullptr;
+    size_t own_stride = 0;   // words
 };
 
 // Plaintext on device (evaluation domain), [level+1][N].
@@ -205,7 +223,11 @@ struct RowsView {
 
 RowMap make_map(uint32_t period, uint32_t block_stride, const std::vector<int> &pids);
 
-void launch_ntt(Context &c, const RowsView &src, const RowsView &dst, bool inverse, cudaStream_t s);
+// Forward or inverse NTT of the rows of src into dst (same period and active
+// rows).  An inverse NTT ends with a multiply by N^-1 mod q, or, when oscale is
+// given, by oscale[pid] (with its Shoup companion oscale_sh[pid]).
+void launch_ntt(Context &c, const RowsView &src, const RowsView &dst, bool inverse, cudaStream_t s,
+                const uint64_t *oscale = nullptr, const uint64_t *oscale_sh = nullptr);
 void launch_copy_rows(Context &c, const RowsView &src, const RowsView &dst, cudaStream_t s);
 
 // Launch bookkeeping: kernel_begin before a launch, kernel_end after it

@@ -159,8 +159,9 @@ __global__ void k_modup_bconv(uint64_t *out, const uint64_t *coef, const uint64_
 //   u_h[b][t][x] = sum_j digits[b][j][t][pi(x)] * key[j][h][krow(t)][x]
 // Each thread owns (t, x) and loops over the windows, so every key word is
 // read once per launch.
-__global__ void k_keyip(uint64_t *u, const uint64_t *digits, const uint64_t *key, int B, int level, int beta,
-                        int nrows_ext, int key_rows, int L1, int logn, uint32_t galois, ModTab mt, int pid_p0) {
+__global__ void k_keyip(uint64_t *u, const uint64_t *digits, const uint64_t *own, size_t own_stride, size_t own_jstride,
+                        const uint64_t *key, int B, int level, int beta, int alpha, int nrows_ext, int key_rows, int L1,
+                        int logn, uint32_t galois, ModTab mt, int pid_p0) {
     const uint32_t n = 1u << logn;
     const size_t total = (size_t)nrows_ext * n;
     for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
@@ -177,10 +178,12 @@ __global__ void k_keyip(uint64_t *u, const uint64_t *digits, const uint64_t *key
         const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
         // keys are in Montgomery form: sum the 128-bit products of the digits
         // (beta q^2 < q 2^64 because beta <= 8 and q < 2^61), reduce once
+        const int jown = t <= level ? t / alpha : -1;   // the digit whose own primes hold row t
         for (int bb = 0; bb < B; bb++) {
             uint64_t h0 = 0, l0 = 0, h1 = 0, l1 = 0;
             for (int j = 0; j < beta; j++) {
-                uint64_t dv = digits[(((size_t)bb * beta + j) * nrows_ext + t) * n + px];
+                uint64_t dv = j == jown ? own[bb * own_stride + j * own_jstride + (size_t)t * n + px]
+                                        : digits[(((size_t)bb * beta + j) * nrows_ext + t) * n + px];
                 mm::mac128(h0, l0, dv, kb[j]);
                 mm::mac128(h1, l1, dv, ka[j]);
             }
@@ -396,15 +399,16 @@ void k_launch_modup_bconv(Context &c, uint64_t *out, const uint64_t *coef, const
            level + 1 + c.num_p, c.logn, c.mods, mc);
 }
 
-void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint64_t *key, int B, int level, int beta,
-                    uint32_t galois, cudaStream_t st) {
+void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint64_t *own, size_t own_stride,
+                    size_t own_jstride, const uint64_t *key, int B, int level, int beta, uint32_t galois,
+                    cudaStream_t st) {
     int nre = level + 1 + c.num_p;
     size_t work = (size_t)nre * c.n;
     dim3 g = grid_for(work);
     // reads: B*beta digit rows + beta*2 key rows; writes: B*2 output rows
     double bytes = W8(work * ((size_t)B * beta + 2 * beta + 2 * B));
-    LAUNCH(c, "keyip", bytes, g, k_keyip, u, digits, key, B, level, beta, nre, c.num_q + c.num_p, c.num_q, c.logn,
-           galois, c.mods, c.num_q);
+    LAUNCH(c, "keyip", bytes, g, k_keyip, u, digits, own, own_stride, own_jstride, key, B, level, beta, c.alpha, nre,
+           c.num_q + c.num_p, c.num_q, c.logn, galois, c.mods, c.num_q);
 }
 
 void k_launch_moddown_bconv(Context &c, uint64_t *v, const uint64_t *u, int B, int level, const ModDownConsts &dc,

@@ -48,8 +48,12 @@ void k_launch_tensor(Context &c, uint64_t *d, const uint64_t *a, const uint64_t 
                      bool acc, cudaStream_t st);
 void k_launch_modup_bconv(Context &c, uint64_t *out, const uint64_t *coef, const uint64_t *deval, size_t deval_stride,
                           int B, int level, const ModUpConsts &mc, cudaStream_t st);
-void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint64_t *key, int B, int level, int beta,
-                    uint32_t galois, cudaStream_t st);
+// u_h[b][t] = sum_j digit_j[b][t] (after the Galois permutation) * key[j][h][t];
+// rows of a digit inside its own primes come from `own` (window b, digit j,
+// row t at own + b * own_stride + j * own_jstride + t * N).
+void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint64_t *own, size_t own_stride,
+                    size_t own_jstride, const uint64_t *key, int B, int level, int beta, uint32_t galois,
+                    cudaStream_t st);
 void k_launch_moddown_bconv(Context &c, uint64_t *v, const uint64_t *u, int B, int level, const ModDownConsts &dc,
                             cudaStream_t st);
 void k_launch_moddown_combine(Context &c, uint64_t *out, const uint64_t *u, const uint64_t *v, const uint64_t *add0,
@@ -60,6 +64,30 @@ void k_launch_rescale_spread(Context &c, uint64_t *tmp, const uint64_t *last, in
 void k_launch_rescale_combine(Context &c, uint64_t *out, const uint64_t *cc, const uint64_t *tmp, int B, int level,
                               const RescaleConsts &rc, cudaStream_t st);
 void k_launch_permute(Context &c, uint64_t *out, const uint64_t *in, size_t rows, uint32_t galois, cudaStream_t st);
+
+// Fused ModUp tail (ntt.cu): y[b][i] = [x_{b,i} (Qhat_{j,u})^-1]_{q_i} in
+// coefficient form ([B][level+1][N]).  For every stored digit row (window b,
+// digit j, target t outside digit j's primes) the strided pass of the forward
+// NTT forms sum_u y[b][j*alpha+u] * Qhat_{j,u} mod prime(t) on the fly; both
+// forward passes then run in place on digits [B][beta][level+1+K][N].
+void launch_modup_ntt(Context &c, uint64_t *digits, const uint64_t *y, int B, int level, cudaStream_t st);
+
+// Fused ModDown tail (ntt.cu).  z[bh][k] = [u_{p_k} Phat_k^-1]_{p_k} in
+// coefficient form ([B*2][K][N]).  The strided pass of v's forward NTT forms
+// v_i = sum_k z_k Phat_k - c P mod q_i (c = number of z_k > p_k / 2) on the
+// fly into vtmp ([B*2][level+1][N]); the contiguous pass writes
+//   out[b][h][i][x] = (u[b][h][i][x] - v[b][h][i][x]) P^-1 + add_h[b][i][perm(x)] + plus[b][h][i][x]
+// (add_h and plus optional; perm = the Galois map of `galois`).
+struct CombineArgs {
+    uint64_t *out;
+    const uint64_t *u;            // [B][2][level+1+K][N]
+    const uint64_t *add0, *add1;  // window stride add_stride words
+    size_t add_stride;
+    uint32_t galois;
+    const uint64_t *plus;         // [B][2][level+1][N]
+};
+void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, int B, int level,
+                        cudaStream_t st);
 
 // Fused sum of products: out (+)= sum_k ct_k (.) pt_k over a batch of
 // ciphertexts at one level (each ct_k [B][2][l+1][N], each pt_k [l+1][N] in

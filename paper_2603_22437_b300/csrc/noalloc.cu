@@ -138,7 +138,7 @@ extern "C" mmfhe_status mmfhe_keyswitch_noalloc(mmfhe_ctx *ctx, const mmfhe_keys
             launch_ntt(*c, v, v, false, st);
         }
         // 3. key inner product, 4. ModDown
-        k_launch_keyip(*c, Ur, Gr, key, (int)B, (int)level, beta, 1, st);
+        k_launch_keyip(*c, Ur, Gr, Gr, (size_t)beta * nre * N, (size_t)nre * N, key, (int)B, (int)level, beta, 1, st);
         RowMap pm{};
         pm.period = (uint32_t)nre;
         pm.block_stride = (uint32_t)nre;

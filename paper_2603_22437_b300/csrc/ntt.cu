@@ -26,6 +26,7 @@
 #include <cstdio>
 
 #include "internal.h"
+#include "kernels.h"
 #include "modarith.cuh"
 
 namespace mmfhe {
@@ -34,9 +35,9 @@ namespace {
 
 constexpr int COLS = 16;        // columns per CTA in the strided pass
 
-__device__ __forceinline__ size_t row_offset(const RowMap &m, uint32_t r, int logn) {
-    return ((size_t)(r / m.period) * m.block_stride + (r % m.period)) << logn;
-}
+// Every pass stages 16 words per thread: a loop over them with a compile-time
+// trip count, so the loads of several iterations are in flight together.
+#define MMFHE_TILE_LOOP(e, NT) _Pragma("unroll 8") for (int it_ = 0, e = threadIdx.x; it_ < 16; it_++, e += (NT))
 
 // Position of register element (group g, index j) of a round covering local
 // stages [A, A+R) of a sub-transform of size 2^LOG, for thread t that owns
@@ -103,22 +104,20 @@ struct Geo {
     static constexpr int RS = T1 + T1 / 16;         // padded block stride in shared memory
 };
 
-// Strided pass. FWD: stages 0..S1-1 (reads src, writes dst); inverse: stages
-// S1-1..0 in place on dst, then the N^-1 factor.
+// Period row and block of grid row r (compact list of active rows).
+__device__ __forceinline__ void row_decode(const RowMap &m, uint32_t r, uint32_t &blk, uint32_t &p) {
+    blk = r / m.nact;
+    p = m.act[r % m.nact];
+}
+__device__ __forceinline__ size_t row_at(const RowMap &m, uint32_t blk, uint32_t p, int logn) {
+    return ((size_t)blk * m.block_stride + p - m.row0) << logn;
+}
+
+// Stages of the strided pass on a staged tile sm[H][COLS] (between the
+// barriers that follow the load and precede the store).
 template <int LOGN, bool FWD>
-__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS)
-    k_ntt_cols(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst, RowMap md, ModTab mt, Twiddles tw) {
+__device__ __forceinline__ void cols_rounds(uint64_t *sm, uint64_t q, uint32_t pid, const Twiddles &tw) {
     using Gm = Geo<LOGN>;
-    __shared__ uint64_t sm[Gm::H * COLS];
-    const uint32_t r = blockIdx.y;
-    const uint8_t pid = md.pid[r % md.period];
-    if (pid == SKIP) return;
-    const uint64_t *S = (FWD ? src + row_offset(ms, r, LOGN) : dst + row_offset(md, r, LOGN));
-    uint64_t *D = dst + row_offset(md, r, LOGN);
-    const int lo0 = blockIdx.x * COLS;
-    const uint64_t q = mt.q[pid];
-    for (int e = threadIdx.x; e < Gm::H * COLS; e += blockDim.x) sm[e] = S[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)];
-    __syncthreads();
     const int c = threadIdx.x % COLS, t = threadIdx.x / COLS;
     const uint64_t *W = (FWD ? tw.fw : tw.iw) + ((size_t)pid << LOGN);
     const uint64_t *Wp = (FWD ? tw.fw_sh : tw.iw_sh) + ((size_t)pid << LOGN);
@@ -137,36 +136,13 @@ __global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS)
         }
         ntt_round<Gm::S1, 0, Gm::R1C, false>(sm, t, q, W, Wp, addr, twi);
     }
-    __syncthreads();
-    if (FWD) {
-        for (int e = threadIdx.x; e < Gm::H * COLS; e += blockDim.x) D[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)] = sm[e];
-    } else {
-        const uint64_t ni = tw.ninv[pid], nip = tw.ninv_sh[pid];
-        for (int e = threadIdx.x; e < Gm::H * COLS; e += blockDim.x)
-            D[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)] = mm::mul_shoup(sm[e], ni, nip, q);
-    }
 }
 
-// Contiguous pass. FWD: stages S1..logN-1 in place on dst, final reduction to
-// [0, q); inverse: stages logN-1..S1 (reads src, writes dst).
+// Stages of the contiguous pass on ROWS staged blocks (padded stride RS),
+// the first being block hi0 of its row.
 template <int LOGN, bool FWD>
-__global__ void __launch_bounds__(256)
-    k_ntt_rows(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst, RowMap md, ModTab mt, Twiddles tw) {
+__device__ __forceinline__ void rows_rounds(uint64_t *sm, int hi0, uint64_t q, uint32_t pid, const Twiddles &tw) {
     using Gm = Geo<LOGN>;
-    __shared__ uint64_t sm[Gm::ROWS * Gm::RS];
-    const uint32_t r = blockIdx.y;
-    const uint8_t pid = md.pid[r % md.period];
-    if (pid == SKIP) return;
-    const uint64_t *S = (FWD ? dst + row_offset(md, r, LOGN) : src + row_offset(ms, r, LOGN));
-    uint64_t *D = dst + row_offset(md, r, LOGN);
-    const int hi0 = blockIdx.x * Gm::ROWS;
-    const uint64_t q = mt.q[pid];
-    const size_t base = (size_t)hi0 * Gm::T1;
-    for (int e = threadIdx.x; e < Gm::ROWS * Gm::T1; e += blockDim.x) {
-        int rr = e / Gm::T1, l = e % Gm::T1;
-        sm[rr * Gm::RS + l + (l >> 4)] = S[base + e];
-    }
-    __syncthreads();
     const int t = threadIdx.x % Gm::TPR, rr = threadIdx.x / Gm::TPR;
     const int hi = hi0 + rr;
     const uint64_t *W = (FWD ? tw.fw : tw.iw) + ((size_t)pid << LOGN);
@@ -190,19 +166,191 @@ __global__ void __launch_bounds__(256)
         }
         ntt_round<Gm::LOGT, 0, Gm::R1R, false>(row, t, q, W, Wp, addr, twi);
     }
+}
+
+// Strided pass. FWD: stages 0..S1-1 (reads src, writes dst); inverse: stages
+// S1-1..0 in place on dst, then the factor oscale[pid] (N^-1 when null).
+template <int LOGN, bool FWD>
+__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
+    k_ntt_cols(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst, RowMap md, ModTab mt, Twiddles tw,
+               const uint64_t *__restrict__ oscale, const uint64_t *__restrict__ oscale_sh) {
+    using Gm = Geo<LOGN>;
+    __shared__ uint64_t sm[Gm::H * COLS];
+    uint32_t blk, p;
+    row_decode(md, blockIdx.y, blk, p);
+    const uint32_t pid = md.pid[p];
+    const uint64_t *S = (FWD ? src + row_at(ms, blk, p, LOGN) : dst + row_at(md, blk, p, LOGN));
+    uint64_t *D = dst + row_at(md, blk, p, LOGN);
+    const int lo0 = blockIdx.x * COLS;
+    const uint64_t q = mt.q[pid];
+    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) sm[e] = S[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)];
     __syncthreads();
-    for (int e = threadIdx.x; e < Gm::ROWS * Gm::T1; e += blockDim.x) {
+    cols_rounds<LOGN, FWD>(sm, q, pid, tw);
+    __syncthreads();
+    if (FWD) {
+        MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) D[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)] = sm[e];
+    } else {
+        const uint64_t ni = oscale ? oscale[pid] : tw.ninv[pid], nip = oscale ? oscale_sh[pid] : tw.ninv_sh[pid];
+        MMFHE_TILE_LOOP(e, Gm::COLS_THREADS)
+            D[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)] = mm::mul_shoup(sm[e], ni, nip, q);
+    }
+}
+
+// Contiguous pass. FWD: stages S1..logN-1 in place on dst, final reduction to
+// [0, q); inverse: stages logN-1..S1 (reads src, writes dst).
+template <int LOGN, bool FWD>
+__global__ void __launch_bounds__(256, 3)
+    k_ntt_rows(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst, RowMap md, ModTab mt, Twiddles tw) {
+    using Gm = Geo<LOGN>;
+    __shared__ uint64_t sm[Gm::ROWS * Gm::RS];
+    uint32_t blk, p;
+    row_decode(md, blockIdx.y, blk, p);
+    const uint32_t pid = md.pid[p];
+    const uint64_t *S = (FWD ? dst + row_at(md, blk, p, LOGN) : src + row_at(ms, blk, p, LOGN));
+    uint64_t *D = dst + row_at(md, blk, p, LOGN);
+    const int hi0 = blockIdx.x * Gm::ROWS;
+    const uint64_t q = mt.q[pid];
+    const size_t base = (size_t)hi0 * Gm::T1;
+    MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
+        int rr = e / Gm::T1, l = e % Gm::T1;
+        sm[rr * Gm::RS + l + (l >> 4)] = S[base + e];
+    }
+    __syncthreads();
+    rows_rounds<LOGN, FWD>(sm, hi0, q, pid, tw);
+    __syncthreads();
+    MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
         int r2 = e / Gm::T1, l = e % Gm::T1;
         uint64_t v = sm[r2 * Gm::RS + l + (l >> 4)];
         D[base + e] = FWD ? mm::reduce_4q(v, q) : v;
     }
 }
 
+// Fused ModUp strided pass: digit row (window blk, period row p = j * nre + t)
+// starts from sum_u y[blk][j*alpha+u] * Qhat_{j,u} mod prime(t), accumulated
+// as 128-bit products with the factor in Montgomery form and reduced once
+// (alpha * q_src * q_t < q_t * 2^64 because alpha <= 8 and q_src < 2^61).
+template <int LOGN>
+__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
+    k_ntt_cols_modup(const uint64_t *__restrict__ y, int nl, int nre, int alpha, int j0, uint64_t *dst, RowMap md,
+                     const uint64_t *__restrict__ m_mont, ModTab mt, Twiddles tw) {
+    using Gm = Geo<LOGN>;
+    __shared__ uint64_t sm[Gm::H * COLS];
+    uint32_t blk, p;
+    row_decode(md, blockIdx.y, blk, p);
+    const uint32_t pid = md.pid[p];
+    const int j = j0 + (int)p / nre, t = (int)p % nre;
+    const int i0 = j * alpha, cnt = min(alpha, nl - i0);
+    const uint64_t *Y = y + (((size_t)blk * nl + i0) << LOGN);
+    uint64_t *D = dst + row_at(md, blk, p, LOGN);
+    const int lo0 = blockIdx.x * COLS;
+    const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
+    uint64_t f[MAX_ALPHA];
+#pragma unroll
+    for (int u = 0; u < MAX_ALPHA; u++) f[u] = u < cnt ? m_mont[((size_t)j * MAX_ALPHA + u) * MAXROWMAP + t] : 0;
+    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) {
+        const size_t idx = (size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS);
+        uint64_t hi = 0, lo = 0;
+#pragma unroll
+        for (int u = 0; u < MAX_ALPHA; u++)
+            if (u < cnt) mm::mac128(hi, lo, Y[((size_t)u << LOGN) + idx], f[u]);
+        sm[e] = mm::redc(hi, lo, q, qinv);
+    }
+    __syncthreads();
+    cols_rounds<LOGN, true>(sm, q, pid, tw);
+    __syncthreads();
+    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) D[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)] = sm[e];
+}
+
+// Fused ModDown strided pass: row (blk = window * 2 + h, p = i) starts from the
+// centered conversion v_i = sum_k z_k Phat_k + c (-P) mod q_i, c = #{k : z_k > p_k / 2},
+// in one Montgomery reduction (K (p_max - 1)(q - 1) + K (q - 1) < q 2^64 for K <= 8).
+template <int LOGN>
+__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
+    k_ntt_cols_moddown(const uint64_t *__restrict__ z, int K, int pid_p0, uint64_t *dst, RowMap md,
+                       const uint64_t *__restrict__ phat_mont, const uint64_t *__restrict__ negp_mont, ModTab mt,
+                       Twiddles tw) {
+    using Gm = Geo<LOGN>;
+    __shared__ uint64_t sm[Gm::H * COLS];
+    uint32_t blk, p;
+    row_decode(md, blockIdx.y, blk, p);
+    const uint32_t pid = md.pid[p];
+    const uint64_t *Z = z + (((size_t)blk * K) << LOGN);
+    uint64_t *D = dst + row_at(md, blk, p, LOGN);
+    const int lo0 = blockIdx.x * COLS;
+    const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
+    uint64_t f[MMFHE_MAX_P], half[MMFHE_MAX_P];
+#pragma unroll
+    for (int k = 0; k < MMFHE_MAX_P; k++) {
+        f[k] = k < K ? phat_mont[(size_t)k * MMFHE_MAX_Q + pid] : 0;
+        half[k] = k < K ? mt.q[pid_p0 + k] >> 1 : 0;
+    }
+    const uint64_t np = negp_mont[pid];
+    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) {
+        const size_t idx = (size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS);
+        uint64_t hi = 0, lo = 0, neg = 0;
+#pragma unroll
+        for (int k = 0; k < MMFHE_MAX_P; k++)
+            if (k < K) {
+                const uint64_t zk = Z[((size_t)k << LOGN) + idx];
+                neg += zk > half[k] ? 1u : 0u;
+                mm::mac128(hi, lo, zk, f[k]);
+            }
+        mm::mac128(hi, lo, neg, np);
+        sm[e] = mm::redc(hi, lo, q, qinv);
+    }
+    __syncthreads();
+    cols_rounds<LOGN, true>(sm, q, pid, tw);
+    __syncthreads();
+    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) D[(size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS)] = sm[e];
+}
+
+// Fused ModDown contiguous pass: forward stages on v (rows blk = window * 2 + h,
+// p = i, in place on vtmp) and the combine
+//   out = (u - v) P^-1 + add_h[perm(x)] + plus  (mod q_i).
+template <int LOGN>
+__global__ void __launch_bounds__(256, 3)
+    k_ntt_rows_combine(const uint64_t *__restrict__ v, RowMap mv, CombineArgs a, int nre,
+                       const uint64_t *__restrict__ Pinv, const uint64_t *__restrict__ Pinv_sh, ModTab mt,
+                       Twiddles tw) {
+    using Gm = Geo<LOGN>;
+    __shared__ uint64_t sm[Gm::ROWS * Gm::RS];
+    uint32_t blk, p;
+    row_decode(mv, blockIdx.y, blk, p);
+    const uint32_t pid = mv.pid[p];
+    const int nl = (int)mv.period;
+    const uint64_t *S = v + row_at(mv, blk, p, LOGN);
+    const int hi0 = blockIdx.x * Gm::ROWS;
+    const uint64_t q = mt.q[pid];
+    const size_t base = (size_t)hi0 * Gm::T1;
+    MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
+        int rr = e / Gm::T1, l = e % Gm::T1;
+        sm[rr * Gm::RS + l + (l >> 4)] = S[base + e];
+    }
+    __syncthreads();
+    rows_rounds<LOGN, true>(sm, hi0, q, pid, tw);
+    __syncthreads();
+    const uint64_t pi = Pinv[pid], pis = Pinv_sh[pid];
+    const uint64_t *U = a.u + (((size_t)blk * nre + p) << LOGN);
+    const uint64_t *A = (blk & 1) ? a.add1 : a.add0;
+    if (A) A += (size_t)(blk >> 1) * a.add_stride + ((size_t)p << LOGN);
+    const uint64_t *Pl = a.plus ? a.plus + (((size_t)blk * nl + p) << LOGN) : nullptr;
+    uint64_t *O = a.out + (((size_t)blk * nl + p) << LOGN);
+    MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
+        int r2 = e / Gm::T1, l = e % Gm::T1;
+        const uint32_t x = (uint32_t)(base + e);
+        const uint64_t vv = mm::reduce_4q(sm[r2 * Gm::RS + l + (l >> 4)], q);
+        uint64_t res = mm::mul_shoup(mm::sub_mod(U[x], vv, q), pi, pis, q);
+        if (A) res = mm::add_mod(res, A[a.galois == 1 ? x : mm::galois_perm(x, a.galois, LOGN)], q);
+        if (Pl) res = mm::add_mod(res, Pl[x], q);
+        O[x] = res;
+    }
+}
+
 __global__ void k_copy_rows(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst, RowMap md, int logn) {
-    const uint32_t r = blockIdx.y;
-    if (md.pid[r % md.period] == SKIP) return;
-    const uint64_t *S = src + row_offset(ms, r, logn);
-    uint64_t *D = dst + row_offset(md, r, logn);
+    uint32_t blk, p;
+    row_decode(md, blockIdx.y, blk, p);
+    const uint64_t *S = src + row_at(ms, blk, p, logn);
+    uint64_t *D = dst + row_at(md, blk, p, logn);
     const uint32_t n = 1u << logn;
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) D[i] = S[i];
 }
@@ -216,6 +364,18 @@ RowMap make_map(uint32_t period, uint32_t block_stride, const std::vector<int> &
     m.block_stride = block_stride;
     for (uint32_t i = 0; i < period; i++) m.pid[i] = pids[i] < 0 ? SKIP : (uint8_t)pids[i];
     return m;
+}
+
+// Fill the active-row list of md (non-SKIP period rows) into both maps.
+static uint32_t set_active(RowMap &ms, RowMap &md) {
+    if (ms.period != md.period) throw Error(MMFHE_ERR_BAD_ARG, "row maps differ in period");
+    uint32_t n = 0;
+    for (uint32_t p = 0; p < md.period; p++)
+        if (md.pid[p] != SKIP) md.act[n++] = (uint8_t)p;
+    md.nact = n;
+    for (uint32_t k = 0; k < n; k++) ms.act[k] = md.act[k];
+    ms.nact = n;
+    return n;
 }
 
 static cudaEvent_t next_event(Context &c) {
@@ -250,15 +410,27 @@ void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cuda
     }
 }
 
+#define MMFHE_LOGN_DISPATCH(logn, CALL)                                              \
+    switch (logn) {                                                                  \
+    case 10: CALL(10); break;                                                        \
+    case 11: CALL(11); break;                                                        \
+    case 12: CALL(12); break;                                                        \
+    case 13: CALL(13); break;                                                        \
+    case 14: CALL(14); break;                                                        \
+    case 15: CALL(15); break;                                                        \
+    case 16: CALL(16); break;                                                        \
+    default: throw Error(MMFHE_ERR_BAD_ARG, "unsupported ring dimension");          \
+    }
+
 template <int LOGN>
 static void ntt_launch_t(Context &c, const uint64_t *sb, RowMap ms, uint64_t *db, RowMap md, size_t nr, bool inverse,
-                         double bytes, cudaStream_t st) {
+                         double bytes, const uint64_t *os, const uint64_t *os_sh, cudaStream_t st) {
     using Gm = Geo<LOGN>;
     dim3 gc(Gm::T1 / COLS, (unsigned)nr), bc(Gm::COLS_THREADS);
     dim3 gr(Gm::H / Gm::ROWS, (unsigned)nr), br(Gm::ROWS * Gm::TPR);
     if (!inverse) {
         kernel_begin(c, st);
-        k_ntt_cols<LOGN, true><<<gc, bc, 0, st>>>(sb, ms, db, md, c.mods, c.tw);
+        k_ntt_cols<LOGN, true><<<gc, bc, 0, st>>>(sb, ms, db, md, c.mods, c.tw, nullptr, nullptr);
         kernel_end(c, "ntt_fwd_cols", gc, bc, bytes, st);
         kernel_begin(c, st);
         k_ntt_rows<LOGN, true><<<gr, br, 0, st>>>(db, md, db, md, c.mods, c.tw);
@@ -268,50 +440,154 @@ static void ntt_launch_t(Context &c, const uint64_t *sb, RowMap ms, uint64_t *db
         k_ntt_rows<LOGN, false><<<gr, br, 0, st>>>(sb, ms, db, md, c.mods, c.tw);
         kernel_end(c, "ntt_inv_rows", gr, br, bytes, st);
         kernel_begin(c, st);
-        k_ntt_cols<LOGN, false><<<gc, bc, 0, st>>>(db, md, db, md, c.mods, c.tw);
+        k_ntt_cols<LOGN, false><<<gc, bc, 0, st>>>(db, md, db, md, c.mods, c.tw, os, os_sh);
         kernel_end(c, "ntt_inv_cols", gc, bc, bytes, st);
     }
 }
 
-void launch_ntt(Context &c, const RowsView &src, const RowsView &dst, bool inverse, cudaStream_t st) {
+void launch_ntt(Context &c, const RowsView &src, const RowsView &dst, bool inverse, cudaStream_t st,
+                const uint64_t *oscale, const uint64_t *oscale_sh) {
     if (src.rows == 0) return;
+    RowMap ms = src.map, md = dst.map;
+    if (src.rows % ms.period) throw Error(MMFHE_ERR_BAD_ARG, "row count is not a whole number of blocks");
+    const uint32_t nact = set_active(ms, md);
+    if (nact == 0) return;
+    const size_t blocks = src.rows / ms.period;
     // grid.y is limited to 65535 rows per launch: split on block boundaries
-    const size_t chunk = (65535 / src.map.period) * src.map.period;
-    for (size_t r0 = 0; r0 < src.rows; r0 += chunk) {
-        size_t nr = std::min<size_t>(chunk, src.rows - r0);
-        RowMap ms = src.map, md = dst.map;
-        size_t blocks0 = r0 / ms.period;
-        const uint64_t *sb = src.base + ((blocks0 * ms.block_stride) << c.logn);
-        uint64_t *db = dst.base + ((blocks0 * md.block_stride) << c.logn);
-        size_t live = 0;   // rows actually transformed (skipped rows move no data)
-        for (size_t r = 0; r < nr; r++) live += md.pid[r % md.period] != SKIP;
-        const double bytes = 2.0 * (double)live * c.n * 8;   // each pass reads and writes every live row once
-        switch (c.logn) {
-        case 10: ntt_launch_t<10>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
-        case 11: ntt_launch_t<11>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
-        case 12: ntt_launch_t<12>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
-        case 13: ntt_launch_t<13>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
-        case 14: ntt_launch_t<14>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
-        case 15: ntt_launch_t<15>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
-        case 16: ntt_launch_t<16>(c, sb, ms, db, md, nr, inverse, bytes, st); break;
-        default: throw Error(MMFHE_ERR_BAD_ARG, "unsupported ring dimension");
-        }
+    const size_t chunk = 65535 / nact;
+    for (size_t b0 = 0; b0 < blocks; b0 += chunk) {
+        const size_t nb = std::min(chunk, blocks - b0);
+        const uint64_t *sb = src.base + ((b0 * ms.block_stride) << c.logn);
+        uint64_t *db = dst.base + ((b0 * md.block_stride) << c.logn);
+        const size_t nr = nb * nact;
+        const double bytes = 2.0 * (double)nr * c.n * 8;   // each pass reads and writes every transformed row once
+#define MMFHE_NTT_CALL(L) ntt_launch_t<L>(c, sb, ms, db, md, nr, inverse, bytes, oscale, oscale_sh, st)
+        MMFHE_LOGN_DISPATCH(c.logn, MMFHE_NTT_CALL)
+#undef MMFHE_NTT_CALL
     }
     CK(cudaGetLastError());
 }
 
 void launch_copy_rows(Context &c, const RowsView &src, const RowsView &dst, cudaStream_t st) {
     if (src.rows == 0) return;
-    const size_t chunk = (65535 / src.map.period) * src.map.period;
-    for (size_t r0 = 0; r0 < src.rows; r0 += chunk) {
-        size_t nr = std::min<size_t>(chunk, src.rows - r0);
-        size_t blocks0 = r0 / src.map.period;
-        const uint64_t *sb = src.base + ((blocks0 * src.map.block_stride) << c.logn);
-        uint64_t *db = dst.base + ((blocks0 * dst.map.block_stride) << c.logn);
+    RowMap ms = src.map, md = dst.map;
+    if (src.rows % ms.period) throw Error(MMFHE_ERR_BAD_ARG, "row count is not a whole number of blocks");
+    const uint32_t nact = set_active(ms, md);
+    if (nact == 0) return;
+    const size_t blocks = src.rows / ms.period;
+    const size_t chunk = 65535 / nact;
+    for (size_t b0 = 0; b0 < blocks; b0 += chunk) {
+        const size_t nb = std::min(chunk, blocks - b0);
+        const uint64_t *sb = src.base + ((b0 * ms.block_stride) << c.logn);
+        uint64_t *db = dst.base + ((b0 * md.block_stride) << c.logn);
+        const size_t nr = nb * nact;
         dim3 g(std::max(1u, c.n / 1024), (unsigned)nr), b(256);
         kernel_begin(c, st);
-        k_copy_rows<<<g, b, 0, st>>>(sb, src.map, db, dst.map, c.logn);
+        k_copy_rows<<<g, b, 0, st>>>(sb, ms, db, md, c.logn);
         kernel_end(c, "copy_rows", g, b, 2.0 * (double)nr * c.n * 8, st);
+    }
+    CK(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------------------
+// fused key-switch NTTs
+// ---------------------------------------------------------------------------
+template <int LOGN>
+static void modup_launch_t(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, size_t nr, int nl,
+                           int nre, int j0, const uint64_t *m_mont, double bytes_cols, double bytes_rows,
+                           cudaStream_t st) {
+    using Gm = Geo<LOGN>;
+    dim3 gc(Gm::T1 / COLS, (unsigned)nr), bc(Gm::COLS_THREADS);
+    dim3 gr(Gm::H / Gm::ROWS, (unsigned)nr), br(Gm::ROWS * Gm::TPR);
+    kernel_begin(c, st);
+    k_ntt_cols_modup<LOGN><<<gc, bc, 0, st>>>(y, nl, nre, c.alpha, j0, digits, md, m_mont, c.mods, c.tw);
+    kernel_end(c, "ntt_modup_cols", gc, bc, bytes_cols, st);
+    kernel_begin(c, st);
+    k_ntt_rows<LOGN, true><<<gr, br, 0, st>>>(digits, md, digits, md, c.mods, c.tw);
+    kernel_end(c, "ntt_fwd_rows", gr, br, bytes_rows, st);
+}
+
+void launch_modup_ntt(Context &c, uint64_t *digits, const uint64_t *y, int B, int level, cudaStream_t st) {
+    const LevelConsts &lc = c.lv[level];
+    const int nl = level + 1, nre = nl + c.num_p, beta = lc.beta;
+    if (B == 0) return;
+    // digits per launch: a launch's period (digits x nre rows) fits one row map
+    const int per = std::max(1, std::min(beta, MAXROWMAP / nre));
+    for (int j0 = 0; j0 < beta; j0 += per) {
+        const int nj = std::min(per, beta - j0);
+        std::vector<int> pids(nj * nre);
+        for (int jj = 0; jj < nj; jj++) {
+            const auto &D = lc.digits[j0 + jj];
+            for (int t = 0; t < nre; t++) {
+                const bool own = t >= D.front() && t <= D.back();
+                pids[jj * nre + t] = own ? -1 : (t < nl ? t : c.num_q + (t - nl));
+            }
+        }
+        RowMap md = make_map(nj * nre, beta * nre, pids), ms = md;
+        const uint32_t nact = set_active(ms, md);
+        uint64_t *dbase = digits + (((size_t)j0 * nre) << c.logn);
+        const size_t chunk = 65535 / nact;
+        for (size_t b0 = 0; b0 < (size_t)B; b0 += chunk) {
+            const size_t nb = std::min(chunk, (size_t)B - b0);
+            const size_t nr = nb * nact;
+            uint64_t *db = dbase + ((b0 * beta * nre) << c.logn);
+            const uint64_t *yb = y + ((b0 * nl) << c.logn);
+            const double row = (double)c.n * 8;
+            // reads each window's y rows of the launched digits once, writes every converted row;
+            // the contiguous pass reads and writes every row
+            int src_rows = 0;
+            for (int jj = 0; jj < nj; jj++) src_rows += (int)lc.digits[j0 + jj].size();
+            const double bc_ = row * ((double)nr + (double)nb * src_rows), br_ = 2.0 * row * (double)nr;
+#define MMFHE_MODUP_CALL(L) modup_launch_t<L>(c, db, yb, md, nr, nl, nre, j0, lc.d_up_mm, bc_, br_, st)
+            MMFHE_LOGN_DISPATCH(c.logn, MMFHE_MODUP_CALL)
+#undef MMFHE_MODUP_CALL
+        }
+    }
+    CK(cudaGetLastError());
+}
+
+template <int LOGN>
+static void moddown_launch_t(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, size_t nr,
+                             const CombineArgs &a, int nre, double bytes_cols, double bytes_rows, cudaStream_t st) {
+    using Gm = Geo<LOGN>;
+    dim3 gc(Gm::T1 / COLS, (unsigned)nr), bc(Gm::COLS_THREADS);
+    dim3 gr(Gm::H / Gm::ROWS, (unsigned)nr), br(Gm::ROWS * Gm::TPR);
+    kernel_begin(c, st);
+    k_ntt_cols_moddown<LOGN><<<gc, bc, 0, st>>>(z, c.num_p, c.num_q, vtmp, mv, c.d_dn_phat_mont, c.d_dn_negp_mont,
+                                                c.mods, c.tw);
+    kernel_end(c, "ntt_moddown_cols", gc, bc, bytes_cols, st);
+    kernel_begin(c, st);
+    k_ntt_rows_combine<LOGN><<<gr, br, 0, st>>>(vtmp, mv, a, nre, c.d_dn_Pinv, c.d_dn_Pinv_sh, c.mods, c.tw);
+    kernel_end(c, "ntt_combine_rows", gr, br, bytes_rows, st);
+}
+
+void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, int B, int level,
+                        cudaStream_t st) {
+    const int nl = level + 1, nre = nl + c.num_p, K = c.num_p;
+    if (B == 0) return;
+    std::vector<int> pids(nl);
+    for (int i = 0; i < nl; i++) pids[i] = i;
+    RowMap mv = make_map(nl, nl, pids), ms = mv;
+    const uint32_t nact = set_active(ms, mv);
+    const size_t blocks = (size_t)B * 2;
+    const size_t chunk = 65535 / nact;
+    for (size_t b0 = 0; b0 < blocks; b0 += chunk) {
+        // chunks hold whole windows, so the (window, h) parity of a block is kept
+        const size_t nb = std::min(chunk & ~(size_t)1, blocks - b0);
+        const size_t nr = nb * nact;
+        CombineArgs ab = a;
+        ab.out = a.out + ((b0 * nl) << c.logn);
+        ab.u = a.u + ((b0 * nre) << c.logn);
+        if (ab.add0) ab.add0 += (b0 / 2) * a.add_stride;
+        if (ab.add1) ab.add1 += (b0 / 2) * a.add_stride;
+        if (ab.plus) ab.plus += (b0 * nl) << c.logn;
+        const double row = (double)c.n * 8;
+        const double bc_ = row * ((double)nr + (double)nb * K);
+        const double br_ = row * ((double)nr * (3 + (ab.plus ? 1 : 0)) + (ab.add0 ? nr / 2.0 : 0) + (ab.add1 ? nr / 2.0 : 0));
+#define MMFHE_MODDOWN_CALL(L)                                                                                   \
+    moddown_launch_t<L>(c, vtmp + ((b0 * nl) << c.logn), z + ((b0 * K) << c.logn), mv, nr, ab, nre, bc_, br_, st)
+        MMFHE_LOGN_DISPATCH(c.logn, MMFHE_MODDOWN_CALL)
+#undef MMFHE_MODDOWN_CALL
     }
     CK(cudaGetLastError());
 }
