@@ -116,15 +116,26 @@ mmfhe_status mmfhe_trace_get(const mmfhe_ctx *ctx, char *buf, size_t capacity, s
  * recorded events and aggregates them by kernel name: up to `capacity`
  * entries are written (names NUL-terminated, truncated to 31 chars);
  * *count is the number of distinct kernels.  bytes = the launches'
- * algorithmic bytes (every distinct word a launch must read or write once). */
+ * algorithmic bytes (every distinct word a launch must read or write once);
+ * butterflies = the NTT butterflies the launches perform (N/2 per stage per
+ * transformed row; 0 for kernels without NTT stages). */
 typedef struct mmfhe_kernel_stat {
     char name[32];
     uint64_t launches;
     double total_ms;
     double bytes;
+    double butterflies;
 } mmfhe_kernel_stat;
 mmfhe_status mmfhe_profile_enable(mmfhe_ctx *ctx, int enable);
 mmfhe_status mmfhe_profile_get(mmfhe_ctx *ctx, mmfhe_kernel_stat *out, uint32_t capacity, uint32_t *count);
+/* Integer-pipe ceiling of the NTT arithmetic on this device (no counterpart in
+ * the paper: a measurement helper for the roofline).  Runs a register-resident
+ * loop of the library's forward butterfly (64-bit words, Harvey lazy reduction
+ * with a Shoup product) on every SM, and the same butterfly on 32-bit words,
+ * and returns butterflies per second for each (CUDA-event timed, after one
+ * warm-up launch).  No memory traffic beyond one word per thread.  Errors:
+ * BAD_ARG (null output), CUDA. */
+mmfhe_status mmfhe_measure_butterfly_peak(mmfhe_ctx *ctx, double *bf64_per_s, double *bf32_per_s);
 
 /* ------------------------------------------------------------------------
  * Evaluation keys (paper: rlk after every ct x ct product, one Galois key

@@ -133,7 +133,7 @@ class Context:
 
     def profile(self, enable=None):
         """Enable/disable per-kernel event profiling, or (enable=None) return
-        {kernel: (launches, total_ms, algorithmic_bytes)}."""
+        {kernel: (launches, total_ms, algorithmic_bytes, butterflies)}."""
         if enable is not None:
             self._c(_lib.lib().mmfhe_profile_enable(self.h, int(enable)))
             return None
@@ -141,7 +141,15 @@ class Context:
         self._c(_lib.lib().mmfhe_profile_get(self.h, None, 0, ctypes.byref(n)))
         arr = (_lib.KernelStat * max(1, n.value))()
         self._c(_lib.lib().mmfhe_profile_get(self.h, arr, n.value, ctypes.byref(n)))
-        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].bytes) for i in range(n.value)}
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].bytes, arr[i].butterflies)
+                for i in range(n.value)}
+
+    def butterfly_peak(self):
+        """(64-bit, 32-bit) forward butterflies per second of a register-resident
+        loop on this device: the integer-pipe ceiling of the NTT arithmetic."""
+        a, b = ctypes.c_double(), ctypes.c_double()
+        self._c(_lib.lib().mmfhe_measure_butterfly_peak(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     def keys(self, user_id=0):
         return Keys(self, user_id)

@@ -54,7 +54,7 @@ class CircuitConfig(ctypes.Structure):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
-                ("bytes", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("butterflies", ctypes.c_double)]
 
 
 class ConstKey(ctypes.Structure):
@@ -76,6 +76,7 @@ _SIGS = {
     "mmfhe_trace_get": [_VP, ctypes.c_char_p, _SZ, ctypes.POINTER(_SZ)],
     "mmfhe_profile_enable": [_VP, _INT],
     "mmfhe_profile_get": [_VP, _VP, _U32, ctypes.POINTER(_U32)],
+    "mmfhe_measure_butterfly_peak": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "mmfhe_keys_create": [_VP, _U64, _PP],
     "mmfhe_keys_set_relin": [_VP, _VP],
     "mmfhe_keys_set_galois": [_VP, _I32, _VP],

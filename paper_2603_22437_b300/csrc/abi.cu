@@ -233,10 +233,21 @@ mmfhe_status mmfhe_profile_get(mmfhe_ctx *ctx, mmfhe_kernel_stat *out, uint32_t 
         it->second.launches++;
         it->second.total_ms += ms;
         it->second.bytes += r.bytes;
+        it->second.butterflies += r.butterflies;
     }
     *count = (uint32_t)agg.size();
     if (out)
         for (uint32_t i = 0; i < capacity && i < order.size(); i++) out[i] = agg[order[i]];
+    ABI_CATCH(c)
+}
+
+mmfhe_status mmfhe_measure_butterfly_peak(mmfhe_ctx *ctx, double *bf64_per_s, double *bf32_per_s) {
+    Context *c = nullptr;
+    ABI_TRY
+    c = ctx_of(ctx);
+    if (!bf64_per_s || !bf32_per_s) throw Error(MMFHE_ERR_BAD_ARG, "null output");
+    CK(cudaSetDevice(c->device));
+    measure_butterfly_peak(*c, bf64_per_s, bf32_per_s);
     ABI_CATCH(c)
 }
 

@@ -157,6 +157,7 @@ struct Context {
         const char *name;
         cudaEvent_t start, stop;
         double bytes;
+        double butterflies;
     };
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> event_pool;
@@ -230,9 +231,13 @@ void launch_ntt(Context &c, const RowsView &src, const RowsView &dst, bool inver
                 const uint64_t *oscale = nullptr, const uint64_t *oscale_sh = nullptr);
 void launch_copy_rows(Context &c, const RowsView &src, const RowsView &dst, cudaStream_t s);
 
+// Butterflies per second of register-resident 64-bit and 32-bit butterfly loops (peaks.cu).
+void measure_butterfly_peak(Context &c, double *bf64, double *bf32);
+
 // Launch bookkeeping: kernel_begin before a launch, kernel_end after it
 // (launch count, optional trace line, optional event pair + algorithmic bytes).
 void kernel_begin(Context &c, cudaStream_t st);
-void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cudaStream_t st);
+void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cudaStream_t st,
+                double butterflies = 0.0);
 
 }  // namespace mmfhe

@@ -179,6 +179,7 @@ __global__ void k_keyip(uint64_t *u, const uint64_t *digits, const uint64_t *own
         // keys are in Montgomery form: sum the 128-bit products of the digits
         // (beta q^2 < q 2^64 because beta <= 8 and q < 2^61), reduce once
         const int jown = t <= level ? t / alpha : -1;   // the digit whose own primes hold row t
+#pragma unroll 2
         for (int bb = 0; bb < B; bb++) {
             uint64_t h0 = 0, l0 = 0, h1 = 0, l1 = 0;
             for (int j = 0; j < beta; j++) {

@@ -63,17 +63,23 @@ __device__ __forceinline__ void ntt_round(uint64_t *sm, int t, uint64_t q, const
     for (int g = 0; g < G; g++)
 #pragma unroll
         for (int j = 0; j < M; j++) x[g * M + j] = sm[addr(elem_index<LOG, A, R>(t, g, j))];
+    // At local stage u the butterflies (j, j + dist) whose lower index j shares
+    // its top u bits use one twiddle: it is loaded once per run of dist pairs.
 #pragma unroll
     for (int uu = 0; uu < R; uu++) {
         const int u = FWD ? uu : R - 1 - uu;
         const int dist = 1 << (R - 1 - u);
 #pragma unroll
         for (int g = 0; g < G; g++) {
+            uint64_t w = 0, wp = 0;
 #pragma unroll
             for (int j = 0; j < M; j++) {
                 if (j & dist) continue;
-                const int widx = twi(A + u, elem_index<LOG, A, R>(t, g, j));
-                const uint64_t w = __ldg(W + widx), wp = __ldg(Wp + widx);
+                if ((j & (dist - 1)) == 0) {   // first pair of a run sharing the twiddle
+                    const int widx = twi(A + u, elem_index<LOG, A, R>(t, g, j));
+                    w = __ldg(W + widx);
+                    wp = __ldg(Wp + widx);
+                }
                 if (FWD)
                     mm::ct_butterfly(x[g * M + j], x[g * M + j + dist], w, wp, q);
                 else
@@ -103,6 +109,11 @@ struct Geo {
     static constexpr int ROWS = (256 / TPR) < H ? (256 / TPR) : H;   // blocks per CTA
     static constexpr int RS = T1 + T1 / 16;         // padded block stride in shared memory
 };
+
+// Bulk prefetch of bytes (multiple of 16, 16-byte aligned start) into L2.
+__device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 
 // Period row and block of grid row r (compact list of active rows).
 __device__ __forceinline__ void row_decode(const RowMap &m, uint32_t r, uint32_t &blk, uint32_t &p) {
@@ -171,7 +182,7 @@ __device__ __forceinline__ void rows_rounds(uint64_t *sm, int hi0, uint64_t q, u
 // Strided pass. FWD: stages 0..S1-1 (reads src, writes dst); inverse: stages
 // S1-1..0 in place on dst, then the factor oscale[pid] (N^-1 when null).
 template <int LOGN, bool FWD>
-__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
+__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 4)
     k_ntt_cols(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst, RowMap md, ModTab mt, Twiddles tw,
                const uint64_t *__restrict__ oscale, const uint64_t *__restrict__ oscale_sh) {
     using Gm = Geo<LOGN>;
@@ -199,7 +210,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
 // Contiguous pass. FWD: stages S1..logN-1 in place on dst, final reduction to
 // [0, q); inverse: stages logN-1..S1 (reads src, writes dst).
 template <int LOGN, bool FWD>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
     k_ntt_rows(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst, RowMap md, ModTab mt, Twiddles tw) {
     using Gm = Geo<LOGN>;
     __shared__ uint64_t sm[Gm::ROWS * Gm::RS];
@@ -225,12 +236,41 @@ __global__ void __launch_bounds__(256, 3)
     }
 }
 
+// Base-conversion staging of a strided-pass tile: element (h, lo0 + c) of the
+// tile is sum_k X[k][h * T1 + lo0 + c] * F[k * fstride] reduced once by
+// Montgomery (F in Montgomery form).  CENTERED adds c * negp with
+// c = #{k : X[k] > P[k] / 2} (the centered correction of the ModDown conversion).
+template <int LOGN, int NT, bool CENTERED = false>
+__device__ __forceinline__ void conv_load(uint64_t *sm, const uint64_t *__restrict__ X, const uint64_t *__restrict__ F,
+                                          int fstride, int lo0, uint64_t q, uint64_t qinv,
+                                          const uint64_t *P = nullptr, uint64_t negp = 0) {
+    using Gm = Geo<LOGN>;
+    uint64_t f[NT], half[NT];
+#pragma unroll
+    for (int k = 0; k < NT; k++) {
+        f[k] = F[(size_t)k * fstride];
+        half[k] = CENTERED ? P[k] >> 1 : 0;
+    }
+    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) {
+        const size_t idx = (size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS);
+        uint64_t hi = 0, lo = 0, neg = 0;
+#pragma unroll
+        for (int k = 0; k < NT; k++) {
+            const uint64_t x = X[((size_t)k << LOGN) + idx];
+            if (CENTERED) neg += x > half[k] ? 1u : 0u;
+            mm::mac128(hi, lo, x, f[k]);
+        }
+        if (CENTERED) mm::mac128(hi, lo, neg, negp);
+        sm[e] = mm::redc(hi, lo, q, qinv);
+    }
+}
+
 // Fused ModUp strided pass: digit row (window blk, period row p = j * nre + t)
 // starts from sum_u y[blk][j*alpha+u] * Qhat_{j,u} mod prime(t), accumulated
 // as 128-bit products with the factor in Montgomery form and reduced once
 // (alpha * q_src * q_t < q_t * 2^64 because alpha <= 8 and q_src < 2^61).
 template <int LOGN>
-__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
+__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 4)
     k_ntt_cols_modup(const uint64_t *__restrict__ y, int nl, int nre, int alpha, int j0, uint64_t *dst, RowMap md,
                      const uint64_t *__restrict__ m_mont, ModTab mt, Twiddles tw) {
     using Gm = Geo<LOGN>;
@@ -244,16 +284,16 @@ __global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
     uint64_t *D = dst + row_at(md, blk, p, LOGN);
     const int lo0 = blockIdx.x * COLS;
     const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
-    uint64_t f[MAX_ALPHA];
-#pragma unroll
-    for (int u = 0; u < MAX_ALPHA; u++) f[u] = u < cnt ? m_mont[((size_t)j * MAX_ALPHA + u) * MAXROWMAP + t] : 0;
-    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) {
-        const size_t idx = (size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS);
-        uint64_t hi = 0, lo = 0;
-#pragma unroll
-        for (int u = 0; u < MAX_ALPHA; u++)
-            if (u < cnt) mm::mac128(hi, lo, Y[((size_t)u << LOGN) + idx], f[u]);
-        sm[e] = mm::redc(hi, lo, q, qinv);
+    const uint64_t *F = m_mont + (size_t)j * MAX_ALPHA * MAXROWMAP + t;
+    switch (cnt) {   // uniform per CTA: the term loop is unrolled for the digit's prime count
+    case 1: conv_load<LOGN, 1>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
+    case 2: conv_load<LOGN, 2>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
+    case 3: conv_load<LOGN, 3>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
+    case 4: conv_load<LOGN, 4>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
+    case 5: conv_load<LOGN, 5>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
+    case 6: conv_load<LOGN, 6>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
+    case 7: conv_load<LOGN, 7>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
+    default: conv_load<LOGN, 8>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
     }
     __syncthreads();
     cols_rounds<LOGN, true>(sm, q, pid, tw);
@@ -265,7 +305,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
 // centered conversion v_i = sum_k z_k Phat_k + c (-P) mod q_i, c = #{k : z_k > p_k / 2},
 // in one Montgomery reduction (K (p_max - 1)(q - 1) + K (q - 1) < q 2^64 for K <= 8).
 template <int LOGN>
-__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
+__global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 4)
     k_ntt_cols_moddown(const uint64_t *__restrict__ z, int K, int pid_p0, uint64_t *dst, RowMap md,
                        const uint64_t *__restrict__ phat_mont, const uint64_t *__restrict__ negp_mont, ModTab mt,
                        Twiddles tw) {
@@ -278,25 +318,18 @@ __global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
     uint64_t *D = dst + row_at(md, blk, p, LOGN);
     const int lo0 = blockIdx.x * COLS;
     const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
-    uint64_t f[MMFHE_MAX_P], half[MMFHE_MAX_P];
-#pragma unroll
-    for (int k = 0; k < MMFHE_MAX_P; k++) {
-        f[k] = k < K ? phat_mont[(size_t)k * MMFHE_MAX_Q + pid] : 0;
-        half[k] = k < K ? mt.q[pid_p0 + k] >> 1 : 0;
-    }
+    const uint64_t *F = phat_mont + pid;
     const uint64_t np = negp_mont[pid];
-    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) {
-        const size_t idx = (size_t)(e / COLS) * Gm::T1 + lo0 + (e % COLS);
-        uint64_t hi = 0, lo = 0, neg = 0;
-#pragma unroll
-        for (int k = 0; k < MMFHE_MAX_P; k++)
-            if (k < K) {
-                const uint64_t zk = Z[((size_t)k << LOGN) + idx];
-                neg += zk > half[k] ? 1u : 0u;
-                mm::mac128(hi, lo, zk, f[k]);
-            }
-        mm::mac128(hi, lo, neg, np);
-        sm[e] = mm::redc(hi, lo, q, qinv);
+    const uint64_t *Hp = mt.q + pid_p0;
+    switch (K) {   // uniform: the term loop is unrolled for the number of special primes
+    case 1: conv_load<LOGN, 1, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
+    case 2: conv_load<LOGN, 2, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
+    case 3: conv_load<LOGN, 3, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
+    case 4: conv_load<LOGN, 4, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
+    case 5: conv_load<LOGN, 5, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
+    case 6: conv_load<LOGN, 6, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
+    case 7: conv_load<LOGN, 7, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
+    default: conv_load<LOGN, 8, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
     }
     __syncthreads();
     cols_rounds<LOGN, true>(sm, q, pid, tw);
@@ -308,7 +341,7 @@ __global__ void __launch_bounds__(Geo<LOGN>::COLS_THREADS, 3)
 // p = i, in place on vtmp) and the combine
 //   out = (u - v) P^-1 + add_h[perm(x)] + plus  (mod q_i).
 template <int LOGN>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(256, 4)
     k_ntt_rows_combine(const uint64_t *__restrict__ v, RowMap mv, CombineArgs a, int nre,
                        const uint64_t *__restrict__ Pinv, const uint64_t *__restrict__ Pinv_sh, ModTab mt,
                        Twiddles tw) {
@@ -322,6 +355,17 @@ __global__ void __launch_bounds__(256, 3)
     const int hi0 = blockIdx.x * Gm::ROWS;
     const uint64_t q = mt.q[pid];
     const size_t base = (size_t)hi0 * Gm::T1;
+    const uint64_t *U = a.u + (((size_t)blk * nre + p) << LOGN);
+    const uint64_t *A = (blk & 1) ? a.add1 : a.add0;
+    if (A) A += (size_t)(blk >> 1) * a.add_stride + ((size_t)p << LOGN);
+    const uint64_t *Pl = a.plus ? a.plus + (((size_t)blk * nl + p) << LOGN) : nullptr;
+    if (threadIdx.x == 0) {
+        // the epilogue's contiguous operands travel to L2 while the stages run
+        constexpr uint32_t seg = Gm::ROWS * Gm::T1 * 8;
+        l2_prefetch(U + base, seg);
+        if (Pl) l2_prefetch(Pl + base, seg);
+        if (A && a.galois == 1) l2_prefetch(A + base, seg);
+    }
     MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
         int rr = e / Gm::T1, l = e % Gm::T1;
         sm[rr * Gm::RS + l + (l >> 4)] = S[base + e];
@@ -330,10 +374,6 @@ __global__ void __launch_bounds__(256, 3)
     rows_rounds<LOGN, true>(sm, hi0, q, pid, tw);
     __syncthreads();
     const uint64_t pi = Pinv[pid], pis = Pinv_sh[pid];
-    const uint64_t *U = a.u + (((size_t)blk * nre + p) << LOGN);
-    const uint64_t *A = (blk & 1) ? a.add1 : a.add0;
-    if (A) A += (size_t)(blk >> 1) * a.add_stride + ((size_t)p << LOGN);
-    const uint64_t *Pl = a.plus ? a.plus + (((size_t)blk * nl + p) << LOGN) : nullptr;
     uint64_t *O = a.out + (((size_t)blk * nl + p) << LOGN);
     MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
         int r2 = e / Gm::T1, l = e % Gm::T1;
@@ -391,10 +431,10 @@ void kernel_begin(Context &c, cudaStream_t st) {
     if (!c.profiling) return;
     cudaEvent_t e = next_event(c);
     CK(cudaEventRecord(e, st));
-    c.prof.push_back(Context::ProfRec{nullptr, e, nullptr, 0.0});
+    c.prof.push_back(Context::ProfRec{nullptr, e, nullptr, 0.0, 0.0});
 }
 
-void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cudaStream_t st) {
+void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cudaStream_t st, double butterflies) {
     c.launches++;
     if (c.tracing) {
         char buf[160];
@@ -405,6 +445,7 @@ void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cuda
         Context::ProfRec &r = c.prof.back();
         r.name = name;
         r.bytes = bytes;
+        r.butterflies = butterflies;
         r.stop = next_event(c);
         CK(cudaEventRecord(r.stop, st));
     }
@@ -422,26 +463,33 @@ void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cuda
     default: throw Error(MMFHE_ERR_BAD_ARG, "unsupported ring dimension");          \
     }
 
+// Butterflies of one pass over nr rows: N/2 per stage.
+template <int LOGN>
+static double bf_cols(size_t nr) { return (double)nr * (double)(1u << (LOGN - 1)) * Geo<LOGN>::S1; }
+template <int LOGN>
+static double bf_rows(size_t nr) { return (double)nr * (double)(1u << (LOGN - 1)) * Geo<LOGN>::LOGT; }
+
 template <int LOGN>
 static void ntt_launch_t(Context &c, const uint64_t *sb, RowMap ms, uint64_t *db, RowMap md, size_t nr, bool inverse,
                          double bytes, const uint64_t *os, const uint64_t *os_sh, cudaStream_t st) {
     using Gm = Geo<LOGN>;
     dim3 gc(Gm::T1 / COLS, (unsigned)nr), bc(Gm::COLS_THREADS);
     dim3 gr(Gm::H / Gm::ROWS, (unsigned)nr), br(Gm::ROWS * Gm::TPR);
+    const double bfc = bf_cols<LOGN>(nr), bfr = bf_rows<LOGN>(nr);
     if (!inverse) {
         kernel_begin(c, st);
         k_ntt_cols<LOGN, true><<<gc, bc, 0, st>>>(sb, ms, db, md, c.mods, c.tw, nullptr, nullptr);
-        kernel_end(c, "ntt_fwd_cols", gc, bc, bytes, st);
+        kernel_end(c, "ntt_fwd_cols", gc, bc, bytes, st, bfc);
         kernel_begin(c, st);
         k_ntt_rows<LOGN, true><<<gr, br, 0, st>>>(db, md, db, md, c.mods, c.tw);
-        kernel_end(c, "ntt_fwd_rows", gr, br, bytes, st);
+        kernel_end(c, "ntt_fwd_rows", gr, br, bytes, st, bfr);
     } else {
         kernel_begin(c, st);
         k_ntt_rows<LOGN, false><<<gr, br, 0, st>>>(sb, ms, db, md, c.mods, c.tw);
-        kernel_end(c, "ntt_inv_rows", gr, br, bytes, st);
+        kernel_end(c, "ntt_inv_rows", gr, br, bytes, st, bfr);
         kernel_begin(c, st);
         k_ntt_cols<LOGN, false><<<gc, bc, 0, st>>>(db, md, db, md, c.mods, c.tw, os, os_sh);
-        kernel_end(c, "ntt_inv_cols", gc, bc, bytes, st);
+        kernel_end(c, "ntt_inv_cols", gc, bc, bytes, st, bfc);
     }
 }
 
@@ -501,10 +549,10 @@ static void modup_launch_t(Context &c, uint64_t *digits, const uint64_t *y, cons
     dim3 gr(Gm::H / Gm::ROWS, (unsigned)nr), br(Gm::ROWS * Gm::TPR);
     kernel_begin(c, st);
     k_ntt_cols_modup<LOGN><<<gc, bc, 0, st>>>(y, nl, nre, c.alpha, j0, digits, md, m_mont, c.mods, c.tw);
-    kernel_end(c, "ntt_modup_cols", gc, bc, bytes_cols, st);
+    kernel_end(c, "ntt_modup_cols", gc, bc, bytes_cols, st, bf_cols<LOGN>(nr));
     kernel_begin(c, st);
     k_ntt_rows<LOGN, true><<<gr, br, 0, st>>>(digits, md, digits, md, c.mods, c.tw);
-    kernel_end(c, "ntt_fwd_rows", gr, br, bytes_rows, st);
+    kernel_end(c, "ntt_fwd_rows", gr, br, bytes_rows, st, bf_rows<LOGN>(nr));
 }
 
 void launch_modup_ntt(Context &c, uint64_t *digits, const uint64_t *y, int B, int level, cudaStream_t st) {
@@ -555,10 +603,10 @@ static void moddown_launch_t(Context &c, uint64_t *vtmp, const uint64_t *z, cons
     kernel_begin(c, st);
     k_ntt_cols_moddown<LOGN><<<gc, bc, 0, st>>>(z, c.num_p, c.num_q, vtmp, mv, c.d_dn_phat_mont, c.d_dn_negp_mont,
                                                 c.mods, c.tw);
-    kernel_end(c, "ntt_moddown_cols", gc, bc, bytes_cols, st);
+    kernel_end(c, "ntt_moddown_cols", gc, bc, bytes_cols, st, bf_cols<LOGN>(nr));
     kernel_begin(c, st);
     k_ntt_rows_combine<LOGN><<<gr, br, 0, st>>>(vtmp, mv, a, nre, c.d_dn_Pinv, c.d_dn_Pinv_sh, c.mods, c.tw);
-    kernel_end(c, "ntt_combine_rows", gr, br, bytes_rows, st);
+    kernel_end(c, "ntt_combine_rows", gr, br, bytes_rows, st, bf_rows<LOGN>(nr));
 }
 
 void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, int B, int level,
