@@ -301,6 +301,66 @@ mmfhe_status mmfhe_eval_vital(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys
                               const uint64_t *const *in_cts, size_t batch, uint64_t *const *out_cts, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Batching runtime.  The paper evaluates windows one call at a time (its
+ * batched packing fills the slots of one window's ciphertexts); these calls
+ * add a runtime around mmfhe_eval for many uneven windows: CUDA-graph replay
+ * of a whole evaluation, and a batcher that groups windows by frame count and
+ * key set.  Not thread-safe per context: one host thread drives a context.
+ * ---------------------------------------------------------------------- */
+/* CUDA graph of one mmfhe_eval call on fixed DEVICE buffers (in_cts[w],
+ * out_cts[w], 16-byte aligned).  The graph owns a private pool for every
+ * intermediate, so a replay shares no scratch with other work; keys, plan and
+ * the buffers must outlive the graph.  Capture runs the evaluation once
+ * (filling the pool; its outputs are written) on an internal stream, waits
+ * for it, then records a second run.  Replay: mmfhe_graph_launch on any
+ * stream; one replay of a graph at a time.  Errors: BAD_ARG (host buffer,
+ * batch 0), NOT_FOUND, CUDA, OUT_OF_MEMORY. */
+typedef struct mmfhe_graph mmfhe_graph;
+mmfhe_status mmfhe_graph_capture(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *const *keys,
+                                 const uint64_t *const *in_cts, size_t batch, uint64_t *const *out_cts,
+                                 mmfhe_graph **out);
+mmfhe_status mmfhe_graph_launch(mmfhe_graph *graph, void *stream);
+/* Kernels one replay launches, and device bytes the graph holds. */
+mmfhe_status mmfhe_graph_info(const mmfhe_graph *graph, uint64_t *kernels, uint64_t *bytes);
+mmfhe_status mmfhe_graph_destroy(mmfhe_graph *graph);
+
+typedef struct mmfhe_batcher_config {
+    uint32_t max_batch;           /* windows per launch, 1..256 */
+    uint32_t use_graphs;          /* nonzero: one captured graph per (frames, keys, batch size), replayed */
+    uint64_t plan_budget_bytes;   /* device bytes of cached plans (least recently used evicted); 0: no limit */
+    uint64_t graph_budget_bytes;  /* device bytes of cached graphs and their staging; 0: no limit */
+} mmfhe_batcher_config;
+typedef struct mmfhe_batcher_stats {
+    uint64_t windows;             /* windows evaluated */
+    uint64_t batches;             /* evaluations (graph replays or mmfhe_eval batches) */
+    uint64_t graph_replays;
+    uint64_t graphs_captured, graphs_evicted;
+    uint64_t plans_created, plans_evicted;
+    uint64_t plan_bytes, graph_bytes;   /* currently held */
+} mmfhe_batcher_stats;
+typedef struct mmfhe_batcher mmfhe_batcher;
+/* base: the circuit every window runs (size = sizeof(mmfhe_circuit_config));
+ * a window of F frames runs it with frames = F (its own plan, created and
+ * encoded with mmfhe_plan_encode_consts on first use). */
+mmfhe_status mmfhe_batcher_create(mmfhe_ctx *ctx, const mmfhe_circuit_config *base, size_t base_size,
+                                  const mmfhe_batcher_config *cfg, mmfhe_batcher **out);
+/* The plan for `frames` (created on first use).  Owned by the batcher: valid
+ * until the batcher is destroyed or the plan is evicted by a later call. */
+mmfhe_status mmfhe_batcher_plan(mmfhe_batcher *b, uint32_t frames, const mmfhe_plan **out);
+/* Queue one window: input [n_in][2][L+1][N] coefficient form, output as for
+ * mmfhe_eval, host or device memory.  Nothing runs until mmfhe_batcher_flush. */
+mmfhe_status mmfhe_batcher_submit(mmfhe_batcher *b, mmfhe_keys *keys, uint32_t frames, const uint64_t *in,
+                                  uint64_t *out);
+/* Evaluate every queued window: windows with equal (frames, keys) are split
+ * into batches of at most max_batch in submission order.  Outputs in host
+ * memory are complete on return; device outputs are ordered on `stream`. */
+mmfhe_status mmfhe_batcher_flush(mmfhe_batcher *b, void *stream);
+/* Drop every graph that uses `keys` (call before mmfhe_keys_unload). */
+mmfhe_status mmfhe_batcher_forget_keys(mmfhe_batcher *b, const mmfhe_keys *keys);
+mmfhe_status mmfhe_batcher_stats_get(const mmfhe_batcher *b, mmfhe_batcher_stats *out);
+mmfhe_status mmfhe_batcher_destroy(mmfhe_batcher *b);
+
+/* ------------------------------------------------------------------------
  * Host-side helpers (no GPU needed).
  * ---------------------------------------------------------------------- */
 /* Batched-packing layout (Sec. "Packing", batched): values[F][R] (real) ->

@@ -11,10 +11,10 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CONST_TAGS, CircuitConfig, ConstKey, MmfheError, Params, check,
-                   ptr, ptr_array, stream_ptr)
+from ._lib import (CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CONST_TAGS, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
+                   MmfheError, Params, check, ptr, ptr_array, stream_ptr)
 
-__all__ = ["Context", "Keys", "Plan", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
+__all__ = ["Context", "Keys", "Plan", "Graph", "Batcher", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
            "Params", "CIRCUIT_FIR_DFT", "CIRCUIT_VITAL", "vital_config", "fir_dft_config", "fir_dft_params",
            "vital_params"]
 
@@ -154,6 +154,13 @@ class Context:
     def keys(self, user_id=0):
         return Keys(self, user_id)
 
+    def graph(self, plan, keys, ins, outs):
+        """Capture one evaluation of `plan` on device buffers as a CUDA graph."""
+        return Graph(self, plan, keys, ins, outs)
+
+    def batcher(self, base_cfg, **kw):
+        return Batcher(self, base_cfg, **kw)
+
     def plan(self, cfg):
         return Plan(self, cfg)
 
@@ -221,6 +228,90 @@ class Context:
         self._c(f(self.h, plan.h, karr, ptr_array(ins), B, ptr_array(outs), stream_ptr(stream)))
 
 
+class Graph:
+    """A captured CUDA graph of one evaluation on fixed device buffers."""
+
+    def __init__(self, ctx, plan, keys, ins, outs):
+        self.ctx = ctx
+        B = len(ins)
+        kl = keys if isinstance(keys, (list, tuple)) else [keys] * B
+        karr = (ctypes.c_void_p * B)(*[k.h.value for k in kl])
+        h = ctypes.c_void_p()
+        ctx._c(_lib.lib().mmfhe_graph_capture(ctx.h, plan.h, karr, ptr_array(ins), B, ptr_array(outs),
+                                               ctypes.byref(h)))
+        self.h = h
+
+    def launch(self, stream=None):
+        self.ctx._c(_lib.lib().mmfhe_graph_launch(self.h, stream_ptr(stream)))
+
+    def info(self):
+        """(kernels per replay, device bytes held)."""
+        k, b = ctypes.c_uint64(), ctypes.c_uint64()
+        self.ctx._c(_lib.lib().mmfhe_graph_info(self.h, ctypes.byref(k), ctypes.byref(b)))
+        return k.value, b.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.lib().mmfhe_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batcher:
+    """Queues windows of any frame count and user; flush() evaluates them in
+    batches (one plan per frame count, one graph per (frames, keys, size))."""
+
+    def __init__(self, ctx, base_cfg, max_batch=16, use_graphs=True, plan_budget_bytes=0, graph_budget_bytes=0):
+        self.ctx = ctx
+        self.base = base_cfg
+        cfg = BatcherConfig(max_batch, int(bool(use_graphs)), plan_budget_bytes, graph_budget_bytes)
+        h = ctypes.c_void_p()
+        ctx._c(_lib.lib().mmfhe_batcher_create(ctx.h, ctypes.byref(base_cfg), ctypes.sizeof(CircuitConfig),
+                                                ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self._held = []   # buffers of queued windows stay alive until flush
+
+    def plan(self, frames):
+        """The batcher's plan for `frames` (borrowed: valid until evicted)."""
+        h = ctypes.c_void_p()
+        self.ctx._c(_lib.lib().mmfhe_batcher_plan(self.h, frames, ctypes.byref(h)))
+        return Plan._borrowed(self.ctx, h)
+
+    def submit(self, keys, frames, inp, out):
+        self.ctx._c(_lib.lib().mmfhe_batcher_submit(self.h, keys.h, frames, ptr(inp), ptr(out)))
+        self._held.append((inp, out))
+
+    def flush(self, stream=None):
+        try:
+            self.ctx._c(_lib.lib().mmfhe_batcher_flush(self.h, stream_ptr(stream)))
+        finally:
+            self._held = []
+
+    def forget_keys(self, keys):
+        self.ctx._c(_lib.lib().mmfhe_batcher_forget_keys(self.h, keys.h))
+
+    def stats(self):
+        st = BatcherStats()
+        self.ctx._c(_lib.lib().mmfhe_batcher_stats_get(self.h, ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in BatcherStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.lib().mmfhe_batcher_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Keys:
     """Evaluation keys of one user, resident in device memory."""
 
@@ -248,9 +339,16 @@ class Plan:
     def __init__(self, ctx, cfg):
         self.ctx = ctx
         self.cfg = cfg
+        self.owned = True
         h = ctypes.c_void_p()
         ctx._c(_lib.lib().mmfhe_plan_create(ctx.h, ctypes.byref(cfg), ctypes.sizeof(CircuitConfig), ctypes.byref(h)))
         self.h = h
+
+    @classmethod
+    def _borrowed(cls, ctx, h):
+        p = cls.__new__(cls)
+        p.ctx, p.cfg, p.h, p.owned = ctx, None, h, False
+        return p
 
     def num_consts(self):
         v = ctypes.c_uint32()
@@ -291,6 +389,6 @@ class Plan:
         return ni.value, no.value, [lv[i] for i in range(no.value)]
 
     def destroy(self):
-        if getattr(self, "h", None):
+        if getattr(self, "h", None) and self.owned:
             _lib.lib().mmfhe_plan_destroy(self.h)
-            self.h = None
+        self.h = None

@@ -57,6 +57,17 @@ class KernelStat(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("butterflies", ctypes.c_double)]
 
 
+class BatcherConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("use_graphs", ctypes.c_uint32),
+                ("plan_budget_bytes", ctypes.c_uint64), ("graph_budget_bytes", ctypes.c_uint64)]
+
+
+class BatcherStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("windows", "batches", "graph_replays", "graphs_captured",
+                                                "graphs_evicted", "plans_created", "plans_evicted", "plan_bytes",
+                                                "graph_bytes")]
+
+
 class ConstKey(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint32), ("band", ctypes.c_uint32), ("index", ctypes.c_uint32),
                 ("level", ctypes.c_uint32)]
@@ -77,6 +88,17 @@ _SIGS = {
     "mmfhe_profile_enable": [_VP, _INT],
     "mmfhe_profile_get": [_VP, _VP, _U32, ctypes.POINTER(_U32)],
     "mmfhe_measure_butterfly_peak": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "mmfhe_graph_capture": [_VP, _VP, _VP, _VP, _SZ, _VP, _PP],
+    "mmfhe_graph_launch": [_VP, _VP],
+    "mmfhe_graph_info": [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64)],
+    "mmfhe_graph_destroy": [_VP],
+    "mmfhe_batcher_create": [_VP, _VP, _SZ, _VP, _PP],
+    "mmfhe_batcher_plan": [_VP, _U32, _PP],
+    "mmfhe_batcher_submit": [_VP, _VP, _U32, _VP, _VP],
+    "mmfhe_batcher_flush": [_VP, _VP],
+    "mmfhe_batcher_forget_keys": [_VP, _VP],
+    "mmfhe_batcher_stats_get": [_VP, _VP],
+    "mmfhe_batcher_destroy": [_VP],
     "mmfhe_keys_create": [_VP, _U64, _PP],
     "mmfhe_keys_set_relin": [_VP, _VP],
     "mmfhe_keys_set_galois": [_VP, _I32, _VP],

@@ -12,19 +12,10 @@
 
 #include "circuits.h"
 #include "engine.h"
+#include "handles.h"
 #include "hostmath.h"
 
 using namespace mmfhe;
-
-struct mmfhe_ctx {
-    Context *c;
-};
-struct mmfhe_keys {
-    Keys k;
-};
-struct mmfhe_plan {
-    Plan *p;
-};
 
 namespace mmfhe {
 Context *create_context(const mmfhe_params &p, int device);
@@ -55,7 +46,7 @@ static Context *ctx_of(mmfhe_ctx *c) {
     return c->c;
 }
 
-static bool is_host_ptr(const void *p) {
+bool mmfhe::is_host_ptr(const void *p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
@@ -113,6 +104,43 @@ static std::vector<uint64_t *> contiguous_out(uint64_t *base, size_t B, size_t s
     std::vector<uint64_t *> v(B);
     for (size_t b = 0; b < B; b++) v[b] = base + b * stride;
     return v;
+}
+
+// Evaluate a plan on `batch` windows; windows with the same key set form one
+// batch (every launch covers all of them).  Pointers may be host or device.
+void mmfhe::eval_windows(Context &c, const Plan &p, const Keys *const *keys, const uint64_t *const *in_cts,
+                         size_t batch, uint64_t *const *out_cts, cudaStream_t st) {
+    std::map<const Keys *, std::vector<size_t>> groups;
+    for (size_t w = 0; w < batch; w++) {
+        check_ptr(in_cts[w], "window input");
+        check_ptr(out_cts[w], "window output");
+        groups[keys[w]].push_back(w);
+    }
+    const size_t in_w = c.ct_words(c.L);
+    std::vector<size_t> out_off(p.out_levels.size());
+    size_t off = 0;
+    for (size_t o = 0; o < p.out_levels.size(); o++) {
+        out_off[o] = off;
+        off += c.ct_words(p.out_levels[o]);
+    }
+    bool host_out = false;
+    for (auto &g : groups) {
+        const Keys &K = *g.first;
+        const int B = (int)g.second.size();
+        std::vector<const uint64_t *> ins(B);
+        std::vector<uint64_t *> outs(B);
+        for (int b = 0; b < B; b++) {
+            ins[b] = in_cts[g.second[b]];
+            outs[b] = out_cts[g.second[b]];
+        }
+        std::vector<CtB> in;
+        for (int i = 0; i < p.n_in; i++) in.push_back(load_cts(c, ins.data(), i * in_w, B, c.L, 1.0, st));
+        std::vector<CtB> res = run_plan(c, p, K, in, st);
+        in.clear();
+        for (size_t o = 0; o < res.size(); o++) host_out |= store_cts(c, res[o], outs.data(), out_off[o], st);
+    }
+    if (host_out) CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
 }
 
 static const Keys &keys_of(const mmfhe_keys *k, const Context *c) {
@@ -566,13 +594,7 @@ mmfhe_status mmfhe_plan_create(mmfhe_ctx *ctx, const mmfhe_circuit_config *cfg, 
     ABI_TRY
     c = ctx_of(ctx);
     if (!cfg || !out || cfg_size != sizeof(mmfhe_circuit_config)) throw Error(MMFHE_ERR_BAD_ARG, "bad config struct");
-    mmfhe_circuit_config cc = *cfg;
-    if (cc.kind == MMFHE_CIRCUIT_VITAL && cc.dft_gain[0] == 0.0 && cc.dft_gain[1] == 0.0) {
-        // default public spectral gains (median DFT magnitude ~0.5 on the synthetic workload)
-        cc.dft_gain[0] = cc.taylor_order == 3 ? 30.0 : 1.5;
-        cc.dft_gain[1] = cc.taylor_order == 3 ? 1.0 : 0.2;
-    }
-    *out = new mmfhe_plan{create_plan(*c, cc)};
+    *out = new mmfhe_plan{create_plan(*c, *cfg)};
     ABI_CATCH(c)
 }
 
@@ -673,44 +695,12 @@ mmfhe_status mmfhe_eval(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *cons
     ABI_TRY
     c = ctx_of(ctx);
     if (!plan || !plan->p) throw Error(MMFHE_ERR_BAD_ARG, "null plan");
-    const Plan &p = *plan->p;
-    if (p.ctx != c) throw Error(MMFHE_ERR_PARAM_MISMATCH, "plan belongs to another context");
+    if (plan->p->ctx != c) throw Error(MMFHE_ERR_PARAM_MISMATCH, "plan belongs to another context");
     if (batch == 0) return MMFHE_OK;
     if (!keys || !in_cts || !out_cts) throw Error(MMFHE_ERR_BAD_ARG, "null window arrays");
-    cudaStream_t st = (cudaStream_t)stream;
-    // group windows by key set (same user -> one batch, keys read once per launch)
-    std::map<const mmfhe_keys *, std::vector<size_t>> groups;
-    for (size_t w = 0; w < batch; w++) {
-        keys_of(keys[w], c);
-        check_ptr(in_cts[w], "window input");
-        check_ptr(out_cts[w], "window output");
-        groups[keys[w]].push_back(w);
-    }
-    const size_t in_w = c->ct_words(c->L);
-    std::vector<size_t> out_off(p.out_levels.size());
-    size_t off = 0;
-    for (size_t o = 0; o < p.out_levels.size(); o++) {
-        out_off[o] = off;
-        off += c->ct_words(p.out_levels[o]);
-    }
-    bool host_out = false;
-    for (auto &g : groups) {
-        const Keys &K = g.first->k;
-        const int B = (int)g.second.size();
-        std::vector<const uint64_t *> ins(B);
-        std::vector<uint64_t *> outs(B);
-        for (int b = 0; b < B; b++) {
-            ins[b] = in_cts[g.second[b]];
-            outs[b] = out_cts[g.second[b]];
-        }
-        std::vector<CtB> in;
-        for (int i = 0; i < p.n_in; i++) in.push_back(load_cts(*c, ins.data(), i * in_w, B, c->L, 1.0, st));
-        std::vector<CtB> res = run_plan(*c, p, K, in, st);
-        in.clear();
-        for (size_t o = 0; o < res.size(); o++) host_out |= store_cts(*c, res[o], outs.data(), out_off[o], st);
-    }
-    if (host_out) CK(cudaStreamSynchronize(st));
-    CK(cudaGetLastError());
+    std::vector<const Keys *> ks(batch);
+    for (size_t w = 0; w < batch; w++) ks[w] = &keys_of(keys[w], c);
+    eval_windows(*c, *plan->p, ks.data(), in_cts, batch, out_cts, (cudaStream_t)stream);
     ABI_CATCH(c)
 }
 

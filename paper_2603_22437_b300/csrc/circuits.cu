@@ -147,7 +147,13 @@ uint64_t key_of(const mmfhe_const_key &k) {
     return ((uint64_t)k.tag << 48) | ((uint64_t)k.band << 40) | (uint64_t)k.index;
 }
 
-Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg) {
+Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
+    mmfhe_circuit_config cfg = cfg_in;
+    if (cfg.kind == MMFHE_CIRCUIT_VITAL && cfg.dft_gain[0] == 0.0 && cfg.dft_gain[1] == 0.0) {
+        // default public spectral gains (median DFT magnitude ~0.5 on the synthetic workload)
+        cfg.dft_gain[0] = cfg.taylor_order == 3 ? 30.0 : 1.5;
+        cfg.dft_gain[1] = cfg.taylor_order == 3 ? 1.0 : 0.2;
+    }
     check_cfg(c, cfg);
     std::unique_ptr<Plan> p(new Plan());
     p->ctx = &c;

@@ -19,18 +19,12 @@
 #include <mutex>
 
 #include "engine.h"
+#include "handles.h"
 #include "internal.h"
 #include "kernels.h"
 
 using namespace mmfhe;
 
-// Same layouts as in abi.cu (opaque handle types of the C ABI).
-struct mmfhe_ctx {
-    Context *c;
-};
-struct mmfhe_keys {
-    Keys k;
-};
 
 namespace {
 

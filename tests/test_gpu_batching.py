@@ -1,0 +1,134 @@
+"""Batching runtime on the GPU: a captured CUDA graph replays the evaluation
+word for word, and the batcher (windows of uneven frame counts from several
+users, grouped, cut into batches, replayed from graphs or evaluated directly)
+returns for every window exactly the words a lone mmfhe_eval returns.
+
+The evaluation itself is pinned to the oracle by test_gpu_parity and
+test_gpu_vital; here the reference is the library's own unbatched call on a
+plan built for the window's frame count."""
+import numpy as np
+import pytest
+
+from test_gpu_parity import gsmall, load_keys, rand_ct  # noqa: F401  (module fixture)
+
+pytestmark = pytest.mark.gpu
+
+
+def io_words(ctx, plan):
+    n_in, n_out, lv = plan.io()
+    return n_in * 2 * (ctx.L + 1) * ctx.n, sum(2 * (l + 1) * ctx.n for l in lv)
+
+
+def window_inputs(P, plan, seed):
+    n_in, _, _ = plan.io()
+    return np.ascontiguousarray(rand_ct(P, P.L, seed, n_in).reshape(-1))
+
+
+def alone(ctx, plan, keys, x):
+    _, ow = io_words(ctx, plan)
+    out = np.empty(ow, dtype=np.uint64)
+    ctx.eval(plan, keys, [x], [out])
+    return out
+
+
+def test_graph_replay_matches_eval(gsmall):
+    import torch
+
+    import paper_2603_22437_b300 as M
+    P, ctx, keys = gsmall["P"], gsmall["ctx"], gsmall["keys"]
+    plan = ctx.plan(M.fir_dft_config(bins=40))
+    plan.encode_consts()
+    iw, ow = io_words(ctx, plan)
+    B = 2
+    d_in = [torch.zeros(iw, dtype=torch.int64, device="cuda") for _ in range(B)]
+    d_out = [torch.zeros(ow, dtype=torch.int64, device="cuda") for _ in range(B)]
+    g = ctx.graph(plan, keys, d_in, d_out)
+    kernels, held = g.info()
+    assert kernels > 100 and held > 0
+    for trial in range(2):
+        xs = [window_inputs(P, plan, 100 + 10 * trial + w) for w in range(B)]
+        for w in range(B):
+            d_in[w].copy_(torch.from_numpy(xs[w].view(np.int64)))
+        l0 = ctx.launch_count()
+        g.launch()
+        torch.cuda.synchronize()
+        assert ctx.launch_count() - l0 == kernels
+        ref = [np.empty(ow, dtype=np.uint64) for _ in range(B)]
+        ctx.eval(plan, keys, xs, ref)
+        for w in range(B):
+            assert np.array_equal(d_out[w].cpu().numpy().view(np.uint64), ref[w]), (trial, w)
+    g.close()
+
+
+def test_graph_rejects_host_buffers(gsmall):
+    import paper_2603_22437_b300 as M
+    P, ctx, keys = gsmall["P"], gsmall["ctx"], gsmall["keys"]
+    plan = ctx.plan(M.fir_dft_config(bins=16))
+    plan.encode_consts()
+    iw, ow = io_words(ctx, plan)
+    with pytest.raises(M.MmfheError) as e:
+        ctx.graph(plan, keys, [np.zeros(iw, dtype=np.uint64)], [np.zeros(ow, dtype=np.uint64)])
+    assert e.value.name == "BAD_ARG"
+
+
+@pytest.mark.parametrize("use_graphs", [True, False])
+def test_batcher_uneven_frames_two_users(gsmall, use_graphs):
+    import paper_2603_22437_b300 as M
+    P, ctx = gsmall["P"], gsmall["ctx"]
+    users = [gsmall["keys"], load_keys(ctx, P, gsmall["rlk"], gsmall["gks"])]
+    frames = [200, 150, 200, 150, 200, 200, 150]
+    refplans = {}
+    for F in sorted(set(frames)):
+        refplans[F] = ctx.plan(M.fir_dft_config(bins=40, frames=F))
+        refplans[F].encode_consts()
+        assert set(refplans[F].rotations()) <= set(gsmall["gks"])
+    b = ctx.batcher(M.fir_dft_config(bins=40), max_batch=2, use_graphs=use_graphs)
+    subs = []
+    for i, F in enumerate(frames):
+        x = window_inputs(P, refplans[F], 500 + i)
+        out = np.zeros(io_words(ctx, refplans[F])[1], dtype=np.uint64)
+        k = users[i % 2]
+        b.submit(k, F, x, out)
+        subs.append((k, F, x, out))
+    b.flush()
+    for i, (k, F, x, out) in enumerate(subs):
+        assert np.array_equal(out, alone(ctx, refplans[F], k, x)), "window %d (F=%d)" % (i, F)
+    st = b.stats()
+    assert st["windows"] == len(frames) and st["plans_created"] == 2
+    # (F, user) groups: (200,u0) x3, (150,u1) x2, (200,u1) x1, (150,u0) x1 -> batches of <= 2
+    assert st["batches"] == 2 + 1 + 1 + 1
+    if use_graphs:
+        assert st["graph_replays"] == st["batches"] and st["graphs_captured"] == 5
+        # a second flush of the same shapes replays the cached graphs
+        for k, F, x, out in subs:
+            out[:] = 0
+            b.submit(k, F, x, out)
+        b.flush()
+        assert b.stats()["graphs_captured"] == 5
+        for i, (k, F, x, out) in enumerate(subs):
+            assert np.array_equal(out, alone(ctx, refplans[F], k, x)), "replay window %d" % i
+    b.forget_keys(users[1])
+    b.close()
+
+
+def test_batcher_plan_budget_evicts(gsmall):
+    import paper_2603_22437_b300 as M
+    P, ctx, keys = gsmall["P"], gsmall["ctx"], gsmall["keys"]
+    b = ctx.batcher(M.fir_dft_config(bins=16), max_batch=4, use_graphs=True, plan_budget_bytes=1)
+    for rnd in range(2):
+        subs = []
+        for i, F in enumerate((200, 180)):
+            plan = b.plan(F)
+            x = window_inputs(P, plan, 900 + 10 * rnd + i)
+            out = np.zeros(io_words(ctx, plan)[1], dtype=np.uint64)
+            b.submit(keys, F, x, out)
+            subs.append((F, x, out))
+        b.flush()
+        for F, x, out in subs:
+            ref = ctx.plan(M.fir_dft_config(bins=16, frames=F))
+            ref.encode_consts()
+            assert np.array_equal(out, alone(ctx, ref, keys, x)), (rnd, F)
+            ref.destroy()
+    st = b.stats()
+    assert st["plans_evicted"] >= 2 and st["plans_created"] >= 3
+    b.close()
