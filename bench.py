@@ -50,6 +50,11 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--workload", default="vital", choices=["vital", "batching"],
+                    help="vital: the headline chain at B windows per step; batching: uneven windows through the "
+                         "batcher against one call per window")
+    ap.add_argument("--windows", type=int, default=64, help="batching workload: windows per step")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -337,6 +342,7 @@ def run_mine(args, rank, world, local):
         keys.set_galois(k, key_words())
     n_in, n_out, out_levels = plan.io()
     B = args.batch
+    tiles = ctx.tuning() if args.no_autotune else ctx.autotune(B)
     in_words = n_in * 2 * len(P_q) * n
     out_words = sum(2 * (l + 1) * n for l in out_levels)
     # device-resident inputs: B windows of uniform ciphertexts
@@ -403,11 +409,109 @@ def run_mine(args, rank, world, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "batch_windows": B, "windows_per_step_all_gpus": world * B,
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2": "inputs larger than L2 (%d MiB of ciphertexts per step)" % (B * in_words * 8 >> 20)},
+                   "l2": "inputs larger than L2 (%d MiB of ciphertexts per step)" % (B * in_words * 8 >> 20),
+                   "tiles": tiles},
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
                        "note": "latency of a window = its batch's step time"},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
         "wall_s_timed": wall,
+    }
+    return line
+
+
+# Uneven windows: whole-second lengths between 5 and 20 s at 20 frames/s; six
+# lengths spanning the three padded sizes (F_pad = 128, 256, 512).
+BATCH_FRAMES = (100, 140, 200, 260, 340, 400)
+
+
+def run_batching(args, rank, world, local):
+    """Uneven windows of one user through the batcher (groups by frame count,
+    batches of up to --batch windows, one captured CUDA graph per batch shape)
+    against the same windows evaluated one mmfhe_eval call per window, and the
+    batcher without graphs.  All three return identical words (checked), so
+    their decrypted accuracy is identical."""
+    import torch
+
+    import paper_2603_22437_b300 as M
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    params = M.vital_params()
+    ctx = M.Context(params, device=local)
+    n = 1 << params.log_n
+    g = synth.rng(9000 + rank)
+    draw = np.random.default_rng(31 + rank)
+    frames = [int(f) for f in draw.choice(BATCH_FRAMES, size=args.windows)]
+    base = M.vital_config()
+    t0 = time.perf_counter()
+    bat = ctx.batcher(base, max_batch=args.batch, use_graphs=True)
+    bat_ng = ctx.batcher(base, max_batch=args.batch, use_graphs=False)
+    plans = {F: bat.plan(F) for F in sorted(set(frames))}
+    rots = sorted(set().union(*[set(p.rotations()) for p in plans.values()]))
+    io = {F: p.io() for F, p in plans.items()}
+    plan_s = time.perf_counter() - t0
+    qp = params.primes_q + params.primes_p
+    keys = ctx.keys(rank)
+
+    def key_words():
+        return np.ascontiguousarray(np.stack([np.stack([synth.uniform_residues(g, qp, n) for _ in range(2)])
+                                              for _ in range(params.dnum)]))
+
+    keys.set_relin(key_words())
+    for k in rots:
+        keys.set_galois(k, key_words())
+    tiles = ctx.tuning() if args.no_autotune else ctx.autotune(args.batch)
+    out_words = {F: sum(2 * (l + 1) * n for l in io[F][2]) for F in io}
+    d_in = [torch.from_numpy(synth.uniform_ciphertexts(7000 + w, params.primes_q, n, io[F][0]).reshape(-1)
+                             .view(np.int64)).to(dev) for w, F in enumerate(frames)]
+    outs = {m: [torch.empty(out_words[F], dtype=torch.int64, device=dev) for F in frames]
+            for m in ("graph", "nograph", "plain")}
+    plain_plans = plans   # the batcher's own plans (no budget: never evicted)
+    stream = torch.cuda.Stream(device=dev)
+
+    def run(mode):
+        if mode == "plain":
+            for w, F in enumerate(frames):
+                ctx.eval(plain_plans[F], keys, [d_in[w]], [outs[mode][w]], stream=stream)
+            return
+        b = bat if mode == "graph" else bat_ng
+        for w, F in enumerate(frames):
+            b.submit(keys, F, d_in[w], outs[mode][w])
+        b.flush(stream)
+
+    res = {}
+    for mode in ("graph", "nograph", "plain"):
+        for _ in range(max(1, args.warmup)):
+            run(mode)   # first graph flush captures the graphs
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier(world)
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            run(mode)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        res[mode] = {"value": job_throughput(world, len(frames) * args.steps, sum(ms) / 1000.0),
+                     "ms_per_step": float(np.mean(ms))}
+    same = all(torch.equal(outs["graph"][w], outs["plain"][w]) and torch.equal(outs["nograph"][w], outs["plain"][w])
+               for w in range(len(frames)))
+    st = bat.stats()
+    line = {
+        "metric": METRIC, "value": res["graph"]["value"], "unit": "windows/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["graph"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "uneven vital-sign windows through the batcher: %d windows per step, lengths drawn "
+                               "from %s frames (5-20 s at 20 Hz), 256 bins, N=2^15 chain; batches of <= %d windows "
+                               "per (frame count, key set), one CUDA graph per batch shape"
+                               % (len(frames), list(BATCH_FRAMES), args.batch),
+                   "frames_histogram": {str(F): frames.count(F) for F in sorted(set(frames))},
+                   "tiles": tiles, "plan_setup_s": plan_s},
+        "batched_graphs": res["graph"], "batched_no_graphs": res["nograph"], "plain_one_call_per_window": res["plain"],
+        "speedup_vs_plain": res["graph"]["value"] / res["plain"]["value"],
+        "identical_words_all_modes": bool(same),
+        "batcher_stats": st,
     }
     return line
 
@@ -417,6 +521,11 @@ def main():
     rank, world, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.workload == "batching":
+        line = run_batching(args, rank, world, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
         return
     line = run_mine(args, rank, world, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

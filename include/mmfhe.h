@@ -301,6 +301,28 @@ mmfhe_status mmfhe_eval_vital(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys
                               const uint64_t *const *in_cts, size_t batch, uint64_t *const *out_cts, void *stream);
 
 /* ------------------------------------------------------------------------
+ * Autotuner (no counterpart in the paper).  The NTT passes and the key inner
+ * product come in tile-shape variants: columns per CTA of the strided pass
+ * (8 or 16), threads per CTA of the contiguous pass (128 or 256) and windows
+ * per thread of the key inner product (1, 2, 4, 8).  mmfhe_autotune times
+ * every variant on `batch` ciphertexts at `level` (NTT: forward + inverse of
+ * all their rows; key inner product: a rotation's digits and key) and keeps
+ * the fastest for every later call on the context.  Every variant computes
+ * the same words.  Errors: BAD_ARG (batch 0 or level above the top), CUDA.
+ * ---------------------------------------------------------------------- */
+typedef struct mmfhe_tuning {
+    uint32_t ntt_cols_width;     /* 8 or 16 */
+    uint32_t ntt_rows_threads;   /* 128 or 256 */
+    uint32_t keyip_windows;      /* 1, 2, 4 or 8 */
+    float ntt_ms[4];             /* last autotune, ms: (8,128), (8,256), (16,128), (16,256) */
+    float keyip_ms[4];           /* last autotune, ms: window groups 1, 2, 4, 8 */
+} mmfhe_tuning;
+mmfhe_status mmfhe_autotune(mmfhe_ctx *ctx, uint32_t batch, uint32_t level, mmfhe_tuning *out);
+mmfhe_status mmfhe_tuning_get(const mmfhe_ctx *ctx, mmfhe_tuning *out);
+/* Set the variants explicitly (timings ignored); BAD_ARG for other values. */
+mmfhe_status mmfhe_tuning_set(mmfhe_ctx *ctx, const mmfhe_tuning *in);
+
+/* ------------------------------------------------------------------------
  * Batching runtime.  The paper evaluates windows one call at a time (its
  * batched packing fills the slots of one window's ciphertexts); these calls
  * add a runtime around mmfhe_eval for many uneven windows: CUDA-graph replay

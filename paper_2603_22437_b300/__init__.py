@@ -12,7 +12,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CONST_TAGS, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
-                   MmfheError, Params, check, ptr, ptr_array, stream_ptr)
+                   MmfheError, Params, Tuning, check, ptr, ptr_array, stream_ptr)
 
 __all__ = ["Context", "Keys", "Plan", "Graph", "Batcher", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
            "Params", "CIRCUIT_FIR_DFT", "CIRCUIT_VITAL", "vital_config", "fir_dft_config", "fir_dft_params",
@@ -154,6 +154,22 @@ class Context:
     def keys(self, user_id=0):
         return Keys(self, user_id)
 
+    def autotune(self, batch, level=None):
+        """Time the NTT / key-inner-product tile variants on `batch`
+        ciphertexts at `level` (default: top) and keep the fastest."""
+        t = Tuning()
+        self._c(_lib.lib().mmfhe_autotune(self.h, batch, self.L if level is None else level, ctypes.byref(t)))
+        return _tuning_dict(t)
+
+    def tuning(self):
+        t = Tuning()
+        self._c(_lib.lib().mmfhe_tuning_get(self.h, ctypes.byref(t)))
+        return _tuning_dict(t)
+
+    def set_tuning(self, cols_width, rows_threads, keyip_windows):
+        t = Tuning(cols_width, rows_threads, keyip_windows)
+        self._c(_lib.lib().mmfhe_tuning_set(self.h, ctypes.byref(t)))
+
     def graph(self, plan, keys, ins, outs):
         """Capture one evaluation of `plan` on device buffers as a CUDA graph."""
         return Graph(self, plan, keys, ins, outs)
@@ -226,6 +242,11 @@ class Context:
         karr = (ctypes.c_void_p * B)(*[k.h.value for k in kl])
         f = _lib.lib().mmfhe_eval_vital if vital else _lib.lib().mmfhe_eval
         self._c(f(self.h, plan.h, karr, ptr_array(ins), B, ptr_array(outs), stream_ptr(stream)))
+
+
+def _tuning_dict(t):
+    return {"ntt_cols_width": t.ntt_cols_width, "ntt_rows_threads": t.ntt_rows_threads,
+            "keyip_windows": t.keyip_windows, "ntt_ms": list(t.ntt_ms), "keyip_ms": list(t.keyip_ms)}
 
 
 class Graph:

@@ -57,6 +57,11 @@ class KernelStat(ctypes.Structure):
                 ("bytes", ctypes.c_double), ("butterflies", ctypes.c_double)]
 
 
+class Tuning(ctypes.Structure):
+    _fields_ = [("ntt_cols_width", ctypes.c_uint32), ("ntt_rows_threads", ctypes.c_uint32),
+                ("keyip_windows", ctypes.c_uint32), ("ntt_ms", ctypes.c_float * 4), ("keyip_ms", ctypes.c_float * 4)]
+
+
 class BatcherConfig(ctypes.Structure):
     _fields_ = [("max_batch", ctypes.c_uint32), ("use_graphs", ctypes.c_uint32),
                 ("plan_budget_bytes", ctypes.c_uint64), ("graph_budget_bytes", ctypes.c_uint64)]
@@ -88,6 +93,9 @@ _SIGS = {
     "mmfhe_profile_enable": [_VP, _INT],
     "mmfhe_profile_get": [_VP, _VP, _U32, ctypes.POINTER(_U32)],
     "mmfhe_measure_butterfly_peak": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "mmfhe_autotune": [_VP, _U32, _U32, _VP],
+    "mmfhe_tuning_get": [_VP, _VP],
+    "mmfhe_tuning_set": [_VP, _VP],
     "mmfhe_graph_capture": [_VP, _VP, _VP, _VP, _SZ, _VP, _PP],
     "mmfhe_graph_launch": [_VP, _VP],
     "mmfhe_graph_info": [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64)],

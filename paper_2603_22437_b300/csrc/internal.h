@@ -122,8 +122,19 @@ struct LevelConsts {
     uint64_t *d_rs_qinv = nullptr, *d_rs_qinv_sh = nullptr, *d_rs_qmod = nullptr;
 };
 
+// Tile shapes and work split picked by the autotuner (tune.cu).
+struct Tune {
+    int cols_w = 16;     // columns per CTA of the strided NTT pass (8 or 16)
+    int rows_t = 256;    // threads per CTA of the contiguous NTT pass (128 or 256)
+    int keyip_wg = 4;    // windows per thread of the key inner product (1, 2, 4 or 8)
+    float ntt_ms[4] = {};     // last autotune: NTT pair per (cols_w, rows_t) in {8,16} x {128,256}
+    float keyip_ms[4] = {};   // last autotune: key inner product per window group 1, 2, 4, 8
+};
+
+
 struct Context {
     int device = 0;
+    Tune tune;
     mmfhe_params params{};
     int logn = 0;
     uint32_t n = 0;
@@ -230,6 +241,10 @@ RowMap make_map(uint32_t period, uint32_t block_stride, const std::vector<int> &
 void launch_ntt(Context &c, const RowsView &src, const RowsView &dst, bool inverse, cudaStream_t s,
                 const uint64_t *oscale = nullptr, const uint64_t *oscale_sh = nullptr);
 void launch_copy_rows(Context &c, const RowsView &src, const RowsView &dst, cudaStream_t s);
+
+// Time the tile-shape variants on a batch of `batch` ciphertexts at `level`
+// and keep the fastest in c.tune (tune.cu).
+void autotune(Context &c, int batch, int level);
 
 // Butterflies per second of register-resident 64-bit and 32-bit butterfly loops (peaks.cu).
 void measure_butterfly_peak(Context &c, double *bf64, double *bf32);

@@ -157,19 +157,19 @@ __global__ void k_modup_bconv(uint64_t *out, const uint64_t *coef, const uint64_
 
 // Key inner product fused with the Galois permutation of the digits:
 //   u_h[b][t][x] = sum_j digits[b][j][t][pi(x)] * key[j][h][krow(t)][x]
-// Each thread owns (t, x) for a group of KEYIP_WG windows: a key word is read
-// once per group (from L2 after the first group), and the group's digit words
-// are loaded together.
-constexpr int KEYIP_WG = 4;
-
-__global__ void __launch_bounds__(EW_THREADS, 3) k_keyip(uint64_t *u, const uint64_t *digits, const uint64_t *own, size_t own_stride, size_t own_jstride,
-                        const uint64_t *key, int B, int level, int beta, int alpha, int nrows_ext, int key_rows, int L1,
-                        int logn, uint32_t galois, ModTab mt, int pid_p0) {
+// Each thread owns (t, x) for a group of WG windows: a key word is read once
+// per group (from L2 after the first group), and the group's digit words are
+// loaded together.  WG is picked by the autotuner (1, 2, 4 or 8).
+template <int WG>
+__global__ void __launch_bounds__(EW_THREADS, WG <= 2 ? 4 : (WG == 4 ? 3 : 2))
+    k_keyip(uint64_t *u, const uint64_t *digits, const uint64_t *own, size_t own_stride, size_t own_jstride,
+            const uint64_t *key, int B, int level, int beta, int alpha, int nrows_ext, int key_rows, int L1, int logn,
+            uint32_t galois, ModTab mt, int pid_p0) {
     const uint32_t n = 1u << logn;
     const size_t per_group = (size_t)nrows_ext * n;
-    const size_t total = per_group * (size_t)((B + KEYIP_WG - 1) / KEYIP_WG);
+    const size_t total = per_group * (size_t)((B + WG - 1) / WG);
     for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
-        const int b0 = (int)(w / per_group) * KEYIP_WG;
+        const int b0 = (int)(w / per_group) * WG;
         const size_t tw = w % per_group;
         const uint32_t x = (uint32_t)(tw & (n - 1));
         const int t = (int)(tw >> logn);
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(EW_THREADS, 3) k_keyip(uint64_t *u, const uint
         const int jown = t <= level ? t / alpha : -1;   // the digit whose own primes hold row t
         // keys are in Montgomery form: sum the 128-bit products of the digits
         // (beta q^2 < q 2^64 because beta <= 8 and q < 2^61), reduce once
-        uint64_t h0[KEYIP_WG] = {}, l0[KEYIP_WG] = {}, h1[KEYIP_WG] = {}, l1[KEYIP_WG] = {};
+        uint64_t h0[WG] = {}, l0[WG] = {}, h1[WG] = {}, l1[WG] = {};
         for (int j = 0; j < beta; j++) {
             const uint64_t kb = key[(((size_t)j * 2 + 0) * key_rows + krow) * n + x];
             const uint64_t ka = key[(((size_t)j * 2 + 1) * key_rows + krow) * n + x];
@@ -193,17 +193,17 @@ __global__ void __launch_bounds__(EW_THREADS, 3) k_keyip(uint64_t *u, const uint
                 src = digits + ((size_t)j * nrows_ext + t) * n + px;
                 wstride = (size_t)beta * nrows_ext * n;
             }
-            uint64_t dv[KEYIP_WG];
+            uint64_t dv[WG];
 #pragma unroll
-            for (int k = 0; k < KEYIP_WG; k++) dv[k] = b0 + k < B ? src[(size_t)(b0 + k) * wstride] : 0;
+            for (int k = 0; k < WG; k++) dv[k] = b0 + k < B ? src[(size_t)(b0 + k) * wstride] : 0;
 #pragma unroll
-            for (int k = 0; k < KEYIP_WG; k++) {
+            for (int k = 0; k < WG; k++) {
                 mm::mac128(h0[k], l0[k], dv[k], kb);
                 mm::mac128(h1[k], l1[k], dv[k], ka);
             }
         }
 #pragma unroll
-        for (int k = 0; k < KEYIP_WG; k++) {
+        for (int k = 0; k < WG; k++) {
             if (b0 + k >= B) break;
             uint64_t *U = u + ((size_t)(b0 + k) * 2 * nrows_ext) * n;
             U[(size_t)t * n + x] = mm::redc(h0[k], l0[k], q, qinv);
@@ -422,11 +422,20 @@ void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint6
                     cudaStream_t st) {
     int nre = level + 1 + c.num_p;
     size_t work = (size_t)nre * c.n;
-    dim3 g = grid_for(work * (size_t)((B + KEYIP_WG - 1) / KEYIP_WG));
+    const int wg = c.tune.keyip_wg;
+    dim3 g = grid_for(work * (size_t)((B + wg - 1) / wg));
     // reads: B*beta digit rows + beta*2 key rows; writes: B*2 output rows
     double bytes = W8(work * ((size_t)B * beta + 2 * beta + 2 * B));
-    LAUNCH(c, "keyip", bytes, g, k_keyip, u, digits, own, own_stride, own_jstride, key, B, level, beta, c.alpha, nre,
-           c.num_q + c.num_p, c.num_q, c.logn, galois, c.mods, c.num_q);
+#define MMFHE_KEYIP(WG)                                                                                        \
+    LAUNCH(c, "keyip", bytes, g, k_keyip<WG>, u, digits, own, own_stride, own_jstride, key, B, level, beta,    \
+           c.alpha, nre, c.num_q + c.num_p, c.num_q, c.logn, galois, c.mods, c.num_q)
+    switch (wg) {
+    case 1: MMFHE_KEYIP(1); break;
+    case 2: MMFHE_KEYIP(2); break;
+    case 8: MMFHE_KEYIP(8); break;
+    default: MMFHE_KEYIP(4); break;
+    }
+#undef MMFHE_KEYIP
 }
 
 void k_launch_moddown_bconv(Context &c, uint64_t *v, const uint64_t *u, int B, int level, const ModDownConsts &dc,

@@ -132,3 +132,34 @@ def test_batcher_plan_budget_evicts(gsmall):
     st = b.stats()
     assert st["plans_evicted"] >= 2 and st["plans_created"] >= 3
     b.close()
+
+
+def test_every_tile_variant_gives_the_same_words(gsmall):
+    """The autotuner only picks among variants that compute identical words:
+    the FIR + DFT circuit (NTTs, fused ModUp / ModDown, key inner products of
+    relinearisations and rotations) under every tile shape equals the
+    default-shape result, which the parity tests pin to the oracle."""
+    import paper_2603_22437_b300 as M
+    P, ctx, keys = gsmall["P"], gsmall["ctx"], gsmall["keys"]
+    plan = ctx.plan(M.fir_dft_config(bins=40))
+    plan.encode_consts()
+    xs = [window_inputs(P, plan, 77 + w) for w in range(3)]
+    saved = ctx.tuning()
+    ctx.set_tuning(16, 256, 4)
+    ref = [np.empty(io_words(ctx, plan)[1], dtype=np.uint64) for _ in xs]
+    ctx.eval(plan, keys, xs, ref)
+    for cw in (8, 16):
+        for rt in (128, 256):
+            for wg in (1, 2, 8):
+                ctx.set_tuning(cw, rt, wg)
+                outs = [np.empty_like(r) for r in ref]
+                ctx.eval(plan, keys, xs, outs)
+                for w in range(3):
+                    assert np.array_equal(outs[w], ref[w]), (cw, rt, wg, w)
+    with pytest.raises(M.MmfheError):
+        ctx.set_tuning(32, 256, 4)
+    t = ctx.autotune(3)
+    assert t["ntt_cols_width"] in (8, 16) and t["ntt_rows_threads"] in (128, 256)
+    assert t["keyip_windows"] in (1, 2, 4, 8)
+    assert min(t["ntt_ms"]) > 0 and min(t["keyip_ms"]) > 0
+    ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"])
