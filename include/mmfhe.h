@@ -383,6 +383,59 @@ mmfhe_status mmfhe_batcher_stats_get(const mmfhe_batcher *b, mmfhe_batcher_stats
 mmfhe_status mmfhe_batcher_destroy(mmfhe_batcher *b);
 
 /* ------------------------------------------------------------------------
+ * Serving loop (no counterpart in the paper's text: a multi-user runtime
+ * around the evaluator).  Windows from many users arrive at any time
+ * (mmfhe_server_submit, thread-safe); a worker thread admits them into
+ * batches of equal frame count (users mixed: each window is key-switched with
+ * its own user's keys) as soon as one of `streams` slots is free
+ * (continuous batching: windows that arrive while others run join the next
+ * batch), runs each batch on its slot's CUDA stream with the slot's private
+ * memory pool (batches on different slots overlap on the device), and keeps
+ * users' evaluation keys resident under key_budget_bytes, reloading an
+ * evicted user's keys from the words registered with mmfhe_server_add_user
+ * (least recently used first; keys of a running batch are never evicted).
+ * While a server exists, its worker thread is the only user of the context.
+ * ---------------------------------------------------------------------- */
+typedef struct mmfhe_server_config {
+    uint32_t max_batch;           /* windows per batch, 1..256 */
+    uint32_t streams;             /* concurrent batches, 1..8 */
+    uint64_t key_budget_bytes;    /* device bytes of resident key sets; 0: no limit */
+} mmfhe_server_config;
+typedef struct mmfhe_server_stats {
+    uint64_t submitted, completed, failed;
+    uint64_t batches;             /* dispatched batches */
+    uint64_t key_loads, key_evictions;
+    uint64_t keys_resident, key_bytes;
+    double mean_batch;            /* windows per batch */
+    double p50_ms, p99_ms;        /* submit -> output written, completed windows */
+    double windows_per_s;         /* completed / (last completion - first submission) */
+} mmfhe_server_stats;
+typedef struct mmfhe_server mmfhe_server;
+/* base: the circuit every window runs (one plan per frame count, created on
+ * first use).  The worker thread starts here. */
+mmfhe_status mmfhe_server_create(mmfhe_ctx *ctx, const mmfhe_circuit_config *base, size_t base_size,
+                                 const mmfhe_server_config *cfg, mmfhe_server **out);
+/* Register a user's evaluation keys: the relinearization key and n_rot
+ * Galois keys (layouts as mmfhe_keys_set_*), host or device words that the
+ * caller keeps unchanged until mmfhe_server_destroy.  Nothing is uploaded
+ * until the user's first window runs.  BAD_ARG if user_id is registered. */
+mmfhe_status mmfhe_server_add_user(mmfhe_server *s, uint64_t user_id, const uint64_t *relin, const int32_t *rotations,
+                                   const uint64_t *const *galois, uint32_t n_rot);
+/* Queue one window (input and output as for mmfhe_eval; host buffers should
+ * be pinned for the copies to overlap).  *ticket identifies it.  NOT_FOUND
+ * for an unknown user. */
+mmfhe_status mmfhe_server_submit(mmfhe_server *s, uint64_t user_id, uint32_t frames, const uint64_t *in,
+                                 uint64_t *out, uint64_t *ticket);
+/* Wait up to timeout_ms for a window: OK (output written; *latency_ms =
+ * submit -> completion), TIMEOUT, or the status its batch failed with. */
+mmfhe_status mmfhe_server_wait(mmfhe_server *s, uint64_t ticket, uint32_t timeout_ms, double *latency_ms);
+/* Wait up to timeout_ms until every submitted window has completed. */
+mmfhe_status mmfhe_server_drain(mmfhe_server *s, uint32_t timeout_ms);
+mmfhe_status mmfhe_server_stats_get(mmfhe_server *s, mmfhe_server_stats *out);
+/* Stop the worker after the queued windows complete, free everything. */
+mmfhe_status mmfhe_server_destroy(mmfhe_server *s);
+
+/* ------------------------------------------------------------------------
  * Host-side helpers (no GPU needed).
  * ---------------------------------------------------------------------- */
 /* Batched-packing layout (Sec. "Packing", batched): values[F][R] (real) ->

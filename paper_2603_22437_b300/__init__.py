@@ -12,9 +12,9 @@ import numpy as np
 
 from . import _lib
 from ._lib import (CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CONST_TAGS, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
-                   MmfheError, Params, Tuning, check, ptr, ptr_array, stream_ptr)
+                   MmfheError, Params, ServerConfig, ServerStats, Tuning, check, ptr, ptr_array, stream_ptr)
 
-__all__ = ["Context", "Keys", "Plan", "Graph", "Batcher", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
+__all__ = ["Context", "Keys", "Plan", "Graph", "Batcher", "Server", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
            "Params", "CIRCUIT_FIR_DFT", "CIRCUIT_VITAL", "vital_config", "fir_dft_config", "fir_dft_params",
            "vital_params"]
 
@@ -177,6 +177,9 @@ class Context:
     def batcher(self, base_cfg, **kw):
         return Batcher(self, base_cfg, **kw)
 
+    def server(self, base_cfg, **kw):
+        return Server(self, base_cfg, **kw)
+
     def plan(self, cfg):
         return Plan(self, cfg)
 
@@ -325,6 +328,63 @@ class Batcher:
         if getattr(self, "h", None):
             _lib.lib().mmfhe_batcher_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Serving loop: submit windows of registered users from any thread; a
+    native worker batches and runs them (see mmfhe_server_* in mmfhe.h)."""
+
+    def __init__(self, ctx, base_cfg, max_batch=16, streams=2, key_budget_bytes=0):
+        self.ctx = ctx
+        cfg = ServerConfig(max_batch, streams, key_budget_bytes)
+        h = ctypes.c_void_p()
+        ctx._c(_lib.lib().mmfhe_server_create(ctx.h, ctypes.byref(base_cfg), ctypes.sizeof(CircuitConfig),
+                                               ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+        self._users = {}     # registered key words stay referenced until close
+        self._live = {}      # ticket -> (input, output) kept alive until waited
+
+    def add_user(self, user_id, relin, galois):
+        """galois: {rotation: words}; the arrays must stay unchanged."""
+        rots = sorted(galois)
+        rarr = (ctypes.c_int32 * max(1, len(rots)))(*rots)
+        garr = ptr_array([galois[r] for r in rots]) if rots else None
+        self.ctx._c(_lib.lib().mmfhe_server_add_user(self.h, user_id, ptr(relin), rarr, garr, len(rots)))
+        self._users[user_id] = (relin, galois, rarr, garr)
+
+    def submit(self, user_id, frames, inp, out):
+        t = ctypes.c_uint64()
+        self.ctx._c(_lib.lib().mmfhe_server_submit(self.h, user_id, frames, ptr(inp), ptr(out), ctypes.byref(t)))
+        self._live[t.value] = (inp, out)
+        return t.value
+
+    def wait(self, ticket, timeout_ms=600000):
+        """Latency (ms) of a completed window; raises on timeout or failure."""
+        lat = ctypes.c_double()
+        self.ctx._c(_lib.lib().mmfhe_server_wait(self.h, ticket, timeout_ms, ctypes.byref(lat)))
+        self._live.pop(ticket, None)
+        return lat.value
+
+    def drain(self, timeout_ms=600000):
+        self.ctx._c(_lib.lib().mmfhe_server_drain(self.h, timeout_ms))
+        self._live.clear()
+
+    def stats(self):
+        st = ServerStats()
+        self.ctx._c(_lib.lib().mmfhe_server_stats_get(self.h, ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.lib().mmfhe_server_destroy(self.h)
+            self.h = None
+            self._live.clear()
 
     def __del__(self):
         try:

@@ -73,6 +73,16 @@ class BatcherStats(ctypes.Structure):
                                                 "graph_bytes")]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32), ("key_budget_bytes", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "batches", "key_loads",
+                                                "key_evictions", "keys_resident", "key_bytes")] + \
+               [(n, ctypes.c_double) for n in ("mean_batch", "p50_ms", "p99_ms", "windows_per_s")]
+
+
 class ConstKey(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint32), ("band", ctypes.c_uint32), ("index", ctypes.c_uint32),
                 ("level", ctypes.c_uint32)]
@@ -100,6 +110,13 @@ _SIGS = {
     "mmfhe_graph_launch": [_VP, _VP],
     "mmfhe_graph_info": [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64)],
     "mmfhe_graph_destroy": [_VP],
+    "mmfhe_server_create": [_VP, _VP, _SZ, _VP, _PP],
+    "mmfhe_server_add_user": [_VP, _U64, _VP, _VP, _VP, _U32],
+    "mmfhe_server_submit": [_VP, _U64, _U32, _VP, _VP, ctypes.POINTER(_U64)],
+    "mmfhe_server_wait": [_VP, _U64, _U32, ctypes.POINTER(ctypes.c_double)],
+    "mmfhe_server_drain": [_VP, _U32],
+    "mmfhe_server_stats_get": [_VP, _VP],
+    "mmfhe_server_destroy": [_VP],
     "mmfhe_batcher_create": [_VP, _VP, _SZ, _VP, _PP],
     "mmfhe_batcher_plan": [_VP, _U32, _PP],
     "mmfhe_batcher_submit": [_VP, _VP, _U32, _VP, _VP],

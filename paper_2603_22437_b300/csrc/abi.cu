@@ -109,12 +109,43 @@ static std::vector<uint64_t *> contiguous_out(uint64_t *base, size_t B, size_t s
 // Evaluate a plan on `batch` windows; windows with the same key set form one
 // batch (every launch covers all of them).  Pointers may be host or device.
 void mmfhe::eval_windows(Context &c, const Plan &p, const Keys *const *keys, const uint64_t *const *in_cts,
-                         size_t batch, uint64_t *const *out_cts, cudaStream_t st) {
-    std::map<const Keys *, std::vector<size_t>> groups;
+                         size_t batch, uint64_t *const *out_cts, cudaStream_t st, bool mix_users) {
+    // groups of windows evaluated together, with the key set they run under
+    std::vector<std::pair<const Keys *, std::vector<size_t>>> groups;
+    std::vector<std::unique_ptr<Keys>> mixed;   // per-window key views of mixed batches
     for (size_t w = 0; w < batch; w++) {
         check_ptr(in_cts[w], "window input");
         check_ptr(out_cts[w], "window output");
-        groups[keys[w]].push_back(w);
+    }
+    if (!mix_users) {
+        std::map<const Keys *, size_t> gi;
+        for (size_t w = 0; w < batch; w++) {
+            auto it = gi.find(keys[w]);
+            if (it == gi.end()) {
+                it = gi.emplace(keys[w], groups.size()).first;
+                groups.push_back({keys[w], {}});
+            }
+            groups[it->second].second.push_back(w);
+        }
+    } else {
+        for (size_t w0 = 0; w0 < batch; w0 += MAX_KEY_WINDOWS) {
+            const size_t nb = std::min<size_t>(MAX_KEY_WINDOWS, batch - w0);
+            std::vector<size_t> idx(nb);
+            bool same = true;
+            for (size_t i = 0; i < nb; i++) {
+                idx[i] = w0 + i;
+                same &= keys[w0 + i] == keys[w0];
+            }
+            if (same) {
+                groups.push_back({keys[w0], idx});
+                continue;
+            }
+            std::unique_ptr<Keys> view(new Keys());
+            view->ctx = &c;
+            for (size_t i = 0; i < nb; i++) view->windows.push_back(keys[w0 + i]);
+            groups.push_back({view.get(), idx});
+            mixed.push_back(std::move(view));
+        }
     }
     const size_t in_w = c.ct_words(c.L);
     std::vector<size_t> out_off(p.out_levels.size());
@@ -147,6 +178,21 @@ static const Keys &keys_of(const mmfhe_keys *k, const Context *c) {
     if (!k) throw Error(MMFHE_ERR_BAD_ARG, "null keys");
     if (k->k.ctx != c) throw Error(MMFHE_ERR_PARAM_MISMATCH, "keys belong to another context");
     return k->k;
+}
+
+Buf mmfhe::load_key(Context &c, const uint64_t *words) {
+    check_ptr(words, "key words");
+    const int rows = c.num_q + c.num_p;
+    const size_t total = (size_t)c.dnum * 2 * rows * c.n;
+    Buf b(c.pool.get(), total);
+    CK(cudaMemcpy(b.get(), words, total * 8, cudaMemcpyDefault));
+    std::vector<int> pids(rows);
+    for (int i = 0; i < rows; i++) pids[i] = i;
+    RowsView v{b.get(), make_map(rows, rows, pids), (size_t)c.dnum * 2 * rows};
+    launch_ntt(c, v, v, false, 0);
+    k_launch_mont_convert(c, v, true, 0);   // keys are kept in Montgomery form (key inner product)
+    CK(cudaStreamSynchronize(0));
+    return b;
 }
 
 extern "C" {
@@ -290,21 +336,6 @@ mmfhe_status mmfhe_keys_create(mmfhe_ctx *ctx, uint64_t user_id, mmfhe_keys **ou
     k->k.user = user_id;
     *out = k;
     ABI_CATCH(c)
-}
-
-static Buf load_key(Context &c, const uint64_t *words) {
-    check_ptr(words, "key words");
-    const int rows = c.num_q + c.num_p;
-    const size_t total = (size_t)c.dnum * 2 * rows * c.n;
-    Buf b(c.pool.get(), total);
-    CK(cudaMemcpy(b.get(), words, total * 8, cudaMemcpyDefault));
-    std::vector<int> pids(rows);
-    for (int i = 0; i < rows; i++) pids[i] = i;
-    RowsView v{b.get(), make_map(rows, rows, pids), (size_t)c.dnum * 2 * rows};
-    launch_ntt(c, v, v, false, 0);
-    k_launch_mont_convert(c, v, true, 0);   // keys are kept in Montgomery form (key inner product)
-    CK(cudaStreamSynchronize(0));
-    return b;
 }
 
 mmfhe_status mmfhe_keys_set_relin(mmfhe_keys *keys, const uint64_t *words) {
@@ -524,8 +555,7 @@ mmfhe_status mmfhe_keyswitch(mmfhe_ctx *ctx, const mmfhe_keys *keys, int which, 
     if (!batch) return MMFHE_OK;
     check_ptr(out, "out"); check_ptr(d, "d");
     const int nl = (int)level + 1;
-    const uint64_t *key = which == 0 ? K.rlk.get() : galois_key(K, norm_rot(*c, rotation));
-    if (!key) throw Error(MMFHE_ERR_NOT_FOUND, "relinearization key not loaded");
+    const KeyPtrs key = which == 0 ? relin_key(K) : galois_key(K, norm_rot(*c, rotation));
     Buf dd(c->pool.get(), batch * nl * c->n);
     CK(cudaMemcpyAsync(dd.get(), d, batch * nl * c->n * 8, cudaMemcpyDefault, st));
     ntt_q_blocks(*c, dd.get(), batch, nl, false, st);

@@ -147,9 +147,10 @@ void digits_fill_own(Context &c, DigitsB &dg, cudaStream_t st) {
     }
 }
 
-CtB keyswitch_moddown(Context &c, const DigitsB &dg, const uint64_t *key, uint32_t galois, const uint64_t *add0,
+CtB keyswitch_moddown(Context &c, const DigitsB &dg, const KeyPtrs &key, uint32_t galois, const uint64_t *add0,
                       const uint64_t *add1, size_t add_stride_words, double scale, cudaStream_t st, const CtB *plus) {
     const int level = dg.level, B = dg.B, nl = level + 1, nre = level + 1 + c.num_p, K = c.num_p;
+    if (key.n != 1 && key.n != B) throw Error(MMFHE_ERR_BAD_ARG, "one switching key per window or one for all");
     if (plus && (plus->level != level || plus->B != B)) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "add: operand levels differ");
     Buf u(c.pool.get(), (size_t)B * 2 * nre * c.n);
     k_launch_keyip(c, u.get(), dg.buf.get(), dg.own, dg.own_stride, 0, key, B, level, dg.beta, galois, st);
@@ -171,11 +172,11 @@ CtB keyswitch_moddown(Context &c, const DigitsB &dg, const uint64_t *key, uint32
 }
 
 CtB relin(Context &c, const Keys &k, const TensorB &t, cudaStream_t st) {
-    if (!k.rlk.get()) throw Error(MMFHE_ERR_NOT_FOUND, "relinearization key not loaded");
+    const KeyPtrs key = relin_key(k);
     const int nl = t.level + 1;
     const uint64_t *base = t.buf.get();
     DigitsB dg = modup(c, base + (size_t)2 * nl * c.n, (size_t)3 * nl, t.B, t.level, st);
-    return keyswitch_moddown(c, dg, k.rlk.get(), 1, base, base + (size_t)nl * c.n, (size_t)3 * nl * c.n, t.scale, st);
+    return keyswitch_moddown(c, dg, key, 1, base, base + (size_t)nl * c.n, (size_t)3 * nl * c.n, t.scale, st);
 }
 
 CtB rescale(Context &c, const CtB &a, cudaStream_t st) {
@@ -195,10 +196,40 @@ CtB rescale(Context &c, const CtB &a, cudaStream_t st) {
     return out;
 }
 
-const uint64_t *galois_key(const Keys &k, int32_t rot) {
+static const uint64_t *one_galois_key(const Keys &k, int32_t rot) {
     auto it = k.gk.find(rot);
     if (it == k.gk.end()) throw Error(MMFHE_ERR_NOT_FOUND, "Galois key for rotation " + std::to_string(rot) + " not loaded");
     return it->second.get();
+}
+
+KeyPtrs galois_key(const Keys &k, int32_t rot) {
+    KeyPtrs p;
+    if (k.windows.empty()) {
+        p.k[0] = one_galois_key(k, rot);
+        p.n = 1;
+        return p;
+    }
+    if (k.windows.size() > (size_t)MAX_KEY_WINDOWS) throw Error(MMFHE_ERR_BAD_ARG, "too many key sets in one batch");
+    for (size_t w = 0; w < k.windows.size(); w++) p.k[w] = one_galois_key(*k.windows[w], rot);
+    p.n = (int)k.windows.size();
+    return p;
+}
+
+KeyPtrs relin_key(const Keys &k) {
+    KeyPtrs p;
+    auto one = [](const Keys &x) {
+        if (!x.rlk.get()) throw Error(MMFHE_ERR_NOT_FOUND, "relinearization key not loaded");
+        return (const uint64_t *)x.rlk.get();
+    };
+    if (k.windows.empty()) {
+        p.k[0] = one(k);
+        p.n = 1;
+        return p;
+    }
+    if (k.windows.size() > (size_t)MAX_KEY_WINDOWS) throw Error(MMFHE_ERR_BAD_ARG, "too many key sets in one batch");
+    for (size_t w = 0; w < k.windows.size(); w++) p.k[w] = one(*k.windows[w]);
+    p.n = (int)k.windows.size();
+    return p;
 }
 
 std::vector<CtB> rotate_hoisted(Context &c, const Keys &k, const CtB &a, const std::vector<int32_t> &rots,
@@ -241,7 +272,7 @@ CtB rotate_add(Context &c, const Keys &k, const CtB &a, int32_t rot, const CtB &
         return r;
     }
     const int nl = a.level + 1;
-    const uint64_t *key = galois_key(k, nr);
+    const KeyPtrs key = galois_key(k, nr);
     DigitsB dg = modup(c, a.ptr() + (size_t)nl * c.n, (size_t)2 * nl, a.B, a.level, st);
     return keyswitch_moddown(c, dg, key, galois_elt(c, nr), a.ptr(), nullptr, (size_t)2 * nl * c.n, a.scale, st,
                              &plus);

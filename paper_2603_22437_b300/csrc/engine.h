@@ -44,10 +44,13 @@ void digits_fill_own(Context &c, DigitsB &dg, cudaStream_t st);
 // ModDown(digits . key); `key` = device key in evaluation domain; galois != 1
 // applies the automorphism to the digits; add0/add1 optional addends (add0
 // read through the same automorphism).
-CtB keyswitch_moddown(Context &c, const DigitsB &dg, const uint64_t *key, uint32_t galois, const uint64_t *add0,
+CtB keyswitch_moddown(Context &c, const DigitsB &dg, const KeyPtrs &key, uint32_t galois, const uint64_t *add0,
                       const uint64_t *add1, size_t add_stride_words, double scale, cudaStream_t st,
                       const CtB *plus = nullptr);
-const uint64_t *galois_key(const Keys &k, int32_t rot);
+// Switching keys of a rotation / of relinearization (per window for a batch
+// mixing users); NOT_FOUND when a key is not loaded.
+KeyPtrs galois_key(const Keys &k, int32_t rot);
+KeyPtrs relin_key(const Keys &k);
 
 CtB rotate(Context &c, const Keys &k, const CtB &a, int32_t rot, cudaStream_t st);
 // Rot(a, rot) + plus, the addition fused into the key switch's last kernel.

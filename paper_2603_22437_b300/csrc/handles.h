@@ -18,11 +18,16 @@ struct mmfhe_plan {
 
 namespace mmfhe {
 
-// Evaluate a plan on `batch` windows (abi.cu); windows with the same key set
-// form one batch.  Pointers may be host or device memory.
+// Evaluate a plan on `batch` windows (abi.cu).  Windows with the same key set
+// form one batch; with mix_users, windows of different key sets share batches
+// of up to MAX_KEY_WINDOWS (each window switched with its own keys).
+// Pointers may be host or device memory.
 void eval_windows(Context &c, const Plan &p, const Keys *const *keys, const uint64_t *const *in_cts, size_t batch,
-                  uint64_t *const *out_cts, cudaStream_t st);
+                  uint64_t *const *out_cts, cudaStream_t st, bool mix_users = false);
 // True unless p is device (or managed) memory.
 bool is_host_ptr(const void *p);
+// Upload one switching key ([dnum][2][L+1+K][N], coefficient form, host or
+// device words) into the evaluation domain in Montgomery form (abi.cu).
+Buf load_key(Context &c, const uint64_t *words);
 
 }  // namespace mmfhe

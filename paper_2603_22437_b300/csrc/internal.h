@@ -222,6 +222,18 @@ struct Keys {
     uint64_t user = 0;
     Buf rlk;                                   // [dnum][2][L+1+K][N] eval
     std::map<int32_t, Buf> gk;                 // rotation (mod N/2) -> key
+    // A batch mixing users: the key set of every window, in window order
+    // (rlk and gk are then unused).
+    std::vector<const Keys *> windows;
+};
+
+// Switching-key words of one key switch: one key for every window (n == 1)
+// or one per window (n == B, a batch mixing users), passed by value to the
+// key inner product.
+constexpr int MAX_KEY_WINDOWS = 64;
+struct KeyPtrs {
+    const uint64_t *k[MAX_KEY_WINDOWS];
+    int n = 0;
 };
 
 // ---------------------------------------------------------------------------

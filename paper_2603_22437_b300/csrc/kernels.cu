@@ -8,6 +8,8 @@
 //   key                [dnum][2][L+1+K][N]        (device, evaluation domain)
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 
 #include "internal.h"
@@ -159,11 +161,12 @@ __global__ void k_modup_bconv(uint64_t *out, const uint64_t *coef, const uint64_
 //   u_h[b][t][x] = sum_j digits[b][j][t][pi(x)] * key[j][h][krow(t)][x]
 // Each thread owns (t, x) for a group of WG windows: a key word is read once
 // per group (from L2 after the first group), and the group's digit words are
-// loaded together.  WG is picked by the autotuner (1, 2, 4 or 8).
-template <int WG>
+// loaded together.  WG is picked by the autotuner (1, 2, 4 or 8).  PW: every
+// window has its own key (a batch mixing users), key.k[b] for window b.
+template <int WG, bool PW>
 __global__ void __launch_bounds__(EW_THREADS, WG <= 2 ? 4 : (WG == 4 ? 3 : 2))
     k_keyip(uint64_t *u, const uint64_t *digits, const uint64_t *own, size_t own_stride, size_t own_jstride,
-            const uint64_t *key, int B, int level, int beta, int alpha, int nrows_ext, int key_rows, int L1, int logn,
+            KeyPtrs key, int B, int level, int beta, int alpha, int nrows_ext, int key_rows, int L1, int logn,
             uint32_t galois, ModTab mt, int pid_p0) {
     const uint32_t n = 1u << logn;
     const size_t per_group = (size_t)nrows_ext * n;
@@ -182,8 +185,20 @@ __global__ void __launch_bounds__(EW_THREADS, WG <= 2 ? 4 : (WG == 4 ? 3 : 2))
         // (beta q^2 < q 2^64 because beta <= 8 and q < 2^61), reduce once
         uint64_t h0[WG] = {}, l0[WG] = {}, h1[WG] = {}, l1[WG] = {};
         for (int j = 0; j < beta; j++) {
-            const uint64_t kb = key[(((size_t)j * 2 + 0) * key_rows + krow) * n + x];
-            const uint64_t ka = key[(((size_t)j * 2 + 1) * key_rows + krow) * n + x];
+            const size_t kb_off = (((size_t)j * 2 + 0) * key_rows + krow) * n + x;
+            const size_t ka_off = (((size_t)j * 2 + 1) * key_rows + krow) * n + x;
+            uint64_t kb[PW ? WG : 1], ka[PW ? WG : 1];
+            if (PW) {
+#pragma unroll
+                for (int k = 0; k < (PW ? WG : 1); k++) {
+                    const uint64_t *K = key.k[b0 + k < B ? b0 + k : b0];
+                    kb[k] = K[kb_off];
+                    ka[k] = K[ka_off];
+                }
+            } else {
+                kb[0] = key.k[0][kb_off];
+                ka[0] = key.k[0][ka_off];
+            }
             const uint64_t *src;
             size_t wstride;
             if (j == jown) {
@@ -198,8 +213,8 @@ __global__ void __launch_bounds__(EW_THREADS, WG <= 2 ? 4 : (WG == 4 ? 3 : 2))
             for (int k = 0; k < WG; k++) dv[k] = b0 + k < B ? src[(size_t)(b0 + k) * wstride] : 0;
 #pragma unroll
             for (int k = 0; k < WG; k++) {
-                mm::mac128(h0[k], l0[k], dv[k], kb);
-                mm::mac128(h1[k], l1[k], dv[k], ka);
+                mm::mac128(h0[k], l0[k], dv[k], kb[PW ? k : 0]);
+                mm::mac128(h1[k], l1[k], dv[k], ka[PW ? k : 0]);
             }
         }
 #pragma unroll
@@ -418,24 +433,33 @@ void k_launch_modup_bconv(Context &c, uint64_t *out, const uint64_t *coef, const
 }
 
 void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint64_t *own, size_t own_stride,
-                    size_t own_jstride, const uint64_t *key, int B, int level, int beta, uint32_t galois,
+                    size_t own_jstride, const KeyPtrs &key, int B, int level, int beta, uint32_t galois,
                     cudaStream_t st) {
+    if (key.n != 1 && key.n != B) throw Error(MMFHE_ERR_BAD_ARG, "keyip: one key or one per window");
+    const bool pw = key.n > 1;
     int nre = level + 1 + c.num_p;
     size_t work = (size_t)nre * c.n;
     const int wg = c.tune.keyip_wg;
     dim3 g = grid_for(work * (size_t)((B + wg - 1) / wg));
-    // reads: B*beta digit rows + beta*2 key rows; writes: B*2 output rows
-    double bytes = W8(work * ((size_t)B * beta + 2 * beta + 2 * B));
-#define MMFHE_KEYIP(WG)                                                                                        \
-    LAUNCH(c, "keyip", bytes, g, k_keyip<WG>, u, digits, own, own_stride, own_jstride, key, B, level, beta,    \
-           c.alpha, nre, c.num_q + c.num_p, c.num_q, c.logn, galois, c.mods, c.num_q)
+    // reads: B*beta digit rows + beta*2 key rows (per window when mixing users); writes: B*2 output rows
+    double bytes = W8(work * ((size_t)B * beta + 2 * beta * (size_t)key.n + 2 * B));
+    auto go = [&](auto wg_c, auto pw_c) {
+        constexpr int WG = decltype(wg_c)::value;
+        constexpr bool PW = decltype(pw_c)::value;
+        kernel_begin(c, st);
+        k_keyip<WG, PW><<<g, EW_THREADS, 0, st>>>(u, digits, own, own_stride, own_jstride, key, B, level, beta, c.alpha,
+                                                  nre, c.num_q + c.num_p, c.num_q, c.logn, galois, c.mods, c.num_q);
+        kernel_end(c, "keyip", g, dim3(EW_THREADS), bytes, st);
+        CK(cudaGetLastError());
+    };
+    using T = std::true_type;
+    using F = std::false_type;
     switch (wg) {
-    case 1: MMFHE_KEYIP(1); break;
-    case 2: MMFHE_KEYIP(2); break;
-    case 8: MMFHE_KEYIP(8); break;
-    default: MMFHE_KEYIP(4); break;
+    case 1: pw ? go(std::integral_constant<int, 1>{}, T{}) : go(std::integral_constant<int, 1>{}, F{}); break;
+    case 2: pw ? go(std::integral_constant<int, 2>{}, T{}) : go(std::integral_constant<int, 2>{}, F{}); break;
+    case 8: pw ? go(std::integral_constant<int, 8>{}, T{}) : go(std::integral_constant<int, 8>{}, F{}); break;
+    default: pw ? go(std::integral_constant<int, 4>{}, T{}) : go(std::integral_constant<int, 4>{}, F{}); break;
     }
-#undef MMFHE_KEYIP
 }
 
 void k_launch_moddown_bconv(Context &c, uint64_t *v, const uint64_t *u, int B, int level, const ModDownConsts &dc,

@@ -48,11 +48,12 @@ void k_launch_tensor(Context &c, uint64_t *d, const uint64_t *a, const uint64_t 
                      bool acc, cudaStream_t st);
 void k_launch_modup_bconv(Context &c, uint64_t *out, const uint64_t *coef, const uint64_t *deval, size_t deval_stride,
                           int B, int level, const ModUpConsts &mc, cudaStream_t st);
-// u_h[b][t] = sum_j digit_j[b][t] (after the Galois permutation) * key[j][h][t];
+// u_h[b][t] = sum_j digit_j[b][t] (after the Galois permutation) * key_b[j][h][t]
+// (key_b = key.k[0] for every window, or key.k[b] when key.n == B);
 // rows of a digit inside its own primes come from `own` (window b, digit j,
 // row t at own + b * own_stride + j * own_jstride + t * N).
 void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint64_t *own, size_t own_stride,
-                    size_t own_jstride, const uint64_t *key, int B, int level, int beta, uint32_t galois,
+                    size_t own_jstride, const KeyPtrs &key, int B, int level, int beta, uint32_t galois,
                     cudaStream_t st);
 void k_launch_moddown_bconv(Context &c, uint64_t *v, const uint64_t *u, int B, int level, const ModDownConsts &dc,
                             cudaStream_t st);

@@ -91,8 +91,7 @@ extern "C" mmfhe_status mmfhe_keyswitch_noalloc(mmfhe_ctx *ctx, const mmfhe_keys
         if (!is_device_ptr(out) || !is_device_ptr(d) || ((uintptr_t)out & 15) || ((uintptr_t)d & 15))
             throw Error(MMFHE_ERR_BAD_ARG, "keyswitch_noalloc needs 16-byte aligned device pointers");
         const Keys &K = keys->k;
-        const uint64_t *key = which == 0 ? K.rlk.get() : galois_key(K, norm_rot(*c, rotation));
-        if (!key) throw Error(MMFHE_ERR_NOT_FOUND, "relinearization key not loaded");
+        const KeyPtrs key = which == 0 ? relin_key(K) : galois_key(K, norm_rot(*c, rotation));
         cudaStream_t st = (cudaStream_t)stream;
         const int nl = (int)level + 1, nre = nl + c->num_p;
         const LevelConsts &lc = c->lv[level];

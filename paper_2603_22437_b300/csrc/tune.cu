@@ -79,13 +79,15 @@ void autotune(Context &c, int batch, int level) {
         CK(cudaMemsetAsync(own.get(), 0, own.words() * 8, st));
         CK(cudaMemsetAsync(key.get(), 0, key.words() * 8, st));
         const uint32_t g = galois_elt(c, 1);
+        KeyPtrs kp;
+        kp.k[0] = key.get();
+        kp.n = 1;
         const int wgs[4] = {1, 2, 4, 8};
         float bk = 1e30f;
         for (int i = 0; i < 4; i++) {
             c.tune.keyip_wg = wgs[i];
             const float ms = time_best(st, [&] {
-                k_launch_keyip(c, u.get(), dg.get(), own.get(), (size_t)nl * c.n, 0, key.get(), batch, level, beta, g,
-                               st);
+                k_launch_keyip(c, u.get(), dg.get(), own.get(), (size_t)nl * c.n, 0, kp, batch, level, beta, g, st);
             });
             best.keyip_ms[i] = ms;
             if (ms < bk) {

@@ -1,0 +1,100 @@
+"""Serving loop on the GPU: windows of several users with their own keys and
+uneven frame counts, submitted from two threads while earlier ones run,
+under a key budget that holds two users' keys (so keys are evicted and
+reloaded).  Every window's output equals, word for word, the same window
+evaluated alone with mmfhe_eval; a user whose keys lack a rotation fails
+alone, without disturbing the others."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from test_gpu_parity import gsmall, rand_ct  # noqa: F401  (module fixture)
+
+pytestmark = pytest.mark.gpu
+
+
+def user_keys(P, rots, seed):
+    """Uniform switching-key words (valid residues; the comparison is
+    word-exact, so keys need not come from a secret)."""
+    g = np.random.default_rng(seed)
+    rows = P.q + P.p
+
+    def one():
+        out = np.empty((P.dnum, 2, len(rows), P.n), dtype=np.uint64)
+        for i, q in enumerate(rows):
+            out[:, :, i, :] = g.integers(0, q, out[:, :, i, :].shape, dtype=np.uint64)
+        return out
+
+    return one(), {r: one() for r in rots}
+
+
+def test_serving_mix_equals_alone(gsmall):
+    import paper_2603_22437_b300 as M
+    P, ctx = gsmall["P"], gsmall["ctx"]
+    base = M.fir_dft_config(bins=40)
+    plans = {}
+    for F in (200, 150):
+        plans[F] = ctx.plan(M.fir_dft_config(bins=40, frames=F))
+        plans[F].encode_consts()
+    rots = sorted(set(plans[200].rotations()) | set(plans[150].rotations()))
+    users = {u: user_keys(P, rots, 40 + u) for u in range(3)}
+    n_in, _, lv = plans[200].io()
+    out_words = sum(2 * (l + 1) * P.n for l in lv)
+    key_set = (1 + len(rots)) * P.dnum * 2 * (len(P.q) + len(P.p)) * P.n * 8
+    srv = ctx.server(base, max_batch=2, streams=2, key_budget_bytes=2 * key_set + key_set // 2)
+    for u, (relin, gal) in users.items():
+        srv.add_user(u, relin, gal)
+    # user 9: no Galois keys at all -> its windows fail with NOT_FOUND
+    bad_relin, _ = user_keys(P, [], 99)
+    srv.add_user(9, bad_relin, {})
+    with pytest.raises(M.MmfheError) as e:
+        srv.submit(12345, 200, np.zeros(8, dtype=np.uint64), np.zeros(8, dtype=np.uint64))
+    assert e.value.name == "NOT_FOUND"
+
+    jobs = []
+    for i in range(14):
+        u = i % 3
+        F = 200 if (i // 3) % 2 == 0 else 150
+        x = np.ascontiguousarray(rand_ct(P, P.L, 300 + i, n_in).reshape(-1))
+        jobs.append((u, F, x, np.zeros(out_words, dtype=np.uint64)))
+    tickets = [None] * len(jobs)
+
+    def producer(idx):
+        for i in idx:
+            u, F, x, out = jobs[i]
+            tickets[i] = srv.submit(u, F, x, out)
+            time.sleep(0.002 * (i % 3))
+
+    th = [threading.Thread(target=producer, args=(list(range(k, len(jobs), 2)),)) for k in range(2)]
+    for t in th:
+        t.start()
+    bad = srv.submit(9, 200, jobs[0][2], np.zeros(out_words, dtype=np.uint64))
+    for t in th:
+        t.join()
+    lat = [srv.wait(t) for t in tickets]
+    assert all(x > 0 for x in lat)
+    with pytest.raises(M.MmfheError) as e:
+        srv.wait(bad)
+    assert e.value.name == "NOT_FOUND"
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(jobs) and st["failed"] == 1 and st["submitted"] == len(jobs) + 1
+    assert st["key_loads"] >= 4 and st["key_evictions"] >= 1
+    assert st["p99_ms"] >= st["p50_ms"] > 0 and 1 <= st["mean_batch"] <= 2
+
+    # alone: each window by itself, with its own user's keys
+    for u in users:
+        relin, gal = users[u]
+        k = ctx.keys(100 + u)
+        k.set_relin(relin)
+        for r, w in gal.items():
+            k.set_galois(r, w)
+        for i, (uu, F, x, out) in enumerate(jobs):
+            if uu != u:
+                continue
+            ref = np.empty(out_words, dtype=np.uint64)
+            ctx.eval(plans[F], k, [x], [ref])
+            assert np.array_equal(out, ref), "window %d (user %d, F=%d)" % (i, u, F)
+        k.unload()
