@@ -165,37 +165,45 @@ struct mmfhe_server {
         cv_done.notify_all();
     }
 
-    // Take queued windows of the oldest window's frame count, in order, up to
-    // max_batch, as long as the distinct users' key sets fit the key budget
-    // together; users of a batch may differ (each window keeps its own keys).
+    // Take queued windows of the oldest window's frame count, up to
+    // max_batch: the oldest window first, then windows whose users' keys are
+    // resident, then the others, in queue order, as long as the distinct
+    // users' key sets fit the key budget together.  Users of a batch may
+    // differ (each window keeps its own keys).
     bool take_batch(std::vector<uint64_t> &tickets, uint32_t &frames, std::vector<User *> &batch_users,
                     std::vector<User *> &window_users) {
         std::lock_guard<std::mutex> g(mu);
         if (queue.empty()) return false;
         frames = reqs[queue.front()].frames;
         uint64_t bytes = 0;
-        for (auto it = queue.begin(); it != queue.end() && tickets.size() < cfg.max_batch;) {
-            Req &r = reqs[*it];
-            if (r.frames != frames) {
-                ++it;
-                continue;
-            }
-            User *u = &users[r.user];
-            const bool known = std::find(batch_users.begin(), batch_users.end(), u) != batch_users.end();
-            if (!known) {
-                const uint64_t need = key_set_bytes(*u);
-                if (cfg.key_budget_bytes && !batch_users.empty() && bytes + need > cfg.key_budget_bytes) {
+        auto take = [&](bool resident_only, bool first_only) {
+            for (auto it = queue.begin(); it != queue.end() && tickets.size() < cfg.max_batch;) {
+                Req &r = reqs[*it];
+                User *u = &users[r.user];
+                if (r.frames != frames || (resident_only && !u->keys)) {
                     ++it;
                     continue;
                 }
-                bytes += need;
-                batch_users.push_back(u);
+                const bool known = std::find(batch_users.begin(), batch_users.end(), u) != batch_users.end();
+                if (!known) {
+                    const uint64_t need = key_set_bytes(*u);
+                    if (cfg.key_budget_bytes && !batch_users.empty() && bytes + need > cfg.key_budget_bytes) {
+                        ++it;
+                        continue;
+                    }
+                    bytes += need;
+                    batch_users.push_back(u);
+                }
+                tickets.push_back(*it);
+                window_users.push_back(u);
+                r.state = RUNNING;
+                it = queue.erase(it);
+                if (first_only) return;
             }
-            tickets.push_back(*it);
-            window_users.push_back(u);
-            r.state = RUNNING;
-            it = queue.erase(it);
-        }
+        };
+        take(false, true);    // the oldest window always goes
+        take(true, false);    // windows that need no key upload
+        take(false, false);   // the rest, budget permitting
         return true;
     }
 
