@@ -303,8 +303,9 @@ mmfhe_status mmfhe_eval_vital(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys
 /* ------------------------------------------------------------------------
  * Autotuner (no counterpart in the paper).  The NTT passes and the key inner
  * product come in tile-shape variants: columns per CTA of the strided pass
- * (8 or 16), threads per CTA of the contiguous pass (128 or 256) and windows
- * per thread of the key inner product (1, 2, 4, 8).  mmfhe_autotune times
+ * (8 or 16), threads per CTA of the contiguous pass (128 or 256), windows per
+ * thread of the key inner product (1, 2, 4, 8) and converted rows per CTA of
+ * the fused ModUp / ModDown strided passes (1, 2, 4).  mmfhe_autotune times
  * every variant on `batch` ciphertexts at `level` (NTT: forward + inverse of
  * all their rows; key inner product: a rotation's digits and key) and keeps
  * the fastest for every later call on the context.  Every variant computes
@@ -314,8 +315,10 @@ typedef struct mmfhe_tuning {
     uint32_t ntt_cols_width;     /* 8 or 16 */
     uint32_t ntt_rows_threads;   /* 128 or 256 */
     uint32_t keyip_windows;      /* 1, 2, 4 or 8 */
+    uint32_t conv_rows;          /* rows per CTA of the fused ModUp / ModDown conversions: 1, 2 or 4 */
     float ntt_ms[4];             /* last autotune, ms: (8,128), (8,256), (16,128), (16,256) */
     float keyip_ms[4];           /* last autotune, ms: window groups 1, 2, 4, 8 */
+    float conv_ms[3];            /* last autotune, ms: ModUp + ModDown with 1, 2, 4 rows per CTA */
 } mmfhe_tuning;
 mmfhe_status mmfhe_autotune(mmfhe_ctx *ctx, uint32_t batch, uint32_t level, mmfhe_tuning *out);
 mmfhe_status mmfhe_tuning_get(const mmfhe_ctx *ctx, mmfhe_tuning *out);

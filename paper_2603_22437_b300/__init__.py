@@ -166,8 +166,8 @@ class Context:
         self._c(_lib.lib().mmfhe_tuning_get(self.h, ctypes.byref(t)))
         return _tuning_dict(t)
 
-    def set_tuning(self, cols_width, rows_threads, keyip_windows):
-        t = Tuning(cols_width, rows_threads, keyip_windows)
+    def set_tuning(self, cols_width, rows_threads, keyip_windows, conv_rows=1):
+        t = Tuning(cols_width, rows_threads, keyip_windows, conv_rows)
         self._c(_lib.lib().mmfhe_tuning_set(self.h, ctypes.byref(t)))
 
     def graph(self, plan, keys, ins, outs):
@@ -249,7 +249,8 @@ class Context:
 
 def _tuning_dict(t):
     return {"ntt_cols_width": t.ntt_cols_width, "ntt_rows_threads": t.ntt_rows_threads,
-            "keyip_windows": t.keyip_windows, "ntt_ms": list(t.ntt_ms), "keyip_ms": list(t.keyip_ms)}
+            "keyip_windows": t.keyip_windows, "conv_rows": t.conv_rows, "ntt_ms": list(t.ntt_ms),
+            "keyip_ms": list(t.keyip_ms), "conv_ms": list(t.conv_ms)}
 
 
 class Graph:

@@ -48,6 +48,15 @@ struct RowMap {
     uint8_t act[MAXROWMAP];
 };
 
+// Groups of rows of one launch that share a base-conversion source: group g
+// holds the active rows act[start[g]] .. act[start[g] + count[g] - 1] of the
+// launch's row map (consecutive, same source rows).
+struct RowGroups {
+    uint32_t n;
+    uint8_t start[MAXROWMAP];
+    uint8_t count[MAXROWMAP];
+};
+
 // Twiddle tables (device): [prime id][N], forward psi^brv(i) and inverse
 // psi^-brv(i) with Shoup companions; n_inv per prime with companion.
 struct Twiddles {
@@ -127,8 +136,10 @@ struct Tune {
     int cols_w = 16;     // columns per CTA of the strided NTT pass (8 or 16)
     int rows_t = 256;    // threads per CTA of the contiguous NTT pass (128 or 256)
     int keyip_wg = 4;    // windows per thread of the key inner product (1, 2, 4 or 8)
+    int conv_rows = 1;   // converted rows per CTA of the fused ModUp / ModDown strided passes (1, 2 or 4)
     float ntt_ms[4] = {};     // last autotune: NTT pair per (cols_w, rows_t) in {8,16} x {128,256}
     float keyip_ms[4] = {};   // last autotune: key inner product per window group 1, 2, 4, 8
+    float conv_ms[3] = {};    // last autotune: fused ModUp + ModDown per rows per CTA 1, 2, 4
 };
 
 

@@ -47,6 +47,25 @@ static uint32_t set_active(RowMap &ms, RowMap &md) {
     return n;
 }
 
+// Consecutive active rows that read the same conversion source, in groups of
+// at most rg: rows p, p' share it when p / src_rows == p' / src_rows (one
+// ModUp digit), or always when src_rows == 0 (every ModDown row).
+static RowGroups make_groups(const RowMap &m, int rg, int src_rows) {
+    RowGroups g{};
+    for (uint32_t k = 0; k < m.nact; k++) {
+        const bool same = g.n > 0 && g.count[g.n - 1] < rg &&
+                          (src_rows == 0 || m.act[k] / src_rows == m.act[g.start[g.n - 1]] / src_rows);
+        if (same) {
+            g.count[g.n - 1]++;
+        } else {
+            g.start[g.n] = (uint8_t)k;
+            g.count[g.n] = 1;
+            g.n++;
+        }
+    }
+    return g;
+}
+
 static cudaEvent_t next_event(Context &c) {
     if (c.event_next == c.event_pool.size()) {
         cudaEvent_t e;
@@ -157,6 +176,7 @@ void launch_modup_ntt(Context &c, uint64_t *digits, const uint64_t *y, int B, in
         }
         RowMap md = make_map(nj * nre, beta * nre, pids), ms = md;
         const uint32_t nact = set_active(ms, md);
+        const RowGroups gr = make_groups(md, c.tune.conv_rows, nre);
         uint64_t *dbase = digits + (((size_t)j0 * nre) << c.logn);
         const size_t chunk = 65535 / nact;
         for (size_t b0 = 0; b0 < (size_t)B; b0 += chunk) {
@@ -170,7 +190,7 @@ void launch_modup_ntt(Context &c, uint64_t *digits, const uint64_t *y, int B, in
             int src_rows = 0;
             for (int jj = 0; jj < nj; jj++) src_rows += (int)lc.digits[j0 + jj].size();
             const double bc_ = row * ((double)nr + (double)nb * src_rows), br_ = 2.0 * row * (double)nr;
-#define MMFHE_MODUP_CALL(L) modup_launch_##L(c, db, yb, md, nr, nl, nre, j0, lc.d_up_mm, bc_, br_, st)
+#define MMFHE_MODUP_CALL(L) modup_launch_##L(c, db, yb, md, gr, nb, nl, nre, j0, lc.d_up_mm, bc_, br_, st)
             MMFHE_LOGN_DISPATCH(c.logn, MMFHE_MODUP_CALL)
 #undef MMFHE_MODUP_CALL
         }
@@ -186,6 +206,7 @@ void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const Com
     for (int i = 0; i < nl; i++) pids[i] = i;
     RowMap mv = make_map(nl, nl, pids), ms = mv;
     const uint32_t nact = set_active(ms, mv);
+    const RowGroups gr = make_groups(mv, c.tune.conv_rows, 0);
     const size_t blocks = (size_t)B * 2;
     const size_t chunk = 65535 / nact;
     for (size_t b0 = 0; b0 < blocks; b0 += chunk) {
@@ -202,7 +223,7 @@ void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const Com
         const double bc_ = row * ((double)nr + (double)nb * K);
         const double br_ = row * ((double)nr * (3 + (ab.plus ? 1 : 0)) + (ab.add0 ? nr / 2.0 : 0) + (ab.add1 ? nr / 2.0 : 0));
 #define MMFHE_MODDOWN_CALL(L)                                                                                   \
-    moddown_launch_##L(c, vtmp + ((b0 * nl) << c.logn), z + ((b0 * K) << c.logn), mv, nr, ab, nre, bc_, br_, st)
+    moddown_launch_##L(c, vtmp + ((b0 * nl) << c.logn), z + ((b0 * K) << c.logn), mv, gr, nb, ab, nre, bc_, br_, st)
         MMFHE_LOGN_DISPATCH(c.logn, MMFHE_MODDOWN_CALL)
 #undef MMFHE_MODDOWN_CALL
     }

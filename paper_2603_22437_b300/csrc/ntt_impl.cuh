@@ -245,105 +245,159 @@ __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16,
     }
 }
 
-// Base-conversion staging of a strided-pass tile: element (h, lo0 + c) of the
-// tile is sum_k X[k][h * T1 + lo0 + c] * F[k * fstride] reduced once by
-// Montgomery (F in Montgomery form).  CENTERED adds c * negp with
-// c = #{k : X[k] > P[k] / 2} (the centered correction of the ModDown conversion).
-template <int LOGN, int CW, int NT, bool CENTERED = false>
-__device__ __forceinline__ void conv_load(uint64_t *sm, const uint64_t *__restrict__ X, const uint64_t *__restrict__ F,
-                                          int fstride, int lo0, uint64_t q, uint64_t qinv,
-                                          const uint64_t *P = nullptr, uint64_t negp = 0) {
+// Per-row constants of a converted group, staged in shared memory: prime,
+// q^-1 mod 2^64, the Montgomery factors f[r][k] (k < 8) and, for the
+// centered conversion, c(-P) mod q and the half moduli of the sources.
+template <int RG>
+struct ConvConsts {
+    uint64_t q[RG], qinv[RG], negp[RG], f[RG][8], half[8];
+    uint32_t pid[RG];
+};
+
+// Base-conversion staging of the tiles of a group of nr <= RG rows: element
+// (h, lo0 + c) of tile r is sum_k X[k][h * T1 + lo0 + c] * f[r][k], reduced
+// once by Montgomery (the factors are in Montgomery form).  The NT source
+// words of an element are loaded once for all rows of the group.  CENTERED
+// adds c * negp[r] with c = #{k : X[k] > P_k / 2} (the ModDown conversion).
+template <int LOGN, int CW, int RG, int NT, bool CENTERED>
+__device__ __forceinline__ void conv_load(uint64_t *tiles, int nr, const uint64_t *__restrict__ X, int lo0,
+                                          const ConvConsts<RG> &cc) {
     using Gm = Geo<LOGN, CW>;
-    uint64_t f[NT], half[NT];
-#pragma unroll
-    for (int k = 0; k < NT; k++) {
-        f[k] = F[(size_t)k * fstride];
-        half[k] = CENTERED ? P[k] >> 1 : 0;
-    }
+    constexpr int TILE = Gm::H * Gm::COLS;
     MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) {
         const size_t idx = (size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS);
-        uint64_t hi = 0, lo = 0, neg = 0;
+        uint64_t x[NT], neg = 0;
 #pragma unroll
         for (int k = 0; k < NT; k++) {
-            const uint64_t x = X[((size_t)k << LOGN) + idx];
-            if (CENTERED) neg += x > half[k] ? 1u : 0u;
-            mm::mac128(hi, lo, x, f[k]);
+            x[k] = X[((size_t)k << LOGN) + idx];
+            if (CENTERED) neg += x[k] > cc.half[k] ? 1u : 0u;
         }
-        if (CENTERED) mm::mac128(hi, lo, neg, negp);
-        sm[e] = mm::redc(hi, lo, q, qinv);
+#pragma unroll
+        for (int r = 0; r < RG; r++) {
+            if (r >= nr) break;
+            uint64_t hi = 0, lo = 0;
+#pragma unroll
+            for (int k = 0; k < NT; k++) mm::mac128(hi, lo, x[k], cc.f[r][k]);
+            if (CENTERED) mm::mac128(hi, lo, neg, cc.negp[r]);
+            tiles[r * TILE + e] = mm::redc(hi, lo, cc.q[r], cc.qinv[r]);
+        }
     }
 }
 
-// Fused ModUp strided pass: digit row (window blk, period row p = j * nre + t)
-// starts from sum_u y[blk][j*alpha+u] * Qhat_{j,u} mod prime(t), accumulated
-// as 128-bit products with the factor in Montgomery form and reduced once
-// (alpha * q_src * q_t < q_t * 2^64 because alpha <= 8 and q_src < 2^61).
-template <int LOGN, int CW>
+// Term counts above 4 (no parameter set here has them) share one loop.
+template <int LOGN, int CW, int RG, bool CENTERED>
+__device__ __forceinline__ void conv_load_any(uint64_t *tiles, int nr, const uint64_t *__restrict__ X, int nt,
+                                              int lo0, const ConvConsts<RG> &cc) {
+    using Gm = Geo<LOGN, CW>;
+    constexpr int TILE = Gm::H * Gm::COLS;
+    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) {
+        const size_t idx = (size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS);
+        uint64_t neg = 0;
+        if (CENTERED)
+            for (int k = 0; k < nt; k++) neg += X[((size_t)k << LOGN) + idx] > cc.half[k] ? 1u : 0u;
+        for (int r = 0; r < nr; r++) {
+            uint64_t hi = 0, lo = 0;
+            for (int k = 0; k < nt; k++) mm::mac128(hi, lo, X[((size_t)k << LOGN) + idx], cc.f[r][k]);
+            if (CENTERED) mm::mac128(hi, lo, neg, cc.negp[r]);
+            tiles[r * TILE + e] = mm::redc(hi, lo, cc.q[r], cc.qinv[r]);
+        }
+    }
+}
+
+template <int LOGN, int CW, int RG, bool CENTERED>
+__device__ __forceinline__ void conv_dispatch(uint64_t *tiles, int nr, const uint64_t *X, int nt, int lo0,
+                                              const ConvConsts<RG> &cc) {
+    switch (nt) {   // uniform per CTA: the term loop is unrolled for the common counts
+    case 1: conv_load<LOGN, CW, RG, 1, CENTERED>(tiles, nr, X, lo0, cc); break;
+    case 2: conv_load<LOGN, CW, RG, 2, CENTERED>(tiles, nr, X, lo0, cc); break;
+    case 3: conv_load<LOGN, CW, RG, 3, CENTERED>(tiles, nr, X, lo0, cc); break;
+    case 4: conv_load<LOGN, CW, RG, 4, CENTERED>(tiles, nr, X, lo0, cc); break;
+    default: conv_load_any<LOGN, CW, RG, CENTERED>(tiles, nr, X, nt, lo0, cc); break;
+    }
+}
+
+// Stages 0..S1-1 of every tile of the group, then the tiles' stores.
+template <int LOGN, int CW, int RG>
+__device__ __forceinline__ void cols_finish_group(uint64_t *tiles, int nr, const ConvConsts<RG> &cc, uint64_t *dst,
+                                                  const RowMap &md, const RowGroups &gr, uint32_t g, uint32_t blk,
+                                                  int lo0, const Twiddles &tw) {
+    using Gm = Geo<LOGN, CW>;
+    constexpr int TILE = Gm::H * Gm::COLS;
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < RG; r++) {
+        if (r >= nr) break;   // nr is uniform per CTA
+        cols_rounds<LOGN, true, CW>(tiles + r * TILE, cc.q[r], cc.pid[r], tw);
+    }
+    __syncthreads();
+    for (int r = 0; r < nr; r++) {
+        uint64_t *D = dst + row_at(md, blk, md.act[gr.start[g] + r], LOGN);
+        const uint64_t *T = tiles + r * TILE;
+        MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) D[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)] = T[e];
+    }
+}
+
+// Fused ModUp strided pass on a group of digit rows (window blk, period rows
+// p = j * nre + t of one digit j): each starts from
+// sum_u y[blk][j*alpha+u] * Qhat_{j,u} mod prime(t), 128-bit products with the
+// factor in Montgomery form reduced once (alpha * q_src * q_t < q_t * 2^64
+// because alpha <= 8 and q_src < 2^61).  Tiles in dynamic shared memory.
+template <int LOGN, int CW, int RG>
 __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::COLS_MINB)
     k_ntt_cols_modup(const uint64_t *__restrict__ y, int nl, int nre, int alpha, int j0, uint64_t *dst, RowMap md,
-                     const uint64_t *__restrict__ m_mont, ModTab mt, Twiddles tw) {
+                     RowGroups gr, const uint64_t *__restrict__ m_mont, ModTab mt, Twiddles tw) {
     using Gm = Geo<LOGN, CW>;
-    __shared__ uint64_t sm[Gm::H * Gm::COLS];
-    uint32_t blk, p;
-    row_decode(md, blockIdx.y, blk, p);
-    const uint32_t pid = md.pid[p];
-    const int j = j0 + (int)p / nre, t = (int)p % nre;
+    extern __shared__ uint64_t tiles[];
+    __shared__ ConvConsts<RG> cc;
+    const uint32_t blk = blockIdx.y / gr.n, g = blockIdx.y % gr.n;
+    const int nr = gr.count[g];
+    const int j = j0 + (int)md.act[gr.start[g]] / nre;
     const int i0 = j * alpha, cnt = min(alpha, nl - i0);
-    const uint64_t *Y = y + (((size_t)blk * nl + i0) << LOGN);
-    uint64_t *D = dst + row_at(md, blk, p, LOGN);
-    const int lo0 = blockIdx.x * Gm::COLS;
-    const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
-    const uint64_t *F = m_mont + (size_t)j * MAX_ALPHA * MAXROWMAP + t;
-    switch (cnt) {   // uniform per CTA: the term loop is unrolled for the digit's prime count
-    case 1: conv_load<LOGN, CW, 1>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
-    case 2: conv_load<LOGN, CW, 2>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
-    case 3: conv_load<LOGN, CW, 3>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
-    case 4: conv_load<LOGN, CW, 4>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
-    case 5: conv_load<LOGN, CW, 5>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
-    case 6: conv_load<LOGN, CW, 6>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
-    case 7: conv_load<LOGN, CW, 7>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
-    default: conv_load<LOGN, CW, 8>(sm, Y, F, MAXROWMAP, lo0, q, qinv); break;
+    if (threadIdx.x < nr) {
+        const int r = threadIdx.x;
+        const uint32_t p = md.act[gr.start[g] + r], pid = md.pid[p];
+        const int t = (int)p % nre;
+        cc.q[r] = mt.q[pid];
+        cc.qinv[r] = mt.qinv[pid];
+        cc.pid[r] = pid;
+        for (int u = 0; u < cnt; u++) cc.f[r][u] = m_mont[((size_t)j * MAX_ALPHA + u) * MAXROWMAP + t];
     }
     __syncthreads();
-    cols_rounds<LOGN, true, CW>(sm, q, pid, tw);
-    __syncthreads();
-    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) D[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)] = sm[e];
+    const uint64_t *Y = y + (((size_t)blk * nl + i0) << LOGN);
+    const int lo0 = blockIdx.x * Gm::COLS;
+    conv_dispatch<LOGN, CW, RG, false>(tiles, nr, Y, cnt, lo0, cc);
+    cols_finish_group<LOGN, CW, RG>(tiles, nr, cc, dst, md, gr, g, blk, lo0, tw);
 }
 
-// Fused ModDown strided pass: row (blk = window * 2 + h, p = i) starts from the
-// centered conversion v_i = sum_k z_k Phat_k + c (-P) mod q_i, c = #{k : z_k > p_k / 2},
-// in one Montgomery reduction (K (p_max - 1)(q - 1) + K (q - 1) < q 2^64 for K <= 8).
-template <int LOGN, int CW>
+// Fused ModDown strided pass on a group of rows (blk = window * 2 + h, p = i):
+// each starts from the centered conversion
+// v_i = sum_k z_k Phat_k + c (-P) mod q_i, c = #{k : z_k > p_k / 2}, in one
+// Montgomery reduction (K (p_max - 1)(q - 1) + K (q - 1) < q 2^64 for K <= 8).
+template <int LOGN, int CW, int RG>
 __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::COLS_MINB)
-    k_ntt_cols_moddown(const uint64_t *__restrict__ z, int K, int pid_p0, uint64_t *dst, RowMap md,
+    k_ntt_cols_moddown(const uint64_t *__restrict__ z, int K, int pid_p0, uint64_t *dst, RowMap md, RowGroups gr,
                        const uint64_t *__restrict__ phat_mont, const uint64_t *__restrict__ negp_mont, ModTab mt,
                        Twiddles tw) {
     using Gm = Geo<LOGN, CW>;
-    __shared__ uint64_t sm[Gm::H * Gm::COLS];
-    uint32_t blk, p;
-    row_decode(md, blockIdx.y, blk, p);
-    const uint32_t pid = md.pid[p];
-    const uint64_t *Z = z + (((size_t)blk * K) << LOGN);
-    uint64_t *D = dst + row_at(md, blk, p, LOGN);
-    const int lo0 = blockIdx.x * Gm::COLS;
-    const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
-    const uint64_t *F = phat_mont + pid;
-    const uint64_t np = negp_mont[pid];
-    const uint64_t *Hp = mt.q + pid_p0;
-    switch (K) {   // uniform: the term loop is unrolled for the number of special primes
-    case 1: conv_load<LOGN, CW, 1, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
-    case 2: conv_load<LOGN, CW, 2, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
-    case 3: conv_load<LOGN, CW, 3, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
-    case 4: conv_load<LOGN, CW, 4, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
-    case 5: conv_load<LOGN, CW, 5, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
-    case 6: conv_load<LOGN, CW, 6, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
-    case 7: conv_load<LOGN, CW, 7, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
-    default: conv_load<LOGN, CW, 8, true>(sm, Z, F, MMFHE_MAX_Q, lo0, q, qinv, Hp, np); break;
+    extern __shared__ uint64_t tiles[];
+    __shared__ ConvConsts<RG> cc;
+    const uint32_t blk = blockIdx.y / gr.n, g = blockIdx.y % gr.n;
+    const int nr = gr.count[g];
+    if (threadIdx.x < nr) {
+        const int r = threadIdx.x;
+        const uint32_t pid = md.pid[md.act[gr.start[g] + r]];
+        cc.q[r] = mt.q[pid];
+        cc.qinv[r] = mt.qinv[pid];
+        cc.pid[r] = pid;
+        cc.negp[r] = negp_mont[pid];
+        for (int k = 0; k < K; k++) cc.f[r][k] = phat_mont[(size_t)k * MMFHE_MAX_Q + pid];
     }
+    if (threadIdx.x < K) cc.half[threadIdx.x] = mt.q[pid_p0 + threadIdx.x] >> 1;
     __syncthreads();
-    cols_rounds<LOGN, true, CW>(sm, q, pid, tw);
-    __syncthreads();
-    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) D[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)] = sm[e];
+    const uint64_t *Z = z + (((size_t)blk * K) << LOGN);
+    const int lo0 = blockIdx.x * Gm::COLS;
+    conv_dispatch<LOGN, CW, RG, true>(tiles, nr, Z, K, lo0, cc);
+    cols_finish_group<LOGN, CW, RG>(tiles, nr, cc, dst, md, gr, g, blk, lo0, tw);
 }
 
 // Fused ModDown contiguous pass: forward stages on v (rows blk = window * 2 + h,
@@ -439,34 +493,71 @@ void ntt_launch_t(Context &c, const uint64_t *sb, RowMap ms, uint64_t *db, RowMa
     }
 }
 
-template <int LOGN, int CW>
-void modup_cols_pass(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, size_t nr, int nl, int nre,
-                     int j0, const uint64_t *m_mont, double bytes, cudaStream_t st) {
+// Dynamic shared memory of a group's tiles (opted in above 48 KB once per kernel).
+template <typename Kern>
+void smem_opt_in(Kern k, size_t bytes) {
+    if (bytes > 48 * 1024) CK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+template <int LOGN, int CW, int RG>
+void modup_cols_pass(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, const RowGroups &gr,
+                     size_t nblk, int nl, int nre, int j0, const uint64_t *m_mont, double bytes, size_t nr,
+                     cudaStream_t st) {
     using Gm = Geo<LOGN, CW>;
-    dim3 g(Gm::T1 / Gm::COLS, (unsigned)nr), b(Gm::COLS_THREADS);
+    const size_t smem = (size_t)RG * Gm::H * Gm::COLS * 8;
+    static bool opted = false;
+    if (!opted) {
+        smem_opt_in(k_ntt_cols_modup<LOGN, CW, RG>, smem);
+        opted = true;
+    }
+    dim3 g(Gm::T1 / Gm::COLS, (unsigned)(nblk * gr.n)), b(Gm::COLS_THREADS);
     kernel_begin(c, st);
-    k_ntt_cols_modup<LOGN, CW><<<g, b, 0, st>>>(y, nl, nre, c.alpha, j0, digits, md, m_mont, c.mods, c.tw);
+    k_ntt_cols_modup<LOGN, CW, RG><<<g, b, smem, st>>>(y, nl, nre, c.alpha, j0, digits, md, gr, m_mont, c.mods, c.tw);
     kernel_end(c, "ntt_modup_cols", g, b, bytes, st, bf_cols<LOGN>(nr));
 }
 
+template <int LOGN, int CW>
+void modup_cols_rg(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, const RowGroups &gr, size_t nblk,
+                   int nl, int nre, int j0, const uint64_t *m_mont, double bytes, size_t nr, cudaStream_t st) {
+    if (c.tune.conv_rows == 4) modup_cols_pass<LOGN, CW, 4>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes, nr, st);
+    else if (c.tune.conv_rows == 2) modup_cols_pass<LOGN, CW, 2>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes, nr, st);
+    else modup_cols_pass<LOGN, CW, 1>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes, nr, st);
+}
+
 template <int LOGN>
-void modup_launch_t(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, size_t nr, int nl, int nre,
-                    int j0, const uint64_t *m_mont, double bytes_cols, double bytes_rows, cudaStream_t st) {
-    if (c.tune.cols_w == 8) modup_cols_pass<LOGN, 8>(c, digits, y, md, nr, nl, nre, j0, m_mont, bytes_cols, st);
-    else modup_cols_pass<LOGN, 16>(c, digits, y, md, nr, nl, nre, j0, m_mont, bytes_cols, st);
+void modup_launch_t(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, const RowGroups &gr,
+                    size_t nblk, int nl, int nre, int j0, const uint64_t *m_mont, double bytes_cols, double bytes_rows,
+                    cudaStream_t st) {
+    const size_t nr = nblk * md.nact;
+    if (c.tune.cols_w == 8) modup_cols_rg<LOGN, 8>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes_cols, nr, st);
+    else modup_cols_rg<LOGN, 16>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes_cols, nr, st);
     if (c.tune.rows_t == 128) rows_pass<LOGN, 128, true>(c, digits, md, digits, md, nr, bytes_rows, st);
     else rows_pass<LOGN, 256, true>(c, digits, md, digits, md, nr, bytes_rows, st);
 }
 
-template <int LOGN, int CW>
-void moddown_cols_pass(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, size_t nr, double bytes,
-                       cudaStream_t st) {
+template <int LOGN, int CW, int RG>
+void moddown_cols_pass(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr,
+                       size_t nblk, double bytes, size_t nr, cudaStream_t st) {
     using Gm = Geo<LOGN, CW>;
-    dim3 g(Gm::T1 / Gm::COLS, (unsigned)nr), b(Gm::COLS_THREADS);
+    const size_t smem = (size_t)RG * Gm::H * Gm::COLS * 8;
+    static bool opted = false;
+    if (!opted) {
+        smem_opt_in(k_ntt_cols_moddown<LOGN, CW, RG>, smem);
+        opted = true;
+    }
+    dim3 g(Gm::T1 / Gm::COLS, (unsigned)(nblk * gr.n)), b(Gm::COLS_THREADS);
     kernel_begin(c, st);
-    k_ntt_cols_moddown<LOGN, CW><<<g, b, 0, st>>>(z, c.num_p, c.num_q, vtmp, mv, c.d_dn_phat_mont, c.d_dn_negp_mont,
-                                                  c.mods, c.tw);
+    k_ntt_cols_moddown<LOGN, CW, RG><<<g, b, smem, st>>>(z, c.num_p, c.num_q, vtmp, mv, gr, c.d_dn_phat_mont,
+                                                         c.d_dn_negp_mont, c.mods, c.tw);
     kernel_end(c, "ntt_moddown_cols", g, b, bytes, st, bf_cols<LOGN>(nr));
+}
+
+template <int LOGN, int CW>
+void moddown_cols_rg(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr, size_t nblk,
+                     double bytes, size_t nr, cudaStream_t st) {
+    if (c.tune.conv_rows == 4) moddown_cols_pass<LOGN, CW, 4>(c, vtmp, z, mv, gr, nblk, bytes, nr, st);
+    else if (c.tune.conv_rows == 2) moddown_cols_pass<LOGN, CW, 2>(c, vtmp, z, mv, gr, nblk, bytes, nr, st);
+    else moddown_cols_pass<LOGN, CW, 1>(c, vtmp, z, mv, gr, nblk, bytes, nr, st);
 }
 
 template <int LOGN, int RT>
@@ -480,10 +571,12 @@ void combine_rows_pass(Context &c, uint64_t *vtmp, const RowMap &mv, size_t nr, 
 }
 
 template <int LOGN>
-void moddown_launch_t(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, size_t nr,
-                      const CombineArgs &a, int nre, double bytes_cols, double bytes_rows, cudaStream_t st) {
-    if (c.tune.cols_w == 8) moddown_cols_pass<LOGN, 8>(c, vtmp, z, mv, nr, bytes_cols, st);
-    else moddown_cols_pass<LOGN, 16>(c, vtmp, z, mv, nr, bytes_cols, st);
+void moddown_launch_t(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr,
+                      size_t nblk, const CombineArgs &a, int nre, double bytes_cols, double bytes_rows,
+                      cudaStream_t st) {
+    const size_t nr = nblk * mv.nact;
+    if (c.tune.cols_w == 8) moddown_cols_rg<LOGN, 8>(c, vtmp, z, mv, gr, nblk, bytes_cols, nr, st);
+    else moddown_cols_rg<LOGN, 16>(c, vtmp, z, mv, gr, nblk, bytes_cols, nr, st);
     if (c.tune.rows_t == 128) combine_rows_pass<LOGN, 128>(c, vtmp, mv, nr, a, nre, bytes_rows, st);
     else combine_rows_pass<LOGN, 256>(c, vtmp, mv, nr, a, nre, bytes_rows, st);
 }

@@ -95,6 +95,33 @@ void autotune(Context &c, int batch, int level) {
                 best.keyip_wg = wgs[i];
             }
         }
+        dg.release();
+        own.release();
+        key.release();
+        // fused ModUp + ModDown passes: converted rows per CTA (uses the tiles picked above)
+        c.tune.cols_w = best.cols_w;
+        c.tune.rows_t = best.rows_t;
+        Buf y(c.pool.get(), (size_t)batch * nl * c.n), dig(c.pool.get(), (size_t)batch * beta * nre * c.n);
+        Buf z(c.pool.get(), (size_t)batch * 2 * c.num_p * c.n), v(c.pool.get(), (size_t)batch * 2 * nl * c.n);
+        Buf out(c.pool.get(), (size_t)batch * 2 * nl * c.n);
+        CK(cudaMemsetAsync(y.get(), 0, y.words() * 8, st));
+        CK(cudaMemsetAsync(z.get(), 0, z.words() * 8, st));
+        CK(cudaMemsetAsync(u.get(), 0, u.words() * 8, st));
+        const CombineArgs ca{out.get(), u.get(), nullptr, nullptr, 0, 1, nullptr};
+        const int rgs[3] = {1, 2, 4};
+        float bg = 1e30f;
+        for (int i = 0; i < 3; i++) {
+            c.tune.conv_rows = rgs[i];
+            const float ms = time_best(st, [&] {
+                launch_modup_ntt(c, dig.get(), y.get(), batch, level, st);
+                launch_moddown_ntt(c, v.get(), z.get(), ca, batch, level, st);
+            });
+            best.conv_ms[i] = ms;
+            if (ms < bg) {
+                bg = ms;
+                best.conv_rows = rgs[i];
+            }
+        }
         CK(cudaStreamSynchronize(st));
     } catch (...) {
         cudaStreamDestroy(st);
@@ -125,6 +152,8 @@ void to_abi(const Tune &t, mmfhe_tuning *out) {
     out->keyip_windows = (uint32_t)t.keyip_wg;
     std::copy(t.ntt_ms, t.ntt_ms + 4, out->ntt_ms);
     std::copy(t.keyip_ms, t.keyip_ms + 4, out->keyip_ms);
+    out->conv_rows = (uint32_t)t.conv_rows;
+    std::copy(t.conv_ms, t.conv_ms + 3, out->conv_ms);
 }
 
 }  // namespace
@@ -156,9 +185,11 @@ mmfhe_status mmfhe_tuning_get(const mmfhe_ctx *ctx, mmfhe_tuning *out) {
 mmfhe_status mmfhe_tuning_set(mmfhe_ctx *ctx, const mmfhe_tuning *in) {
     if (!ctx || !ctx->c || !in) return tfail(nullptr, MMFHE_ERR_BAD_ARG, "null argument");
     Context *c = ctx->c;
-    const uint32_t w = in->ntt_cols_width, r = in->ntt_rows_threads, k = in->keyip_windows;
-    if ((w != 8 && w != 16) || (r != 128 && r != 256) || (k != 1 && k != 2 && k != 4 && k != 8))
+    const uint32_t w = in->ntt_cols_width, r = in->ntt_rows_threads, k = in->keyip_windows, g = in->conv_rows;
+    if ((w != 8 && w != 16) || (r != 128 && r != 256) || (k != 1 && k != 2 && k != 4 && k != 8) ||
+        (g != 1 && g != 2 && g != 4))
         return tfail(c, MMFHE_ERR_BAD_ARG, "unsupported tile shape");
+    c->tune.conv_rows = (int)g;
     c->tune.cols_w = (int)w;
     c->tune.rows_t = (int)r;
     c->tune.keyip_wg = (int)k;

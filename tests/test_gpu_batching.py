@@ -137,8 +137,9 @@ def test_batcher_plan_budget_evicts(gsmall):
 def test_every_tile_variant_gives_the_same_words(gsmall):
     """The autotuner only picks among variants that compute identical words:
     the FIR + DFT circuit (NTTs, fused ModUp / ModDown, key inner products of
-    relinearisations and rotations) under every tile shape equals the
-    default-shape result, which the parity tests pin to the oracle."""
+    relinearisations and rotations) under every tile shape and conversion
+    row grouping equals the default-shape result, which the parity tests pin
+    to the oracle."""
     import paper_2603_22437_b300 as M
     P, ctx, keys = gsmall["P"], gsmall["ctx"], gsmall["keys"]
     plan = ctx.plan(M.fir_dft_config(bins=40))
@@ -150,16 +151,17 @@ def test_every_tile_variant_gives_the_same_words(gsmall):
     ctx.eval(plan, keys, xs, ref)
     for cw in (8, 16):
         for rt in (128, 256):
-            for wg in (1, 2, 8):
-                ctx.set_tuning(cw, rt, wg)
+            for wg, rg in ((1, 4), (2, 2), (8, 1), (4, 4)):
+                ctx.set_tuning(cw, rt, wg, rg)
                 outs = [np.empty_like(r) for r in ref]
                 ctx.eval(plan, keys, xs, outs)
                 for w in range(3):
-                    assert np.array_equal(outs[w], ref[w]), (cw, rt, wg, w)
+                    assert np.array_equal(outs[w], ref[w]), (cw, rt, wg, rg, w)
     with pytest.raises(M.MmfheError):
         ctx.set_tuning(32, 256, 4)
     t = ctx.autotune(3)
     assert t["ntt_cols_width"] in (8, 16) and t["ntt_rows_threads"] in (128, 256)
     assert t["keyip_windows"] in (1, 2, 4, 8)
     assert min(t["ntt_ms"]) > 0 and min(t["keyip_ms"]) > 0
-    ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"])
+    assert t["conv_rows"] in (1, 2, 4) and min(t["conv_ms"]) > 0
+    ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"], saved["conv_rows"])
