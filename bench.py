@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--key-budget-gib", type=float, default=48.0, help="serving workload: resident key budget")
     ap.add_argument("--windows", type=int, default=64, help="batching workload: windows per step")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--tiles", default=None,
+                    help="cols_width,rows_threads,keyip_windows,conv_rows: set the tile shapes instead of autotuning")
     return ap.parse_args()
 
 
@@ -285,6 +287,14 @@ def ncu_traffic(kernel):
     return None if k is None else k.get("dram_bytes_per_launch_full_size")
 
 
+def pick_tiles(ctx, args, batch):
+    """Tile shapes: given (--tiles), defaults (--no-autotune) or autotuned."""
+    if args.tiles:
+        ctx.set_tuning(*[int(v) for v in args.tiles.split(",")])
+        return ctx.tuning()
+    return ctx.tuning() if args.no_autotune else ctx.autotune(batch)
+
+
 def roofline_of(prof, bf64_peak, bf32_peak):
     """Roofline of the dominant kernel (most event time in the profiled step).
 
@@ -347,7 +357,7 @@ def run_mine(args, rank, world, local):
         keys.set_galois(k, key_words())
     n_in, n_out, out_levels = plan.io()
     B = args.batch
-    tiles = ctx.tuning() if args.no_autotune else ctx.autotune(B)
+    tiles = pick_tiles(ctx, args, B)
     in_words = n_in * 2 * len(P_q) * n
     out_words = sum(2 * (l + 1) * n for l in out_levels)
     # device-resident inputs: B windows of uniform ciphertexts
@@ -466,7 +476,7 @@ def run_batching(args, rank, world, local):
     keys.set_relin(key_words())
     for k in rots:
         keys.set_galois(k, key_words())
-    tiles = ctx.tuning() if args.no_autotune else ctx.autotune(args.batch)
+    tiles = pick_tiles(ctx, args, args.batch)
     out_words = {F: sum(2 * (l + 1) * n for l in io[F][2]) for F in io}
     d_in = [torch.from_numpy(synth.uniform_ciphertexts(7000 + w, params.primes_q, n, io[F][0]).reshape(-1)
                              .view(np.int64)).to(dev) for w, F in enumerate(frames)]
