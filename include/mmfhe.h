@@ -403,6 +403,7 @@ typedef struct mmfhe_server_config {
     uint32_t max_batch;           /* windows per batch, 1..256 */
     uint32_t streams;             /* concurrent batches, 1..8 */
     uint64_t key_budget_bytes;    /* device bytes of resident key sets; 0: no limit */
+    uint32_t batch_wait_us;       /* a free slot waits up to this long for a batch to fill (0: dispatch at once) */
 } mmfhe_server_config;
 typedef struct mmfhe_server_stats {
     uint64_t submitted, completed, failed;

@@ -341,9 +341,9 @@ class Server:
     """Serving loop: submit windows of registered users from any thread; a
     native worker batches and runs them (see mmfhe_server_* in mmfhe.h)."""
 
-    def __init__(self, ctx, base_cfg, max_batch=16, streams=2, key_budget_bytes=0):
+    def __init__(self, ctx, base_cfg, max_batch=16, streams=2, key_budget_bytes=0, batch_wait_us=0):
         self.ctx = ctx
-        cfg = ServerConfig(max_batch, streams, key_budget_bytes)
+        cfg = ServerConfig(max_batch, streams, key_budget_bytes, batch_wait_us)
         h = ctypes.c_void_p()
         ctx._c(_lib.lib().mmfhe_server_create(ctx.h, ctypes.byref(base_cfg), ctypes.sizeof(CircuitConfig),
                                                ctypes.byref(cfg), ctypes.byref(h)))

@@ -75,7 +75,8 @@ class BatcherStats(ctypes.Structure):
 
 
 class ServerConfig(ctypes.Structure):
-    _fields_ = [("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32), ("key_budget_bytes", ctypes.c_uint64)]
+    _fields_ = [("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32), ("key_budget_bytes", ctypes.c_uint64),
+                ("batch_wait_us", ctypes.c_uint32)]
 
 
 class ServerStats(ctypes.Structure):

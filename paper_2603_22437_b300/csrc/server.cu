@@ -165,6 +165,20 @@ struct mmfhe_server {
         cv_done.notify_all();
     }
 
+    // True when a batch should go now: max_batch windows of the oldest
+    // window's frame count are queued, or the oldest has waited batch_wait_us.
+    bool batch_ready() {
+        std::lock_guard<std::mutex> g(mu);
+        if (queue.empty()) return false;
+        if (cfg.batch_wait_us == 0 || stop) return true;
+        const Req &first = reqs[queue.front()];
+        if (Clock::now() - first.t_submit >= std::chrono::microseconds(cfg.batch_wait_us)) return true;
+        uint32_t n = 0;
+        for (uint64_t t : queue)
+            if (reqs[t].frames == first.frames && ++n >= cfg.max_batch) return true;
+        return false;
+    }
+
     // Take queued windows of the oldest window's frame count, up to
     // max_batch: the oldest window first, then windows whose users' keys are
     // resident, then the others, in queue order, as long as the distinct
@@ -280,7 +294,7 @@ struct mmfhe_server {
                 std::vector<uint64_t> tickets;
                 uint32_t frames = 0;
                 std::vector<User *> bu, wu;
-                if (take_batch(tickets, frames, bu, wu)) {
+                if (batch_ready() && take_batch(tickets, frames, bu, wu)) {
                     try {
                         // windows whose user lacks a key the plan needs fail alone
                         const Plan &p = plan_for(frames);
@@ -338,8 +352,8 @@ struct mmfhe_server {
             for (Slot &s : slots) busy |= s.busy;
             std::unique_lock<std::mutex> lk(mu);
             if (stop && queue.empty() && !busy) break;
-            // idle: sleep until a submission; running: poll the slots' events
-            if (busy)
+            // running or filling a batch: poll; idle: sleep until a submission
+            if (busy || !queue.empty())
                 cv_work.wait_for(lk, std::chrono::microseconds(50));
             else
                 cv_work.wait_for(lk, std::chrono::milliseconds(20), [this] { return stop || !queue.empty(); });
