@@ -727,3 +727,88 @@ class VitalCircuit:
             outs.append(ev.rotsum(nb, lay.r_c, self.span(b)))
             outs.append(ev.rotsum(db, lay.r_c, self.span(b)))
         return outs
+
+
+# ---------------------------------------------------------------------------
+# Polynomial network: the paper's FC network with square activations
+# (Sec. "Cloud-Side Algorithms", fully connected layers with a square
+# activation; the weights are learned).  Every layer is a dense map on a slot
+# period of D = width slots; slot D - 1 of every period holds the constant 1,
+# so the biases are the last column of each D x D matrix and row D - 1 keeps
+# the constant (W[D-1][D-1] = 1).  A square follows every layer but the last.
+# ---------------------------------------------------------------------------
+@dataclass
+class FcConfig:
+    dims: tuple = (120, 32, 16, 6)   # d_0 (inputs), d_1, ..., d_L (outputs)
+    width: int = 128                 # D, a power of two above every d_l
+
+
+class FcCircuit:
+    def __init__(self, P, cfg=FcConfig()):
+        D = cfg.width
+        assert D & (D - 1) == 0 and max(cfg.dims) < D <= P.slots
+        self.P, self.cfg, self.D = P, cfg, D
+        self.layers = len(cfg.dims) - 1
+        self.n1, self.n2 = bsgs_split(D)
+        # input level of layer l: a dense layer and a square take one level each
+        self.levels = [P.L - 2 * l for l in range(self.layers)]
+        assert self.levels[-1] >= 1, "not enough levels for the network"
+
+    def present(self, l):
+        """Structurally non-zero diagonals of layer l: rows d_{l+1} and the
+        constant row, columns d_l and the constant column."""
+        D = self.D
+        rows = list(range(self.cfg.dims[l + 1])) + [D - 1]
+        cols = list(range(self.cfg.dims[l])) + [D - 1]
+        return sorted({(j - i) % D for i in rows for j in cols})
+
+    def diagonal(self, W, k):
+        """diag_k[j] = W[j mod D][(j mod D + k) mod D] over all slots."""
+        D = self.D
+        i = np.arange(self.P.slots) % D
+        return np.asarray(W, dtype=np.float64)[i, (i + k) % D]
+
+    def constants(self, mats):
+        P, out = self.P, {}
+        for l in range(self.layers):
+            lv = self.levels[l]
+            for k in self.present(l):
+                v = prerotate(self.diagonal(mats[l], k), k // self.n1, self.n1, 1)
+                out[("fcw", l, k)] = ck.encode(P, v, P.q[lv], lv)
+        return out
+
+    def rotations(self):
+        ks = set(range(1, self.n1)) | {g * self.n1 for g in range(1, self.n2)}
+        return sorted(ks)
+
+    def run(self, ev, consts, x):
+        for l in range(self.layers):
+            babies = {"x": ev.hoisted(x, list(range(self.n1)))}
+            cl = {("x", k): consts[("fcw", l, k)] for k in self.present(l)}
+            y = ev.rescale(ev.bsgs(babies, cl, self.n1, 1, x.level))
+            if l < self.layers - 1:
+                y = ev.rescale(ev.square_sum([y]))
+            x = y
+        return x
+
+
+def fc_pack(x, D, slots):
+    """Input slot vector: features in slots 0..d_0-1, the constant 1 in slot
+    D - 1, repeated with period D."""
+    v = np.zeros(D)
+    v[: len(x)] = x
+    v[D - 1] = 1.0
+    return np.tile(v, slots // D)
+
+
+def fc_forward(mats, x, D):
+    """FP64 forward pass of the same network on one period."""
+    v = np.zeros(D)
+    v[: len(x)] = x
+    v[D - 1] = 1.0
+    for l, W in enumerate(mats):
+        v = np.asarray(W, dtype=np.float64) @ v
+        if l < len(mats) - 1:
+            v = v * v
+    return v
+

@@ -176,3 +176,11 @@ def vital_params():
     """Vital-sign chain: N = 2^15, depth 11 (12 Q primes: 60 + 11 x 40 bits),
     four 60-bit special primes, dnum = 3 (alpha = 4); log QP ~ 740 <= 881."""
     return make_params(15, 12, 60, 40, 4, 60, 3, 40)
+
+
+def fc_params():
+    """Polynomial-network instance (encrypted FC network of depth 5: three
+    dense layers and two squares): N = 2^14, q_0 ~ 2^60 and five ~2^40
+    primes, two 60-bit special primes, dnum = 3 (alpha = 2);
+    log QP ~ 380 <= 438 (HE Standard, N = 2^14, 128-bit classical)."""
+    return make_params(14, 6, 60, 40, 2, 60, 3, 40)
