@@ -233,6 +233,7 @@ mmfhe_status mmfhe_ct_bsgs(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out
  * ---------------------------------------------------------------------- */
 #define MMFHE_CIRCUIT_FIR_DFT 1 /* 64-tap bandpass FIR + windowed fftshifted DFT on every bin */
 #define MMFHE_CIRCUIT_VITAL 2   /* vital-sign chain K1->K2 | K4->K5->K7->K3->|X|^2->sharpen->avg */
+#define MMFHE_CIRCUIT_FC 3      /* polynomial network: dense layers with a square after each but the last */
 
 typedef struct mmfhe_circuit_config {
     uint32_t kind;             /* MMFHE_CIRCUIT_* */
@@ -246,6 +247,14 @@ typedef struct mmfhe_circuit_config {
     uint32_t band_hi_mhz[2];
     double dft_gain[2];        /* VITAL: public per-band DFT gains (both 0: defaults
                                   30, 1 for third order; 1.5, 0.2 for first order) */
+    /* FC (the paper's fully connected network with square activations):
+     * bins = D, the slot period of every layer (a power of two), taps = the
+     * number of layers L (1..8), fc_dims[0..L] = the widths d_0 (inputs) ..
+     * d_L (outputs), all below D.  Slot D-1 of every period holds the
+     * constant 1 (biases = column D-1; row D-1 keeps the constant).  Input:
+     * one ciphertext at the top level holding the inputs in slots 0..d_0-1
+     * and 1 in slot D-1 of every period; output at level top - 2L + 1. */
+    uint32_t fc_dims[9];
 } mmfhe_circuit_config;
 
 /* Constant tags of mmfhe_const_key.tag */
@@ -259,6 +268,7 @@ typedef struct mmfhe_circuit_config {
 #define MMFHE_CONST_DFT_C 8  /* FIR_DFT: C = Re W diagonal `index` */
 #define MMFHE_CONST_DFT_S 9  /* FIR_DFT: S = Im W */
 #define MMFHE_CONST_DFT_MS 10 /* FIR_DFT: -S */
+#define MMFHE_CONST_FCW 11   /* FC: diagonal `index` of layer `band` (pre-rotated) */
 
 typedef struct mmfhe_const_key {
     uint32_t tag, band, index, level;
@@ -277,6 +287,11 @@ mmfhe_status mmfhe_plan_get_const(const mmfhe_plan *plan, uint32_t i, uint64_t *
 /* Design and encode every constant with the library's own FP64 design
  * (Hamming-windowed-sinc taps, Hann-windowed DFT rows) and encoder. */
 mmfhe_status mmfhe_plan_encode_consts(mmfhe_plan *plan);
+/* FC plans: encode layer `layer` from its D x D matrix W (row-major,
+ * y = W v on every period; only the structurally present diagonals are
+ * stored).  The constants of an FC plan are learned, so
+ * mmfhe_plan_encode_consts returns BAD_ARG for it. */
+mmfhe_status mmfhe_plan_set_fc_layer(mmfhe_plan *plan, uint32_t layer, const double *W);
 /* Rotation amounts whose Galois keys the plan needs (ascending, in [0, N/2)). */
 mmfhe_status mmfhe_plan_rotations(const mmfhe_plan *plan, int32_t *out, uint32_t capacity, uint32_t *count);
 /* Input/output shape: ciphertexts per window in and out, and the level of
@@ -324,6 +339,27 @@ mmfhe_status mmfhe_autotune(mmfhe_ctx *ctx, uint32_t batch, uint32_t level, mmfh
 mmfhe_status mmfhe_tuning_get(const mmfhe_ctx *ctx, mmfhe_tuning *out);
 /* Set the variants explicitly (timings ignored); BAD_ARG for other values. */
 mmfhe_status mmfhe_tuning_set(mmfhe_ctx *ctx, const mmfhe_tuning *in);
+
+/* ------------------------------------------------------------------------
+ * Polynomial network training (plaintext, FP32, on the GPU; no counterpart
+ * in the paper beyond its learned FC weights).  Trains z_l = W_l [a_{l-1}; 1],
+ * a_l = z_l + alpha z_l^2 after every layer but the last, softmax
+ * cross-entropy, momentum SGD (0.9) on mini-batches of `batch` rows, inputs
+ * standardised (folded back, so the weights act on raw inputs).  X: host
+ * float [n][dims[0]]; labels: host int32 in [0, dims[layers]); weights out:
+ * host float, W_0 [d_1][d_0 + 1], W_1 [d_2][d_1 + 1], ... back to back (last
+ * column = bias).  *train_accuracy (nullable): argmax accuracy on X. */
+mmfhe_status mmfhe_train_poly_net(mmfhe_ctx *ctx, const float *X, const int32_t *labels, uint64_t n,
+                                  const uint32_t *dims, uint32_t layers, float alpha, uint32_t epochs,
+                                  uint32_t batch, float lr, uint64_t seed, float *weights, float *train_accuracy);
+/* Host only.  The same network with pure squares (the form of
+ * MMFHE_CIRCUIT_FC): z + alpha z^2 = alpha (z + 1/(2 alpha))^2 - 1/(4 alpha),
+ * the shift folded into each hidden layer's bias and alpha, -1/(4 alpha) into
+ * the next layer.  mats out: layers x width x width doubles, row-major, bias
+ * in column width-1, mats[l][width-1][width-1] = 1.  BAD_ARG if a width is
+ * not below `width` or `width` is not a power of two. */
+mmfhe_status mmfhe_fold_poly_net(const uint32_t *dims, uint32_t layers, float alpha, const float *weights,
+                                 uint32_t width, double *mats);
 
 /* ------------------------------------------------------------------------
  * Batching runtime.  The paper evaluates windows one call at a time (its

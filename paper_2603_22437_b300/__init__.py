@@ -11,12 +11,12 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CONST_TAGS, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
+from ._lib import (CIRCUIT_FC, CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CONST_TAGS, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
                    MmfheError, Params, ServerConfig, ServerStats, Tuning, check, ptr, ptr_array, stream_ptr)
 
 __all__ = ["Context", "Keys", "Plan", "Graph", "Batcher", "Server", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
-           "Params", "CIRCUIT_FIR_DFT", "CIRCUIT_VITAL", "vital_config", "fir_dft_config", "fir_dft_params",
-           "vital_params"]
+           "Params", "CIRCUIT_FIR_DFT", "CIRCUIT_VITAL", "CIRCUIT_FC", "vital_config", "fir_dft_config",
+           "fc_config", "fir_dft_params", "vital_params", "fc_params", "fold_poly_net"]
 
 
 def params_select(log_n, num_q, q0_bits, q_bits, num_p, p_bits, dnum):
@@ -77,6 +77,32 @@ def vital_config(bins=256, frames=200, fs_mhz=20000, taps=64, taylor_order=3,
         c.band_lo_mhz[b], c.band_hi_mhz[b] = bands_mhz[b]
         c.dft_gain[b] = dft_gains[b]
     return c
+
+
+def fc_params():
+    """N = 2^14, q_0 ~ 2^60 + 5 x 2^40, two 60-bit special primes, dnum = 3:
+    depth 5, enough for three dense layers and two squares."""
+    return params_select(14, 6, 60, 40, 2, 60, 3)
+
+
+def fc_config(dims=(120, 32, 16, 6), width=128):
+    """Polynomial network: dense layers d_0 -> ... -> d_L on a slot period of
+    `width` (slot width-1 holds the constant 1), square after each but the last."""
+    c = CircuitConfig()
+    c.kind, c.bins, c.taps = CIRCUIT_FC, width, len(dims) - 1
+    for i, d in enumerate(dims):
+        c.fc_dims[i] = d
+    return c
+
+
+def fold_poly_net(dims, alpha, weights, width=128):
+    """Trained quadratic-activation weights -> the pure-square D x D layer
+    matrices of an FC plan (host only)."""
+    d = (ctypes.c_uint32 * len(dims))(*dims)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    mats = np.empty((len(dims) - 1, width, width), dtype=np.float64)
+    check(_lib.lib().mmfhe_fold_poly_net(d, len(dims) - 1, float(alpha), ptr(w), width, ptr(mats)))
+    return mats
 
 
 def fir_dft_config(bins=64, frames=200, fs_mhz=20000, taps=64, band_mhz=(800, 2500)):
@@ -153,6 +179,19 @@ class Context:
 
     def keys(self, user_id=0):
         return Keys(self, user_id)
+
+    def train_poly_net(self, X, labels, dims, alpha=0.1, epochs=30, batch=128, lr=0.05, seed=1):
+        """Plaintext GPU training of the quadratic-activation network.
+        Returns (flat float32 weights, training accuracy)."""
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        y = np.ascontiguousarray(labels, dtype=np.int32)
+        d = (ctypes.c_uint32 * len(dims))(*dims)
+        nw = sum(dims[l + 1] * (dims[l] + 1) for l in range(len(dims) - 1))
+        w = np.empty(nw, dtype=np.float32)
+        acc = ctypes.c_float()
+        self._c(_lib.lib().mmfhe_train_poly_net(self.h, ptr(X), ptr(y), len(y), d, len(dims) - 1, float(alpha), epochs,
+                                                 batch, float(lr), seed, ptr(w), ctypes.byref(acc)))
+        return w, acc.value
 
     def autotune(self, batch, level=None):
         """Time the NTT / key-inner-product tile variants on `batch`
@@ -456,6 +495,11 @@ class Plan:
 
     def encode_consts(self):
         self.ctx._c(_lib.lib().mmfhe_plan_encode_consts(self.h))
+
+    def set_fc_layer(self, layer, W):
+        """FC plans: encode a layer from its D x D matrix."""
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        self.ctx._c(_lib.lib().mmfhe_plan_set_fc_layer(self.h, layer, ptr(W)))
 
     def rotations(self):
         n = ctypes.c_uint32()

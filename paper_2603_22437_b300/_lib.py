@@ -20,9 +20,9 @@ ERRORS = {
     -1: "BAD_ARG", -2: "BAD_BLOB", -3: "PARAM_MISMATCH", -4: "LEVEL_MISMATCH", -5: "OUT_OF_MEMORY",
     -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "BUSY",
 }
-CIRCUIT_FIR_DFT, CIRCUIT_VITAL = 1, 2
+CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_FC = 1, 2, 3
 CONST_TAGS = {1: "idx", 2: "one", 3: "fir", 4: "dre", 5: "dim", 6: "fw", 7: "fone", 8: "dft_c", 9: "dft_s",
-              10: "dft_ms"}
+              10: "dft_ms", 11: "fcw"}
 
 
 class MmfheError(RuntimeError):
@@ -49,7 +49,7 @@ class CircuitConfig(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("bins", ctypes.c_uint32), ("frames", ctypes.c_uint32),
                 ("fs_mhz", ctypes.c_uint32), ("taps", ctypes.c_uint32), ("taylor_order", ctypes.c_uint32),
                 ("num_bands", ctypes.c_uint32), ("band_lo_mhz", ctypes.c_uint32 * 2),
-                ("band_hi_mhz", ctypes.c_uint32 * 2), ("dft_gain", ctypes.c_double * 2)]
+                ("band_hi_mhz", ctypes.c_uint32 * 2), ("dft_gain", ctypes.c_double * 2), ("fc_dims", ctypes.c_uint32 * 9)]
 
 
 class KernelStat(ctypes.Structure):
@@ -105,6 +105,10 @@ _SIGS = {
     "mmfhe_profile_enable": [_VP, _INT],
     "mmfhe_profile_get": [_VP, _VP, _U32, ctypes.POINTER(_U32)],
     "mmfhe_measure_butterfly_peak": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "mmfhe_plan_set_fc_layer": [_VP, _U32, _VP],
+    "mmfhe_train_poly_net": [_VP, _VP, _VP, _U64, _VP, _U32, ctypes.c_float, _U32, _U32, ctypes.c_float, _U64, _VP,
+                             ctypes.POINTER(ctypes.c_float)],
+    "mmfhe_fold_poly_net": [_VP, _U32, ctypes.c_float, _VP, _U32, _VP],
     "mmfhe_autotune": [_VP, _U32, _U32, _VP],
     "mmfhe_tuning_get": [_VP, _VP],
     "mmfhe_tuning_set": [_VP, _VP],

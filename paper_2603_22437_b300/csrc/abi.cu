@@ -697,6 +697,16 @@ mmfhe_status mmfhe_plan_encode_consts(mmfhe_plan *plan) {
     ABI_CATCH(c)
 }
 
+mmfhe_status mmfhe_plan_set_fc_layer(mmfhe_plan *plan, uint32_t layer, const double *W) {
+    Context *c = nullptr;
+    ABI_TRY
+    if (!plan || !plan->p || !W) throw Error(MMFHE_ERR_BAD_ARG, "null argument");
+    c = plan->p->ctx;
+    CK(cudaSetDevice(c->device));
+    plan_set_fc_layer(*plan->p, layer, W);
+    ABI_CATCH(c)
+}
+
 mmfhe_status mmfhe_plan_rotations(const mmfhe_plan *plan, int32_t *out, uint32_t capacity, uint32_t *count) {
     if (!plan || !plan->p || !count) return fail(nullptr, MMFHE_ERR_BAD_ARG, "null argument");
     const auto &r = plan->p->rotations;

@@ -131,7 +131,17 @@ void encode_slots(const mmfhe_params &p, const double *slots, double scale, int 
 // ---------------------------------------------------------------------------
 // plan structure
 // ---------------------------------------------------------------------------
+static void check_fc_cfg(const Context &c, const mmfhe_circuit_config &cfg) {
+    const uint32_t D = cfg.bins, L = cfg.taps;
+    if (D < 2 || (D & (D - 1)) || D > c.n / 2) throw Error(MMFHE_ERR_BAD_ARG, "FC width must be a power of two within the slots");
+    if (L < 1 || L > 8) throw Error(MMFHE_ERR_BAD_ARG, "FC networks have 1..8 layers");
+    for (uint32_t l = 0; l <= L; l++)
+        if (cfg.fc_dims[l] < 1 || cfg.fc_dims[l] >= D) throw Error(MMFHE_ERR_BAD_ARG, "FC layer widths must be 1..D-1");
+    if (c.L - 2 * (int)L + 1 < 0) throw Error(MMFHE_ERR_BAD_ARG, "not enough levels in the parameter set for this circuit");
+}
+
 static void check_cfg(const Context &c, const mmfhe_circuit_config &cfg) {
+    if (cfg.kind == MMFHE_CIRCUIT_FC) return check_fc_cfg(c, cfg);
     if (cfg.kind != MMFHE_CIRCUIT_FIR_DFT && cfg.kind != MMFHE_CIRCUIT_VITAL) throw Error(MMFHE_ERR_BAD_ARG, "unknown circuit kind");
     if (cfg.frames < 2 || cfg.bins < 1 || cfg.taps < 1 || cfg.fs_mhz < 1) throw Error(MMFHE_ERR_BAD_ARG, "bad circuit sizes");
     int fpad = next_pow2((int)cfg.frames);
@@ -147,6 +157,43 @@ uint64_t key_of(const mmfhe_const_key &k) {
     return ((uint64_t)k.tag << 48) | ((uint64_t)k.band << 40) | (uint64_t)k.index;
 }
 
+// Structurally present diagonals of FC layer l: rows d_{l+1} and the constant
+// row, columns d_l and the constant column.
+std::vector<int> fc_present(const mmfhe_circuit_config &cfg, int l) {
+    const int D = (int)cfg.bins;
+    std::vector<int> rows, cols;
+    for (uint32_t i = 0; i < cfg.fc_dims[l + 1]; i++) rows.push_back((int)i);
+    for (uint32_t j = 0; j < cfg.fc_dims[l]; j++) cols.push_back((int)j);
+    rows.push_back(D - 1);
+    cols.push_back(D - 1);
+    std::set<int> ks;
+    for (int i : rows)
+        for (int j : cols) ks.insert(((j - i) % D + D) % D);
+    return std::vector<int>(ks.begin(), ks.end());
+}
+
+static Plan *create_fc_plan(Context &c, const mmfhe_circuit_config &cfg) {
+    std::unique_ptr<Plan> p(new Plan());
+    p->ctx = &c;
+    p->cfg = cfg;
+    const int D = (int)cfg.bins, L = (int)cfg.taps;
+    std::tie(p->n1_dft, p->n2_dft) = bsgs_split(D);
+    for (int l = 0; l < L; l++) {
+        const int lv = c.L - 2 * l;   // a dense layer and a square take one level each
+        for (int k : fc_present(cfg, l)) p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCW, (uint32_t)l, (uint32_t)k, (uint32_t)lv});
+    }
+    std::set<int32_t> rots;
+    for (int b = 1; b < p->n1_dft; b++) rots.insert(norm_rot(c, b));
+    for (int g = 1; g < p->n2_dft; g++) rots.insert(norm_rot(c, g * p->n1_dft));
+    rots.erase(0);
+    p->rotations.assign(rots.begin(), rots.end());
+    p->n_in = 1;
+    p->out_levels = {c.L - 2 * L + 1};
+    p->consts.resize(p->keys.size());
+    for (size_t i = 0; i < p->keys.size(); i++) p->index[key_of(p->keys[i])] = (int)i;
+    return p.release();
+}
+
 Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
     mmfhe_circuit_config cfg = cfg_in;
     if (cfg.kind == MMFHE_CIRCUIT_VITAL && cfg.dft_gain[0] == 0.0 && cfg.dft_gain[1] == 0.0) {
@@ -155,6 +202,7 @@ Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
         cfg.dft_gain[1] = cfg.taylor_order == 3 ? 1.0 : 0.2;
     }
     check_cfg(c, cfg);
+    if (cfg.kind == MMFHE_CIRCUIT_FC) return create_fc_plan(c, cfg);
     std::unique_ptr<Plan> p(new Plan());
     p->ctx = &c;
     p->cfg = cfg;
@@ -332,6 +380,8 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
 
 void plan_encode_consts(Plan &p, cudaStream_t st) {
     Context &c = *p.ctx;
+    if (p.cfg.kind == MMFHE_CIRCUIT_FC)
+        throw Error(MMFHE_ERR_BAD_ARG, "FC constants are learned weights: set them with mmfhe_plan_set_fc_layer");
     std::vector<uint64_t> words;
     for (size_t i = 0; i < p.keys.size(); i++) {
         const mmfhe_const_key &k = p.keys[i];
@@ -499,7 +549,57 @@ static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std:
     return out;
 }
 
+// Polynomial network: per layer, hoisted baby rotations of the input, the
+// BSGS product with the layer's diagonals, a rescale, and a square (relin,
+// rescale) after every layer but the last.
+static std::vector<CtB> run_fc(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st) {
+    const int L = (int)p.cfg.taps, n1 = p.n1_dft;
+    std::vector<int32_t> rot(n1);
+    std::vector<int> idx(n1);
+    for (int b = 0; b < n1; b++) rot[b] = idx[b] = b;
+    CtB x = std::move(in[0]);
+    for (int l = 0; l < L; l++) {
+        std::vector<CtB> babies = rotate_hoisted(c, k, x, rot, st);
+        BsgsTerm t;
+        t.baby = &babies;
+        t.baby_idx = idx;
+        for (int d : fc_present(p.cfg, l)) t.diags.push_back({d, &plan_const(p, MMFHE_CONST_FCW, (uint32_t)l, (uint32_t)d)});
+        CtB y = rescale(c, bsgs(c, k, {t}, n1, 1, st), st);
+        if (l < L - 1) {
+            TensorB sq = tensor_new(c, y.B, y.level);
+            tensor_acc(c, sq, y, y, 1, true, st);
+            y = rescale(c, relin(c, k, sq, st), st);
+        }
+        x = std::move(y);
+    }
+    std::vector<CtB> out;
+    out.push_back(std::move(x));
+    return out;
+}
+
+void plan_set_fc_layer(Plan &p, uint32_t layer, const double *W) {
+    Context &c = *p.ctx;
+    if (p.cfg.kind != MMFHE_CIRCUIT_FC) throw Error(MMFHE_ERR_BAD_ARG, "not an FC plan");
+    if (layer >= p.cfg.taps) throw Error(MMFHE_ERR_BAD_ARG, "layer out of range");
+    const int D = (int)p.cfg.bins, n1 = p.n1_dft, slots = (int)c.n / 2;
+    std::vector<double> v(slots), r(slots);
+    std::vector<uint64_t> words;
+    for (int k : fc_present(p.cfg, (int)layer)) {
+        // diag_k[j] = W[j mod D][(j mod D + k) mod D], pre-rotated by the giant step
+        for (int j = 0; j < slots; j++) v[j] = W[(size_t)(j % D) * D + ((j % D) + k) % D];
+        const int sh = (k / n1) * n1;   // Rot(v, -sh)[j] = v[j - sh]
+        for (int j = 0; j < slots; j++) r[j] = v[((j - sh) % slots + slots) % slots];
+        const auto it = p.index.find(key_of(mmfhe_const_key{MMFHE_CONST_FCW, layer, (uint32_t)k, 0}));
+        const mmfhe_const_key &key = p.keys[it->second];
+        words.assign((size_t)(key.level + 1) * c.n, 0);
+        encode_slots(c.params, r.data(), (double)c.primes[key.level], (int)key.level, words.data());
+        plan_set_const(p, (uint32_t)it->second, words.data(), 0);
+        CK(cudaStreamSynchronize(0));
+    }
+}
+
 std::vector<CtB> run_plan(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st) {
+    if (p.cfg.kind == MMFHE_CIRCUIT_FC) return run_fc(c, p, k, in, st);
     if (p.cfg.kind == MMFHE_CIRCUIT_FIR_DFT) return run_fir_dft(c, p, k, in, st);
     return run_vital(c, p, k, in, st);
 }

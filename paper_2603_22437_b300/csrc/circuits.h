@@ -33,6 +33,8 @@ Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg);
 const PtDev &plan_const(const Plan &p, uint32_t tag, uint32_t band, uint32_t idx);
 void plan_set_const(Plan &p, uint32_t i, const uint64_t *words, cudaStream_t st);
 void plan_encode_consts(Plan &p, cudaStream_t st);
+void plan_set_fc_layer(Plan &p, uint32_t layer, const double *W);
+std::vector<int> fc_present(const mmfhe_circuit_config &cfg, int l);
 std::vector<CtB> run_plan(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st);
 
 }  // namespace mmfhe
