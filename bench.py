@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", default="vital", choices=["vital", "batching", "serving"],
+    ap.add_argument("--workload", default="vital", choices=["vital", "batching", "serving", "fc"],
                     help="vital: the headline chain at B windows per step; batching: uneven windows through the "
                          "batcher against one call per window; serving: Poisson arrivals from many users through "
                          "the serving loop")
@@ -650,14 +650,95 @@ def run_serving(args, rank, world, local):
     return line
 
 
+def run_fc(args, rank, world, local):
+    """Encrypted inference of the learned polynomial network (three dense
+    layers 120 -> 32 -> 16 -> 6 with squares, N = 2^14, depth 5) on synthetic
+    gesture features: the network is trained on the GPU in plaintext, folded
+    to pure squares, and --batch encrypted feature vectors are classified per
+    launch.  Reports inferences/s and the plaintext training accuracy."""
+    import torch
+
+    import paper_2603_22437_b300 as M
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    params = M.fc_params()
+    ctx = M.Context(params, device=local)
+    n = 1 << params.log_n
+    dims = (120, 32, 16, 6)
+    X, y = synth.gesture_dataset(0, 6000)
+    alpha = float(np.float32(0.1))
+    t0 = time.perf_counter()
+    w, train_acc = ctx.train_poly_net(X[:5000], y[:5000], dims, alpha=alpha, epochs=20, batch=128, lr=0.05, seed=3)
+    train_s = time.perf_counter() - t0
+    mats = M.fold_poly_net(dims, alpha, w, 128)
+    plan = ctx.plan(M.fc_config(dims))
+    for l, W in enumerate(mats):
+        plan.set_fc_layer(l, W)
+    g = synth.rng(6000 + rank)
+    qp = params.primes_q + params.primes_p
+    keys = ctx.keys(rank)
+
+    def key_words():
+        return np.ascontiguousarray(np.stack([np.stack([synth.uniform_residues(g, qp, n) for _ in range(2)])
+                                              for _ in range(params.dnum)]))
+
+    keys.set_relin(key_words())
+    for k in plan.rotations():
+        keys.set_galois(k, key_words())
+    tiles = pick_tiles(ctx, args, args.batch)
+    _, _, lv = plan.io()
+    B = args.batch
+    d_in = [torch.from_numpy(synth.uniform_ciphertexts(500 + i, params.primes_q, n, 1).reshape(-1).view(np.int64))
+            .to(dev) for i in range(B)]
+    d_out = [torch.empty(2 * (lv[0] + 1) * n, dtype=torch.int64, device=dev) for _ in range(B)]
+    stream = torch.cuda.Stream(device=dev)
+    for _ in range(args.warmup):
+        ctx.eval(plan, keys, d_in, d_out, stream=stream)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        ctx.eval(plan, keys, d_in, d_out, stream=stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    test_acc = float(np.mean([np.argmax(cc_fc_forward(mats, x)) == t for x, t in zip(X[5000:], y[5000:])]))
+    return {
+        "metric": "encrypted polynomial-network inferences/s", "value": job_throughput(world, B * args.steps,
+                                                                                      sum(ms) / 1000.0),
+        "unit": "inferences/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": float(np.mean(ms)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "learned polynomial network 120 -> 32 -> 16 -> 6 (dense layers, square "
+                               "activations) on synthetic 6-class gesture features, CKKS N=2^14, depth 5, "
+                               "%d encrypted feature vectors per launch" % B, "tiles": tiles},
+        "plaintext_training": {"train_accuracy": train_acc, "test_accuracy": test_acc, "seconds": train_s,
+                               "samples": 5000, "epochs": 20},
+    }
+
+
+def cc_fc_forward(mats, x):
+    """FP64 forward of the folded network (the labels encrypted inference must reproduce)."""
+    v = np.zeros(128)
+    v[: len(x)] = x
+    v[127] = 1.0
+    for l, W in enumerate(mats):
+        v = W @ v
+        if l < len(mats) - 1:
+            v = v * v
+    return v[:6]
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.workload in ("batching", "serving"):
-        line = (run_batching if args.workload == "batching" else run_serving)(args, rank, world, local)
+    if args.workload in ("batching", "serving", "fc"):
+        line = {"batching": run_batching, "serving": run_serving, "fc": run_fc}[args.workload](args, rank, world, local)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
