@@ -4,7 +4,8 @@ Workload (the configuration the headline metric is quoted on): the full
 vital-sign chain (K1 -> K2 | K4 -> K5 -> K7 -> K3 -> |X|^2 -> sharpen ->
 weighted average; depth 11) at N = 2^15 with 12 + 4 primes, one 10 s window
 = 200 frames x 256 range bins = 16 input ciphertexts.  A step evaluates a
-batch of B windows of one user (every launch covers the whole batch).
+batch of B windows of one user (every launch covers the whole batch);
+B = 64 by default (profiles/vital_chain_batch_sweep.md).
 
 Inputs are synthetic: uniform residues for the ciphertexts and switching keys
 (under RLWE a ciphertext or key is indistinguishable from such words, and the
@@ -47,7 +48,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=16, help="windows per step (per GPU)")
+    ap.add_argument("--batch", type=int, default=64, help="windows per step (per GPU)")
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -276,9 +277,10 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def ncu_traffic(kernel):
+def ncu_traffic(kernel, batch):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
-    was captured on the current kernel sources."""
+    was captured on the current kernel sources; scaled from the captured batch
+    to `batch` windows (every launch covers all windows of the batch)."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -286,7 +288,9 @@ def ncu_traffic(kernel):
     if j.get("csrc_hash") != csrc_hash():
         return None
     k = j.get("kernels", {}).get(kernel)
-    return None if k is None else k.get("dram_bytes_per_launch_full_size")
+    if k is None:
+        return None
+    return k.get("dram_bytes_per_launch_full_size") * batch / j.get("batch", batch)
 
 
 def pick_tiles(ctx, args, batch):
@@ -297,7 +301,7 @@ def pick_tiles(ctx, args, batch):
     return ctx.tuning() if args.no_autotune else ctx.autotune(batch)
 
 
-def roofline_of(prof, bf64_peak, bf32_peak):
+def roofline_of(prof, bf64_peak, bf32_peak, batch):
     """Roofline of the dominant kernel (most event time in the profiled step).
 
     Two ceilings apply to every NTT pass: HBM (algorithmic bytes / time against
@@ -321,7 +325,7 @@ def roofline_of(prof, bf64_peak, bf32_peak):
     main, other = (alu, hbm) if alu and alu["frac"] > hbm["frac"] else (hbm, alu)
     r = {"kernel": name}
     r.update(main)
-    r.update({"traffic": ncu_traffic(name), "other": other, "launches_per_step": nl,
+    r.update({"traffic": ncu_traffic(name, batch), "other": other, "launches_per_step": nl,
               "avg_launch_us": 1000.0 * ms / nl, "share_of_step": ms / tot_ms,
               "butterfly_peak_per_s": {"u64": bf64_peak, "u32": bf32_peak},
               "kernels": {k: {"launches": v[0], "ms": round(v[1], 3),
@@ -445,7 +449,7 @@ def run_mine(args, rank, world, local):
     prof = ctx.profile()
     ctx.profile(False)
     bf64_peak, bf32_peak = ctx.butterfly_peak()
-    roofline = roofline_of(prof, bf64_peak, bf32_peak)
+    roofline = roofline_of(prof, bf64_peak, bf32_peak, B)
     line = {
         "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
