@@ -260,10 +260,14 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
+KERNEL_SOURCES = ("internal.h", "kernels.h", "kernels.cu", "modarith.cuh", "ntt_impl.cuh")
+
+
 def csrc_hash():
+    """Hash of the device-kernel sources (the files ncu counters depend on)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2603_22437_b300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in KERNEL_SOURCES + tuple(sorted(x for x in os.listdir(d) if x.startswith("ntt_l"))):
         h.update(f.encode())
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
