@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", default="vital", choices=["vital", "batching", "serving", "fc"],
+    ap.add_argument("--workload", default="vital", choices=["vital", "batching", "serving", "fc", "per-frame"],
                     help="vital: the headline chain at B windows per step; batching: uneven windows through the "
                          "batcher against one call per window; serving: Poisson arrivals from many users through "
                          "the serving loop")
@@ -727,6 +727,74 @@ def run_fc(args, rank, world, local):
     }
 
 
+def run_per_frame(args, rank, world, local):
+    """The vital chain with per-frame packing (the paper's slow baseline: one
+    ciphertext per frame and part, 4F = 800 input ciphertexts per window)
+    against batched packing (16 per window) on the same windows count B,
+    same formulas and outputs."""
+    import torch
+
+    import paper_2603_22437_b300 as M
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    params = M.vital_params()
+    ctx = M.Context(params, device=local)
+    n = 1 << params.log_n
+    g = synth.rng(7100 + rank)
+    qp = params.primes_q + params.primes_p
+    plans = {"per_frame": ctx.plan(M.vital_config(per_frame=True)), "batched": ctx.plan(M.vital_config())}
+    for p in plans.values():
+        p.encode_consts()
+    rots = sorted(set(plans["per_frame"].rotations()) | set(plans["batched"].rotations()))
+    keys = ctx.keys(rank)
+
+    def key_words():
+        return np.ascontiguousarray(np.stack([np.stack([synth.uniform_residues(g, qp, n) for _ in range(2)])
+                                              for _ in range(params.dnum)]))
+
+    keys.set_relin(key_words())
+    for k in rots:
+        keys.set_galois(k, key_words())
+    B = args.batch
+    tiles = pick_tiles(ctx, args, B)
+    stream = torch.cuda.Stream(device=dev)
+    res = {}
+    for name, plan in plans.items():
+        n_in, _, lv = plan.io()
+        host = synth.uniform_ciphertexts(7200, params.primes_q, n, n_in).reshape(-1).view(np.int64)
+        one = torch.from_numpy(host).to(dev)
+        d_in = [one.clone() for _ in range(B)]
+        del one
+        d_out = [torch.empty(sum(2 * (l + 1) * n for l in lv), dtype=torch.int64, device=dev) for _ in range(B)]
+        for _ in range(max(1, args.warmup)):
+            ctx.eval(plan, keys, d_in, d_out, stream=stream, vital=True)
+        torch.cuda.synchronize()
+        l0 = ctx.launch_count()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for i in range(args.steps):
+            ev[i][0].record(stream)
+            ctx.eval(plan, keys, d_in, d_out, stream=stream, vital=True)
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        res[name] = {"value": job_throughput(world, B * args.steps, sum(ms) / 1000.0), "ms_per_step": float(np.mean(ms)),
+                     "input_ciphertexts_per_window": n_in, "launches_per_step": (ctx.launch_count() - l0) // args.steps}
+        del d_in, d_out
+        torch.cuda.empty_cache()
+    return {
+        "metric": METRIC, "value": res["per_frame"]["value"], "unit": "windows/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["per_frame"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "vital-sign chain with per-frame packing (one ciphertext per frame and part, "
+                               "200 frames x 256 bins, 800 input cts per window) against batched packing, "
+                               "N=2^15, B=%d windows per launch" % B, "tiles": tiles},
+        "per_frame": res["per_frame"], "batched": res["batched"],
+        "batched_over_per_frame": res["batched"]["value"] / res["per_frame"]["value"],
+    }
+
+
 def cc_fc_forward(mats, x):
     """FP64 forward of the folded network (the labels encrypted inference must reproduce)."""
     v = np.zeros(128)
@@ -745,8 +813,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.workload in ("batching", "serving", "fc"):
-        line = {"batching": run_batching, "serving": run_serving, "fc": run_fc}[args.workload](args, rank, world, local)
+    if args.workload in ("batching", "serving", "fc", "per-frame"):
+        line = {"batching": run_batching, "serving": run_serving, "fc": run_fc,
+                "per-frame": run_per_frame}[args.workload](args, rank, world, local)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

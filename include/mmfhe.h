@@ -234,6 +234,12 @@ mmfhe_status mmfhe_ct_bsgs(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out
 #define MMFHE_CIRCUIT_FIR_DFT 1 /* 64-tap bandpass FIR + windowed fftshifted DFT on every bin */
 #define MMFHE_CIRCUIT_VITAL 2   /* vital-sign chain K1->K2 | K4->K5->K7->K3->|X|^2->sharpen->avg */
 #define MMFHE_CIRCUIT_FC 3      /* polynomial network: dense layers with a square after each but the last */
+/* The vital chain with per-frame packing (the paper's slow baseline, Sec.
+ * "Packing"): one ciphertext per frame and part, range bin r in slot r.
+ * Inputs per window: stream 1 frames t = 0..F-1 as (Re, Im), then stream 2
+ * alike (4F ciphertexts at the top level).  Same formulas, level schedule and
+ * outputs as MMFHE_CIRCUIT_VITAL (third order only), values in slot 0. */
+#define MMFHE_CIRCUIT_VITAL_PER_FRAME 4
 
 typedef struct mmfhe_circuit_config {
     uint32_t kind;             /* MMFHE_CIRCUIT_* */
@@ -292,6 +298,16 @@ mmfhe_status mmfhe_plan_encode_consts(mmfhe_plan *plan);
  * stored).  The constants of an FC plan are learned, so
  * mmfhe_plan_encode_consts returns BAD_ARG for it. */
 mmfhe_status mmfhe_plan_set_fc_layer(mmfhe_plan *plan, uint32_t layer, const double *W);
+/* Per-frame plans: the public scalar constants (count from
+ * mmfhe_plan_num_scalars), in this order: per band the FIR taps h[0..taps);
+ * per band, per DFT bin k, the coefficients g w[t] cos(2 pi k t / F) for
+ * t = 1..F-1 then -g w[t] sin(2 pi k t / F) (g = the band gain / 3, w =
+ * Hann); per band, per bin k, the frequency k fs / F in Hz.  A scalar c
+ * multiplies as the constant polynomial round(q_l c) at level l.  The plan
+ * starts with the library's FP64 design; set_scalars replaces it. */
+mmfhe_status mmfhe_plan_num_scalars(const mmfhe_plan *plan, uint32_t *count);
+mmfhe_status mmfhe_plan_get_scalars(const mmfhe_plan *plan, double *out, uint32_t capacity);
+mmfhe_status mmfhe_plan_set_scalars(mmfhe_plan *plan, const double *values, uint32_t count);
 /* Rotation amounts whose Galois keys the plan needs (ascending, in [0, N/2)). */
 mmfhe_status mmfhe_plan_rotations(const mmfhe_plan *plan, int32_t *out, uint32_t capacity, uint32_t *count);
 /* Input/output shape: ciphertexts per window in and out, and the level of
@@ -307,7 +323,7 @@ mmfhe_status mmfhe_plan_io(const mmfhe_plan *plan, uint32_t *n_in, uint32_t *n_o
  * no-op. */
 mmfhe_status mmfhe_eval(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *const *keys,
                         const uint64_t *const *in_cts, size_t batch, uint64_t *const *out_cts, void *stream);
-/* mmfhe_eval restricted to MMFHE_CIRCUIT_VITAL plans (paper Sec. "Example
+/* mmfhe_eval restricted to MMFHE_CIRCUIT_VITAL (and _PER_FRAME) plans (paper Sec. "Example
  * Pipelines", Encrypted Vital Signs; depth per Table 1).  Window inputs:
  * stream 1 (K1) G groups x (Re, Im), then stream 2 (K4) G x (Re, Im), at the
  * top level.  Outputs: num_r, den_r (target bin), num_RR, den_RR, num_HR,

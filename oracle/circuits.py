@@ -240,6 +240,16 @@ class Evaluator:
     def mul_plain_sum(self, pairs):
         return ck.mul_plain_sum(self.P, pairs)
 
+    def lincomb(self, terms, scale):
+        """sum_i c_i x_i for real constants c_i, each encoded at `scale`
+        (constant polynomials), not rescaled."""
+        self._t("lincomb", terms[0][0].level, len(terms))
+        acc = None
+        for x, c in terms:
+            t = ck.mul_scalar(self.P, x, c, scale)
+            acc = t if acc is None else ck.add(self.P, acc, t)
+        return acc
+
     def rotsum(self, a, stride, span):
         """x <- x + Rot(x, stride 2^i), i < log2(span): slot j then holds
         sum_{m < span} x[j + m stride]."""
@@ -811,4 +821,114 @@ def fc_forward(mats, x, D):
         if l < len(mats) - 1:
             v = v * v
     return v
+
+
+# ---------------------------------------------------------------------------
+# Per-frame packing (the paper's slow baseline, Sec. "Packing"): one
+# ciphertext per frame and stream part, range bin r in slot r.  Sums over bins
+# become rotate-and-sums (the result lands in slot 0); everything across
+# frames -- the FIR, the t-1 pairs of K7, the DFT -- is ciphertext-level
+# arithmetic with scalar constants.  Same formulas and level schedule as
+# VitalCircuit, so the decrypted outputs agree with the FP64 pipeline alike.
+# ---------------------------------------------------------------------------
+class PerFrameVitalCircuit:
+    def __init__(self, P, cfg=VitalConfig()):
+        assert cfg.taylor_order == 3 and cfg.bins <= P.slots
+        self.P, self.cfg = P, cfg
+        self.base = VitalCircuit.__new__(VitalCircuit)   # shares the public DSP design
+        self.base.P, self.base.cfg = P, cfg
+        self.bands = [band_bins(cfg.frames, cfg.fs_mhz, b) for b in cfg.bands_mhz]
+        self.span = next_pow2(cfg.bins)
+        assert P.L - 11 >= 0, "not enough levels for the chain"
+
+    def constants(self):
+        """Slot vectors of the side branch (bin index, ones) at level L0 - 2."""
+        P, R = self.P, self.cfg.bins
+        lv = P.L - 2
+        idx, one = np.zeros(P.slots), np.zeros(P.slots)
+        idx[:R] = np.arange(R)
+        one[:R] = 1.0
+        return {"idx": ck.encode(P, idx, P.q[lv], lv), "one": ck.encode(P, one, P.q[lv], lv)}
+
+    def rotations(self):
+        return sorted({1 << i for i in range(int(math.log2(self.span)))})
+
+    def scalars(self):
+        """The public scalar constants, in the order the library's plan keeps
+        them: per band the FIR taps h[0..taps); per band, per bin k, the DFT
+        coefficients g w[t] cos(2 pi k t / F) for t = 1..F-1, then
+        -g w[t] sin(2 pi k t / F) (g includes the 1/3); per band, per bin k,
+        the frequency k fs / F in Hz."""
+        cfg, F = self.cfg, self.cfg.frames
+        out = []
+        for b in range(len(self.bands)):
+            out.extend(self.base.taps(b))
+        wn, t = hann(F), np.arange(1, F)
+        for b, ks in enumerate(self.bands):
+            g = self.base.dft_gain(b)
+            for k in ks:
+                ang = 2 * np.pi * k * t / F
+                out.extend(g * wn[t] * np.cos(ang))
+                out.extend(-g * wn[t] * np.sin(ang))
+        for ks in self.bands:
+            out.extend(k * (cfg.fs_mhz / 1000) / F for k in ks)
+        return np.array(out, dtype=np.float64)
+
+    def run(self, ev, consts, s1, s2, scalars=None):
+        """s1, s2: lists of F (re, im) ciphertext pairs (one pair per frame),
+        top level.  Returns [num_r, den_r, num_RR, den_RR, num_HR, den_HR]
+        with the values in slot 0."""
+        P, cfg = self.P, self.cfg
+        F = cfg.frames
+        q = P.q
+        sc = iter(self.scalars() if scalars is None else scalars)
+        taps = [[next(sc) for _ in range(cfg.taps)] for _ in self.bands]
+        dft = [{k: ([next(sc) for _ in range(1, F)], [next(sc) for _ in range(1, F)]) for k in ks} for ks in self.bands]
+        fhz = [[next(sc) for _ in ks] for ks in self.bands]
+        # side branch: K1 energy, summed over frames; K2 w = E^2
+        E = None
+        for re, im in s1:
+            p = ev.rescale(ev.square_sum([re, im]))
+            E = p if E is None else ev.add(E, p)
+        w = ev.rescale(ev.square_sum([E]))
+        num_r = ev.rotsum(ev.rescale(ev.mul_plain(w, consts["idx"])), 1, self.span)
+        den_r = ev.rotsum(ev.rescale(ev.mul_plain(w, consts["one"])), 1, self.span)
+        # K4 soft I/Q: per frame p, m = p^2, I = sum_r m Re, Q = sum_r m Im
+        I, Q = [], []
+        for re, im in s2:
+            p = ev.rescale(ev.square_sum([re, im]))
+            m = ev.rescale(ev.square_sum([p]))
+            for part, out in ((re, I), (im, Q)):
+                x = ev.drop(part, m.level)
+                out.append(ev.rotsum(ev.rescale(ev.relin(ev.tensor(m, x))), 1, self.span))
+        outs = [num_r, den_r]
+        S = {}
+        for b, ks in enumerate(self.bands):
+            # K5 causal FIR over frames
+            h = taps[b]
+            lv = I[0].level
+            If = [ev.rescale(ev.lincomb([(I[t - k], h[k]) for k in range(cfg.taps) if t - k >= 0], q[lv]))
+                  for t in range(F)]
+            Qf = [ev.rescale(ev.lincomb([(Q[t - k], h[k]) for k in range(cfg.taps) if t - k >= 0], q[lv]))
+                  for t in range(F)]
+            # K7 third order, frames t >= 1 (dphi[0] = 0)
+            dphi = [None]
+            for t in range(1, F):
+                y = ev.rescale(ev.relin(ev.tensor_sub(ev.tensor(Qf[t], If[t - 1]), ev.tensor(If[t], Qf[t - 1]))))
+                x = ev.rescale(ev.relin(ev.tensor_add(ev.tensor(If[t], If[t - 1]), ev.tensor(Qf[t], Qf[t - 1]))))
+                u = ev.rescale(ev.relin(ev.tensor_sub(ev.tensor_mul_int(ev.tensor(x, x), 3), ev.tensor(y, y))))
+                dphi.append(ev.rescale(ev.relin(ev.tensor(ev.drop(y, u.level), u))))
+            # K3 narrowband DFT (gain carries the 1/3), |X|^2
+            lv = dphi[1].level
+            for k in ks:
+                cre, cim = dft[b][k]
+                re_k = ev.rescale(ev.lincomb([(dphi[t], cre[t - 1]) for t in range(1, F)], q[lv]))
+                im_k = ev.rescale(ev.lincomb([(dphi[t], cim[t - 1]) for t in range(1, F)], q[lv]))
+                Pk = ev.rescale(ev.square_sum([re_k, im_k]))
+                S[k] = ev.rescale(ev.square_sum([Pk]))    # merge + sharpen: bands are disjoint in k
+        for b, ks in enumerate(self.bands):
+            lv = S[ks[0]].level
+            outs.append(ev.rescale(ev.lincomb([(S[k], f) for k, f in zip(ks, fhz[b])], q[lv])))
+            outs.append(ev.rescale(ev.lincomb([(S[k], 1.0) for k in ks], q[lv])))
+        return outs
 

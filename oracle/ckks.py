@@ -297,6 +297,15 @@ def mul_int(P, a, k):
     return Ciphertext(c0, c1, a.level, a.scale)
 
 
+def mul_scalar(P, a, c, scale):
+    """ct * c for a real constant c encoded at `scale`: the constant
+    polynomial round(scale c) (the encoding of a vector equal to c in every
+    slot), so an exact integer multiply; the scale multiplies by `scale`."""
+    m = int(round_half_away(scale * c))
+    r = mul_int(P, a, m)
+    return Ciphertext(r.c0, r.c1, a.level, a.scale * scale)
+
+
 def drop_level(P, a, level):
     """Discard the top limbs (no division, scale unchanged)."""
     assert level <= a.level

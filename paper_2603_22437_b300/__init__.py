@@ -11,7 +11,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (CIRCUIT_FC, CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CONST_TAGS, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
+from ._lib import (CIRCUIT_FC, CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_VITAL_PER_FRAME, CONST_TAGS, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
                    MmfheError, Params, ServerConfig, ServerStats, Tuning, check, ptr, ptr_array, stream_ptr)
 
 __all__ = ["Context", "Keys", "Plan", "Graph", "Batcher", "Server", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
@@ -69,9 +69,12 @@ def pack_window(log_n, values):
 
 
 def vital_config(bins=256, frames=200, fs_mhz=20000, taps=64, taylor_order=3,
-                 bands_mhz=((100, 600), (800, 2500)), dft_gains=(0.0, 0.0)):
+                 bands_mhz=((100, 600), (800, 2500)), dft_gains=(0.0, 0.0), per_frame=False):
+    """The vital chain; per_frame=True: the per-frame packing (one ciphertext
+    per frame and part, the paper's slow baseline)."""
     c = CircuitConfig()
-    c.kind, c.bins, c.frames, c.fs_mhz, c.taps, c.taylor_order = CIRCUIT_VITAL, bins, frames, fs_mhz, taps, taylor_order
+    kind = CIRCUIT_VITAL_PER_FRAME if per_frame else CIRCUIT_VITAL
+    c.kind, c.bins, c.frames, c.fs_mhz, c.taps, c.taylor_order = kind, bins, frames, fs_mhz, taps, taylor_order
     c.num_bands = 2
     for b in range(2):
         c.band_lo_mhz[b], c.band_hi_mhz[b] = bands_mhz[b]
@@ -495,6 +498,18 @@ class Plan:
 
     def encode_consts(self):
         self.ctx._c(_lib.lib().mmfhe_plan_encode_consts(self.h))
+
+    def scalars(self):
+        n = ctypes.c_uint32()
+        self.ctx._c(_lib.lib().mmfhe_plan_num_scalars(self.h, ctypes.byref(n)))
+        out = np.empty(n.value, dtype=np.float64)
+        if n.value:
+            self.ctx._c(_lib.lib().mmfhe_plan_get_scalars(self.h, ptr(out), n.value))
+        return out
+
+    def set_scalars(self, values):
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        self.ctx._c(_lib.lib().mmfhe_plan_set_scalars(self.h, ptr(v), len(v)))
 
     def set_fc_layer(self, layer, W):
         """FC plans: encode a layer from its D x D matrix."""

@@ -20,7 +20,7 @@ ERRORS = {
     -1: "BAD_ARG", -2: "BAD_BLOB", -3: "PARAM_MISMATCH", -4: "LEVEL_MISMATCH", -5: "OUT_OF_MEMORY",
     -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "BUSY",
 }
-CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_FC = 1, 2, 3
+CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_FC, CIRCUIT_VITAL_PER_FRAME = 1, 2, 3, 4
 CONST_TAGS = {1: "idx", 2: "one", 3: "fir", 4: "dre", 5: "dim", 6: "fw", 7: "fone", 8: "dft_c", 9: "dft_s",
               10: "dft_ms", 11: "fcw"}
 
@@ -106,6 +106,9 @@ _SIGS = {
     "mmfhe_profile_get": [_VP, _VP, _U32, ctypes.POINTER(_U32)],
     "mmfhe_measure_butterfly_peak": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "mmfhe_plan_set_fc_layer": [_VP, _U32, _VP],
+    "mmfhe_plan_num_scalars": [_VP, ctypes.POINTER(_U32)],
+    "mmfhe_plan_get_scalars": [_VP, _VP, _U32],
+    "mmfhe_plan_set_scalars": [_VP, _VP, _U32],
     "mmfhe_train_poly_net": [_VP, _VP, _VP, _U64, _VP, _U32, ctypes.c_float, _U32, _U32, ctypes.c_float, _U64, _VP,
                              ctypes.POINTER(ctypes.c_float)],
     "mmfhe_fold_poly_net": [_VP, _U32, ctypes.c_float, _VP, _U32, _VP],

@@ -697,6 +697,29 @@ mmfhe_status mmfhe_plan_encode_consts(mmfhe_plan *plan) {
     ABI_CATCH(c)
 }
 
+mmfhe_status mmfhe_plan_num_scalars(const mmfhe_plan *plan, uint32_t *count) {
+    if (!plan || !plan->p || !count) return fail(nullptr, MMFHE_ERR_BAD_ARG, "null argument");
+    *count = (uint32_t)plan->p->scalars.size();
+    return MMFHE_OK;
+}
+
+mmfhe_status mmfhe_plan_get_scalars(const mmfhe_plan *plan, double *out, uint32_t capacity) {
+    if (!plan || !plan->p || !out) return fail(nullptr, MMFHE_ERR_BAD_ARG, "null argument");
+    const auto &v = plan->p->scalars;
+    if (capacity < v.size()) return fail(plan->p->ctx, MMFHE_ERR_BAD_ARG, "capacity too small");
+    std::copy(v.begin(), v.end(), out);
+    return MMFHE_OK;
+}
+
+mmfhe_status mmfhe_plan_set_scalars(mmfhe_plan *plan, const double *values, uint32_t count) {
+    Context *c = nullptr;
+    ABI_TRY
+    if (!plan || !plan->p || !values) throw Error(MMFHE_ERR_BAD_ARG, "null argument");
+    c = plan->p->ctx;
+    plan_set_scalars(*plan->p, values, count);
+    ABI_CATCH(c)
+}
+
 mmfhe_status mmfhe_plan_set_fc_layer(mmfhe_plan *plan, uint32_t layer, const double *W) {
     Context *c = nullptr;
     ABI_TRY
@@ -746,7 +769,8 @@ mmfhe_status mmfhe_eval(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *cons
 
 mmfhe_status mmfhe_eval_vital(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *const *keys,
                               const uint64_t *const *in_cts, size_t batch, uint64_t *const *out_cts, void *stream) {
-    if (!plan || !plan->p || plan->p->cfg.kind != MMFHE_CIRCUIT_VITAL)
+    if (!plan || !plan->p ||
+        (plan->p->cfg.kind != MMFHE_CIRCUIT_VITAL && plan->p->cfg.kind != MMFHE_CIRCUIT_VITAL_PER_FRAME))
         return fail(ctx ? ctx->c : nullptr, MMFHE_ERR_BAD_ARG, "plan is not a vital-sign circuit");
     return mmfhe_eval(ctx, plan, keys, in_cts, batch, out_cts, stream);
 }

@@ -140,8 +140,20 @@ static void check_fc_cfg(const Context &c, const mmfhe_circuit_config &cfg) {
     if (c.L - 2 * (int)L + 1 < 0) throw Error(MMFHE_ERR_BAD_ARG, "not enough levels in the parameter set for this circuit");
 }
 
+static bool is_vital(const mmfhe_circuit_config &cfg) {
+    return cfg.kind == MMFHE_CIRCUIT_VITAL || cfg.kind == MMFHE_CIRCUIT_VITAL_PER_FRAME;
+}
+
 static void check_cfg(const Context &c, const mmfhe_circuit_config &cfg) {
     if (cfg.kind == MMFHE_CIRCUIT_FC) return check_fc_cfg(c, cfg);
+    if (cfg.kind == MMFHE_CIRCUIT_VITAL_PER_FRAME) {
+        if (cfg.frames < 2 || cfg.bins < 1 || cfg.taps < 1 || cfg.fs_mhz < 1 || cfg.taps > cfg.frames)
+            throw Error(MMFHE_ERR_BAD_ARG, "bad circuit sizes");
+        if ((uint32_t)next_pow2((int)cfg.bins) > c.n / 2) throw Error(MMFHE_ERR_BAD_ARG, "more bins than slots");
+        if (cfg.taylor_order != 3 || cfg.num_bands != 2) throw Error(MMFHE_ERR_BAD_ARG, "per-frame chain: third order, two bands");
+        if (c.L < 11) throw Error(MMFHE_ERR_BAD_ARG, "not enough levels for the vital chain");
+        return;
+    }
     if (cfg.kind != MMFHE_CIRCUIT_FIR_DFT && cfg.kind != MMFHE_CIRCUIT_VITAL) throw Error(MMFHE_ERR_BAD_ARG, "unknown circuit kind");
     if (cfg.frames < 2 || cfg.bins < 1 || cfg.taps < 1 || cfg.fs_mhz < 1) throw Error(MMFHE_ERR_BAD_ARG, "bad circuit sizes");
     int fpad = next_pow2((int)cfg.frames);
@@ -194,15 +206,61 @@ static Plan *create_fc_plan(Context &c, const mmfhe_circuit_config &cfg) {
     return p.release();
 }
 
+// The library's FP64 design of the per-frame chain's scalar constants, in the
+// order of mmfhe_plan_set_scalars.
+static std::vector<double> per_frame_scalars(const Plan &p) {
+    const mmfhe_circuit_config &cfg = p.cfg;
+    const int F = (int)cfg.frames;
+    const double fs = cfg.fs_mhz / 1000.0;
+    std::vector<double> out;
+    for (int b = 0; b < 2; b++) {
+        std::vector<double> h = fir_bandpass((int)cfg.taps, cfg.band_lo_mhz[b] / 1000.0, cfg.band_hi_mhz[b] / 1000.0, fs);
+        out.insert(out.end(), h.begin(), h.end());
+    }
+    for (int b = 0; b < 2; b++) {
+        const double gain = cfg.dft_gain[b] / 3.0;
+        for (int k : p.bands[b]) {
+            for (int t = 1; t < F; t++) out.push_back(gain * hann(t, F) * std::cos(2 * M_PI * k * t / F));
+            for (int t = 1; t < F; t++) out.push_back(-gain * hann(t, F) * std::sin(2 * M_PI * k * t / F));
+        }
+    }
+    for (int b = 0; b < 2; b++)
+        for (int k : p.bands[b]) out.push_back(k * fs / F);
+    return out;
+}
+
+static Plan *create_per_frame_plan(Context &c, const mmfhe_circuit_config &cfg) {
+    std::unique_ptr<Plan> p(new Plan());
+    p->ctx = &c;
+    p->cfg = cfg;
+    const int L = c.L, F = (int)cfg.frames;
+    for (int b = 0; b < 2; b++) {
+        p->bands[b] = band_bins(F, (int)cfg.fs_mhz, (int)cfg.band_lo_mhz[b], (int)cfg.band_hi_mhz[b]);
+        if (p->bands[b].empty()) throw Error(MMFHE_ERR_BAD_ARG, "empty frequency band");
+    }
+    p->span[0] = next_pow2((int)cfg.bins);
+    p->keys.push_back(mmfhe_const_key{MMFHE_CONST_IDX, 0, 0, (uint32_t)(L - 2)});
+    p->keys.push_back(mmfhe_const_key{MMFHE_CONST_ONE, 0, 0, (uint32_t)(L - 2)});
+    for (int i = 0; (1 << i) < p->span[0]; i++) p->rotations.push_back(norm_rot(c, 1 << i));
+    std::sort(p->rotations.begin(), p->rotations.end());
+    p->n_in = 4 * F;
+    p->out_levels = {L - 3, L - 3, L - 11, L - 11, L - 11, L - 11};
+    p->scalars = per_frame_scalars(*p);
+    p->consts.resize(p->keys.size());
+    for (size_t i = 0; i < p->keys.size(); i++) p->index[key_of(p->keys[i])] = (int)i;
+    return p.release();
+}
+
 Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
     mmfhe_circuit_config cfg = cfg_in;
-    if (cfg.kind == MMFHE_CIRCUIT_VITAL && cfg.dft_gain[0] == 0.0 && cfg.dft_gain[1] == 0.0) {
+    if (is_vital(cfg) && cfg.dft_gain[0] == 0.0 && cfg.dft_gain[1] == 0.0) {
         // default public spectral gains (median DFT magnitude ~0.5 on the synthetic workload)
         cfg.dft_gain[0] = cfg.taylor_order == 3 ? 30.0 : 1.5;
         cfg.dft_gain[1] = cfg.taylor_order == 3 ? 1.0 : 0.2;
     }
     check_cfg(c, cfg);
     if (cfg.kind == MMFHE_CIRCUIT_FC) return create_fc_plan(c, cfg);
+    if (cfg.kind == MMFHE_CIRCUIT_VITAL_PER_FRAME) return create_per_frame_plan(c, cfg);
     std::unique_ptr<Plan> p(new Plan());
     p->ctx = &c;
     p->cfg = cfg;
@@ -328,6 +386,10 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
     switch (k.tag) {
     case MMFHE_CONST_IDX:
     case MMFHE_CONST_ONE:
+        if (cfg.kind == MMFHE_CIRCUIT_VITAL_PER_FRAME) {   // bin r in slot r
+            for (int r = 0; r < (int)cfg.bins; r++) v[r] = k.tag == MMFHE_CONST_IDX ? (double)r : 1.0;
+            return v;
+        }
         for (int r = 0; r < Rc; r++) {
             int gb = (int)k.index * Rc + r;
             if (gb < (int)cfg.bins) v[slot(0, r)] = k.tag == MMFHE_CONST_IDX ? (double)gb : 1.0;
@@ -598,8 +660,127 @@ void plan_set_fc_layer(Plan &p, uint32_t layer, const double *W) {
     }
 }
 
+// Per-frame packing: in = stream 1 (Re_t, Im_t) for t < F, then stream 2.
+// Sums over bins are rotate-and-sums (result in slot 0); sums over frames and
+// the FIR / DFT are scalar linear combinations of frame ciphertexts.
+static std::vector<CtB> run_vital_per_frame(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in,
+                                            cudaStream_t st) {
+    const mmfhe_circuit_config &cfg = p.cfg;
+    const int F = (int)cfg.frames, T = (int)cfg.taps;
+    const uint32_t span = (uint32_t)p.span[0];
+    const std::vector<double> &sc = p.scalars;
+    size_t si = 0;
+    std::vector<double> taps[2];
+    for (int b = 0; b < 2; b++) taps[b].assign(sc.begin() + si, sc.begin() + si + T), si += T;
+    std::vector<std::vector<double>> cre[2], cim[2];
+    for (int b = 0; b < 2; b++)
+        for (size_t kk = 0; kk < p.bands[b].size(); kk++) {
+            cre[b].emplace_back(sc.begin() + si, sc.begin() + si + F - 1), si += F - 1;
+            cim[b].emplace_back(sc.begin() + si, sc.begin() + si + F - 1), si += F - 1;
+        }
+    std::vector<double> fhz[2];
+    for (int b = 0; b < 2; b++) fhz[b].assign(sc.begin() + si, sc.begin() + si + p.bands[b].size()), si += p.bands[b].size();
+    auto qs = [&](int level) { return (double)c.primes[level]; };
+    // side branch: K1 energy summed over frames; K2 w = E^2; index / ones; rotate-sum over bins
+    CtB E;
+    for (int t = 0; t < F; t++) {
+        CtB pt = rescale(c, square_sum(c, k, {&in[2 * t], &in[2 * t + 1]}, st), st);
+        if (t == 0) {
+            E = std::move(pt);
+        } else {
+            CtB e2 = ct_new(c, E.B, E.level, E.scale);
+            ct_addsub(c, e2, E, pt, false, st);
+            E = std::move(e2);
+        }
+    }
+    CtB w = rescale(c, square_sum(c, k, {&E}, st), st);
+    CtB num = ct_new(c, w.B, w.level, w.scale), den = ct_new(c, w.B, w.level, w.scale);
+    ct_mul_plain(c, num, w, plan_const(p, MMFHE_CONST_IDX, 0, 0), false, st);
+    ct_mul_plain(c, den, w, plan_const(p, MMFHE_CONST_ONE, 0, 0), false, st);
+    std::vector<CtB> outs;
+    outs.push_back(rotsum(c, k, rescale(c, num, st), 1, span, st));
+    outs.push_back(rotsum(c, k, rescale(c, den, st), 1, span, st));
+    // K4 soft I/Q per frame
+    std::vector<CtB> I, Q;
+    for (int t = 0; t < F; t++) {
+        const CtB &re = in[2 * F + 2 * t], &im = in[2 * F + 2 * t + 1];
+        CtB pp = rescale(c, square_sum(c, k, {&re, &im}, st), st);
+        CtB m = rescale(c, square_sum(c, k, {&pp}, st), st);
+        for (int part = 0; part < 2; part++) {
+            CtB x = ct_drop(c, part == 0 ? re : im, m.level, st);
+            TensorB tt = tensor_new(c, m.B, m.level);
+            tensor_acc(c, tt, m, x, 1, true, st);
+            (part == 0 ? I : Q).push_back(rotsum(c, k, rescale(c, relin(c, k, tt, st), st), 1, span, st));
+        }
+    }
+    std::map<int, CtB> S;
+    for (int b = 0; b < 2; b++) {
+        // K5 causal FIR over frames
+        std::vector<CtB> If, Qf;
+        for (int t = 0; t < F; t++) {
+            for (int part = 0; part < 2; part++) {
+                const std::vector<CtB> &X = part == 0 ? I : Q;
+                std::vector<std::pair<const CtB *, double>> terms;
+                for (int kk = 0; kk < T && t - kk >= 0; kk++) terms.push_back({&X[t - kk], taps[b][kk]});
+                (part == 0 ? If : Qf).push_back(rescale(c, lincomb(c, terms, qs(X[0].level), st), st));
+            }
+        }
+        // K7 third order, frames t >= 1 (dphi[0] = 0)
+        std::vector<CtB> dphi(F);
+        for (int t = 1; t < F; t++) {
+            TensorB ty = tensor_new(c, If[t].B, If[t].level);
+            tensor_acc(c, ty, Qf[t], If[t - 1], 1, true, st);
+            tensor_acc(c, ty, If[t], Qf[t - 1], -1, false, st);
+            CtB y = rescale(c, relin(c, k, ty, st), st);
+            TensorB tx = tensor_new(c, If[t].B, If[t].level);
+            tensor_acc(c, tx, If[t], If[t - 1], 1, true, st);
+            tensor_acc(c, tx, Qf[t], Qf[t - 1], 1, false, st);
+            CtB x = rescale(c, relin(c, k, tx, st), st);
+            TensorB tu = tensor_new(c, x.B, x.level);
+            tensor_acc(c, tu, x, x, 3, true, st);
+            tensor_acc(c, tu, y, y, -1, false, st);
+            CtB u = rescale(c, relin(c, k, tu, st), st);
+            CtB yd = ct_drop(c, y, u.level, st);
+            TensorB tp = tensor_new(c, u.B, u.level);
+            tensor_acc(c, tp, yd, u, 1, true, st);
+            dphi[t] = rescale(c, relin(c, k, tp, st), st);
+        }
+        // K3 narrowband DFT per bin, |X|^2, square (bands are disjoint in k)
+        for (size_t kk = 0; kk < p.bands[b].size(); kk++) {
+            std::vector<std::pair<const CtB *, double>> tre, tim;
+            for (int t = 1; t < F; t++) {
+                tre.push_back({&dphi[t], cre[b][kk][t - 1]});
+                tim.push_back({&dphi[t], cim[b][kk][t - 1]});
+            }
+            const double s = qs(dphi[1].level);
+            CtB xr = rescale(c, lincomb(c, tre, s, st), st);
+            CtB xi = rescale(c, lincomb(c, tim, s, st), st);
+            CtB pk = rescale(c, square_sum(c, k, {&xr, &xi}, st), st);
+            S[p.bands[b][kk]] = rescale(c, square_sum(c, k, {&pk}, st), st);
+        }
+    }
+    for (int b = 0; b < 2; b++) {
+        std::vector<std::pair<const CtB *, double>> tn, td;
+        for (size_t kk = 0; kk < p.bands[b].size(); kk++) {
+            tn.push_back({&S[p.bands[b][kk]], fhz[b][kk]});
+            td.push_back({&S[p.bands[b][kk]], 1.0});
+        }
+        const double s = qs(S[p.bands[b][0]].level);
+        outs.push_back(rescale(c, lincomb(c, tn, s, st), st));
+        outs.push_back(rescale(c, lincomb(c, td, s, st), st));
+    }
+    return outs;
+}
+
+void plan_set_scalars(Plan &p, const double *v, size_t n) {
+    if (p.cfg.kind != MMFHE_CIRCUIT_VITAL_PER_FRAME) throw Error(MMFHE_ERR_BAD_ARG, "only per-frame plans hold scalars");
+    if (n != p.scalars.size()) throw Error(MMFHE_ERR_BAD_ARG, "wrong number of scalars");
+    p.scalars.assign(v, v + n);
+}
+
 std::vector<CtB> run_plan(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st) {
     if (p.cfg.kind == MMFHE_CIRCUIT_FC) return run_fc(c, p, k, in, st);
+    if (p.cfg.kind == MMFHE_CIRCUIT_VITAL_PER_FRAME) return run_vital_per_frame(c, p, k, in, st);
     if (p.cfg.kind == MMFHE_CIRCUIT_FIR_DFT) return run_fir_dft(c, p, k, in, st);
     return run_vital(c, p, k, in, st);
 }

@@ -22,6 +22,7 @@ struct Plan {
     std::vector<int32_t> rotations;
     int n_in = 0;
     std::vector<int> out_levels;
+    std::vector<double> scalars;                // per-frame chain: public scalar constants
 };
 
 uint64_t key_of(const mmfhe_const_key &k);
@@ -34,6 +35,7 @@ const PtDev &plan_const(const Plan &p, uint32_t tag, uint32_t band, uint32_t idx
 void plan_set_const(Plan &p, uint32_t i, const uint64_t *words, cudaStream_t st);
 void plan_encode_consts(Plan &p, cudaStream_t st);
 void plan_set_fc_layer(Plan &p, uint32_t layer, const double *W);
+void plan_set_scalars(Plan &p, const double *v, size_t n);
 std::vector<int> fc_present(const mmfhe_circuit_config &cfg, int l);
 std::vector<CtB> run_plan(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st);
 

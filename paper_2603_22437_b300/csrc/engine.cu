@@ -7,6 +7,7 @@
 // one-element set: the Galois automorphism is applied to the ModUp digits
 // inside the key inner product and to c0 inside the ModDown combine.
 #include <algorithm>
+#include <cmath>
 #include <map>
 
 #include "engine.h"
@@ -276,6 +277,33 @@ CtB rotate_add(Context &c, const Keys &k, const CtB &a, int32_t rot, const CtB &
     DigitsB dg = modup(c, a.ptr() + (size_t)nl * c.n, (size_t)2 * nl, a.B, a.level, st);
     return keyswitch_moddown(c, dg, key, galois_elt(c, nr), a.ptr(), nullptr, (size_t)2 * nl * c.n, a.scale, st,
                              &plus);
+}
+
+CtB lincomb(Context &c, const std::vector<std::pair<const CtB *, double>> &terms, double scale, cudaStream_t st) {
+    if (terms.empty()) throw Error(MMFHE_ERR_BAD_ARG, "lincomb of no terms");
+    const CtB &x0 = *terms[0].first;
+    const int nl = x0.level + 1;
+    CtB out = ct_new(c, x0.B, x0.level, x0.scale * scale);
+    const size_t chunk = (size_t)std::min(MAX_SUM_TERMS, c.sum_terms_max);
+    for (size_t t0 = 0; t0 < terms.size(); t0 += chunk) {
+        LincombTerms lt{};
+        lt.n = (int)std::min(chunk, terms.size() - t0);
+        for (int j = 0; j < lt.n; j++) {
+            const CtB &x = *terms[t0 + j].first;
+            if (x.level != x0.level || x.B != x0.B) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "lincomb: operands differ");
+            lt.ct[j] = x.ptr();
+            // round half away from zero, as the encoder does
+            const double v = std::round(scale * terms[t0 + j].second);
+            const long long m = (long long)v;
+            for (int i = 0; i < nl; i++) {
+                const uint64_t q = c.primes[i];
+                const uint64_t r = m >= 0 ? (uint64_t)m % q : (q - ((uint64_t)(-m) % q)) % q;
+                lt.s[j][i] = (uint64_t)(((unsigned __int128)r * c.mods.r64[i]) % q);   // Montgomery form
+            }
+        }
+        k_launch_lincomb(c, out.ptr(), lt, x0.B, x0.level, t0 > 0, st);
+    }
+    return out;
 }
 
 CtB rotsum(Context &c, const Keys &k, const CtB &a, int32_t stride, uint32_t span, cudaStream_t st) {

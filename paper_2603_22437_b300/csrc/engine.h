@@ -59,6 +59,11 @@ std::vector<CtB> rotate_hoisted(Context &c, const Keys &k, const CtB &a, const s
                                 cudaStream_t st);
 CtB rotsum(Context &c, const Keys &k, const CtB &a, int32_t stride, uint32_t span, cudaStream_t st);
 
+// sum_i c_i * x_i for real constants c_i, each encoded at `scale` as the
+// constant polynomial round(scale c_i) (an exact integer multiply); all x_i
+// at one level and batch; not rescaled; result scale x.scale * scale.
+CtB lincomb(Context &c, const std::vector<std::pair<const CtB *, double>> &terms, double scale, cudaStream_t st);
+
 // One BSGS operand: baby rotations of an input (baby[i] = Rot(x, baby_idx[i] * stride))
 // and the diagonals it is multiplied with, keyed by delta = g*n1 + b.
 struct BsgsTerm {

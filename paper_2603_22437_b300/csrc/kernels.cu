@@ -349,6 +349,21 @@ __global__ void k_mul_plain_sum(uint64_t *out, SumTerms terms, size_t words, int
     }
 }
 
+// out[w] (+)= sum_k ct_k[w] * s_k[row(w)]: a linear combination of ciphertext
+// batches with scalar constants (constant polynomials: the same residue at
+// every position of a limb), the scalars in Montgomery form, one reduction.
+__global__ void k_lincomb(uint64_t *out, LincombTerms terms, size_t words, int logn, int nl, ModTab mt,
+                          int accumulate) {
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < words; w += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)((w >> logn) % nl);
+        const uint64_t q = mt.q[i], qinv = mt.qinv[i];
+        uint64_t hi = 0, lo = 0;
+        for (int t = 0; t < terms.n; t++) mm::mac128(hi, lo, __ldg(terms.ct[t] + w), terms.s[t][i]);
+        const uint64_t v = mm::redc(hi, lo, q, qinv);
+        out[w] = accumulate ? mm::add_mod(out[w], v, q) : v;
+    }
+}
+
 // Automorphism of whole rows in the evaluation domain.
 __global__ void k_permute(uint64_t *out, const uint64_t *in, size_t rows, int logn, uint32_t galois) {
     const uint32_t n = 1u << logn;
@@ -504,6 +519,17 @@ void k_launch_mul_plain_sum(Context &c, uint64_t *out, const SumTerms &terms, in
     // reads every term once, its constant once, writes (and reads, when accumulating) the output
     double bytes = W8(words * (terms.n + (acc ? 2 : 1)) + (size_t)terms.n * nl * c.n);
     LAUNCH(c, "mul_plain_sum", bytes, g, k_mul_plain_sum, out, terms, words, c.logn, nl, c.mods, acc ? 1 : 0);
+}
+
+void k_launch_lincomb(Context &c, uint64_t *out, const LincombTerms &terms, int B, int level, bool acc,
+                      cudaStream_t st) {
+    const int nl = level + 1;
+    const size_t words = (size_t)B * 2 * nl * c.n;
+    if (!words || terms.n == 0) return;
+    if (terms.n > c.sum_terms_max) throw Error(MMFHE_ERR_BAD_ARG, "lincomb: too many terms for one reduction");
+    dim3 g = grid_for(words);
+    LAUNCH(c, "lincomb", W8(words * (terms.n + (acc ? 2 : 1))), g, k_lincomb, out, terms, words, c.logn, nl, c.mods,
+           acc ? 1 : 0);
 }
 
 void k_launch_permute(Context &c, uint64_t *out, const uint64_t *in, size_t rows, uint32_t galois, cudaStream_t st) {

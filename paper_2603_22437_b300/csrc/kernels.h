@@ -102,4 +102,15 @@ struct SumTerms {
 void k_launch_mul_plain_sum(Context &c, uint64_t *out, const SumTerms &terms, int B, int level, bool acc,
                             cudaStream_t st);
 
+// Linear combination with scalar constants: out (+)= sum_k s_k * ct_k over a
+// batch at one level, s_k[i] = the scalar's residue mod q_i in Montgomery
+// form; at most Context::sum_terms_max terms per launch.
+struct LincombTerms {
+    const uint64_t *ct[MAX_SUM_TERMS];
+    uint64_t s[MAX_SUM_TERMS][MMFHE_MAX_Q];
+    int n;
+};
+void k_launch_lincomb(Context &c, uint64_t *out, const LincombTerms &terms, int B, int level, bool acc,
+                      cudaStream_t st);
+
 }  // namespace mmfhe
