@@ -159,17 +159,65 @@ __global__ void k_modup_bconv(uint64_t *out, const uint64_t *coef, const uint64_
 
 // Key inner product fused with the Galois permutation of the digits:
 //   u_h[b][t][x] = sum_j digits[b][j][t][pi(x)] * key[j][h][krow(t)][x]
-// Each thread owns (t, x) for a group of WG windows: a key word is read once
-// per group (from L2 after the first group), and the group's digit words are
-// loaded together.  WG is picked by the autotuner (1, 2, 4 or 8).  PW: every
-// window has its own key (a batch mixing users), key.k[b] for window b.
-template <int WG, bool PW>
+// A thread owns (t, x); the digit words of WG windows are loaded together.
+// One key for every window: the thread holds the beta key words and walks all
+// windows, so the key is read once per launch.  PW (a batch mixing users,
+// key.k[b] for window b): a thread owns (t, x) for one group of WG windows.
+// WG is picked by the autotuner (1, 2, 4 or 8).
+template <int WG, bool PW, int KB>
 __global__ void __launch_bounds__(EW_THREADS, WG <= 2 ? 4 : (WG == 4 ? 3 : 2))
     k_keyip(uint64_t *u, const uint64_t *digits, const uint64_t *own, size_t own_stride, size_t own_jstride,
             KeyPtrs key, int B, int level, int beta, int alpha, int nrows_ext, int key_rows, int L1, int logn,
             uint32_t galois, ModTab mt, int pid_p0) {
     const uint32_t n = 1u << logn;
     const size_t per_group = (size_t)nrows_ext * n;
+    if (!PW) {
+        // one key for every window: a thread keeps the beta key word pairs of
+        // its (t, x) in registers and walks all windows, WG at a time, so the
+        // key is read from memory once per launch
+        for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < per_group;
+             w += (size_t)gridDim.x * blockDim.x) {
+            const uint32_t x = (uint32_t)(w & (n - 1));
+            const int t = (int)(w >> logn);
+            const int pid = t <= level ? t : pid_p0 + (t - level - 1);
+            const int krow = t <= level ? t : L1 + (t - level - 1);
+            const uint32_t px = galois == 1 ? x : mm::galois_perm(x, galois, logn);
+            const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
+            const int jown = t <= level ? t / alpha : -1;
+            uint64_t kb[KB], ka[KB];   // beta <= KB
+#pragma unroll
+            for (int j = 0; j < KB; j++) {
+                kb[j] = j < beta ? key.k[0][(((size_t)j * 2 + 0) * key_rows + krow) * n + x] : 0;
+                ka[j] = j < beta ? key.k[0][(((size_t)j * 2 + 1) * key_rows + krow) * n + x] : 0;
+            }
+            for (int b0 = 0; b0 < B; b0 += WG) {
+                uint64_t h0[WG] = {}, l0[WG] = {}, h1[WG] = {}, l1[WG] = {};
+#pragma unroll
+                for (int j = 0; j < KB; j++) {
+                    if (j >= beta) break;
+                    const uint64_t *src = j == jown ? own + j * own_jstride + (size_t)t * n + px
+                                                    : digits + ((size_t)j * nrows_ext + t) * n + px;
+                    const size_t wstride = j == jown ? own_stride : (size_t)beta * nrows_ext * n;
+                    uint64_t dv[WG];
+#pragma unroll
+                    for (int k = 0; k < WG; k++) dv[k] = b0 + k < B ? src[(size_t)(b0 + k) * wstride] : 0;
+#pragma unroll
+                    for (int k = 0; k < WG; k++) {
+                        mm::mac128(h0[k], l0[k], dv[k], kb[j]);
+                        mm::mac128(h1[k], l1[k], dv[k], ka[j]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < WG; k++) {
+                    if (b0 + k >= B) break;
+                    uint64_t *U = u + ((size_t)(b0 + k) * 2 * nrows_ext) * n;
+                    U[(size_t)t * n + x] = mm::redc(h0[k], l0[k], q, qinv);
+                    U[((size_t)nrows_ext + t) * n + x] = mm::redc(h1[k], l1[k], q, qinv);
+                }
+            }
+        }
+        return;
+    }
     const size_t total = per_group * (size_t)((B + WG - 1) / WG);
     for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
         const int b0 = (int)(w / per_group) * WG;
@@ -331,7 +379,8 @@ __global__ void k_rescale_combine(uint64_t *out, const uint64_t *c, const uint64
 }
 
 // out[w] (+)= sum_k ct_k[w] * pt_k[row(w)][x]: one read of every term, one
-// write of the output (the BSGS inner sum of a giant step).
+// write of the output (the BSGS inner sum of a giant step).  The constants of
+// a giant step stay in L2 across the batch.
 __global__ void k_mul_plain_sum(uint64_t *out, SumTerms terms, size_t words, int logn, int nl, ModTab mt,
                                 int accumulate) {
     const uint32_t n = 1u << logn;
@@ -455,14 +504,16 @@ void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint6
     int nre = level + 1 + c.num_p;
     size_t work = (size_t)nre * c.n;
     const int wg = c.tune.keyip_wg;
-    dim3 g = grid_for(work * (size_t)((B + wg - 1) / wg));
+    // shared key: one thread per (t, x) walks the windows; per-window keys: one per (t, x, window group)
+    dim3 g = grid_for(pw ? work * (size_t)((B + wg - 1) / wg) : work);
     // reads: B*beta digit rows + beta*2 key rows (per window when mixing users); writes: B*2 output rows
     double bytes = W8(work * ((size_t)B * beta + 2 * beta * (size_t)key.n + 2 * B));
     auto go = [&](auto wg_c, auto pw_c) {
         constexpr int WG = decltype(wg_c)::value;
         constexpr bool PW = decltype(pw_c)::value;
         kernel_begin(c, st);
-        k_keyip<WG, PW><<<g, EW_THREADS, 0, st>>>(u, digits, own, own_stride, own_jstride, key, B, level, beta, c.alpha,
+        auto kern = beta <= 4 ? k_keyip<WG, PW, 4> : k_keyip<WG, PW, MAX_DNUM>;
+        kern<<<g, EW_THREADS, 0, st>>>(u, digits, own, own_stride, own_jstride, key, B, level, beta, c.alpha,
                                                   nre, c.num_q + c.num_p, c.num_q, c.logn, galois, c.mods, c.num_q);
         kernel_end(c, "keyip", g, dim3(EW_THREADS), bytes, st);
         CK(cudaGetLastError());
