@@ -221,6 +221,10 @@ class Evaluator:
         self._t("add", a.level)
         return ck.add(self.P, a, b)
 
+    def add_plain(self, a, pt):
+        self._t("add_plain", a.level)
+        return ck.add_plain(self.P, a, pt)
+
     def mul_plain(self, a, pt):
         self._t("mul_plain", a.level)
         return ck.mul_plain(self.P, a, pt)
@@ -330,6 +334,9 @@ class CountingEvaluator(Evaluator):
         return [_Shape(a.level) for _ in ks]
 
     def add(self, a, b):
+        return _Shape(a.level)
+
+    def add_plain(self, a, pt):
         return _Shape(a.level)
 
     def mul_plain(self, a, pt):
@@ -932,3 +939,234 @@ class PerFrameVitalCircuit:
             outs.append(ev.rescale(ev.lincomb([(S[k], 1.0) for k in ks], q[lv])))
         return outs
 
+
+
+# ---------------------------------------------------------------------------
+# Gesture chain (Sec. "Example Pipelines", Encrypted Dynamic Radar
+# Classification; depth accounting of Table 1, pipeline 2): per frame K3
+# Doppler DFT -> K1 power map -> K6 notch -> K2 soft power (gamma = 4) ->
+# feature weighting p x w; frame accumulation; FC1^2 -> FC2^2 -> FC3.
+#
+# Slot layout (Sec. "Packing"): within a frame, antenna a, range bin r and
+# chirp c sit in slot a R D + r D + c; the A R D slots are padded to
+# ARD_pad = 2^ceil(log2(A R D)) and k = (N/2) / ARD_pad frames share one
+# ciphertext pair (frame f in pair f // k at offset (f mod k) ARD_pad).
+#
+# Readings (restated in the design notes): the notch of Eq. (notch mask)
+# zeroes d in the closed range [floor(D/2), ceil(D/2)] (the half-open range
+# printed is empty for even D; the closed one is the zero-Doppler bin D/2
+# after the fftshift); the weighted feature is p (.) w with p the notched
+# power map and w = p^4 (both ciphertexts); FC1 reads every feature slot
+# (hybrid diagonal method: width extended diagonals, then a rotate-and-sum
+# over the ARD_pad / width blocks of a period); its bias and the constant 1
+# of slot width-1 (biases of later layers) are one plaintext added after
+# FC1's rescale, encoded at the ciphertext's scale.
+# ---------------------------------------------------------------------------
+@dataclass
+class GestureConfig:
+    antennas: int = 4           # A (virtual antennas)
+    bins: int = 64              # R range bins
+    chirps: int = 32            # D chirps = Doppler bins
+    frames: int = 60            # F
+    fc_dims: tuple = (31, 16, 6)  # d_1, d_2, classes (d_0 = A R D feature slots)
+    width: int = 32             # slot period of the FC layers after FC1
+
+    @property
+    def ard(self):
+        return self.antennas * self.bins * self.chirps
+
+
+def notch_mask(D):
+    """m[d] of Eq. (notch mask), read as zero on [floor(D/2), ceil(D/2)]."""
+    m = np.ones(D)
+    m[D // 2: -(-D // 2) + 1] = 0.0
+    return m
+
+
+class GestureLayout:
+    def __init__(self, slots, cfg):
+        self.cfg = cfg
+        self.ard_pad = next_pow2(cfg.ard)
+        assert self.ard_pad <= slots
+        self.k = slots // self.ard_pad           # frames per ciphertext pair
+        self.pairs = -(-cfg.frames // self.k)
+        self.slots = slots
+
+    def pack(self, zt):
+        """zt [F, A, R, D] complex -> list of (re, im) slot vectors."""
+        cfg = self.cfg
+        out = []
+        for p in range(self.pairs):
+            re, im = np.zeros(self.slots), np.zeros(self.slots)
+            for j in range(self.k):
+                f = p * self.k + j
+                if f < cfg.frames:
+                    v = zt[f].reshape(-1)
+                    re[j * self.ard_pad: j * self.ard_pad + cfg.ard] = v.real
+                    im[j * self.ard_pad: j * self.ard_pad + cfg.ard] = v.imag
+            out.append((re, im))
+        return out
+
+    def active(self):
+        """1 on the A R D feature slots of every frame position."""
+        v = np.zeros(self.slots)
+        for j in range(self.k):
+            v[j * self.ard_pad: j * self.ard_pad + self.cfg.ard] = 1.0
+        return v
+
+
+class GestureCircuit:
+    def __init__(self, P, cfg=GestureConfig()):
+        self.P, self.cfg = P, cfg
+        self.lay = GestureLayout(P.slots, cfg)
+        D, W = cfg.chirps, cfg.width
+        assert W & (W - 1) == 0 and max(cfg.fc_dims) < W and W <= self.lay.ard_pad
+        assert len(cfg.fc_dims) == 3 and P.L >= 11, "depth-11 chain"
+        self.n1, _ = bsgs_split(2 * D)           # K3: deltas -(D-1) .. D-1
+        self.deltas = list(range(-(D - 1), D))
+        self.nf1, _ = bsgs_split(W)              # FC layers
+        self.fc_tail = FcCircuit.__new__(FcCircuit)   # layers 2 and 3 on period W
+        self.fc_tail.P, self.fc_tail.D = P, W
+        self.fc_tail.cfg = FcConfig(dims=tuple(cfg.fc_dims), width=W)
+        self.fc_tail.layers = 2
+        self.fc_tail.n1, self.fc_tail.n2 = bsgs_split(W)
+        L = P.L
+        # levels (Table 1): K3 L->L-1, |z|^2 ->L-2, notch ->L-3, two squares
+        # ->L-5, weighting ->L-6, FC1 ->L-7, square ->L-8, FC2 ->L-9, square
+        # ->L-10, FC3 ->L-11
+        self.lv_dft, self.lv_notch, self.lv_fc1 = L, L - 2, L - 6
+        self.lv_fc = [L - 6, L - 8, L - 10]
+
+    # -- public constants --------------------------------------------------
+    def doppler_diagonal(self, M, delta):
+        """diag_delta[s] = M[i][i + delta], i = s mod D, on active slots whose
+        block holds column i + delta (block-diagonal I (x) M of Eq. K3)."""
+        D = self.cfg.chirps
+        i = np.arange(self.P.slots) % D
+        j = i + delta
+        ok = (j >= 0) & (j < D)
+        v = np.zeros(self.P.slots)
+        v[ok] = M[i[ok], j[ok]]
+        return v * self.lay.active()
+
+    def fc1_diagonal(self, W0, k):
+        """Extended diagonal k of FC1 (W0: width x (A R D), no bias column):
+        diag_k[s] = W0[s mod width][(s + k) mod ARD_pad] (zero on padding
+        columns)."""
+        P, cfg, n = self.P, self.cfg, self.lay.ard_pad
+        s = np.arange(P.slots)
+        col = (s + k) % n
+        v = np.zeros(P.slots)
+        ok = col < cfg.ard
+        v[ok] = W0[s[ok] % cfg.width, col[ok]]
+        return v
+
+    def fc1_out_scale(self, scale_in):
+        """Scale of FC1's rescaled output, following the evaluator's scale
+        arithmetic step by step (products multiply scales, a rescale at
+        level l divides by q_l, constants carry scale q_l)."""
+        q, L = self.P.q, self.P.L
+        s = scale_in * q[L] / q[L]                 # K3
+        s = s * s / q[L - 1]                       # |z|^2
+        p = s * q[L - 2] / q[L - 2]                # notch
+        w = p * p / q[L - 3]
+        w = w * w / q[L - 4]                       # gamma = 4
+        f = p * w / q[L - 5]                       # weighting
+        return f * q[L - 6] / q[L - 6]             # FC1
+
+    def constants(self, mats, scale_in=None):
+        """mats[0]: width x (A R D + 1) (bias last); mats[1], mats[2]:
+        width x width in the FC layout (bias column width-1)."""
+        P, cfg, q = self.P, self.cfg, self.P.q
+        L = P.L
+        Wd = dft_kernel(cfg.chirps)
+        C, S = Wd.real, Wd.imag
+        out = {}
+        for delta in self.deltas:
+            g = delta // self.n1
+            for tag, M in (("gdft_c", C), ("gdft_s", S), ("gdft_ms", -S)):
+                v = prerotate(self.doppler_diagonal(M, delta), g, self.n1, 1)
+                out[(tag, delta)] = ck.encode(P, v, q[L], L)
+        m = np.tile(notch_mask(cfg.chirps), P.slots // cfg.chirps) * self.lay.active()
+        out[("notch",)] = ck.encode(P, m, q[L - 2], L - 2)
+        W0 = np.asarray(mats[0], dtype=np.float64)
+        assert W0.shape == (cfg.width, cfg.ard + 1)
+        lv = self.lv_fc[0]
+        for k in range(cfg.width):
+            v = prerotate(self.fc1_diagonal(W0[:, :cfg.ard], k), k // self.nf1, self.nf1, 1)
+            out[("fcw", 0, k)] = ck.encode(P, v, q[lv], lv)
+        b = W0[:, cfg.ard].copy()
+        b[cfg.width - 1] = 1.0
+        s_out = self.fc1_out_scale(P.scale if scale_in is None else scale_in)
+        out[("fcb",)] = ck.encode(P, np.tile(b, P.slots // cfg.width), s_out, lv - 1)
+        for l in (1, 2):
+            lv = self.lv_fc[l]
+            for k in self.fc_tail.present(l - 1):
+                v = prerotate(self.fc_tail.diagonal(mats[l], k), k // self.nf1, self.nf1, 1)
+                out[("fcw", l, k)] = ck.encode(P, v, q[lv], lv)
+        return out
+
+    def rotations(self):
+        P, cfg, lay = self.P, self.cfg, self.lay
+        ks = set(range(1, self.n1))
+        ks |= {(d // self.n1) * self.n1 for d in self.deltas}
+        ks |= {lay.ard_pad << i for i in range(int(math.log2(lay.k)))}
+        ks |= set(range(1, self.nf1)) | {g * self.nf1 for g in range(1, cfg.width // self.nf1)}
+        ks |= {cfg.width << i for i in range(int(math.log2(lay.ard_pad // cfg.width)))}
+        return sorted({k % P.slots for k in ks} - {0})
+
+    # -- the circuit ---------------------------------------------------------
+    def features(self, ev, consts, pairs):
+        """K3 -> K1 -> K6 -> soft power -> weighting per pair, then the
+        accumulation over every frame; returns the feature ciphertext
+        (every frame position of it holds the sum) at level L - 6."""
+        acc = None
+        for re, im in pairs:
+            babies = {"re": ev.hoisted(re, list(range(self.n1))), "im": ev.hoisted(im, list(range(self.n1)))}
+            c_re = {}
+            c_im = {}
+            for delta in self.deltas:
+                c_re[("re", delta)] = consts[("gdft_c", delta)]
+                c_re[("im", delta)] = consts[("gdft_ms", delta)]
+                c_im[("re", delta)] = consts[("gdft_s", delta)]
+                c_im[("im", delta)] = consts[("gdft_c", delta)]
+            d_re = ev.rescale(ev.bsgs(babies, c_re, self.n1, 1, re.level))
+            d_im = ev.rescale(ev.bsgs(babies, c_im, self.n1, 1, re.level))
+            p = ev.rescale(ev.square_sum([d_re, d_im]))            # K1
+            p = ev.rescale(ev.mul_plain(p, consts[("notch",)]))    # K6
+            w = ev.rescale(ev.square_sum([p]))                     # K2, gamma = 4
+            w = ev.rescale(ev.square_sum([w]))
+            f = ev.rescale(ev.relin(ev.tensor(ev.drop(p, w.level), w)))   # p x w
+            acc = f if acc is None else ev.add(acc, f)
+        return ev.rotsum(acc, self.lay.ard_pad, self.lay.k)
+
+    def run(self, ev, consts, pairs):
+        """pairs: the window's (re, im) ciphertexts at the top level.
+        Returns the logits ciphertext (level L - 11, logits in slots
+        0..classes-1 of every width-slot period)."""
+        cfg = self.cfg
+        x = self.features(ev, consts, pairs)
+        babies = {"x": ev.hoisted(x, list(range(self.nf1)))}
+        cl = {("x", k): consts[("fcw", 0, k)] for k in range(cfg.width)}
+        y = ev.rescale(ev.bsgs(babies, cl, self.nf1, 1, x.level))
+        y = ev.rotsum(y, cfg.width, self.lay.ard_pad // cfg.width)
+        y = ev.add_plain(y, consts[("fcb",)])
+        x = ev.rescale(ev.square_sum([y]))
+        for l in (1, 2):
+            babies = {"x": ev.hoisted(x, list(range(self.nf1)))}
+            cl = {("x", k): consts[("fcw", l, k)] for k in self.fc_tail.present(l - 1)}
+            y = ev.rescale(ev.bsgs(babies, cl, self.nf1, 1, x.level))
+            x = ev.rescale(ev.square_sum([y])) if l == 1 else y
+        return x
+
+
+def gesture_forward(mats, feat, cfg):
+    """FP64 forward pass of the same network on the accumulated features
+    feat [A, R, D] (slot order a R D + r D + d)."""
+    W0 = np.asarray(mats[0], dtype=np.float64)
+    v = W0[:, : cfg.ard] @ feat.reshape(-1) + W0[:, cfg.ard]
+    v[cfg.width - 1] = 1.0
+    v = v * v
+    v = np.asarray(mats[1], dtype=np.float64) @ v
+    v = v * v
+    return np.asarray(mats[2], dtype=np.float64) @ v

@@ -283,6 +283,14 @@ def add(P, a, b):
     return Ciphertext(ring_add(a.c0, b.c0, pr), ring_add(a.c1, b.c1, pr), a.level, a.scale)
 
 
+def add_plain(P, a, pt):
+    """ct + pt: the plaintext joins c0; pt must be encoded at the
+    ciphertext's scale and level."""
+    assert a.level == pt.level and abs(pt.scale / a.scale - 1.0) < 1e-9
+    pr = q_primes(P, a.level)
+    return Ciphertext(ring_add(a.c0, pt.m, pr), a.c1.copy(), a.level, a.scale)
+
+
 def sub(P, a, b):
     assert a.level == b.level
     pr = q_primes(P, a.level)

@@ -184,3 +184,10 @@ def fc_params():
     primes, two 60-bit special primes, dnum = 3 (alpha = 2);
     log QP ~ 380 <= 438 (HE Standard, N = 2^14, 128-bit classical)."""
     return make_params(14, 6, 60, 40, 2, 60, 3, 40)
+
+
+def gesture_params():
+    """Gesture chain: N = 2^15, depth 11 (12 Q primes: 60 + 11 x 50 bits,
+    Delta = 2^50), four 60-bit special primes, dnum = 3 (alpha = 4);
+    log QP ~ 850 <= 881."""
+    return make_params(15, 12, 60, 50, 4, 60, 3, 50)

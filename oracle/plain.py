@@ -9,10 +9,16 @@ K3 narrowband windowed DFT, |X|^2, merge + square, weighted frequency
 average.  Client preprocessing (Sec. "Pre-Cloud Client-Side Algorithms"):
 clutter removal by mean subtraction over frames, then normalisation --
 stream 1 by the window maximum, stream 2 frame by frame.
+
+The gesture chain (Sec. "Example Pipelines", pipeline 2 of Table 1) on
+[frames x antennas x bins x chirps] arrays: K3 windowed fftshifted Doppler
+DFT per (frame, antenna, bin), K1 power, K6 notch, w = p^4, feature p w,
+summed over frames.  Its client preprocessing: mean subtraction over frames,
+then one window-global scale so every Doppler value has |d| <= 1.
 """
 import numpy as np
 
-from .circuits import VitalConfig, band_bins, fir_bandpass, hann
+from .circuits import GestureConfig, VitalConfig, band_bins, dft_kernel, fir_bandpass, hann, notch_mask
 
 
 def preprocess(z):
@@ -66,3 +72,22 @@ def main_chain(s2, cfg=VitalConfig()):
         bd["den"] = float(sum(S[k] for k in ks))
         bd["bpm"] = 60.0 * bd["num"] / bd["den"]
     return out
+
+
+def gesture_preprocess(z):
+    """z [F, A, R, D] complex -> clutter-removed, scaled frames: divided by
+    max |z~| times sum_n w[n] (the DFT's window gain) so |d| <= 1."""
+    zt = z - z.mean(axis=0, keepdims=True)
+    D = z.shape[-1]
+    return zt / (np.abs(zt).max() * hann(D).sum())
+
+
+def gesture_features(zt, cfg=GestureConfig()):
+    """Accumulated weighted features [A, R, D] and the intermediates."""
+    W = dft_kernel(cfg.chirps)
+    d = np.einsum("kn,farn->fark", W, zt)          # K3 per (frame, antenna, bin)
+    p = d.real ** 2 + d.imag ** 2                  # K1
+    p = p * notch_mask(cfg.chirps)                 # K6
+    w = p ** 4                                     # soft power, gamma = 4
+    f = p * w                                      # feature weighting
+    return {"d": d, "p": p, "w": w, "f": f, "feat": f.sum(axis=0)}

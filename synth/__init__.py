@@ -190,6 +190,91 @@ def gesture_features(seed, frames=60, fs=20.0, rbins=56, dbins=32, segs=4):
     return np.log1p(np.concatenate(f)), cls
 
 
+# ---------------------------------------------------------------------------
+# Synthetic gesture windows (range-profile level: the cloud's encrypted input)
+# ---------------------------------------------------------------------------
+GESTURE_CARRIER_HZ = 60.5e9          # BGT60TR13C-class 60 GHz radar
+GESTURE_LAMBDA_M = C_LIGHT / GESTURE_CARRIER_HZ
+GESTURE_RANGE_RES_M = 0.0375         # 4 GHz chirp bandwidth
+GESTURE_CHIRP_S = 0.5e-3             # chirp repetition: +-2.5 m/s unambiguous
+
+
+class GestureWindow:
+    """Complex range profiles z[t, a, r, c] (F frames x A antennas x R range
+    bins x D chirps) of one gesture window, with its class label."""
+
+    def __init__(self, z, label, fs):
+        self.z = z
+        self.label = label
+        self.fs = fs
+
+
+def _trajectory(g, cls, frames, fs):
+    """Radial velocity v(t) (m/s) of one of the six gesture classes (push,
+    pull, push-pull, fast oscillation, double tap, hold), speed U(0.2, 1.5)
+    m/s, random start within the first 30 % of the window."""
+    t = np.arange(frames) / fs
+    T = frames / fs
+    speed = g.uniform(0.2, 1.5)
+    ph = g.uniform(0, 2 * np.pi)
+    t0 = g.uniform(0, 0.3 * T)
+    tt = np.clip(t - t0, 0, None)
+    if cls == 0:
+        v = -speed * (tt > 0)
+    elif cls == 1:
+        v = speed * (tt > 0)
+    elif cls == 2:
+        v = speed * np.sin(2 * np.pi * tt / T + ph) * (tt > 0)
+    elif cls == 3:
+        v = speed * np.sin(6 * np.pi * tt / T + ph) * (tt > 0)
+    elif cls == 4:
+        s = np.sin(4 * np.pi * tt / T)
+        v = speed * np.sign(s) * (np.abs(s) > 0.5)
+    else:
+        v = 0.05 * speed * g.normal(size=frames)
+    return v
+
+
+def gesture_window(seed, frames=60, antennas=4, rbins=64, chirps=32, fs=20.0, sigma=1.0):
+    """One 3 s gesture window at the range-FFT output (the paper's client
+    input type (ii)).
+
+    1-3 point scatterers (hand and fingers) follow the class trajectory:
+    range r(t) = r_0 + integral of v, r_0 ~ U(0.25, 0.6) m, each scatterer
+    offset by U(-3, 3) cm in range, its velocity scaled by U(0.9, 1.1) and
+    seen at an angle theta ~ U(-30, 30) degrees.  A scatterer of amplitude a
+    adds, in frame t, antenna k and chirp c, a range response split linearly
+    between the two bins around r / dr with the phase
+    4 pi (r + v T_c c) / lambda + pi k sin(theta).  SNR = a^2 / (2 sigma^2)
+    ~ U(10, 25) dB per sample; every sample gets N(0, sigma^2) noise per real
+    component; two static reflectors (clutter) sit at random bins."""
+    g = rng(seed)
+    cls = int(g.integers(GESTURE_CLASSES))
+    v = _trajectory(g, cls, frames, fs)
+    r = np.clip(g.uniform(0.25, 0.6) + np.cumsum(v) / fs, 0.05, (rbins - 2) * GESTURE_RANGE_RES_M)
+    z = sigma * (g.normal(size=(frames, antennas, rbins, chirps)) + 1j * g.normal(size=(frames, antennas, rbins, chirps)))
+    c = np.arange(chirps)[None, :]
+    k = np.arange(antennas)[:, None]
+    snr_db = g.uniform(10, 25)
+    for _ in range(int(g.integers(1, 4))):
+        a = np.sqrt(2 * sigma ** 2 * 10 ** (snr_db / 10)) * g.uniform(0.5, 1.0)
+        rs = np.clip(r + g.uniform(-0.03, 0.03), 0.0, (rbins - 2) * GESTURE_RANGE_RES_M)
+        vs = v * g.uniform(0.9, 1.1)
+        th = np.deg2rad(g.uniform(-30, 30))
+        pos = rs / GESTURE_RANGE_RES_M
+        b0 = np.floor(pos).astype(int)
+        frac = (pos - b0)[:, None, None]
+        phase = (4 * np.pi * (rs[:, None, None] + vs[:, None, None] * GESTURE_CHIRP_S * c[None]) / GESTURE_LAMBDA_M
+                 + np.pi * k[None] * np.sin(th))
+        sig = a * np.exp(1j * phase)                         # [F, A, D]
+        t = np.arange(frames)
+        z[t, :, b0, :] += (1 - frac) * sig
+        z[t, :, b0 + 1, :] += frac * sig
+    for _ in range(2):                                       # static clutter
+        z[:, :, int(g.integers(rbins)), :] += 30 * sigma * np.exp(1j * g.uniform(0, 2 * np.pi))
+    return GestureWindow(z, cls, fs)
+
+
 def gesture_dataset(first_seed, count):
     X = np.empty((count, GESTURE_FEATURES))
     y = np.empty(count, dtype=np.int32)

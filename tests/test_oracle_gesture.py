@@ -1,0 +1,141 @@
+"""Oracle pins of the gesture chain (K3 Doppler DFT -> K1 -> K6 -> soft
+power gamma = 4 -> weighting -> frame accumulation -> FC1^2 -> FC2^2 -> FC3):
+the FP64 pipeline against numpy's FFT, the notch against its definition, the
+slot-domain BSGS and hybrid FC1 decompositions against dense products, and
+the homomorphic circuit decrypting to the FP64 pipeline."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import ckks as ck
+from oracle import circuits as cc
+from oracle import params as pm
+from oracle import plain
+
+TINY = cc.GestureConfig(antennas=2, bins=4, chirps=8, frames=20, fc_dims=(7, 5, 3), width=16)
+
+
+def tiny_params():
+    """Test-only ring (N = 2^11, no security claim) with the gesture chain's
+    modulus shape: q_0 60 bits + 11 x 50 bits, four 60-bit special primes,
+    dnum = 3."""
+    return pm.make_params(11, 12, 60, 50, 4, 60, 3, 50)
+
+
+def random_gesture_net(cfg, seed):
+    g = np.random.default_rng(seed)
+    W, (d1, d2, c) = cfg.width, cfg.fc_dims
+    W0 = np.zeros((W, cfg.ard + 1))
+    W0[:d1, : cfg.ard] = g.normal(0, 1.0, (d1, cfg.ard))
+    W0[:d1, cfg.ard] = g.normal(0, 0.3, d1)
+    W1 = np.zeros((W, W))
+    W1[:d2, :d1] = g.normal(0, 0.5 / np.sqrt(d1), (d2, d1))
+    W1[:d2, W - 1] = g.normal(0, 0.1, d2)
+    W1[W - 1, W - 1] = 1.0
+    W2 = np.zeros((W, W))
+    W2[:c, :d2] = g.normal(0, 0.5 / np.sqrt(d2), (c, d2))
+    W2[:c, W - 1] = g.normal(0, 0.1, c)
+    W2[W - 1, W - 1] = 1.0
+    return [W0, W1, W2]
+
+
+def tiny_window(seed, cfg=TINY):
+    w = synth.gesture_window(seed, frames=cfg.frames, antennas=cfg.antennas, rbins=cfg.bins, chirps=cfg.chirps)
+    return plain.gesture_preprocess(w.z)
+
+
+def test_doppler_dft_equals_fftshifted_fft():
+    zt = tiny_window(1, cc.GestureConfig())
+    D = zt.shape[-1]
+    ref = np.fft.fftshift(np.fft.fft(zt * cc.hann(D), axis=-1), axes=-1)
+    d = plain.gesture_features(zt)["d"]
+    assert np.allclose(d, ref, atol=1e-12)
+    assert np.abs(d).max() <= 1.0
+
+
+def test_notch_zeroes_exactly_the_zero_doppler_bin():
+    assert list(np.nonzero(cc.notch_mask(32) == 0)[0]) == [16]
+    assert list(np.nonzero(cc.notch_mask(33) == 0)[0]) == [16, 17]
+    # a chirp-constant (zero-Doppler) signal peaks at the notched bin
+    cfg = cc.GestureConfig(antennas=1, bins=1, chirps=32, frames=1)
+    zt = np.ones((1, 1, 1, 32), dtype=complex) / cc.hann(32).sum()
+    r = plain.gesture_features(zt, cfg)
+    assert np.argmax(np.abs(r["d"][0, 0, 0])) == 16
+    assert r["p"][0, 0, 0, 16] == 0.0 and r["p"][0, 0, 0, 15] > 0.0
+
+
+def test_block_diagonal_bsgs_in_the_clear():
+    """Slot-domain restatement of K3's BSGS (diagonals, pre-rotation, floor
+    split of negative deltas) equals I (x) M applied block by block."""
+    P = tiny_params()
+    circ = cc.GestureCircuit(P, TINY)
+    D, n1 = TINY.chirps, circ.n1
+    M = cc.dft_kernel(D).imag
+    v = np.random.default_rng(2).normal(size=P.slots) * circ.lay.active()
+    babies = [cc.rotate_slots(v, b) for b in range(n1)]
+    groups = {}
+    for delta in circ.deltas:
+        dg = cc.prerotate(circ.doppler_diagonal(M, delta), delta // n1, n1, 1)
+        groups.setdefault(delta // n1, []).append(dg * babies[delta % n1])
+    out = sum(cc.rotate_slots(sum(t), g * n1) for g, t in groups.items())
+    ref = (v.reshape(-1, D) @ M.T).reshape(-1) * circ.lay.active()
+    assert np.allclose(out, ref, atol=1e-12)
+
+
+def test_hybrid_fc1_in_the_clear():
+    P = tiny_params()
+    circ = cc.GestureCircuit(P, TINY)
+    mats = random_gesture_net(TINY, 3)
+    W0 = mats[0][:, : TINY.ard]
+    x = np.random.default_rng(4).normal(size=TINY.ard)
+    xs = np.zeros(P.slots)
+    for j in range(circ.lay.k):
+        xs[j * circ.lay.ard_pad: j * circ.lay.ard_pad + TINY.ard] = x
+    t = sum(circ.fc1_diagonal(W0, k) * cc.rotate_slots(xs, k) for k in range(TINY.width))
+    y = t.copy()
+    for i in range(int(np.log2(circ.lay.ard_pad // TINY.width))):
+        y = y + cc.rotate_slots(y, TINY.width << i)
+    assert np.allclose(y, np.tile(W0 @ x, P.slots // TINY.width), atol=1e-9)
+
+
+def test_depth_and_rotations_full_size():
+    P = pm.gesture_params()
+    circ = cc.GestureCircuit(P)
+    assert (circ.lay.k, circ.lay.pairs) == (2, 30)
+    ev = cc.CountingEvaluator(P)
+
+    class Any(dict):
+        def __missing__(self, k):
+            return None
+    pairs = [(cc._Shape(P.L), cc._Shape(P.L)) for _ in range(circ.lay.pairs)]
+    assert circ.run(ev, Any(), pairs).level == 0    # depth 11 (Table 1)
+    assert len(circ.rotations()) == 23
+
+
+def test_gesture_circuit_decrypts_to_fp64():
+    P = tiny_params()
+    circ = cc.GestureCircuit(P, TINY)
+    rots = circ.rotations()
+    kd = synth.KeyDraws(51, P.n, P.q, P.p, P.dnum, rots)
+    sk = ck.SecretKey(P, kd.secret)
+    pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
+    rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
+    gks = {k: ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
+    mats = random_gesture_net(TINY, 5)
+    consts = circ.constants(mats)
+    zt = tiny_window(6)
+    cts = [tuple(ck.encrypt(P, pk, ck.encode(P, v, P.scale, P.L), *synth.encryption_draws(70 + 2 * i + h, P.n))
+                 for h, v in enumerate(pair)) for i, pair in enumerate(circ.lay.pack(zt))]
+    ev = cc.Evaluator(P, rlk, gks)
+    ref = plain.gesture_features(zt, TINY)["feat"]
+    feat = circ.features(ev, consts, cts)
+    assert feat.level == P.L - 6
+    dec = ck.decrypt_decode(P, sk, feat)
+    for j in range(circ.lay.k):
+        got = dec[j * circ.lay.ard_pad: j * circ.lay.ard_pad + TINY.ard]
+        assert np.allclose(got, ref.reshape(-1), atol=1e-9 * max(1.0, np.abs(ref).max()))
+    out = circ.run(ev, consts, cts)
+    assert out.level == 0
+    logits = ck.decrypt_decode(P, sk, out)[: TINY.fc_dims[-1]]
+    want = cc.gesture_forward(mats, ref, TINY)[: TINY.fc_dims[-1]]
+    assert np.allclose(logits, want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
