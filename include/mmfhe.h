@@ -240,6 +240,22 @@ mmfhe_status mmfhe_ct_bsgs(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out
  * alike (4F ciphertexts at the top level).  Same formulas, level schedule and
  * outputs as MMFHE_CIRCUIT_VITAL (third order only), values in slot 0. */
 #define MMFHE_CIRCUIT_VITAL_PER_FRAME 4
+/* The gesture chain (paper Sec. "Example Pipelines", Encrypted Dynamic Radar
+ * Classification; depth 11 per Table 1): per frame K3 windowed fftshifted
+ * Doppler DFT over the D chirps (Eq. K3, block-diagonal BSGS), K1 power, K6
+ * notch (zero on Doppler bins floor(D/2)..ceil(D/2)), soft power w = p^4,
+ * feature p w; sum over frames; FC1 (reads every feature slot) + bias +
+ * square, FC2 + square, FC3.  Slot of antenna a, range bin r, chirp c within
+ * a frame: a R D + r D + c; ARD_pad = 2^ceil(log2(A R D)); k = (N/2) /
+ * ARD_pad frames per ciphertext, frame f in pair f / k at offset
+ * (f mod k) ARD_pad.  Window input: pairs = ceil(F / k) ciphertext pairs,
+ * (Re, Im) of pair 0, then pair 1, ... at the top level (2 pairs inputs).
+ * Output: one ciphertext at level top - 11, logits in slots 0..classes-1 of
+ * every fc_width-slot period.  Fields: bins = R, frames = F, antennas = A,
+ * chirps = D, fc_width = the FC slot period (a power of two <= ARD_pad,
+ * above every FC width), fc_dims = {A R D, d_1, d_2, classes}, input_scale =
+ * the encryption scale (sets the scale of FC1's bias vector). */
+#define MMFHE_CIRCUIT_GESTURE 5
 
 typedef struct mmfhe_circuit_config {
     uint32_t kind;             /* MMFHE_CIRCUIT_* */
@@ -261,6 +277,12 @@ typedef struct mmfhe_circuit_config {
      * one ciphertext at the top level holding the inputs in slots 0..d_0-1
      * and 1 in slot D-1 of every period; output at level top - 2L + 1. */
     uint32_t fc_dims[9];
+    /* GESTURE only (zero otherwise) */
+    uint32_t antennas;         /* A virtual antennas */
+    uint32_t chirps;           /* D chirps per frame = Doppler bins */
+    uint32_t fc_width;         /* slot period of the FC layers */
+    uint32_t reserved;
+    double input_scale;        /* encryption scale Delta of the inputs */
 } mmfhe_circuit_config;
 
 /* Constant tags of mmfhe_const_key.tag */
@@ -274,7 +296,14 @@ typedef struct mmfhe_circuit_config {
 #define MMFHE_CONST_DFT_C 8  /* FIR_DFT: C = Re W diagonal `index` */
 #define MMFHE_CONST_DFT_S 9  /* FIR_DFT: S = Im W */
 #define MMFHE_CONST_DFT_MS 10 /* FIR_DFT: -S */
-#define MMFHE_CONST_FCW 11   /* FC: diagonal `index` of layer `band` (pre-rotated) */
+#define MMFHE_CONST_FCW 11   /* FC: diagonal `index` of layer `band` (pre-rotated); GESTURE layer 0:
+                                extended diagonal `index` (0..fc_width-1) of FC1 */
+#define MMFHE_CONST_GDFT_C 12  /* GESTURE: Re W Doppler diagonal delta = index - D (pre-rotated) */
+#define MMFHE_CONST_GDFT_S 13  /* GESTURE: Im W */
+#define MMFHE_CONST_GDFT_MS 14 /* GESTURE: -Im W */
+#define MMFHE_CONST_NOTCH 15   /* GESTURE: notch mask m[c] on every active slot */
+#define MMFHE_CONST_FCB 16     /* GESTURE: FC1 bias b[s mod fc_width], 1 in slot fc_width-1, encoded at
+                                  the scale of FC1's rescaled output */
 
 typedef struct mmfhe_const_key {
     uint32_t tag, band, index, level;
@@ -296,7 +325,11 @@ mmfhe_status mmfhe_plan_encode_consts(mmfhe_plan *plan);
 /* FC plans: encode layer `layer` from its D x D matrix W (row-major,
  * y = W v on every period; only the structurally present diagonals are
  * stored).  The constants of an FC plan are learned, so
- * mmfhe_plan_encode_consts returns BAD_ARG for it. */
+ * mmfhe_plan_encode_consts returns BAD_ARG for it.  GESTURE plans: layer 0
+ * is fc_width x (A R D + 1) (column j < A R D weighs feature slot j, the
+ * last column is the bias; row fc_width-1 is ignored: that slot becomes the
+ * constant 1), layers 1 and 2 are fc_width x fc_width as for FC plans;
+ * mmfhe_plan_encode_consts encodes the Doppler DFT and notch constants. */
 mmfhe_status mmfhe_plan_set_fc_layer(mmfhe_plan *plan, uint32_t layer, const double *W);
 /* Per-frame plans: the public scalar constants (count from
  * mmfhe_plan_num_scalars), in this order: per band the FIR taps h[0..taps);
@@ -361,7 +394,8 @@ mmfhe_status mmfhe_tuning_set(mmfhe_ctx *ctx, const mmfhe_tuning *in);
  * in the paper beyond its learned FC weights).  Trains z_l = W_l [a_{l-1}; 1],
  * a_l = z_l + alpha z_l^2 after every layer but the last, softmax
  * cross-entropy, momentum SGD (0.9) on mini-batches of `batch` rows, inputs
- * standardised (folded back, so the weights act on raw inputs).  X: host
+ * standardised (spread floored at 5 % of the largest input's; folded back,
+ * so the weights act on raw inputs).  X: host
  * float [n][dims[0]]; labels: host int32 in [0, dims[layers]); weights out:
  * host float, W_0 [d_1][d_0 + 1], W_1 [d_2][d_1 + 1], ... back to back (last
  * column = bias).  *train_accuracy (nullable): argmax accuracy on X. */
@@ -376,6 +410,13 @@ mmfhe_status mmfhe_train_poly_net(mmfhe_ctx *ctx, const float *X, const int32_t 
  * not below `width` or `width` is not a power of two. */
 mmfhe_status mmfhe_fold_poly_net(const uint32_t *dims, uint32_t layers, float alpha, const float *weights,
                                  uint32_t width, double *mats);
+/* Host only.  The same folding for a network whose input width d_0 may reach
+ * or exceed `width` (a GESTURE plan's FC1 reads every feature slot): layer 0
+ * out: first = width x (d_0 + 1) doubles (bias in column d_0, entry
+ * [width-1][d_0] = 1); layers 1.. out: mats = (layers-1) x width x width as
+ * in mmfhe_fold_poly_net.  BAD_ARG as there, for d_1.. only. */
+mmfhe_status mmfhe_fold_poly_net_wide(const uint32_t *dims, uint32_t layers, float alpha, const float *weights,
+                                      uint32_t width, double *first, double *mats);
 
 /* ------------------------------------------------------------------------
  * Batching runtime.  The paper evaluates windows one call at a time (its

@@ -85,9 +85,9 @@ def gesture_preprocess(z):
 def gesture_features(zt, cfg=GestureConfig()):
     """Accumulated weighted features [A, R, D] and the intermediates."""
     W = dft_kernel(cfg.chirps)
-    d = np.einsum("kn,farn->fark", W, zt)          # K3 per (frame, antenna, bin)
+    d = (zt.reshape(-1, cfg.chirps) @ W.T).reshape(zt.shape)   # K3 per (frame, antenna, bin)
     p = d.real ** 2 + d.imag ** 2                  # K1
     p = p * notch_mask(cfg.chirps)                 # K6
-    w = p ** 4                                     # soft power, gamma = 4
+    w = (p * p) ** 2                               # soft power, gamma = 4
     f = p * w                                      # feature weighting
     return {"d": d, "p": p, "w": w, "f": f, "feat": f.sum(axis=0)}

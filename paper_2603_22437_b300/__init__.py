@@ -11,12 +11,13 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (CIRCUIT_FC, CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_VITAL_PER_FRAME, CONST_TAGS, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
+from ._lib import (CIRCUIT_FC, CIRCUIT_FIR_DFT, CIRCUIT_GESTURE, CIRCUIT_VITAL, CIRCUIT_VITAL_PER_FRAME, CONST_TAGS, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
                    MmfheError, Params, ServerConfig, ServerStats, Tuning, check, ptr, ptr_array, stream_ptr)
 
 __all__ = ["Context", "Keys", "Plan", "Graph", "Batcher", "Server", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
            "Params", "CIRCUIT_FIR_DFT", "CIRCUIT_VITAL", "CIRCUIT_FC", "vital_config", "fir_dft_config",
-           "fc_config", "fir_dft_params", "vital_params", "fc_params", "fold_poly_net"]
+           "fc_config", "fir_dft_params", "vital_params", "fc_params", "fold_poly_net", "CIRCUIT_GESTURE",
+           "gesture_params", "gesture_config", "fold_poly_net_wide"]
 
 
 def params_select(log_n, num_q, q0_bits, q_bits, num_p, p_bits, dnum):
@@ -106,6 +107,38 @@ def fold_poly_net(dims, alpha, weights, width=128):
     mats = np.empty((len(dims) - 1, width, width), dtype=np.float64)
     check(_lib.lib().mmfhe_fold_poly_net(d, len(dims) - 1, float(alpha), ptr(w), width, ptr(mats)))
     return mats
+
+
+def fold_poly_net_wide(dims, alpha, weights, width=32):
+    """As fold_poly_net for a network whose input width d_0 may exceed
+    `width` (a gesture plan's FC1): returns (first, mats), first = width x
+    (d_0 + 1), mats = (layers-1) x width x width."""
+    d = (ctypes.c_uint32 * len(dims))(*dims)
+    w = np.ascontiguousarray(weights, dtype=np.float32)
+    first = np.empty((width, dims[0] + 1), dtype=np.float64)
+    mats = np.empty((max(1, len(dims) - 2), width, width), dtype=np.float64)
+    check(_lib.lib().mmfhe_fold_poly_net_wide(d, len(dims) - 1, float(alpha), ptr(w), width, ptr(first), ptr(mats)))
+    return first, mats[: len(dims) - 2]
+
+
+def gesture_params():
+    """N = 2^15, depth 11 (q_0 60 bits + 11 x 50 bits, Delta = 2^50),
+    K = 4 x 60 bits, dnum = 3."""
+    return params_select(15, 12, 60, 50, 4, 60, 3)
+
+
+def gesture_config(antennas=4, bins=64, chirps=32, frames=60, fc_dims=(31, 16, 6), fc_width=32,
+                   input_scale=2.0 ** 50):
+    """The gesture chain: K3 Doppler DFT -> K1 -> K6 -> w = p^4 -> p w,
+    summed over frames, then FC1^2 -> FC2^2 -> FC3 (fc_dims = d_1, d_2,
+    classes on a slot period of fc_width)."""
+    c = CircuitConfig()
+    c.kind, c.bins, c.frames = CIRCUIT_GESTURE, bins, frames
+    c.antennas, c.chirps, c.fc_width, c.input_scale = antennas, chirps, fc_width, float(input_scale)
+    c.fc_dims[0] = antennas * bins * chirps
+    for i, d in enumerate(fc_dims):
+        c.fc_dims[i + 1] = d
+    return c
 
 
 def fir_dft_config(bins=64, frames=200, fs_mhz=20000, taps=64, band_mhz=(800, 2500)):

@@ -20,9 +20,9 @@ ERRORS = {
     -1: "BAD_ARG", -2: "BAD_BLOB", -3: "PARAM_MISMATCH", -4: "LEVEL_MISMATCH", -5: "OUT_OF_MEMORY",
     -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "BUSY",
 }
-CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_FC, CIRCUIT_VITAL_PER_FRAME = 1, 2, 3, 4
+CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_FC, CIRCUIT_VITAL_PER_FRAME, CIRCUIT_GESTURE = 1, 2, 3, 4, 5
 CONST_TAGS = {1: "idx", 2: "one", 3: "fir", 4: "dre", 5: "dim", 6: "fw", 7: "fone", 8: "dft_c", 9: "dft_s",
-              10: "dft_ms", 11: "fcw"}
+              10: "dft_ms", 11: "fcw", 12: "gdft_c", 13: "gdft_s", 14: "gdft_ms", 15: "notch", 16: "fcb"}
 
 
 class MmfheError(RuntimeError):
@@ -49,7 +49,9 @@ class CircuitConfig(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_uint32), ("bins", ctypes.c_uint32), ("frames", ctypes.c_uint32),
                 ("fs_mhz", ctypes.c_uint32), ("taps", ctypes.c_uint32), ("taylor_order", ctypes.c_uint32),
                 ("num_bands", ctypes.c_uint32), ("band_lo_mhz", ctypes.c_uint32 * 2),
-                ("band_hi_mhz", ctypes.c_uint32 * 2), ("dft_gain", ctypes.c_double * 2), ("fc_dims", ctypes.c_uint32 * 9)]
+                ("band_hi_mhz", ctypes.c_uint32 * 2), ("dft_gain", ctypes.c_double * 2), ("fc_dims", ctypes.c_uint32 * 9),
+                ("antennas", ctypes.c_uint32), ("chirps", ctypes.c_uint32), ("fc_width", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("input_scale", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):
@@ -112,6 +114,7 @@ _SIGS = {
     "mmfhe_train_poly_net": [_VP, _VP, _VP, _U64, _VP, _U32, ctypes.c_float, _U32, _U32, ctypes.c_float, _U64, _VP,
                              ctypes.POINTER(ctypes.c_float)],
     "mmfhe_fold_poly_net": [_VP, _U32, ctypes.c_float, _VP, _U32, _VP],
+    "mmfhe_fold_poly_net_wide": [_VP, _U32, ctypes.c_float, _VP, _U32, _VP, _VP],
     "mmfhe_autotune": [_VP, _U32, _U32, _VP],
     "mmfhe_tuning_get": [_VP, _VP],
     "mmfhe_tuning_set": [_VP, _VP],

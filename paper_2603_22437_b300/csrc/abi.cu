@@ -113,6 +113,8 @@ void mmfhe::eval_windows(Context &c, const Plan &p, const Keys *const *keys, con
     // groups of windows evaluated together, with the key set they run under
     std::vector<std::pair<const Keys *, std::vector<size_t>>> groups;
     std::vector<std::unique_ptr<Keys>> mixed;   // per-window key views of mixed batches
+    // a gesture batch holds every pair of every window: one key set per batch
+    if (p.cfg.kind == MMFHE_CIRCUIT_GESTURE) mix_users = false;
     for (size_t w = 0; w < batch; w++) {
         check_ptr(in_cts[w], "window input");
         check_ptr(out_cts[w], "window output");
@@ -165,7 +167,19 @@ void mmfhe::eval_windows(Context &c, const Plan &p, const Keys *const *keys, con
             outs[b] = out_cts[g.second[b]];
         }
         std::vector<CtB> in;
-        for (int i = 0; i < p.n_in; i++) in.push_back(load_cts(c, ins.data(), i * in_w, B, c.L, 1.0, st));
+        if (p.cfg.kind == MMFHE_CIRCUIT_GESTURE) {
+            // Re and Im of all pairs of all windows, window-major
+            std::vector<const uint64_t *> re((size_t)B * p.pairs), im((size_t)B * p.pairs);
+            for (int b = 0; b < B; b++)
+                for (int j = 0; j < p.pairs; j++) {
+                    re[(size_t)b * p.pairs + j] = ins[b] + (size_t)(2 * j) * in_w;
+                    im[(size_t)b * p.pairs + j] = ins[b] + (size_t)(2 * j + 1) * in_w;
+                }
+            in.push_back(load_cts(c, re.data(), 0, B * p.pairs, c.L, 1.0, st));
+            in.push_back(load_cts(c, im.data(), 0, B * p.pairs, c.L, 1.0, st));
+        } else {
+            for (int i = 0; i < p.n_in; i++) in.push_back(load_cts(c, ins.data(), i * in_w, B, c.L, 1.0, st));
+        }
         std::vector<CtB> res = run_plan(c, p, K, in, st);
         in.clear();
         for (size_t o = 0; o < res.size(); o++) host_out |= store_cts(c, res[o], outs.data(), out_off[o], st);

@@ -14,6 +14,16 @@
 //                DFT (+1); |X|^2 (+2); merge bands + square (+3); frequency
 //                weights and band indicator (+4), rotate-sum.
 // Slot layout: slot(t, r) = t R_c + r, F_pad = 2^ceil(log2 F), R_c = N/2 / F_pad.
+//
+// Gesture chain (Sec. "Example Pipelines", Encrypted Dynamic Radar
+// Classification; Table 1 pipeline 2), L0 = top level: per ciphertext pair
+// K3 Doppler DFT (block-diagonal BSGS, hoisted baby steps of Re and Im,
+// L0-1), K1 p = Re^2 + Im^2 (L0-2), K6 notch mask (L0-3), w = p^4 (L0-5),
+// feature p w (L0-6); frames summed (pairs added, then a rotate-and-sum
+// over the frames sharing a ciphertext); FC1 with extended diagonals over
+// every feature slot and a rotate-and-sum to one period (L0-7), + bias and
+// the constant 1, square (L0-8); FC2 + square (L0-10); FC3 (L0-11).  Every
+// pair of every window of the batch is one ciphertext of each launch.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -144,8 +154,23 @@ static bool is_vital(const mmfhe_circuit_config &cfg) {
     return cfg.kind == MMFHE_CIRCUIT_VITAL || cfg.kind == MMFHE_CIRCUIT_VITAL_PER_FRAME;
 }
 
+static void check_gesture_cfg(const Context &c, const mmfhe_circuit_config &cfg) {
+    const uint64_t A = cfg.antennas, R = cfg.bins, D = cfg.chirps, W = cfg.fc_width;
+    if (A < 1 || R < 1 || D < 2 || cfg.frames < 1) throw Error(MMFHE_ERR_BAD_ARG, "bad gesture sizes");
+    const uint64_t ard = A * R * D;
+    if ((uint64_t)next_pow2((int)std::min<uint64_t>(ard, 1u << 30)) > c.n / 2)
+        throw Error(MMFHE_ERR_BAD_ARG, "a frame needs more slots than a ciphertext has");
+    if (W < 2 || (W & (W - 1)) || W > (uint64_t)next_pow2((int)ard)) throw Error(MMFHE_ERR_BAD_ARG, "bad FC width");
+    if (cfg.fc_dims[0] != ard) throw Error(MMFHE_ERR_BAD_ARG, "fc_dims[0] must be A R D");
+    for (int l = 1; l <= 3; l++)
+        if (cfg.fc_dims[l] < 1 || cfg.fc_dims[l] >= W) throw Error(MMFHE_ERR_BAD_ARG, "FC widths must be 1..fc_width-1");
+    if (!(cfg.input_scale > 1.0)) throw Error(MMFHE_ERR_BAD_ARG, "input_scale must be the encryption scale");
+    if (c.L < 11) throw Error(MMFHE_ERR_BAD_ARG, "not enough levels for the gesture chain");
+}
+
 static void check_cfg(const Context &c, const mmfhe_circuit_config &cfg) {
     if (cfg.kind == MMFHE_CIRCUIT_FC) return check_fc_cfg(c, cfg);
+    if (cfg.kind == MMFHE_CIRCUIT_GESTURE) return check_gesture_cfg(c, cfg);
     if (cfg.kind == MMFHE_CIRCUIT_VITAL_PER_FRAME) {
         if (cfg.frames < 2 || cfg.bins < 1 || cfg.taps < 1 || cfg.fs_mhz < 1 || cfg.taps > cfg.frames)
             throw Error(MMFHE_ERR_BAD_ARG, "bad circuit sizes");
@@ -169,19 +194,80 @@ uint64_t key_of(const mmfhe_const_key &k) {
     return ((uint64_t)k.tag << 48) | ((uint64_t)k.band << 40) | (uint64_t)k.index;
 }
 
-// Structurally present diagonals of FC layer l: rows d_{l+1} and the constant
-// row, columns d_l and the constant column.
-std::vector<int> fc_present(const mmfhe_circuit_config &cfg, int l) {
-    const int D = (int)cfg.bins;
+// Structurally present diagonals of a D x D layer d_in -> d_out: rows d_out
+// and the constant row, columns d_in and the constant column.
+static std::vector<int> present_diags(int D, int din, int dout) {
     std::vector<int> rows, cols;
-    for (uint32_t i = 0; i < cfg.fc_dims[l + 1]; i++) rows.push_back((int)i);
-    for (uint32_t j = 0; j < cfg.fc_dims[l]; j++) cols.push_back((int)j);
+    for (int i = 0; i < dout; i++) rows.push_back(i);
+    for (int j = 0; j < din; j++) cols.push_back(j);
     rows.push_back(D - 1);
     cols.push_back(D - 1);
     std::set<int> ks;
     for (int i : rows)
         for (int j : cols) ks.insert(((j - i) % D + D) % D);
     return std::vector<int>(ks.begin(), ks.end());
+}
+
+// Structurally present diagonals of FC layer l.  Gesture plans: layers 1 and
+// 2 on the period fc_width (layer 0 has every extended diagonal).
+std::vector<int> fc_present(const mmfhe_circuit_config &cfg, int l) {
+    if (cfg.kind == MMFHE_CIRCUIT_GESTURE)
+        return present_diags((int)cfg.fc_width, (int)cfg.fc_dims[l], (int)cfg.fc_dims[l + 1]);
+    return present_diags((int)cfg.bins, (int)cfg.fc_dims[l], (int)cfg.fc_dims[l + 1]);
+}
+
+static int floor_div(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+static Plan *create_gesture_plan(Context &c, const mmfhe_circuit_config &cfg) {
+    std::unique_ptr<Plan> p(new Plan());
+    p->ctx = &c;
+    p->cfg = cfg;
+    const int L = c.L, D = (int)cfg.chirps, W = (int)cfg.fc_width, slots = (int)c.n / 2;
+    const int ard = (int)(cfg.antennas * cfg.bins * cfg.chirps);
+    p->ard_pad = next_pow2(ard);
+    p->fpc = slots / p->ard_pad;
+    p->pairs = ((int)cfg.frames + p->fpc - 1) / p->fpc;
+    p->n1_k3 = bsgs_split(2 * D).first;
+    p->n1_fc = bsgs_split(W).first;
+    std::set<int32_t> rots;
+    for (int delta = -(D - 1); delta < D; delta++) {
+        for (uint32_t tag : {MMFHE_CONST_GDFT_C, MMFHE_CONST_GDFT_S, MMFHE_CONST_GDFT_MS})
+            p->keys.push_back(mmfhe_const_key{tag, 0, (uint32_t)(delta + D), (uint32_t)L});
+        rots.insert(norm_rot(c, floor_div(delta, p->n1_k3) * p->n1_k3));
+    }
+    p->keys.push_back(mmfhe_const_key{MMFHE_CONST_NOTCH, 0, 0, (uint32_t)(L - 2)});
+    for (int k = 0; k < W; k++) p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCW, 0, (uint32_t)k, (uint32_t)(L - 6)});
+    p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCB, 0, 0, (uint32_t)(L - 7)});
+    for (int l = 1; l <= 2; l++)
+        for (int k : fc_present(cfg, l))
+            p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCW, (uint32_t)l, (uint32_t)k, (uint32_t)(L - 6 - 2 * l)});
+    for (int b = 1; b < p->n1_k3; b++) rots.insert(norm_rot(c, b));
+    for (int f = 1; f < p->fpc; f <<= 1) rots.insert(norm_rot(c, f * p->ard_pad));
+    for (int b = 1; b < p->n1_fc; b++) rots.insert(norm_rot(c, b));
+    for (int g = 1; g < W / p->n1_fc; g++) rots.insert(norm_rot(c, g * p->n1_fc));
+    for (int s = W; s < p->ard_pad; s <<= 1) rots.insert(norm_rot(c, s));
+    rots.erase(0);
+    p->rotations.assign(rots.begin(), rots.end());
+    p->n_in = 2 * p->pairs;
+    p->out_levels = {L - 11};
+    p->consts.resize(p->keys.size());
+    for (size_t i = 0; i < p->keys.size(); i++) p->index[key_of(p->keys[i])] = (int)i;
+    return p.release();
+}
+
+// Scale of FC1's rescaled output for inputs encrypted at scale `s0`: the
+// evaluator's scale arithmetic step by step (products multiply scales, a
+// rescale at level l divides by q_l, constants carry q_l).
+static double gesture_fc1_scale(const Context &c, double s0) {
+    auto q = [&](int l) { return (double)c.primes[l]; };
+    const int L = c.L;
+    double s = s0 * q(L) / q(L);
+    s = s * s / q(L - 1);
+    const double p = s * q(L - 2) / q(L - 2);
+    double w = p * p / q(L - 3);
+    w = w * w / q(L - 4);
+    const double f = p * w / q(L - 5);
+    return f * q(L - 6) / q(L - 6);
 }
 
 static Plan *create_fc_plan(Context &c, const mmfhe_circuit_config &cfg) {
@@ -253,6 +339,10 @@ static Plan *create_per_frame_plan(Context &c, const mmfhe_circuit_config &cfg) 
 
 Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
     mmfhe_circuit_config cfg = cfg_in;
+    if (cfg.kind == MMFHE_CIRCUIT_GESTURE) {
+        check_cfg(c, cfg);
+        return create_gesture_plan(c, cfg);
+    }
     if (is_vital(cfg) && cfg.dft_gain[0] == 0.0 && cfg.dft_gain[1] == 0.0) {
         // default public spectral gains (median DFT magnitude ~0.5 on the synthetic workload)
         cfg.dft_gain[0] = cfg.taylor_order == 3 ? 30.0 : 1.5;
@@ -432,6 +522,32 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
         }
         return prerot(d / p.n1_dft, p.n1_dft, Rc);
     }
+    case MMFHE_CONST_GDFT_C:
+    case MMFHE_CONST_GDFT_S:
+    case MMFHE_CONST_GDFT_MS: {
+        // block-diagonal I (x) M of Eq. K3 on every active slot:
+        // diag_delta[s] = M[i][i + delta], i = s mod D
+        const int D = (int)cfg.chirps, delta = (int)k.index - D;
+        const int ard = (int)(cfg.antennas * cfg.bins * cfg.chirps);
+        for (int s = 0; s < n; s++) {
+            const int i = s % D, j = i + delta;
+            if (j < 0 || j >= D || s % p.ard_pad >= ard) continue;
+            const int sig = (i + D / 2) % D;
+            const double ang = -2 * M_PI * sig * j / D, w = hann(j, D);
+            double val = k.tag == MMFHE_CONST_GDFT_C ? w * std::cos(ang) : w * std::sin(ang);
+            v[s] = k.tag == MMFHE_CONST_GDFT_MS ? -val : val;
+        }
+        return prerot(floor_div(delta, p.n1_k3), p.n1_k3, 1);
+    }
+    case MMFHE_CONST_NOTCH: {
+        // Eq. (notch mask): zero on Doppler bins floor(D/2) .. ceil(D/2)
+        const int D = (int)cfg.chirps, ard = (int)(cfg.antennas * cfg.bins * cfg.chirps);
+        for (int s = 0; s < n; s++) {
+            const int d = s % D;
+            v[s] = (s % p.ard_pad < ard && !(d >= D / 2 && d <= (D + 1) / 2)) ? 1.0 : 0.0;
+        }
+        return v;
+    }
     case MMFHE_CONST_FW:
     case MMFHE_CONST_FONE:
         for (int kk : p.bands[k.band]) v[slot(kk, 0)] = k.tag == MMFHE_CONST_FW ? kk * fs / F : 1.0;
@@ -447,6 +563,7 @@ void plan_encode_consts(Plan &p, cudaStream_t st) {
     std::vector<uint64_t> words;
     for (size_t i = 0; i < p.keys.size(); i++) {
         const mmfhe_const_key &k = p.keys[i];
+        if (k.tag == MMFHE_CONST_FCW || k.tag == MMFHE_CONST_FCB) continue;   // learned: set_fc_layer
         std::vector<double> v = const_slots(p, k);
         words.assign((size_t)(k.level + 1) * c.n, 0);
         encode_slots(c.params, v.data(), (double)c.primes[k.level], (int)k.level, words.data());
@@ -639,8 +756,128 @@ static std::vector<CtB> run_fc(Context &c, const Plan &p, const Keys &k, std::ve
     return out;
 }
 
+static void encode_and_set(Plan &p, const mmfhe_const_key &key0, const std::vector<double> &v, double scale) {
+    Context &c = *p.ctx;
+    const auto it = p.index.find(key_of(key0));
+    if (it == p.index.end()) throw Error(MMFHE_ERR_NOT_FOUND, "plan constant missing");
+    const mmfhe_const_key &key = p.keys[it->second];
+    std::vector<uint64_t> words((size_t)(key.level + 1) * c.n, 0);
+    encode_slots(c.params, v.data(), scale > 0 ? scale : (double)c.primes[key.level], (int)key.level, words.data());
+    plan_set_const(p, (uint32_t)it->second, words.data(), 0);
+    CK(cudaStreamSynchronize(0));
+}
+
+// Gesture FC layers.  Layer 0: W is fc_width x (A R D + 1); extended
+// diagonal k: diag_k[s] = W[s mod w][(s + k) mod ARD_pad] (zero on padding
+// columns and on row w-1), pre-rotated by its giant step; the bias vector
+// b[s mod w] with 1 in slot w-1, encoded at the scale of FC1's rescaled
+// output.  Layers 1, 2: w x w as in FC plans.
+static void gesture_set_fc_layer(Plan &p, uint32_t layer, const double *W) {
+    Context &c = *p.ctx;
+    const mmfhe_circuit_config &cfg = p.cfg;
+    const int w = (int)cfg.fc_width, n1 = p.n1_fc, slots = (int)c.n / 2;
+    const int ard = (int)(cfg.antennas * cfg.bins * cfg.chirps);
+    std::vector<double> v(slots), r(slots);
+    auto prerot = [&](int g) {
+        const int sh = g * n1;
+        for (int j = 0; j < slots; j++) r[j] = v[((j - sh) % slots + slots) % slots];
+    };
+    if (layer == 0) {
+        const size_t ld = (size_t)ard + 1;
+        for (int k = 0; k < w; k++) {
+            for (int s = 0; s < slots; s++) {
+                const int col = (s + k) % p.ard_pad, row = s % w;
+                v[s] = (col < ard && row != w - 1) ? W[(size_t)row * ld + col] : 0.0;
+            }
+            prerot(k / n1);
+            encode_and_set(p, mmfhe_const_key{MMFHE_CONST_FCW, 0, (uint32_t)k, 0}, r, 0.0);
+        }
+        for (int s = 0; s < slots; s++) v[s] = s % w == w - 1 ? 1.0 : W[(size_t)(s % w) * ld + ard];
+        encode_and_set(p, mmfhe_const_key{MMFHE_CONST_FCB, 0, 0, 0}, v, gesture_fc1_scale(c, cfg.input_scale));
+        return;
+    }
+    for (int k : fc_present(cfg, (int)layer)) {
+        for (int s = 0; s < slots; s++) v[s] = W[(size_t)(s % w) * w + ((s % w) + k) % w];
+        prerot(k / n1);
+        encode_and_set(p, mmfhe_const_key{MMFHE_CONST_FCW, layer, (uint32_t)k, 0}, r, 0.0);
+    }
+}
+
+// Gesture chain: in[0] / in[1] = Re / Im of every pair of every window
+// (batch B pairs, window-major).
+static std::vector<CtB> run_gesture(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in,
+                                    cudaStream_t st) {
+    const mmfhe_circuit_config &cfg = p.cfg;
+    const int D = (int)cfg.chirps, W = (int)cfg.fc_width;
+    CtB feat;
+    {
+        // K3: d_re = C re - S im, d_im = S re + C im (Eq. K3), one BSGS each
+        std::vector<int32_t> rb(p.n1_k3);
+        std::vector<int> idx(p.n1_k3);
+        for (int b = 0; b < p.n1_k3; b++) rb[b] = idx[b] = b;
+        std::vector<CtB> bre = rotate_hoisted(c, k, in[0], rb, st);
+        std::vector<CtB> bim = rotate_hoisted(c, k, in[1], rb, st);
+        in.clear();
+        BsgsTerm t[4];
+        for (int i = 0; i < 4; i++) {
+            t[i].baby = i % 2 == 0 ? &bre : &bim;
+            t[i].baby_idx = idx;
+        }
+        for (int delta = -(D - 1); delta < D; delta++) {
+            const uint32_t ix = (uint32_t)(delta + D);
+            t[0].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_C, 0, ix)});
+            t[1].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_MS, 0, ix)});
+            t[2].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_S, 0, ix)});
+            t[3].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_C, 0, ix)});
+        }
+        CtB dre = rescale(c, bsgs(c, k, {t[0], t[1]}, p.n1_k3, 1, st), st);
+        CtB dim = rescale(c, bsgs(c, k, {t[2], t[3]}, p.n1_k3, 1, st), st);
+        bre.clear();
+        bim.clear();
+        CtB pw = rescale(c, square_sum(c, k, {&dre, &dim}, st), st);              // K1
+        CtB pm = ct_new(c, pw.B, pw.level, pw.scale);
+        ct_mul_plain(c, pm, pw, plan_const(p, MMFHE_CONST_NOTCH, 0, 0), false, st);   // K6
+        CtB pn = rescale(c, pm, st);
+        CtB w2 = rescale(c, square_sum(c, k, {&pn}, st), st);                     // w = p^4
+        CtB w4 = rescale(c, square_sum(c, k, {&w2}, st), st);
+        CtB pd = ct_drop(c, pn, w4.level, st);
+        TensorB tw = tensor_new(c, w4.B, w4.level);
+        tensor_acc(c, tw, pd, w4, 1, true, st);
+        CtB f = rescale(c, relin(c, k, tw, st), st);                              // p x w
+        feat = rotsum(c, k, group_sum(c, f, p.pairs, st), p.ard_pad, (uint32_t)p.fpc, st);
+    }
+    const int n1 = p.n1_fc;
+    std::vector<int32_t> rb(n1);
+    std::vector<int> idx(n1);
+    for (int b = 0; b < n1; b++) rb[b] = idx[b] = b;
+    CtB x = std::move(feat);
+    for (int l = 0; l < 3; l++) {
+        std::vector<CtB> babies = rotate_hoisted(c, k, x, rb, st);
+        BsgsTerm t;
+        t.baby = &babies;
+        t.baby_idx = idx;
+        if (l == 0)
+            for (int d = 0; d < W; d++) t.diags.push_back({d, &plan_const(p, MMFHE_CONST_FCW, 0, (uint32_t)d)});
+        else
+            for (int d : fc_present(cfg, l)) t.diags.push_back({d, &plan_const(p, MMFHE_CONST_FCW, (uint32_t)l, (uint32_t)d)});
+        CtB y = rescale(c, bsgs(c, k, {t}, n1, 1, st), st);
+        babies.clear();
+        if (l == 0)
+            y = add_plain(c, rotsum(c, k, y, W, (uint32_t)(p.ard_pad / W), st), plan_const(p, MMFHE_CONST_FCB, 0, 0), st);
+        if (l < 2) y = rescale(c, square_sum(c, k, {&y}, st), st);
+        x = std::move(y);
+    }
+    std::vector<CtB> out;
+    out.push_back(std::move(x));
+    return out;
+}
+
 void plan_set_fc_layer(Plan &p, uint32_t layer, const double *W) {
     Context &c = *p.ctx;
+    if (p.cfg.kind == MMFHE_CIRCUIT_GESTURE) {
+        if (layer > 2) throw Error(MMFHE_ERR_BAD_ARG, "layer out of range");
+        return gesture_set_fc_layer(p, layer, W);
+    }
     if (p.cfg.kind != MMFHE_CIRCUIT_FC) throw Error(MMFHE_ERR_BAD_ARG, "not an FC plan");
     if (layer >= p.cfg.taps) throw Error(MMFHE_ERR_BAD_ARG, "layer out of range");
     const int D = (int)p.cfg.bins, n1 = p.n1_dft, slots = (int)c.n / 2;
@@ -780,6 +1017,7 @@ void plan_set_scalars(Plan &p, const double *v, size_t n) {
 
 std::vector<CtB> run_plan(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st) {
     if (p.cfg.kind == MMFHE_CIRCUIT_FC) return run_fc(c, p, k, in, st);
+    if (p.cfg.kind == MMFHE_CIRCUIT_GESTURE) return run_gesture(c, p, k, in, st);
     if (p.cfg.kind == MMFHE_CIRCUIT_VITAL_PER_FRAME) return run_vital_per_frame(c, p, k, in, st);
     if (p.cfg.kind == MMFHE_CIRCUIT_FIR_DFT) return run_fir_dft(c, p, k, in, st);
     return run_vital(c, p, k, in, st);

@@ -23,6 +23,9 @@ struct Plan {
     int n_in = 0;
     std::vector<int> out_levels;
     std::vector<double> scalars;                // per-frame chain: public scalar constants
+    // gesture chain: padded frame size, frames per ciphertext, ciphertext
+    // pairs per window, BSGS baby steps of the Doppler DFT and of the FC layers
+    int ard_pad = 0, fpc = 0, pairs = 0, n1_k3 = 0, n1_fc = 0;
 };
 
 uint64_t key_of(const mmfhe_const_key &k);

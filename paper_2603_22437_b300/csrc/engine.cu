@@ -306,6 +306,21 @@ CtB lincomb(Context &c, const std::vector<std::pair<const CtB *, double>> &terms
     return out;
 }
 
+CtB add_plain(Context &c, const CtB &a, const PtDev &pt, cudaStream_t st) {
+    if (a.level != pt.level) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "add_plain: level mismatch");
+    if (!pt.mont) throw Error(MMFHE_ERR_BAD_ARG, "add_plain: plaintext must be in Montgomery form");
+    CtB r = ct_copy(c, a, st);
+    k_launch_add_plain(c, r.ptr(), pt.buf.get(), r.B, r.level, st);
+    return r;
+}
+
+CtB group_sum(Context &c, const CtB &a, int G, cudaStream_t st) {
+    if (G < 1 || a.B % G) throw Error(MMFHE_ERR_BAD_ARG, "group_sum: batch not a multiple of the group");
+    CtB r = ct_new(c, a.B / G, a.level, a.scale);
+    k_launch_group_sum(c, r.ptr(), a.ptr(), r.B, G, a.level, st);
+    return r;
+}
+
 CtB rotsum(Context &c, const Keys &k, const CtB &a, int32_t stride, uint32_t span, cudaStream_t st) {
     if (span <= 1) return ct_copy(c, a, st);
     // x <- x + Rot(x, stride s): the addition happens inside the key switch's last kernel
@@ -323,10 +338,12 @@ CtB bsgs(Context &c, const Keys &k, const std::vector<BsgsTerm> &terms, int n1, 
         std::map<int, int> pos;
         for (size_t i = 0; i < t.baby_idx.size(); i++) pos[t.baby_idx[i]] = (int)i;
         for (const auto &d : t.diags) {
-            auto it = pos.find(d.first % n1);
+            // delta = g n1 + b with 0 <= b < n1 (floor division: deltas may be negative)
+            const int g = d.first >= 0 ? d.first / n1 : -((-d.first + n1 - 1) / n1);
+            auto it = pos.find(d.first - g * n1);
             if (it == pos.end()) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: missing baby step");
             const CtB *bb = &(*t.baby)[it->second];
-            groups[d.first / n1].push_back(Item{bb, d.second});
+            groups[g].push_back(Item{bb, d.second});
             level = bb->level;
             B = bb->B;
             scale = bb->scale * d.second->scale;

@@ -59,6 +59,12 @@ std::vector<CtB> rotate_hoisted(Context &c, const Keys &k, const CtB &a, const s
                                 cudaStream_t st);
 CtB rotsum(Context &c, const Keys &k, const CtB &a, int32_t stride, uint32_t span, cudaStream_t st);
 
+// a + pt (pt at a's level, Montgomery form, encoded at a's scale): joins c0.
+CtB add_plain(Context &c, const CtB &a, const PtDev &pt, cudaStream_t st);
+
+// Sums consecutive groups of G ciphertexts of a batch: out[b] = sum_g a[b G + g].
+CtB group_sum(Context &c, const CtB &a, int G, cudaStream_t st);
+
 // sum_i c_i * x_i for real constants c_i, each encoded at `scale` as the
 // constant polynomial round(scale c_i) (an exact integer multiply); all x_i
 // at one level and batch; not rescaled; result scale x.scale * scale.

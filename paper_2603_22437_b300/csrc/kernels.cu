@@ -66,6 +66,33 @@ __global__ void k_mul_plain(uint64_t *out, const uint64_t *a, const uint64_t *pt
     }
 }
 
+// c0 of every window (+)= pt (pt in Montgomery form: redc brings it back);
+// c1 is untouched.  Ciphertext layout [B][2][nl][N].
+__global__ void k_add_plain(uint64_t *ct, const uint64_t *pt, size_t words, int logn, int nl, ModTab mt) {
+    const uint32_t n = 1u << logn;
+    const size_t per = (size_t)nl << logn;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < words; w += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = w / per, r = w - b * per;
+        const int i = (int)(r >> logn);
+        const uint64_t q = mt.q[i];
+        uint64_t *dst = ct + b * 2 * per + r;
+        *dst = mm::add_mod(*dst, mm::redc(0, pt[((size_t)i << logn) + (r & (n - 1))], q, mt.qinv[i]), q);
+    }
+}
+
+// out[b] = sum_{g < G} in[b G + g] (ciphertexts of `wpc` words, rows of nl Q primes).
+__global__ void k_group_sum(uint64_t *out, const uint64_t *in, size_t words, size_t wpc, int G, int logn, int nl,
+                            ModTab mt) {
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < words; w += (size_t)gridDim.x * blockDim.x) {
+        const size_t b = w / wpc, r = w - b * wpc;
+        const uint64_t q = mt.q[(r >> logn) % nl];
+        const uint64_t *src = in + b * G * wpc + r;
+        uint64_t acc = src[0];
+        for (int g = 1; g < G; g++) acc = mm::add_mod(acc, src[(size_t)g * wpc], q);
+        out[w] = acc;
+    }
+}
+
 // Rows into (to = 1) or out of (to = 0) Montgomery form, in place.
 __global__ void k_mont_convert(uint64_t *base, RowMap map, size_t rows, int logn, ModTab mt, int to) {
     const uint32_t n = 1u << logn;
@@ -464,6 +491,22 @@ void k_launch_mul_plain(Context &c, uint64_t *out, const uint64_t *a, const uint
     double bytes = W8((acc ? 3 : 2) * words + ((size_t)period << c.logn));
     LAUNCH(c, acc ? "mul_plain_acc" : "mul_plain", bytes, g, k_mul_plain, out, a, pt, words, c.logn, period, c.mods,
            pl, acc ? 1 : 0, mont ? 1 : 0);
+}
+
+void k_launch_add_plain(Context &c, uint64_t *ct, const uint64_t *pt, int B, int level, cudaStream_t st) {
+    const int nl = level + 1;
+    const size_t words = ((size_t)B * nl) << c.logn;
+    if (!words) return;
+    dim3 g = grid_for(words);
+    LAUNCH(c, "add_plain", W8(2 * words + ((size_t)nl << c.logn)), g, k_add_plain, ct, pt, words, c.logn, nl, c.mods);
+}
+
+void k_launch_group_sum(Context &c, uint64_t *out, const uint64_t *in, int B, int G, int level, cudaStream_t st) {
+    const int nl = level + 1;
+    const size_t wpc = ((size_t)2 * nl) << c.logn, words = (size_t)B * wpc;
+    if (!words) return;
+    dim3 g = grid_for(words);
+    LAUNCH(c, "group_sum", W8(words * (size_t)(G + 1)), g, k_group_sum, out, in, words, wpc, G, c.logn, nl, c.mods);
 }
 
 void k_launch_mont_convert(Context &c, const RowsView &v, bool to, cudaStream_t st) {

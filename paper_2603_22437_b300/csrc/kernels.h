@@ -44,6 +44,10 @@ void k_launch_mul_plain(Context &c, uint64_t *out, const uint64_t *a, const uint
                         const PidList &pl, uint32_t period, bool acc, cudaStream_t st, bool mont = false);
 // Convert rows of a view into (to) or out of Montgomery form, in place.
 void k_launch_mont_convert(Context &c, const RowsView &v, bool to, cudaStream_t st);
+// c0 rows of B ciphertexts at `level` += pt (Montgomery form, level+1 rows).
+void k_launch_add_plain(Context &c, uint64_t *ct, const uint64_t *pt, int B, int level, cudaStream_t st);
+// out[b] = sum_{g < G} in[b G + g], B output ciphertexts at `level`.
+void k_launch_group_sum(Context &c, uint64_t *out, const uint64_t *in, int B, int G, int level, cudaStream_t st);
 void k_launch_tensor(Context &c, uint64_t *d, const uint64_t *a, const uint64_t *b, int B, int level, long long coef,
                      bool acc, cudaStream_t st);
 void k_launch_modup_bconv(Context &c, uint64_t *out, const uint64_t *coef, const uint64_t *deval, size_t deval_stride,

@@ -95,6 +95,43 @@ struct DevBuf {
 
 }  // namespace
 
+// Fold the quadratic activations into pure squares.  Layer l's matrix is
+// D x D (bias in column D-1, M[D-1][D-1] = 1); with `wide`, layer 0 goes to
+// `first` as D x (d_0 + 1) (bias in column d_0) and layers 1.. to mats.
+static mmfhe_status fold(const uint32_t *dims, uint32_t layers, float alpha, const float *weights, uint32_t width,
+                         bool wide, double *first, double *mats) {
+    if (!dims || !weights || (!mats && !wide) || layers < 1 || layers > 8 || alpha <= 0.f || width < 2 ||
+        (width & (width - 1)))
+        return MMFHE_ERR_BAD_ARG;
+    const int L = (int)layers, D = (int)width;
+    for (int l = wide ? 1 : 0; l <= L; l++)
+        if (dims[l] < 1 || (int)dims[l] >= D) return MMFHE_ERR_BAD_ARG;
+    if (dims[0] < 1) return MMFHE_ERR_BAD_ARG;
+    const double a = alpha, beta = 1.0 / (2.0 * a), gamma = 1.0 / (4.0 * a);
+    size_t off = 0;
+    for (int l = 0; l < L; l++) {
+        const int din = (int)dims[l], dout = (int)dims[l + 1];
+        const bool w0 = wide && l == 0;
+        const int cols = w0 ? din + 1 : D, bcol = w0 ? din : D - 1;
+        double *M = w0 ? first : mats + (size_t)(wide ? l - 1 : l) * D * D;
+        std::fill(M, M + (size_t)D * cols, 0.0);
+        for (int o = 0; o < dout; o++) {
+            const float *row = weights + off + (size_t)o * (din + 1);
+            double bias = row[din];
+            for (int j = 0; j < din; j++) {
+                // the input of a layer after the first is a = alpha s - gamma (s = the previous square)
+                M[(size_t)o * cols + j] = l > 0 ? a * row[j] : row[j];
+                if (l > 0) bias -= gamma * row[j];
+            }
+            // a hidden layer's square takes (z + beta)^2
+            M[(size_t)o * cols + bcol] = bias + (l < L - 1 ? beta : 0.0);
+        }
+        M[(size_t)(D - 1) * cols + bcol] = 1.0;
+        off += (size_t)dout * (din + 1);
+    }
+    return MMFHE_OK;
+}
+
 extern "C" {
 
 mmfhe_status mmfhe_train_poly_net(mmfhe_ctx *ctx, const float *X, const int32_t *labels, uint64_t n,
@@ -119,7 +156,11 @@ mmfhe_status mmfhe_train_poly_net(mmfhe_ctx *ctx, const float *X, const int32_t 
         for (int j = 0; j < d0; j++) mu[j] /= (double)n;
         for (uint64_t i = 0; i < n; i++)
             for (int j = 0; j < d0; j++) sd[j] += (X[i * d0 + j] - mu[j]) * (X[i * d0 + j] - mu[j]);
-        for (int j = 0; j < d0; j++) sd[j] = std::sqrt(sd[j] / (double)n) + 1e-6;
+        // a floor of 5 % of the largest spread keeps near-constant inputs
+        // from inflating their folded weights (encoded at scale q_l later)
+        double sd_max = 0.0;
+        for (int j = 0; j < d0; j++) sd_max = std::max(sd_max, sd[j] = std::sqrt(sd[j] / (double)n));
+        for (int j = 0; j < d0; j++) sd[j] = std::max(sd[j], 0.05 * sd_max) + 1e-12;
         std::vector<float> Xs(n * d0);
         for (uint64_t i = 0; i < n; i++)
             for (int j = 0; j < d0; j++) Xs[i * d0 + j] = (float)((X[i * d0 + j] - mu[j]) / sd[j]);
@@ -230,32 +271,13 @@ mmfhe_status mmfhe_train_poly_net(mmfhe_ctx *ctx, const float *X, const int32_t 
 
 mmfhe_status mmfhe_fold_poly_net(const uint32_t *dims, uint32_t layers, float alpha, const float *weights,
                                  uint32_t width, double *mats) {
-    if (!dims || !weights || !mats || layers < 1 || layers > 8 || alpha <= 0.f || width < 2 || (width & (width - 1)))
-        return MMFHE_ERR_BAD_ARG;
-    const int L = (int)layers, D = (int)width;
-    for (int l = 0; l <= L; l++)
-        if (dims[l] < 1 || (int)dims[l] >= D) return MMFHE_ERR_BAD_ARG;
-    const double a = alpha, beta = 1.0 / (2.0 * a), gamma = 1.0 / (4.0 * a);
-    size_t off = 0;
-    for (int l = 0; l < L; l++) {
-        const int din = (int)dims[l], dout = (int)dims[l + 1];
-        double *M = mats + (size_t)l * D * D;
-        std::fill(M, M + (size_t)D * D, 0.0);
-        for (int o = 0; o < dout; o++) {
-            const float *row = weights + off + (size_t)o * (din + 1);
-            double bias = row[din];
-            for (int j = 0; j < din; j++) {
-                // the input of a layer after the first is a = alpha s - gamma (s = the previous square)
-                M[(size_t)o * D + j] = l > 0 ? a * row[j] : row[j];
-                if (l > 0) bias -= gamma * row[j];
-            }
-            // a hidden layer's square takes (z + beta)^2
-            M[(size_t)o * D + D - 1] = bias + (l < L - 1 ? beta : 0.0);
-        }
-        M[(size_t)(D - 1) * D + D - 1] = 1.0;
-        off += (size_t)dout * (din + 1);
-    }
-    return MMFHE_OK;
+    return fold(dims, layers, alpha, weights, width, false, nullptr, mats);
+}
+
+mmfhe_status mmfhe_fold_poly_net_wide(const uint32_t *dims, uint32_t layers, float alpha, const float *weights,
+                                      uint32_t width, double *first, double *mats) {
+    if (!first || (layers > 1 && !mats)) return MMFHE_ERR_BAD_ARG;
+    return fold(dims, layers, alpha, weights, width, true, first, mats);
 }
 
 }  // extern "C"

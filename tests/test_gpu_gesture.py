@@ -1,0 +1,198 @@
+"""Gesture chain on the GPU (paper Sec. "Example Pipelines", Encrypted
+Dynamic Radar Classification; Table 1 pipeline 2): output ciphertexts word
+for word against the oracle for two windows in one batch; the library's own
+constant encodings against the oracle's; and a network trained by the
+library's plaintext trainer on pooled features of synthetic gesture windows,
+whose decrypted encrypted-chain labels equal the FP64 labels."""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ckks as ck
+from oracle import circuits as cc
+from oracle import params as pm
+from oracle import plain
+from test_gpu_parity import compare_plan_consts, lib_params, load_keys, window_words
+
+pytestmark = pytest.mark.gpu
+
+KEY_SEED = 61
+SMALL = cc.GestureConfig(frames=4)          # the full frame shape, 2 ciphertext pairs
+POOL_R = 4                                  # training features: antennas summed, range pooled by 4
+
+
+def oracle_setup(cfg):
+    P = pm.gesture_params()
+    circ = cc.GestureCircuit(P, cfg)
+    rots = circ.rotations()
+    kd = synth.KeyDraws(KEY_SEED, P.n, P.q, P.p, P.dnum, rots)
+    sk = ck.SecretKey(P, kd.secret)
+    pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
+    rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
+    gks = {k: ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
+    return P, circ, sk, pk, rlk, gks
+
+
+def random_mats(cfg, seed):
+    g = np.random.default_rng(seed)
+    W, (d1, d2, c) = cfg.width, cfg.fc_dims
+    W0 = np.zeros((W, cfg.ard + 1))
+    W0[:d1, : cfg.ard] = g.normal(0, 1.0, (d1, cfg.ard))
+    W0[:d1, cfg.ard] = g.normal(0, 0.3, d1)
+    mats = [W0]
+    for a, b in ((d1, d2), (d2, c)):
+        M = np.zeros((W, W))
+        M[:b, :a] = g.normal(0, 0.5 / np.sqrt(a), (b, a))
+        M[:b, W - 1] = g.normal(0, 0.1, b)
+        M[W - 1, W - 1] = 1.0
+        mats.append(M)
+    return mats
+
+
+def encrypt_pairs(P, pk, circ, zt, seed):
+    return [tuple(ck.encrypt(P, pk, ck.encode(P, v, P.scale, P.L), *synth.encryption_draws(seed + 2 * i + h, P.n))
+                  for h, v in enumerate(pair)) for i, pair in enumerate(circ.lay.pack(zt))]
+
+
+def _oracle_window(w):
+    """Worker (spawned process): the oracle's output words of window w."""
+    P, circ, sk, pk, rlk, gks = oracle_setup(SMALL)
+    zt = plain.gesture_preprocess(synth.gesture_window(300 + w, frames=SMALL.frames).z)
+    cts = encrypt_pairs(P, pk, circ, zt, 5000 + 100 * w)
+    out = circ.run(cc.Evaluator(P, rlk, gks), circ.constants(random_mats(SMALL, 9)), cts)
+    return window_words([c for pair in cts for c in pair]), out.words(), out.scale
+
+
+@pytest.fixture(scope="module")
+def gest():
+    # the oracle runs in spawned processes, started before this process touches the GPU
+    pool = mp.get_context("spawn").Pool(2)
+    pending = pool.map_async(_oracle_window, [0, 1])
+    import paper_2603_22437_b300 as M
+    P, circ, sk, pk, rlk, gks = oracle_setup(SMALL)
+    ctx = M.Context(lib_params(P))
+    keys = load_keys(ctx, P, rlk, gks)
+    yield dict(P=P, circ=circ, sk=sk, pk=pk, rlk=rlk, gks=gks, ctx=ctx, keys=keys, pending=pending)
+    pool.close()
+    pool.join()
+
+
+def install(plan, consts, D):
+    for i, (tag, band, index, level) in enumerate(plan.const_keys()):
+        if tag in ("gdft_c", "gdft_s", "gdft_ms"):
+            key = (tag, index - D)
+        elif tag == "fcw":
+            key = ("fcw", band, index)
+        else:
+            key = (tag,)
+        assert consts[key].level == level, key
+        plan.set_const(i, np.ascontiguousarray(consts[key].m))
+
+
+def gesture_config(M, cfg):
+    return M.gesture_config(antennas=cfg.antennas, bins=cfg.bins, chirps=cfg.chirps, frames=cfg.frames,
+                            fc_dims=cfg.fc_dims, fc_width=cfg.width)
+
+
+def test_gesture_word_exact_two_windows(gest):
+    import paper_2603_22437_b300 as M
+    P, circ, ctx, keys = gest["P"], gest["circ"], gest["ctx"], gest["keys"]
+    plan = ctx.plan(gesture_config(M, SMALL))
+    assert plan.rotations() == circ.rotations()
+    assert plan.io() == (2 * circ.lay.pairs, 1, [0])
+    consts = circ.constants(random_mats(SMALL, 9))
+    install(plan, consts, SMALL.chirps)
+    ref = gest["pending"].get(timeout=1800)
+    ins = [r[0] for r in ref]
+    outs = [np.empty(2 * P.n, dtype=np.uint64) for _ in ref]
+    ctx.eval(plan, keys, ins, outs)
+    for w, (_, want, scale) in enumerate(ref):
+        assert np.array_equal(outs[w], want.reshape(-1)), "window %d" % w
+        assert abs(gesture_out_scale(P, circ) / scale - 1) < 1e-12
+    # the library's own encoding of the same constants agrees to +-1
+    lib = ctx.plan(gesture_config(M, SMALL))
+    lib.encode_consts()
+    for l, W in enumerate(random_mats(SMALL, 9)):
+        lib.set_fc_layer(l, W)
+    compare_plan_consts(plan, lib, P)
+
+
+def pooled(feat):
+    """[A, R, D] -> antennas summed, range pooled by POOL_R: [R / POOL_R * D]."""
+    A, R, D = feat.shape
+    return feat.sum(0).reshape(R // POOL_R, POOL_R, D).sum(1).reshape(-1)
+
+
+def _features(seed):
+    w = synth.gesture_window(seed)
+    return pooled(plain.gesture_features(plain.gesture_preprocess(w.z))["feat"]), w.label
+
+
+def expand_first(first, cfg, kappa):
+    """FC1 over the pooled features (scaled by kappa) -> FC1 over every
+    feature slot a R D + r D + d (pooling and scale folded into W0)."""
+    W0 = np.zeros((cfg.width, cfg.ard + 1))
+    a, r, d = np.meshgrid(np.arange(cfg.antennas), np.arange(cfg.bins), np.arange(cfg.chirps), indexing="ij")
+    slot = (a * cfg.bins * cfg.chirps + r * cfg.chirps + d).reshape(-1)
+    pool_idx = ((r // POOL_R) * cfg.chirps + d).reshape(-1)
+    W0[:, slot] = kappa * first[:, pool_idx]
+    W0[:, cfg.ard] = first[:, -1]
+    return W0
+
+
+def test_trained_gesture_labels_equal_fp64(gest):
+    import paper_2603_22437_b300 as M
+    from test_fc_fold import quad_forward
+    P, ctx, keys = gest["P"], gest["ctx"], gest["keys"]
+    cfg = cc.GestureConfig()
+    circ = cc.GestureCircuit(P, cfg)
+    n_train, n_test = 2000, 400
+    with mp.get_context("spawn").Pool(8) as pool:
+        data = pool.map(_features, range(20000, 20000 + n_train + n_test), chunksize=25)
+    X = np.array([d[0] for d in data])
+    y = np.array([d[1] for d in data], dtype=np.int32)
+    kappa = 1.0 / X[:n_train].std(axis=0).max()
+    dims = (X.shape[1],) + tuple(cfg.fc_dims)
+    alpha = float(np.float32(0.1))
+    w, train_acc = ctx.train_poly_net(X[:n_train] * kappa, y[:n_train], dims, alpha=alpha, epochs=40, batch=64,
+                                      lr=0.005, seed=5)
+    test_pred = np.array([quad_forward(w, dims, alpha, x * kappa).argmax() for x in X[n_train:]])
+    test_acc = float((test_pred == y[n_train:]).mean())
+    print("gesture network: train %.3f test %.3f" % (train_acc, test_acc))
+    assert train_acc > 0.7 and test_acc > 0.6, (train_acc, test_acc)
+    first, tail = M.fold_poly_net_wide(dims, alpha, w, cfg.width)
+    mats = [expand_first(first, cfg, kappa), tail[0], tail[1]]
+    plan = ctx.plan(gesture_config(M, cfg))
+    plan.encode_consts()
+    for l, Wm in enumerate(mats):
+        plan.set_fc_layer(l, Wm)
+    sel = list(range(20000 + n_train, 20000 + n_train + 3))
+    wins = [synth.gesture_window(s) for s in sel]
+    zts = [plain.gesture_preprocess(wd.z) for wd in wins]
+    cts = [encrypt_pairs(P, gest["pk"], circ, zt, 7000 + 200 * i) for i, zt in enumerate(zts)]
+    ins = [window_words([c for pair in ct for c in pair]) for ct in cts]
+    outs = [np.empty(2 * P.n, dtype=np.uint64) for _ in sel]
+    ctx.eval(plan, keys, ins, outs)
+    C = cfg.fc_dims[-1]
+    for j, zt in enumerate(zts):
+        feat = plain.gesture_features(zt)["feat"]
+        want = cc.gesture_forward(mats, feat, cfg)[:C]
+        quad = quad_forward(w, dims, alpha, pooled(feat) * kappa)
+        ct = ck.Ciphertext(outs[j].reshape(2, 1, P.n)[0], outs[j].reshape(2, 1, P.n)[1], 0, gesture_out_scale(P, circ))
+        got = ck.decrypt_decode(P, gest["sk"], ct)[:C]
+        assert got.argmax() == want.argmax() == quad.argmax()
+        assert np.allclose(got, want, atol=1e-4 * max(1.0, np.abs(want).max()))
+
+
+def gesture_out_scale(P, circ):
+    """Scale of the logits ciphertext: the evaluator's scale arithmetic
+    after FC1 (FC1's output scale from the circuit, then square, FC2,
+    square, FC3 with constants at q_l)."""
+    q, L = P.q, P.L
+    s = circ.fc1_out_scale(P.scale)
+    s = s * s / q[L - 7]
+    s = s * q[L - 8] / q[L - 8]
+    s = s * s / q[L - 9]
+    return s * q[L - 10] / q[L - 10]
