@@ -1052,12 +1052,12 @@ class GestureCircuit:
     def fc1_diagonal(self, W0, k):
         """Extended diagonal k of FC1 (W0: width x (A R D), no bias column):
         diag_k[s] = W0[s mod width][(s + k) mod ARD_pad] (zero on padding
-        columns)."""
+        columns and on row width-1, the constant's slot)."""
         P, cfg, n = self.P, self.cfg, self.lay.ard_pad
         s = np.arange(P.slots)
         col = (s + k) % n
         v = np.zeros(P.slots)
-        ok = col < cfg.ard
+        ok = (col < cfg.ard) & (s % cfg.width != cfg.width - 1)   # slot width-1 carries the constant
         v[ok] = W0[s[ok] % cfg.width, col[ok]]
         return v
 
