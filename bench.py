@@ -48,12 +48,14 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=64, help="windows per step (per GPU)")
+    ap.add_argument("--batch", type=int, default=None,
+                    help="windows per step (per GPU); default 64 (vital), 8 (gesture)")
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--workload", default="vital", choices=["vital", "batching", "serving", "fc", "per-frame"],
+    ap.add_argument("--workload", default="vital",
+                    choices=["vital", "batching", "serving", "fc", "per-frame", "gesture"],
                     help="vital: the headline chain at B windows per step; batching: uneven windows through the "
                          "batcher against one call per window; serving: Poisson arrivals from many users through "
                          "the serving loop")
@@ -65,7 +67,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--tiles", default=None,
                     help="cols_width,rows_threads,keyip_windows,conv_rows: set the tile shapes instead of autotuning")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.batch is None:
+        args.batch = 8 if args.workload == "gesture" else 64
+    return args
 
 
 # ---------------------------------------------------------------------------
@@ -219,6 +224,71 @@ class OracleSample:
         dt = time.perf_counter() - t0
         frac = ev.ks_weight / self.total_weight
         return frac / dt, dt, frac
+
+
+class GestureOracleSample(OracleSample):
+    """The same time-boxed oracle sample for the gesture chain: one 3 s
+    window (30 ciphertext pairs; the two encrypted pairs repeat, the cost of
+    a pair does not depend on its values)."""
+
+    def __init__(self, seed=4343):
+        import synth
+        from oracle import ckks as ck
+        from oracle import circuits as cc
+        from oracle import params as pm
+        from oracle import plain
+        self.ck, self.cc = ck, cc
+        P = pm.gesture_params()
+        circ = cc.GestureCircuit(P, cc.GestureConfig())
+        rots = circ.rotations()
+        kd = synth.KeyDraws(seed, P.n, P.q, P.p, P.dnum, rots)
+        sk = ck.SecretKey(P, kd.secret)
+        pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
+        self.rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
+        self.gks = {k: ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
+        del kd
+        self.consts = circ.constants(gesture_random_mats(circ.cfg, seed))
+        packed = circ.lay.pack(plain.gesture_preprocess(synth.gesture_window(seed).z))
+        two = [tuple(ck.encrypt(P, pk, ck.encode(P, v, P.scale, P.L), *synth.encryption_draws(seed + 2 * i + h, P.n))
+                     for h, v in enumerate(packed[i])) for i in range(2)]
+        self.pairs = [two[i % 2] for i in range(circ.lay.pairs)]
+        self.P, self.circ = P, circ
+        counter = cc.CountingEvaluator(P)
+
+        class Shapes(dict):
+            def __missing__(self, k):
+                return None
+        circ.run(counter, Shapes(), [(cc._Shape(P.L), cc._Shape(P.L))] * circ.lay.pairs)
+        self.total_weight = counter.ks_weight
+
+    def run(self, budget_s):
+        ev = self.cc.BudgetEvaluator(self.P, self.rlk, self.gks, budget_s)
+        t0 = time.perf_counter()
+        try:
+            self.circ.run(ev, self.consts, self.pairs)
+        except self.cc.SampleBudgetExceeded:
+            pass
+        dt = time.perf_counter() - t0
+        frac = ev.ks_weight / self.total_weight
+        return frac / dt, dt, frac
+
+
+def gesture_random_mats(cfg, seed):
+    """Random-init weights of the gesture network (the chain's cost does not
+    depend on them): FC1 width x (A R D + 1), FC2 and FC3 width x width with
+    the constant row."""
+    g = np.random.default_rng(seed)
+    W, (d1, d2, c) = cfg.width, cfg.fc_dims
+    W0 = np.zeros((W, cfg.ard + 1))
+    W0[:d1] = g.normal(0, 1.0 / np.sqrt(cfg.ard), (d1, cfg.ard + 1))
+    mats = [W0]
+    for a, b in ((d1, d2), (d2, c)):
+        M = np.zeros((W, W))
+        M[:b, :a] = g.normal(0, 1.0 / np.sqrt(a), (b, a))
+        M[:b, W - 1] = g.normal(0, 0.1, b)
+        M[W - 1, W - 1] = 1.0
+        mats.append(M)
+    return mats
 
 
 def cpu_cores():
@@ -795,6 +865,121 @@ def run_per_frame(args, rank, world, local):
     }
 
 
+GESTURE_WORKLOAD = ("gesture chain (K3 Doppler DFT, K1, K6 notch, soft power gamma=4, weighting, frame sum, "
+                    "FC1^2, FC2^2, FC3; depth 11), CKKS N=2^15, Q=60+11x50 bits, P=4x60 bits, dnum=3, "
+                    "60 frames x 4 antennas x 64 bins x 32 chirps per 3 s window, 60 input cts")
+
+
+class GestureShape:
+    """The gesture network's shape (the sizes of the library's default
+    gesture_config)."""
+    antennas, bins, chirps, fc_dims, width = 4, 64, 32, (31, 16, 6), 32
+    ard = 4 * 64 * 32
+
+
+def run_gesture(args, rank, world, local):
+    """The gesture chain on B windows per step (every ciphertext pair of every
+    window in each launch): windows/s, e2e through mmfhe_eval with pinned host
+    buffers, per-kernel roofline, clocks."""
+    import torch
+
+    import paper_2603_22437_b300 as M
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    params = M.gesture_params()
+    ctx = M.Context(params, device=local)
+    plan = ctx.plan(M.gesture_config())
+    plan.encode_consts()
+    for l, W in enumerate(gesture_random_mats(GestureShape, 11)):
+        plan.set_fc_layer(l, W)
+    P_q, P_p = params.primes_q, params.primes_p
+    n = 1 << params.log_n
+    g = synth.rng(7300 + rank)
+    qp = P_q + P_p
+    keys = ctx.keys(rank)
+
+    def key_words():
+        return np.ascontiguousarray(np.stack([np.stack([synth.uniform_residues(g, qp, n) for _ in range(2)])
+                                              for _ in range(params.dnum)]))
+
+    keys.set_relin(key_words())
+    for k in plan.rotations():
+        keys.set_galois(k, key_words())
+    n_in, _, out_levels = plan.io()
+    B = args.batch
+    tiles = pick_tiles(ctx, args, B)
+    in_words = n_in * 2 * len(P_q) * n
+    out_words = sum(2 * (l + 1) * n for l in out_levels)
+    # one window of uniform ciphertexts, copied to every slot of the batch
+    host = synth.uniform_ciphertexts(7400 + rank, P_q, n, n_in).reshape(-1)
+    one = torch.from_numpy(host.view(np.int64)).to(dev)
+    d_in = [one.clone() for _ in range(B)]
+    del one
+    d_out = [torch.empty(out_words, dtype=torch.int64, device=dev) for _ in range(B)]
+    stream = torch.cuda.Stream(device=dev)
+
+    def step(ins, outs):
+        ctx.eval(plan, keys, ins, outs, stream=stream)
+
+    for _ in range(args.warmup):
+        step(d_in, d_out)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = ctx.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        step(d_in, d_out)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    barrier(world)
+    launches = ctx.launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    value = job_throughput(world, B * args.steps, sum(step_ms) / 1000.0)
+    # e2e: one synchronous mmfhe_eval per step on pinned host buffers
+    pin_in = [torch.from_numpy(host.view(np.int64)).pin_memory() for _ in range(B)]
+    pin_out = [torch.empty(out_words, dtype=torch.int64).pin_memory() for _ in range(B)]
+    step(pin_in, pin_out)
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step(pin_in, pin_out)
+    torch.cuda.synchronize()
+    e2e = {"value": job_throughput(world, B * args.e2e_steps, time.perf_counter() - t0), "unit": "windows/s",
+           "h2d_bytes_per_step": B * in_words * 8, "d2h_bytes_per_step": B * out_words * 8,
+           "api": "mmfhe_eval on pinned host buffers (copies in, evaluation, copies out in sequence)"}
+    ctx.profile(True)
+    step(d_in, d_out)
+    torch.cuda.synchronize()
+    prof = ctx.profile()
+    ctx.profile(False)
+    bf64_peak, bf32_peak = ctx.butterfly_peak()
+    roofline = roofline_of(prof, bf64_peak, bf32_peak, B)
+    roofline["traffic"] = None   # the committed DRAM counters are of the vital chain's launches
+    return {
+        "metric": "encrypted gesture windows/s", "value": value, "unit": "windows/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": GESTURE_WORKLOAD, "batch_windows": B, "windows_per_step_all_gpus": world * B,
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2 (%d MiB of ciphertexts per step)" % (B * in_words * 8 >> 20),
+                   "weights": "random-init FC weights of the network's shape", "tiles": tiles},
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
+                       "note": "latency of a window = its batch's step time"},
+        "paper_context": "5.76 s per 3 s gesture window on one RTX 3090 Ti (FIDESlib), batched packing",
+        "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk, "wall_s_timed": wall,
+    }
+
+
 def cc_fc_forward(mats, x):
     """FP64 forward of the folded network (the labels encrypted inference must reproduce)."""
     v = np.zeros(128)
@@ -816,6 +1001,17 @@ def main():
     if args.workload in ("batching", "serving", "fc", "per-frame"):
         line = {"batching": run_batching, "serving": run_serving, "fc": run_fc,
                 "per-frame": run_per_frame}[args.workload](args, rank, world, local)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+    if args.workload == "gesture":
+        line = run_gesture(args, rank, world, local)
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            v, dt, frac = GestureOracleSample().run(args.cpu_sample_s)
+            line["cpu_baseline"] = {"value": v, "unit": "windows/s", "cores": 1, "kind": "oracle",
+                                    "host_cores_available": cpu_cores(),
+                                    "sample": "first %.1f s of one gesture window's chain (%.2f%% of its key-switch "
+                                              "limb units)" % (dt, 100 * frac)}
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <set>
 
 #include "engine.h"
 #include "hostmath.h"
@@ -350,9 +351,60 @@ CtB bsgs(Context &c, const Keys &k, const std::vector<BsgsTerm> &terms, int n1, 
         }
     }
     if (groups.empty()) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: no diagonals");
+    // the distinct baby steps: when they fit one reduction, every giant step's
+    // inner sum comes from one pass over them (MULTI_SUM_GROUPS at a time)
+    std::vector<const CtB *> babies;
+    std::map<const CtB *, int> bpos;
+    for (auto &kv : groups)
+        for (const Item &it : kv.second)
+            if (bpos.emplace(it.baby, (int)babies.size()).second) babies.push_back(it.baby);
+    const int tmax = std::min(MAX_SUM_TERMS, c.sum_terms_max);
+    bool fused = (int)babies.size() <= tmax && groups.size() > 1;
+    for (auto &kv : groups) {   // one diagonal per baby step and group
+        std::set<const CtB *> seen;
+        for (const Item &it : kv.second) fused &= seen.insert(it.baby).second;
+    }
+    std::map<int, CtB> inners;
+    if (fused) {
+        for (const CtB *bb : babies)
+            if (bb->level != level || bb->B != B) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "bsgs: operand levels differ");
+        std::vector<int> gs;
+        for (auto &kv : groups) gs.push_back(kv.first);
+        for (size_t g0 = 0; g0 < gs.size(); g0 += MULTI_SUM_GROUPS) {
+            MultiSumTerms mt{};
+            mt.nt = (int)babies.size();
+            mt.ng = (int)std::min<size_t>(MULTI_SUM_GROUPS, gs.size() - g0);
+            for (int t = 0; t < mt.nt; t++) mt.ct[t] = babies[t]->ptr();
+            for (int j = 0; j < mt.ng; j++) {
+                const int g = gs[g0 + j];
+                CtB inner = ct_new(c, B, level, scale);
+                mt.out[j] = inner.ptr();
+                for (const Item &it : groups[g]) {
+                    if (it.pt->level != level) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "bsgs: operand levels differ");
+                    if (!it.pt->mont) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: diagonals must be in Montgomery form");
+                    mt.pt[j][bpos[it.baby]] = it.pt->buf.get();
+                }
+                inners.emplace(g, std::move(inner));
+            }
+            k_launch_mul_plain_sum_multi(c, mt, B, level, false, st);
+        }
+    }
     CtB acc;
     bool have = false;
     for (auto &kv : groups) {
+        if (!inners.empty()) {
+            CtB &inner = inners.at(kv.first);
+            if (!have) {
+                acc = kv.first != 0 ? rotate(c, k, inner, kv.first * n1 * stride, st) : std::move(inner);
+                have = true;
+            } else if (kv.first != 0) {
+                acc = rotate_add(c, k, inner, kv.first * n1 * stride, acc, st);   // acc + Rot(inner)
+            } else {
+                ct_addsub(c, acc, acc, inner, false, st);
+            }
+            inners.erase(kv.first);
+            continue;
+        }
         // one fused launch per MAX_SUM_TERMS products of the giant step
         CtB inner = ct_new(c, B, level, scale);
         const auto &items = kv.second;

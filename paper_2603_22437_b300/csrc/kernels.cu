@@ -93,6 +93,52 @@ __global__ void k_group_sum(uint64_t *out, const uint64_t *in, size_t words, siz
     }
 }
 
+// All giant steps of a BSGS product from one read of the baby steps.  A CTA
+// owns MULTI_X consecutive slots x of one row (h, i) and walks every window:
+// its threads keep the ng x T constant words of their own x in shared memory
+// (read once per launch; each thread touches only its own column, so no
+// barrier is needed), load the T baby words of a window once, and write the
+// ng giant-step sums.
+constexpr int MULTI_X = 64;
+template <int T>
+__global__ void __launch_bounds__(MULTI_X)
+    k_mul_plain_sum_multi(MultiSumTerms a, int B, int logn, int nl, ModTab mt, int accumulate) {
+    extern __shared__ uint64_t sp[];   // [ng][T][MULTI_X]
+    const uint32_t n = 1u << logn;
+    const uint32_t tiles = n / MULTI_X;
+    const uint32_t row = blockIdx.x / tiles;          // h * nl + i
+    const int i = (int)(row % (uint32_t)nl);
+    const uint32_t x = (blockIdx.x % tiles) * MULTI_X + threadIdx.x;
+    const size_t poff = ((size_t)i << logn) + x;
+    const int ng = a.ng, nt = a.nt;
+    for (int g = 0; g < ng; g++)
+#pragma unroll
+        for (int t = 0; t < T; t++)
+            sp[(g * T + t) * MULTI_X + threadIdx.x] = (t < nt && a.pt[g][t]) ? __ldg(a.pt[g][t] + poff) : 0;
+    const uint64_t q = mt.q[i], qinv = mt.qinv[i];
+    const size_t wstride = (size_t)2 * nl << logn;
+    const size_t off = ((size_t)row << logn) + x;
+    uint64_t v[T], vn[T];
+#pragma unroll
+    for (int t = 0; t < T; t++) v[t] = t < nt ? __ldg(a.ct[t] + off) : 0;
+    for (int b = 0; b < B; b++) {
+        const size_t wo = (size_t)b * wstride + off;
+        // the next window's baby words load under this window's arithmetic
+#pragma unroll
+        for (int t = 0; t < T; t++) vn[t] = (t < nt && b + 1 < B) ? __ldg(a.ct[t] + wo + wstride) : 0;
+        for (int g = 0; g < ng; g++) {
+            uint64_t hi = 0, lo = 0;
+#pragma unroll
+            for (int t = 0; t < T; t++) mm::mac128(hi, lo, v[t], sp[(g * T + t) * MULTI_X + threadIdx.x]);
+            const uint64_t r = mm::redc(hi, lo, q, qinv);
+            uint64_t *o = a.out[g] + wo;
+            *o = accumulate ? mm::add_mod(*o, r, q) : r;
+        }
+#pragma unroll
+        for (int t = 0; t < T; t++) v[t] = vn[t];
+    }
+}
+
 // Rows into (to = 1) or out of (to = 0) Montgomery form, in place.
 __global__ void k_mont_convert(uint64_t *base, RowMap map, size_t rows, int logn, ModTab mt, int to) {
     const uint32_t n = 1u << logn;
@@ -613,6 +659,31 @@ void k_launch_mul_plain_sum(Context &c, uint64_t *out, const SumTerms &terms, in
     // reads every term once, its constant once, writes (and reads, when accumulating) the output
     double bytes = W8(words * (terms.n + (acc ? 2 : 1)) + (size_t)terms.n * nl * c.n);
     LAUNCH(c, "mul_plain_sum", bytes, g, k_mul_plain_sum, out, terms, words, c.logn, nl, c.mods, acc ? 1 : 0);
+}
+
+void k_launch_mul_plain_sum_multi(Context &c, const MultiSumTerms &terms, int B, int level, bool acc,
+                                  cudaStream_t st) {
+    const int nl = level + 1;
+    if (B <= 0 || terms.ng <= 0 || terms.nt <= 0) return;
+    if (terms.ng > MULTI_SUM_GROUPS || terms.nt > MAX_SUM_TERMS || terms.nt > c.sum_terms_max)
+        throw Error(MMFHE_ERR_BAD_ARG, "mul_plain_sum_multi: too many groups or terms");
+    if (c.n % MULTI_X) throw Error(MMFHE_ERR_BAD_ARG, "mul_plain_sum_multi: ring too small");
+    const int T = terms.nt <= 8 ? 8 : MAX_SUM_TERMS;
+    const size_t smem = (size_t)terms.ng * T * MULTI_X * sizeof(uint64_t);
+    const dim3 g((unsigned)((size_t)2 * nl * c.n / MULTI_X));
+    const size_t words = (size_t)B * 2 * nl * c.n;
+    // reads every baby step once and every constant once; writes (and reads, when accumulating) ng outputs
+    const double bytes = W8(words * (size_t)(terms.nt + terms.ng * (acc ? 2 : 1)) +
+                            (size_t)terms.ng * terms.nt * nl * c.n);
+    auto go = [&](auto kern) {
+        if (smem > 48 * 1024) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        kernel_begin(c, st);
+        kern<<<g, MULTI_X, smem, st>>>(terms, B, c.logn, nl, c.mods, acc ? 1 : 0);
+        kernel_end(c, "mul_plain_sum", g, dim3(MULTI_X), bytes, st);
+        CK(cudaGetLastError());
+    };
+    if (T == 8) go(k_mul_plain_sum_multi<8>);
+    else go(k_mul_plain_sum_multi<MAX_SUM_TERMS>);
 }
 
 void k_launch_lincomb(Context &c, uint64_t *out, const LincombTerms &terms, int B, int level, bool acc,

@@ -106,6 +106,19 @@ struct SumTerms {
 void k_launch_mul_plain_sum(Context &c, uint64_t *out, const SumTerms &terms, int B, int level, bool acc,
                             cudaStream_t st);
 
+// Every giant step of a BSGS product in one pass over its baby steps:
+// out_g (+)= sum_t ct_t * pt_{g,t} for g < ng (pt_{g,t} = nullptr: absent),
+// ng <= MULTI_SUM_GROUPS, nt <= min(MAX_SUM_TERMS, Context::sum_terms_max).
+constexpr int MULTI_SUM_GROUPS = 4;
+struct MultiSumTerms {
+    const uint64_t *ct[MAX_SUM_TERMS];
+    const uint64_t *pt[MULTI_SUM_GROUPS][MAX_SUM_TERMS];
+    uint64_t *out[MULTI_SUM_GROUPS];
+    int nt, ng;
+};
+void k_launch_mul_plain_sum_multi(Context &c, const MultiSumTerms &terms, int B, int level, bool acc,
+                                  cudaStream_t st);
+
 // Linear combination with scalar constants: out (+)= sum_k s_k * ct_k over a
 // batch at one level, s_k[i] = the scalar's residue mod q_i in Montgomery
 // form; at most Context::sum_terms_max terms per launch.
