@@ -351,20 +351,22 @@ def measured_peaks():
     return 6400.0, "fallback"
 
 
-def ncu_traffic(kernel, batch):
+def ncu_traffic(kernel, batch, workload=None):
     """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
     was captured on the current kernel sources; scaled from the captured batch
-    to `batch` windows (every launch covers all windows of the batch)."""
+    to `batch` windows (every launch covers all windows of the batch).
+    workload=None: the vital chain; "gesture": the gesture chain's capture."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
     j = json.load(open(p))
     if j.get("csrc_hash") != csrc_hash():
         return None
-    k = j.get("kernels", {}).get(kernel)
+    sec = j if workload is None else j.get(workload, {})
+    k = sec.get("kernels", {}).get(kernel)
     if k is None:
         return None
-    return k.get("dram_bytes_per_launch_full_size") * batch / j.get("batch", batch)
+    return k.get("dram_bytes_per_launch_full_size") * batch / sec.get("batch", batch)
 
 
 def pick_tiles(ctx, args, batch):
@@ -964,7 +966,8 @@ def run_gesture(args, rank, world, local):
     ctx.profile(False)
     bf64_peak, bf32_peak = ctx.butterfly_peak()
     roofline = roofline_of(prof, bf64_peak, bf32_peak, B)
-    roofline["traffic"] = None   # the committed DRAM counters are of the vital chain's launches
+    roofline["traffic"] = ncu_traffic(roofline["kernel"], B, "gesture")
+    roofline["traffic_source"] = "profiles/ncu_traffic.json (gesture capture at B = 4, scaled by B / 4)"
     return {
         "metric": "encrypted gesture windows/s", "value": value, "unit": "windows/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
