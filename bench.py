@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", default="vital",
-                    choices=["vital", "batching", "serving", "fc", "per-frame", "gesture"],
+                    choices=["vital", "batching", "serving", "serving-mix", "fc", "per-frame", "gesture"],
                     help="vital: the headline chain at B windows per step; batching: uneven windows through the "
                          "batcher against one call per window; serving: Poisson arrivals from many users through "
                          "the serving loop")
@@ -730,6 +730,115 @@ def run_serving(args, rank, world, local):
     return line
 
 
+def run_serving_mix(args, rank, world, local):
+    """Poisson arrivals from --users devices mixing 10 s vital-sign windows and
+    3 s gesture windows (every fourth device is a gesture device): two
+    parameter sets on one GPU (vital N=2^15 Delta=2^40, gesture N=2^15
+    Delta=2^50), one serving loop each, both running concurrently on their
+    own streams; keys resident under a budget per server.  Latency = submit ->
+    output in host memory, per window kind."""
+    import torch
+
+    import paper_2603_22437_b300 as M
+    import synth
+
+    torch.cuda.set_device(local)
+    g = synth.rng(5100 + rank)
+    kinds = {}
+    for name, params, cfg, budget_gib, max_batch in (
+            ("vital", M.vital_params(), M.vital_config(), args.key_budget_gib, args.batch),
+            ("gesture", M.gesture_params(), M.gesture_config(), 16.0, 4)):
+        ctx = M.Context(params, device=local)
+        n = 1 << params.log_n
+        plan = ctx.plan(cfg)
+        rots = plan.rotations()
+        n_in, _, lv = plan.io()
+        qp = params.primes_q + params.primes_p
+
+        def key_words():
+            return torch.from_numpy(np.ascontiguousarray(np.stack([np.stack([synth.uniform_residues(g, qp, n)
+                                                                              for _ in range(2)])
+                                                                    for _ in range(params.dnum)])).view(np.int64)).pin_memory()
+
+        relin = key_words()
+        gal = {r: key_words() for r in rots}
+        srv = ctx.server(cfg, max_batch=max_batch, streams=2, key_budget_bytes=int(budget_gib * 2**30),
+                         batch_wait_us=20000)
+        if name == "gesture":
+            for l, W in enumerate(gesture_random_mats(GestureShape, 13)):
+                srv.set_fc_layer(l, W)
+        nbuf = 4
+        ins = [torch.from_numpy(synth.uniform_ciphertexts(8100 + 10 * len(kinds) + i, params.primes_q, n, n_in)
+                                .reshape(-1).view(np.int64)).pin_memory() for i in range(nbuf)]
+        out_words = sum(2 * (l + 1) * n for l in lv)
+        outs = [torch.empty(out_words, dtype=torch.int64).pin_memory() for _ in range(256)]
+        kinds[name] = dict(ctx=ctx, srv=srv, ins=ins, outs=outs, relin=relin, gal=gal,
+                           frames=200 if name == "vital" else 60,
+                           key_set=(1 + len(rots)) * relin.numel() * 8, budget_gib=budget_gib, ring=0)
+    devices = [("gesture" if u % 4 == 0 else "vital") for u in range(args.users)]
+    for u, kname in enumerate(devices):
+        k = kinds[kname]
+        k["srv"].add_user(u, k["relin"], k["gal"])
+
+    def submit(u):
+        k = kinds[devices[u]]
+        t = k["srv"].submit(u, k["frames"], k["ins"][k["ring"] % len(k["ins"])], k["outs"][k["ring"] % len(k["outs"])])
+        k["ring"] += 1
+        return devices[u], t
+
+    draw = np.random.default_rng(78 + rank)
+    warm = [submit(u) for u in list(range(min(8, args.users))) * 2]   # plans, first key loads, pools
+    for kname, t in warm:
+        kinds[kname]["srv"].wait(t)
+    phases = []
+    for load in [float(x) for x in args.loads.split(",")]:
+        st0 = {kn: k["srv"].stats() for kn, k in kinds.items()}
+        arrivals = np.cumsum(draw.exponential(1.0 / load, size=int(load * args.phase_s * 1.5) + 8))
+        arrivals = arrivals[arrivals < args.phase_s]
+        tickets = []
+        t0 = time.perf_counter()
+        for at in arrivals:
+            dt = at - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            tickets.append(submit(int(draw.integers(args.users))))
+        lat = {"vital": [], "gesture": []}
+        for kname, t in tickets:
+            lat[kname].append(kinds[kname]["srv"].wait(t))
+        t_end = time.perf_counter()
+        st1 = {kn: k["srv"].stats() for kn, k in kinds.items()}
+        ph = {"offered_windows_per_s": load, "windows": len(tickets),
+              "achieved_windows_per_s": len(tickets) / (t_end - t0)}
+        for kname in kinds:
+            L = lat[kname]
+            b = st1[kname]["batches"] - st0[kname]["batches"]
+            ph[kname] = {"windows": len(L), "p50_ms": float(np.percentile(L, 50)) if L else None,
+                         "p99_ms": float(np.percentile(L, 99)) if L else None, "batches": b,
+                         "mean_batch": (st1[kname]["completed"] - st0[kname]["completed"]) / max(1, b),
+                         "key_loads": st1[kname]["key_loads"] - st0[kname]["key_loads"]}
+        phases.append(ph)
+    stats = {kn: k["srv"].stats() for kn, k in kinds.items()}
+    for k in kinds.values():
+        k["srv"].close()
+    top = max(phases, key=lambda p: p["achieved_windows_per_s"])
+    all_lat_p99 = max(top[kn]["p99_ms"] or 0.0 for kn in kinds)
+    return {
+        "metric": METRIC, "value": top["achieved_windows_per_s"], "unit": "windows/s", "n_gpus": world,
+        "steps": len(phases), "warmup": 1, "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serving mix: Poisson arrivals from %d devices (3 of 4 send 10 s vital-sign windows, "
+                               "N=2^15 Delta=2^40 chain; 1 of 4 sends 3 s gesture windows, N=2^15 Delta=2^50 "
+                               "chain), own key sets; one serving loop per parameter set on one GPU, 2 stream "
+                               "slots each; key budgets %.0f / %.0f GiB (%.2f / %.2f GiB per key set)"
+                               % (args.users, kinds["vital"]["budget_gib"], kinds["gesture"]["budget_gib"],
+                                  kinds["vital"]["key_set"] / 2**30, kinds["gesture"]["key_set"] / 2**30)},
+        "latency_ms": {"p99_worst_kind": all_lat_p99, "vital_p50": top["vital"]["p50_ms"],
+                       "vital_p99": top["vital"]["p99_ms"], "gesture_p50": top["gesture"]["p50_ms"],
+                       "gesture_p99": top["gesture"]["p99_ms"], "note": "at the highest achieved load"},
+        "phases": phases, "server_stats": stats,
+    }
+
+
 def run_fc(args, rank, world, local):
     """Encrypted inference of the learned polynomial network (three dense
     layers 120 -> 32 -> 16 -> 6 with squares, N = 2^14, depth 5) on synthetic
@@ -1001,8 +1110,8 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.workload in ("batching", "serving", "fc", "per-frame"):
-        line = {"batching": run_batching, "serving": run_serving, "fc": run_fc,
+    if args.workload in ("batching", "serving", "serving-mix", "fc", "per-frame"):
+        line = {"batching": run_batching, "serving": run_serving, "serving-mix": run_serving_mix, "fc": run_fc,
                 "per-frame": run_per_frame}[args.workload](args, rank, world, local)
         if rank == 0:
             print(json.dumps(line), flush=True)

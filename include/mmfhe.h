@@ -521,6 +521,12 @@ mmfhe_status mmfhe_server_add_user(mmfhe_server *s, uint64_t user_id, const uint
 /* Queue one window (input and output as for mmfhe_eval; host buffers should
  * be pinned for the copies to overlap).  *ticket identifies it.  NOT_FOUND
  * for an unknown user. */
+/* Learned layers (FC and GESTURE servers): layer `layer` as for
+ * mmfhe_plan_set_fc_layer, `count` doubles (FC: D x D; GESTURE: layer 0
+ * fc_width x (A R D + 1), layers 1-2 fc_width x fc_width), copied and applied
+ * to every plan the server creates.  Call before the first submit (BUSY
+ * after); BAD_ARG for another circuit, layer or size. */
+mmfhe_status mmfhe_server_set_fc_layer(mmfhe_server *s, uint32_t layer, const double *W, size_t count);
 mmfhe_status mmfhe_server_submit(mmfhe_server *s, uint64_t user_id, uint32_t frames, const uint64_t *in,
                                  uint64_t *out, uint64_t *ticket);
 /* Wait up to timeout_ms for a window: OK (output written; *latency_ms =

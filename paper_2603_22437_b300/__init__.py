@@ -434,6 +434,11 @@ class Server:
         self.ctx._c(_lib.lib().mmfhe_server_add_user(self.h, user_id, ptr(relin), rarr, garr, len(rots)))
         self._users[user_id] = (relin, galois, rarr, garr)
 
+    def set_fc_layer(self, layer, W):
+        """FC / gesture servers: a learned layer for every plan (before the first submit)."""
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        self.ctx._c(_lib.lib().mmfhe_server_set_fc_layer(self.h, layer, ptr(W), W.size))
+
     def submit(self, user_id, frames, inp, out):
         t = ctypes.c_uint64()
         self.ctx._c(_lib.lib().mmfhe_server_submit(self.h, user_id, frames, ptr(inp), ptr(out), ctypes.byref(t)))

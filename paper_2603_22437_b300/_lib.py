@@ -124,6 +124,7 @@ _SIGS = {
     "mmfhe_graph_destroy": [_VP],
     "mmfhe_server_create": [_VP, _VP, _SZ, _VP, _PP],
     "mmfhe_server_add_user": [_VP, _U64, _VP, _VP, _VP, _U32],
+    "mmfhe_server_set_fc_layer": [_VP, _U32, _VP, _SZ],
     "mmfhe_server_submit": [_VP, _U64, _U32, _VP, _VP, ctypes.POINTER(_U64)],
     "mmfhe_server_wait": [_VP, _U64, _U32, ctypes.POINTER(ctypes.c_double)],
     "mmfhe_server_drain": [_VP, _U32],

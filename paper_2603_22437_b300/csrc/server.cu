@@ -67,7 +67,8 @@ struct mmfhe_server {
         std::vector<User *> users;   // distinct users of the running batch (pinned)
     };
     std::vector<Slot> slots;
-    std::map<uint32_t, std::unique_ptr<Plan>> plans;   // worker thread only
+    std::map<uint32_t, std::unique_ptr<Plan>> plans;   // worker thread creates; count read under mu
+    std::map<uint32_t, std::vector<double>> fc_layers; // learned layers applied to every plan (guarded by mu)
 
     // statistics (guarded by mu)
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batch_windows = 0;
@@ -93,7 +94,14 @@ struct mmfhe_server {
             mmfhe_circuit_config cc = base;
             cc.frames = frames;
             std::unique_ptr<Plan> p(create_plan(*c, cc));
-            plan_encode_consts(*p, 0);
+            if (base.kind != MMFHE_CIRCUIT_FC) plan_encode_consts(*p, 0);
+            std::map<uint32_t, std::vector<double>> layers;
+            {
+                std::lock_guard<std::mutex> g(mu);
+                layers = fc_layers;
+            }
+            for (auto &kv : layers) plan_set_fc_layer(*p, kv.first, kv.second.data());
+            std::lock_guard<std::mutex> g(mu);
             it = plans.emplace(frames, std::move(p)).first;
         }
         return *it->second;
@@ -423,6 +431,21 @@ mmfhe_status mmfhe_server_add_user(mmfhe_server *s, uint64_t user_id, const uint
         if (!galois[i]) return sfail(s->c, MMFHE_ERR_BAD_ARG, "null Galois key");
         u.galois.push_back({rotations[i], galois[i]});
     }
+    return MMFHE_OK;
+}
+
+mmfhe_status mmfhe_server_set_fc_layer(mmfhe_server *s, uint32_t layer, const double *W, size_t count) {
+    if (!s || !W) return sfail(nullptr, MMFHE_ERR_BAD_ARG, "null argument");
+    const mmfhe_circuit_config &b = s->base;
+    size_t want = 0;
+    if (b.kind == MMFHE_CIRCUIT_FC && layer < b.taps) want = (size_t)b.bins * b.bins;
+    if (b.kind == MMFHE_CIRCUIT_GESTURE && layer < 3)
+        want = layer == 0 ? (size_t)b.fc_width * (b.fc_dims[0] + 1) : (size_t)b.fc_width * b.fc_width;
+    if (!want) return sfail(s->c, MMFHE_ERR_BAD_ARG, "the server's circuit has no such learned layer");
+    if (count != want) return sfail(s->c, MMFHE_ERR_BAD_ARG, "wrong layer size");
+    std::lock_guard<std::mutex> g(s->mu);
+    if (!s->plans.empty() || s->submitted) return sfail(s->c, MMFHE_ERR_BUSY, "layers are set before the first submit");
+    s->fc_layers[layer].assign(W, W + count);
     return MMFHE_OK;
 }
 

@@ -98,3 +98,82 @@ def test_serving_mix_equals_alone(gsmall):
             ctx.eval(plans[F], k, [x], [ref])
             assert np.array_equal(out, ref), "window %d (user %d, F=%d)" % (i, u, F)
         k.unload()
+
+
+def test_serving_vital_and_gesture_windows_concurrently(gsmall):
+    """Two parameter sets on one GPU (the small FIR+DFT instance and the
+    gesture chain's N = 2^15, Delta = 2^50 ring), one server each, windows of
+    both kinds and several users submitted interleaved from two threads:
+    every output equals the window evaluated alone."""
+    import paper_2603_22437_b300 as M
+    from oracle import params as pm
+    from test_gpu_parity import lib_params
+    P1, ctx1 = gsmall["P"], gsmall["ctx"]
+    P2 = pm.gesture_params()
+    ctx2 = M.Context(lib_params(P2))
+    gcfg = M.gesture_config(antennas=1, bins=8, chirps=32, frames=4, fc_dims=(7, 5, 3), fc_width=16)
+    cfg1 = M.fir_dft_config(bins=40)
+    plan1, plan2 = ctx1.plan(cfg1), ctx2.plan(gcfg)
+    plan1.encode_consts()
+    plan2.encode_consts()
+    g = np.random.default_rng(5)
+    ard = 1 * 8 * 32
+    mats = [np.zeros((16, ard + 1)), np.zeros((16, 16)), np.zeros((16, 16))]
+    mats[0][:7] = g.normal(0, 0.1, (7, ard + 1))
+    mats[1][:5, :7] = g.normal(0, 0.3, (5, 7))
+    mats[2][:3, :5] = g.normal(0, 0.3, (3, 5))
+    for m in mats[1:]:
+        m[15, 15] = 1.0
+    for l, W in enumerate(mats):
+        plan2.set_fc_layer(l, W)
+    users1 = {u: user_keys(P1, plan1.rotations(), 60 + u) for u in range(2)}
+    users2 = {u: user_keys(P2, plan2.rotations(), 70 + u) for u in range(2)}
+    srv1 = ctx1.server(cfg1, max_batch=2, streams=2)
+    srv2 = ctx2.server(gcfg, max_batch=2, streams=1)
+    for l, W in enumerate(mats):
+        srv2.set_fc_layer(l, W)
+    with pytest.raises(M.MmfheError):
+        srv1.set_fc_layer(0, mats[1])      # the FIR+DFT circuit has no learned layers
+    for u, (r, gal) in users1.items():
+        srv1.add_user(u, r, gal)
+    for u, (r, gal) in users2.items():
+        srv2.add_user(u, r, gal)
+    jobs = []
+    for i in range(8):
+        kind = i % 2
+        P, plan = (P1, plan1) if kind == 0 else (P2, plan2)
+        n_in, _, lv = plan.io()
+        x = np.ascontiguousarray(rand_ct(P, P.L, 500 + i, n_in).reshape(-1))
+        out = np.zeros(sum(2 * (l + 1) * P.n for l in lv), dtype=np.uint64)
+        jobs.append((kind, (i // 2) % 2, x, out))
+    tickets = [None] * len(jobs)
+
+    def producer(idx):
+        for i in idx:
+            kind, u, x, out = jobs[i]
+            srv = srv1 if kind == 0 else srv2
+            tickets[i] = (srv, srv.submit(u, 200 if kind == 0 else 4, x, out))
+
+    th = [threading.Thread(target=producer, args=(list(range(k, len(jobs), 2)),)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for srv, t in tickets:
+        assert srv.wait(t) > 0
+    assert srv1.stats()["completed"] == 4 and srv2.stats()["completed"] == 4
+    srv1.close()
+    srv2.close()
+    for kind, ctx, plan, users in ((0, ctx1, plan1, users1), (1, ctx2, plan2, users2)):
+        for u, (relin, gal) in users.items():
+            k = ctx.keys(200 + u)
+            k.set_relin(relin)
+            for r, w in gal.items():
+                k.set_galois(r, w)
+            for i, (kk, uu, x, out) in enumerate(jobs):
+                if kk != kind or uu != u:
+                    continue
+                ref = np.empty_like(out)
+                ctx.eval(plan, k, [x], [ref])
+                assert np.array_equal(out, ref), "window %d (kind %d, user %d)" % (i, kind, u)
+            k.unload()
