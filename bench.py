@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", default="vital",
-                    choices=["vital", "batching", "serving", "serving-mix", "fc", "per-frame", "gesture"],
+                    choices=["vital", "batching", "serving", "serving-mix", "fc", "per-frame", "gesture",
+                             "ntt-ablation"],
                     help="vital: the headline chain at B windows per step; batching: uneven windows through the "
                          "batcher against one call per window; serving: Poisson arrivals from many users through "
                          "the serving loop")
@@ -839,6 +840,83 @@ def run_serving_mix(args, rank, world, local):
     }
 
 
+def run_ntt_ablation(args, rank, world, local):
+    """Word-size ablation: the batched negacyclic NTT (forward + inverse) of B
+    RNS polynomials at N = 2^15, 64-bit words (the chains' primes) against
+    32-bit words (30-bit primes) for the same modulus size: the vital chain's
+    Q (500 bits: 12 x 64-bit limbs, 17 x 32-bit) and its key-switching QP
+    (740 bits: 16 limbs, 25 limbs).  Device-resident rows, CUDA events."""
+    import torch
+
+    import paper_2603_22437_b300 as M
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    params = M.vital_params()
+    ctx = M.Context(params, device=local)
+    log_n, n = params.log_n, 1 << params.log_n
+    B = args.batch
+    g = np.random.default_rng(3)
+    stream = torch.cuda.Stream(device=dev)
+    peak64, peak32 = ctx.butterfly_peak()
+    reps = max(3, args.steps)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    for name, limbs64, limbs32 in (("Q of the vital chain (500 bits)", 12, 17), ("QP of its key switch (740 bits)", 16, 25)):
+        bits64 = sum(np.log2(float(q)) for q in (params.primes_q + params.primes_p)[:limbs64])
+        primes32 = M.ntt32_primes(log_n, 30, limbs32)
+        bits32 = sum(np.log2(float(q)) for q in primes32)
+        # 64-bit: the evaluator's batched transform over Q primes (the QP case uses all Q rows plus
+        # the first P rows' worth of extra Q-prime rows: the work per row is the same)
+        nl = min(limbs64, len(params.primes_q))
+        blocks = B * limbs64 // nl
+        x64 = torch.from_numpy(np.stack([g.integers(0, params.primes_q[i % nl], n, dtype=np.uint64)
+                                         for i in range(blocks * nl)]).view(np.int64)).to(dev)
+        ms64 = timed(lambda: (ctx.ntt_batch(x64, blocks, nl, False, stream), ctx.ntt_batch(x64, blocks, nl, True, stream)))
+        nt = M.Ntt32(log_n, primes32, device=local)
+        x32 = torch.from_numpy(np.stack([g.integers(0, primes32[i % limbs32], n, dtype=np.uint32)
+                                         for i in range(B * limbs32)]).view(np.int32)).to(dev)
+        ms32 = timed(lambda: (nt.run(x32, False, stream), nt.run(x32, True, stream)))
+        nt.close()
+        bf64 = 2 * blocks * nl * (n // 2) * log_n
+        bf32 = 2 * B * limbs32 * (n // 2) * log_n
+        out[name] = {
+            "polys": B, "u64": {"limbs": limbs64, "modulus_bits": round(bits64, 1), "ms_fwd_inv": ms64,
+                                "Gbutterfly_s": bf64 / ms64 / 1e6, "frac_of_u64_ceiling": bf64 / ms64 / 1e6 / (peak64 / 1e9),
+                                "GB_s_hbm": 2 * 2 * blocks * nl * n * 8 / ms64 / 1e6},
+            "u32": {"limbs": limbs32, "modulus_bits": round(bits32, 1), "ms_fwd_inv": ms32,
+                    "Gbutterfly_s": bf32 / ms32 / 1e6, "frac_of_u32_ceiling": bf32 / ms32 / 1e6 / (peak32 / 1e9),
+                    "GB_s_hbm": 2 * 2 * B * limbs32 * n * 4 / ms32 / 1e6},
+            # modulus bits transformed per ms: rows x mean bits per row / time
+            "u32_speedup_per_modulus_bit": (B * bits32 / ms32) / (blocks * nl * (bits64 / limbs64) / ms64),
+        }
+        del x64, x32
+        torch.cuda.empty_cache()
+    q500 = out["Q of the vital chain (500 bits)"]
+    return {
+        "metric": "RNS polynomial NTTs/s (forward + inverse), 64-bit vs 32-bit words at equal modulus",
+        "value": B / (q500["u32"]["ms_fwd_inv"] / 1000.0), "unit": "polys/s", "n_gpus": world,
+        "steps": reps, "warmup": args.warmup, "ms_per_step": q500["u32"]["ms_fwd_inv"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32 vs u64", "data": "synthetic",
+        "config": {"workload": "word-size ablation: batched negacyclic NTT + inverse of %d RNS polynomials at "
+                               "N=2^15, 64-bit limbs (the chain's primes) vs 32-bit limbs (30-bit primes) of equal "
+                               "modulus size" % B},
+        "butterfly_peak_per_s": {"u64": peak64, "u32": peak32}, "ablation": out,
+    }
+
+
 def run_fc(args, rank, world, local):
     """Encrypted inference of the learned polynomial network (three dense
     layers 120 -> 32 -> 16 -> 6 with squares, N = 2^14, depth 5) on synthetic
@@ -1110,9 +1188,9 @@ def main():
     if args.impl == "reference":
         run_reference(args, rank, world)
         return
-    if args.workload in ("batching", "serving", "serving-mix", "fc", "per-frame"):
+    if args.workload in ("batching", "serving", "serving-mix", "fc", "per-frame", "ntt-ablation"):
         line = {"batching": run_batching, "serving": run_serving, "serving-mix": run_serving_mix, "fc": run_fc,
-                "per-frame": run_per_frame}[args.workload](args, rank, world, local)
+                "per-frame": run_per_frame, "ntt-ablation": run_ntt_ablation}[args.workload](args, rank, world, local)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return

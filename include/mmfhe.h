@@ -163,6 +163,11 @@ mmfhe_status mmfhe_keys_unload(mmfhe_keys *keys);
  * evaluation order (row j holds a(psi^(2 brv(j) + 1))); inverse takes that
  * order back to coefficients. */
 mmfhe_status mmfhe_ntt(mmfhe_ctx *ctx, uint64_t *rows, const uint32_t *prime_idx, size_t num_rows, int inverse, void *stream);
+/* The batched transform the evaluator runs on ciphertexts: blocks x limbs
+ * rows of N words in DEVICE memory (16-byte aligned), row (b, i) reduced mod
+ * q_i, limbs 1..num_q; asynchronous on `stream` (two launches: the strided
+ * and the contiguous pass over every row).  BAD_ARG for host memory. */
+mmfhe_status mmfhe_ntt_batch(mmfhe_ctx *ctx, uint64_t *rows, size_t blocks, uint32_t limbs, int inverse, void *stream);
 /* out[r] = a[r] * b[r] in Z_q[X]/(X^N+1), coefficient form (at most 64 rows). */
 mmfhe_status mmfhe_poly_mul(mmfhe_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b,
                             const uint32_t *prime_idx, size_t num_rows, void *stream);
@@ -417,6 +422,28 @@ mmfhe_status mmfhe_fold_poly_net(const uint32_t *dims, uint32_t layers, float al
  * in mmfhe_fold_poly_net.  BAD_ARG as there, for d_1.. only. */
 mmfhe_status mmfhe_fold_poly_net_wide(const uint32_t *dims, uint32_t layers, float alpha, const float *weights,
                                       uint32_t width, double *first, double *mats);
+
+/* ------------------------------------------------------------------------
+ * Word-size ablation (no counterpart in the paper, whose CKKS library fixes
+ * the word size): the same negacyclic NTT on 32-bit RNS words, primes below
+ * 2^30, one shared-memory pass per row (a 32-bit row of N <= 2^15 words fits
+ * in shared memory).  Output order and convention as mmfhe_ntt (bit-reversed
+ * evaluation order; the inverse takes it back and multiplies by N^-1).
+ * ---------------------------------------------------------------------- */
+typedef struct mmfhe_ntt32 mmfhe_ntt32;
+/* Host only: the `count` largest primes below 2^bits that are 1 mod 2N,
+ * descending.  BAD_ARG: log_n outside 10..15, bits outside log_n+2..30, or
+ * too few such primes. */
+mmfhe_status mmfhe_ntt32_select_primes(uint32_t log_n, uint32_t bits, uint32_t count, uint32_t *out);
+/* Twiddle tables for num_primes (1..64) primes on `device`.  BAD_BLOB: a
+ * prime not below 2^30, not 1 mod 2N or not prime. */
+mmfhe_status mmfhe_ntt32_create(uint32_t log_n, const uint32_t *primes, uint32_t num_primes, int device,
+                                mmfhe_ntt32 **out);
+/* In place on num_rows rows of N words, row r under prime r mod num_primes,
+ * inputs reduced mod their prime.  rows: device (16-byte aligned) or host
+ * memory (staged through the device; the call then waits for the stream). */
+mmfhe_status mmfhe_ntt32_run(mmfhe_ntt32 *p, uint32_t *rows, size_t num_rows, int inverse, void *stream);
+mmfhe_status mmfhe_ntt32_destroy(mmfhe_ntt32 *p);
 
 /* ------------------------------------------------------------------------
  * Batching runtime.  The paper evaluates windows one call at a time (its

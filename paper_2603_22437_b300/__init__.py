@@ -17,7 +17,7 @@ from ._lib import (CIRCUIT_FC, CIRCUIT_FIR_DFT, CIRCUIT_GESTURE, CIRCUIT_VITAL, 
 __all__ = ["Context", "Keys", "Plan", "Graph", "Batcher", "Server", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
            "Params", "CIRCUIT_FIR_DFT", "CIRCUIT_VITAL", "CIRCUIT_FC", "vital_config", "fir_dft_config",
            "fc_config", "fir_dft_params", "vital_params", "fc_params", "fold_poly_net", "CIRCUIT_GESTURE",
-           "gesture_params", "gesture_config", "fold_poly_net_wide"]
+           "gesture_params", "gesture_config", "fold_poly_net_wide", "Ntt32", "ntt32_primes"]
 
 
 def params_select(log_n, num_q, q0_bits, q_bits, num_p, p_bits, dnum):
@@ -141,6 +141,41 @@ def gesture_config(antennas=4, bins=64, chirps=32, frames=60, fc_dims=(31, 16, 6
     return c
 
 
+def ntt32_primes(log_n, bits, count):
+    """The `count` largest primes below 2^bits that are 1 mod 2N (host only)."""
+    out = (ctypes.c_uint32 * count)()
+    check(_lib.lib().mmfhe_ntt32_select_primes(log_n, bits, count, out))
+    return [out[i] for i in range(count)]
+
+
+class Ntt32:
+    """Word-size ablation: the negacyclic NTT on 32-bit RNS words (primes
+    below 2^30), one shared-memory pass per row."""
+
+    def __init__(self, log_n, primes, device=0):
+        arr = (ctypes.c_uint32 * len(primes))(*primes)
+        h = ctypes.c_void_p()
+        check(_lib.lib().mmfhe_ntt32_create(log_n, arr, len(primes), device, ctypes.byref(h)))
+        self.h, self.log_n, self.primes = h, log_n, list(primes)
+
+    def run(self, rows, inverse=False, stream=None):
+        """In place on uint32 rows [..., N] (numpy or a CUDA tensor), row r
+        under primes[r mod len(primes)]."""
+        n_rows = (rows.numel() if hasattr(rows, "numel") else rows.size) >> self.log_n
+        check(_lib.lib().mmfhe_ntt32_run(self.h, ptr(rows), n_rows, int(inverse), stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.lib().mmfhe_ntt32_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def fir_dft_config(bins=64, frames=200, fs_mhz=20000, taps=64, band_mhz=(800, 2500)):
     c = CircuitConfig()
     c.kind, c.bins, c.frames, c.fs_mhz, c.taps = CIRCUIT_FIR_DFT, bins, frames, fs_mhz, taps
@@ -262,6 +297,10 @@ class Context:
     def ntt(self, rows, prime_idx, inverse=False, stream=None):
         pid = np.ascontiguousarray(prime_idx, dtype=np.uint32)
         self._c(_lib.lib().mmfhe_ntt(self.h, ptr(rows), ptr(pid), len(pid), int(inverse), stream_ptr(stream)))
+
+    def ntt_batch(self, rows, blocks, limbs, inverse=False, stream=None):
+        """The evaluator's batched transform on device rows [blocks][limbs][N] (asynchronous)."""
+        self._c(_lib.lib().mmfhe_ntt_batch(self.h, ptr(rows), blocks, limbs, int(inverse), stream_ptr(stream)))
 
     def poly_mul(self, out, a, b, prime_idx, stream=None):
         pid = np.ascontiguousarray(prime_idx, dtype=np.uint32)

@@ -125,6 +125,11 @@ _SIGS = {
     "mmfhe_server_create": [_VP, _VP, _SZ, _VP, _PP],
     "mmfhe_server_add_user": [_VP, _U64, _VP, _VP, _VP, _U32],
     "mmfhe_server_set_fc_layer": [_VP, _U32, _VP, _SZ],
+    "mmfhe_ntt32_select_primes": [_U32, _U32, _U32, _VP],
+    "mmfhe_ntt_batch": [_VP, _VP, _SZ, _U32, ctypes.c_int, _VP],
+    "mmfhe_ntt32_create": [_U32, _VP, _U32, ctypes.c_int, _PP],
+    "mmfhe_ntt32_run": [_VP, _VP, _SZ, ctypes.c_int, _VP],
+    "mmfhe_ntt32_destroy": [_VP],
     "mmfhe_server_submit": [_VP, _U64, _U32, _VP, _VP, ctypes.POINTER(_U64)],
     "mmfhe_server_wait": [_VP, _U64, _U32, ctypes.POINTER(ctypes.c_double)],
     "mmfhe_server_drain": [_VP, _U32],

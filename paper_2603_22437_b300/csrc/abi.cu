@@ -409,6 +409,20 @@ mmfhe_status mmfhe_ntt(mmfhe_ctx *ctx, uint64_t *rows, const uint32_t *prime_idx
     ABI_CATCH(c)
 }
 
+mmfhe_status mmfhe_ntt_batch(mmfhe_ctx *ctx, uint64_t *rows, size_t blocks, uint32_t limbs, int inverse,
+                             void *stream) {
+    Context *c = nullptr;
+    ABI_TRY
+    c = ctx_of(ctx);
+    if (blocks == 0) return MMFHE_OK;
+    if (!rows || is_host_ptr(rows) || ((uintptr_t)rows & 15)) throw Error(MMFHE_ERR_BAD_ARG, "rows must be 16-byte aligned device memory");
+    if (limbs < 1 || (int)limbs > c->num_q) throw Error(MMFHE_ERR_BAD_ARG, "limbs must be 1..num_q");
+    CK(cudaSetDevice(c->device));
+    ntt_q_blocks(*c, rows, blocks, (int)limbs, inverse != 0, (cudaStream_t)stream);
+    CK(cudaGetLastError());
+    ABI_CATCH(c)
+}
+
 mmfhe_status mmfhe_poly_mul(mmfhe_ctx *ctx, uint64_t *out, const uint64_t *a, const uint64_t *b,
                             const uint32_t *prime_idx, size_t num_rows, void *stream) {
     Context *c = nullptr;
