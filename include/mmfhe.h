@@ -125,6 +125,7 @@ typedef struct mmfhe_kernel_stat {
     double total_ms;
     double bytes;
     double butterflies;
+    double macs;        /* multiply-accumulates of fused base conversions (ModUp, ModDown strided passes) */
 } mmfhe_kernel_stat;
 mmfhe_status mmfhe_profile_enable(mmfhe_ctx *ctx, int enable);
 mmfhe_status mmfhe_profile_get(mmfhe_ctx *ctx, mmfhe_kernel_stat *out, uint32_t capacity, uint32_t *count);
@@ -136,6 +137,10 @@ mmfhe_status mmfhe_profile_get(mmfhe_ctx *ctx, mmfhe_kernel_stat *out, uint32_t 
  * warm-up launch).  No memory traffic beyond one word per thread.  Errors:
  * BAD_ARG (null output), CUDA. */
 mmfhe_status mmfhe_measure_butterfly_peak(mmfhe_ctx *ctx, double *bf64_per_s, double *bf32_per_s);
+/* The same for the base conversion's arithmetic: a register-resident loop of
+ * Montgomery multiply-accumulates (four 64-bit products summed in 128 bits,
+ * one reduction) on every SM; returns products per second. */
+mmfhe_status mmfhe_measure_mac_peak(mmfhe_ctx *ctx, double *mac64_per_s);
 
 /* ------------------------------------------------------------------------
  * Evaluation keys (paper: rlk after every ct x ct product, one Galois key

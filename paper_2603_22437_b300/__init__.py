@@ -230,7 +230,7 @@ class Context:
 
     def profile(self, enable=None):
         """Enable/disable per-kernel event profiling, or (enable=None) return
-        {kernel: (launches, total_ms, algorithmic_bytes, butterflies)}."""
+        {kernel: (launches, total_ms, algorithmic_bytes, butterflies, conversion_macs)}."""
         if enable is not None:
             self._c(_lib.lib().mmfhe_profile_enable(self.h, int(enable)))
             return None
@@ -238,8 +238,8 @@ class Context:
         self._c(_lib.lib().mmfhe_profile_get(self.h, None, 0, ctypes.byref(n)))
         arr = (_lib.KernelStat * max(1, n.value))()
         self._c(_lib.lib().mmfhe_profile_get(self.h, arr, n.value, ctypes.byref(n)))
-        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].bytes, arr[i].butterflies)
-                for i in range(n.value)}
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].total_ms, arr[i].bytes, arr[i].butterflies,
+                                       arr[i].macs) for i in range(n.value)}
 
     def butterfly_peak(self):
         """(64-bit, 32-bit) forward butterflies per second of a register-resident
@@ -247,6 +247,13 @@ class Context:
         a, b = ctypes.c_double(), ctypes.c_double()
         self._c(_lib.lib().mmfhe_measure_butterfly_peak(self.h, ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def mac_peak(self):
+        """Products per second of a register-resident loop of the base
+        conversion's Montgomery multiply-accumulate on this device."""
+        a = ctypes.c_double()
+        self._c(_lib.lib().mmfhe_measure_mac_peak(self.h, ctypes.byref(a)))
+        return a.value
 
     def keys(self, user_id=0):
         return Keys(self, user_id)

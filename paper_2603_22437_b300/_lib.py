@@ -56,7 +56,7 @@ class CircuitConfig(ctypes.Structure):
 
 class KernelStat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
-                ("bytes", ctypes.c_double), ("butterflies", ctypes.c_double)]
+                ("bytes", ctypes.c_double), ("butterflies", ctypes.c_double), ("macs", ctypes.c_double)]
 
 
 class Tuning(ctypes.Structure):
@@ -107,6 +107,7 @@ _SIGS = {
     "mmfhe_profile_enable": [_VP, _INT],
     "mmfhe_profile_get": [_VP, _VP, _U32, ctypes.POINTER(_U32)],
     "mmfhe_measure_butterfly_peak": [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "mmfhe_measure_mac_peak": [_VP, _VP],
     "mmfhe_plan_set_fc_layer": [_VP, _U32, _VP],
     "mmfhe_plan_num_scalars": [_VP, ctypes.POINTER(_U32)],
     "mmfhe_plan_get_scalars": [_VP, _VP, _U32],

@@ -322,6 +322,7 @@ mmfhe_status mmfhe_profile_get(mmfhe_ctx *ctx, mmfhe_kernel_stat *out, uint32_t 
         it->second.total_ms += ms;
         it->second.bytes += r.bytes;
         it->second.butterflies += r.butterflies;
+        it->second.macs += r.macs;
     }
     *count = (uint32_t)agg.size();
     if (out)
@@ -336,6 +337,16 @@ mmfhe_status mmfhe_measure_butterfly_peak(mmfhe_ctx *ctx, double *bf64_per_s, do
     if (!bf64_per_s || !bf32_per_s) throw Error(MMFHE_ERR_BAD_ARG, "null output");
     CK(cudaSetDevice(c->device));
     measure_butterfly_peak(*c, bf64_per_s, bf32_per_s);
+    ABI_CATCH(c)
+}
+
+mmfhe_status mmfhe_measure_mac_peak(mmfhe_ctx *ctx, double *mac64_per_s) {
+    Context *c = nullptr;
+    ABI_TRY
+    c = ctx_of(ctx);
+    if (!mac64_per_s) throw Error(MMFHE_ERR_BAD_ARG, "null output");
+    CK(cudaSetDevice(c->device));
+    *mac64_per_s = measure_mac_peak(*c);
     ABI_CATCH(c)
 }
 

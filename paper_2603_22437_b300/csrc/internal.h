@@ -180,6 +180,7 @@ struct Context {
         cudaEvent_t start, stop;
         double bytes;
         double butterflies;
+        double macs;   // multiply-accumulates of fused base conversions
     };
     std::vector<ProfRec> prof;
     std::vector<cudaEvent_t> event_pool;
@@ -271,11 +272,14 @@ void autotune(Context &c, int batch, int level);
 
 // Butterflies per second of register-resident 64-bit and 32-bit butterfly loops (peaks.cu).
 void measure_butterfly_peak(Context &c, double *bf64, double *bf32);
+// Products per second of a register-resident loop of the base conversion's
+// Montgomery multiply-accumulate (four products per reduction) (peaks.cu).
+double measure_mac_peak(Context &c);
 
 // Launch bookkeeping: kernel_begin before a launch, kernel_end after it
 // (launch count, optional trace line, optional event pair + algorithmic bytes).
 void kernel_begin(Context &c, cudaStream_t st);
 void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cudaStream_t st,
-                double butterflies = 0.0);
+                double butterflies = 0.0, double macs = 0.0);
 
 }  // namespace mmfhe

@@ -79,10 +79,11 @@ void kernel_begin(Context &c, cudaStream_t st) {
     if (!c.profiling) return;
     cudaEvent_t e = next_event(c);
     CK(cudaEventRecord(e, st));
-    c.prof.push_back(Context::ProfRec{nullptr, e, nullptr, 0.0, 0.0});
+    c.prof.push_back(Context::ProfRec{nullptr, e, nullptr, 0.0, 0.0, 0.0});
 }
 
-void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cudaStream_t st, double butterflies) {
+void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cudaStream_t st, double butterflies,
+                double macs) {
     c.launches++;
     if (c.tracing) {
         char buf[160];
@@ -94,6 +95,7 @@ void kernel_end(Context &c, const char *name, dim3 g, dim3 b, double bytes, cuda
         r.name = name;
         r.bytes = bytes;
         r.butterflies = butterflies;
+        r.macs = macs;
         r.stop = next_event(c);
         CK(cudaEventRecord(r.stop, st));
     }
@@ -190,7 +192,13 @@ void launch_modup_ntt(Context &c, uint64_t *digits, const uint64_t *y, int B, in
             int src_rows = 0;
             for (int jj = 0; jj < nj; jj++) src_rows += (int)lc.digits[j0 + jj].size();
             const double bc_ = row * ((double)nr + (double)nb * src_rows), br_ = 2.0 * row * (double)nr;
-#define MMFHE_MODUP_CALL(L) modup_launch_##L(c, db, yb, md, gr, nb, nl, nre, j0, lc.d_up_mm, bc_, br_, st)
+            // conversion work: every converted word of digit j sums |D_j| products
+            double macs = 0.0;
+            for (int jj = 0; jj < nj; jj++) {
+                const double dj = (double)lc.digits[j0 + jj].size();
+                macs += (double)nb * (double)(nre - (int)dj) * dj * (double)c.n;
+            }
+#define MMFHE_MODUP_CALL(L) modup_launch_##L(c, db, yb, md, gr, nb, nl, nre, j0, lc.d_up_mm, bc_, br_, macs, st)
             MMFHE_LOGN_DISPATCH(c.logn, MMFHE_MODUP_CALL)
 #undef MMFHE_MODUP_CALL
         }
@@ -223,7 +231,8 @@ void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const Com
         const double bc_ = row * ((double)nr + (double)nb * K);
         const double br_ = row * ((double)nr * (3 + (ab.plus ? 1 : 0)) + (ab.add0 ? nr / 2.0 : 0) + (ab.add1 ? nr / 2.0 : 0));
 #define MMFHE_MODDOWN_CALL(L)                                                                                   \
-    moddown_launch_##L(c, vtmp + ((b0 * nl) << c.logn), z + ((b0 * K) << c.logn), mv, gr, nb, ab, nre, bc_, br_, st)
+    moddown_launch_##L(c, vtmp + ((b0 * nl) << c.logn), z + ((b0 * K) << c.logn), mv, gr, nb, ab, nre, bc_, br_,   \
+                       (double)nr * c.n * (K + 1), st)
         MMFHE_LOGN_DISPATCH(c.logn, MMFHE_MODDOWN_CALL)
 #undef MMFHE_MODDOWN_CALL
     }

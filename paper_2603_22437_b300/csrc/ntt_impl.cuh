@@ -502,7 +502,7 @@ void smem_opt_in(Kern k, size_t bytes) {
 template <int LOGN, int CW, int RG>
 void modup_cols_pass(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, const RowGroups &gr,
                      size_t nblk, int nl, int nre, int j0, const uint64_t *m_mont, double bytes, size_t nr,
-                     cudaStream_t st) {
+                     double macs, cudaStream_t st) {
     using Gm = Geo<LOGN, CW>;
     const size_t smem = (size_t)RG * Gm::H * Gm::COLS * 8;
     static bool opted = false;
@@ -513,31 +513,32 @@ void modup_cols_pass(Context &c, uint64_t *digits, const uint64_t *y, const RowM
     dim3 g(Gm::T1 / Gm::COLS, (unsigned)(nblk * gr.n)), b(Gm::COLS_THREADS);
     kernel_begin(c, st);
     k_ntt_cols_modup<LOGN, CW, RG><<<g, b, smem, st>>>(y, nl, nre, c.alpha, j0, digits, md, gr, m_mont, c.mods, c.tw);
-    kernel_end(c, "ntt_modup_cols", g, b, bytes, st, bf_cols<LOGN>(nr));
+    kernel_end(c, "ntt_modup_cols", g, b, bytes, st, bf_cols<LOGN>(nr), macs);
 }
 
 template <int LOGN, int CW>
 void modup_cols_rg(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, const RowGroups &gr, size_t nblk,
-                   int nl, int nre, int j0, const uint64_t *m_mont, double bytes, size_t nr, cudaStream_t st) {
-    if (c.tune.conv_rows == 4) modup_cols_pass<LOGN, CW, 4>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes, nr, st);
-    else if (c.tune.conv_rows == 2) modup_cols_pass<LOGN, CW, 2>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes, nr, st);
-    else modup_cols_pass<LOGN, CW, 1>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes, nr, st);
+                   int nl, int nre, int j0, const uint64_t *m_mont, double bytes, size_t nr, double macs,
+                   cudaStream_t st) {
+    if (c.tune.conv_rows == 4) modup_cols_pass<LOGN, CW, 4>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes, nr, macs, st);
+    else if (c.tune.conv_rows == 2) modup_cols_pass<LOGN, CW, 2>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes, nr, macs, st);
+    else modup_cols_pass<LOGN, CW, 1>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes, nr, macs, st);
 }
 
 template <int LOGN>
 void modup_launch_t(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, const RowGroups &gr,
                     size_t nblk, int nl, int nre, int j0, const uint64_t *m_mont, double bytes_cols, double bytes_rows,
-                    cudaStream_t st) {
+                    double macs, cudaStream_t st) {
     const size_t nr = nblk * md.nact;
-    if (c.tune.cols_w == 8) modup_cols_rg<LOGN, 8>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes_cols, nr, st);
-    else modup_cols_rg<LOGN, 16>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes_cols, nr, st);
+    if (c.tune.cols_w == 8) modup_cols_rg<LOGN, 8>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes_cols, nr, macs, st);
+    else modup_cols_rg<LOGN, 16>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes_cols, nr, macs, st);
     if (c.tune.rows_t == 128) rows_pass<LOGN, 128, true>(c, digits, md, digits, md, nr, bytes_rows, st);
     else rows_pass<LOGN, 256, true>(c, digits, md, digits, md, nr, bytes_rows, st);
 }
 
 template <int LOGN, int CW, int RG>
 void moddown_cols_pass(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr,
-                       size_t nblk, double bytes, size_t nr, cudaStream_t st) {
+                       size_t nblk, double bytes, size_t nr, double macs, cudaStream_t st) {
     using Gm = Geo<LOGN, CW>;
     const size_t smem = (size_t)RG * Gm::H * Gm::COLS * 8;
     static bool opted = false;
@@ -549,15 +550,15 @@ void moddown_cols_pass(Context &c, uint64_t *vtmp, const uint64_t *z, const RowM
     kernel_begin(c, st);
     k_ntt_cols_moddown<LOGN, CW, RG><<<g, b, smem, st>>>(z, c.num_p, c.num_q, vtmp, mv, gr, c.d_dn_phat_mont,
                                                          c.d_dn_negp_mont, c.mods, c.tw);
-    kernel_end(c, "ntt_moddown_cols", g, b, bytes, st, bf_cols<LOGN>(nr));
+    kernel_end(c, "ntt_moddown_cols", g, b, bytes, st, bf_cols<LOGN>(nr), macs);
 }
 
 template <int LOGN, int CW>
 void moddown_cols_rg(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr, size_t nblk,
-                     double bytes, size_t nr, cudaStream_t st) {
-    if (c.tune.conv_rows == 4) moddown_cols_pass<LOGN, CW, 4>(c, vtmp, z, mv, gr, nblk, bytes, nr, st);
-    else if (c.tune.conv_rows == 2) moddown_cols_pass<LOGN, CW, 2>(c, vtmp, z, mv, gr, nblk, bytes, nr, st);
-    else moddown_cols_pass<LOGN, CW, 1>(c, vtmp, z, mv, gr, nblk, bytes, nr, st);
+                     double bytes, size_t nr, double macs, cudaStream_t st) {
+    if (c.tune.conv_rows == 4) moddown_cols_pass<LOGN, CW, 4>(c, vtmp, z, mv, gr, nblk, bytes, nr, macs, st);
+    else if (c.tune.conv_rows == 2) moddown_cols_pass<LOGN, CW, 2>(c, vtmp, z, mv, gr, nblk, bytes, nr, macs, st);
+    else moddown_cols_pass<LOGN, CW, 1>(c, vtmp, z, mv, gr, nblk, bytes, nr, macs, st);
 }
 
 template <int LOGN, int RT>
@@ -573,10 +574,10 @@ void combine_rows_pass(Context &c, uint64_t *vtmp, const RowMap &mv, size_t nr, 
 template <int LOGN>
 void moddown_launch_t(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr,
                       size_t nblk, const CombineArgs &a, int nre, double bytes_cols, double bytes_rows,
-                      cudaStream_t st) {
+                      double macs, cudaStream_t st) {
     const size_t nr = nblk * mv.nact;
-    if (c.tune.cols_w == 8) moddown_cols_rg<LOGN, 8>(c, vtmp, z, mv, gr, nblk, bytes_cols, nr, st);
-    else moddown_cols_rg<LOGN, 16>(c, vtmp, z, mv, gr, nblk, bytes_cols, nr, st);
+    if (c.tune.cols_w == 8) moddown_cols_rg<LOGN, 8>(c, vtmp, z, mv, gr, nblk, bytes_cols, nr, macs, st);
+    else moddown_cols_rg<LOGN, 16>(c, vtmp, z, mv, gr, nblk, bytes_cols, nr, macs, st);
     if (c.tune.rows_t == 128) combine_rows_pass<LOGN, 128>(c, vtmp, mv, nr, a, nre, bytes_rows, st);
     else combine_rows_pass<LOGN, 256>(c, vtmp, mv, nr, a, nre, bytes_rows, st);
 }

@@ -11,14 +11,14 @@ void ntt_launch_14(Context &c, const uint64_t *sb, RowMap ms, uint64_t *db, RowM
 
 void modup_launch_14(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, const RowGroups &gr,
                      size_t nblk, int nl, int nre, int j0, const uint64_t *m_mont, double bytes_cols,
-                     double bytes_rows, cudaStream_t st) {
-    modup_launch_t<14>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes_cols, bytes_rows, st);
+                     double bytes_rows, double macs, cudaStream_t st) {
+    modup_launch_t<14>(c, digits, y, md, gr, nblk, nl, nre, j0, m_mont, bytes_cols, bytes_rows, macs, st);
 }
 
 void moddown_launch_14(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr,
                        size_t nblk, const CombineArgs &a, int nre, double bytes_cols, double bytes_rows,
-                       cudaStream_t st) {
-    moddown_launch_t<14>(c, vtmp, z, mv, gr, nblk, a, nre, bytes_cols, bytes_rows, st);
+                       double macs, cudaStream_t st) {
+    moddown_launch_t<14>(c, vtmp, z, mv, gr, nblk, a, nre, bytes_cols, bytes_rows, macs, st);
 }
 
 }  // namespace mmfhe

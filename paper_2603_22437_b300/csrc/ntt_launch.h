@@ -13,10 +13,10 @@ namespace mmfhe {
                         bool inverse, double bytes, const uint64_t *os, const uint64_t *os_sh, cudaStream_t st); \
     void modup_launch_##L(Context &c, uint64_t *digits, const uint64_t *y, const RowMap &md, const RowGroups &gr, \
                           size_t nblk, int nl, int nre, int j0, const uint64_t *m_mont, double bytes_cols,     \
-                          double bytes_rows, cudaStream_t st);                                                  \
+                          double bytes_rows, double macs, cudaStream_t st);                                     \
     void moddown_launch_##L(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr, \
                             size_t nblk, const CombineArgs &a, int nre, double bytes_cols, double bytes_rows,  \
-                            cudaStream_t st);
+                            double macs, cudaStream_t st);
 MMFHE_NTT_ENTRY_DECL(10)
 MMFHE_NTT_ENTRY_DECL(11)
 MMFHE_NTT_ENTRY_DECL(12)

@@ -69,7 +69,63 @@ __global__ void __launch_bounds__(PEAK_THREADS)
     sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
 }
 
+// The base conversion's arithmetic: four Montgomery products summed in 128
+// bits and reduced once, as the fused ModUp / ModDown passes run it.  Each
+// iteration forms four outputs from the thread's 16 words (16 products) and
+// feeds them back, so nothing is hoisted out of the loop.
+__global__ void __launch_bounds__(PEAK_THREADS)
+    k_peak_mac64(uint64_t *sink, uint64_t q, uint64_t qinv, const uint64_t *__restrict__ f, int iters) {
+    uint64_t x[16], fm[4];
+#pragma unroll
+    for (int i = 0; i < 16; i++) x[i] = (threadIdx.x * 16u + i * 977u) % q;
+#pragma unroll
+    for (int u = 0; u < 4; u++) fm[u] = f[u];
+    for (int it = 0; it < iters; it++) {
+        uint64_t r[4];
+#pragma unroll
+        for (int o = 0; o < 4; o++) {
+            uint64_t hi = 0, lo = 0;
+#pragma unroll
+            for (int u = 0; u < 4; u++) mm::mac128(hi, lo, x[4 * o + u], fm[u]);
+            r[o] = mm::redc(hi, lo, q, qinv);
+        }
+#pragma unroll
+        for (int o = 0; o < 4; o++) x[4 * o + (o + it) % 4] = r[o];
+    }
+    uint64_t acc = 0;
+#pragma unroll
+    for (int i = 0; i < 16; i++) acc ^= x[i];
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 }  // namespace
+
+double measure_mac_peak(Context &c) {
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c.device));
+    const unsigned blocks = (unsigned)sms * 8;
+    const size_t threads = (size_t)blocks * PEAK_THREADS;
+    const uint64_t q = c.primes[0], qinv = c.mods.qinv[0];
+    uint64_t h[4];
+    for (int u = 0; u < 4; u++) h[u] = (q / 5 + 104729ull * (uint64_t)(u + 1)) % q;
+    Buf sink(c.pool.get(), threads);
+    Buf fb(c.pool.get(), 4);
+    CK(cudaMemcpy(fb.get(), h, sizeof h, cudaMemcpyHostToDevice));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float ms = 0.f;
+    k_peak_mac64<<<blocks, PEAK_THREADS>>>(sink.get(), q, qinv, fb.get(), PEAK_ITERS);   // warm-up
+    CK(cudaEventRecord(e0));
+    k_peak_mac64<<<blocks, PEAK_THREADS>>>(sink.get(), q, qinv, fb.get(), PEAK_ITERS);
+    CK(cudaEventRecord(e1));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    CK(cudaEventDestroy(e0));
+    CK(cudaEventDestroy(e1));
+    CK(cudaGetLastError());
+    return (double)threads * PEAK_ITERS * 16 / (ms * 1e-3);
+}
 
 // Returns butterflies per second of the 64-bit and 32-bit loops on this device.
 void measure_butterfly_peak(Context &c, double *bf64, double *bf32) {
