@@ -520,6 +520,8 @@ def run_mine(args, rank, world, local):
     e2e_pipe_s = time.perf_counter() - t0
     srv_stats = srv.stats()
     srv.close()
+    if srv_stats["failed"] or srv_stats["completed"] != srv_stats["submitted"]:
+        raise RuntimeError("serving e2e: %d of %d windows failed" % (srv_stats["failed"], srv_stats["submitted"]))
     e2e = {"value": job_throughput(world, B * e2e_steps, e2e_pipe_s), "unit": "windows/s",
            "h2d_bytes_per_step": B * in_words * 8, "d2h_bytes_per_step": B * out_words * 8,
            "api": "mmfhe_server (2 stream slots, batches of %d filled within 20 ms, copies overlap the previous "
@@ -1101,9 +1103,11 @@ def run_gesture(args, rank, world, local):
         return np.ascontiguousarray(np.stack([np.stack([synth.uniform_residues(g, qp, n) for _ in range(2)])
                                               for _ in range(params.dnum)]))
 
-    keys.set_relin(key_words())
+    relin_w = key_words()
+    gal_w = {k: key_words() for k in plan.rotations()}
+    keys.set_relin(relin_w)
     for k in plan.rotations():
-        keys.set_galois(k, key_words())
+        keys.set_galois(k, gal_w[k])
     n_in, _, out_levels = plan.io()
     B = args.batch
     tiles = pick_tiles(ctx, args, B)
@@ -1141,8 +1145,10 @@ def run_gesture(args, rank, world, local):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     value = job_throughput(world, B * args.steps, sum(step_ms) / 1000.0)
-    # e2e: one synchronous mmfhe_eval per step on pinned host buffers
-    pin_in = [torch.from_numpy(host.view(np.int64)).pin_memory() for _ in range(B)]
+    # e2e: one synchronous mmfhe_eval per step on pinned host buffers (copies in, evaluation, copies
+    # out in sequence).  The two-slot serving API would hold two batches' scratch at once.
+    pin_one = torch.from_numpy(host.view(np.int64)).pin_memory()
+    pin_in = [pin_one] * B            # the windows of a step share one pinned input (read only)
     pin_out = [torch.empty(out_words, dtype=torch.int64).pin_memory() for _ in range(B)]
     step(pin_in, pin_out)
     torch.cuda.synchronize()

@@ -112,30 +112,34 @@ def test_depth_and_rotations_full_size():
     assert len(circ.rotations()) == 23
 
 
-def test_gesture_circuit_decrypts_to_fp64():
+@pytest.mark.parametrize("frames", [20, 13])
+def test_gesture_circuit_decrypts_to_fp64(frames):
+    """20 frames fill two ciphertext pairs of 16 frame positions; 13 leave
+    the last positions of the only pair empty (ragged tail)."""
+    cfg = cc.GestureConfig(antennas=2, bins=4, chirps=8, frames=frames, fc_dims=(7, 5, 3), width=16)
     P = tiny_params()
-    circ = cc.GestureCircuit(P, TINY)
+    circ = cc.GestureCircuit(P, cfg)
     rots = circ.rotations()
     kd = synth.KeyDraws(51, P.n, P.q, P.p, P.dnum, rots)
     sk = ck.SecretKey(P, kd.secret)
     pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
     rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
     gks = {k: ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
-    mats = random_gesture_net(TINY, 5)
+    mats = random_gesture_net(cfg, 5)
     consts = circ.constants(mats)
-    zt = tiny_window(6)
+    zt = tiny_window(6, cfg)
     cts = [tuple(ck.encrypt(P, pk, ck.encode(P, v, P.scale, P.L), *synth.encryption_draws(70 + 2 * i + h, P.n))
                  for h, v in enumerate(pair)) for i, pair in enumerate(circ.lay.pack(zt))]
     ev = cc.Evaluator(P, rlk, gks)
-    ref = plain.gesture_features(zt, TINY)["feat"]
+    ref = plain.gesture_features(zt, cfg)["feat"]
     feat = circ.features(ev, consts, cts)
     assert feat.level == P.L - 6
     dec = ck.decrypt_decode(P, sk, feat)
     for j in range(circ.lay.k):
-        got = dec[j * circ.lay.ard_pad: j * circ.lay.ard_pad + TINY.ard]
+        got = dec[j * circ.lay.ard_pad: j * circ.lay.ard_pad + cfg.ard]
         assert np.allclose(got, ref.reshape(-1), atol=1e-9 * max(1.0, np.abs(ref).max()))
     out = circ.run(ev, consts, cts)
     assert out.level == 0
-    logits = ck.decrypt_decode(P, sk, out)[: TINY.fc_dims[-1]]
-    want = cc.gesture_forward(mats, ref, TINY)[: TINY.fc_dims[-1]]
+    logits = ck.decrypt_decode(P, sk, out)[: cfg.fc_dims[-1]]
+    want = cc.gesture_forward(mats, ref, cfg)[: cfg.fc_dims[-1]]
     assert np.allclose(logits, want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
