@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=None,
-                    help="windows per step (per GPU); default 64 (vital), 8 (gesture)")
+                    help="windows per step (per GPU); default 64 (vital), 16 (gesture)")
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--cpu-sample-s", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -70,7 +70,7 @@ def parse():
                     help="cols_width,rows_threads,keyip_windows,conv_rows: set the tile shapes instead of autotuning")
     args = ap.parse_args()
     if args.batch is None:
-        args.batch = 8 if args.workload == "gesture" else 64
+        args.batch = 16 if args.workload == "gesture" else 64
     return args
 
 

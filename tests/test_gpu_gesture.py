@@ -196,3 +196,38 @@ def gesture_out_scale(P, circ):
     s = s * q[L - 8] / q[L - 8]
     s = s * s / q[L - 9]
     return s * q[L - 10] / q[L - 10]
+
+
+def test_gesture_bench_launch_configuration(gest):
+    """The bench's launch configuration: B = 16 full windows (30 pairs
+    each, 480 ciphertexts per Doppler launch), autotuned tiles, device
+    buffers.  Every window equals, word for word, the same window in a batch
+    of two (whose kernels the word-exact test above ties to the oracle)."""
+    import torch
+
+    import paper_2603_22437_b300 as M
+    from test_gpu_parity import rand_ct
+    P, ctx, keys = gest["P"], gest["ctx"], gest["keys"]
+    cfg = cc.GestureConfig()
+    plan = ctx.plan(gesture_config(M, cfg))
+    plan.encode_consts()
+    for l, W in enumerate(random_mats(cfg, 17)):
+        plan.set_fc_layer(l, W)
+    n_in, _, lv = plan.io()
+    saved = ctx.tuning()
+    B = 16
+    t = ctx.autotune(B)
+    wins = [np.ascontiguousarray(rand_ct(P, P.L, 900 + w, n_in).reshape(-1)) for w in range(3)]
+    d_in = [torch.from_numpy(wins[w % 3].view(np.int64)).cuda() for w in range(B)]
+    d_out = [torch.zeros(2 * P.n, dtype=torch.int64, device="cuda") for _ in range(B)]
+    ctx.eval(plan, keys, d_in, d_out)
+    torch.cuda.synchronize()
+    ref = []
+    for w0 in (0, 2):
+        outs = [np.empty(2 * P.n, dtype=np.uint64) for _ in range(2)]
+        ctx.eval(plan, keys, [wins[w0], wins[(w0 + 1) % 3]], outs)
+        ref += outs
+    ref = {0: ref[0], 1: ref[1], 2: ref[2]}
+    for w in range(B):
+        assert np.array_equal(d_out[w].cpu().numpy().view(np.uint64), ref[w % 3]), "window %d (tiles %s)" % (w, t)
+    ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"], saved["conv_rows"])

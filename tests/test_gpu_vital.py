@@ -116,24 +116,25 @@ def test_library_encoded_plan_matches(vital):
 
 
 def test_vital_full_batch_in_bench_launch_configuration(vital):
-    """The bench's launch configuration: B = 16 windows per launch, tiles
-    chosen by the autotuner for that batch, device-resident buffers.  Window
-    0 of every pair must equal the oracle's output words; window 1 the words
-    it has in the B = 2 run (itself checked against the decrypted FP64
-    pipeline above)."""
+    """The bench's launch configuration: B = 64 windows per launch (the
+    bench default), tiles chosen by the autotuner for that batch,
+    device-resident buffers.  Window 0 of every pair must equal the oracle's
+    output words; window 1 the words it has in the B = 2 run (itself checked
+    against the decrypted FP64 pipeline above)."""
     import torch
 
     P, ctx = vital["P"], vital["ctx"]
     saved = ctx.tuning()
-    t = ctx.autotune(16)
+    B = 64
+    t = ctx.autotune(B)
     outs2, lv = out_buffers(vital, 2)
     ctx.eval(vital["plan"], vital["keys"], vital["ins"], outs2, vital=True)
-    d_in = [torch.from_numpy(vital["ins"][w % 2].reshape(-1).view(np.int64)).cuda() for w in range(16)]
-    d_out = [torch.zeros(outs2[0].size, dtype=torch.int64, device="cuda") for _ in range(16)]
+    d_in = [torch.from_numpy(vital["ins"][w % 2].reshape(-1).view(np.int64)).cuda() for w in range(B)]
+    d_out = [torch.zeros(outs2[0].size, dtype=torch.int64, device="cuda") for _ in range(B)]
     ctx.eval(vital["plan"], vital["keys"], d_in, d_out, vital=True)
     torch.cuda.synchronize()
     ref0 = np.concatenate([r.words().reshape(-1) for r in vital["ref0"]])
-    for w in range(16):
+    for w in range(B):
         got = d_out[w].cpu().numpy().view(np.uint64)
         assert np.array_equal(got, ref0 if w % 2 == 0 else outs2[1]), "window %d (tiles %s)" % (w, t)
     ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"], saved["conv_rows"])
