@@ -299,8 +299,9 @@ typedef struct mmfhe_circuit_config {
 #define MMFHE_CONST_IDX 1   /* side branch: bin-index vector of group `index` */
 #define MMFHE_CONST_ONE 2   /* side branch: ones vector of group `index` */
 #define MMFHE_CONST_FIR 3   /* FIR diagonal delta=`index` of band `band` (pre-rotated) */
-#define MMFHE_CONST_DRE 4   /* VITAL DFT real rows, diagonal `index`, band `band` */
-#define MMFHE_CONST_DIM 5   /* VITAL DFT imaginary rows */
+#define MMFHE_CONST_DRE 4   /* VITAL DFT rows of band `band`, diagonal `index`: Re X_k in row k, Im X_k in
+                               row k + F_pad/2 (both bands run in one BSGS product) */
+#define MMFHE_CONST_DIM 5   /* reserved (no current plan uses it) */
 #define MMFHE_CONST_FW 6    /* frequency weights f_k (Hz) of band `band` */
 #define MMFHE_CONST_FONE 7  /* band indicator of band `band` */
 #define MMFHE_CONST_DFT_C 8  /* FIR_DFT: C = Re W diagonal `index` */

@@ -534,8 +534,12 @@ class VitalCircuit:
       main: K4 p (L0-1), m = p^2 (L0-2), I, Q = sum m Re, m Im (L0-3),
             rotate-sum over bins; K5 FIR per band (L0-4); K7 y, x (L0-5),
             third order: u = 3x^2 - y^2 (L0-6), dphi3 = y u (L0-7);
-            K3 narrowband DFT (+1); |X|^2 (+2); merge RR+HR, square (+3);
-            x f_k and x 1 per band (+4), rotate-sum -> num_b, den_b.
+            K3 narrowband DFT of both bands in one BSGS product (+1): real
+            rows at position k, imaginary rows at k + F_pad/2, RR and HR
+            from their own baby steps; |X|^2 (+2), the imaginary half
+            added onto the real by one rotation (the bands' disjoint k
+            make this the RR + HR merge); square (+3); x f_k and x 1 per
+            band (+4), rotate-sum -> num_b, den_b.
     Outputs: [num_r, den_r, num_RR, den_RR, num_HR, den_HR].
     """
 
@@ -561,20 +565,22 @@ class VitalCircuit:
         """g_b, times 1/3 for the third-order chain (which carries 3 dphi)."""
         return self.cfg.gains()[b] * (1.0 / 3.0 if self.cfg.taylor_order == 3 else 1.0)
 
-    def dft_time_matrices(self, b):
+    def dft_time_matrix(self, b):
+        """Band b's narrowband DFT rows over the frames: Re X_k in row k,
+        Im X_k in row k + F_pad/2 (X_k = g_b sum_t w[t] dphi[t] e^{-j 2 pi k t / F})."""
         F, Fp = self.cfg.frames, self.lay.f_pad
+        H = Fp // 2
+        assert max(self.bands[b]) < H, "band beyond half the padded window"
         w = hann(F)
         t = np.arange(F)
-        out = {}
-        for name in ("dre", "dim"):
-            M = np.zeros((Fp, Fp))
-            sup = np.zeros((Fp, Fp), dtype=bool)
-            for k in self.bands[b]:
-                ang = 2 * np.pi * k * t / F
-                M[k, :F] = self.dft_gain(b) * w * (np.cos(ang) if name == "dre" else -np.sin(ang))
-                sup[k, :F] = True
-            out[name] = {"support": sup, "values": M}
-        return out
+        M = np.zeros((Fp, Fp))
+        sup = np.zeros((Fp, Fp), dtype=bool)
+        for k in self.bands[b]:
+            ang = 2 * np.pi * k * t / F
+            M[k, :F] = self.dft_gain(b) * w * np.cos(ang)
+            M[k + H, :F] = -self.dft_gain(b) * w * np.sin(ang)
+            sup[k, :F] = sup[k + H, :F] = True
+        return {"support": sup, "values": M}
 
     def span(self, b):
         return next_pow2(max(self.bands[b]) + 1)
@@ -599,13 +605,13 @@ class VitalCircuit:
         ks |= {-g * self.n1_fir * lay.r_c for g in range(1, self.n2_fir)}
         ks.add(-lay.r_c)
         for b in range(len(self.bands)):
-            for name, M in self.dft_time_matrices(b).items():
-                for delta in matrix_diagonals(M, lay):
-                    if delta % self.n1_dft:
-                        ks.add((delta % self.n1_dft) * lay.r_c)
-                    if delta // self.n1_dft:
-                        ks.add((delta // self.n1_dft) * self.n1_dft * lay.r_c)
+            for delta in matrix_diagonals(self.dft_time_matrix(b), lay):
+                if delta % self.n1_dft:
+                    ks.add((delta % self.n1_dft) * lay.r_c)
+                if delta // self.n1_dft:
+                    ks.add((delta // self.n1_dft) * self.n1_dft * lay.r_c)
             ks |= {lay.r_c << i for i in range(int(math.log2(self.span(b))))}
+        ks.add((lay.f_pad // 2) * lay.r_c)
         return sorted({k % self.P.slots for k in ks})
 
     def constant_keys(self):
@@ -616,9 +622,8 @@ class VitalCircuit:
         for b in range(len(self.bands)):
             keys += [("fir", b, k) for k in range(self.cfg.taps)]
         for b in range(len(self.bands)):
-            for name, M in self.dft_time_matrices(b).items():
-                rows, cols = np.nonzero(M["support"])
-                keys += [(name, b, int(d)) for d in sorted(set(((cols - rows) % self.lay.f_pad).tolist()))]
+            rows, cols = np.nonzero(self.dft_time_matrix(b)["support"])
+            keys += [("dft", b, int(d)) for d in sorted(set(((cols - rows) % self.lay.f_pad).tolist()))]
         for b in range(len(self.bands)):
             keys += [("fw", b), ("fone", b)]
         return keys
@@ -643,10 +648,9 @@ class VitalCircuit:
                 out[("fir", b, k)] = ck.encode(P, v, P.q[lv], lv)
         lv = self.lv_dphi
         for b in range(len(self.bands)):
-            for name, M in self.dft_time_matrices(b).items():
-                for delta, v in matrix_diagonals(M, lay).items():
-                    v = prerotate(v, delta // self.n1_dft, self.n1_dft, lay.r_c)
-                    out[(name, b, delta)] = ck.encode(P, v, P.q[lv], lv)
+            for delta, v in matrix_diagonals(self.dft_time_matrix(b), lay).items():
+                v = prerotate(v, delta // self.n1_dft, self.n1_dft, lay.r_c)
+                out[("dft", b, delta)] = ck.encode(P, v, P.q[lv], lv)
         lv = self.lv_final_const
         fs_hz = cfg.fs_mhz / 1000
         for b, ks in enumerate(self.bands):
@@ -717,25 +721,24 @@ class VitalCircuit:
             else:
                 dphis.append(y)
 
-        # K3 narrowband DFT, |X|^2
+        # K3 narrowband DFT of both bands in one BSGS product (their baby
+        # steps hoisted per band, the giant steps shared), |X|^2
         n1 = self.n1_dft
-        powers = []
+        babies, cl = {}, {}
         for b, dphi in enumerate(dphis):
-            cre, cim = {}, {}
+            name = "band%d" % b
             for key, pt in consts.items():
-                if key[0] in ("dre", "dim") and key[1] == b:
-                    (cre if key[0] == "dre" else cim)[("x", key[2])] = pt
-            need = sorted({d % n1 for (_, d) in list(cre) + list(cim)})
-            hs = ev.hoisted(dphi, [bb * lay.r_c for bb in need])
-            babies = {"x": dict(zip(need, hs))}
-            Xre = ev.rescale(ev.bsgs(babies, cre, n1, lay.r_c, dphi.level))
-            Xim = ev.rescale(ev.bsgs(babies, cim, n1, lay.r_c, dphi.level))
-            powers.append(ev.rescale(ev.square_sum([Xre, Xim])))
+                if key[0] == "dft" and key[1] == b:
+                    cl[(name, key[2])] = pt
+            need = sorted({d % n1 for (nm, d) in cl if nm == name})
+            babies[name] = dict(zip(need, ev.hoisted(dphi, [bb * lay.r_c for bb in need])))
+        X = ev.rescale(ev.bsgs(babies, cl, n1, lay.r_c, dphis[0].level))
+        pw = ev.rescale(ev.square_sum([X]))
+        # Re^2 at k, Im^2 at k + F_pad/2: one rotation adds them (and, the
+        # bands' k being disjoint, merges RR and HR)
+        Mg = ev.add(pw, ev.rotate(pw, (lay.f_pad // 2) * lay.r_c))
 
-        # merge (disjoint bins) and sharpen (gamma = 2), weighted frequency average
-        Mg = powers[0]
-        for pw in powers[1:]:
-            Mg = ev.add(Mg, pw)
+        # sharpen (gamma = 2), weighted frequency average
         S = ev.rescale(ev.square_sum([Mg]))
         outs = [num_r, den_r]
         for b in range(len(self.bands)):

@@ -11,7 +11,9 @@
 //                hoisted baby steps shared by both bands (L0-4); K7:
 //                y = Qf If' - If Qf', x = If If' + Qf Qf' (L0-5), third order
 //                u = 3x^2 - y^2 (L0-6), 3 dphi = y u (L0-7); K3 narrowband
-//                DFT (+1); |X|^2 (+2); merge bands + square (+3); frequency
+//                DFT of both bands in one BSGS product, Re rows at k and Im
+//                rows at k + F_pad/2 (+1); |X|^2 (+2), halves and bands
+//                merged by one rotate-and-add; square (+3); frequency
 //                weights and band indicator (+4), rotate-sum.
 // Slot layout: slot(t, r) = t R_c + r, F_pad = 2^ceil(log2 F), R_c = N/2 / F_pad.
 //
@@ -404,15 +406,16 @@ Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
         for (int b = 0; b < 2; b++) {
             p->bands[b] = band_bins(F, (int)cfg.fs_mhz, (int)cfg.band_lo_mhz[b], (int)cfg.band_hi_mhz[b]);
             if (p->bands[b].empty()) throw Error(MMFHE_ERR_BAD_ARG, "empty frequency band");
-            if (p->bands[b].back() >= Fp) throw Error(MMFHE_ERR_BAD_ARG, "band beyond window");
+            if (p->bands[b].back() >= Fp / 2) throw Error(MMFHE_ERR_BAD_ARG, "band beyond half the padded window");
+            // rows: Re X_k at k, Im X_k at k + F_pad/2
             std::set<int> present;
             for (int k : p->bands[b])
-                for (int t = 0; t < F; t++) present.insert(((t - k) % Fp + Fp) % Fp);
+                for (int t = 0; t < F; t++)
+                    for (int row : {k, k + Fp / 2}) present.insert(((t - row) % Fp + Fp) % Fp);
             p->dft_deltas[b].assign(present.begin(), present.end());
         }
         for (int b = 0; b < 2; b++)
-            for (uint32_t tag : {MMFHE_CONST_DRE, MMFHE_CONST_DIM})
-                for (int d : p->dft_deltas[b]) add(tag, b, d, lv_dphi);
+            for (int d : p->dft_deltas[b]) add(MMFHE_CONST_DRE, b, d, lv_dphi);
         for (int b = 0; b < 2; b++) {
             add(MMFHE_CONST_FW, b, 0, lv_final);
             add(MMFHE_CONST_FONE, b, 0, lv_final);
@@ -430,6 +433,7 @@ Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
             p->span[b] = next_pow2(p->bands[b].back() + 1);
             for (int i = 0; (1 << i) < p->span[b]; i++) rot(p->r_c << i);
         }
+        rot((Fp / 2) * p->r_c);
         p->n_in = 4 * p->groups;
         p->out_levels = {lv_side - 1, lv_side - 1, lv_final - 1, lv_final - 1, lv_final - 1, lv_final - 1};
     }
@@ -493,15 +497,19 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
             for (int r = 0; r < rmax; r++) v[slot(t, r)] = h[kk];
         return prerot(kk / p.n1_fir, p.n1_fir, -Rc);
     }
-    case MMFHE_CONST_DRE:
-    case MMFHE_CONST_DIM: {
+    case MMFHE_CONST_DRE: {
+        // band b's DFT rows: Re X_k in row k, Im X_k in row k + F_pad/2;
+        // diag_d[row] = M[row, row + d]
         int b = (int)k.band, d = (int)k.index;
         double gain = cfg.dft_gain[b] * (cfg.taylor_order == 3 ? 1.0 / 3.0 : 1.0);
         for (int kk : p.bands[b]) {
-            int t = (kk + d) % Fp;   // diag_d[row kk] = M[kk, kk + d]
-            if (t < F) {
-                double ang = 2 * M_PI * kk * t / F;
-                v[slot(kk, 0)] = gain * hann(t, F) * (k.tag == MMFHE_CONST_DRE ? std::cos(ang) : -std::sin(ang));
+            for (int part = 0; part < 2; part++) {
+                const int row = kk + part * (Fp / 2);
+                const int t = (row + d) % Fp;
+                if (t < F) {
+                    double ang = 2 * M_PI * kk * t / F;
+                    v[slot(row, 0)] = gain * hann(t, F) * (part == 0 ? std::cos(ang) : -std::sin(ang));
+                }
             }
         }
         return prerot(d / p.n1_dft, p.n1_dft, Rc);
@@ -691,29 +699,29 @@ static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std:
     }
     bI.clear();
     bQ.clear();
-    // ---- K3 narrowband DFT, |X|^2 ----
-    CtB power[2];
+    // ---- K3 narrowband DFT of both bands in one BSGS product (baby steps
+    // hoisted per band, giant steps shared), |X|^2 ----
+    std::vector<CtB> hs[2];
+    BsgsTerm t[2];
     for (int band = 0; band < 2; band++) {
         std::set<int> need;
         for (int d : p.dft_deltas[band]) need.insert(d % p.n1_dft);
         std::vector<int> idx(need.begin(), need.end());
         std::vector<int32_t> rr;
         for (int b : idx) rr.push_back(b * Rc);
-        std::vector<CtB> hs = rotate_hoisted(c, k, dphi[band], rr, st);
-        CtB X[2];
-        for (int part = 0; part < 2; part++) {
-            BsgsTerm t;
-            t.baby = &hs;
-            t.baby_idx = idx;
-            uint32_t tag = part == 0 ? MMFHE_CONST_DRE : MMFHE_CONST_DIM;
-            for (int d : p.dft_deltas[band]) t.diags.push_back({d, &plan_const(p, tag, band, d)});
-            X[part] = rescale(c, bsgs(c, k, {t}, p.n1_dft, Rc, st), st);
-        }
-        power[band] = rescale(c, square_sum(c, k, {&X[0], &X[1]}, st), st);
+        hs[band] = rotate_hoisted(c, k, dphi[band], rr, st);
+        t[band].baby = &hs[band];
+        t[band].baby_idx = idx;
+        for (int d : p.dft_deltas[band]) t[band].diags.push_back({d, &plan_const(p, MMFHE_CONST_DRE, band, d)});
     }
-    // ---- merge + sharpen, weighted frequency average ----
-    ct_addsub(c, power[0], power[0], power[1], false, st);
-    CtB S = rescale(c, square_sum(c, k, {&power[0]}, st), st);
+    CtB X = rescale(c, bsgs(c, k, {t[0], t[1]}, p.n1_dft, Rc, st), st);
+    hs[0].clear();
+    hs[1].clear();
+    CtB pw = rescale(c, square_sum(c, k, {&X}, st), st);
+    // Re^2 at k, Im^2 at k + F_pad/2: one rotation adds them (and merges RR and HR, disjoint in k)
+    CtB merged = rotate_add(c, k, pw, (p.f_pad / 2) * Rc, pw, st);
+    // ---- sharpen, weighted frequency average ----
+    CtB S = rescale(c, square_sum(c, k, {&merged}, st), st);
     std::vector<CtB> out;
     out.push_back(std::move(num_r));
     out.push_back(std::move(den_r));

@@ -359,7 +359,7 @@ CtB bsgs(Context &c, const Keys &k, const std::vector<BsgsTerm> &terms, int n1, 
         for (const Item &it : kv.second)
             if (bpos.emplace(it.baby, (int)babies.size()).second) babies.push_back(it.baby);
     const int tmax = std::min(MAX_SUM_TERMS, c.sum_terms_max);
-    bool fused = (int)babies.size() <= tmax && groups.size() > 1;
+    bool fused = groups.size() > 1;
     for (auto &kv : groups) {   // one diagonal per baby step and group
         std::set<const CtB *> seen;
         for (const Item &it : kv.second) fused &= seen.insert(it.baby).second;
@@ -371,22 +371,26 @@ CtB bsgs(Context &c, const Keys &k, const std::vector<BsgsTerm> &terms, int n1, 
         std::vector<int> gs;
         for (auto &kv : groups) gs.push_back(kv.first);
         for (size_t g0 = 0; g0 < gs.size(); g0 += MULTI_SUM_GROUPS) {
-            MultiSumTerms mt{};
-            mt.nt = (int)babies.size();
-            mt.ng = (int)std::min<size_t>(MULTI_SUM_GROUPS, gs.size() - g0);
-            for (int t = 0; t < mt.nt; t++) mt.ct[t] = babies[t]->ptr();
-            for (int j = 0; j < mt.ng; j++) {
-                const int g = gs[g0 + j];
-                CtB inner = ct_new(c, B, level, scale);
-                mt.out[j] = inner.ptr();
-                for (const Item &it : groups[g]) {
-                    if (it.pt->level != level) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "bsgs: operand levels differ");
-                    if (!it.pt->mont) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: diagonals must be in Montgomery form");
-                    mt.pt[j][bpos[it.baby]] = it.pt->buf.get();
+            const int ng = (int)std::min<size_t>(MULTI_SUM_GROUPS, gs.size() - g0);
+            for (int j = 0; j < ng; j++) inners.emplace(gs[g0 + j], ct_new(c, B, level, scale));
+            // the baby steps in chunks of one reduction each, accumulated
+            for (size_t t0 = 0; t0 < babies.size(); t0 += (size_t)tmax) {
+                MultiSumTerms mt{};
+                mt.nt = (int)std::min<size_t>((size_t)tmax, babies.size() - t0);
+                mt.ng = ng;
+                for (int t = 0; t < mt.nt; t++) mt.ct[t] = babies[t0 + t]->ptr();
+                for (int j = 0; j < ng; j++) {
+                    const int g = gs[g0 + j];
+                    mt.out[j] = inners.at(g).ptr();
+                    for (const Item &it : groups[g]) {
+                        if (it.pt->level != level) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "bsgs: operand levels differ");
+                        if (!it.pt->mont) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: diagonals must be in Montgomery form");
+                        const int pos = bpos[it.baby] - (int)t0;
+                        if (pos >= 0 && pos < mt.nt) mt.pt[j][pos] = it.pt->buf.get();
+                    }
                 }
-                inners.emplace(g, std::move(inner));
+                k_launch_mul_plain_sum_multi(c, mt, B, level, t0 > 0, st);
             }
-            k_launch_mul_plain_sum_multi(c, mt, B, level, false, st);
         }
     }
     CtB acc;

@@ -201,8 +201,8 @@ def install_oracle_consts(plan, consts):
             key = (tag, index)
         elif tag in ("fw", "fone"):
             key = (tag, band)
-        elif tag in ("dre", "dim"):
-            key = (tag, band, index)
+        elif tag == "dre":
+            key = ("dft", band, index)
         elif tag == "fir" and ("fir", band, index) in consts:
             key = ("fir", band, index)
         else:
