@@ -532,14 +532,17 @@ class VitalCircuit:
       side: K1 p (L0-1), rotate-sum over frames; K2 w = E^2 (L0-2);
             index / one vectors (L0-3), rotate-sum over bins -> num_r, den_r.
       main: K4 p (L0-1), m = p^2 (L0-2), I, Q = sum m Re, m Im (L0-3),
-            rotate-sum over bins; K5 FIR per band (L0-4); K7 y, x (L0-5),
-            third order: u = 3x^2 - y^2 (L0-6), dphi3 = y u (L0-7);
-            K3 narrowband DFT of both bands in one BSGS product (+1): real
-            rows at position k, imaginary rows at k + F_pad/2, RR and HR
-            from their own baby steps; |X|^2 (+2), the imaginary half
-            added onto the real by one rotation (the bands' disjoint k
-            make this the RR + HR merge); square (+3); x f_k and x 1 per
-            band (+4), rotate-sum -> num_b, den_b.
+            rotate-sum over bins (the sums sit in bin slot 0 of every
+            frame); K5 FIR of both bands in one BSGS product per part
+            (L0-4): band b's output lands in bin slot b of every frame (the
+            HR taps read baby steps shifted by one slot); K7 y, x (L0-5),
+            third order: u = 3x^2 - y^2 (L0-6), dphi3 = y u (L0-7), both
+            bands at once slot by slot; K3 narrowband DFT (+1): real rows
+            at position k, imaginary rows at k + F_pad/2, band b in slot b;
+            |X|^2 (+2), the imaginary half added onto the real by one
+            rotation; square (+3); x f_k and x 1 (+4), rotate-sum -> num
+            and den with RR in slot 0, HR in slot 1; one rotation each
+            brings HR to slot 0.
     Outputs: [num_r, den_r, num_RR, den_RR, num_HR, den_HR].
     """
 
@@ -567,7 +570,8 @@ class VitalCircuit:
 
     def dft_time_matrix(self, b):
         """Band b's narrowband DFT rows over the frames: Re X_k in row k,
-        Im X_k in row k + F_pad/2 (X_k = g_b sum_t w[t] dphi[t] e^{-j 2 pi k t / F})."""
+        Im X_k in row k + F_pad/2 (X_k = g_b sum_t w[t] dphi[t] e^{-j 2 pi k t / F});
+        applied in bin slot b."""
         F, Fp = self.cfg.frames, self.lay.f_pad
         H = Fp // 2
         assert max(self.bands[b]) < H, "band beyond half the padded window"
@@ -585,14 +589,19 @@ class VitalCircuit:
     def span(self, b):
         return next_pow2(max(self.bands[b]) + 1)
 
+    def span_all(self):
+        return max(self.span(b) for b in range(len(self.bands)))
+
     def fir_diagonals(self, b):
+        """Band b's causal FIR as diagonals over the frames, in bin slot b
+        (its input baby steps are shifted by b slots)."""
         lay, F = self.lay, self.cfg.frames
         h = self.taps(b)
         out = {}
         for k in range(self.cfg.taps):
             v = np.zeros(lay.slots)
             for t in range(k, F):
-                v[lay.slot(t, 0)] = h[k]
+                v[lay.slot(t, b)] = h[k]
             out[k] = v
         return out
 
@@ -601,7 +610,7 @@ class VitalCircuit:
         ks = set()
         ks |= {lay.r_c << i for i in range(int(math.log2(lay.f_pad)))}
         ks |= {1 << i for i in range(int(math.log2(lay.r_c)))}
-        ks |= {-b * lay.r_c for b in range(1, self.n1_fir)}
+        ks |= {-b * lay.r_c - s for b in range(self.n1_fir) for s in (0, 1)}
         ks |= {-g * self.n1_fir * lay.r_c for g in range(1, self.n2_fir)}
         ks.add(-lay.r_c)
         for b in range(len(self.bands)):
@@ -610,9 +619,10 @@ class VitalCircuit:
                     ks.add((delta % self.n1_dft) * lay.r_c)
                 if delta // self.n1_dft:
                     ks.add((delta // self.n1_dft) * self.n1_dft * lay.r_c)
-            ks |= {lay.r_c << i for i in range(int(math.log2(self.span(b))))}
+        ks |= {lay.r_c << i for i in range(int(math.log2(self.span_all())))}
         ks.add((lay.f_pad // 2) * lay.r_c)
-        return sorted({k % self.P.slots for k in ks})
+        ks.add(1)
+        return sorted({k % self.P.slots for k in ks} - {0})
 
     def constant_keys(self):
         """Keys of every constant ``constants()`` encodes, without encoding."""
@@ -621,11 +631,12 @@ class VitalCircuit:
             keys += [("idx", c), ("one", c)]
         for b in range(len(self.bands)):
             keys += [("fir", b, k) for k in range(self.cfg.taps)]
+        present = set()
         for b in range(len(self.bands)):
             rows, cols = np.nonzero(self.dft_time_matrix(b)["support"])
-            keys += [("dft", b, int(d)) for d in sorted(set(((cols - rows) % self.lay.f_pad).tolist()))]
-        for b in range(len(self.bands)):
-            keys += [("fw", b), ("fone", b)]
+            present |= set(((cols - rows) % self.lay.f_pad).tolist())
+        keys += [("dft", int(d)) for d in sorted(present)]
+        keys += [("fw",), ("fone",)]
         return keys
 
     def constants(self):
@@ -647,19 +658,23 @@ class VitalCircuit:
                 v = prerotate(v, k // self.n1_fir, self.n1_fir, -lay.r_c)
                 out[("fir", b, k)] = ck.encode(P, v, P.q[lv], lv)
         lv = self.lv_dphi
+        diags = {}
         for b in range(len(self.bands)):
             for delta, v in matrix_diagonals(self.dft_time_matrix(b), lay).items():
-                v = prerotate(v, delta // self.n1_dft, self.n1_dft, lay.r_c)
-                out[("dft", b, delta)] = ck.encode(P, v, P.q[lv], lv)
+                # band b's rows act on bin slot b
+                diags[delta] = diags.get(delta, 0.0) + np.roll(v, b)
+        for delta, v in diags.items():
+            v = prerotate(v, delta // self.n1_dft, self.n1_dft, lay.r_c)
+            out[("dft", delta)] = ck.encode(P, v, P.q[lv], lv)
         lv = self.lv_final_const
         fs_hz = cfg.fs_mhz / 1000
+        fw, fo = np.zeros(lay.slots), np.zeros(lay.slots)
         for b, ks in enumerate(self.bands):
-            fw, fo = np.zeros(lay.slots), np.zeros(lay.slots)
             for k in ks:
-                fw[lay.slot(k, 0)] = k * fs_hz / cfg.frames          # Hz; the client multiplies by 60
-                fo[lay.slot(k, 0)] = 1.0
-            out[("fw", b)] = ck.encode(P, fw, P.q[lv], lv)
-            out[("fone", b)] = ck.encode(P, fo, P.q[lv], lv)
+                fw[lay.slot(k, b)] = k * fs_hz / cfg.frames          # Hz; the client multiplies by 60
+                fo[lay.slot(k, b)] = 1.0
+        out[("fw",)] = ck.encode(P, fw, P.q[lv], lv)
+        out[("fone",)] = ck.encode(P, fo, P.q[lv], lv)
         return out
 
     # -- the chain -----------------------------------------------------------
@@ -699,53 +714,49 @@ class VitalCircuit:
             iq.append(ev.rotsum(ev.rescale(ev.relin(t)), 1, lay.r_c))
         I, Q = iq
 
-        # K5 FIR per band: babies of I and Q hoisted once, shared by both bands
+        # K5 FIR of both bands in one BSGS product per part: the baby steps
+        # of I (and Q) are hoisted once, unshifted for RR (output in bin
+        # slot 0) and shifted by one slot for HR (output in slot 1)
         n1 = self.n1_fir
-        bI = ev.hoisted(I, [-b * lay.r_c for b in range(n1)])
-        bQ = ev.hoisted(Q, [-b * lay.r_c for b in range(n1)])
-        dphis = []
+        fir = {}
         for b in range(len(self.bands)):
-            fir = {("x", k): consts[("fir", b, k)] for k in range(cfg.taps)}
-            If = ev.rescale(ev.bsgs({"x": bI}, fir, n1, -lay.r_c, I.level))
-            Qf = ev.rescale(ev.bsgs({"x": bQ}, fir, n1, -lay.r_c, Q.level))
-            # K7 differential phase
-            If1 = ev.rotate(If, -lay.r_c)
-            Qf1 = ev.rotate(Qf, -lay.r_c)
-            y = ev.rescale(ev.relin(ev.tensor_sub(ev.tensor(Qf, If1), ev.tensor(If, Qf1))))
-            x = ev.rescale(ev.relin(ev.tensor_add(ev.tensor(If, If1), ev.tensor(Qf, Qf1))))
-            if cfg.taylor_order == 3:
-                u = ev.tensor_sub(ev.tensor_mul_int(ev.tensor(x, x), 3), ev.tensor(y, y))
-                u = ev.rescale(ev.relin(u))
-                yd = ev.drop(y, u.level)
-                dphis.append(ev.rescale(ev.relin(ev.tensor(yd, u))))
-            else:
-                dphis.append(y)
+            for k in range(cfg.taps):
+                fir[("s%d" % b, k)] = consts[("fir", b, k)]
+        filtered = []
+        for x in (I, Q):
+            rots = [-j * lay.r_c - s for s in (0, 1) for j in range(n1)]
+            hs = ev.hoisted(x, rots)
+            babies = {"s0": dict(zip(range(n1), hs[:n1])), "s1": dict(zip(range(n1), hs[n1:]))}
+            filtered.append(ev.rescale(ev.bsgs(babies, fir, n1, -lay.r_c, x.level)))
+        If, Qf = filtered
+        # K7 differential phase, both bands slot by slot
+        If1 = ev.rotate(If, -lay.r_c)
+        Qf1 = ev.rotate(Qf, -lay.r_c)
+        y = ev.rescale(ev.relin(ev.tensor_sub(ev.tensor(Qf, If1), ev.tensor(If, Qf1))))
+        x = ev.rescale(ev.relin(ev.tensor_add(ev.tensor(If, If1), ev.tensor(Qf, Qf1))))
+        if cfg.taylor_order == 3:
+            u = ev.tensor_sub(ev.tensor_mul_int(ev.tensor(x, x), 3), ev.tensor(y, y))
+            u = ev.rescale(ev.relin(u))
+            yd = ev.drop(y, u.level)
+            dphi = ev.rescale(ev.relin(ev.tensor(yd, u)))
+        else:
+            dphi = y
 
-        # K3 narrowband DFT of both bands in one BSGS product (their baby
-        # steps hoisted per band, the giant steps shared), |X|^2
+        # K3 narrowband DFT (both bands, each in its bin slot), |X|^2
         n1 = self.n1_dft
-        babies, cl = {}, {}
-        for b, dphi in enumerate(dphis):
-            name = "band%d" % b
-            for key, pt in consts.items():
-                if key[0] == "dft" and key[1] == b:
-                    cl[(name, key[2])] = pt
-            need = sorted({d % n1 for (nm, d) in cl if nm == name})
-            babies[name] = dict(zip(need, ev.hoisted(dphi, [bb * lay.r_c for bb in need])))
-        X = ev.rescale(ev.bsgs(babies, cl, n1, lay.r_c, dphis[0].level))
+        cl = {("x", key[1]): pt for key, pt in consts.items() if key[0] == "dft"}
+        need = sorted({d % n1 for (_, d) in cl})
+        babies = {"x": dict(zip(need, ev.hoisted(dphi, [bb * lay.r_c for bb in need])))}
+        X = ev.rescale(ev.bsgs(babies, cl, n1, lay.r_c, dphi.level))
         pw = ev.rescale(ev.square_sum([X]))
-        # Re^2 at k, Im^2 at k + F_pad/2: one rotation adds them (and, the
-        # bands' k being disjoint, merges RR and HR)
+        # Re^2 at k, Im^2 at k + F_pad/2: one rotation adds them
         Mg = ev.add(pw, ev.rotate(pw, (lay.f_pad // 2) * lay.r_c))
 
-        # sharpen (gamma = 2), weighted frequency average
+        # sharpen (gamma = 2), weighted frequency average (RR in slot 0, HR in slot 1)
         S = ev.rescale(ev.square_sum([Mg]))
-        outs = [num_r, den_r]
-        for b in range(len(self.bands)):
-            nb = ev.rescale(ev.mul_plain(S, consts[("fw", b)]))
-            db = ev.rescale(ev.mul_plain(S, consts[("fone", b)]))
-            outs.append(ev.rotsum(nb, lay.r_c, self.span(b)))
-            outs.append(ev.rotsum(db, lay.r_c, self.span(b)))
+        num = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[("fw",)])), lay.r_c, self.span_all())
+        den = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[("fone",)])), lay.r_c, self.span_all())
+        outs = [num_r, den_r, num, den, ev.rotate(num, 1), ev.rotate(den, 1)]
         return outs
 
 

@@ -403,37 +403,38 @@ Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
         }
         for (int b = 0; b < 2; b++)
             for (uint32_t k = 0; k < cfg.taps; k++) add(MMFHE_CONST_FIR, b, k, lv_fir);
+        // from the FIR on, band b lives in bin slot b of every frame
+        if (p->r_c < 2) throw Error(MMFHE_ERR_BAD_ARG, "the vital chain needs two bin slots per frame");
+        std::set<int> present;
         for (int b = 0; b < 2; b++) {
             p->bands[b] = band_bins(F, (int)cfg.fs_mhz, (int)cfg.band_lo_mhz[b], (int)cfg.band_hi_mhz[b]);
             if (p->bands[b].empty()) throw Error(MMFHE_ERR_BAD_ARG, "empty frequency band");
             if (p->bands[b].back() >= Fp / 2) throw Error(MMFHE_ERR_BAD_ARG, "band beyond half the padded window");
             // rows: Re X_k at k, Im X_k at k + F_pad/2
-            std::set<int> present;
             for (int k : p->bands[b])
                 for (int t = 0; t < F; t++)
                     for (int row : {k, k + Fp / 2}) present.insert(((t - row) % Fp + Fp) % Fp);
-            p->dft_deltas[b].assign(present.begin(), present.end());
+            p->span[b] = next_pow2(p->bands[b].back() + 1);
         }
-        for (int b = 0; b < 2; b++)
-            for (int d : p->dft_deltas[b]) add(MMFHE_CONST_DRE, b, d, lv_dphi);
-        for (int b = 0; b < 2; b++) {
-            add(MMFHE_CONST_FW, b, 0, lv_final);
-            add(MMFHE_CONST_FONE, b, 0, lv_final);
-        }
+        p->dft_deltas[0].assign(present.begin(), present.end());
+        for (int d : p->dft_deltas[0]) add(MMFHE_CONST_DRE, 0, d, lv_dphi);
+        add(MMFHE_CONST_FW, 0, 0, lv_final);
+        add(MMFHE_CONST_FONE, 0, 0, lv_final);
         for (int i = 0; (1 << i) < Fp; i++) rot(p->r_c << i);
         for (int i = 0; (1 << i) < p->r_c; i++) rot(1 << i);
-        for (int b = 1; b < p->n1_fir; b++) rot(-b * p->r_c);
+        for (int b = 0; b < p->n1_fir; b++) {
+            rot(-b * p->r_c);
+            rot(-b * p->r_c - 1);
+        }
         for (int g = 1; g < p->n2_fir; g++) rot(-g * p->n1_fir * p->r_c);
         rot(-p->r_c);
-        for (int b = 0; b < 2; b++) {
-            for (int d : p->dft_deltas[b]) {
-                if (d % p->n1_dft) rot((d % p->n1_dft) * p->r_c);
-                if (d / p->n1_dft) rot((d / p->n1_dft) * p->n1_dft * p->r_c);
-            }
-            p->span[b] = next_pow2(p->bands[b].back() + 1);
-            for (int i = 0; (1 << i) < p->span[b]; i++) rot(p->r_c << i);
+        for (int d : p->dft_deltas[0]) {
+            if (d % p->n1_dft) rot((d % p->n1_dft) * p->r_c);
+            if (d / p->n1_dft) rot((d / p->n1_dft) * p->n1_dft * p->r_c);
         }
+        for (int i = 0; (1 << i) < std::max(p->span[0], p->span[1]); i++) rot(p->r_c << i);
         rot((Fp / 2) * p->r_c);
+        rot(1);
         p->n_in = 4 * p->groups;
         p->out_levels = {lv_side - 1, lv_side - 1, lv_final - 1, lv_final - 1, lv_final - 1, lv_final - 1};
     }
@@ -492,23 +493,26 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
     case MMFHE_CONST_FIR: {
         int b = (int)k.band, kk = (int)k.index;
         std::vector<double> h = fir_bandpass((int)cfg.taps, cfg.band_lo_mhz[b] / 1000.0, cfg.band_hi_mhz[b] / 1000.0, fs);
-        int rmax = cfg.kind == MMFHE_CIRCUIT_VITAL ? 1 : Rc;
+        // VITAL: band b's taps act in bin slot b; FIR_DFT: every bin
+        const int r0 = cfg.kind == MMFHE_CIRCUIT_VITAL ? b : 0, r1 = cfg.kind == MMFHE_CIRCUIT_VITAL ? b + 1 : Rc;
         for (int t = kk; t < F; t++)
-            for (int r = 0; r < rmax; r++) v[slot(t, r)] = h[kk];
+            for (int r = r0; r < r1; r++) v[slot(t, r)] = h[kk];
         return prerot(kk / p.n1_fir, p.n1_fir, -Rc);
     }
     case MMFHE_CONST_DRE: {
-        // band b's DFT rows: Re X_k in row k, Im X_k in row k + F_pad/2;
-        // diag_d[row] = M[row, row + d]
-        int b = (int)k.band, d = (int)k.index;
-        double gain = cfg.dft_gain[b] * (cfg.taylor_order == 3 ? 1.0 / 3.0 : 1.0);
-        for (int kk : p.bands[b]) {
-            for (int part = 0; part < 2; part++) {
-                const int row = kk + part * (Fp / 2);
-                const int t = (row + d) % Fp;
-                if (t < F) {
-                    double ang = 2 * M_PI * kk * t / F;
-                    v[slot(row, 0)] = gain * hann(t, F) * (part == 0 ? std::cos(ang) : -std::sin(ang));
+        // the DFT rows of both bands: Re X_k in row k, Im X_k in row k + F_pad/2,
+        // band b in bin slot b; diag_d[row] = M[row, row + d]
+        const int d = (int)k.index;
+        for (int b = 0; b < 2; b++) {
+            const double gain = cfg.dft_gain[b] * (cfg.taylor_order == 3 ? 1.0 / 3.0 : 1.0);
+            for (int kk : p.bands[b]) {
+                for (int part = 0; part < 2; part++) {
+                    const int row = kk + part * (Fp / 2);
+                    const int t = (row + d) % Fp;
+                    if (t < F) {
+                        double ang = 2 * M_PI * kk * t / F;
+                        v[slot(row, b)] = gain * hann(t, F) * (part == 0 ? std::cos(ang) : -std::sin(ang));
+                    }
                 }
             }
         }
@@ -558,7 +562,9 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
     }
     case MMFHE_CONST_FW:
     case MMFHE_CONST_FONE:
-        for (int kk : p.bands[k.band]) v[slot(kk, 0)] = k.tag == MMFHE_CONST_FW ? kk * fs / F : 1.0;
+        // both bands: frequency k fs / F (or 1) at (k, band)
+        for (int b = 0; b < 2; b++)
+            for (int kk : p.bands[b]) v[slot(kk, b)] = k.tag == MMFHE_CONST_FW ? kk * fs / F : 1.0;
         return v;
     }
     throw Error(MMFHE_ERR_BAD_ARG, "unknown constant tag");
@@ -660,79 +666,87 @@ static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std:
         iq[part] = rotsum(c, k, rescale(c, relin(c, k, t, st), st), 1, (uint32_t)Rc, st);
     }
     m.clear();
-    // ---- K5 FIR (hoisted babies shared by both bands) + K7 ----
-    std::vector<int> idx_fir(p.n1_fir), rot_fir(p.n1_fir);
-    for (int b = 0; b < p.n1_fir; b++) { idx_fir[b] = b; rot_fir[b] = -b * Rc; }
-    std::vector<CtB> bI = rotate_hoisted(c, k, iq[0], rot_fir, st);
-    std::vector<CtB> bQ = rotate_hoisted(c, k, iq[1], rot_fir, st);
-    CtB dphi[2];
-    for (int band = 0; band < 2; band++) {
-        BsgsTerm t;
-        t.baby_idx = idx_fir;
-        for (uint32_t kk = 0; kk < p.cfg.taps; kk++) t.diags.push_back({(int)kk, &plan_const(p, MMFHE_CONST_FIR, band, kk)});
-        t.baby = &bI;
-        CtB If = rescale(c, bsgs(c, k, {t}, p.n1_fir, -Rc, st), st);
-        t.baby = &bQ;
-        CtB Qf = rescale(c, bsgs(c, k, {t}, p.n1_fir, -Rc, st), st);
-        CtB If1 = rotate(c, k, If, -Rc, st);
-        CtB Qf1 = rotate(c, k, Qf, -Rc, st);
-        TensorB ty = tensor_new(c, B, If.level);
-        tensor_acc(c, ty, Qf, If1, 1, true, st);
-        tensor_acc(c, ty, If, Qf1, -1, false, st);
-        CtB y = rescale(c, relin(c, k, ty, st), st);
-        TensorB tx = tensor_new(c, B, If.level);
-        tensor_acc(c, tx, If, If1, 1, true, st);
-        tensor_acc(c, tx, Qf, Qf1, 1, false, st);
-        CtB x = rescale(c, relin(c, k, tx, st), st);
-        if (p.cfg.taylor_order == 3) {
-            TensorB tu = tensor_new(c, B, x.level);
-            tensor_acc(c, tu, x, x, 3, true, st);
-            tensor_acc(c, tu, y, y, -1, false, st);
-            CtB u = rescale(c, relin(c, k, tu, st), st);
-            CtB yd = ct_drop(c, y, u.level, st);
-            TensorB tp = tensor_new(c, B, u.level);
-            tensor_acc(c, tp, yd, u, 1, true, st);
-            dphi[band] = rescale(c, relin(c, k, tp, st), st);
-        } else {
-            dphi[band] = std::move(y);
+    // ---- K5 FIR of both bands in one BSGS product per part: baby steps
+    // hoisted once, unshifted for RR (bin slot 0), one slot on for HR (slot 1) ----
+    std::vector<int> idx_fir(p.n1_fir);
+    std::vector<int32_t> rot_fir;
+    for (int sft = 0; sft < 2; sft++)
+        for (int b = 0; b < p.n1_fir; b++) rot_fir.push_back(-b * Rc - sft);
+    for (int b = 0; b < p.n1_fir; b++) idx_fir[b] = b;
+    CtB filt[2];
+    for (int part = 0; part < 2; part++) {
+        std::vector<CtB> hs = rotate_hoisted(c, k, iq[part], rot_fir, st);
+        std::vector<CtB> b0(std::make_move_iterator(hs.begin()), std::make_move_iterator(hs.begin() + p.n1_fir));
+        std::vector<CtB> b1(std::make_move_iterator(hs.begin() + p.n1_fir), std::make_move_iterator(hs.end()));
+        BsgsTerm t[2];
+        for (int band = 0; band < 2; band++) {
+            t[band].baby = band == 0 ? &b0 : &b1;
+            t[band].baby_idx = idx_fir;
+            for (uint32_t kk = 0; kk < p.cfg.taps; kk++)
+                t[band].diags.push_back({(int)kk, &plan_const(p, MMFHE_CONST_FIR, band, kk)});
         }
+        filt[part] = rescale(c, bsgs(c, k, {t[0], t[1]}, p.n1_fir, -Rc, st), st);
     }
-    bI.clear();
-    bQ.clear();
-    // ---- K3 narrowband DFT of both bands in one BSGS product (baby steps
-    // hoisted per band, giant steps shared), |X|^2 ----
-    std::vector<CtB> hs[2];
-    BsgsTerm t[2];
-    for (int band = 0; band < 2; band++) {
-        std::set<int> need;
-        for (int d : p.dft_deltas[band]) need.insert(d % p.n1_dft);
-        std::vector<int> idx(need.begin(), need.end());
-        std::vector<int32_t> rr;
-        for (int b : idx) rr.push_back(b * Rc);
-        hs[band] = rotate_hoisted(c, k, dphi[band], rr, st);
-        t[band].baby = &hs[band];
-        t[band].baby_idx = idx;
-        for (int d : p.dft_deltas[band]) t[band].diags.push_back({d, &plan_const(p, MMFHE_CONST_DRE, band, d)});
+    // ---- K7, both bands slot by slot ----
+    const CtB &If = filt[0], &Qf = filt[1];
+    CtB If1 = rotate(c, k, If, -Rc, st);
+    CtB Qf1 = rotate(c, k, Qf, -Rc, st);
+    TensorB ty = tensor_new(c, B, If.level);
+    tensor_acc(c, ty, Qf, If1, 1, true, st);
+    tensor_acc(c, ty, If, Qf1, -1, false, st);
+    CtB y = rescale(c, relin(c, k, ty, st), st);
+    TensorB tx = tensor_new(c, B, If.level);
+    tensor_acc(c, tx, If, If1, 1, true, st);
+    tensor_acc(c, tx, Qf, Qf1, 1, false, st);
+    CtB x = rescale(c, relin(c, k, tx, st), st);
+    CtB dphi;
+    if (p.cfg.taylor_order == 3) {
+        TensorB tu = tensor_new(c, B, x.level);
+        tensor_acc(c, tu, x, x, 3, true, st);
+        tensor_acc(c, tu, y, y, -1, false, st);
+        CtB u = rescale(c, relin(c, k, tu, st), st);
+        CtB yd = ct_drop(c, y, u.level, st);
+        TensorB tp = tensor_new(c, B, u.level);
+        tensor_acc(c, tp, yd, u, 1, true, st);
+        dphi = rescale(c, relin(c, k, tp, st), st);
+    } else {
+        dphi = std::move(y);
     }
-    CtB X = rescale(c, bsgs(c, k, {t[0], t[1]}, p.n1_dft, Rc, st), st);
-    hs[0].clear();
-    hs[1].clear();
+    // ---- K3 narrowband DFT (both bands, each in its bin slot), |X|^2 ----
+    std::set<int> need;
+    for (int d : p.dft_deltas[0]) need.insert(d % p.n1_dft);
+    std::vector<int> idx(need.begin(), need.end());
+    std::vector<int32_t> rr;
+    for (int b : idx) rr.push_back(b * Rc);
+    std::vector<CtB> hs = rotate_hoisted(c, k, dphi, rr, st);
+    BsgsTerm td;
+    td.baby = &hs;
+    td.baby_idx = idx;
+    for (int d : p.dft_deltas[0]) td.diags.push_back({d, &plan_const(p, MMFHE_CONST_DRE, 0, d)});
+    CtB X = rescale(c, bsgs(c, k, {td}, p.n1_dft, Rc, st), st);
+    hs.clear();
     CtB pw = rescale(c, square_sum(c, k, {&X}, st), st);
-    // Re^2 at k, Im^2 at k + F_pad/2: one rotation adds them (and merges RR and HR, disjoint in k)
+    // Re^2 at k, Im^2 at k + F_pad/2: one rotation adds them
     CtB merged = rotate_add(c, k, pw, (p.f_pad / 2) * Rc, pw, st);
-    // ---- sharpen, weighted frequency average ----
+    // ---- sharpen, weighted frequency average (RR in slot 0, HR in slot 1) ----
     CtB S = rescale(c, square_sum(c, k, {&merged}, st), st);
+    const uint32_t span = (uint32_t)std::max(p.span[0], p.span[1]);
+    CtB sums[2];
+    for (int i2 = 0; i2 < 2; i2++) {
+        const PtDev &pt = plan_const(p, i2 == 0 ? MMFHE_CONST_FW : MMFHE_CONST_FONE, 0, 0);
+        CtB t = ct_new(c, B, S.level, S.scale * pt.scale);
+        ct_mul_plain(c, t, S, pt, false, st);
+        sums[i2] = rotsum(c, k, rescale(c, t, st), Rc, span, st);
+    }
     std::vector<CtB> out;
     out.push_back(std::move(num_r));
     out.push_back(std::move(den_r));
-    for (int band = 0; band < 2; band++) {
-        for (uint32_t tag : {MMFHE_CONST_FW, MMFHE_CONST_FONE}) {
-            const PtDev &pt = plan_const(p, tag, band, 0);
-            CtB t = ct_new(c, B, S.level, S.scale * pt.scale);
-            ct_mul_plain(c, t, S, pt, false, st);
-            out.push_back(rotsum(c, k, rescale(c, t, st), Rc, (uint32_t)p.span[band], st));
-        }
-    }
+    CtB hr_num = rotate(c, k, sums[0], 1, st);
+    CtB hr_den = rotate(c, k, sums[1], 1, st);
+    out.push_back(std::move(sums[0]));
+    out.push_back(std::move(sums[1]));
+    out.push_back(std::move(hr_num));
+    out.push_back(std::move(hr_den));
     return out;
 }
 

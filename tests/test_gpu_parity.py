@@ -200,9 +200,9 @@ def install_oracle_consts(plan, consts):
         if tag in ("idx", "one"):
             key = (tag, index)
         elif tag in ("fw", "fone"):
-            key = (tag, band)
+            key = (tag,)
         elif tag == "dre":
-            key = ("dft", band, index)
+            key = ("dft", index)
         elif tag == "fir" and ("fir", band, index) in consts:
             key = ("fir", band, index)
         else:
