@@ -213,6 +213,10 @@ class Evaluator:
         self._t("rotate", a.level, k)
         return ck.rotate(self.P, a, k, self.gks)
 
+    def conjugate(self, a):
+        self._t("conjugate", a.level)
+        return ck.conjugate(self.P, a, self.gks)
+
     def hoisted(self, a, ks):
         self._t("hoisted", a.level, tuple(ks))
         return ck.rotate_hoisted(self.P, a, ks, self.gks)
@@ -325,12 +329,16 @@ class CountingEvaluator(Evaluator):
         return _Shape(a.level - 1)
 
     def rotate(self, a, k):
-        if k % self.P.slots:
+        if ck.key_id(self.P, k):
             self._ks(a.level)
         return _Shape(a.level)
 
+    def conjugate(self, a):
+        self._ks(a.level)
+        return _Shape(a.level)
+
     def hoisted(self, a, ks):
-        self._ks(a.level, sum(1 for k in ks if k % self.P.slots))
+        self._ks(a.level, sum(1 for k in ks if ck.key_id(self.P, k)))
         return [_Shape(a.level) for _ in ks]
 
     def add(self, a, b):
@@ -387,14 +395,20 @@ class BudgetEvaluator(Evaluator):
     def rotate(self, a, k):
         self._check()
         r = super().rotate(a, k)
-        if k % self.P.slots:
+        if ck.key_id(self.P, k):
             self.ks_weight += a.level + 1 + self.K
         return r
 
     def hoisted(self, a, ks):
         self._check()
         r = super().hoisted(a, ks)
-        self.ks_weight += (a.level + 1 + self.K) * sum(1 for k in ks if k % self.P.slots)
+        self.ks_weight += (a.level + 1 + self.K) * sum(1 for k in ks if ck.key_id(self.P, k))
+        return r
+
+    def conjugate(self, a):
+        self._check()
+        r = super().conjugate(a)
+        self.ks_weight += a.level + 1 + self.K
         return r
 
 
@@ -984,6 +998,7 @@ class GestureConfig:
     frames: int = 60            # F
     fc_dims: tuple = (31, 16, 6)  # d_1, d_2, classes (d_0 = A R D feature slots)
     width: int = 32             # slot period of the FC layers after FC1
+    complex_slots: bool = False # Re + i Im in one complex slot: one ciphertext per frame group
 
     @property
     def ard(self):
@@ -1005,6 +1020,10 @@ class GestureLayout:
         self.k = slots // self.ard_pad           # frames per ciphertext pair
         self.pairs = -(-cfg.frames // self.k)
         self.slots = slots
+
+    def pack_complex(self, zt):
+        """zt [F, A, R, D] complex -> list of complex slot vectors (Re + i Im)."""
+        return [re + 1j * im for re, im in self.pack(zt)]
 
     def pack(self, zt):
         """zt [F, A, R, D] complex -> list of (re, im) slot vectors."""
@@ -1059,7 +1078,7 @@ class GestureCircuit:
         i = np.arange(self.P.slots) % D
         j = i + delta
         ok = (j >= 0) & (j < D)
-        v = np.zeros(self.P.slots)
+        v = np.zeros(self.P.slots, dtype=M.dtype)
         v[ok] = M[i[ok], j[ok]]
         return v * self.lay.active()
 
@@ -1098,6 +1117,10 @@ class GestureCircuit:
         out = {}
         for delta in self.deltas:
             g = delta // self.n1
+            if cfg.complex_slots:
+                v = prerotate(self.doppler_diagonal(Wd, delta), g, self.n1, 1)
+                out[("gdft_w", delta)] = ck.encode(P, v, q[L], L)
+                continue
             for tag, M in (("gdft_c", C), ("gdft_s", S), ("gdft_ms", -S)):
                 v = prerotate(self.doppler_diagonal(M, delta), g, self.n1, 1)
                 out[(tag, delta)] = ck.encode(P, v, q[L], L)
@@ -1127,26 +1150,38 @@ class GestureCircuit:
         ks |= {lay.ard_pad << i for i in range(int(math.log2(lay.k)))}
         ks |= set(range(1, self.nf1)) | {g * self.nf1 for g in range(1, cfg.width // self.nf1)}
         ks |= {cfg.width << i for i in range(int(math.log2(lay.ard_pad // cfg.width)))}
-        return sorted({k % P.slots for k in ks} - {0})
+        out = sorted({k % P.slots for k in ks} - {0})
+        return ([ck.ROT_CONJ] if cfg.complex_slots else []) + out
 
     # -- the circuit ---------------------------------------------------------
     def features(self, ev, consts, pairs):
         """K3 -> K1 -> K6 -> soft power -> weighting per pair, then the
         accumulation over every frame; returns the feature ciphertext
-        (every frame position of it holds the sum) at level L - 6."""
+        (every frame position of it holds the sum) at level L - 6.  pairs:
+        (re, im) ciphertexts, or with complex slots one ciphertext each."""
         acc = None
-        for re, im in pairs:
-            babies = {"re": ev.hoisted(re, list(range(self.n1))), "im": ev.hoisted(im, list(range(self.n1)))}
-            c_re = {}
-            c_im = {}
-            for delta in self.deltas:
-                c_re[("re", delta)] = consts[("gdft_c", delta)]
-                c_re[("im", delta)] = consts[("gdft_ms", delta)]
-                c_im[("re", delta)] = consts[("gdft_s", delta)]
-                c_im[("im", delta)] = consts[("gdft_c", delta)]
-            d_re = ev.rescale(ev.bsgs(babies, c_re, self.n1, 1, re.level))
-            d_im = ev.rescale(ev.bsgs(babies, c_im, self.n1, 1, re.level))
-            p = ev.rescale(ev.square_sum([d_re, d_im]))            # K1
+        for pair in pairs:
+            if self.cfg.complex_slots:
+                # K3 on Re + i Im: one product with the complex W (Eq. K3 in one
+                # step); K1 |d|^2 = d conj(d)
+                z = pair
+                babies = {"z": ev.hoisted(z, list(range(self.n1)))}
+                cw = {("z", delta): consts[("gdft_w", delta)] for delta in self.deltas}
+                d = ev.rescale(ev.bsgs(babies, cw, self.n1, 1, z.level))
+                p = ev.rescale(ev.relin(ev.tensor(d, ev.conjugate(d))))   # K1
+            else:
+                re, im = pair
+                babies = {"re": ev.hoisted(re, list(range(self.n1))), "im": ev.hoisted(im, list(range(self.n1)))}
+                c_re = {}
+                c_im = {}
+                for delta in self.deltas:
+                    c_re[("re", delta)] = consts[("gdft_c", delta)]
+                    c_re[("im", delta)] = consts[("gdft_ms", delta)]
+                    c_im[("re", delta)] = consts[("gdft_s", delta)]
+                    c_im[("im", delta)] = consts[("gdft_c", delta)]
+                d_re = ev.rescale(ev.bsgs(babies, c_re, self.n1, 1, re.level))
+                d_im = ev.rescale(ev.bsgs(babies, c_im, self.n1, 1, re.level))
+                p = ev.rescale(ev.square_sum([d_re, d_im]))            # K1
             p = ev.rescale(ev.mul_plain(p, consts[("notch",)]))    # K6
             w = ev.rescale(ev.square_sum([p]))                     # K2, gamma = 4
             w = ev.rescale(ev.square_sum([w]))

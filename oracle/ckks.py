@@ -172,6 +172,16 @@ def decode(P, pt):
     return decode_coeffs(P, crt_centered(P, pt.m, pt.level), pt.scale)
 
 
+def decode_complex(P, pt):
+    """Complex slot values z_j = m(zeta^(5^j)) / scale."""
+    N = P.n
+    m = np.array([float(x) for x in crt_centered(P, pt.m, pt.level)], dtype=np.float64) / pt.scale
+    k = np.arange(N)
+    E = N * np.fft.ifft(m * np.exp(1j * np.pi * k / N))
+    pos, _ = _slot_index(N)
+    return E[pos]
+
+
 # ----------------------------------------------------------------------------
 # keys
 # ----------------------------------------------------------------------------
@@ -219,9 +229,21 @@ def gen_switch_key(P, sk, s_from_rns, a_draw, e_draw):
     return SwitchKey(P, data)
 
 
+# Key id of the conjugation X -> X^(2N-1) (slot values z -> conj(z)).
+ROT_CONJ = -(1 << 31)
+
+
 def galois_element(P, k):
-    """g = 5^(k mod N/2) mod 2N: left rotation of the slot vector by k."""
+    """g = 5^(k mod N/2) mod 2N: left rotation of the slot vector by k;
+    k = ROT_CONJ: g = 2N - 1, complex conjugation of every slot."""
+    if k == ROT_CONJ:
+        return 2 * P.n - 1
     return pow(5, k % P.slots, 2 * P.n)
+
+
+def key_id(P, k):
+    """Index of the switching key of rotation k (or ROT_CONJ)."""
+    return k if k == ROT_CONJ else k % P.slots
 
 
 def gen_relin_key(P, sk, a_draw, e_draw):
@@ -548,6 +570,12 @@ def rotate(P, a, k, gks):
     return rotate_hoisted(P, a, [k], gks)[0]
 
 
+def conjugate(P, a, gks):
+    """Slot-wise complex conjugate (the automorphism X -> X^(2N-1)), switched
+    back to s with the key ROT_CONJ, on the rotation's schedule."""
+    return rotate_hoisted(P, a, [ROT_CONJ], gks)[0]
+
+
 def rotate_hoisted(P, a, ks, gks):
     """Rotations of one ciphertext by every k in ``ks`` sharing one ModUp of c1:
     the automorphism is applied to the ModUp digits, then inner product and
@@ -557,12 +585,12 @@ def rotate_hoisted(P, a, ks, gks):
     prqp = qp_primes(P, a.level)
     out = []
     for k in ks:
-        if k % P.slots == 0:
+        if key_id(P, k) == 0:
             out.append(a.copy())
             continue
         g = galois_element(P, k)
         rd = [ring_automorphism(y, g, prqp) for y in digits]
-        u0, u1 = inner_product(P, rd, gks[k % P.slots], a.level)
+        u0, u1 = inner_product(P, rd, gks[key_id(P, k)], a.level)
         c0 = ring_automorphism(a.c0, g, pr)
         out.append(Ciphertext(ring_add(c0, moddown(P, u0, a.level), pr), moddown(P, u1, a.level), a.level, a.scale))
     return out

@@ -143,3 +143,73 @@ def test_gesture_circuit_decrypts_to_fp64(frames):
     logits = ck.decrypt_decode(P, sk, out)[: cfg.fc_dims[-1]]
     want = cc.gesture_forward(mats, ref, cfg)[: cfg.fc_dims[-1]]
     assert np.allclose(logits, want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
+
+
+def test_conjugation_is_slotwise_complex_conjugate():
+    """The automorphism X -> X^(2N-1) with its switching key conjugates every
+    slot (textbook CKKS property), within the encryption noise."""
+    P = tiny_params()
+    kd = synth.KeyDraws(81, P.n, P.q, P.p, P.dnum, [ck.ROT_CONJ])
+    sk = ck.SecretKey(P, kd.secret)
+    pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
+    gks = {ck.ROT_CONJ: ck.gen_galois_key(P, sk, ck.ROT_CONJ, *kd.gk[ck.ROT_CONJ])}
+    g = np.random.default_rng(82)
+    z = g.normal(size=P.slots) + 1j * g.normal(size=P.slots)
+    ct = ck.encrypt(P, pk, ck.encode(P, z, P.scale, P.L), *synth.encryption_draws(83, P.n))
+    assert np.allclose(ck.decode_complex(P, ck.decrypt(P, sk, ct)), z, atol=1e-8)
+    cz = ck.conjugate(P, ct, gks)
+    assert np.allclose(ck.decode_complex(P, ck.decrypt(P, sk, cz)), np.conj(z), atol=1e-8)
+    assert not np.allclose(np.conj(z), z, atol=1e-3)
+
+
+def test_complex_block_diagonal_bsgs_in_the_clear():
+    """With Re + i Im in one slot, one product by the complex W (its
+    diagonals, pre-rotation, floor split) equals d_re + i d_im of Eq. K3."""
+    P = tiny_params()
+    cfg = cc.GestureConfig(antennas=2, bins=4, chirps=8, frames=20, fc_dims=(7, 5, 3), width=16, complex_slots=True)
+    circ = cc.GestureCircuit(P, cfg)
+    D, n1 = cfg.chirps, circ.n1
+    W = cc.dft_kernel(D)
+    g = np.random.default_rng(7)
+    v = (g.normal(size=P.slots) + 1j * g.normal(size=P.slots)) * circ.lay.active()
+    babies = [cc.rotate_slots(v, b) for b in range(n1)]
+    groups = {}
+    for delta in circ.deltas:
+        dg = cc.prerotate(circ.doppler_diagonal(W, delta), delta // n1, n1, 1)
+        groups.setdefault(delta // n1, []).append(dg * babies[delta % n1])
+    out = sum(cc.rotate_slots(sum(t), gg * n1) for gg, t in groups.items())
+    ref = (v.reshape(-1, D) @ W.T).reshape(-1) * circ.lay.active()
+    assert np.allclose(out, ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("frames", [20, 13])
+def test_complex_slot_gesture_circuit_decrypts_to_fp64(frames):
+    cfg = cc.GestureConfig(antennas=2, bins=4, chirps=8, frames=frames, fc_dims=(7, 5, 3), width=16,
+                           complex_slots=True)
+    P = tiny_params()
+    circ = cc.GestureCircuit(P, cfg)
+    rots = circ.rotations()
+    assert rots[0] == ck.ROT_CONJ
+    kd = synth.KeyDraws(52, P.n, P.q, P.p, P.dnum, rots)
+    sk = ck.SecretKey(P, kd.secret)
+    pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
+    rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
+    gks = {ck.key_id(P, k): ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
+    mats = random_gesture_net(cfg, 5)
+    consts = circ.constants(mats)
+    zt = tiny_window(6, cfg)
+    cts = [ck.encrypt(P, pk, ck.encode(P, v, P.scale, P.L), *synth.encryption_draws(90 + i, P.n))
+           for i, v in enumerate(circ.lay.pack_complex(zt))]
+    ev = cc.Evaluator(P, rlk, gks)
+    ref = plain.gesture_features(zt, cfg)["feat"]
+    feat = circ.features(ev, consts, cts)
+    assert feat.level == P.L - 6
+    dec = ck.decrypt_decode(P, sk, feat)
+    for j in range(circ.lay.k):
+        got = dec[j * circ.lay.ard_pad: j * circ.lay.ard_pad + cfg.ard]
+        assert np.allclose(got, ref.reshape(-1), atol=1e-9 * max(1.0, np.abs(ref).max()))
+    out = circ.run(ev, consts, cts)
+    assert out.level == 0
+    logits = ck.decrypt_decode(P, sk, out)[: cfg.fc_dims[-1]]
+    want = cc.gesture_forward(mats, ref, cfg)[: cfg.fc_dims[-1]]
+    assert np.allclose(logits, want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
