@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--key-budget-gib", type=float, default=48.0, help="serving workload: resident key budget")
     ap.add_argument("--windows", type=int, default=64, help="batching workload: windows per step")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--complex-slots", action="store_true",
+                    help="gesture workload: Re + i Im in one complex slot (one input ciphertext per frame group)")
     ap.add_argument("--tiles", default=None,
                     help="cols_width,rows_threads,keyip_windows,conv_rows: set the tile shapes instead of autotuning")
     args = ap.parse_args()
@@ -1115,7 +1117,7 @@ def run_gesture(args, rank, world, local):
     dev = torch.device("cuda", local)
     params = M.gesture_params()
     ctx = M.Context(params, device=local)
-    plan = ctx.plan(M.gesture_config())
+    plan = ctx.plan(M.gesture_config(complex_slots=args.complex_slots))
     plan.encode_consts()
     for l, W in enumerate(gesture_random_mats(GestureShape, 11)):
         plan.set_fc_layer(l, W)
@@ -1199,7 +1201,9 @@ def run_gesture(args, rank, world, local):
         "metric": "encrypted gesture windows/s", "value": value, "unit": "windows/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": GESTURE_WORKLOAD, "batch_windows": B, "windows_per_step_all_gpus": world * B,
+        "config": {"workload": GESTURE_WORKLOAD + (", complex-slot packing (Re + i Im in one slot, 30 input cts)"
+                                                   if args.complex_slots else ""),
+                   "batch_windows": B, "windows_per_step_all_gpus": world * B,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%d MiB of ciphertexts per step)" % (B * in_words * 8 >> 20),
                    "weights": "random-init FC weights of the network's shape", "tiles": tiles},

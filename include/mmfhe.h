@@ -152,7 +152,10 @@ mmfhe_status mmfhe_keys_create(mmfhe_ctx *ctx, uint64_t user_id, mmfhe_keys **ou
 /* words: switching key from s^2 to s, layout above.  Errors: BAD_ARG. */
 mmfhe_status mmfhe_keys_set_relin(mmfhe_keys *keys, const uint64_t *words);
 /* Galois key for the left rotation Rot(x, k)[j] = x[(j + k) mod N/2], i.e.
- * the automorphism X -> X^g, g = 5^(k mod N/2) mod 2N; switches s(X^g) to s. */
+ * the automorphism X -> X^g, g = 5^(k mod N/2) mod 2N; switches s(X^g) to s.
+ * rotation = MMFHE_ROT_CONJ: the key of the conjugation g = 2N - 1 (every
+ * slot to its complex conjugate). */
+#define MMFHE_ROT_CONJ ((int32_t)0x80000000)
 mmfhe_status mmfhe_keys_set_galois(mmfhe_keys *keys, int32_t rotation, const uint64_t *words);
 mmfhe_status mmfhe_keys_unload(mmfhe_keys *keys);
 
@@ -259,7 +262,8 @@ mmfhe_status mmfhe_ct_bsgs(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out
  * a frame: a R D + r D + c; ARD_pad = 2^ceil(log2(A R D)); k = (N/2) /
  * ARD_pad frames per ciphertext, frame f in pair f / k at offset
  * (f mod k) ARD_pad.  Window input: pairs = ceil(F / k) ciphertext pairs,
- * (Re, Im) of pair 0, then pair 1, ... at the top level (2 pairs inputs).
+ * (Re, Im) of pair 0, then pair 1, ... at the top level (2 pairs inputs);
+ * with complex_slots one ciphertext of Re + i Im per pair (pairs inputs).
  * Output: one ciphertext at level top - 11, logits in slots 0..classes-1 of
  * every fc_width-slot period.  Fields: bins = R, frames = F, antennas = A,
  * chirps = D, fc_width = the FC slot period (a power of two <= ARD_pad,
@@ -291,7 +295,9 @@ typedef struct mmfhe_circuit_config {
     uint32_t antennas;         /* A virtual antennas */
     uint32_t chirps;           /* D chirps per frame = Doppler bins */
     uint32_t fc_width;         /* slot period of the FC layers */
-    uint32_t reserved;
+    uint32_t complex_slots;    /* 1: Re + i Im of a frame group in one ciphertext (complex slots): one
+                                  input per pair, K3 one complex product, K1 d conj(d); needs
+                                  the conjugation key MMFHE_ROT_CONJ */
     double input_scale;        /* encryption scale Delta of the inputs */
 } mmfhe_circuit_config;
 
@@ -315,6 +321,8 @@ typedef struct mmfhe_circuit_config {
 #define MMFHE_CONST_NOTCH 15   /* GESTURE: notch mask m[c] on every active slot */
 #define MMFHE_CONST_FCB 16     /* GESTURE: FC1 bias b[s mod fc_width], 1 in slot fc_width-1, encoded at
                                   the scale of FC1's rescaled output */
+#define MMFHE_CONST_GDFT_W 17  /* GESTURE with complex slots: the complex W Doppler diagonal delta =
+                                  index - D (pre-rotated), encoded as complex slots */
 
 typedef struct mmfhe_const_key {
     uint32_t tag, band, index, level;
@@ -352,7 +360,8 @@ mmfhe_status mmfhe_plan_set_fc_layer(mmfhe_plan *plan, uint32_t layer, const dou
 mmfhe_status mmfhe_plan_num_scalars(const mmfhe_plan *plan, uint32_t *count);
 mmfhe_status mmfhe_plan_get_scalars(const mmfhe_plan *plan, double *out, uint32_t capacity);
 mmfhe_status mmfhe_plan_set_scalars(mmfhe_plan *plan, const double *values, uint32_t count);
-/* Rotation amounts whose Galois keys the plan needs (ascending, in [0, N/2)). */
+/* Rotation amounts whose Galois keys the plan needs (ascending, in [0, N/2);
+ * MMFHE_ROT_CONJ first when the circuit conjugates). */
 mmfhe_status mmfhe_plan_rotations(const mmfhe_plan *plan, int32_t *out, uint32_t capacity, uint32_t *count);
 /* Input/output shape: ciphertexts per window in and out, and the level of
  * every output ciphertext (levels capacity 16).  Window input layout:

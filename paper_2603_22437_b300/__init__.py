@@ -11,13 +11,13 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (CIRCUIT_FC, CIRCUIT_FIR_DFT, CIRCUIT_GESTURE, CIRCUIT_VITAL, CIRCUIT_VITAL_PER_FRAME, CONST_TAGS, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
+from ._lib import (CIRCUIT_FC, CIRCUIT_FIR_DFT, CIRCUIT_GESTURE, CIRCUIT_VITAL, CIRCUIT_VITAL_PER_FRAME, CONST_TAGS, ROT_CONJ, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
                    MmfheError, Params, ServerConfig, ServerStats, Tuning, check, ptr, ptr_array, stream_ptr)
 
 __all__ = ["Context", "Keys", "Plan", "Graph", "Batcher", "Server", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
            "Params", "CIRCUIT_FIR_DFT", "CIRCUIT_VITAL", "CIRCUIT_FC", "vital_config", "fir_dft_config",
            "fc_config", "fir_dft_params", "vital_params", "fc_params", "fold_poly_net", "CIRCUIT_GESTURE",
-           "gesture_params", "gesture_config", "fold_poly_net_wide", "Ntt32", "ntt32_primes"]
+           "gesture_params", "gesture_config", "fold_poly_net_wide", "Ntt32", "ntt32_primes", "ROT_CONJ"]
 
 
 def params_select(log_n, num_q, q0_bits, q_bits, num_p, p_bits, dnum):
@@ -128,12 +128,14 @@ def gesture_params():
 
 
 def gesture_config(antennas=4, bins=64, chirps=32, frames=60, fc_dims=(31, 16, 6), fc_width=32,
-                   input_scale=2.0 ** 50):
+                   input_scale=2.0 ** 50, complex_slots=False):
     """The gesture chain: K3 Doppler DFT -> K1 -> K6 -> w = p^4 -> p w,
     summed over frames, then FC1^2 -> FC2^2 -> FC3 (fc_dims = d_1, d_2,
-    classes on a slot period of fc_width)."""
+    classes on a slot period of fc_width).  complex_slots: Re + i Im of a
+    frame group in one ciphertext (needs the key ROT_CONJ)."""
     c = CircuitConfig()
     c.kind, c.bins, c.frames = CIRCUIT_GESTURE, bins, frames
+    c.complex_slots = int(bool(complex_slots))
     c.antennas, c.chirps, c.fc_width, c.input_scale = antennas, chirps, fc_width, float(input_scale)
     c.fc_dims[0] = antennas * bins * chirps
     for i, d in enumerate(fc_dims):

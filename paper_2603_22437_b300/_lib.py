@@ -22,7 +22,9 @@ ERRORS = {
 }
 CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_FC, CIRCUIT_VITAL_PER_FRAME, CIRCUIT_GESTURE = 1, 2, 3, 4, 5
 CONST_TAGS = {1: "idx", 2: "one", 3: "fir", 4: "dre", 5: "dim", 6: "fw", 7: "fone", 8: "dft_c", 9: "dft_s",
-              10: "dft_ms", 11: "fcw", 12: "gdft_c", 13: "gdft_s", 14: "gdft_ms", 15: "notch", 16: "fcb"}
+              10: "dft_ms", 11: "fcw", 12: "gdft_c", 13: "gdft_s", 14: "gdft_ms", 15: "notch", 16: "fcb",
+              17: "gdft_w"}
+ROT_CONJ = -(1 << 31)   # key id of the slot-wise complex conjugation
 
 
 class MmfheError(RuntimeError):
@@ -51,7 +53,7 @@ class CircuitConfig(ctypes.Structure):
                 ("num_bands", ctypes.c_uint32), ("band_lo_mhz", ctypes.c_uint32 * 2),
                 ("band_hi_mhz", ctypes.c_uint32 * 2), ("dft_gain", ctypes.c_double * 2), ("fc_dims", ctypes.c_uint32 * 9),
                 ("antennas", ctypes.c_uint32), ("chirps", ctypes.c_uint32), ("fc_width", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32), ("input_scale", ctypes.c_double)]
+                ("complex_slots", ctypes.c_uint32), ("input_scale", ctypes.c_double)]
 
 
 class KernelStat(ctypes.Structure):

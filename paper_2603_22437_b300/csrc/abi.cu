@@ -167,7 +167,13 @@ void mmfhe::eval_windows(Context &c, const Plan &p, const Keys *const *keys, con
             outs[b] = out_cts[g.second[b]];
         }
         std::vector<CtB> in;
-        if (p.cfg.kind == MMFHE_CIRCUIT_GESTURE) {
+        if (p.cfg.kind == MMFHE_CIRCUIT_GESTURE && p.cfg.complex_slots) {
+            // one complex-slot ciphertext per pair, window-major
+            std::vector<const uint64_t *> z((size_t)B * p.pairs);
+            for (int b = 0; b < B; b++)
+                for (int j = 0; j < p.pairs; j++) z[(size_t)b * p.pairs + j] = ins[b] + (size_t)j * in_w;
+            in.push_back(load_cts(c, z.data(), 0, B * p.pairs, c.L, 1.0, st));
+        } else if (p.cfg.kind == MMFHE_CIRCUIT_GESTURE) {
             // Re and Im of all pairs of all windows, window-major
             std::vector<const uint64_t *> re((size_t)B * p.pairs), im((size_t)B * p.pairs);
             for (int b = 0; b < B; b++)

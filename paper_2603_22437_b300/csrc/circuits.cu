@@ -116,13 +116,15 @@ static void fft_inplace(std::vector<std::complex<double>> &a) {
     }
 }
 
-void encode_slots(const mmfhe_params &p, const double *slots, double scale, int level, uint64_t *out) {
+void encode_slots(const mmfhe_params &p, const double *slots, double scale, int level, uint64_t *out,
+                  const double *imag) {
     const uint32_t N = 1u << p.log_n, n = N / 2;
     std::vector<std::complex<double>> Z(N);
     uint64_t e = 1;
     for (uint32_t j = 0; j < n; j++) {
-        Z[(e - 1) / 2] = slots[j];
-        Z[(2 * N - e - 1) / 2] = slots[j];   // real slots: the conjugate equals the value
+        const std::complex<double> z(slots[j], imag ? imag[j] : 0.0);
+        Z[(e - 1) / 2] = z;
+        Z[(2 * N - e - 1) / 2] = std::conj(z);   // the conjugate-symmetric extension
         e = (e * 5) % (2 * N);
     }
     fft_inplace(Z);
@@ -233,10 +235,14 @@ static Plan *create_gesture_plan(Context &c, const mmfhe_circuit_config &cfg) {
     p->n1_fc = bsgs_split(W).first;
     std::set<int32_t> rots;
     for (int delta = -(D - 1); delta < D; delta++) {
-        for (uint32_t tag : {MMFHE_CONST_GDFT_C, MMFHE_CONST_GDFT_S, MMFHE_CONST_GDFT_MS})
-            p->keys.push_back(mmfhe_const_key{tag, 0, (uint32_t)(delta + D), (uint32_t)L});
+        if (cfg.complex_slots)
+            p->keys.push_back(mmfhe_const_key{MMFHE_CONST_GDFT_W, 0, (uint32_t)(delta + D), (uint32_t)L});
+        else
+            for (uint32_t tag : {MMFHE_CONST_GDFT_C, MMFHE_CONST_GDFT_S, MMFHE_CONST_GDFT_MS})
+                p->keys.push_back(mmfhe_const_key{tag, 0, (uint32_t)(delta + D), (uint32_t)L});
         rots.insert(norm_rot(c, floor_div(delta, p->n1_k3) * p->n1_k3));
     }
+    if (cfg.complex_slots) rots.insert(MMFHE_ROT_CONJ);
     p->keys.push_back(mmfhe_const_key{MMFHE_CONST_NOTCH, 0, 0, (uint32_t)(L - 2)});
     for (int k = 0; k < W; k++) p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCW, 0, (uint32_t)k, (uint32_t)(L - 6)});
     p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCB, 0, 0, (uint32_t)(L - 7)});
@@ -250,7 +256,7 @@ static Plan *create_gesture_plan(Context &c, const mmfhe_circuit_config &cfg) {
     for (int s = W; s < p->ard_pad; s <<= 1) rots.insert(norm_rot(c, s));
     rots.erase(0);
     p->rotations.assign(rots.begin(), rots.end());
-    p->n_in = 2 * p->pairs;
+    p->n_in = cfg.complex_slots ? p->pairs : 2 * p->pairs;
     p->out_levels = {L - 11};
     p->consts.resize(p->keys.size());
     for (size_t i = 0; i < p->keys.size(); i++) p->index[key_of(p->keys[i])] = (int)i;
@@ -536,7 +542,8 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
     }
     case MMFHE_CONST_GDFT_C:
     case MMFHE_CONST_GDFT_S:
-    case MMFHE_CONST_GDFT_MS: {
+    case MMFHE_CONST_GDFT_MS:
+    case MMFHE_CONST_GDFT_W: {   // GDFT_W: the real part (C); plan_encode_consts adds S as the imaginary part
         // block-diagonal I (x) M of Eq. K3 on every active slot:
         // diag_delta[s] = M[i][i + delta], i = s mod D
         const int D = (int)cfg.chirps, delta = (int)k.index - D;
@@ -546,7 +553,8 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
             if (j < 0 || j >= D || s % p.ard_pad >= ard) continue;
             const int sig = (i + D / 2) % D;
             const double ang = -2 * M_PI * sig * j / D, w = hann(j, D);
-            double val = k.tag == MMFHE_CONST_GDFT_C ? w * std::cos(ang) : w * std::sin(ang);
+            double val = (k.tag == MMFHE_CONST_GDFT_C || k.tag == MMFHE_CONST_GDFT_W) ? w * std::cos(ang)
+                                                                                  : w * std::sin(ang);
             v[s] = k.tag == MMFHE_CONST_GDFT_MS ? -val : val;
         }
         return prerot(floor_div(delta, p.n1_k3), p.n1_k3, 1);
@@ -578,9 +586,15 @@ void plan_encode_consts(Plan &p, cudaStream_t st) {
     for (size_t i = 0; i < p.keys.size(); i++) {
         const mmfhe_const_key &k = p.keys[i];
         if (k.tag == MMFHE_CONST_FCW || k.tag == MMFHE_CONST_FCB) continue;   // learned: set_fc_layer
-        std::vector<double> v = const_slots(p, k);
+        std::vector<double> v = const_slots(p, k), im;
+        if (k.tag == MMFHE_CONST_GDFT_W) {   // complex W = C + i S
+            mmfhe_const_key ks = k;
+            ks.tag = MMFHE_CONST_GDFT_S;
+            im = const_slots(p, ks);
+        }
         words.assign((size_t)(k.level + 1) * c.n, 0);
-        encode_slots(c.params, v.data(), (double)c.primes[k.level], (int)k.level, words.data());
+        encode_slots(c.params, v.data(), (double)c.primes[k.level], (int)k.level, words.data(),
+                     im.empty() ? nullptr : im.data());
         plan_set_const(p, (uint32_t)i, words.data(), st);
         CK(cudaStreamSynchronize(st));
     }
@@ -833,30 +847,48 @@ static std::vector<CtB> run_gesture(Context &c, const Plan &p, const Keys &k, st
     const int D = (int)cfg.chirps, W = (int)cfg.fc_width;
     CtB feat;
     {
-        // K3: d_re = C re - S im, d_im = S re + C im (Eq. K3), one BSGS each
         std::vector<int32_t> rb(p.n1_k3);
         std::vector<int> idx(p.n1_k3);
         for (int b = 0; b < p.n1_k3; b++) rb[b] = idx[b] = b;
-        std::vector<CtB> bre = rotate_hoisted(c, k, in[0], rb, st);
-        std::vector<CtB> bim = rotate_hoisted(c, k, in[1], rb, st);
-        in.clear();
-        BsgsTerm t[4];
-        for (int i = 0; i < 4; i++) {
-            t[i].baby = i % 2 == 0 ? &bre : &bim;
-            t[i].baby_idx = idx;
+        CtB pw;
+        if (cfg.complex_slots) {
+            // K3 on Re + i Im: one product with the complex W; K1 |d|^2 = d conj(d)
+            std::vector<CtB> bz = rotate_hoisted(c, k, in[0], rb, st);
+            in.clear();
+            BsgsTerm tz;
+            tz.baby = &bz;
+            tz.baby_idx = idx;
+            for (int delta = -(D - 1); delta < D; delta++)
+                tz.diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_W, 0, (uint32_t)(delta + D))});
+            CtB d = rescale(c, bsgs(c, k, {tz}, p.n1_k3, 1, st), st);
+            bz.clear();
+            CtB dc = rotate(c, k, d, MMFHE_ROT_CONJ, st);
+            TensorB tt = tensor_new(c, d.B, d.level);
+            tensor_acc(c, tt, d, dc, 1, true, st);
+            pw = rescale(c, relin(c, k, tt, st), st);
+        } else {
+            // K3: d_re = C re - S im, d_im = S re + C im (Eq. K3), one BSGS each
+            std::vector<CtB> bre = rotate_hoisted(c, k, in[0], rb, st);
+            std::vector<CtB> bim = rotate_hoisted(c, k, in[1], rb, st);
+            in.clear();
+            BsgsTerm t[4];
+            for (int i = 0; i < 4; i++) {
+                t[i].baby = i % 2 == 0 ? &bre : &bim;
+                t[i].baby_idx = idx;
+            }
+            for (int delta = -(D - 1); delta < D; delta++) {
+                const uint32_t ix = (uint32_t)(delta + D);
+                t[0].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_C, 0, ix)});
+                t[1].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_MS, 0, ix)});
+                t[2].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_S, 0, ix)});
+                t[3].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_C, 0, ix)});
+            }
+            CtB dre = rescale(c, bsgs(c, k, {t[0], t[1]}, p.n1_k3, 1, st), st);
+            CtB dim = rescale(c, bsgs(c, k, {t[2], t[3]}, p.n1_k3, 1, st), st);
+            bre.clear();
+            bim.clear();
+            pw = rescale(c, square_sum(c, k, {&dre, &dim}, st), st);                  // K1
         }
-        for (int delta = -(D - 1); delta < D; delta++) {
-            const uint32_t ix = (uint32_t)(delta + D);
-            t[0].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_C, 0, ix)});
-            t[1].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_MS, 0, ix)});
-            t[2].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_S, 0, ix)});
-            t[3].diags.push_back({delta, &plan_const(p, MMFHE_CONST_GDFT_C, 0, ix)});
-        }
-        CtB dre = rescale(c, bsgs(c, k, {t[0], t[1]}, p.n1_k3, 1, st), st);
-        CtB dim = rescale(c, bsgs(c, k, {t[2], t[3]}, p.n1_k3, 1, st), st);
-        bre.clear();
-        bim.clear();
-        CtB pw = rescale(c, square_sum(c, k, {&dre, &dim}, st), st);              // K1
         CtB pm = ct_new(c, pw.B, pw.level, pw.scale);
         ct_mul_plain(c, pm, pw, plan_const(p, MMFHE_CONST_NOTCH, 0, 0), false, st);   // K6
         CtB pn = rescale(c, pm, st);

@@ -31,7 +31,9 @@ struct Plan {
 uint64_t key_of(const mmfhe_const_key &k);
 std::vector<int> band_bins(int frames, int fs_mhz, int lo_mhz, int hi_mhz);
 std::vector<double> fir_bandpass(int taps, double f_lo, double f_hi, double fs);
-void encode_slots(const mmfhe_params &p, const double *slots, double scale, int level, uint64_t *out);
+// imag (nullable): imaginary parts of complex slots.
+void encode_slots(const mmfhe_params &p, const double *slots, double scale, int level, uint64_t *out,
+                  const double *imag = nullptr);
 
 Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg);
 const PtDev &plan_const(const Plan &p, uint32_t tag, uint32_t band, uint32_t idx);

@@ -23,12 +23,14 @@ PidList pids_q(int nl) {
 }
 
 int32_t norm_rot(const Context &c, int32_t k) {
+    if (k == MMFHE_ROT_CONJ) return k;
     int32_t n2 = (int32_t)(c.n / 2);
     int32_t r = k % n2;
     return r < 0 ? r + n2 : r;
 }
 
 uint32_t galois_elt(const Context &c, int32_t k) {
+    if (k == MMFHE_ROT_CONJ) return (uint32_t)(2 * c.n - 1);   // slot-wise complex conjugation
     return (uint32_t)hm::powmod(5, (uint64_t)norm_rot(c, k), 2ull * c.n);
 }
 

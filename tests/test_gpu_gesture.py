@@ -20,6 +20,7 @@ pytestmark = pytest.mark.gpu
 
 KEY_SEED = 61
 SMALL = cc.GestureConfig(frames=4)          # the full frame shape, 2 ciphertext pairs
+SMALL_C = cc.GestureConfig(frames=4, complex_slots=True)   # complex-slot packing: 2 ciphertexts
 POOL_R = 4                                  # training features: antennas summed, range pooled by 4
 
 
@@ -31,7 +32,7 @@ def oracle_setup(cfg):
     sk = ck.SecretKey(P, kd.secret)
     pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
     rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
-    gks = {k: ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
+    gks = {ck.key_id(P, k): ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
     return P, circ, sk, pk, rlk, gks
 
 
@@ -52,36 +53,50 @@ def random_mats(cfg, seed):
 
 
 def encrypt_pairs(P, pk, circ, zt, seed):
+    """The window's input ciphertexts: (re, im) per pair, or with complex
+    slots one Re + i Im ciphertext per pair."""
+    if circ.cfg.complex_slots:
+        return [ck.encrypt(P, pk, ck.encode(P, v, P.scale, P.L), *synth.encryption_draws(seed + 2 * i, P.n))
+                for i, v in enumerate(circ.lay.pack_complex(zt))]
     return [tuple(ck.encrypt(P, pk, ck.encode(P, v, P.scale, P.L), *synth.encryption_draws(seed + 2 * i + h, P.n))
                   for h, v in enumerate(pair)) for i, pair in enumerate(circ.lay.pack(zt))]
 
 
-def _oracle_window(w):
+def flat(cts):
+    return [c for x in cts for c in (x if isinstance(x, tuple) else (x,))]
+
+
+def _oracle_window(job):
     """Worker (spawned process): the oracle's output words of window w."""
-    P, circ, sk, pk, rlk, gks = oracle_setup(SMALL)
-    zt = plain.gesture_preprocess(synth.gesture_window(300 + w, frames=SMALL.frames).z)
+    w, cplx = job
+    cfg = SMALL_C if cplx else SMALL
+    P, circ, sk, pk, rlk, gks = oracle_setup(cfg)
+    zt = plain.gesture_preprocess(synth.gesture_window(300 + w, frames=cfg.frames).z)
     cts = encrypt_pairs(P, pk, circ, zt, 5000 + 100 * w)
-    out = circ.run(cc.Evaluator(P, rlk, gks), circ.constants(random_mats(SMALL, 9)), cts)
-    return window_words([c for pair in cts for c in pair]), out.words(), out.scale
+    out = circ.run(cc.Evaluator(P, rlk, gks), circ.constants(random_mats(cfg, 9)), cts)
+    return window_words(flat(cts)), out.words(), out.scale
 
 
 @pytest.fixture(scope="module")
 def gest():
     # the oracle runs in spawned processes, started before this process touches the GPU
-    pool = mp.get_context("spawn").Pool(2)
-    pending = pool.map_async(_oracle_window, [0, 1])
+    pool = mp.get_context("spawn").Pool(4)
+    pending = pool.map_async(_oracle_window, [(0, False), (1, False), (0, True), (1, True)])
     import paper_2603_22437_b300 as M
     P, circ, sk, pk, rlk, gks = oracle_setup(SMALL)
     ctx = M.Context(lib_params(P))
     keys = load_keys(ctx, P, rlk, gks)
-    yield dict(P=P, circ=circ, sk=sk, pk=pk, rlk=rlk, gks=gks, ctx=ctx, keys=keys, pending=pending)
+    _, circ_c, sk_c, pk_c, rlk_c, gks_c = oracle_setup(SMALL_C)
+    keys_c = load_keys(ctx, P, rlk_c, gks_c)
+    yield dict(P=P, circ=circ, sk=sk, pk=pk, rlk=rlk, gks=gks, ctx=ctx, keys=keys, pending=pending,
+               circ_c=circ_c, sk_c=sk_c, pk_c=pk_c, keys_c=keys_c)
     pool.close()
     pool.join()
 
 
 def install(plan, consts, D):
     for i, (tag, band, index, level) in enumerate(plan.const_keys()):
-        if tag in ("gdft_c", "gdft_s", "gdft_ms"):
+        if tag in ("gdft_c", "gdft_s", "gdft_ms", "gdft_w"):
             key = (tag, index - D)
         elif tag == "fcw":
             key = ("fcw", band, index)
@@ -93,7 +108,7 @@ def install(plan, consts, D):
 
 def gesture_config(M, cfg):
     return M.gesture_config(antennas=cfg.antennas, bins=cfg.bins, chirps=cfg.chirps, frames=cfg.frames,
-                            fc_dims=cfg.fc_dims, fc_width=cfg.width)
+                            fc_dims=cfg.fc_dims, fc_width=cfg.width, complex_slots=cfg.complex_slots)
 
 
 def test_gesture_word_exact_two_windows(gest):
@@ -104,7 +119,7 @@ def test_gesture_word_exact_two_windows(gest):
     assert plan.io() == (2 * circ.lay.pairs, 1, [0])
     consts = circ.constants(random_mats(SMALL, 9))
     install(plan, consts, SMALL.chirps)
-    ref = gest["pending"].get(timeout=1800)
+    ref = gest["pending"].get(timeout=1800)[:2]
     ins = [r[0] for r in ref]
     outs = [np.empty(2 * P.n, dtype=np.uint64) for _ in ref]
     ctx.eval(plan, keys, ins, outs)
@@ -115,6 +130,28 @@ def test_gesture_word_exact_two_windows(gest):
     lib = ctx.plan(gesture_config(M, SMALL))
     lib.encode_consts()
     for l, W in enumerate(random_mats(SMALL, 9)):
+        lib.set_fc_layer(l, W)
+    compare_plan_consts(plan, lib, P)
+
+
+def test_complex_slot_gesture_word_exact_two_windows(gest):
+    """Complex-slot packing (Re + i Im in one slot, one input ciphertext per
+    pair, the conjugation key): two windows in one batch word for word
+    against the oracle; the library's complex encodings to +-1."""
+    import paper_2603_22437_b300 as M
+    P, circ, ctx, keys = gest["P"], gest["circ_c"], gest["ctx"], gest["keys_c"]
+    plan = ctx.plan(gesture_config(M, SMALL_C))
+    assert plan.rotations() == circ.rotations() and plan.rotations()[0] == M.ROT_CONJ
+    assert plan.io() == (circ.lay.pairs, 1, [0])
+    install(plan, circ.constants(random_mats(SMALL_C, 9)), SMALL_C.chirps)
+    ref = gest["pending"].get(timeout=1800)[2:]
+    outs = [np.empty(2 * P.n, dtype=np.uint64) for _ in ref]
+    ctx.eval(plan, keys, [r[0] for r in ref], outs)
+    for w, (_, want, scale) in enumerate(ref):
+        assert np.array_equal(outs[w], want.reshape(-1)), "window %d" % w
+    lib = ctx.plan(gesture_config(M, SMALL_C))
+    lib.encode_consts()
+    for l, W in enumerate(random_mats(SMALL_C, 9)):
         lib.set_fc_layer(l, W)
     compare_plan_consts(plan, lib, P)
 
@@ -183,6 +220,22 @@ def test_trained_gesture_labels_equal_fp64(gest):
         ct = ck.Ciphertext(outs[j].reshape(2, 1, P.n)[0], outs[j].reshape(2, 1, P.n)[1], 0, gesture_out_scale(P, circ))
         got = ck.decrypt_decode(P, gest["sk"], ct)[:C]
         assert got.argmax() == want.argmax() == quad.argmax()
+        assert np.allclose(got, want, atol=1e-4 * max(1.0, np.abs(want).max()))
+    # the same network on complex-slot packing (one input ciphertext per pair)
+    cfg_c = cc.GestureConfig(complex_slots=True)
+    circ_c = cc.GestureCircuit(P, cfg_c)
+    plan_c = ctx.plan(gesture_config(M, cfg_c))
+    plan_c.encode_consts()
+    for l, Wm in enumerate(mats):
+        plan_c.set_fc_layer(l, Wm)
+    cts_c = [encrypt_pairs(P, gest["pk_c"], circ_c, zt, 8000 + 200 * i) for i, zt in enumerate(zts)]
+    outs_c = [np.empty(2 * P.n, dtype=np.uint64) for _ in sel]
+    ctx.eval(plan_c, gest["keys_c"], [window_words(ct) for ct in cts_c], outs_c)
+    for j, zt in enumerate(zts):
+        want = cc.gesture_forward(mats, plain.gesture_features(zt)["feat"], cfg)[:C]
+        o = outs_c[j].reshape(2, 1, P.n)
+        got = ck.decrypt_decode(P, gest["sk_c"], ck.Ciphertext(o[0], o[1], 0, gesture_out_scale(P, circ_c)))[:C]
+        assert got.argmax() == want.argmax()
         assert np.allclose(got, want, atol=1e-4 * max(1.0, np.abs(want).max()))
 
 
