@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--windows", type=int, default=64, help="batching workload: windows per step")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--complex-slots", action="store_true",
-                    help="gesture workload: Re + i Im in one complex slot (one input ciphertext per frame group)")
+                    help="vital and gesture workloads: Re + i Im in one complex slot (half the input ciphertexts)")
     ap.add_argument("--tiles", default=None,
                     help="cols_width,rows_threads,keyip_windows,conv_rows: set the tile shapes instead of autotuning")
     args = ap.parse_args()
@@ -458,7 +458,7 @@ def run_mine(args, rank, world, local):
     dev = torch.device("cuda", local)
     params = M.vital_params()
     ctx = M.Context(params, device=local)
-    plan = ctx.plan(M.vital_config())
+    plan = ctx.plan(M.vital_config(complex_slots=args.complex_slots))
     plan.encode_consts()
     rots = plan.rotations()
     P_q, P_p = params.primes_q, params.primes_p
@@ -532,7 +532,7 @@ def run_mine(args, rank, world, local):
     torch.cuda.synchronize()
     e2e_sync = job_throughput(world, B * args.e2e_steps, time.perf_counter() - t0)
     # (b) the serving API (two stream slots): the next batch's copies run under this batch's kernels
-    srv = ctx.server(M.vital_config(), max_batch=B, streams=2, batch_wait_us=20000)
+    srv = ctx.server(M.vital_config(complex_slots=args.complex_slots), max_batch=B, streams=2, batch_wait_us=20000)
     srv.add_user(rank, *keys_words)
     e2e_steps = max(8, args.e2e_steps)   # enough batches that the pipeline's fill and drain are amortised
     outs_ring = [[torch.empty(out_words, dtype=torch.int64).pin_memory() for _ in range(B)] for _ in range(2)]
@@ -569,7 +569,9 @@ def run_mine(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch_windows": B, "windows_per_step_all_gpus": world * B,
+        "config": {"workload": WORKLOAD + (", complex-slot packing (Re + i Im in one slot, 8 input cts)"
+                                           if args.complex_slots else ""),
+                   "batch_windows": B, "windows_per_step_all_gpus": world * B,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%d MiB of ciphertexts per step)" % (B * in_words * 8 >> 20),
                    "tiles": tiles},

@@ -295,9 +295,12 @@ typedef struct mmfhe_circuit_config {
     uint32_t antennas;         /* A virtual antennas */
     uint32_t chirps;           /* D chirps per frame = Doppler bins */
     uint32_t fc_width;         /* slot period of the FC layers */
-    uint32_t complex_slots;    /* 1: Re + i Im of a frame group in one ciphertext (complex slots): one
-                                  input per pair, K3 one complex product, K1 d conj(d); needs
-                                  the conjugation key MMFHE_ROT_CONJ */
+    uint32_t complex_slots;    /* GESTURE and VITAL: 1 = Re + i Im in one ciphertext of complex slots
+                                  (half the inputs; |z|^2 as z conj(z), so the conjugation key
+                                  MMFHE_ROT_CONJ is needed).  GESTURE: one input per pair, K3 one
+                                  complex product.  VITAL: stream 1 then stream 2, one ciphertext
+                                  per group; K4 gives I + i Q, one FIR product per band, K7 from
+                                  w = Z conj(Z at t-1), the phase from w^3 - conj(w^3) = 2i Im(w^3) */
     double input_scale;        /* encryption scale Delta of the inputs */
 } mmfhe_circuit_config;
 

@@ -92,6 +92,8 @@ class VitalConfig:
     taps: int = 64
     bands_mhz: tuple = ((100, 600), (800, 2500))     # respiration, heart (Sec. "Example Pipelines")
     taylor_order: int = 3
+    # complex-slot packing: each stream's Re + i Im in one ciphertext per group
+    complex_slots: bool = False
     # public per-band spectral gains g_b of the narrowband DFT
     # X_b[k] = g_b * sum_t w[t] dphi[t] exp(-j 2 pi k t / F) (None = defaults)
     dft_gains: tuple = None
@@ -229,6 +231,10 @@ class Evaluator:
         self._t("add_plain", a.level)
         return ck.add_plain(self.P, a, pt)
 
+    def sub(self, a, b):
+        self._t("sub", a.level)
+        return ck.sub(self.P, a, b)
+
     def mul_plain(self, a, pt):
         self._t("mul_plain", a.level)
         return ck.mul_plain(self.P, a, pt)
@@ -346,6 +352,8 @@ class CountingEvaluator(Evaluator):
 
     def add_plain(self, a, pt):
         return _Shape(a.level)
+
+    sub = add
 
     def mul_plain(self, a, pt):
         return _Shape(a.level)
@@ -579,7 +587,12 @@ class VitalCircuit:
         return fir_bandpass(self.cfg.taps, lo / 1000, hi / 1000, self.cfg.fs_mhz / 1000)
 
     def dft_gain(self, b):
-        """g_b, times 1/3 for the third-order chain (which carries 3 dphi)."""
+        """g_b over the factor the chain's phase signal carries: 3 dphi for
+        the third-order chain; with complex slots 2i Im(w^3) = 6i dphi (third
+        order) or 2i Im(w) = 2i dphi (first order), whose square is negated
+        by the i (and squared away by the sharpening)."""
+        if self.cfg.complex_slots:
+            return self.cfg.gains()[b] / (6.0 if self.cfg.taylor_order == 3 else 2.0)
         return self.cfg.gains()[b] * (1.0 / 3.0 if self.cfg.taylor_order == 3 else 1.0)
 
     def dft_time_matrix(self, b):
@@ -636,7 +649,8 @@ class VitalCircuit:
         ks |= {lay.r_c << i for i in range(int(math.log2(self.span_all())))}
         ks.add((lay.f_pad // 2) * lay.r_c)
         ks.add(1)
-        return sorted({k % self.P.slots for k in ks} - {0})
+        out = sorted({k % self.P.slots for k in ks} - {0})
+        return ([ck.ROT_CONJ] if self.cfg.complex_slots else []) + out
 
     def constant_keys(self):
         """Keys of every constant ``constants()`` encodes, without encoding."""
@@ -694,9 +708,12 @@ class VitalCircuit:
     # -- the chain -----------------------------------------------------------
     def run(self, ev, consts, s1, s2):
         """s1, s2: lists of G (re, im) ciphertext pairs (stream 1 feeds K1,
-        stream 2 feeds K4), all at the top level.  Returns six ciphertexts."""
+        stream 2 feeds K4), all at the top level; with complex slots lists
+        of G ciphertexts of Re + i Im.  Returns six ciphertexts."""
         P, lay, cfg = self.P, self.lay, self.cfg
         G = lay.groups
+        if cfg.complex_slots:
+            return self._run_complex(ev, consts, s1, s2)
         # side branch: K1 energy, K2 soft power attention (gamma = 2)
         w = []
         for re, im in s1:
@@ -772,6 +789,73 @@ class VitalCircuit:
         den = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[("fone",)])), lay.r_c, self.span_all())
         outs = [num_r, den_r, num, den, ev.rotate(num, 1), ev.rotate(den, 1)]
         return outs
+
+    def _run_complex(self, ev, consts, s1, s2):
+        """The same chain on complex slots z = Re + i Im: |z|^2 = z conj(z);
+        K4 gives Z = I + i Q in one ciphertext; the FIR is real-linear, so one
+        product per band filters both parts; K7 forms w = Z conj(Z') = x + i y,
+        third order Im(w^3) = 3 x^2 y - y^3 = 3 dphi, taken as
+        w^3 - conj(w^3) = 2i Im(w^3) (the DFT gains absorb 2i, reading in
+        dft_gain); first order w - conj(w) = 2i y."""
+        lay, cfg = self.lay, self.cfg
+        G = lay.groups
+
+        def abs2(z):
+            return ev.rescale(ev.relin(ev.tensor(z, ev.conjugate(z))))
+
+        w = []
+        for z in s1:
+            E = ev.rotsum(abs2(z), lay.r_c, lay.f_pad)
+            w.append(ev.rescale(ev.square_sum([E])))
+        num = den = None
+        for c in range(G):
+            tn = ev.mul_plain(w[c], consts[("idx", c)])
+            td = ev.mul_plain(w[c], consts[("one", c)])
+            num = tn if num is None else ev.add(num, tn)
+            den = td if den is None else ev.add(den, td)
+        num_r = ev.rotsum(ev.rescale(num), 1, lay.r_c)
+        den_r = ev.rotsum(ev.rescale(den), 1, lay.r_c)
+
+        # K4: Z = sum_r m z (I + i Q), P_phi = 2
+        m = [ev.rescale(ev.square_sum([abs2(z)])) for z in s2]
+        lv = m[0].level
+        t = None
+        for c in range(G):
+            tc = ev.tensor(m[c], ev.drop(s2[c], lv))
+            t = tc if t is None else ev.tensor_add(t, tc)
+        Z = ev.rotsum(ev.rescale(ev.relin(t)), 1, lay.r_c)
+
+        # K5: both bands in one product (RR in bin slot 0, HR in slot 1)
+        n1 = self.n1_fir
+        fir = {}
+        for b in range(len(self.bands)):
+            for k in range(cfg.taps):
+                fir[("s%d" % b, k)] = consts[("fir", b, k)]
+        hs = ev.hoisted(Z, [-j * lay.r_c - s for s in (0, 1) for j in range(n1)])
+        babies = {"s0": dict(zip(range(n1), hs[:n1])), "s1": dict(zip(range(n1), hs[n1:]))}
+        Zf = ev.rescale(ev.bsgs(babies, fir, n1, -lay.r_c, Z.level))
+
+        # K7: w = Zf conj(Zf at t-1) = x + i y
+        wc = ev.rescale(ev.relin(ev.tensor(Zf, ev.conjugate(ev.rotate(Zf, -lay.r_c)))))
+        if cfg.taylor_order == 3:
+            w2 = ev.rescale(ev.square_sum([wc]))
+            w3 = ev.rescale(ev.relin(ev.tensor(ev.drop(wc, w2.level), w2)))
+            dphi = ev.sub(w3, ev.conjugate(w3))
+        else:
+            dphi = ev.sub(wc, ev.conjugate(wc))
+
+        # K3, |X|^2 (negated by the i), sharpen, weighted frequency average
+        n1 = self.n1_dft
+        cl = {("x", key[1]): pt for key, pt in consts.items() if key[0] == "dft"}
+        need = sorted({d % n1 for (_, d) in cl})
+        babies = {"x": dict(zip(need, ev.hoisted(dphi, [bb * lay.r_c for bb in need])))}
+        X = ev.rescale(ev.bsgs(babies, cl, n1, lay.r_c, dphi.level))
+        pw = ev.rescale(ev.square_sum([X]))
+        Mg = ev.add(pw, ev.rotate(pw, (lay.f_pad // 2) * lay.r_c))
+        S = ev.rescale(ev.square_sum([Mg]))
+        num = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[("fw",)])), lay.r_c, self.span_all())
+        den = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[("fone",)])), lay.r_c, self.span_all())
+        return [num_r, den_r, num, den, ev.rotate(num, 1), ev.rotate(den, 1)]
 
 
 # ---------------------------------------------------------------------------

@@ -70,10 +70,12 @@ def pack_window(log_n, values):
 
 
 def vital_config(bins=256, frames=200, fs_mhz=20000, taps=64, taylor_order=3,
-                 bands_mhz=((100, 600), (800, 2500)), dft_gains=(0.0, 0.0), per_frame=False):
+                 bands_mhz=((100, 600), (800, 2500)), dft_gains=(0.0, 0.0), per_frame=False, complex_slots=False):
     """The vital chain; per_frame=True: the per-frame packing (one ciphertext
-    per frame and part, the paper's slow baseline)."""
+    per frame and part, the paper's slow baseline); complex_slots=True: each
+    stream's Re + i Im in one ciphertext per group (needs the key ROT_CONJ)."""
     c = CircuitConfig()
+    c.complex_slots = int(bool(complex_slots))
     kind = CIRCUIT_VITAL_PER_FRAME if per_frame else CIRCUIT_VITAL
     c.kind, c.bins, c.frames, c.fs_mhz, c.taps, c.taylor_order = kind, bins, frames, fs_mhz, taps, taylor_order
     c.num_bands = 2

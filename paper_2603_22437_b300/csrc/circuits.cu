@@ -441,7 +441,8 @@ Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
         for (int i = 0; (1 << i) < std::max(p->span[0], p->span[1]); i++) rot(p->r_c << i);
         rot((Fp / 2) * p->r_c);
         rot(1);
-        p->n_in = 4 * p->groups;
+        if (cfg.complex_slots) rots.insert(MMFHE_ROT_CONJ);
+        p->n_in = (cfg.complex_slots ? 2 : 4) * p->groups;
         p->out_levels = {lv_side - 1, lv_side - 1, lv_final - 1, lv_final - 1, lv_final - 1, lv_final - 1};
     }
     rots.erase(0);
@@ -510,7 +511,9 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
         // band b in bin slot b; diag_d[row] = M[row, row + d]
         const int d = (int)k.index;
         for (int b = 0; b < 2; b++) {
-            const double gain = cfg.dft_gain[b] * (cfg.taylor_order == 3 ? 1.0 / 3.0 : 1.0);
+            // the phase signal carries 3 dphi (third order); with complex slots 6i dphi or 2i dphi
+            const double gain = cfg.complex_slots ? cfg.dft_gain[b] / (cfg.taylor_order == 3 ? 6.0 : 2.0)
+                                                  : cfg.dft_gain[b] * (cfg.taylor_order == 3 ? 1.0 / 3.0 : 1.0);
             for (int kk : p.bands[b]) {
                 for (int part = 0; part < 2; part++) {
                     const int row = kk + part * (Fp / 2);
@@ -642,7 +645,130 @@ static std::vector<CtB> run_fir_dft(Context &c, const Plan &p, const Keys &k, st
     return out;
 }
 
+// The vital chain on complex slots (z = Re + i Im per group and stream):
+// |z|^2 = z conj(z); K4 gives Z = I + i Q; one FIR product per band filters
+// both parts; K7 w = Z conj(Z at t-1) = x + i y, the phase signal
+// w^3 - conj(w^3) = 2i Im(w^3) (third order) or w - conj(w) (first); K3,
+// |X|^2, sharpening and the sums as in the split chain.
+static std::vector<CtB> run_vital_complex(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in,
+                                          cudaStream_t st) {
+    const int G = p.groups, Rc = p.r_c, Fp = p.f_pad;
+    const int B = in[0].B;
+    auto abs2 = [&](const CtB &z) {
+        CtB zc = rotate(c, k, z, MMFHE_ROT_CONJ, st);
+        TensorB t = tensor_new(c, B, z.level);
+        tensor_acc(c, t, z, zc, 1, true, st);
+        return rescale(c, relin(c, k, t, st), st);
+    };
+    // ---- side branch: K1, K2 ----
+    std::vector<CtB> w;
+    for (int g = 0; g < G; g++) {
+        CtB E = rotsum(c, k, abs2(in[g]), Rc, (uint32_t)Fp, st);
+        w.push_back(rescale(c, square_sum(c, k, {&E}, st), st));
+    }
+    const PtDev &idx0 = plan_const(p, MMFHE_CONST_IDX, 0, 0);
+    CtB num = ct_new(c, B, w[0].level, w[0].scale * idx0.scale);
+    CtB den = ct_new(c, B, w[0].level, w[0].scale * idx0.scale);
+    for (int g = 0; g < G; g++) {
+        ct_mul_plain(c, num, w[g], plan_const(p, MMFHE_CONST_IDX, 0, g), g > 0, st);
+        ct_mul_plain(c, den, w[g], plan_const(p, MMFHE_CONST_ONE, 0, g), g > 0, st);
+    }
+    w.clear();
+    CtB num_r = rotsum(c, k, rescale(c, num, st), 1, (uint32_t)Rc, st);
+    CtB den_r = rotsum(c, k, rescale(c, den, st), 1, (uint32_t)Rc, st);
+    // ---- K4: Z = sum_r m z ----
+    std::vector<CtB> m;
+    for (int g = 0; g < G; g++) {
+        CtB pp = abs2(in[G + g]);
+        m.push_back(rescale(c, square_sum(c, k, {&pp}, st), st));
+    }
+    const int lv = m[0].level;
+    TensorB t4 = tensor_new(c, B, lv);
+    for (int g = 0; g < G; g++) {
+        CtB x = ct_drop(c, in[G + g], lv, st);
+        tensor_acc(c, t4, m[g], x, 1, g == 0, st);
+    }
+    m.clear();
+    CtB Z = rotsum(c, k, rescale(c, relin(c, k, t4, st), st), 1, (uint32_t)Rc, st);
+    // ---- K5: both bands in one product (RR in bin slot 0, HR in slot 1) ----
+    std::vector<int> idx_fir(p.n1_fir);
+    std::vector<int32_t> rot_fir;
+    for (int sft = 0; sft < 2; sft++)
+        for (int b = 0; b < p.n1_fir; b++) rot_fir.push_back(-b * Rc - sft);
+    for (int b = 0; b < p.n1_fir; b++) idx_fir[b] = b;
+    CtB Zf;
+    {
+        std::vector<CtB> hs = rotate_hoisted(c, k, Z, rot_fir, st);
+        std::vector<CtB> b0(std::make_move_iterator(hs.begin()), std::make_move_iterator(hs.begin() + p.n1_fir));
+        std::vector<CtB> b1(std::make_move_iterator(hs.begin() + p.n1_fir), std::make_move_iterator(hs.end()));
+        BsgsTerm t[2];
+        for (int band = 0; band < 2; band++) {
+            t[band].baby = band == 0 ? &b0 : &b1;
+            t[band].baby_idx = idx_fir;
+            for (uint32_t kk = 0; kk < p.cfg.taps; kk++)
+                t[band].diags.push_back({(int)kk, &plan_const(p, MMFHE_CONST_FIR, band, kk)});
+        }
+        Zf = rescale(c, bsgs(c, k, {t[0], t[1]}, p.n1_fir, -Rc, st), st);
+    }
+    // ---- K7: w = Zf conj(Zf at t-1) ----
+    CtB zpc = rotate(c, k, rotate(c, k, Zf, -Rc, st), MMFHE_ROT_CONJ, st);
+    TensorB tw = tensor_new(c, B, Zf.level);
+    tensor_acc(c, tw, Zf, zpc, 1, true, st);
+    CtB wc = rescale(c, relin(c, k, tw, st), st);
+    CtB dphi;
+    {
+        CtB top;
+        if (p.cfg.taylor_order == 3) {
+            CtB w2 = rescale(c, square_sum(c, k, {&wc}, st), st);
+            CtB wd = ct_drop(c, wc, w2.level, st);
+            TensorB t3 = tensor_new(c, B, w2.level);
+            tensor_acc(c, t3, wd, w2, 1, true, st);
+            top = rescale(c, relin(c, k, t3, st), st);
+        } else {
+            top = std::move(wc);
+        }
+        CtB topc = rotate(c, k, top, MMFHE_ROT_CONJ, st);
+        dphi = ct_new(c, B, top.level, top.scale);
+        ct_addsub(c, dphi, top, topc, true, st);
+    }
+    // ---- K3, |X|^2 (negated by the i), sharpen, weighted frequency average ----
+    std::set<int> need;
+    for (int d : p.dft_deltas[0]) need.insert(d % p.n1_dft);
+    std::vector<int> idx(need.begin(), need.end());
+    std::vector<int32_t> rr;
+    for (int b : idx) rr.push_back(b * Rc);
+    std::vector<CtB> hs = rotate_hoisted(c, k, dphi, rr, st);
+    BsgsTerm td;
+    td.baby = &hs;
+    td.baby_idx = idx;
+    for (int d : p.dft_deltas[0]) td.diags.push_back({d, &plan_const(p, MMFHE_CONST_DRE, 0, d)});
+    CtB X = rescale(c, bsgs(c, k, {td}, p.n1_dft, Rc, st), st);
+    hs.clear();
+    CtB pw = rescale(c, square_sum(c, k, {&X}, st), st);
+    CtB merged = rotate_add(c, k, pw, (p.f_pad / 2) * Rc, pw, st);
+    CtB S = rescale(c, square_sum(c, k, {&merged}, st), st);
+    const uint32_t span = (uint32_t)std::max(p.span[0], p.span[1]);
+    CtB sums[2];
+    for (int i2 = 0; i2 < 2; i2++) {
+        const PtDev &pt = plan_const(p, i2 == 0 ? MMFHE_CONST_FW : MMFHE_CONST_FONE, 0, 0);
+        CtB tt = ct_new(c, B, S.level, S.scale * pt.scale);
+        ct_mul_plain(c, tt, S, pt, false, st);
+        sums[i2] = rotsum(c, k, rescale(c, tt, st), Rc, span, st);
+    }
+    std::vector<CtB> out;
+    out.push_back(std::move(num_r));
+    out.push_back(std::move(den_r));
+    CtB hr_num = rotate(c, k, sums[0], 1, st);
+    CtB hr_den = rotate(c, k, sums[1], 1, st);
+    out.push_back(std::move(sums[0]));
+    out.push_back(std::move(sums[1]));
+    out.push_back(std::move(hr_num));
+    out.push_back(std::move(hr_den));
+    return out;
+}
+
 static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st) {
+    if (p.cfg.complex_slots) return run_vital_complex(c, p, k, in, st);
     const int G = p.groups, Rc = p.r_c, Fp = p.f_pad;
     const int B = in[0].B;
     // ---- side branch: K1, K2 ----

@@ -138,3 +138,65 @@ def test_vital_full_batch_in_bench_launch_configuration(vital):
         got = d_out[w].cpu().numpy().view(np.uint64)
         assert np.array_equal(got, ref0 if w % 2 == 0 else outs2[1]), "window %d (tiles %s)" % (w, t)
     ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"], saved["conv_rows"])
+
+
+@pytest.fixture(scope="module")
+def vital_complex():
+    """The same window with complex-slot packing (stream 1 then stream 2, one
+    Re + i Im ciphertext per group), its own keys (the conjugation key)."""
+    import paper_2603_22437_b300 as M
+    P = pm.vital_params()
+    cfg = cc.VitalConfig(bins=256, taylor_order=3, complex_slots=True)
+    circ = cc.VitalCircuit(P, cfg)
+    rots = circ.rotations()
+    kd = synth.KeyDraws(22, P.n, P.q, P.p, P.dnum, rots)
+    sk = ck.SecretKey(P, kd.secret)
+    pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
+    rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
+    gks = {ck.key_id(P, k): ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
+    del kd
+    consts = circ.constants()
+    win = synth.vital_window(1001, frames=200, bins=256, randomize_rates=True)
+    s1, s2 = plain.preprocess(win.z)
+    lay = circ.lay
+
+    def stream(x, seed):
+        v = lay.pack(x.real) + 1j * lay.pack(x.imag)
+        return [ck.encrypt(P, pk, ck.encode(P, v[c], P.scale, P.L), *synth.encryption_draws(seed + c, P.n))
+                for c in range(lay.groups)]
+
+    c1, c2 = stream(s1, 400), stream(s2, 500)
+    ref = circ.run(cc.Evaluator(P, rlk, gks), consts, c1, c2)
+    ctx = M.Context(lib_params(P))
+    keys = load_keys(ctx, P, rlk, gks)
+    plan = ctx.plan(M.vital_config(bins=256, taylor_order=3, complex_slots=True))
+    install_oracle_consts(plan, consts)
+    return dict(P=P, cfg=cfg, circ=circ, sk=sk, s=(s1, s2), ins=[window_words(c1 + c2)], ref=ref, ctx=ctx,
+                keys=keys, plan=plan)
+
+
+def test_complex_slot_vital_word_exact_and_decrypted(vital_complex):
+    """Complex-slot packing (half the input ciphertexts, 148 key switches
+    against 169): output words equal the oracle's; decrypted rates within
+    1e-3 bpm of the FP64 pipeline; the library's own constants to +-1."""
+    import paper_2603_22437_b300 as M
+    v = vital_complex
+    P, ctx, plan = v["P"], v["ctx"], v["plan"]
+    assert plan.rotations() == v["circ"].rotations() and plan.rotations()[0] == M.ROT_CONJ
+    n_in, n_out, lv = plan.io()
+    assert n_in == 8 and n_out == 6 and lv == [o.level for o in v["ref"]]
+    outs, lv = out_buffers(v, 1)
+    ctx.eval(plan, v["keys"], v["ins"], outs, vital=True)
+    got = split(P, outs[0], lv)
+    for o, (g, r) in enumerate(zip(got, v["ref"])):
+        assert np.array_equal(g, r.words()), "output %d" % o
+    dv = [ck.decrypt_decode(P, v["sk"], r)[0] for r in v["ref"]]
+    sb, mc = plain.side_branch(v["s"][0]), plain.main_chain(v["s"][1], cc.VitalConfig(bins=256, taylor_order=3))
+    assert abs(dv[0] / dv[1] - sb["num"] / sb["den"]) < 1e-6
+    for b in range(2):
+        bd = mc["bands"][b]
+        if bd["den"] > 1e-4:
+            assert abs(60 * dv[2 + 2 * b] / dv[3 + 2 * b] - bd["bpm"]) < 1e-3
+    lib = ctx.plan(M.vital_config(bins=256, taylor_order=3, complex_slots=True))
+    lib.encode_consts()
+    compare_plan_consts(plan, lib, P)
