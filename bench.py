@@ -70,6 +70,9 @@ def parse():
                     help="vital and gesture workloads: Re + i Im in one complex slot (half the input ciphertexts)")
     ap.add_argument("--tiles", default=None,
                     help="cols_width,rows_threads,keyip_windows,conv_rows: set the tile shapes instead of autotuning")
+    ap.add_argument("--keyip-fusion", action="store_true",
+                    help="form the key inner product inside the ModDown passes instead of storing it with its "
+                         "own kernel (ablation; same words, slower on B300)")
     args = ap.parse_args()
     if args.batch is None:
         args.batch = 16 if args.workload == "gesture" else 64
@@ -400,10 +403,13 @@ def ncu_traffic(kernel, batch, workload=None):
 
 def pick_tiles(ctx, args, batch):
     """Tile shapes: given (--tiles), defaults (--no-autotune) or autotuned."""
+    fused = 1 if args.keyip_fusion else 0
     if args.tiles:
-        ctx.set_tuning(*[int(v) for v in args.tiles.split(",")])
+        ctx.set_tuning(*[int(v) for v in args.tiles.split(",")], keyip_fused=fused)
         return ctx.tuning()
-    return ctx.tuning() if args.no_autotune else ctx.autotune(batch)
+    t = ctx.tuning() if args.no_autotune else ctx.autotune(batch)
+    ctx.set_tuning(t["ntt_cols_width"], t["ntt_rows_threads"], t["keyip_windows"], t["conv_rows"], fused)
+    return ctx.tuning()
 
 
 def roofline_of(prof, bf64_peak, bf32_peak, batch, mac_peak=None):

@@ -406,6 +406,11 @@ typedef struct mmfhe_tuning {
     float ntt_ms[4];             /* last autotune, ms: (8,128), (8,256), (16,128), (16,256) */
     float keyip_ms[4];           /* last autotune, ms: window groups 1, 2, 4, 8 */
     float conv_ms[3];            /* last autotune, ms: ModUp + ModDown with 1, 2, 4 rows per CTA */
+    uint32_t keyip_fused;        /* 0 (default): a key switch's inner-product words are stored by their own
+                                    kernel; 1: formed inside the ModDown passes that consume them (P rows in
+                                    the inverse NTT's load, Q rows in the combine) and never stored, which
+                                    measures slower on B300.  Same words either way.  The autotuner leaves
+                                    it unchanged. */
 } mmfhe_tuning;
 mmfhe_status mmfhe_autotune(mmfhe_ctx *ctx, uint32_t batch, uint32_t level, mmfhe_tuning *out);
 mmfhe_status mmfhe_tuning_get(const mmfhe_ctx *ctx, mmfhe_tuning *out);

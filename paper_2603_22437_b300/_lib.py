@@ -64,7 +64,7 @@ class KernelStat(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("ntt_cols_width", ctypes.c_uint32), ("ntt_rows_threads", ctypes.c_uint32),
                 ("keyip_windows", ctypes.c_uint32), ("conv_rows", ctypes.c_uint32), ("ntt_ms", ctypes.c_float * 4),
-                ("keyip_ms", ctypes.c_float * 4), ("conv_ms", ctypes.c_float * 3)]
+                ("keyip_ms", ctypes.c_float * 4), ("conv_ms", ctypes.c_float * 3), ("keyip_fused", ctypes.c_uint32)]
 
 
 class BatcherConfig(ctypes.Structure):

@@ -156,6 +156,30 @@ CtB keyswitch_moddown(Context &c, const DigitsB &dg, const KeyPtrs &key, uint32_
     const int level = dg.level, B = dg.B, nl = level + 1, nre = level + 1 + c.num_p, K = c.num_p;
     if (key.n != 1 && key.n != B) throw Error(MMFHE_ERR_BAD_ARG, "one switching key per window or one for all");
     if (plus && (plus->level != level || plus->B != B)) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "add: operand levels differ");
+    if (c.tune.keyip_fused) {
+        // the inner product's words are formed where they are consumed: its P rows in the
+        // load of z's inverse NTT, its Q rows in the combine (never stored)
+        KeyipArgs ka{};
+        ka.digits = dg.buf.get();
+        ka.own = dg.own;
+        ka.own_stride = dg.own_stride;
+        ka.key = key;
+        ka.beta = dg.beta;
+        ka.alpha = c.alpha;
+        ka.nre = nre;
+        ka.level = level;
+        ka.key_rows = c.num_q + c.num_p;
+        ka.L1 = c.num_q;
+        ka.w0 = 0;
+        ka.galois = galois;
+        Buf z(c.pool.get(), (size_t)B * 2 * K * c.n);
+        launch_keyip_p_inv(c, z.get(), ka, B, level, st);
+        Buf v(c.pool.get(), (size_t)B * 2 * nl * c.n);
+        CtB out = ct_new(c, B, level, scale);
+        CombineArgs a{out.ptr(), nullptr, add0, add1, add_stride_words, galois, plus ? plus->ptr() : nullptr};
+        launch_moddown_ntt(c, v.get(), z.get(), a, B, level, st, &ka);
+        return out;
+    }
     Buf u(c.pool.get(), (size_t)B * 2 * nre * c.n);
     k_launch_keyip(c, u.get(), dg.buf.get(), dg.own, dg.own_stride, 0, key, B, level, dg.beta, galois, st);
     // z = [u_P Phat^-1]_P in coefficient form, [B*2][K][N]

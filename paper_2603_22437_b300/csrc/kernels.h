@@ -85,14 +85,35 @@ void launch_modup_ntt(Context &c, uint64_t *digits, const uint64_t *y, int B, in
 // (add_h and plus optional; perm = the Galois map of `galois`).
 struct CombineArgs {
     uint64_t *out;
-    const uint64_t *u;            // [B][2][level+1+K][N]
+    const uint64_t *u;            // [B][2][level+1+K][N]; null: computed in place from KeyipArgs
     const uint64_t *add0, *add1;  // window stride add_stride words
     size_t add_stride;
     uint32_t galois;
     const uint64_t *plus;         // [B][2][level+1][N]
 };
+
+// Operands of the key inner product when its output words are formed inside
+// the ModDown passes that consume them, instead of being stored: word (b, h,
+// t, x) = redc(sum_j digit_j[b][t][perm(x)] * key_b[j][h][t][x]), the same
+// 128-bit sum and single Montgomery reduction as k_launch_keyip, so the words
+// are identical.  Window b's digits sit at digits + b * beta * nre * N, its
+// own-prime rows at own + b * own_stride; w0 is the batch index of the
+// launch's first window (key lookup and digit offsets).
+struct KeyipArgs {
+    const uint64_t *digits;
+    const uint64_t *own;
+    size_t own_stride;
+    KeyPtrs key;
+    int beta, alpha, nre, level, key_rows, L1;
+    int w0;
+    uint32_t galois;
+};
 void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, int B, int level,
-                        cudaStream_t st);
+                        cudaStream_t st, const KeyipArgs *ka = nullptr);
+// The P rows of the key inner product, formed in the load of the inverse
+// NTT's contiguous pass, then the strided pass: z[bh][k] =
+// [u_{p_k} Phat_k^-1]_{p_k} in coefficient form ([B*2][K][N]).
+void launch_keyip_p_inv(Context &c, uint64_t *z, const KeyipArgs &ka, int B, int level, cudaStream_t st);
 
 // Fused sum of products: out (+)= sum_k ct_k (.) pt_k over a batch of
 // ciphertexts at one level (each ct_k [B][2][l+1][N], each pt_k [l+1][N] in

@@ -206,8 +206,36 @@ void launch_modup_ntt(Context &c, uint64_t *digits, const uint64_t *y, int B, in
     CK(cudaGetLastError());
 }
 
+void launch_keyip_p_inv(Context &c, uint64_t *z, const KeyipArgs &ka, int B, int level, cudaStream_t st) {
+    const int K = c.num_p;
+    if (B == 0) return;
+    std::vector<int> pids(K);
+    for (int k = 0; k < K; k++) pids[k] = c.num_q + k;
+    RowMap mz = make_map(K, K, pids), ms = mz;
+    set_active(ms, mz);
+    const size_t chunk = 65535 / (2 * (size_t)K);   // windows per launch
+    const double row = (double)c.n * 8;
+    for (size_t w0 = 0; w0 < (size_t)B; w0 += chunk) {
+        const size_t nw = std::min(chunk, (size_t)B - w0);
+        const size_t nr = nw * 2 * K;
+        KeyipArgs kc = ka;
+        kc.w0 = ka.w0 + (int)w0;
+        // reads each window's beta digit rows of the P primes and the keys' rows (once per
+        // launch when shared), writes every z row; the strided pass reads and writes z
+        const double kn = ka.key.n == 1 ? 1.0 : (double)nw;
+        const double br_ = row * ((double)nr + (double)nw * ka.beta * K + kn * ka.beta * 2.0 * K);
+        const double bc_ = 2.0 * row * (double)nr;
+#define MMFHE_KPI_CALL(L)                                                                                         \
+    keyip_p_inv_launch_##L(c, z + ((w0 * 2 * K) << c.logn), kc, mz, nr, br_, bc_, c.lv[level].d_ks_scale,         \
+                           c.lv[level].d_ks_scale_sh, st)
+        MMFHE_LOGN_DISPATCH(c.logn, MMFHE_KPI_CALL)
+#undef MMFHE_KPI_CALL
+    }
+    CK(cudaGetLastError());
+}
+
 void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, int B, int level,
-                        cudaStream_t st) {
+                        cudaStream_t st, const KeyipArgs *ka) {
     const int nl = level + 1, nre = nl + c.num_p, K = c.num_p;
     if (B == 0) return;
     std::vector<int> pids(nl);
@@ -223,16 +251,25 @@ void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const Com
         const size_t nr = nb * nact;
         CombineArgs ab = a;
         ab.out = a.out + ((b0 * nl) << c.logn);
-        ab.u = a.u + ((b0 * nre) << c.logn);
+        if (ab.u) ab.u = a.u + ((b0 * nre) << c.logn);
         if (ab.add0) ab.add0 += (b0 / 2) * a.add_stride;
         if (ab.add1) ab.add1 += (b0 / 2) * a.add_stride;
         if (ab.plus) ab.plus += (b0 * nl) << c.logn;
+        KeyipArgs kc{};
+        if (ka) {
+            kc = *ka;
+            kc.w0 = ka->w0 + (int)(b0 / 2);
+        }
         const double row = (double)c.n * 8;
         const double bc_ = row * ((double)nr + (double)nb * K);
-        const double br_ = row * ((double)nr * (3 + (ab.plus ? 1 : 0)) + (ab.add0 ? nr / 2.0 : 0) + (ab.add1 ? nr / 2.0 : 0));
+        // v read and out written per row; u read, or the key inner product's digit rows
+        // (once per window) and key rows (once per launch when shared)
+        double ub = (double)nr;
+        if (ka) ub = (double)(nb / 2) * ka->beta * nl + (ka->key.n == 1 ? 1.0 : nb / 2.0) * ka->beta * 2.0 * nl;
+        const double br_ = row * ((double)nr * (2 + (ab.plus ? 1 : 0)) + ub + (ab.add0 ? nr / 2.0 : 0) + (ab.add1 ? nr / 2.0 : 0));
 #define MMFHE_MODDOWN_CALL(L)                                                                                   \
     moddown_launch_##L(c, vtmp + ((b0 * nl) << c.logn), z + ((b0 * K) << c.logn), mv, gr, nb, ab, nre, bc_, br_,   \
-                       (double)nr * c.n * (K + 1), st)
+                       (double)nr * c.n * (K + 1), ka ? &kc : nullptr, st)
         MMFHE_LOGN_DISPATCH(c.logn, MMFHE_MODDOWN_CALL)
 #undef MMFHE_MODDOWN_CALL
     }

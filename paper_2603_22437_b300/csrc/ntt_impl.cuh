@@ -369,6 +369,58 @@ __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::CO
     cols_finish_group<LOGN, CW, RG>(tiles, nr, cc, dst, md, gr, g, blk, lo0, tw);
 }
 
+// Key inner product word of window w (relative to a.w0), output part h,
+// extended row t, position x: the beta 128-bit products (keys in Montgomery
+// form) summed and reduced once, exactly as k_launch_keyip stores it.
+template <int KB>
+__device__ __forceinline__ uint64_t keyip_word(const KeyipArgs &a, uint32_t w, int h, int t, uint32_t x, int logn,
+                                              uint64_t q, uint64_t qinv) {
+    const uint32_t px = a.galois == 1 ? x : mm::galois_perm(x, a.galois, logn);
+    const int krow = t <= a.level ? t : a.L1 + (t - a.level - 1);
+    const int jown = t <= a.level ? t / a.alpha : -1;
+    const size_t wa = (size_t)a.w0 + w;
+    const uint64_t *K = a.key.k[a.key.n == 1 ? 0 : wa];
+    const uint64_t *D = a.digits + ((wa * a.beta * a.nre + t) << logn) + px;
+    uint64_t hi = 0, lo = 0;
+#pragma unroll
+    for (int j = 0; j < KB; j++) {
+        if (j >= a.beta) break;
+        const uint64_t kv = K[((((size_t)j * 2 + h) * a.key_rows + krow) << logn) + x];
+        const uint64_t d = j == jown ? a.own[wa * a.own_stride + ((size_t)t << logn) + px]
+                                     : D[((size_t)j * a.nre) << logn];
+        mm::mac128(hi, lo, d, kv);
+    }
+    return mm::redc(hi, lo, q, qinv);
+}
+
+// Inverse contiguous pass over the P rows of the key inner product, whose
+// words are formed in the load: row r = (w * 2 + h) * K + k of z holds
+// part h of window w at special prime k.
+template <int LOGN, int RT, int KB>
+__global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16, RT>::ROWS_MINB)
+    k_ntt_rows_inv_keyip(KeyipArgs a, int K, int pid_p0, uint64_t *z, ModTab mt, Twiddles tw) {
+    using Gm = Geo<LOGN, 16, RT>;
+    __shared__ uint64_t sm[Gm::ROWS * Gm::RS];
+    const uint32_t r = blockIdx.y, blk = r / (uint32_t)K;
+    const int k = (int)(r % (uint32_t)K), t = a.level + 1 + k;
+    const uint32_t pid = (uint32_t)(pid_p0 + k);
+    const int hi0 = blockIdx.x * Gm::ROWS;
+    const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
+    const size_t base = (size_t)hi0 * Gm::T1;
+    MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
+        int rr = e / Gm::T1, l = e % Gm::T1;
+        sm[rr * Gm::RS + l + (l >> 4)] = keyip_word<KB>(a, blk >> 1, (int)(blk & 1), t, (uint32_t)(base + e), LOGN, q, qinv);
+    }
+    __syncthreads();
+    rows_rounds<LOGN, false, RT>(sm, hi0, q, pid, tw);
+    __syncthreads();
+    uint64_t *D = z + ((size_t)r << LOGN);
+    MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
+        int r2 = e / Gm::T1, l = e % Gm::T1;
+        D[base + e] = sm[r2 * Gm::RS + l + (l >> 4)];
+    }
+}
+
 // Fused ModDown strided pass on a group of rows (blk = window * 2 + h, p = i):
 // each starts from the centered conversion
 // v_i = sum_k z_k Phat_k + c (-P) mod q_i, c = #{k : z_k > p_k / 2}, in one
@@ -402,12 +454,13 @@ __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::CO
 
 // Fused ModDown contiguous pass: forward stages on v (rows blk = window * 2 + h,
 // p = i, in place on vtmp) and the combine
-//   out = (u - v) P^-1 + add_h[perm(x)] + plus  (mod q_i).
-template <int LOGN, int RT>
+//   out = (u - v) P^-1 + add_h[perm(x)] + plus  (mod q_i),
+// u read from a.u (KB = 0) or formed from the key inner product's operands.
+template <int LOGN, int RT, int KB>
 __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16, RT>::ROWS_MINB)
     k_ntt_rows_combine(const uint64_t *__restrict__ v, RowMap mv, CombineArgs a, int nre,
                        const uint64_t *__restrict__ Pinv, const uint64_t *__restrict__ Pinv_sh, ModTab mt,
-                       Twiddles tw) {
+                       Twiddles tw, KeyipArgs ka) {
     using Gm = Geo<LOGN, 16, RT>;
     __shared__ uint64_t sm[Gm::ROWS * Gm::RS];
     uint32_t blk, p;
@@ -418,14 +471,14 @@ __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16,
     const int hi0 = blockIdx.x * Gm::ROWS;
     const uint64_t q = mt.q[pid];
     const size_t base = (size_t)hi0 * Gm::T1;
-    const uint64_t *U = a.u + (((size_t)blk * nre + p) << LOGN);
+    const uint64_t *U = KB ? nullptr : a.u + (((size_t)blk * nre + p) << LOGN);
     const uint64_t *A = (blk & 1) ? a.add1 : a.add0;
     if (A) A += (size_t)(blk >> 1) * a.add_stride + ((size_t)p << LOGN);
     const uint64_t *Pl = a.plus ? a.plus + (((size_t)blk * nl + p) << LOGN) : nullptr;
     if (threadIdx.x == 0) {
         // the epilogue's contiguous operands travel to L2 while the stages run
         constexpr uint32_t seg = Gm::ROWS * Gm::T1 * 8;
-        l2_prefetch(U + base, seg);
+        if (!KB) l2_prefetch(U + base, seg);
         if (Pl) l2_prefetch(Pl + base, seg);
         if (A && a.galois == 1) l2_prefetch(A + base, seg);
     }
@@ -436,13 +489,14 @@ __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16,
     __syncthreads();
     rows_rounds<LOGN, true, RT>(sm, hi0, q, pid, tw);
     __syncthreads();
-    const uint64_t pi = Pinv[pid], pis = Pinv_sh[pid];
+    const uint64_t pi = Pinv[pid], pis = Pinv_sh[pid], qinv = mt.qinv[pid];
     uint64_t *O = a.out + (((size_t)blk * nl + p) << LOGN);
     MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
         int r2 = e / Gm::T1, l = e % Gm::T1;
         const uint32_t x = (uint32_t)(base + e);
         const uint64_t vv = mm::reduce_4q(sm[r2 * Gm::RS + l + (l >> 4)], q);
-        uint64_t res = mm::mul_shoup(mm::sub_mod(U[x], vv, q), pi, pis, q);
+        const uint64_t uu = KB ? keyip_word<KB ? KB : 1>(ka, blk >> 1, (int)(blk & 1), (int)p, x, LOGN, q, qinv) : U[x];
+        uint64_t res = mm::mul_shoup(mm::sub_mod(uu, vv, q), pi, pis, q);
         if (A) res = mm::add_mod(res, A[a.galois == 1 ? x : mm::galois_perm(x, a.galois, LOGN)], q);
         if (Pl) res = mm::add_mod(res, Pl[x], q);
         O[x] = res;
@@ -563,23 +617,58 @@ void moddown_cols_rg(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap
 
 template <int LOGN, int RT>
 void combine_rows_pass(Context &c, uint64_t *vtmp, const RowMap &mv, size_t nr, const CombineArgs &a, int nre,
-                       double bytes, cudaStream_t st) {
+                       double bytes, const KeyipArgs *ka, cudaStream_t st) {
     using Gm = Geo<LOGN, 16, RT>;
     dim3 g(Gm::H / Gm::ROWS, (unsigned)nr), b(Gm::ROWS_THREADS);
     kernel_begin(c, st);
-    k_ntt_rows_combine<LOGN, RT><<<g, b, 0, st>>>(vtmp, mv, a, nre, c.d_dn_Pinv, c.d_dn_Pinv_sh, c.mods, c.tw);
-    kernel_end(c, "ntt_combine_rows", g, b, bytes, st, bf_rows<LOGN>(nr));
+    if (!ka) {
+        k_ntt_rows_combine<LOGN, RT, 0><<<g, b, 0, st>>>(vtmp, mv, a, nre, c.d_dn_Pinv, c.d_dn_Pinv_sh, c.mods, c.tw,
+                                                         KeyipArgs{});
+        kernel_end(c, "ntt_combine_rows", g, b, bytes, st, bf_rows<LOGN>(nr));
+        return;
+    }
+    if (ka->beta <= 4)
+        k_ntt_rows_combine<LOGN, RT, 4><<<g, b, 0, st>>>(vtmp, mv, a, nre, c.d_dn_Pinv, c.d_dn_Pinv_sh, c.mods, c.tw, *ka);
+    else
+        k_ntt_rows_combine<LOGN, RT, MAX_DNUM><<<g, b, 0, st>>>(vtmp, mv, a, nre, c.d_dn_Pinv, c.d_dn_Pinv_sh, c.mods,
+                                                                c.tw, *ka);
+    kernel_end(c, "ntt_combine_keyip_rows", g, b, bytes, st, bf_rows<LOGN>(nr), (double)nr * c.n * ka->beta);
 }
 
 template <int LOGN>
 void moddown_launch_t(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr,
                       size_t nblk, const CombineArgs &a, int nre, double bytes_cols, double bytes_rows,
-                      double macs, cudaStream_t st) {
+                      double macs, const KeyipArgs *ka, cudaStream_t st) {
     const size_t nr = nblk * mv.nact;
     if (c.tune.cols_w == 8) moddown_cols_rg<LOGN, 8>(c, vtmp, z, mv, gr, nblk, bytes_cols, nr, macs, st);
     else moddown_cols_rg<LOGN, 16>(c, vtmp, z, mv, gr, nblk, bytes_cols, nr, macs, st);
-    if (c.tune.rows_t == 128) combine_rows_pass<LOGN, 128>(c, vtmp, mv, nr, a, nre, bytes_rows, st);
-    else combine_rows_pass<LOGN, 256>(c, vtmp, mv, nr, a, nre, bytes_rows, st);
+    if (c.tune.rows_t == 128) combine_rows_pass<LOGN, 128>(c, vtmp, mv, nr, a, nre, bytes_rows, ka, st);
+    else combine_rows_pass<LOGN, 256>(c, vtmp, mv, nr, a, nre, bytes_rows, ka, st);
+}
+
+template <int LOGN, int RT>
+void inv_keyip_rows_pass(Context &c, uint64_t *z, const KeyipArgs &ka, size_t nr, double bytes, cudaStream_t st) {
+    using Gm = Geo<LOGN, 16, RT>;
+    dim3 g(Gm::H / Gm::ROWS, (unsigned)nr), b(Gm::ROWS_THREADS);
+    kernel_begin(c, st);
+    if (ka.beta <= 4)
+        k_ntt_rows_inv_keyip<LOGN, RT, 4><<<g, b, 0, st>>>(ka, c.num_p, c.num_q, z, c.mods, c.tw);
+    else
+        k_ntt_rows_inv_keyip<LOGN, RT, MAX_DNUM><<<g, b, 0, st>>>(ka, c.num_p, c.num_q, z, c.mods, c.tw);
+    kernel_end(c, "ntt_inv_keyip_rows", g, b, bytes, st, bf_rows<LOGN>(nr), (double)nr * c.n * ka.beta);
+}
+
+// The P rows of the key inner product into z ([rows of (window, h)][K][N]):
+// the contiguous inverse pass forming them, then the strided inverse pass
+// with the factor oscale[pid].
+template <int LOGN>
+void keyip_p_inv_launch_t(Context &c, uint64_t *z, const KeyipArgs &ka, const RowMap &mz, size_t nr,
+                          double bytes_rows, double bytes_cols, const uint64_t *os, const uint64_t *os_sh,
+                          cudaStream_t st) {
+    if (c.tune.rows_t == 128) inv_keyip_rows_pass<LOGN, 128>(c, z, ka, nr, bytes_rows, st);
+    else inv_keyip_rows_pass<LOGN, 256>(c, z, ka, nr, bytes_rows, st);
+    if (c.tune.cols_w == 8) cols_pass<LOGN, 8, false>(c, z, mz, z, mz, nr, bytes_cols, os, os_sh, st);
+    else cols_pass<LOGN, 16, false>(c, z, mz, z, mz, nr, bytes_cols, os, os_sh, st);
 }
 
 }  // namespace

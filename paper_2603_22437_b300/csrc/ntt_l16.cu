@@ -17,8 +17,14 @@ void modup_launch_16(Context &c, uint64_t *digits, const uint64_t *y, const RowM
 
 void moddown_launch_16(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr,
                        size_t nblk, const CombineArgs &a, int nre, double bytes_cols, double bytes_rows,
-                       double macs, cudaStream_t st) {
-    moddown_launch_t<16>(c, vtmp, z, mv, gr, nblk, a, nre, bytes_cols, bytes_rows, macs, st);
+                       double macs, const KeyipArgs *ka, cudaStream_t st) {
+    moddown_launch_t<16>(c, vtmp, z, mv, gr, nblk, a, nre, bytes_cols, bytes_rows, macs, ka, st);
+}
+
+void keyip_p_inv_launch_16(Context &c, uint64_t *z, const KeyipArgs &ka, const RowMap &mz, size_t nr,
+                          double bytes_rows, double bytes_cols, const uint64_t *os, const uint64_t *os_sh,
+                          cudaStream_t st) {
+    keyip_p_inv_launch_t<16>(c, z, ka, mz, nr, bytes_rows, bytes_cols, os, os_sh, st);
 }
 
 }  // namespace mmfhe

@@ -16,7 +16,10 @@ namespace mmfhe {
                           double bytes_rows, double macs, cudaStream_t st);                                     \
     void moddown_launch_##L(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr, \
                             size_t nblk, const CombineArgs &a, int nre, double bytes_cols, double bytes_rows,  \
-                            double macs, cudaStream_t st);
+                            double macs, const KeyipArgs *ka, cudaStream_t st);                                 \
+    void keyip_p_inv_launch_##L(Context &c, uint64_t *z, const KeyipArgs &ka, const RowMap &mz, size_t nr,      \
+                                double bytes_rows, double bytes_cols, const uint64_t *os, const uint64_t *os_sh, \
+                                cudaStream_t st);
 MMFHE_NTT_ENTRY_DECL(10)
 MMFHE_NTT_ENTRY_DECL(11)
 MMFHE_NTT_ENTRY_DECL(12)

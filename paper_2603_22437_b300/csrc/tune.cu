@@ -154,6 +154,7 @@ void to_abi(const Tune &t, mmfhe_tuning *out) {
     std::copy(t.keyip_ms, t.keyip_ms + 4, out->keyip_ms);
     out->conv_rows = (uint32_t)t.conv_rows;
     std::copy(t.conv_ms, t.conv_ms + 3, out->conv_ms);
+    out->keyip_fused = (uint32_t)t.keyip_fused;
 }
 
 }  // namespace
@@ -187,8 +188,9 @@ mmfhe_status mmfhe_tuning_set(mmfhe_ctx *ctx, const mmfhe_tuning *in) {
     Context *c = ctx->c;
     const uint32_t w = in->ntt_cols_width, r = in->ntt_rows_threads, k = in->keyip_windows, g = in->conv_rows;
     if ((w != 8 && w != 16) || (r != 128 && r != 256) || (k != 1 && k != 2 && k != 4 && k != 8) ||
-        (g != 1 && g != 2 && g != 4))
+        (g != 1 && g != 2 && g != 4) || in->keyip_fused > 1)
         return tfail(c, MMFHE_ERR_BAD_ARG, "unsupported tile shape");
+    c->tune.keyip_fused = (int)in->keyip_fused;
     c->tune.conv_rows = (int)g;
     c->tune.cols_w = (int)w;
     c->tune.rows_t = (int)r;

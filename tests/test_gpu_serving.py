@@ -30,9 +30,17 @@ def user_keys(P, rots, seed):
     return one(), {r: one() for r in rots}
 
 
-def test_serving_mix_equals_alone(gsmall):
+@pytest.mark.parametrize("keyip_fused", [0, 1])
+def test_serving_mix_equals_alone(gsmall, keyip_fused):
+    """keyip_fused = 1: the batches mixing users form each window's key
+    inner product (its own key) inside the ModDown passes; the windows
+    evaluated alone use the stored inner product, so the two paths are
+    compared word for word."""
     import paper_2603_22437_b300 as M
     P, ctx = gsmall["P"], gsmall["ctx"]
+    saved = ctx.tuning()
+    ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"], saved["conv_rows"],
+                   keyip_fused)
     base = M.fir_dft_config(bins=40)
     plans = {}
     for F in (200, 150):
@@ -85,6 +93,7 @@ def test_serving_mix_equals_alone(gsmall):
     assert st["p99_ms"] >= st["p50_ms"] > 0 and 1 <= st["mean_batch"] <= 2
 
     # alone: each window by itself, with its own user's keys
+    ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"], saved["conv_rows"], 0)
     for u in users:
         relin, gal = users[u]
         k = ctx.keys(100 + u)
@@ -98,6 +107,8 @@ def test_serving_mix_equals_alone(gsmall):
             ctx.eval(plans[F], k, [x], [ref])
             assert np.array_equal(out, ref), "window %d (user %d, F=%d)" % (i, u, F)
         k.unload()
+    ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"], saved["conv_rows"],
+                   saved["keyip_fused"])
 
 
 def test_serving_vital_and_gesture_windows_concurrently(gsmall):
