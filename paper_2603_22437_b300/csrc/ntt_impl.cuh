@@ -119,6 +119,17 @@ struct Geo {
     static constexpr int ROWS_MINB = (1024 / ROWS_THREADS) < 32 ? (1024 / ROWS_THREADS) : 32;
 };
 
+// Tile staging by asynchronous 8-byte copies global -> shared: a thread's
+// 16 words are all in flight at once and hold no registers until the wait.
+__device__ __forceinline__ void cp_async8(uint64_t *smem_dst, const uint64_t *gsrc) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(s), "l"(gsrc) : "memory");
+}
+// Completes this thread's copies (the barrier that follows publishes them).
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 // Bulk prefetch of bytes (multiple of 16, 16-byte aligned start) into L2.
 __device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -203,7 +214,8 @@ __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::CO
     uint64_t *D = dst + row_at(md, blk, p, LOGN);
     const int lo0 = blockIdx.x * Gm::COLS;
     const uint64_t q = mt.q[pid];
-    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) sm[e] = S[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)];
+    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) cp_async8(&sm[e], &S[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)]);
+    cp_async_wait_all();
     __syncthreads();
     cols_rounds<LOGN, FWD, CW>(sm, q, pid, tw);
     __syncthreads();
@@ -233,8 +245,9 @@ __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16,
     const size_t base = (size_t)hi0 * Gm::T1;
     MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
         int rr = e / Gm::T1, l = e % Gm::T1;
-        sm[rr * Gm::RS + l + (l >> 4)] = S[base + e];
+        cp_async8(&sm[rr * Gm::RS + l + (l >> 4)], &S[base + e]);
     }
+    cp_async_wait_all();
     __syncthreads();
     rows_rounds<LOGN, FWD, RT>(sm, hi0, q, pid, tw);
     __syncthreads();
@@ -484,8 +497,9 @@ __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16,
     }
     MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
         int rr = e / Gm::T1, l = e % Gm::T1;
-        sm[rr * Gm::RS + l + (l >> 4)] = S[base + e];
+        cp_async8(&sm[rr * Gm::RS + l + (l >> 4)], &S[base + e]);
     }
+    cp_async_wait_all();
     __syncthreads();
     rows_rounds<LOGN, true, RT>(sm, hi0, q, pid, tw);
     __syncthreads();
