@@ -30,6 +30,7 @@ import hashlib
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -136,7 +137,9 @@ class ClockSampler:
     def __init__(self, device):
         self.device = device
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % device)
+        # the raw samples (the JSON line carries their summary); MMFHE_CLOCKS_DIR keeps them
+        self.path = os.path.join(os.environ.get("MMFHE_CLOCKS_DIR", tempfile.gettempdir()),
+                                 "mmfhe_clocks_rank%d.csv" % device)
 
     def start(self):
         try:
