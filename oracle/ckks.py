@@ -594,3 +594,81 @@ def rotate_hoisted(P, a, ks, gks):
         c0 = ring_automorphism(a.c0, g, pr)
         out.append(Ciphertext(ring_add(c0, moddown(P, u0, a.level), pr), moddown(P, u1, a.level), a.level, a.scale))
     return out
+
+
+# ----------------------------------------------------------------------------
+# double-hoisted BSGS product (Bossuat, Mouchet, Troncoso-Pastoriza and
+# Hubaux, Eurocrypt 2021, Sec. 4): the baby rotations, the inner sums and the
+# giant-step sum stay in the extended basis Q_level * P, scaled by P, and are
+# brought down to Q once
+# ----------------------------------------------------------------------------
+def encode_qp(P, z, scale, level):
+    """``encode`` with rows over Q_level * P (the extended basis): the same
+    integer coefficients, reduced mod every q_i and p_k."""
+    return Plaintext(ring_from_signed(encode_coeffs(P, z, scale), qp_primes(P, level)), level, scale)
+
+
+def times_p(P, c, level):
+    """P * c over Q_level * P for c over Q_level: rows P c_i mod q_i, and zero
+    rows mod every p_k (P is 0 there)."""
+    Pprod = _prod(P.p)
+    rows = [nat.mul_scalar(c[i], Pprod % q, q) for i, q in enumerate(q_primes(P, level))]
+    rows += [np.zeros(P.n, dtype=np.uint64) for _ in P.p]
+    return np.stack(rows)
+
+
+def bsgs_double_hoisted(P, a, diags, n1, stride, gks):
+    """sum_g Rot_{g n1 stride}( sum_b D'_{g,b} (.) Rot_{b stride}(a) ), not
+    rescaled, with every intermediate over Q_level * P:
+
+      baby b  = (P sigma_b(c0) + u0, u1), u = <sigma_b(ModUp(c1)), key of b stride>,
+                one ModUp of c1 shared by all babies, no ModDown;
+      inner g = sum_b D'_{g,b} (.) baby b, with D' encoded over Q_level * P;
+      giant g = inner g for g = 0; otherwise the c1 of inner g is brought to
+                Q by ModDown and switched with the key of g n1 stride (ModUp,
+                automorphism of the digits, inner product w), and
+                (sigma_g(c0 of inner g) + w0, w1) is the term;
+      result  = ModDown of each part of the sum of the terms.
+
+    ``diags``: {delta: Plaintext over Q_level * P (encode_qp)}, delta =
+    g n1 + b with 0 <= b < n1 (floor division), each pre-rotated by
+    -g n1 stride as in the single-hoisted product."""
+    level = a.level
+    prq, prqp = q_primes(P, level), qp_primes(P, level)
+    groups = {}
+    for d in sorted(diags):
+        groups.setdefault(d // n1, []).append(d)
+    need = sorted({d - (d // n1) * n1 for d in diags})
+    digits = modup(P, a.c1, level)
+    babies = {}
+    for b in need:
+        k = b * stride
+        if key_id(P, k) == 0:
+            babies[b] = (times_p(P, a.c0, level), times_p(P, a.c1, level))
+            continue
+        g = galois_element(P, k)
+        u0, u1 = inner_product(P, [ring_automorphism(y, g, prqp) for y in digits], gks[key_id(P, k)], level)
+        babies[b] = (ring_add(times_p(P, ring_automorphism(a.c0, g, prq), level), u0, prqp), u1)
+    acc0 = acc1 = None
+    scale = None
+    for gi in sorted(groups):
+        in0 = np.zeros((len(prqp), P.n), dtype=np.uint64)
+        in1 = np.zeros((len(prqp), P.n), dtype=np.uint64)
+        for d in groups[gi]:
+            pt = diags[d]
+            assert pt.level == level and pt.m.shape[0] == len(prqp)
+            b0, b1 = babies[d - gi * n1]
+            in0 = ring_add(in0, ring_mul(P, b0, pt.m, prqp), prqp)
+            in1 = ring_add(in1, ring_mul(P, b1, pt.m, prqp), prqp)
+            scale = a.scale * pt.scale
+        k = gi * n1 * stride
+        if key_id(P, k) == 0:
+            t0, t1 = in0, in1
+        else:
+            g = galois_element(P, k)
+            dg = modup(P, moddown(P, in1, level), level)
+            w0, w1 = inner_product(P, [ring_automorphism(y, g, prqp) for y in dg], gks[key_id(P, k)], level)
+            t0, t1 = ring_add(ring_automorphism(in0, g, prqp), w0, prqp), w1
+        acc0 = t0 if acc0 is None else ring_add(acc0, t0, prqp)
+        acc1 = t1 if acc1 is None else ring_add(acc1, t1, prqp)
+    return Ciphertext(moddown(P, acc0, level), moddown(P, acc1, level), level, scale)
