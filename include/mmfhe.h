@@ -102,6 +102,30 @@ const char *mmfhe_last_error(const mmfhe_ctx *ctx);
 mmfhe_status mmfhe_sync(mmfhe_ctx *ctx, void *stream, uint32_t timeout_ms);
 /* Number of kernels this library has launched on ctx since creation. */
 mmfhe_status mmfhe_launch_count(const mmfhe_ctx *ctx, uint64_t *out);
+/* Device memory held by this library on the context's device (no
+ * counterpart in the paper beyond its Table 5 "peak GPU memory"): every
+ * context, key set, plan, scratch pool, graph and staging buffer of the
+ * library on that device, summed over all contexts there.  peak_bytes is the
+ * high-water mark since the last mmfhe_mem_peak_reset (or since the library
+ * was loaded); allocations counts the library's cudaMalloc calls on the
+ * device; pool_bytes / pool_free_bytes are ctx's own scratch pool (cached
+ * blocks included) and the part of it not in use.  Errors: BAD_ARG. */
+typedef struct mmfhe_mem_stats {
+    uint64_t device_bytes;
+    uint64_t peak_bytes;
+    uint64_t allocations;
+    uint64_t pool_bytes;
+    uint64_t pool_free_bytes;
+} mmfhe_mem_stats;
+mmfhe_status mmfhe_mem_stats_get(const mmfhe_ctx *ctx, mmfhe_mem_stats *out);
+/* Restart the high-water mark at the current device_bytes. */
+mmfhe_status mmfhe_mem_peak_reset(mmfhe_ctx *ctx);
+/* Host-side fault injection for tests of the failure paths (no GPU fault is
+ * involved): after `after` more successful device allocations, every device
+ * allocation of the library's evaluator (pools, context tables, batcher
+ * staging) fails with OUT_OF_MEMORY without calling cudaMalloc, until the
+ * hook is disarmed with after < 0.  Process-wide; needs no device. */
+mmfhe_status mmfhe_debug_fail_allocations(int64_t after);
 /* Launch trace for auditing data obliviousness (Theorem 2: the execution
  * trace depends only on public parameters).  enable != 0 clears the trace and
  * starts recording one line "kernel grid(x,y,z) block(x,y,z)" per launch;
@@ -220,9 +244,14 @@ mmfhe_status mmfhe_keyswitch(mmfhe_ctx *ctx, const mmfhe_keys *keys, int which, 
  * until the process exits; a call that needs more (batch x rows of
  * (level+1) + beta (level+1+K) + 2 (level+1+K) + 4 (level+1), N words each)
  * returns BAD_ARG -- at N = 2^15, top level 11, K = 4, dnum = 3 that is one
- * ciphertext per call.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress) with that device current; make that
- * first call before any stream capture.  All calls share the array and it
+ * ciphertext per call.  d and out must be memory of the context's own
+ * device (BAD_ARG otherwise).  The first call on a context looks up the
+ * array's device address (cudaGetSymbolAddress) with the context's device
+ * current and keeps it in the context; make that first call before any
+ * stream capture.  The address belongs to the device's primary CUDA context:
+ * a device reset (cudaDeviceReset) invalidates it together with every other
+ * device object of the mmfhe context, so destroy mmfhe contexts before a
+ * reset and create new ones after it.  All calls share the array and it
  * keeps the last call's contents (no region needs clearing: every word read
  * is written earlier in the same call); calls that overlap on the GPU, on
  * any stream or context of the same device, race on it -- serialise them. */
@@ -386,6 +415,99 @@ mmfhe_status mmfhe_eval(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *cons
  * den_HR (frequency-weighted sums in Hz; BPM = 60 num/den). */
 mmfhe_status mmfhe_eval_vital(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *const *keys,
                               const uint64_t *const *in_cts, size_t batch, uint64_t *const *out_cts, void *stream);
+
+/* ------------------------------------------------------------------------
+ * What crosses the trust boundary, serialized and checked (paper Sec.
+ * "System Design": the client uploads its ciphertexts and its public
+ * evaluation keys rlk and gk once at enrollment; the cloud returns
+ * ciphertexts).  Blobs and headers carry the fingerprint of the parameter
+ * set they were made for, so an object made for another parameter set is
+ * refused (PARAM_MISMATCH) instead of being evaluated into garbage.
+ * ---------------------------------------------------------------------- */
+/* Parameter-set fingerprint: word-wise FNV-1a (h = offset basis
+ * 0xcbf29ce484222325; for every 64-bit word w: h = (h xor w) *
+ * 0x100000001b3 mod 2^64) over the words log_n, num_q, num_p, dnum,
+ * q_0..q_L, p_0..p_{K-1}.  Host only.  Errors: BAD_ARG. */
+mmfhe_status mmfhe_params_hash(const mmfhe_params *params, uint64_t *out);
+
+/* 32-byte header of one ciphertext: its level, log2 of its scale and the
+ * fingerprint of its parameter set. */
+#define MMFHE_CT_MAGIC 0x54434D4Du   /* bytes "MMCT" */
+typedef struct mmfhe_ct_header {
+    uint32_t magic;        /* MMFHE_CT_MAGIC */
+    uint16_t version;      /* 1 */
+    uint16_t reserved0;
+    uint32_t level;        /* l: the ciphertext has l+1 limbs */
+    uint32_t reserved1;
+    double log2_scale;     /* log2 of the scale Delta the message is multiplied by */
+    uint64_t params_hash;  /* mmfhe_params_hash of its parameter set */
+} mmfhe_ct_header;
+/* Fill a header (host only; what a client attaches to each ciphertext it
+ * encrypts at `level` and `scale`).  Errors: BAD_ARG, LEVEL_MISMATCH. */
+mmfhe_status mmfhe_ct_header_make(const mmfhe_params *params, uint32_t level, double scale, mmfhe_ct_header *out);
+
+/* mmfhe_eval with a header per ciphertext.  in_hdrs[w] holds the n_in
+ * headers of window w's inputs (mmfhe_plan_io), out_hdrs[w] receives the
+ * n_out headers of its outputs (level, tracked log2 scale, fingerprint).
+ * Checked before any work is queued: BAD_BLOB (not a header), PARAM_MISMATCH
+ * (another parameter set; keys or plan of another context; GESTURE plans:
+ * a scale other than the plan's input_scale), LEVEL_MISMATCH (an input not
+ * at the top level), BAD_ARG (inputs of one call at different scales).
+ * Otherwise as mmfhe_eval; the words computed do not depend on the scale. */
+mmfhe_status mmfhe_eval_checked(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *const *keys,
+                                const mmfhe_ct_header *const *in_hdrs, const uint64_t *const *in_cts, size_t batch,
+                                mmfhe_ct_header *const *out_hdrs, uint64_t *const *out_cts, void *stream);
+
+/* Blobs: little-endian 64-bit words in host memory, 8-byte aligned.
+ *   word 0  magic 0x424C424548464D4D (bytes "MMFHEBLB")
+ *   word 1  version (1) in the low 32 bits, kind in the high 32 bits
+ *   word 2  mmfhe_params_hash of the parameter set
+ *   word 3  body length in words (W)
+ *   words 4 .. 4+W-1  body
+ *   word 4+W  checksum: word-wise FNV-1a (as in mmfhe_params_hash) of words 0 .. 3+W
+ * MMFHE_BLOB_KEYS body: count C (the relinearization key, then C-1 Galois
+ * keys), the words per key dnum*2*(L+1+K)*N, C key ids (0 for the
+ * relinearization key, then a rotation in [1, N/2) or MMFHE_ROT_CONJ, as
+ * signed 64-bit words), then the C keys, each in the layout of
+ * mmfhe_keys_set_relin.
+ * MMFHE_BLOB_PLAN body: sizeof(mmfhe_circuit_config), the configuration's
+ * bytes zero-padded to whole words, the constant count C, C levels, then the
+ * C constants in the plan's order (mmfhe_plan_const_key), constant i as
+ * uint64[level_i+1][N] in coefficient form. */
+#define MMFHE_BLOB_KEYS 1u
+#define MMFHE_BLOB_PLAN 2u
+/* Serialize a user's evaluation keys (host only): the relinearization key and
+ * n_rot Galois keys (layouts as mmfhe_keys_set_*).  out == NULL: *size gets
+ * the blob's size in bytes and nothing is written.  Errors: BAD_ARG (null
+ * key, rotation 0, capacity too small), BAD_BLOB (a residue not below its
+ * prime). */
+mmfhe_status mmfhe_keys_blob_write(const mmfhe_params *params, const uint64_t *relin, uint32_t n_rot,
+                                   const int32_t *rotations, const uint64_t *const *galois, void *out, size_t capacity,
+                                   size_t *size);
+/* Serialize a plan: its configuration and `count` encoded constants at the
+ * given levels (host only; out == NULL: size only).  Errors: BAD_ARG,
+ * LEVEL_MISMATCH, BAD_BLOB (a residue not below its prime). */
+mmfhe_status mmfhe_plan_blob_write(const mmfhe_params *params, const mmfhe_circuit_config *cfg, size_t cfg_size,
+                                   uint32_t count, const uint32_t *levels, const uint64_t *const *consts, void *out,
+                                   size_t capacity, size_t *size);
+/* Validate a blob against a parameter set without a GPU (what mmfhe_keys_load
+ * and mmfhe_plan_load check before they upload anything): BAD_BLOB for a
+ * wrong magic, version or kind, a truncated or oversized blob, inconsistent
+ * counts or sizes, a bad key id, a residue not below its prime, or a
+ * checksum mismatch; PARAM_MISMATCH for another parameter set; BAD_ARG for a
+ * null, unaligned or device pointer.  *kind (nullable) gets the blob's kind. */
+mmfhe_status mmfhe_blob_check(const mmfhe_params *params, const void *blob, size_t size, uint32_t *kind);
+/* Make a serialized key set resident (enrollment, paper Sec. "System
+ * Design"): validated as mmfhe_blob_check against the context's parameters,
+ * then uploaded; the blob is not referenced after the call.  Errors as
+ * mmfhe_blob_check, plus BAD_BLOB (a rotation key twice), OUT_OF_MEMORY,
+ * CUDA.  Release with mmfhe_keys_unload. */
+mmfhe_status mmfhe_keys_load(mmfhe_ctx *ctx, uint64_t user_id, const void *blob, size_t size, mmfhe_keys **out);
+/* Create a plan from a serialized configuration and its encoded constants:
+ * validated as mmfhe_blob_check, then BAD_BLOB if the configuration is
+ * invalid or its plan has another constant count or levels.  Release with
+ * mmfhe_plan_destroy. */
+mmfhe_status mmfhe_plan_load(mmfhe_ctx *ctx, const void *blob, size_t size, mmfhe_plan **out);
 
 /* ------------------------------------------------------------------------
  * Autotuner (no counterpart in the paper).  The NTT passes and the key inner
@@ -568,15 +690,25 @@ mmfhe_status mmfhe_server_create(mmfhe_ctx *ctx, const mmfhe_circuit_config *bas
  * until the user's first window runs.  BAD_ARG if user_id is registered. */
 mmfhe_status mmfhe_server_add_user(mmfhe_server *s, uint64_t user_id, const uint64_t *relin, const int32_t *rotations,
                                    const uint64_t *const *galois, uint32_t n_rot);
-/* Queue one window (input and output as for mmfhe_eval; host buffers should
- * be pinned for the copies to overlap).  *ticket identifies it.  NOT_FOUND
- * for an unknown user. */
 /* Learned layers (FC and GESTURE servers): layer `layer` as for
  * mmfhe_plan_set_fc_layer, `count` doubles (FC: D x D; GESTURE: layer 0
  * fc_width x (A R D + 1), layers 1-2 fc_width x fc_width), copied and applied
  * to every plan the server creates.  Call before the first submit (BUSY
  * after); BAD_ARG for another circuit, layer or size. */
 mmfhe_status mmfhe_server_set_fc_layer(mmfhe_server *s, uint32_t layer, const double *W, size_t count);
+/* Caller-encoded public constants: `count` words (coefficient form,
+ * uint64[level+1][N], the plan's constant `index` as listed by
+ * mmfhe_plan_const_key for a plan of `frames` frames) replace the library's
+ * own encoding of that constant in the plan the server creates for that
+ * frame count (for a client that designs its constants itself, and for
+ * parity tests that install an independent encoding).  Copied; call before
+ * the first submit (BUSY after).  A wrong index or size makes the windows of
+ * that frame count fail with BAD_ARG. */
+mmfhe_status mmfhe_server_set_const(mmfhe_server *s, uint32_t frames, uint32_t index, const uint64_t *words,
+                                    size_t count);
+/* Queue one window (input and output as for mmfhe_eval; host buffers should
+ * be pinned for the copies to overlap).  *ticket identifies it.  NOT_FOUND
+ * for an unknown user. */
 mmfhe_status mmfhe_server_submit(mmfhe_server *s, uint64_t user_id, uint32_t frames, const uint64_t *in,
                                  uint64_t *out, uint64_t *ticket);
 /* Wait up to timeout_ms for a window: OK (output written; *latency_ms =

@@ -12,7 +12,8 @@ import numpy as np
 
 from . import _lib
 from ._lib import (CIRCUIT_FC, CIRCUIT_FIR_DFT, CIRCUIT_GESTURE, CIRCUIT_VITAL, CIRCUIT_VITAL_PER_FRAME, CONST_TAGS, ROT_CONJ, BatcherConfig, BatcherStats, CircuitConfig, ConstKey,
-                   MmfheError, Params, ServerConfig, ServerStats, Tuning, check, ptr, ptr_array, stream_ptr)
+                   BLOB_KEYS, BLOB_PLAN, CtHeader, MmfheError, Params, ServerConfig, ServerStats, Tuning, check, ptr,
+                   ptr_array, stream_ptr)
 
 __all__ = ["Context", "Keys", "Plan", "Graph", "Batcher", "Server", "params_select", "params_from_primes", "encode", "pack_window", "MmfheError",
            "Params", "CIRCUIT_FIR_DFT", "CIRCUIT_VITAL", "CIRCUIT_FC", "vital_config", "fir_dft_config",
@@ -53,6 +54,70 @@ def encode(params, slots, scale, level):
     out = np.empty((level + 1, 1 << params.log_n), dtype=np.uint64)
     check(_lib.lib().mmfhe_encode(ctypes.byref(params), ptr(slots), float(scale), level, ptr(out)))
     return out
+
+
+def params_hash(params):
+    """The parameter-set fingerprint carried by headers and blobs."""
+    v = ctypes.c_uint64()
+    _lib.check(_lib.lib().mmfhe_params_hash(ctypes.byref(params), ctypes.byref(v)))
+    return v.value
+
+
+def ct_header(params, level, scale):
+    """The 32-byte header of a ciphertext at `level` and `scale`."""
+    h = _lib.CtHeader()
+    _lib.check(_lib.lib().mmfhe_ct_header_make(ctypes.byref(params), level, float(scale), ctypes.byref(h)))
+    return h
+
+
+def _blob_buffer(nbytes):
+    return np.zeros((nbytes + 7) // 8, dtype=np.uint64)
+
+
+def keys_blob(params, relin, galois):
+    """Serialize evaluation keys: relin words and {rotation: words}."""
+    rots = sorted(galois, key=lambda r: (r != ROT_CONJ, r))
+    relin = np.ascontiguousarray(relin, dtype=np.uint64)
+    gal = [np.ascontiguousarray(galois[r], dtype=np.uint64) for r in rots]
+    rarr = (ctypes.c_int32 * max(1, len(rots)))(*rots)
+    garr = ptr_array(gal) if gal else None
+    size = ctypes.c_size_t()
+    L = _lib.lib()
+    _lib.check(L.mmfhe_keys_blob_write(ctypes.byref(params), ptr(relin), len(rots), rarr, garr, None, 0,
+                                       ctypes.byref(size)))
+    out = _blob_buffer(size.value)
+    _lib.check(L.mmfhe_keys_blob_write(ctypes.byref(params), ptr(relin), len(rots), rarr, garr, ptr(out),
+                                       out.nbytes, ctypes.byref(size)))
+    return out
+
+
+def plan_blob(params, cfg, consts):
+    """Serialize a plan: its configuration and [(level, words)] constants in
+    the plan's order."""
+    levels = (ctypes.c_uint32 * max(1, len(consts)))(*[lv for lv, _ in consts])
+    words = [np.ascontiguousarray(w, dtype=np.uint64) for _, w in consts]
+    warr = ptr_array(words) if words else None
+    size = ctypes.c_size_t()
+    L = _lib.lib()
+    args = (ctypes.byref(params), ctypes.byref(cfg), ctypes.sizeof(CircuitConfig), len(consts), levels, warr)
+    _lib.check(L.mmfhe_plan_blob_write(*args, None, 0, ctypes.byref(size)))
+    out = _blob_buffer(size.value)
+    _lib.check(L.mmfhe_plan_blob_write(*args, ptr(out), out.nbytes, ctypes.byref(size)))
+    return out
+
+
+def blob_check(params, blob):
+    """Validate a blob without a GPU; returns its kind (BLOB_KEYS or BLOB_PLAN)."""
+    kind = ctypes.c_uint32()
+    _lib.check(_lib.lib().mmfhe_blob_check(ctypes.byref(params), ptr(blob), blob.nbytes, ctypes.byref(kind)))
+    return kind.value
+
+
+def debug_fail_allocations(after):
+    """Host-side failure injection for tests: after `after` more successful
+    device allocations every library allocation fails with OUT_OF_MEMORY
+    (without calling cudaMalloc); after < 0 disarms."""
+    _lib.check(_lib.lib().mmfhe_debug_fail_allocations(int(after)))
 
 
 def pack_window(log_n, values):
@@ -221,6 +286,16 @@ class Context:
         self._c(_lib.lib().mmfhe_launch_count(self.h, ctypes.byref(v)))
         return v.value
 
+    def mem_stats(self):
+        """Device bytes the library holds on this context's device (now and
+        at the high-water mark), its cudaMalloc count, and this context's pool."""
+        m = _lib.MemStats()
+        self._c(_lib.lib().mmfhe_mem_stats_get(self.h, ctypes.byref(m)))
+        return {n: int(getattr(m, n)) for n, _ in _lib.MemStats._fields_}
+
+    def mem_peak_reset(self):
+        self._c(_lib.lib().mmfhe_mem_peak_reset(self.h))
+
     def trace(self, enable=None):
         """Enable/disable the launch trace, or (enable=None) return it."""
         if enable is not None:
@@ -305,6 +380,20 @@ class Context:
     def plan(self, cfg):
         return Plan(self, cfg)
 
+    def keys_load(self, blob, user_id=0):
+        """Resident keys from a serialized key blob (validated first)."""
+        h = ctypes.c_void_p()
+        self._c(_lib.lib().mmfhe_keys_load(self.h, user_id, ptr(blob), blob.nbytes, ctypes.byref(h)))
+        return Keys._from_handle(self, h)
+
+    def plan_load(self, blob):
+        """A plan from a serialized plan blob (validated first)."""
+        h = ctypes.c_void_p()
+        self._c(_lib.lib().mmfhe_plan_load(self.h, ptr(blob), blob.nbytes, ctypes.byref(h)))
+        p = Plan._borrowed(self, h)
+        p.owned = True
+        return p
+
     # --- primitives (coefficient-form buffers) -----------------------------
     def ntt(self, rows, prime_idx, inverse=False, stream=None):
         pid = np.ascontiguousarray(prime_idx, dtype=np.uint32)
@@ -371,6 +460,21 @@ class Context:
         karr = (ctypes.c_void_p * B)(*[k.h.value for k in kl])
         f = _lib.lib().mmfhe_eval_vital if vital else _lib.lib().mmfhe_eval
         self._c(f(self.h, plan.h, karr, ptr_array(ins), B, ptr_array(outs), stream_ptr(stream)))
+
+    def eval_checked(self, plan, keys, in_hdrs, ins, outs, stream=None):
+        """mmfhe_eval with ciphertext headers: in_hdrs[w] = list of n_in
+        CtHeader; returns the output headers per window."""
+        B = len(ins)
+        n_in, n_out, _ = plan.io()
+        kl = keys if isinstance(keys, (list, tuple)) else [keys] * B
+        karr = (ctypes.c_void_p * B)(*[k.h.value for k in kl])
+        hin = [(_lib.CtHeader * n_in)(*h) for h in in_hdrs]
+        hout = [(_lib.CtHeader * n_out)() for _ in range(B)]
+        hin_arr = (ctypes.c_void_p * B)(*[ctypes.addressof(h) for h in hin])
+        hout_arr = (ctypes.c_void_p * B)(*[ctypes.addressof(h) for h in hout])
+        self._c(_lib.lib().mmfhe_eval_checked(self.h, plan.h, karr, hin_arr, ptr_array(ins), B, hout_arr,
+                                              ptr_array(outs), stream_ptr(stream)))
+        return [list(h) for h in hout]
 
 
 def _tuning_dict(t):
@@ -490,6 +594,12 @@ class Server:
         W = np.ascontiguousarray(W, dtype=np.float64)
         self.ctx._c(_lib.lib().mmfhe_server_set_fc_layer(self.h, layer, ptr(W), W.size))
 
+    def set_const(self, frames, index, words):
+        """Install a caller-encoded constant (coefficient form) in the plan the
+        server creates for `frames` (before the first submit)."""
+        w = np.ascontiguousarray(words, dtype=np.uint64)
+        self.ctx._c(_lib.lib().mmfhe_server_set_const(self.h, frames, index, ptr(w), w.size))
+
     def submit(self, user_id, frames, inp, out):
         t = ctypes.c_uint64()
         self.ctx._c(_lib.lib().mmfhe_server_submit(self.h, user_id, frames, ptr(inp), ptr(out), ctypes.byref(t)))
@@ -533,6 +643,12 @@ class Keys:
         h = ctypes.c_void_p()
         ctx._c(_lib.lib().mmfhe_keys_create(ctx.h, user_id, ctypes.byref(h)))
         self.h = h
+
+    @classmethod
+    def _from_handle(cls, ctx, h):
+        k = cls.__new__(cls)
+        k.ctx, k.h = ctx, h
+        return k
 
     def set_relin(self, words):
         self.ctx._c(_lib.lib().mmfhe_keys_set_relin(self.h, ptr(words)))

@@ -89,6 +89,20 @@ class ServerStats(ctypes.Structure):
                [(n, ctypes.c_double) for n in ("mean_batch", "p50_ms", "p99_ms", "windows_per_s")]
 
 
+class MemStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("device_bytes", "peak_bytes", "allocations", "pool_bytes",
+                                                "pool_free_bytes")]
+
+
+class CtHeader(ctypes.Structure):
+    _fields_ = [("magic", ctypes.c_uint32), ("version", ctypes.c_uint16), ("reserved0", ctypes.c_uint16),
+                ("level", ctypes.c_uint32), ("reserved1", ctypes.c_uint32), ("log2_scale", ctypes.c_double),
+                ("params_hash", ctypes.c_uint64)]
+
+
+BLOB_KEYS, BLOB_PLAN = 1, 2
+
+
 class ConstKey(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint32), ("band", ctypes.c_uint32), ("index", ctypes.c_uint32),
                 ("level", ctypes.c_uint32)]
@@ -104,6 +118,9 @@ _SIGS = {
     "mmfhe_ctx_destroy": [_VP],
     "mmfhe_sync": [_VP, _VP, _U32],
     "mmfhe_launch_count": [_VP, ctypes.POINTER(_U64)],
+    "mmfhe_mem_stats_get": [_VP, ctypes.POINTER(MemStats)],
+    "mmfhe_mem_peak_reset": [_VP],
+    "mmfhe_debug_fail_allocations": [ctypes.c_int64],
     "mmfhe_trace_enable": [_VP, _INT],
     "mmfhe_trace_get": [_VP, ctypes.c_char_p, _SZ, ctypes.POINTER(_SZ)],
     "mmfhe_profile_enable": [_VP, _INT],
@@ -128,6 +145,7 @@ _SIGS = {
     "mmfhe_server_create": [_VP, _VP, _SZ, _VP, _PP],
     "mmfhe_server_add_user": [_VP, _U64, _VP, _VP, _VP, _U32],
     "mmfhe_server_set_fc_layer": [_VP, _U32, _VP, _SZ],
+    "mmfhe_server_set_const": [_VP, _U32, _U32, _VP, _SZ],
     "mmfhe_ntt32_select_primes": [_U32, _U32, _U32, _VP],
     "mmfhe_ntt_batch": [_VP, _VP, _SZ, _U32, ctypes.c_int, _VP],
     "mmfhe_ntt32_create": [_U32, _VP, _U32, ctypes.c_int, _PP],
@@ -174,6 +192,15 @@ _SIGS = {
     "mmfhe_eval": [_VP, _VP, _VP, _VP, _SZ, _VP, _VP],
     "mmfhe_eval_vital": [_VP, _VP, _VP, _VP, _SZ, _VP, _VP],
     "mmfhe_pack_window": [_U32, _U32, _U32, _VP, _VP],
+    "mmfhe_params_hash": [ctypes.POINTER(Params), ctypes.POINTER(_U64)],
+    "mmfhe_ct_header_make": [ctypes.POINTER(Params), _U32, ctypes.c_double, ctypes.POINTER(CtHeader)],
+    "mmfhe_eval_checked": [_VP, _VP, _VP, _VP, _VP, _SZ, _VP, _VP, _VP],
+    "mmfhe_keys_blob_write": [ctypes.POINTER(Params), _VP, _U32, _VP, _VP, _VP, _SZ, ctypes.POINTER(_SZ)],
+    "mmfhe_plan_blob_write": [ctypes.POINTER(Params), ctypes.POINTER(CircuitConfig), _SZ, _U32, _VP, _VP, _VP, _SZ,
+                              ctypes.POINTER(_SZ)],
+    "mmfhe_blob_check": [ctypes.POINTER(Params), _VP, _SZ, ctypes.POINTER(_U32)],
+    "mmfhe_keys_load": [_VP, _U64, _VP, _SZ, _PP],
+    "mmfhe_plan_load": [_VP, _VP, _SZ, _PP],
     "mmfhe_encode": [ctypes.POINTER(Params), _VP, ctypes.c_double, _U32, _VP],
 }
 

@@ -25,6 +25,8 @@ mmfhe_status params_select(uint32_t, uint32_t, uint32_t, uint32_t, uint32_t, uin
 
 static thread_local std::string g_last_error;
 
+void mmfhe::set_thread_error(const std::string &msg) { g_last_error = msg; }
+
 static mmfhe_status fail(Context *c, mmfhe_status code, const char *msg) {
     g_last_error = msg;
     if (c) c->last_error = msg;
@@ -109,7 +111,8 @@ static std::vector<uint64_t *> contiguous_out(uint64_t *base, size_t B, size_t s
 // Evaluate a plan on `batch` windows; windows with the same key set form one
 // batch (every launch covers all of them).  Pointers may be host or device.
 void mmfhe::eval_windows(Context &c, const Plan &p, const Keys *const *keys, const uint64_t *const *in_cts,
-                         size_t batch, uint64_t *const *out_cts, cudaStream_t st, bool mix_users) {
+                         size_t batch, uint64_t *const *out_cts, cudaStream_t st, bool mix_users, double in_scale,
+                         std::vector<double> *out_scales) {
     // groups of windows evaluated together, with the key set they run under
     std::vector<std::pair<const Keys *, std::vector<size_t>>> groups;
     std::vector<std::unique_ptr<Keys>> mixed;   // per-window key views of mixed batches
@@ -172,7 +175,7 @@ void mmfhe::eval_windows(Context &c, const Plan &p, const Keys *const *keys, con
             std::vector<const uint64_t *> z((size_t)B * p.pairs);
             for (int b = 0; b < B; b++)
                 for (int j = 0; j < p.pairs; j++) z[(size_t)b * p.pairs + j] = ins[b] + (size_t)j * in_w;
-            in.push_back(load_cts(c, z.data(), 0, B * p.pairs, c.L, 1.0, st));
+            in.push_back(load_cts(c, z.data(), 0, B * p.pairs, c.L, in_scale, st));
         } else if (p.cfg.kind == MMFHE_CIRCUIT_GESTURE) {
             // Re and Im of all pairs of all windows, window-major
             std::vector<const uint64_t *> re((size_t)B * p.pairs), im((size_t)B * p.pairs);
@@ -181,13 +184,17 @@ void mmfhe::eval_windows(Context &c, const Plan &p, const Keys *const *keys, con
                     re[(size_t)b * p.pairs + j] = ins[b] + (size_t)(2 * j) * in_w;
                     im[(size_t)b * p.pairs + j] = ins[b] + (size_t)(2 * j + 1) * in_w;
                 }
-            in.push_back(load_cts(c, re.data(), 0, B * p.pairs, c.L, 1.0, st));
-            in.push_back(load_cts(c, im.data(), 0, B * p.pairs, c.L, 1.0, st));
+            in.push_back(load_cts(c, re.data(), 0, B * p.pairs, c.L, in_scale, st));
+            in.push_back(load_cts(c, im.data(), 0, B * p.pairs, c.L, in_scale, st));
         } else {
-            for (int i = 0; i < p.n_in; i++) in.push_back(load_cts(c, ins.data(), i * in_w, B, c.L, 1.0, st));
+            for (int i = 0; i < p.n_in; i++) in.push_back(load_cts(c, ins.data(), i * in_w, B, c.L, in_scale, st));
         }
         std::vector<CtB> res = run_plan(c, p, K, in, st);
         in.clear();
+        if (out_scales) {
+            out_scales->clear();
+            for (auto &r : res) out_scales->push_back(r.scale);
+        }
         for (size_t o = 0; o < res.size(); o++) host_out |= store_cts(c, res[o], outs.data(), out_off[o], st);
     }
     if (host_out) CK(cudaStreamSynchronize(st));
@@ -266,6 +273,26 @@ mmfhe_status mmfhe_sync(mmfhe_ctx *ctx, void *stream, uint32_t timeout_ms) {
 mmfhe_status mmfhe_launch_count(const mmfhe_ctx *ctx, uint64_t *out) {
     if (!ctx || !ctx->c || !out) return fail(nullptr, MMFHE_ERR_BAD_ARG, "null argument");
     *out = ctx->c->launches;
+    return MMFHE_OK;
+}
+
+mmfhe_status mmfhe_mem_stats_get(const mmfhe_ctx *ctx, mmfhe_mem_stats *out) {
+    if (!ctx || !ctx->c || !out) return fail(nullptr, MMFHE_ERR_BAD_ARG, "null argument");
+    Context *c = ctx->c;
+    mem_stats(c->device, &out->device_bytes, &out->peak_bytes, &out->allocations);
+    out->pool_bytes = c->pool ? c->pool->bytes_held() : 0;
+    out->pool_free_bytes = c->pool ? c->pool->bytes_free() : 0;
+    return MMFHE_OK;
+}
+
+mmfhe_status mmfhe_mem_peak_reset(mmfhe_ctx *ctx) {
+    if (!ctx || !ctx->c) return fail(nullptr, MMFHE_ERR_BAD_ARG, "null context");
+    mem_peak_reset(ctx->c->device);
+    return MMFHE_OK;
+}
+
+mmfhe_status mmfhe_debug_fail_allocations(int64_t after) {
+    set_fail_after(after);
     return MMFHE_OK;
 }
 

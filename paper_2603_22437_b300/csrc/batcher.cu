@@ -142,11 +142,13 @@ struct mmfhe_batcher {
     struct GraphEntry {
         std::unique_ptr<mmfhe_graph> g;
         uint64_t *stage_in = nullptr, *stage_out = nullptr;
+        size_t in_bytes = 0, out_bytes = 0;
+        int device = 0;
         uint64_t bytes = 0, last_use = 0;
         ~GraphEntry() {
             g.reset();
-            if (stage_in) cudaFree(stage_in);
-            if (stage_out) cudaFree(stage_out);
+            dev_free(device, stage_in, in_bytes);
+            dev_free(device, stage_out, out_bytes);
         }
     };
     using GraphKey = std::tuple<uint32_t, const Keys *, uint32_t>;   // frames, keys, batch size
@@ -234,8 +236,13 @@ struct mmfhe_batcher {
         auto it = graphs.find(key);
         if (it == graphs.end()) {
             std::unique_ptr<GraphEntry> e(new GraphEntry());
-            CK(cudaMalloc(&e->stage_in, std::max<size_t>(8, b * pe.in_words * 8)));
-            CK(cudaMalloc(&e->stage_out, std::max<size_t>(8, b * pe.out_words * 8)));
+            e->device = c->device;
+            e->in_bytes = std::max<size_t>(8, b * pe.in_words * 8);
+            e->out_bytes = std::max<size_t>(8, b * pe.out_words * 8);
+            e->stage_in = (uint64_t *)dev_alloc(c->device, e->in_bytes);
+            if (!e->stage_in) throw Error(MMFHE_ERR_OUT_OF_MEMORY, "batcher staging allocation failed");
+            e->stage_out = (uint64_t *)dev_alloc(c->device, e->out_bytes);
+            if (!e->stage_out) throw Error(MMFHE_ERR_OUT_OF_MEMORY, "batcher staging allocation failed");
             CK(cudaMemset(e->stage_in, 0, b * pe.in_words * 8));
             std::vector<const uint64_t *> ins(b);
             std::vector<uint64_t *> outs(b);

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <set>
@@ -23,6 +24,62 @@ void cuda_check(cudaError_t e, const char *what) {
 // ---------------------------------------------------------------------------
 // pool
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// library-wide device memory accounting and the allocation-failure hook
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int kMaxTrackedDevices = 64;
+std::atomic<uint64_t> g_dev_bytes[kMaxTrackedDevices];
+std::atomic<uint64_t> g_dev_peak[kMaxTrackedDevices];
+std::atomic<uint64_t> g_dev_allocs[kMaxTrackedDevices];
+std::atomic<int64_t> g_fail_after{-1};
+
+int tracked(int device) { return device >= 0 && device < kMaxTrackedDevices ? device : kMaxTrackedDevices - 1; }
+}  // namespace
+
+void *dev_alloc(int device, size_t bytes) {
+    int64_t f = g_fail_after.load();
+    while (f > 0 && !g_fail_after.compare_exchange_weak(f, f - 1)) {
+    }
+    if (f == 0) throw Error(MMFHE_ERR_OUT_OF_MEMORY, "injected allocation failure (" + std::to_string(bytes) + " bytes)");
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    const int d = tracked(device);
+    uint64_t now = g_dev_bytes[d].fetch_add(bytes) + bytes;
+    uint64_t pk = g_dev_peak[d].load();
+    while (now > pk && !g_dev_peak[d].compare_exchange_weak(pk, now)) {
+    }
+    g_dev_allocs[d].fetch_add(1);
+    return p;
+}
+
+void dev_free(int device, void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    g_dev_bytes[tracked(device)].fetch_sub(bytes);
+}
+
+void mem_stats(int device, uint64_t *bytes, uint64_t *peak, uint64_t *allocs) {
+    const int d = tracked(device);
+    *bytes = g_dev_bytes[d].load();
+    *peak = g_dev_peak[d].load();
+    *allocs = g_dev_allocs[d].load();
+}
+
+void mem_peak_reset(int device) {
+    const int d = tracked(device);
+    g_dev_peak[d].store(g_dev_bytes[d].load());
+}
+
+void set_fail_after(int64_t n) { g_fail_after.store(n < 0 ? -1 : n); }
+
+// ---------------------------------------------------------------------------
+// pool
+// ---------------------------------------------------------------------------
 Pool::~Pool() { trim(); }
 
 uint64_t *Pool::get(size_t words) {
@@ -30,32 +87,32 @@ uint64_t *Pool::get(size_t words) {
     if (it != free_.end()) {
         uint64_t *p = it->second;
         free_.erase(it);
+        free_bytes_ -= words * 8;
         return p;
     }
-    void *p = nullptr;
-    cudaError_t e = cudaMalloc(&p, words * sizeof(uint64_t));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
+    void *p = dev_alloc(device_, words * sizeof(uint64_t));
+    if (!p) {
         cudaDeviceSynchronize();
         trim();   // release cached blocks and retry once
-        e = cudaMalloc(&p, words * sizeof(uint64_t));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            throw Error(MMFHE_ERR_OUT_OF_MEMORY, "device allocation of " + std::to_string(words * 8) + " bytes failed");
-        }
+        p = dev_alloc(device_, words * sizeof(uint64_t));
+        if (!p) throw Error(MMFHE_ERR_OUT_OF_MEMORY, "device allocation of " + std::to_string(words * 8) + " bytes failed");
     }
     held_ += words * 8;
     return (uint64_t *)p;
 }
 
-void Pool::put(uint64_t *p, size_t words) { free_.emplace(words, p); }
+void Pool::put(uint64_t *p, size_t words) {
+    free_.emplace(words, p);
+    free_bytes_ += words * 8;
+}
 
 void Pool::trim() {
     for (auto &kv : free_) {
-        cudaFree(kv.second);
+        dev_free(device_, kv.second, kv.first * 8);
         held_ -= kv.first * 8;
     }
     free_.clear();
+    free_bytes_ = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -137,9 +194,10 @@ static void validate(const mmfhe_params &p) {
 // context
 // ---------------------------------------------------------------------------
 static uint64_t *upload(Context &c, const std::vector<uint64_t> &h) {
-    void *p = nullptr;
-    CK(cudaMalloc(&p, std::max<size_t>(8, h.size() * 8)));
-    c.owned.push_back(p);
+    const size_t bytes = std::max<size_t>(8, h.size() * 8);
+    void *p = dev_alloc(c.device, bytes);
+    if (!p) throw Error(MMFHE_ERR_OUT_OF_MEMORY, "device allocation of context tables failed");
+    c.owned.push_back({p, bytes});
     if (!h.empty()) CK(cudaMemcpy(p, h.data(), h.size() * 8, cudaMemcpyHostToDevice));
     return (uint64_t *)p;
 }
@@ -362,7 +420,7 @@ void destroy_context(Context *c) {
     cudaSetDevice(c->device);
     cudaDeviceSynchronize();
     c->pool.reset();
-    for (void *p : c->owned) cudaFree(p);
+    for (auto &o : c->owned) dev_free(c->device, o.first, o.second);
     for (cudaEvent_t e : c->event_pool) cudaEventDestroy(e);
     delete c;
 }

@@ -74,13 +74,27 @@ public:
     uint64_t *get(size_t words);
     void put(uint64_t *p, size_t words);
     size_t bytes_held() const { return held_; }
+    size_t bytes_free() const { return free_bytes_; }
     void trim();
 
 private:
     int device_;
     std::multimap<size_t, uint64_t *> free_;
     size_t held_ = 0;
+    size_t free_bytes_ = 0;
 };
+
+// Every device allocation of the evaluator goes through dev_alloc / dev_free,
+// which keep per-device totals (current bytes, high-water mark, number of
+// cudaMalloc calls).  dev_alloc returns nullptr when cudaMalloc fails and
+// throws OUT_OF_MEMORY while the failure hook (set_fail_after) is armed:
+// after n more successful allocations, every later one fails without calling
+// cudaMalloc until the hook is disarmed (n < 0).
+void *dev_alloc(int device, size_t bytes);
+void dev_free(int device, void *p, size_t bytes);
+void mem_stats(int device, uint64_t *bytes, uint64_t *peak, uint64_t *allocs);
+void mem_peak_reset(int device);
+void set_fail_after(int64_t n);
 
 // Pooled device buffer (RAII).
 class Buf {
@@ -170,7 +184,8 @@ struct Context {
     std::unique_ptr<Pool> pool;
     uint64_t launches = 0;
     std::string last_error;
-    std::vector<void *> owned;       // cudaMalloc'd tables
+    std::vector<std::pair<void *, size_t>> owned;   // device tables (pointer, bytes)
+    uint64_t *noalloc_scratch = nullptr;              // device address of the no-allocation scratch array
     // optional launch trace (kernel name + shape) for the data-obliviousness test
     bool tracing = false;
     std::vector<std::string> trace;

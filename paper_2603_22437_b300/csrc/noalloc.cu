@@ -12,11 +12,9 @@
 // The scratch array below is file-scope device memory: every GPU that loads
 // the library holds it until the process exits.  Host code cannot use the
 // name g_ks_scratch as a device address (on the host it is only a stand-in
-// symbol); its device address is obtained with cudaGetSymbolAddress once per
-// device, with that device current, on the first call made on that device.
+// symbol); its device address is obtained with cudaGetSymbolAddress, with the
+// context's device current, on the first call made with each context.
 #include <cuda_runtime.h>
-
-#include <mutex>
 
 #include "engine.h"
 #include "handles.h"
@@ -31,24 +29,20 @@ namespace {
 constexpr size_t kScratchWords = MMFHE_NOALLOC_SCRATCH_BYTES / sizeof(uint64_t);
 static __device__ __align__(256) uint64_t g_ks_scratch[kScratchWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-uint64_t *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on `device` (current device).
-uint64_t *scratch_address(int device) {
-    if (device < 0 || device >= kMaxDevices) throw Error(MMFHE_ERR_BAD_ARG, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[device]) {
+// Device address of the scratch array, looked up once per context with the
+// context's device current (the caller has made it current) and kept in the
+// context, so a context created after a device reset looks it up afresh.
+uint64_t *scratch_address(Context &c) {
+    if (!c.noalloc_scratch) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_ks_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             throw Error(MMFHE_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch) failed: ") + cudaGetErrorString(e));
         }
-        g_scratch_addr[device] = (uint64_t *)p;
+        c.noalloc_scratch = (uint64_t *)p;
     }
-    return g_scratch_addr[device];
+    return c.noalloc_scratch;
 }
 
 // Row map without heap use: rows [0, period) map to the given prime ids.
@@ -60,13 +54,17 @@ RowMap map_q(int nl, uint32_t block_stride) {
     return m;
 }
 
-bool is_device_ptr(const void *p) {
+// True for device memory of `device` itself and for managed memory; false for
+// host memory and for another GPU's memory (the kernels run on `device` and
+// would fault on a peer's pointer).
+bool is_device_ptr(const void *p, int device) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 mmfhe_status fail(Context *c, mmfhe_status code, const char *msg) {
@@ -88,8 +86,9 @@ extern "C" mmfhe_status mmfhe_keyswitch_noalloc(mmfhe_ctx *ctx, const mmfhe_keys
         if ((int)level > c->L) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "level above the top level");
         if (batch == 0) return MMFHE_OK;
         if (!out || !d) throw Error(MMFHE_ERR_BAD_ARG, "null pointer");
-        if (!is_device_ptr(out) || !is_device_ptr(d) || ((uintptr_t)out & 15) || ((uintptr_t)d & 15))
-            throw Error(MMFHE_ERR_BAD_ARG, "keyswitch_noalloc needs 16-byte aligned device pointers");
+        if (!is_device_ptr(out, c->device) || !is_device_ptr(d, c->device) || ((uintptr_t)out & 15) ||
+            ((uintptr_t)d & 15))
+            throw Error(MMFHE_ERR_BAD_ARG, "keyswitch_noalloc needs 16-byte aligned pointers to the context's device");
         const Keys &K = keys->k;
         const KeyPtrs key = which == 0 ? relin_key(K) : galois_key(K, norm_rot(*c, rotation));
         cudaStream_t st = (cudaStream_t)stream;
@@ -105,7 +104,7 @@ extern "C" mmfhe_status mmfhe_keyswitch_noalloc(mmfhe_ctx *ctx, const mmfhe_keys
             throw Error(MMFHE_ERR_BAD_ARG, "keyswitch_noalloc: batch x level needs " + std::to_string(rows * N * 8) +
                                                 " bytes of scratch, more than the fixed " +
                                                 std::to_string((size_t)MMFHE_NOALLOC_SCRATCH_BYTES) + " bytes");
-        uint64_t *S = scratch_address(c->device);
+        uint64_t *S = scratch_address(*c);
         uint64_t *Dr = S;
         uint64_t *Gr = Dr + B * nl * N;
         uint64_t *Ur = Gr + B * beta * nre * N;

@@ -69,6 +69,9 @@ struct mmfhe_server {
     std::vector<Slot> slots;
     std::map<uint32_t, std::unique_ptr<Plan>> plans;   // worker thread creates; count read under mu
     std::map<uint32_t, std::vector<double>> fc_layers; // learned layers applied to every plan (guarded by mu)
+    // caller-encoded constants: frame count -> constant index -> coefficient-form words; set before the
+    // first submit (guarded by mu), read-only afterwards
+    std::map<uint32_t, std::map<uint32_t, std::vector<uint64_t>>> const_words;
 
     // statistics (guarded by mu)
     uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batch_windows = 0;
@@ -101,6 +104,21 @@ struct mmfhe_server {
                 layers = fc_layers;
             }
             for (auto &kv : layers) plan_set_fc_layer(*p, kv.first, kv.second.data());
+            const std::map<uint32_t, std::vector<uint64_t>> *words = nullptr;
+            {
+                std::lock_guard<std::mutex> g(mu);
+                auto f = const_words.find(frames);
+                if (f != const_words.end()) words = &f->second;
+            }
+            if (words) {
+                for (auto &kv : *words) {
+                    if (kv.first >= p->keys.size()) throw Error(MMFHE_ERR_BAD_ARG, "server constant index out of range");
+                    if (kv.second.size() != (size_t)(p->keys[kv.first].level + 1) * c->n)
+                        throw Error(MMFHE_ERR_BAD_ARG, "server constant size does not match the plan's constant");
+                    plan_set_const(*p, kv.first, kv.second.data(), 0);
+                }
+                CK(cudaStreamSynchronize(0));
+            }
             std::lock_guard<std::mutex> g(mu);
             it = plans.emplace(frames, std::move(p)).first;
         }
@@ -446,6 +464,15 @@ mmfhe_status mmfhe_server_set_fc_layer(mmfhe_server *s, uint32_t layer, const do
     std::lock_guard<std::mutex> g(s->mu);
     if (!s->plans.empty() || s->submitted) return sfail(s->c, MMFHE_ERR_BUSY, "layers are set before the first submit");
     s->fc_layers[layer].assign(W, W + count);
+    return MMFHE_OK;
+}
+
+mmfhe_status mmfhe_server_set_const(mmfhe_server *s, uint32_t frames, uint32_t index, const uint64_t *words,
+                                    size_t count) {
+    if (!s || !words || !count) return sfail(nullptr, MMFHE_ERR_BAD_ARG, "null argument");
+    std::lock_guard<std::mutex> g(s->mu);
+    if (!s->plans.empty() || s->submitted) return sfail(s->c, MMFHE_ERR_BUSY, "constants are set before the first submit");
+    s->const_words[frames][index].assign(words, words + count);
     return MMFHE_OK;
 }
 

@@ -3,13 +3,17 @@ word for word, and the batcher (windows of uneven frame counts from several
 users, grouped, cut into batches, replayed from graphs or evaluated directly)
 returns for every window exactly the words a lone mmfhe_eval returns.
 
-The evaluation itself is pinned to the oracle by test_gpu_parity and
-test_gpu_vital; here the reference is the library's own unbatched call on a
-plan built for the window's frame count."""
+The batcher's plans carry the oracle's encoded constants, and one window of
+every frame count (F = 200 and the uneven F = 150) is compared word for
+word with the CPU oracle's evaluation of the same input words; every window
+is also compared with the library's own unbatched call on a plan built for
+its frame count."""
 import numpy as np
 import pytest
 
-from test_gpu_parity import gsmall, load_keys, rand_ct  # noqa: F401  (module fixture)
+from oracle import ckks as ck
+from oracle import circuits as cc
+from test_gpu_parity import gsmall, install_oracle_consts, load_keys, rand_ct  # noqa: F401  (module fixture)
 
 pytestmark = pytest.mark.gpu
 
@@ -22,6 +26,29 @@ def io_words(ctx, plan):
 def window_inputs(P, plan, seed):
     n_in, _, _ = plan.io()
     return np.ascontiguousarray(rand_ct(P, P.L, seed, n_in).reshape(-1))
+
+
+_ORACLE_CIRCUITS = {}
+
+
+def oracle_fir_dft(P, bins, frames):
+    """The oracle's FIR + DFT circuit and its encoded constants (cached)."""
+    key = (P.n, tuple(P.q), bins, frames)
+    if key not in _ORACLE_CIRCUITS:
+        circ = cc.FirDftCircuit(P, cc.FirDftConfig(bins=bins, frames=frames))
+        _ORACLE_CIRCUITS[key] = (circ, circ.constants())
+    return _ORACLE_CIRCUITS[key]
+
+
+def oracle_fir_dft_words(P, rlk, gks, bins, frames, x):
+    """The oracle's output words of the FIR + DFT circuit on the input words x
+    ([n_in][2][L+1][N] flattened: group c's Re then Im ciphertext)."""
+    circ, consts = oracle_fir_dft(P, bins, frames)
+    w = x.reshape(-1, 2, P.L + 1, P.n)
+    cts = [ck.Ciphertext(w[i][0].copy(), w[i][1].copy(), P.L, P.scale) for i in range(w.shape[0])]
+    pairs = [(cts[2 * c], cts[2 * c + 1]) for c in range(circ.lay.groups)]
+    res = circ.run(cc.Evaluator(P, rlk, gks), consts, pairs)
+    return np.concatenate([ct.words().reshape(-1) for pr in res for ct in pr])
 
 
 def alone(ctx, plan, keys, x):
@@ -78,11 +105,13 @@ def test_batcher_uneven_frames_two_users(gsmall, use_graphs):
     users = [gsmall["keys"], load_keys(ctx, P, gsmall["rlk"], gsmall["gks"])]
     frames = [200, 150, 200, 150, 200, 200, 150]
     refplans = {}
-    for F in sorted(set(frames)):
-        refplans[F] = ctx.plan(M.fir_dft_config(bins=40, frames=F))
-        refplans[F].encode_consts()
-        assert set(refplans[F].rotations()) <= set(gsmall["gks"])
     b = ctx.batcher(M.fir_dft_config(bins=40), max_batch=2, use_graphs=use_graphs)
+    for F in sorted(set(frames)):
+        _, consts = oracle_fir_dft(P, 40, F)
+        refplans[F] = ctx.plan(M.fir_dft_config(bins=40, frames=F))
+        install_oracle_consts(refplans[F], consts)
+        install_oracle_consts(b.plan(F), consts)
+        assert set(refplans[F].rotations()) <= set(gsmall["gks"])
     subs = []
     for i, F in enumerate(frames):
         x = window_inputs(P, refplans[F], 500 + i)
@@ -93,6 +122,12 @@ def test_batcher_uneven_frames_two_users(gsmall, use_graphs):
     b.flush()
     for i, (k, F, x, out) in enumerate(subs):
         assert np.array_equal(out, alone(ctx, refplans[F], k, x)), "window %d (F=%d)" % (i, F)
+    if use_graphs:
+        # the first window of each frame count against the CPU oracle
+        for F in (200, 150):
+            i = frames.index(F)
+            ref = oracle_fir_dft_words(P, gsmall["rlk"], gsmall["gks"], 40, F, subs[i][2])
+            assert np.array_equal(subs[i][3], ref), "window %d (F=%d) differs from the oracle" % (i, F)
     st = b.stats()
     assert st["windows"] == len(frames) and st["plans_created"] == 2
     # (F, user) groups: (200,u0) x3, (150,u1) x2, (200,u1) x1, (150,u0) x1 -> batches of <= 2

@@ -195,8 +195,11 @@ def test_sync_timeout_returns_status(gsmall):
 # ---------------------------------------------------------------------------
 # circuits
 # ---------------------------------------------------------------------------
-def install_oracle_consts(plan, consts):
-    for i, (tag, band, index, level) in enumerate(plan.const_keys()):
+def oracle_const_words(plan, consts):
+    """The oracle's encoded constants in the plan's constant order
+    (coefficient-form words, one array per constant)."""
+    out = []
+    for tag, band, index, level in plan.const_keys():
         if tag in ("idx", "one"):
             key = (tag, index)
         elif tag in ("fw", "fone"):
@@ -209,7 +212,13 @@ def install_oracle_consts(plan, consts):
             key = (tag, index)
         pt = consts[key]
         assert pt.level == level, key
-        plan.set_const(i, np.ascontiguousarray(pt.m))
+        out.append(np.ascontiguousarray(pt.m))
+    return out
+
+
+def install_oracle_consts(plan, consts):
+    for i, words in enumerate(oracle_const_words(plan, consts)):
+        plan.set_const(i, words)
 
 
 def encrypt_window(P, pk, lay, arrays, seed):

@@ -2,15 +2,19 @@
 uneven frame counts, submitted from two threads while earlier ones run,
 under a key budget that holds two users' keys (so keys are evicted and
 reloaded).  Every window's output equals, word for word, the same window
-evaluated alone with mmfhe_eval; a user whose keys lack a rotation fails
-alone, without disturbing the others."""
+evaluated alone with mmfhe_eval; the server's plans carry the oracle's
+encoded constants, and the first window of every user also equals the CPU
+oracle's evaluation with that user's key words; a user whose keys lack a
+rotation fails alone, without disturbing the others."""
 import threading
 import time
 
 import numpy as np
 import pytest
 
-from test_gpu_parity import gsmall, rand_ct  # noqa: F401  (module fixture)
+from oracle import ckks as ck
+from test_gpu_batching import oracle_fir_dft, oracle_fir_dft_words
+from test_gpu_parity import gsmall, install_oracle_consts, oracle_const_words, rand_ct  # noqa: F401  (module fixture)
 
 pytestmark = pytest.mark.gpu
 
@@ -45,7 +49,7 @@ def test_serving_mix_equals_alone(gsmall, keyip_fused):
     plans = {}
     for F in (200, 150):
         plans[F] = ctx.plan(M.fir_dft_config(bins=40, frames=F))
-        plans[F].encode_consts()
+        install_oracle_consts(plans[F], oracle_fir_dft(P, 40, F)[1])
     rots = sorted(set(plans[200].rotations()) | set(plans[150].rotations()))
     users = {u: user_keys(P, rots, 40 + u) for u in range(3)}
     n_in, _, lv = plans[200].io()
@@ -54,6 +58,9 @@ def test_serving_mix_equals_alone(gsmall, keyip_fused):
     srv = ctx.server(base, max_batch=2, streams=2, key_budget_bytes=2 * key_set + key_set // 2)
     for u, (relin, gal) in users.items():
         srv.add_user(u, relin, gal)
+    for F, plan in plans.items():
+        for i, words in enumerate(oracle_const_words(plan, oracle_fir_dft(P, 40, F)[1])):
+            srv.set_const(F, i, words)
     # user 9: no Galois keys at all -> its windows fail with NOT_FOUND
     bad_relin, _ = user_keys(P, [], 99)
     srv.add_user(9, bad_relin, {})
@@ -107,6 +114,12 @@ def test_serving_mix_equals_alone(gsmall, keyip_fused):
             ctx.eval(plans[F], k, [x], [ref])
             assert np.array_equal(out, ref), "window %d (user %d, F=%d)" % (i, u, F)
         k.unload()
+        # the user's first window against the CPU oracle with the user's key words
+        i = next(i for i, j in enumerate(jobs) if j[0] == u)
+        _, F, x, out = jobs[i]
+        orlk = ck.SwitchKey(P, relin)
+        ogks = {r: ck.SwitchKey(P, w) for r, w in gal.items()}
+        assert np.array_equal(out, oracle_fir_dft_words(P, orlk, ogks, 40, F, x)), "window %d vs the oracle" % i
     ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"], saved["conv_rows"],
                    saved["keyip_fused"])
 
