@@ -19,8 +19,8 @@ pinned host buffers through the serving API (mmfhe_server, two stream slots:
 a batch's host <-> device copies run under the previous batch's kernels);
 the synchronous mmfhe_eval with host buffers is reported beside it.
 Per-kernel roofline: one extra profiled step with CUDA events around every
-launch (algorithmic bytes from the library).  cpu_baseline: the CPU oracle
-on a time-boxed sample of one window's chain.
+launch (algorithmic bytes from the library).  cpu_baseline: the CPU oracle,
+one whole window's chain per host process.
 
 Multi-GPU: replicas (windows of different users are independent); each rank
 evaluates its own batch, no data-path collective; timing = max over ranks.
@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=None,
                     help="windows per step (per GPU); default 64 (vital), 16 (gesture)")
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--cpu-sample-s", type=float, default=20.0)
+    ap.add_argument("--cpu-sample-s", type=float, default=None,
+                    help="time-box of the CPU oracle baseline per process; default: one whole vital window "
+                         "(gesture: 20 s, a whole gesture window takes the oracle minutes)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--workload", default="vital",
@@ -67,6 +69,12 @@ def parse():
     ap.add_argument("--key-budget-gib", type=float, default=48.0, help="serving workload: resident key budget")
     ap.add_argument("--windows", type=int, default=64, help="batching workload: windows per step")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch-list", action="store_true",
+                    help="vital workload: set-up, warm-up and the timed steps only (no e2e, no profiled step, no CPU "
+                         "baseline), for an ncu launch list whose last launches are the timed steps")
+    ap.add_argument("--learned", type=float, default=None, metavar="B_OVER_A",
+                    help="gesture workload: the learned feature map p + B_OVER_A p^2 (depth 9, two Q primes "
+                         "less) in place of the paper's p (p^2)^2")
     ap.add_argument("--complex-slots", action="store_true",
                     help="vital and gesture workloads: Re + i Im in one complex slot (half the input ciphertexts)")
     ap.add_argument("--tiles", default=None,
@@ -223,8 +231,9 @@ class OracleSample:
         self.total_weight = counter.ks_weight
 
     def run(self, budget_s):
-        """Returns (windows per second, elapsed seconds, completed fraction)."""
-        ev = self.cc.BudgetEvaluator(self.P, self.rlk, self.gks, budget_s)
+        """Returns (windows per second, elapsed seconds, completed fraction);
+        budget_s None: the whole chain."""
+        ev = self.cc.BudgetEvaluator(self.P, self.rlk, self.gks, float("inf") if budget_s is None else budget_s)
         t0 = time.perf_counter()
         try:
             self.circ.run(ev, self.consts, self.s1, self.s2)
@@ -271,7 +280,7 @@ class GestureOracleSample(OracleSample):
         self.total_weight = counter.ks_weight
 
     def run(self, budget_s):
-        ev = self.cc.BudgetEvaluator(self.P, self.rlk, self.gks, budget_s)
+        ev = self.cc.BudgetEvaluator(self.P, self.rlk, self.gks, float("inf") if budget_s is None else budget_s)
         t0 = time.perf_counter()
         try:
             self.circ.run(ev, self.consts, self.pairs)
@@ -310,8 +319,10 @@ def _oracle_sample_worker(job):
 
 def cpu_baseline(kind, budget_s, max_procs=8):
     """The oracle as it stands on the host cores: one single-threaded process
-    per core (up to max_procs), each timing its own window's chain for
-    budget_s; the job's throughput is the sum of the processes' rates."""
+    per core (up to max_procs).  budget_s None: each process evaluates one
+    whole window's chain and times it; otherwise each times the first budget_s
+    of its window's chain.  The job's throughput is the sum of the processes'
+    rates."""
     import multiprocessing as mp
     procs = max(1, min(max_procs, cpu_cores()))
     with mp.get_context("spawn").Pool(procs) as pool:
@@ -320,10 +331,14 @@ def cpu_baseline(kind, budget_s, max_procs=8):
     dt = float(np.mean([r[1] for r in res]))
     frac = float(np.mean([r[2] for r in res]))
     what = "gesture window's" if kind == "gesture" else "window's"
+    if budget_s is None:
+        sample = ("%d processes, each one whole %s chain (%.1f s on average, set-up untimed); throughput summed "
+                  "over the processes" % (procs, what, dt))
+    else:
+        sample = ("%d processes, each the first %.1f s of one %s chain (%.2f%% of its key-switch limb units on "
+                  "average); throughput summed over the processes" % (procs, dt, what, 100 * frac))
     return {"value": rate, "unit": "windows/s", "cores": procs, "kind": "oracle",
-            "host_cores_available": cpu_cores(),
-            "sample": "%d processes, each the first %.1f s of one %s chain (%.2f%% of its key-switch limb units "
-                      "on average); throughput summed over the processes" % (procs, dt, what, 100 * frac)}
+            "host_cores_available": cpu_cores(), "sample": sample}
 
 
 def cpu_cores():
@@ -333,30 +348,35 @@ def cpu_cores():
         return os.cpu_count()
 
 
+def _reference_step(seed):
+    """One step of the reference arm: the oracle's set-up (untimed), then one
+    whole window's chain, timed."""
+    return OracleSample(seed).run(None)
+
+
 def run_reference(args, rank, world):
-    """The oracle as it stands, on the host cores: K bounded samples."""
+    """The oracle as it stands, on the host cores: K steps, each one whole
+    window's chain on one core, run concurrently (one spawned process per
+    step, up to the host's cores at a time)."""
     if rank != 0:
         return
-    t_setup = time.perf_counter()
-    sample = OracleSample()
-    setup_s = time.perf_counter() - t_setup
-    per_step = max(5.0, min(30.0, 150.0 / (args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        sample.run(per_step / 4)
-    vals, times = [], []
-    for _ in range(args.steps):
-        v, dt, frac = sample.run(per_step)
-        vals.append(v)
-        times.append(dt)
-    value = float(np.mean(vals))
+    import multiprocessing as mp
+    procs = max(1, min(args.steps, cpu_cores()))
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(procs) as pool:
+        res = pool.map(_reference_step, [4242 + 17 * i for i in range(args.steps)])
+    wall = time.perf_counter() - t0
+    times = [r[1] for r in res]
+    value = float(np.mean([1.0 / t for t in times]))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean(times)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "batch_windows": 1, "parallelism": "single-threaded CPU oracle"},
+        "config": {"workload": WORKLOAD, "batch_windows": 1, "parallelism": "single-threaded CPU oracle per step"},
         "cpu_baseline": {"value": value, "unit": "windows/s", "cores": 1, "kind": "oracle",
-                         "sample": "first %.0f s of one window's chain per step, progress in key-switch limb units "
-                                   "(setup %.0f s untimed)" % (per_step, setup_s)},
+                         "sample": "each step one whole window's chain on one core (set-up untimed); %d steps run "
+                                   "concurrently on %d cores, %.0f s wall; warm-up steps are not run (the oracle "
+                                   "has nothing to warm)" % (args.steps, procs, wall)},
         "e2e": {"value": value, "unit": "windows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -509,6 +529,7 @@ def run_mine(args, rank, world, local):
     torch.cuda.synchronize()
 
     # ---- timed region: device-resident ----
+    ctx.mem_peak_reset()
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = ctx.launch_count()
@@ -525,8 +546,13 @@ def run_mine(args, rank, world, local):
     barrier(world)
     launches = ctx.launch_count() - launches0
     clk = clocks.stop()
+    mem = ctx.mem_stats()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     value = job_throughput(world, B * args.steps, sum(step_ms) / 1000.0)
+    if args.launch_list:
+        return {"metric": METRIC, "value": value, "unit": "windows/s", "launch_list_run": True, "batch_windows": B,
+                "steps": args.steps, "launches_per_step": launches // max(1, args.steps),
+                "launches_total": ctx.launch_count(), "ms_per_step": float(np.mean(step_ms))}
 
     # ---- e2e: pinned host buffers, host <-> device copies inside the timed region ----
     pin_in = [torch.from_numpy(x.view(np.int64)).pin_memory() for x in host_in]
@@ -584,12 +610,43 @@ def run_mine(args, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%d MiB of ciphertexts per step)" % (B * in_words * 8 >> 20),
                    "tiles": tiles},
-        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                       "note": "latency of a window = its batch's step time"},
+        "latency_ms": {"p50": srv_stats["p50_ms"], "p99": srv_stats["p99_ms"],
+                       "note": "per window, submit to output written, through mmfhe_server in the e2e run "
+                               "(%d windows)" % (B * e2e_steps),
+                       "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))}},
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk,
+        "memory": memory_line(mem, B, "5.3 GB peak cloud GPU memory per batched vital window (paper Table 5, "
+                                      "RTX 3090 Ti)"),
+        "accuracy": accuracy_line(),
         "wall_s_timed": wall,
     }
     return line
+
+
+def memory_line(mem, batch, paper):
+    """Device memory the library held over the timed region (its own
+    accounting: contexts, keys, plan constants, scratch pools)."""
+    return {"peak_gib": mem["peak_bytes"] / 2.0 ** 30, "held_after_gib": mem["device_bytes"] / 2.0 ** 30,
+            "per_window_gib": mem["peak_bytes"] / 2.0 ** 30 / batch, "batch_windows": batch,
+            "source": "mmfhe_mem_stats_get high-water mark, reset before the timed steps", "paper": paper}
+
+
+ACCURACY_PROFILE = os.path.join("profiles", "accuracy_vital_64_windows.json")
+
+
+def accuracy_line():
+    """Decrypted rates against the FP64 pipeline over 64 seeded windows, from
+    the committed record of tests/test_gpu_accuracy.py (the bench's own
+    windows are uniform words, which decrypt to nothing)."""
+    p = os.path.join(ROOT, ACCURACY_PROFILE)
+    if not os.path.exists(p):
+        return None
+    j = json.load(open(p))
+    keys = ("windows", "inside_precision_window", "below_floor", "above_ceiling", "mae_bpm_inside",
+            "max_bpm_inside", "max_err_target_bin")
+    out = {k: j[k] for k in keys if k in j}
+    out["source"] = ACCURACY_PROFILE + " (tests/test_gpu_accuracy.py, B = 64, seeds 4000..4063)"
+    return out
 
 
 # Uneven windows: whole-second lengths between 5 and 20 s at 20 frames/s; six
@@ -1126,9 +1183,11 @@ def run_gesture(args, rank, world, local):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    params = M.gesture_params()
+    learned = args.learned is not None
+    coef = (1.0, args.learned) if learned else None
+    params = M.gesture_params(learned=learned)
     ctx = M.Context(params, device=local)
-    plan = ctx.plan(M.gesture_config(complex_slots=args.complex_slots))
+    plan = ctx.plan(M.gesture_config(complex_slots=args.complex_slots, feature_coef=coef))
     plan.encode_consts()
     for l, W in enumerate(gesture_random_mats(GestureShape, 11)):
         plan.set_fc_layer(l, W)
@@ -1166,6 +1225,7 @@ def run_gesture(args, rank, world, local):
     for _ in range(args.warmup):
         step(d_in, d_out)
     torch.cuda.synchronize()
+    ctx.mem_peak_reset()
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = ctx.launch_count()
@@ -1182,10 +1242,13 @@ def run_gesture(args, rank, world, local):
     barrier(world)
     launches = ctx.launch_count() - launches0
     clk = clocks.stop()
+    mem = ctx.mem_stats()
     step_ms = [a.elapsed_time(b) for a, b in ev]
     value = job_throughput(world, B * args.steps, sum(step_ms) / 1000.0)
-    # e2e: one synchronous mmfhe_eval per step on pinned host buffers (copies in, evaluation, copies
-    # out in sequence).  The two-slot serving API would hold two batches' scratch at once.
+    # e2e: (a) one synchronous mmfhe_eval per step on pinned host buffers (copies in, evaluation,
+    # copies out in sequence); (b) the serving API with two stream slots, the next batch's copies
+    # under this batch's kernels (the feature stage runs in chunks of whole windows, so two
+    # batches' scratch fit beside each other)
     pin_one = torch.from_numpy(host.view(np.int64)).pin_memory()
     pin_in = [pin_one] * B            # the windows of a step share one pinned input (read only)
     pin_out = [torch.empty(out_words, dtype=torch.int64).pin_memory() for _ in range(B)]
@@ -1196,9 +1259,35 @@ def run_gesture(args, rank, world, local):
     for _ in range(args.e2e_steps):
         step(pin_in, pin_out)
     torch.cuda.synchronize()
-    e2e = {"value": job_throughput(world, B * args.e2e_steps, time.perf_counter() - t0), "unit": "windows/s",
+    e2e_sync = job_throughput(world, B * args.e2e_steps, time.perf_counter() - t0)
+    gcfg = M.gesture_config(complex_slots=args.complex_slots, feature_coef=coef)
+    srv = ctx.server(gcfg, max_batch=B, streams=2, batch_wait_us=20000)
+    for l, W in enumerate(gesture_random_mats(GestureShape, 11)):
+        srv.set_fc_layer(l, W)
+    srv.add_user(rank, relin_w, gal_w)
+    e2e_steps = max(4, args.e2e_steps)
+    outs_ring = [[torch.empty(out_words, dtype=torch.int64).pin_memory() for _ in range(B)] for _ in range(2)]
+    for w in range(B):   # warm-up: the server's plan, key upload and pools
+        srv.submit(rank, gcfg.frames, pin_in[w], outs_ring[0][w])
+    srv.drain()
+    barrier(world)
+    t0 = time.perf_counter()
+    for s_ in range(e2e_steps):
+        for w in range(B):
+            srv.submit(rank, gcfg.frames, pin_in[w], outs_ring[s_ % 2][w])
+    srv.drain()
+    e2e_pipe_s = time.perf_counter() - t0
+    srv_stats = srv.stats()
+    srv.close()
+    if srv_stats["failed"] or srv_stats["completed"] != srv_stats["submitted"]:
+        raise RuntimeError("gesture serving e2e: %d of %d windows failed" % (srv_stats["failed"], srv_stats["submitted"]))
+    e2e = {"value": job_throughput(world, B * e2e_steps, e2e_pipe_s), "unit": "windows/s",
            "h2d_bytes_per_step": B * in_words * 8, "d2h_bytes_per_step": B * out_words * 8,
-           "api": "mmfhe_eval on pinned host buffers (copies in, evaluation, copies out in sequence)"}
+           "api": "mmfhe_server (2 stream slots, batches of %d filled within 20 ms, copies overlap the previous "
+                  "batch's kernels)" % B,
+           "mean_batch": srv_stats["mean_batch"],
+           "synchronous_mmfhe_eval": {"value": e2e_sync, "unit": "windows/s"}}
+    mem_srv = ctx.mem_stats()
     ctx.profile(True)
     step(d_in, d_out)
     torch.cuda.synchronize()
@@ -1213,15 +1302,22 @@ def run_gesture(args, rank, world, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": GESTURE_WORKLOAD + (", complex-slot packing (Re + i Im in one slot, 30 input cts)"
-                                                   if args.complex_slots else ""),
+                                                   if args.complex_slots else "")
+                   + (", learned feature map p + %g p^2 (depth 9, Q = 60 + 9 x 50 bits) in place of p (p^2)^2"
+                      % args.learned if learned else ""),
                    "batch_windows": B, "windows_per_step_all_gpus": world * B,
                    "parallelism": "replicas" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2 (%d MiB of ciphertexts per step)" % (B * in_words * 8 >> 20),
                    "weights": "random-init FC weights of the network's shape", "tiles": tiles},
-        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99)),
-                       "note": "latency of a window = its batch's step time"},
+        "latency_ms": {"p50": srv_stats["p50_ms"], "p99": srv_stats["p99_ms"],
+                       "note": "per window, submit to output written, through mmfhe_server in the e2e run "
+                               "(%d windows)" % (B * e2e_steps),
+                       "step_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))}},
         "paper_context": "5.76 s per 3 s gesture window on one RTX 3090 Ti (FIDESlib), batched packing",
         "e2e": e2e, "gpu_launches": launches, "roofline": roofline, "clocks": clk, "wall_s_timed": wall,
+        "memory": dict(memory_line(mem, B, "7.5 GB peak cloud GPU memory per batched gesture window (paper Table "
+                                           "5, RTX 3090 Ti)"),
+                       peak_with_two_serving_slots_gib=mem_srv["peak_bytes"] / 2.0 ** 30),
     }
 
 
@@ -1252,12 +1348,12 @@ def main():
     if args.workload == "gesture":
         line = run_gesture(args, rank, world, local)
         if rank == 0 and world == 1 and not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline("gesture", args.cpu_sample_s)
+            line["cpu_baseline"] = cpu_baseline("gesture", args.cpu_sample_s or 20.0)
         if rank == 0:
             print(json.dumps(line), flush=True)
         return
     line = run_mine(args, rank, world, local)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.launch_list:
         line["cpu_baseline"] = cpu_baseline("vital", args.cpu_sample_s)
     if rank == 0:
         print(json.dumps(line), flush=True)

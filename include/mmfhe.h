@@ -268,6 +268,24 @@ mmfhe_status mmfhe_ct_bsgs(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out
                            uint32_t level, int32_t stride, uint32_t n1, const uint32_t *deltas,
                            const uint64_t *const *diags, size_t num_diags, void *stream);
 
+/* Double-hoisted BSGS product (Bossuat, Mouchet, Troncoso-Pastoriza and
+ * Hubaux, Eurocrypt 2021, Sec. 4; the paper's hoisting of rotations, Sec.
+ * "Discussion"): out = sum_g Rot( sum_{s, b} D'_{s,g,b} (.) Rot(in, b*stride
+ * + offsets[s]), g*n1*stride ) over num_sets baby sets of the same input.
+ * Diagonal i belongs to set set_of[i], delta = deltas[i] = g*n1 + b, diags[i]
+ * = its pre-rotated encoding over Q_level (uint64[level+1][N], coefficient
+ * form; the library extends it to the special primes from the centered
+ * residues mod q_0, so coefficients must be below q_0 / 2 in magnitude,
+ * BAD_ARG otherwise).  The baby rotations share one ModUp and stay in the
+ * extended basis Q_level * P with their inner sums; a giant step brings only
+ * the c1 of its inner sum down to Q_level for its key switch; one ModDown
+ * ends the product.  The words differ from mmfhe_ct_bsgs's (other rounding).
+ * Not rescaled.  Errors: BAD_ARG, LEVEL_MISMATCH, NOT_FOUND. */
+mmfhe_status mmfhe_ct_bsgs_dh(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out, const uint64_t *in, size_t batch,
+                              uint32_t level, int32_t stride, uint32_t n1, uint32_t num_sets, const int32_t *offsets,
+                              const uint32_t *set_of, const uint32_t *deltas, const uint64_t *const *diags,
+                              size_t num_diags, void *stream);
+
 /* ------------------------------------------------------------------------
  * Circuits (plans).  A plan holds a circuit's public configuration
  * (Sec. "Leakage Profile": R, F, filter order, Taylor order, ...) and its
@@ -331,7 +349,18 @@ typedef struct mmfhe_circuit_config {
                                   per group; K4 gives I + i Q, one FIR product per band, K7 from
                                   w = Z conj(Z at t-1), the phase from w^3 - conj(w^3) = 2i Im(w^3) */
     double input_scale;        /* encryption scale Delta of the inputs */
+    /* GESTURE: the feature map between the notch and the frame accumulation.
+     * MMFHE_FEATURE_POWER (0): the paper's soft power gamma = 4 and feature
+     * weighting, f = p w with w = p^4 (degree 5, three levels; Table 1).
+     * MMFHE_FEATURE_LEARNED (1): f = a p + b p^2 with (a, b) = feature_coef,
+     * learned together with the network (one level): the chain needs two
+     * levels less, so its parameter set has two Q primes less.  Output level
+     * top - 11 (power) or top - 9 (learned). */
+    uint32_t feature_map;
+    double feature_coef[2];
 } mmfhe_circuit_config;
+#define MMFHE_FEATURE_POWER 0
+#define MMFHE_FEATURE_LEARNED 1
 
 /* Constant tags of mmfhe_const_key.tag */
 #define MMFHE_CONST_IDX 1   /* side branch: bin-index vector of group `index` */
@@ -355,6 +384,9 @@ typedef struct mmfhe_circuit_config {
                                   the scale of FC1's rescaled output */
 #define MMFHE_CONST_GDFT_W 17  /* GESTURE with complex slots: the complex W Doppler diagonal delta =
                                   index - D (pre-rotated), encoded as complex slots */
+#define MMFHE_CONST_NOTCH_B 18 /* GESTURE, learned feature map: b times the notch mask */
+#define MMFHE_CONST_FEAT_A 19  /* GESTURE, learned feature map: a on every active slot, encoded at the
+                                  scale of the notched power (one level below the notch) */
 
 typedef struct mmfhe_const_key {
     uint32_t tag, band, index, level;

@@ -18,7 +18,10 @@ G = ceil(R / R_c) ciphertexts per real/imaginary part; padding is zero.
 Readings of passages the paper leaves open (each restated in the design
 notes): constants are encoded at scale q_l of the level they multiply so the
 rescale returns the ciphertext scale; BSGS baby steps are hoisted, giant steps
-are ordinary rotations, one rescale follows each matrix product; products that
+are ordinary rotations, one rescale follows each matrix product -- except the
+vital chain's FIR and DFT products, which are double-hoisted (babies, inner
+sums and giant-step terms in the extended basis Q*P, one ModDown at the end,
+diagonals encoded over Q*P; Bossuat et al., Eurocrypt 2021, Sec. 4); products that
 are summed share one relinearization (lazy relinearization); the 1/3 of the
 third-order Taylor term is realised as 3 x^2 - y^2 (exact integer multiply)
 with the 1/3 folded into the DFT constants; the DFT of the vital chain keeps
@@ -303,6 +306,21 @@ class Evaluator:
         return acc
 
 
+    def bsgs_dh(self, sets, consts, n1, stride):
+        """The double-hoisted BSGS product (A9; Bossuat, Mouchet,
+        Troncoso-Pastoriza and Hubaux, Eurocrypt 2021, Sec. 4): baby set
+        `name` holds Rot(x_name, b stride + off_name) for
+        ``sets[name] = (x_name, off_name)``; ``consts[(name, delta)]`` =
+        pre-rotated diagonal D'_{g,b} encoded over Q*P (delta = g n1 + b).
+        Babies, inner sums and giant-step terms stay in the extended basis;
+        one ModDown ends the product.  Not rescaled."""
+        level = next(iter(sets.values()))[0].level
+        for (name, delta) in sorted(consts):
+            self._t("mul_plain_qp", level, name, delta)
+        self._t("bsgs_dh", level, tuple(sorted((n, o) for n, (_, o) in sets.items())), n1, stride)
+        return ck.bsgs_double_hoisted_sets(self.P, sets, consts, n1, stride, self.gks)
+
+
 class _Shape:
     """Level/scale stand-in for a ciphertext in a counting run."""
 
@@ -310,11 +328,18 @@ class _Shape:
         self.level, self.scale = level, scale
 
 
+def _scale_of(x):
+    """Scale of a stand-in or constant; a constant left out of a counting run
+    (None) counts as scale 1."""
+    return 1.0 if x is None else x.scale
+
+
 class CountingEvaluator(Evaluator):
     """Runs a circuit without computing it: every operation returns a
-    level-tracking stand-in and key switches are tallied, each weighted by
-    the number of limbs it touches (level + 1 + K).  Used to size a bounded
-    sample of the oracle's work."""
+    level- and scale-tracking stand-in and key switches are tallied, each
+    weighted by the number of limbs it touches (level + 1 + K).  Used to
+    size a bounded sample of the oracle's work, and for the output scales
+    of a circuit (the scale arithmetic of the real evaluator)."""
 
     def __init__(self, P):
         super().__init__(P, None, None)
@@ -325,52 +350,66 @@ class CountingEvaluator(Evaluator):
         self.ks_weight += n * (level + 1 + self.K)
 
     def tensor(self, a, b):
-        return _Shape(a.level)
+        return _Shape(a.level, a.scale * b.scale)
 
     def relin(self, t):
         self._ks(t.level)
-        return _Shape(t.level)
+        return _Shape(t.level, t.scale)
 
     def rescale(self, a):
-        return _Shape(a.level - 1)
+        return _Shape(a.level - 1, a.scale / self.P.q[a.level])
 
     def rotate(self, a, k):
         if ck.key_id(self.P, k):
             self._ks(a.level)
-        return _Shape(a.level)
+        return _Shape(a.level, a.scale)
 
     def conjugate(self, a):
         self._ks(a.level)
-        return _Shape(a.level)
+        return _Shape(a.level, a.scale)
 
     def hoisted(self, a, ks):
         self._ks(a.level, sum(1 for k in ks if ck.key_id(self.P, k)))
-        return [_Shape(a.level) for _ in ks]
+        return [_Shape(a.level, a.scale) for _ in ks]
 
     def add(self, a, b):
-        return _Shape(a.level)
+        return _Shape(a.level, a.scale)
 
     def add_plain(self, a, pt):
-        return _Shape(a.level)
+        return _Shape(a.level, a.scale)
 
     sub = add
 
     def mul_plain(self, a, pt):
-        return _Shape(a.level)
+        return _Shape(a.level, a.scale * _scale_of(pt))
 
     def drop(self, a, level):
-        return _Shape(level)
+        return _Shape(level, a.scale)
 
     def tensor_add(self, x, y):
-        return _Shape(x.level)
+        return _Shape(x.level, x.scale)
 
     tensor_sub = tensor_add
 
     def tensor_mul_int(self, x, k):
-        return _Shape(x.level)
+        return _Shape(x.level, x.scale)
 
     def mul_plain_sum(self, pairs):
-        return _Shape(pairs[0][0].level)
+        return _Shape(pairs[0][0].level, pairs[0][0].scale * _scale_of(pairs[0][1]))
+
+    def bsgs_dh(self, sets, consts, n1, stride):
+        x = next(iter(sets.values()))[0]
+        self._ks(x.level, dh_key_switches(self.P, sets, consts, n1, stride))
+        return _Shape(x.level, x.scale * _scale_of(next(iter(consts.values()))))
+
+
+def dh_key_switches(P, sets, consts, n1, stride):
+    """Key switches of a double-hoisted BSGS product: one per distinct
+    baby rotation and one per giant step with a nonzero rotation."""
+    babies = {(name, d - (d // n1) * n1) for name, d in consts}
+    n = sum(1 for name, b in babies if ck.key_id(P, b * stride + sets[name][1]))
+    n += sum(1 for g in {d // n1 for _, d in consts} if ck.key_id(P, g * n1 * stride))
+    return n
 
 
 class SampleBudgetExceeded(Exception):
@@ -417,6 +456,12 @@ class BudgetEvaluator(Evaluator):
         self._check()
         r = super().conjugate(a)
         self.ks_weight += a.level + 1 + self.K
+        return r
+
+    def bsgs_dh(self, sets, consts, n1, stride):
+        self._check()
+        r = super().bsgs_dh(sets, consts, n1, stride)
+        self.ks_weight += (r.level + 1 + self.K) * dh_key_switches(self.P, sets, consts, n1, stride)
         return r
 
 
@@ -680,11 +725,13 @@ class VitalCircuit:
                     one[lay.slot(0, r)] = 1.0
             out[("idx", c)] = ck.encode(P, idx, P.q[lv], lv)
             out[("one", c)] = ck.encode(P, one, P.q[lv], lv)
+        # the FIR and DFT diagonals multiply double-hoisted baby steps, which
+        # live in the extended basis: encoded over Q_l * P
         lv = self.lv_fir
         for b in range(len(self.bands)):
             for k, v in self.fir_diagonals(b).items():
                 v = prerotate(v, k // self.n1_fir, self.n1_fir, -lay.r_c)
-                out[("fir", b, k)] = ck.encode(P, v, P.q[lv], lv)
+                out[("fir", b, k)] = ck.encode_qp(P, v, P.q[lv], lv)
         lv = self.lv_dphi
         diags = {}
         for b in range(len(self.bands)):
@@ -693,7 +740,7 @@ class VitalCircuit:
                 diags[delta] = diags.get(delta, 0.0) + np.roll(v, b)
         for delta, v in diags.items():
             v = prerotate(v, delta // self.n1_dft, self.n1_dft, lay.r_c)
-            out[("dft", delta)] = ck.encode(P, v, P.q[lv], lv)
+            out[("dft", delta)] = ck.encode_qp(P, v, P.q[lv], lv)
         lv = self.lv_final_const
         fs_hz = cfg.fs_mhz / 1000
         fw, fo = np.zeros(lay.slots), np.zeros(lay.slots)
@@ -745,9 +792,9 @@ class VitalCircuit:
             iq.append(ev.rotsum(ev.rescale(ev.relin(t)), 1, lay.r_c))
         I, Q = iq
 
-        # K5 FIR of both bands in one BSGS product per part: the baby steps
-        # of I (and Q) are hoisted once, unshifted for RR (output in bin
-        # slot 0) and shifted by one slot for HR (output in slot 1)
+        # K5 FIR of both bands in one double-hoisted BSGS product per part:
+        # the baby steps of I (and Q) share one ModUp, unshifted for RR
+        # (output in bin slot 0) and shifted by one slot for HR (slot 1)
         n1 = self.n1_fir
         fir = {}
         for b in range(len(self.bands)):
@@ -755,10 +802,8 @@ class VitalCircuit:
                 fir[("s%d" % b, k)] = consts[("fir", b, k)]
         filtered = []
         for x in (I, Q):
-            rots = [-j * lay.r_c - s for s in (0, 1) for j in range(n1)]
-            hs = ev.hoisted(x, rots)
-            babies = {"s0": dict(zip(range(n1), hs[:n1])), "s1": dict(zip(range(n1), hs[n1:]))}
-            filtered.append(ev.rescale(ev.bsgs(babies, fir, n1, -lay.r_c, x.level)))
+            sets = {"s0": (x, 0), "s1": (x, -1)}
+            filtered.append(ev.rescale(ev.bsgs_dh(sets, fir, n1, -lay.r_c)))
         If, Qf = filtered
         # K7 differential phase, both bands slot by slot
         If1 = ev.rotate(If, -lay.r_c)
@@ -776,9 +821,7 @@ class VitalCircuit:
         # K3 narrowband DFT (both bands, each in its bin slot), |X|^2
         n1 = self.n1_dft
         cl = {("x", key[1]): pt for key, pt in consts.items() if key[0] == "dft"}
-        need = sorted({d % n1 for (_, d) in cl})
-        babies = {"x": dict(zip(need, ev.hoisted(dphi, [bb * lay.r_c for bb in need])))}
-        X = ev.rescale(ev.bsgs(babies, cl, n1, lay.r_c, dphi.level))
+        X = ev.rescale(ev.bsgs_dh({"x": (dphi, 0)}, cl, n1, lay.r_c))
         pw = ev.rescale(ev.square_sum([X]))
         # Re^2 at k, Im^2 at k + F_pad/2: one rotation adds them
         Mg = ev.add(pw, ev.rotate(pw, (lay.f_pad // 2) * lay.r_c))
@@ -831,9 +874,7 @@ class VitalCircuit:
         for b in range(len(self.bands)):
             for k in range(cfg.taps):
                 fir[("s%d" % b, k)] = consts[("fir", b, k)]
-        hs = ev.hoisted(Z, [-j * lay.r_c - s for s in (0, 1) for j in range(n1)])
-        babies = {"s0": dict(zip(range(n1), hs[:n1])), "s1": dict(zip(range(n1), hs[n1:]))}
-        Zf = ev.rescale(ev.bsgs(babies, fir, n1, -lay.r_c, Z.level))
+        Zf = ev.rescale(ev.bsgs_dh({"s0": (Z, 0), "s1": (Z, -1)}, fir, n1, -lay.r_c))
 
         # K7: w = Zf conj(Zf at t-1) = x + i y
         wc = ev.rescale(ev.relin(ev.tensor(Zf, ev.conjugate(ev.rotate(Zf, -lay.r_c)))))
@@ -847,9 +888,7 @@ class VitalCircuit:
         # K3, |X|^2 (negated by the i), sharpen, weighted frequency average
         n1 = self.n1_dft
         cl = {("x", key[1]): pt for key, pt in consts.items() if key[0] == "dft"}
-        need = sorted({d % n1 for (_, d) in cl})
-        babies = {"x": dict(zip(need, ev.hoisted(dphi, [bb * lay.r_c for bb in need])))}
-        X = ev.rescale(ev.bsgs(babies, cl, n1, lay.r_c, dphi.level))
+        X = ev.rescale(ev.bsgs_dh({"x": (dphi, 0)}, cl, n1, lay.r_c))
         pw = ev.rescale(ev.square_sum([X]))
         Mg = ev.add(pw, ev.rotate(pw, (lay.f_pad // 2) * lay.r_c))
         S = ev.rescale(ev.square_sum([Mg]))
@@ -1083,6 +1122,14 @@ class GestureConfig:
     fc_dims: tuple = (31, 16, 6)  # d_1, d_2, classes (d_0 = A R D feature slots)
     width: int = 32             # slot period of the FC layers after FC1
     complex_slots: bool = False # Re + i Im in one complex slot: one ciphertext per frame group
+    # feature map between the notch and the frame accumulation: None = the
+    # paper's soft power gamma = 4 and weighting f = p (p^2)^2 (three levels);
+    # (a, b) = the learned f = a p + b p^2 (one level)
+    feature_coef: tuple = None
+
+    @property
+    def feature_depth(self):
+        return 3 if self.feature_coef is None else 1
 
     @property
     def ard(self):
@@ -1138,7 +1185,7 @@ class GestureCircuit:
         self.lay = GestureLayout(P.slots, cfg)
         D, W = cfg.chirps, cfg.width
         assert W & (W - 1) == 0 and max(cfg.fc_dims) < W and W <= self.lay.ard_pad
-        assert len(cfg.fc_dims) == 3 and P.L >= 11, "depth-11 chain"
+        assert len(cfg.fc_dims) == 3
         self.n1, _ = bsgs_split(2 * D)           # K3: deltas -(D-1) .. D-1
         self.deltas = list(range(-(D - 1), D))
         self.nf1, _ = bsgs_split(W)              # FC layers
@@ -1150,9 +1197,12 @@ class GestureCircuit:
         L = P.L
         # levels (Table 1): K3 L->L-1, |z|^2 ->L-2, notch ->L-3, two squares
         # ->L-5, weighting ->L-6, FC1 ->L-7, square ->L-8, FC2 ->L-9, square
-        # ->L-10, FC3 ->L-11
-        self.lv_dft, self.lv_notch, self.lv_fc1 = L, L - 2, L - 6
-        self.lv_fc = [L - 6, L - 8, L - 10]
+        # ->L-10, FC3 ->L-11; the learned feature map a p + b p^2 takes one
+        # level instead of three (features at L-4, logits at L-9)
+        lf = L - 3 - cfg.feature_depth
+        assert lf - 5 >= 0, "not enough levels for the gesture chain"
+        self.lv_dft, self.lv_notch, self.lv_fc1 = L, L - 2, lf
+        self.lv_fc = [lf, lf - 2, lf - 4]
 
     # -- public constants --------------------------------------------------
     def doppler_diagonal(self, M, delta):
@@ -1168,8 +1218,12 @@ class GestureCircuit:
 
     def fc1_diagonal(self, W0, k):
         """Extended diagonal k of FC1 (W0: width x (A R D), no bias column):
-        diag_k[s] = W0[s mod width][(s + k) mod ARD_pad] (zero on padding
-        columns and on row width-1, the constant's slot)."""
+        diag_k[s] = W0[s mod width][(s + k) mod ARD_pad], zero on padding
+        columns and on row width-1.  Slot width-1 of every period carries the
+        constant 1 that the later layers read as their bias input (the FC
+        layers of Sec. "Encrypted ML Inference" fold the bias into the
+        matrix); FC1's own bias vector, with that 1 in slot width-1, is added
+        after the rescale, so FC1's product must leave the slot empty."""
         P, cfg, n = self.P, self.cfg, self.lay.ard_pad
         s = np.arange(P.slots)
         col = (s + k) % n
@@ -1178,14 +1232,22 @@ class GestureCircuit:
         v[ok] = W0[s[ok] % cfg.width, col[ok]]
         return v
 
-    def fc1_out_scale(self, scale_in):
-        """Scale of FC1's rescaled output, following the evaluator's scale
-        arithmetic step by step (products multiply scales, a rescale at
-        level l divides by q_l, constants carry scale q_l)."""
+    def notch_scale(self, scale_in):
+        """Scale of the notched power, following the evaluator's scale
+        arithmetic (products multiply scales, a rescale at level l divides
+        by q_l, constants carry scale q_l)."""
         q, L = self.P.q, self.P.L
         s = scale_in * q[L] / q[L]                 # K3
         s = s * s / q[L - 1]                       # |z|^2
-        p = s * q[L - 2] / q[L - 2]                # notch
+        return s * q[L - 2] / q[L - 2]             # notch
+
+    def fc1_out_scale(self, scale_in):
+        """Scale of FC1's rescaled output (the same arithmetic)."""
+        q, L = self.P.q, self.P.L
+        p = self.notch_scale(scale_in)
+        if self.cfg.feature_coef is not None:
+            f = p * p / q[L - 3]                   # (notched p) x (b p + a)
+            return f * q[L - 4] / q[L - 4]         # FC1
         w = p * p / q[L - 3]
         w = w * w / q[L - 4]                       # gamma = 4
         f = p * w / q[L - 5]                       # weighting
@@ -1210,6 +1272,12 @@ class GestureCircuit:
                 out[(tag, delta)] = ck.encode(P, v, q[L], L)
         m = np.tile(notch_mask(cfg.chirps), P.slots // cfg.chirps) * self.lay.active()
         out[("notch",)] = ck.encode(P, m, q[L - 2], L - 2)
+        if cfg.feature_coef is not None:
+            a, b = cfg.feature_coef
+            out[("notch_b",)] = ck.encode(P, b * m, q[L - 2], L - 2)
+            # a joins the product b p by addition: encoded at that ciphertext's scale
+            scale_in = P.scale if scale_in is None else scale_in
+            out[("feat_a",)] = ck.encode(P, a * self.lay.active(), self.notch_scale(scale_in), L - 3)
         W0 = np.asarray(mats[0], dtype=np.float64)
         assert W0.shape == (cfg.width, cfg.ard + 1)
         lv = self.lv_fc[0]
@@ -1239,9 +1307,10 @@ class GestureCircuit:
 
     # -- the circuit ---------------------------------------------------------
     def features(self, ev, consts, pairs):
-        """K3 -> K1 -> K6 -> soft power -> weighting per pair, then the
-        accumulation over every frame; returns the feature ciphertext
-        (every frame position of it holds the sum) at level L - 6.  pairs:
+        """K3 -> K1 -> K6 -> soft power -> weighting (or the learned feature
+        map) per pair, then the accumulation over every frame; returns the
+        feature ciphertext (every frame position of it holds the sum) at
+        level L - 6 (learned: L - 4).  pairs:
         (re, im) ciphertexts, or with complex slots one ciphertext each."""
         acc = None
         for pair in pairs:
@@ -1266,6 +1335,13 @@ class GestureCircuit:
                 d_re = ev.rescale(ev.bsgs(babies, c_re, self.n1, 1, re.level))
                 d_im = ev.rescale(ev.bsgs(babies, c_im, self.n1, 1, re.level))
                 p = ev.rescale(ev.square_sum([d_re, d_im]))            # K1
+            if self.cfg.feature_coef is not None:
+                # learned map a p + b p^2 = (notched p) x (b notched p + a), one level
+                pb = ev.add_plain(ev.rescale(ev.mul_plain(p, consts[("notch_b",)])), consts[("feat_a",)])
+                pn = ev.rescale(ev.mul_plain(p, consts[("notch",)]))   # K6
+                f = ev.rescale(ev.relin(ev.tensor(pn, pb)))
+                acc = f if acc is None else ev.add(acc, f)
+                continue
             p = ev.rescale(ev.mul_plain(p, consts[("notch",)]))    # K6
             w = ev.rescale(ev.square_sum([p]))                     # K2, gamma = 4
             w = ev.rescale(ev.square_sum([w]))

@@ -633,34 +633,55 @@ def bsgs_double_hoisted(P, a, diags, n1, stride, gks):
     ``diags``: {delta: Plaintext over Q_level * P (encode_qp)}, delta =
     g n1 + b with 0 <= b < n1 (floor division), each pre-rotated by
     -g n1 stride as in the single-hoisted product."""
-    level = a.level
+    return bsgs_double_hoisted_sets(P, {"x": (a, 0)}, {("x", d): pt for d, pt in diags.items()}, n1, stride, gks)
+
+
+def bsgs_double_hoisted_sets(P, sets, diags, n1, stride, gks):
+    """The double-hoisted product over several baby sets sharing the giant
+    steps: set `name` holds the baby rotations Rot(x_name, b stride + off_name)
+    of its input ``sets[name] = (x_name, off_name)``, and
+
+      result = sum_g Rot_{g n1 stride}( sum_{name, b} D'_{name,g,b} (.) baby_{name,b} ),
+
+    every baby, inner sum and giant-step term over Q_level * P as in
+    ``bsgs_double_hoisted`` (one ModUp of c1 per distinct input ciphertext,
+    shared by all its babies; one ModDown of each part at the end).
+    ``diags``: {(name, delta): Plaintext over Q_level * P}, delta = g n1 + b,
+    0 <= b < n1, pre-rotated by -g n1 stride."""
+    level = next(iter(sets.values()))[0].level
     prq, prqp = q_primes(P, level), qp_primes(P, level)
     groups = {}
-    for d in sorted(diags):
-        groups.setdefault(d // n1, []).append(d)
-    need = sorted({d - (d // n1) * n1 for d in diags})
-    digits = modup(P, a.c1, level)
+    for key in sorted(diags):
+        groups.setdefault(key[1] // n1, []).append(key)
+    digits = {}
     babies = {}
-    for b in need:
-        k = b * stride
-        if key_id(P, k) == 0:
-            babies[b] = (times_p(P, a.c0, level), times_p(P, a.c1, level))
+    for name, d in sorted(diags):
+        b = d - (d // n1) * n1
+        if (name, b) in babies:
             continue
+        x, off = sets[name]
+        assert x.level == level
+        k = b * stride + off
+        if key_id(P, k) == 0:
+            babies[(name, b)] = (times_p(P, x.c0, level), times_p(P, x.c1, level))
+            continue
+        if id(x) not in digits:
+            digits[id(x)] = modup(P, x.c1, level)
         g = galois_element(P, k)
-        u0, u1 = inner_product(P, [ring_automorphism(y, g, prqp) for y in digits], gks[key_id(P, k)], level)
-        babies[b] = (ring_add(times_p(P, ring_automorphism(a.c0, g, prq), level), u0, prqp), u1)
+        u0, u1 = inner_product(P, [ring_automorphism(y, g, prqp) for y in digits[id(x)]], gks[key_id(P, k)], level)
+        babies[(name, b)] = (ring_add(times_p(P, ring_automorphism(x.c0, g, prq), level), u0, prqp), u1)
     acc0 = acc1 = None
     scale = None
     for gi in sorted(groups):
         in0 = np.zeros((len(prqp), P.n), dtype=np.uint64)
         in1 = np.zeros((len(prqp), P.n), dtype=np.uint64)
-        for d in groups[gi]:
-            pt = diags[d]
+        for name, d in groups[gi]:
+            pt = diags[(name, d)]
             assert pt.level == level and pt.m.shape[0] == len(prqp)
-            b0, b1 = babies[d - gi * n1]
+            b0, b1 = babies[(name, d - gi * n1)]
             in0 = ring_add(in0, ring_mul(P, b0, pt.m, prqp), prqp)
             in1 = ring_add(in1, ring_mul(P, b1, pt.m, prqp), prqp)
-            scale = a.scale * pt.scale
+            scale = sets[name][0].scale * pt.scale
         k = gi * n1 * stride
         if key_id(P, k) == 0:
             t0, t1 = in0, in1

@@ -186,6 +186,13 @@ def fc_params():
     return make_params(14, 6, 60, 40, 2, 60, 3, 40)
 
 
+def gesture_learned_params():
+    """Gesture chain with the learned degree-2 feature map: depth 9 (10 Q
+    primes: 60 + 9 x 50 bits, Delta = 2^50), four 60-bit special primes,
+    dnum = 3; log QP ~ 750 <= 881."""
+    return make_params(15, 10, 60, 50, 4, 60, 3, 50)
+
+
 def gesture_params():
     """Gesture chain: N = 2^15, depth 11 (12 Q primes: 60 + 11 x 50 bits,
     Delta = 2^50), four 60-bit special primes, dnum = 3 (alpha = 4);

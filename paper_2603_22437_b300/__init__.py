@@ -188,18 +188,23 @@ def fold_poly_net_wide(dims, alpha, weights, width=32):
     return first, mats[: len(dims) - 2]
 
 
-def gesture_params():
-    """N = 2^15, depth 11 (q_0 60 bits + 11 x 50 bits, Delta = 2^50),
-    K = 4 x 60 bits, dnum = 3."""
-    return params_select(15, 12, 60, 50, 4, 60, 3)
+def gesture_params(learned=False):
+    """N = 2^15, Delta = 2^50: q_0 60 bits + 11 x 50 bits for the paper's
+    depth-11 chain, or + 9 x 50 bits for the chain with the learned degree-2
+    feature map (depth 9); K = 4 x 60 bits, dnum = 3."""
+    return params_select(15, 10 if learned else 12, 60, 50, 4, 60, 3)
+
+
+FEATURE_POWER, FEATURE_LEARNED = 0, 1
 
 
 def gesture_config(antennas=4, bins=64, chirps=32, frames=60, fc_dims=(31, 16, 6), fc_width=32,
-                   input_scale=2.0 ** 50, complex_slots=False):
-    """The gesture chain: K3 Doppler DFT -> K1 -> K6 -> w = p^4 -> p w,
-    summed over frames, then FC1^2 -> FC2^2 -> FC3 (fc_dims = d_1, d_2,
-    classes on a slot period of fc_width).  complex_slots: Re + i Im of a
-    frame group in one ciphertext (needs the key ROT_CONJ)."""
+                   input_scale=2.0 ** 50, complex_slots=False, feature_coef=None):
+    """The gesture chain: K3 Doppler DFT -> K1 -> K6 -> feature map, summed
+    over frames, then FC1^2 -> FC2^2 -> FC3 (fc_dims = d_1, d_2, classes on a
+    slot period of fc_width).  Feature map: the paper's w = p^4 and p w, or
+    with feature_coef = (a, b) the learned a p + b p^2.  complex_slots:
+    Re + i Im of a frame group in one ciphertext (needs the key ROT_CONJ)."""
     c = CircuitConfig()
     c.kind, c.bins, c.frames = CIRCUIT_GESTURE, bins, frames
     c.complex_slots = int(bool(complex_slots))
@@ -207,6 +212,9 @@ def gesture_config(antennas=4, bins=64, chirps=32, frames=60, fc_dims=(31, 16, 6
     c.fc_dims[0] = antennas * bins * chirps
     for i, d in enumerate(fc_dims):
         c.fc_dims[i + 1] = d
+    if feature_coef is not None:
+        c.feature_map = FEATURE_LEARNED
+        c.feature_coef[0], c.feature_coef[1] = float(feature_coef[0]), float(feature_coef[1])
     return c
 
 
@@ -451,6 +459,16 @@ class Context:
         da = np.ascontiguousarray(deltas, dtype=np.uint32)
         self._c(_lib.lib().mmfhe_ct_bsgs(self.h, keys.h, ptr(out), ptr(a), batch, level, stride, n1, ptr(da),
                                          ptr_array(diags), len(diags), stream_ptr(stream)))
+
+    def ct_bsgs_dh(self, keys, out, a, batch, level, stride, n1, offsets, diags, stream=None):
+        """Double-hoisted BSGS product; diags = [(set, delta, words over Q_level)]."""
+        offs = np.ascontiguousarray(offsets, dtype=np.int32)
+        so = np.ascontiguousarray([d[0] for d in diags], dtype=np.uint32)
+        da = np.ascontiguousarray([d[1] for d in diags], dtype=np.uint32)
+        words = [np.ascontiguousarray(d[2]) for d in diags]
+        self._c(_lib.lib().mmfhe_ct_bsgs_dh(self.h, keys.h, ptr(out), ptr(a), batch, level, stride, n1, len(offs),
+                                            ptr(offs), ptr(so), ptr(da), ptr_array(words), len(words),
+                                            stream_ptr(stream)))
 
     # --- circuits -------------------------------------------------------------
     def eval(self, plan, keys, ins, outs, stream=None, vital=False):

@@ -23,7 +23,7 @@ ERRORS = {
 CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_FC, CIRCUIT_VITAL_PER_FRAME, CIRCUIT_GESTURE = 1, 2, 3, 4, 5
 CONST_TAGS = {1: "idx", 2: "one", 3: "fir", 4: "dre", 5: "dim", 6: "fw", 7: "fone", 8: "dft_c", 9: "dft_s",
               10: "dft_ms", 11: "fcw", 12: "gdft_c", 13: "gdft_s", 14: "gdft_ms", 15: "notch", 16: "fcb",
-              17: "gdft_w"}
+              17: "gdft_w", 18: "notch_b", 19: "feat_a"}
 ROT_CONJ = -(1 << 31)   # key id of the slot-wise complex conjugation
 
 
@@ -53,7 +53,8 @@ class CircuitConfig(ctypes.Structure):
                 ("num_bands", ctypes.c_uint32), ("band_lo_mhz", ctypes.c_uint32 * 2),
                 ("band_hi_mhz", ctypes.c_uint32 * 2), ("dft_gain", ctypes.c_double * 2), ("fc_dims", ctypes.c_uint32 * 9),
                 ("antennas", ctypes.c_uint32), ("chirps", ctypes.c_uint32), ("fc_width", ctypes.c_uint32),
-                ("complex_slots", ctypes.c_uint32), ("input_scale", ctypes.c_double)]
+                ("complex_slots", ctypes.c_uint32), ("input_scale", ctypes.c_double),
+                ("feature_map", ctypes.c_uint32), ("feature_coef", ctypes.c_double * 2)]
 
 
 class KernelStat(ctypes.Structure):
@@ -180,6 +181,7 @@ _SIGS = {
     "mmfhe_keyswitch_noalloc": [_VP, _VP, _INT, _I32, _VP, _VP, _SZ, _U32, _VP],
     "mmfhe_ct_rotsum": [_VP, _VP, _VP, _VP, _SZ, _U32, _I32, _U32, _VP],
     "mmfhe_ct_bsgs": [_VP, _VP, _VP, _VP, _SZ, _U32, _I32, _U32, _VP, _VP, _SZ, _VP],
+    "mmfhe_ct_bsgs_dh": [_VP, _VP, _VP, _VP, _SZ, _U32, _I32, _U32, _U32, _VP, _VP, _VP, _VP, _SZ, _VP],
     "mmfhe_plan_create": [_VP, ctypes.POINTER(CircuitConfig), _SZ, _PP],
     "mmfhe_plan_destroy": [_VP],
     "mmfhe_plan_num_consts": [_VP, ctypes.POINTER(_U32)],

@@ -690,6 +690,38 @@ mmfhe_status mmfhe_ct_bsgs(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out
     ABI_CATCH(c)
 }
 
+mmfhe_status mmfhe_ct_bsgs_dh(mmfhe_ctx *ctx, const mmfhe_keys *keys, uint64_t *out, const uint64_t *in, size_t batch,
+                              uint32_t level, int32_t stride, uint32_t n1, uint32_t num_sets, const int32_t *offsets,
+                              const uint32_t *set_of, const uint32_t *deltas, const uint64_t *const *diags,
+                              size_t num_diags, void *stream) {
+    Context *c = nullptr;
+    ABI_TRY
+    PRIM_SETUP(level)
+    const Keys &K = keys_of(keys, c);
+    if (!batch) return MMFHE_OK;
+    if (!num_diags || !deltas || !diags || !set_of || n1 == 0) throw Error(MMFHE_ERR_BAD_ARG, "no diagonals");
+    if (num_sets == 0 || num_sets > 64 || !offsets) throw Error(MMFHE_ERR_BAD_ARG, "1..64 baby sets");
+    check_ptr(out, "out"); check_ptr(in, "in");
+    CtB A = load_cts(*c, contiguous(in, batch, W).data(), 0, (int)batch, (int)level, 1.0, st);
+    std::vector<PtDev> pts;
+    pts.reserve(num_diags);
+    std::vector<BsgsSet> sets(num_sets);
+    for (uint32_t s = 0; s < num_sets; s++) {
+        sets[s].x = &A;
+        sets[s].offset = offsets[s];
+    }
+    for (size_t i = 0; i < num_diags; i++) {
+        check_ptr(diags[i], "diagonal");
+        if (set_of[i] >= num_sets) throw Error(MMFHE_ERR_BAD_ARG, "diagonal of an unknown baby set");
+        pts.push_back(pt_qp_from_coeffs(*c, diags[i], (int)level, 1.0, st));
+    }
+    for (size_t i = 0; i < num_diags; i++) sets[set_of[i]].diags.push_back({(int)deltas[i], &pts[i]});
+    CtB r = bsgs_dh(*c, K, sets, (int)n1, stride, st);
+    store_cts(*c, r, contiguous_out(out, batch, W).data(), 0, st);
+    CK(cudaStreamSynchronize(st));
+    ABI_CATCH(c)
+}
+
 // ---- plans ----
 mmfhe_status mmfhe_plan_create(mmfhe_ctx *ctx, const mmfhe_circuit_config *cfg, size_t cfg_size, mmfhe_plan **out) {
     Context *c = nullptr;

@@ -158,6 +158,12 @@ static bool is_vital(const mmfhe_circuit_config &cfg) {
     return cfg.kind == MMFHE_CIRCUIT_VITAL || cfg.kind == MMFHE_CIRCUIT_VITAL_PER_FRAME;
 }
 
+// Levels the gesture chain's feature map takes: the paper's p (p^2)^2 three,
+// the learned a p + b p^2 one.
+static int gesture_feature_depth(const mmfhe_circuit_config &cfg) {
+    return cfg.feature_map == MMFHE_FEATURE_LEARNED ? 1 : 3;
+}
+
 static void check_gesture_cfg(const Context &c, const mmfhe_circuit_config &cfg) {
     const uint64_t A = cfg.antennas, R = cfg.bins, D = cfg.chirps, W = cfg.fc_width;
     if (A < 1 || R < 1 || D < 2 || cfg.frames < 1) throw Error(MMFHE_ERR_BAD_ARG, "bad gesture sizes");
@@ -169,7 +175,9 @@ static void check_gesture_cfg(const Context &c, const mmfhe_circuit_config &cfg)
     for (int l = 1; l <= 3; l++)
         if (cfg.fc_dims[l] < 1 || cfg.fc_dims[l] >= W) throw Error(MMFHE_ERR_BAD_ARG, "FC widths must be 1..fc_width-1");
     if (!(cfg.input_scale > 1.0)) throw Error(MMFHE_ERR_BAD_ARG, "input_scale must be the encryption scale");
-    if (c.L < 11) throw Error(MMFHE_ERR_BAD_ARG, "not enough levels for the gesture chain");
+    if (cfg.feature_map != MMFHE_FEATURE_POWER && cfg.feature_map != MMFHE_FEATURE_LEARNED)
+        throw Error(MMFHE_ERR_BAD_ARG, "unknown feature map");
+    if (c.L < 8 + gesture_feature_depth(cfg)) throw Error(MMFHE_ERR_BAD_ARG, "not enough levels for the gesture chain");
 }
 
 static void check_cfg(const Context &c, const mmfhe_circuit_config &cfg) {
@@ -244,11 +252,17 @@ static Plan *create_gesture_plan(Context &c, const mmfhe_circuit_config &cfg) {
     }
     if (cfg.complex_slots) rots.insert(MMFHE_ROT_CONJ);
     p->keys.push_back(mmfhe_const_key{MMFHE_CONST_NOTCH, 0, 0, (uint32_t)(L - 2)});
-    for (int k = 0; k < W; k++) p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCW, 0, (uint32_t)k, (uint32_t)(L - 6)});
-    p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCB, 0, 0, (uint32_t)(L - 7)});
+    if (cfg.feature_map == MMFHE_FEATURE_LEARNED) {
+        p->keys.push_back(mmfhe_const_key{MMFHE_CONST_NOTCH_B, 0, 0, (uint32_t)(L - 2)});
+        p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FEAT_A, 0, 0, (uint32_t)(L - 3)});
+    }
+    // FC1 reads the features: level L - 3 - (the feature map's depth)
+    const int lf = L - 3 - gesture_feature_depth(cfg);
+    for (int k = 0; k < W; k++) p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCW, 0, (uint32_t)k, (uint32_t)lf});
+    p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCB, 0, 0, (uint32_t)(lf - 1)});
     for (int l = 1; l <= 2; l++)
         for (int k : fc_present(cfg, l))
-            p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCW, (uint32_t)l, (uint32_t)k, (uint32_t)(L - 6 - 2 * l)});
+            p->keys.push_back(mmfhe_const_key{MMFHE_CONST_FCW, (uint32_t)l, (uint32_t)k, (uint32_t)(lf - 2 * l)});
     for (int b = 1; b < p->n1_k3; b++) rots.insert(norm_rot(c, b));
     for (int f = 1; f < p->fpc; f <<= 1) rots.insert(norm_rot(c, f * p->ard_pad));
     for (int b = 1; b < p->n1_fc; b++) rots.insert(norm_rot(c, b));
@@ -257,7 +271,7 @@ static Plan *create_gesture_plan(Context &c, const mmfhe_circuit_config &cfg) {
     rots.erase(0);
     p->rotations.assign(rots.begin(), rots.end());
     p->n_in = cfg.complex_slots ? p->pairs : 2 * p->pairs;
-    p->out_levels = {L - 11};
+    p->out_levels = {lf - 5};
     p->consts.resize(p->keys.size());
     for (size_t i = 0; i < p->keys.size(); i++) p->index[key_of(p->keys[i])] = (int)i;
     return p.release();
@@ -266,12 +280,23 @@ static Plan *create_gesture_plan(Context &c, const mmfhe_circuit_config &cfg) {
 // Scale of FC1's rescaled output for inputs encrypted at scale `s0`: the
 // evaluator's scale arithmetic step by step (products multiply scales, a
 // rescale at level l divides by q_l, constants carry q_l).
-static double gesture_fc1_scale(const Context &c, double s0) {
+// Scale of the notched power (after K3, K1 and the notch).
+static double gesture_notch_scale(const Context &c, double s0) {
     auto q = [&](int l) { return (double)c.primes[l]; };
     const int L = c.L;
     double s = s0 * q(L) / q(L);
     s = s * s / q(L - 1);
-    const double p = s * q(L - 2) / q(L - 2);
+    return s * q(L - 2) / q(L - 2);
+}
+
+static double gesture_fc1_scale(const Context &c, const mmfhe_circuit_config &cfg) {
+    auto q = [&](int l) { return (double)c.primes[l]; };
+    const int L = c.L;
+    const double p = gesture_notch_scale(c, cfg.input_scale);
+    if (cfg.feature_map == MMFHE_FEATURE_LEARNED) {
+        const double f = p * p / q(L - 3);         // (notched p) x (b p + a)
+        return f * q(L - 4) / q(L - 4);
+    }
     double w = p * p / q(L - 3);
     w = w * w / q(L - 4);
     const double f = p * w / q(L - 5);
@@ -460,10 +485,20 @@ const PtDev &plan_const(const Plan &p, uint32_t tag, uint32_t band, uint32_t idx
     return pt;
 }
 
+// The vital chain's FIR and DFT products are double-hoisted: their diagonals
+// multiply baby steps over the extended basis Q_l * P and are kept there.
+static bool const_is_qp(const Plan &p, const mmfhe_const_key &k) {
+    return p.cfg.kind == MMFHE_CIRCUIT_VITAL && (k.tag == MMFHE_CONST_FIR || k.tag == MMFHE_CONST_DRE);
+}
+
 void plan_set_const(Plan &p, uint32_t i, const uint64_t *words_host_or_dev, cudaStream_t st) {
     Context &c = *p.ctx;
     if (i >= p.keys.size()) throw Error(MMFHE_ERR_BAD_ARG, "constant index out of range");
     const int level = (int)p.keys[i].level;
+    if (const_is_qp(p, p.keys[i])) {
+        p.consts[i] = pt_qp_from_coeffs(c, words_host_or_dev, level, (double)c.primes[level], st);
+        return;
+    }
     PtDev pt = pt_new(c, level, (double)c.primes[level]);
     CK(cudaMemcpyAsync(pt.buf.get(), words_host_or_dev, (size_t)(level + 1) * c.n * 8, cudaMemcpyDefault, st));
     ntt_q_blocks(c, pt.buf.get(), 1, level + 1, false, st);
@@ -562,13 +597,21 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
         }
         return prerot(floor_div(delta, p.n1_k3), p.n1_k3, 1);
     }
-    case MMFHE_CONST_NOTCH: {
-        // Eq. (notch mask): zero on Doppler bins floor(D/2) .. ceil(D/2)
+    case MMFHE_CONST_NOTCH:
+    case MMFHE_CONST_NOTCH_B: {
+        // Eq. (notch mask): zero on Doppler bins floor(D/2) .. ceil(D/2); NOTCH_B: times b
         const int D = (int)cfg.chirps, ard = (int)(cfg.antennas * cfg.bins * cfg.chirps);
+        const double g = k.tag == MMFHE_CONST_NOTCH_B ? cfg.feature_coef[1] : 1.0;
         for (int s = 0; s < n; s++) {
             const int d = s % D;
-            v[s] = (s % p.ard_pad < ard && !(d >= D / 2 && d <= (D + 1) / 2)) ? 1.0 : 0.0;
+            v[s] = (s % p.ard_pad < ard && !(d >= D / 2 && d <= (D + 1) / 2)) ? g : 0.0;
         }
+        return v;
+    }
+    case MMFHE_CONST_FEAT_A: {
+        // a on every active slot (the notched product it joins is zero elsewhere)
+        const int ard = (int)(cfg.antennas * cfg.bins * cfg.chirps);
+        for (int s = 0; s < n; s++) v[s] = s % p.ard_pad < ard ? cfg.feature_coef[0] : 0.0;
         return v;
     }
     case MMFHE_CONST_FW:
@@ -596,8 +639,10 @@ void plan_encode_consts(Plan &p, cudaStream_t st) {
             im = const_slots(p, ks);
         }
         words.assign((size_t)(k.level + 1) * c.n, 0);
-        encode_slots(c.params, v.data(), (double)c.primes[k.level], (int)k.level, words.data(),
-                     im.empty() ? nullptr : im.data());
+        // a constant that is added (not multiplied) is encoded at the scale of its ciphertext
+        const double scale = k.tag == MMFHE_CONST_FEAT_A ? gesture_notch_scale(c, p.cfg.input_scale)
+                                                         : (double)c.primes[k.level];
+        encode_slots(c.params, v.data(), scale, (int)k.level, words.data(), im.empty() ? nullptr : im.data());
         plan_set_const(p, (uint32_t)i, words.data(), st);
         CK(cudaStreamSynchronize(st));
     }
@@ -650,6 +695,27 @@ static std::vector<CtB> run_fir_dft(Context &c, const Plan &p, const Keys &k, st
 // both parts; K7 w = Z conj(Z at t-1) = x + i y, the phase signal
 // w^3 - conj(w^3) = 2i Im(w^3) (third order) or w - conj(w) (first); K3,
 // |X|^2, sharpening and the sums as in the split chain.
+// Baby sets of the vital FIR product on x: RR taps on Rot(x, -b R_c) (output
+// in bin slot 0), HR taps on Rot(x, -b R_c - 1) (slot 1).
+static std::vector<BsgsSet> fir_sets(const Plan &p, const CtB &x) {
+    std::vector<BsgsSet> sets(2);
+    for (int band = 0; band < 2; band++) {
+        sets[band].x = &x;
+        sets[band].offset = -band;
+        for (uint32_t kk = 0; kk < p.cfg.taps; kk++)
+            sets[band].diags.push_back({(int)kk, &plan_const(p, MMFHE_CONST_FIR, band, kk)});
+    }
+    return sets;
+}
+
+// The narrowband DFT's single baby set on dphi: Rot(dphi, b R_c).
+static std::vector<BsgsSet> dft_sets(const Plan &p, const CtB &dphi) {
+    std::vector<BsgsSet> sets(1);
+    sets[0].x = &dphi;
+    for (int d : p.dft_deltas[0]) sets[0].diags.push_back({d, &plan_const(p, MMFHE_CONST_DRE, 0, d)});
+    return sets;
+}
+
 static std::vector<CtB> run_vital_complex(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in,
                                           cudaStream_t st) {
     const int G = p.groups, Rc = p.r_c, Fp = p.f_pad;
@@ -690,26 +756,8 @@ static std::vector<CtB> run_vital_complex(Context &c, const Plan &p, const Keys 
     }
     m.clear();
     CtB Z = rotsum(c, k, rescale(c, relin(c, k, t4, st), st), 1, (uint32_t)Rc, st);
-    // ---- K5: both bands in one product (RR in bin slot 0, HR in slot 1) ----
-    std::vector<int> idx_fir(p.n1_fir);
-    std::vector<int32_t> rot_fir;
-    for (int sft = 0; sft < 2; sft++)
-        for (int b = 0; b < p.n1_fir; b++) rot_fir.push_back(-b * Rc - sft);
-    for (int b = 0; b < p.n1_fir; b++) idx_fir[b] = b;
-    CtB Zf;
-    {
-        std::vector<CtB> hs = rotate_hoisted(c, k, Z, rot_fir, st);
-        std::vector<CtB> b0(std::make_move_iterator(hs.begin()), std::make_move_iterator(hs.begin() + p.n1_fir));
-        std::vector<CtB> b1(std::make_move_iterator(hs.begin() + p.n1_fir), std::make_move_iterator(hs.end()));
-        BsgsTerm t[2];
-        for (int band = 0; band < 2; band++) {
-            t[band].baby = band == 0 ? &b0 : &b1;
-            t[band].baby_idx = idx_fir;
-            for (uint32_t kk = 0; kk < p.cfg.taps; kk++)
-                t[band].diags.push_back({(int)kk, &plan_const(p, MMFHE_CONST_FIR, band, kk)});
-        }
-        Zf = rescale(c, bsgs(c, k, {t[0], t[1]}, p.n1_fir, -Rc, st), st);
-    }
+    // ---- K5: both bands in one double-hoisted product (RR in bin slot 0, HR in slot 1) ----
+    CtB Zf = rescale(c, bsgs_dh(c, k, fir_sets(p, Z), p.n1_fir, -Rc, st), st);
     // ---- K7: w = Zf conj(Zf at t-1) ----
     CtB zpc = rotate(c, k, rotate(c, k, Zf, -Rc, st), MMFHE_ROT_CONJ, st);
     TensorB tw = tensor_new(c, B, Zf.level);
@@ -732,18 +780,7 @@ static std::vector<CtB> run_vital_complex(Context &c, const Plan &p, const Keys 
         ct_addsub(c, dphi, top, topc, true, st);
     }
     // ---- K3, |X|^2 (negated by the i), sharpen, weighted frequency average ----
-    std::set<int> need;
-    for (int d : p.dft_deltas[0]) need.insert(d % p.n1_dft);
-    std::vector<int> idx(need.begin(), need.end());
-    std::vector<int32_t> rr;
-    for (int b : idx) rr.push_back(b * Rc);
-    std::vector<CtB> hs = rotate_hoisted(c, k, dphi, rr, st);
-    BsgsTerm td;
-    td.baby = &hs;
-    td.baby_idx = idx;
-    for (int d : p.dft_deltas[0]) td.diags.push_back({d, &plan_const(p, MMFHE_CONST_DRE, 0, d)});
-    CtB X = rescale(c, bsgs(c, k, {td}, p.n1_dft, Rc, st), st);
-    hs.clear();
+    CtB X = rescale(c, bsgs_dh(c, k, dft_sets(p, dphi), p.n1_dft, Rc, st), st);
     CtB pw = rescale(c, square_sum(c, k, {&X}, st), st);
     CtB merged = rotate_add(c, k, pw, (p.f_pad / 2) * Rc, pw, st);
     CtB S = rescale(c, square_sum(c, k, {&merged}, st), st);
@@ -806,27 +843,12 @@ static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std:
         iq[part] = rotsum(c, k, rescale(c, relin(c, k, t, st), st), 1, (uint32_t)Rc, st);
     }
     m.clear();
-    // ---- K5 FIR of both bands in one BSGS product per part: baby steps
-    // hoisted once, unshifted for RR (bin slot 0), one slot on for HR (slot 1) ----
-    std::vector<int> idx_fir(p.n1_fir);
-    std::vector<int32_t> rot_fir;
-    for (int sft = 0; sft < 2; sft++)
-        for (int b = 0; b < p.n1_fir; b++) rot_fir.push_back(-b * Rc - sft);
-    for (int b = 0; b < p.n1_fir; b++) idx_fir[b] = b;
+    // ---- K5 FIR of both bands in one double-hoisted BSGS product per part:
+    // baby steps share one ModUp, unshifted for RR (bin slot 0), one slot on
+    // for HR (slot 1) ----
     CtB filt[2];
-    for (int part = 0; part < 2; part++) {
-        std::vector<CtB> hs = rotate_hoisted(c, k, iq[part], rot_fir, st);
-        std::vector<CtB> b0(std::make_move_iterator(hs.begin()), std::make_move_iterator(hs.begin() + p.n1_fir));
-        std::vector<CtB> b1(std::make_move_iterator(hs.begin() + p.n1_fir), std::make_move_iterator(hs.end()));
-        BsgsTerm t[2];
-        for (int band = 0; band < 2; band++) {
-            t[band].baby = band == 0 ? &b0 : &b1;
-            t[band].baby_idx = idx_fir;
-            for (uint32_t kk = 0; kk < p.cfg.taps; kk++)
-                t[band].diags.push_back({(int)kk, &plan_const(p, MMFHE_CONST_FIR, band, kk)});
-        }
-        filt[part] = rescale(c, bsgs(c, k, {t[0], t[1]}, p.n1_fir, -Rc, st), st);
-    }
+    for (int part = 0; part < 2; part++)
+        filt[part] = rescale(c, bsgs_dh(c, k, fir_sets(p, iq[part]), p.n1_fir, -Rc, st), st);
     // ---- K7, both bands slot by slot ----
     const CtB &If = filt[0], &Qf = filt[1];
     CtB If1 = rotate(c, k, If, -Rc, st);
@@ -853,18 +875,7 @@ static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std:
         dphi = std::move(y);
     }
     // ---- K3 narrowband DFT (both bands, each in its bin slot), |X|^2 ----
-    std::set<int> need;
-    for (int d : p.dft_deltas[0]) need.insert(d % p.n1_dft);
-    std::vector<int> idx(need.begin(), need.end());
-    std::vector<int32_t> rr;
-    for (int b : idx) rr.push_back(b * Rc);
-    std::vector<CtB> hs = rotate_hoisted(c, k, dphi, rr, st);
-    BsgsTerm td;
-    td.baby = &hs;
-    td.baby_idx = idx;
-    for (int d : p.dft_deltas[0]) td.diags.push_back({d, &plan_const(p, MMFHE_CONST_DRE, 0, d)});
-    CtB X = rescale(c, bsgs(c, k, {td}, p.n1_dft, Rc, st), st);
-    hs.clear();
+    CtB X = rescale(c, bsgs_dh(c, k, dft_sets(p, dphi), p.n1_dft, Rc, st), st);
     CtB pw = rescale(c, square_sum(c, k, {&X}, st), st);
     // Re^2 at k, Im^2 at k + F_pad/2: one rotation adds them
     CtB merged = rotate_add(c, k, pw, (p.f_pad / 2) * Rc, pw, st);
@@ -955,7 +966,7 @@ static void gesture_set_fc_layer(Plan &p, uint32_t layer, const double *W) {
             encode_and_set(p, mmfhe_const_key{MMFHE_CONST_FCW, 0, (uint32_t)k, 0}, r, 0.0);
         }
         for (int s = 0; s < slots; s++) v[s] = s % w == w - 1 ? 1.0 : W[(size_t)(s % w) * ld + ard];
-        encode_and_set(p, mmfhe_const_key{MMFHE_CONST_FCB, 0, 0, 0}, v, gesture_fc1_scale(c, cfg.input_scale));
+        encode_and_set(p, mmfhe_const_key{MMFHE_CONST_FCB, 0, 0, 0}, v, gesture_fc1_scale(c, cfg));
         return;
     }
     for (int k : fc_present(cfg, (int)layer)) {
@@ -967,10 +978,70 @@ static void gesture_set_fc_layer(Plan &p, uint32_t layer, const double *W) {
 
 // Gesture chain: in[0] / in[1] = Re / Im of every pair of every window
 // (batch B pairs, window-major).
+// The gesture chain's feature stage runs on at most this many ciphertext
+// pairs at a time (whole windows): its hoisted Doppler baby steps and key
+// switches hold about 0.17 GB of scratch per pair at N = 2^15, so a batch of
+// 16 windows (480 pairs) in one piece would need about 80 GB.  Every
+// operation of the stage acts on each ciphertext alone, so the chunking
+// changes no word.
+constexpr int GESTURE_PAIRS_PER_CHUNK = 128;
+
+static CtB gesture_features(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st);
+
 static std::vector<CtB> run_gesture(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in,
                                     cudaStream_t st) {
     const mmfhe_circuit_config &cfg = p.cfg;
-    const int D = (int)cfg.chirps, W = (int)cfg.fc_width;
+    const int W = (int)cfg.fc_width;
+    const int B = in[0].B / p.pairs;
+    const int wchunk = std::max(1, GESTURE_PAIRS_PER_CHUNK / p.pairs);
+    CtB feat;
+    if (B <= wchunk) {
+        feat = gesture_features(c, p, k, in, st);
+    } else {
+        // the windows' pairs are window-major: a chunk of whole windows is a contiguous slice
+        for (int b0 = 0; b0 < B; b0 += wchunk) {
+            const int nb = std::min(wchunk, B - b0);
+            std::vector<CtB> part;
+            for (const CtB &x : in) part.push_back(ct_slice(c, x, b0 * p.pairs, nb * p.pairs, st));
+            CtB f = gesture_features(c, p, k, part, st);
+            if (b0 == 0) feat = ct_new(c, B, f.level, f.scale);
+            ct_place(c, feat, b0, f, st);
+        }
+        in.clear();
+    }
+    const int n1 = p.n1_fc;
+    std::vector<int32_t> rb(n1);
+    std::vector<int> idx(n1);
+    for (int b = 0; b < n1; b++) rb[b] = idx[b] = b;
+    CtB x = std::move(feat);
+    for (int l = 0; l < 3; l++) {
+        std::vector<CtB> babies = rotate_hoisted(c, k, x, rb, st);
+        BsgsTerm t;
+        t.baby = &babies;
+        t.baby_idx = idx;
+        if (l == 0)
+            for (int d = 0; d < W; d++) t.diags.push_back({d, &plan_const(p, MMFHE_CONST_FCW, 0, (uint32_t)d)});
+        else
+            for (int d : fc_present(cfg, l)) t.diags.push_back({d, &plan_const(p, MMFHE_CONST_FCW, (uint32_t)l, (uint32_t)d)});
+        CtB y = rescale(c, bsgs(c, k, {t}, n1, 1, st), st);
+        babies.clear();
+        if (l == 0)
+            y = add_plain(c, rotsum(c, k, y, W, (uint32_t)(p.ard_pad / W), st), plan_const(p, MMFHE_CONST_FCB, 0, 0), st);
+        if (l < 2) y = rescale(c, square_sum(c, k, {&y}, st), st);
+        x = std::move(y);
+    }
+    std::vector<CtB> out;
+    out.push_back(std::move(x));
+    return out;
+}
+
+// K3 -> K1 -> K6 -> soft power -> weighting on every pair of the given
+// windows (in: Re and Im of every pair, or one complex-slot ciphertext per
+// pair, window-major), then the accumulation over each window's frames: one
+// feature ciphertext per window.
+static CtB gesture_features(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st) {
+    const mmfhe_circuit_config &cfg = p.cfg;
+    const int D = (int)cfg.chirps;
     CtB feat;
     {
         std::vector<int32_t> rb(p.n1_k3);
@@ -1018,38 +1089,26 @@ static std::vector<CtB> run_gesture(Context &c, const Plan &p, const Keys &k, st
         CtB pm = ct_new(c, pw.B, pw.level, pw.scale);
         ct_mul_plain(c, pm, pw, plan_const(p, MMFHE_CONST_NOTCH, 0, 0), false, st);   // K6
         CtB pn = rescale(c, pm, st);
+        if (cfg.feature_map == MMFHE_FEATURE_LEARNED) {
+            // learned map a p + b p^2 = (notched p) x (b notched p + a): one level
+            const PtDev &nb = plan_const(p, MMFHE_CONST_NOTCH_B, 0, 0);
+            CtB pbm = ct_new(c, pw.B, pw.level, pw.scale * nb.scale);
+            ct_mul_plain(c, pbm, pw, nb, false, st);
+            CtB pba = add_plain(c, rescale(c, pbm, st), plan_const(p, MMFHE_CONST_FEAT_A, 0, 0), st);
+            TensorB tf = tensor_new(c, pn.B, pn.level);
+            tensor_acc(c, tf, pn, pba, 1, true, st);
+            CtB f = rescale(c, relin(c, k, tf, st), st);
+            return rotsum(c, k, group_sum(c, f, p.pairs, st), p.ard_pad, (uint32_t)p.fpc, st);
+        }
         CtB w2 = rescale(c, square_sum(c, k, {&pn}, st), st);                     // w = p^4
         CtB w4 = rescale(c, square_sum(c, k, {&w2}, st), st);
         CtB pd = ct_drop(c, pn, w4.level, st);
         TensorB tw = tensor_new(c, w4.B, w4.level);
         tensor_acc(c, tw, pd, w4, 1, true, st);
-        CtB f = rescale(c, relin(c, k, tw, st), st);                              // p x w
+        CtB f = rescale(c, relin(c, k, tw, st), st);                          // p x w
         feat = rotsum(c, k, group_sum(c, f, p.pairs, st), p.ard_pad, (uint32_t)p.fpc, st);
     }
-    const int n1 = p.n1_fc;
-    std::vector<int32_t> rb(n1);
-    std::vector<int> idx(n1);
-    for (int b = 0; b < n1; b++) rb[b] = idx[b] = b;
-    CtB x = std::move(feat);
-    for (int l = 0; l < 3; l++) {
-        std::vector<CtB> babies = rotate_hoisted(c, k, x, rb, st);
-        BsgsTerm t;
-        t.baby = &babies;
-        t.baby_idx = idx;
-        if (l == 0)
-            for (int d = 0; d < W; d++) t.diags.push_back({d, &plan_const(p, MMFHE_CONST_FCW, 0, (uint32_t)d)});
-        else
-            for (int d : fc_present(cfg, l)) t.diags.push_back({d, &plan_const(p, MMFHE_CONST_FCW, (uint32_t)l, (uint32_t)d)});
-        CtB y = rescale(c, bsgs(c, k, {t}, n1, 1, st), st);
-        babies.clear();
-        if (l == 0)
-            y = add_plain(c, rotsum(c, k, y, W, (uint32_t)(p.ard_pad / W), st), plan_const(p, MMFHE_CONST_FCB, 0, 0), st);
-        if (l < 2) y = rescale(c, square_sum(c, k, {&y}, st), st);
-        x = std::move(y);
-    }
-    std::vector<CtB> out;
-    out.push_back(std::move(x));
-    return out;
+    return feat;
 }
 
 void plan_set_fc_layer(Plan &p, uint32_t layer, const double *W) {

@@ -372,6 +372,8 @@ Context *create_context(const mmfhe_params &p, int device) {
         uint64_t qmax = 0;
         for (int i = 0; i < c->num_q; i++) qmax = std::max(qmax, c->primes[i]);
         c->sum_terms_max = (int)std::min<uint64_t>(16, (~0ull) / qmax);
+        for (int i = c->num_q; i < np; i++) qmax = std::max(qmax, c->primes[i]);
+        c->sum_terms_max_qp = (int)std::min<uint64_t>(16, (~0ull) / qmax);
         // twiddles: fw[i] = psi^brv(i), iw[i] = psi^-brv(i)
         const uint32_t n = c->n;
         std::vector<uint64_t> tw(4ull * np * n), ninv(2ull * np);

@@ -74,6 +74,30 @@ void ct_mul_plain(Context &c, CtB &out, const CtB &a, const PtDev &pt, bool acc,
                        a.level + 1, acc, st, pt.mont);
 }
 
+PtDev pt_qp_from_coeffs(Context &c, const uint64_t *words, int level, double scale, cudaStream_t st) {
+    const int nl = level + 1, nre = nl + c.num_p;
+    PtDev pt;
+    pt.level = level;
+    pt.scale = scale;
+    pt.qp = true;
+    pt.buf = Buf(c.pool.get(), (size_t)nre * c.n);
+    CK(cudaMemcpyAsync(pt.buf.get(), words, (size_t)nl * c.n * 8, cudaMemcpyDefault, st));
+    Buf flag(c.pool.get(), 1);
+    CK(cudaMemsetAsync(flag.get(), 0, 8, st));
+    k_launch_qp_extend(c, pt.buf.get(), level, (int *)flag.get(), st);
+    uint64_t bad = 0;
+    CK(cudaMemcpyAsync(&bad, flag.get(), 8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (bad) throw Error(MMFHE_ERR_BAD_ARG, "plaintext coefficients of magnitude q_0 / 2 or more: no extension to the special primes");
+    std::vector<int> pids(nre);
+    for (int t = 0; t < nre; t++) pids[t] = t < nl ? t : c.num_q + (t - nl);
+    RowsView v{pt.buf.get(), make_map(nre, nre, pids), (size_t)nre};
+    launch_ntt(c, v, v, false, st);
+    k_launch_mont_convert(c, v, true, st);
+    pt.mont = true;
+    return pt;
+}
+
 void pt_to_mont(Context &c, PtDev &pt, cudaStream_t st) {
     if (pt.mont) return;
     const int nl = pt.level + 1;
@@ -90,6 +114,20 @@ CtB ct_copy(Context &c, const CtB &a, cudaStream_t st) {
     CtB r = ct_new(c, a.B, a.level, a.scale);
     CK(cudaMemcpyAsync(r.ptr(), a.ptr(), (size_t)a.B * c.ct_words(a.level) * 8, cudaMemcpyDeviceToDevice, st));
     return r;
+}
+
+CtB ct_slice(Context &c, const CtB &a, int b0, int nb, cudaStream_t st) {
+    if (b0 < 0 || nb < 0 || b0 + nb > a.B) throw Error(MMFHE_ERR_BAD_ARG, "slice outside the batch");
+    CtB r = ct_new(c, nb, a.level, a.scale);
+    const size_t w = c.ct_words(a.level);
+    CK(cudaMemcpyAsync(r.ptr(), a.ptr() + (size_t)b0 * w, (size_t)nb * w * 8, cudaMemcpyDeviceToDevice, st));
+    return r;
+}
+
+void ct_place(Context &c, CtB &dst, int b0, const CtB &src, cudaStream_t st) {
+    if (src.level != dst.level || b0 < 0 || b0 + src.B > dst.B) throw Error(MMFHE_ERR_BAD_ARG, "place outside the batch");
+    const size_t w = c.ct_words(src.level);
+    CK(cudaMemcpyAsync(dst.ptr() + (size_t)b0 * w, src.ptr(), (size_t)src.B * w * 8, cudaMemcpyDeviceToDevice, st));
 }
 
 CtB ct_drop(Context &c, const CtB &a, int level, cudaStream_t st) {
@@ -462,6 +500,144 @@ CtB bsgs(Context &c, const Keys &k, const std::vector<BsgsTerm> &terms, int n1, 
         }
     }
     return acc;
+}
+
+// ModDown of `blocks` blocks over Q_l * P (block k at u + k * ustride rows)
+// into out [blocks][l+1][N]: inverse NTT of the P rows with Phat^-1 folded,
+// centered conversion inside v's forward NTT, (u - v) P^-1 in its last pass.
+static void moddown_blocks(Context &c, uint64_t *out, const uint64_t *u, size_t ustride, size_t blocks, int level,
+                           cudaStream_t st) {
+    const int nl = level + 1, nre = nl + c.num_p, K = c.num_p;
+    Buf z(c.pool.get(), blocks * K * c.n);
+    std::vector<int> pids(nre, -1);
+    for (int kk = 0; kk < K; kk++) pids[nl + kk] = c.num_q + kk;
+    RowsView pv{const_cast<uint64_t *>(u), make_map(nre, (uint32_t)ustride, pids), blocks * nre};
+    RowMap zm = make_map(nre, K, pids);
+    zm.row0 = nl;
+    RowsView zv{z.get(), zm, blocks * nre};
+    launch_ntt(c, pv, zv, true, st, c.lv[level].d_ks_scale, c.lv[level].d_ks_scale_sh);
+    Buf v(c.pool.get(), blocks * nl * c.n);
+    CombineArgs a{out, u, nullptr, nullptr, 0, 1, nullptr};
+    a.u_stride = ustride;
+    launch_moddown_ntt_blocks(c, v.get(), z.get(), a, blocks, level, st);
+}
+
+CtB bsgs_dh(Context &c, const Keys &k, const std::vector<BsgsSet> &sets, int n1, int32_t stride, cudaStream_t st) {
+    if (sets.empty() || !sets[0].x) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: no input");
+    const CtB &x0 = *sets[0].x;
+    const int level = x0.level, B = x0.B, nl = level + 1, nre = nl + c.num_p;
+    const size_t qp_words = (size_t)B * 2 * nre * c.n;
+    const ModDownConsts dc = moddown_consts(c);
+    auto floor_div = [&](int d) { return d >= 0 ? d / n1 : -((-d + n1 - 1) / n1); };
+    // babies needed per set, giant groups of (set, baby, diagonal)
+    struct Item { int set, b; const PtDev *pt; };
+    std::map<int, std::vector<Item>> groups;
+    std::vector<std::set<int>> need(sets.size());
+    double scale = 0;
+    for (size_t s = 0; s < sets.size(); s++) {
+        const BsgsSet &bs = sets[s];
+        if (!bs.x || bs.x->level != level || bs.x->B != B) throw Error(MMFHE_ERR_LEVEL_MISMATCH, "bsgs: operand levels differ");
+        for (const auto &d : bs.diags) {
+            const PtDev *pt = d.second;
+            if (pt->level != level || !pt->qp || !pt->mont)
+                throw Error(MMFHE_ERR_BAD_ARG, "bsgs: diagonals must be over the extended basis, in Montgomery form");
+            const int g = floor_div(d.first), b = d.first - g * n1;
+            groups[g].push_back(Item{(int)s, b, pt});
+            need[s].insert(b);
+            scale = bs.x->scale * pt->scale;
+        }
+    }
+    if (groups.empty()) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: no diagonals");
+    // every key before any work
+    for (size_t s = 0; s < sets.size(); s++)
+        for (int b : need[s]) {
+            const int32_t r = norm_rot(c, b * stride + sets[s].offset);
+            if (r) galois_key(k, r);
+        }
+    for (auto &kv : groups) {
+        const int32_t r = norm_rot(c, kv.first * n1 * stride);
+        if (r) galois_key(k, r);
+    }
+    // babies over Q_l * P; one ModUp per distinct input
+    std::map<const CtB *, DigitsB> digits;
+    std::map<std::pair<int, int>, Buf> babies;
+    for (size_t s = 0; s < sets.size(); s++) {
+        const CtB &x = *sets[s].x;
+        for (int b : need[s]) {
+            Buf u(c.pool.get(), qp_words);
+            const int32_t r = norm_rot(c, b * stride + sets[s].offset);
+            if (r == 0) {
+                k_launch_qp_times_p(c, u.get(), x.ptr(), B, level, dc, st);
+            } else {
+                auto it = digits.find(&x);
+                if (it == digits.end())
+                    it = digits.emplace(&x, modup(c, x.ptr() + (size_t)nl * c.n, (size_t)2 * nl, B, level, st)).first;
+                const DigitsB &dg = it->second;
+                const uint32_t gal = galois_elt(c, r);
+                k_launch_keyip(c, u.get(), dg.buf.get(), dg.own, dg.own_stride, 0, galois_key(k, r), B, level, dg.beta,
+                               gal, st);
+                k_launch_qp_add_pc0(c, u.get(), x.ptr(), B, level, gal, dc, st);
+            }
+            babies.emplace(std::make_pair((int)s, b), std::move(u));
+        }
+    }
+    digits.clear();
+    // inner sums, MULTI_SUM_GROUPS giant steps per pass over the babies; each
+    // giant-step term accumulated into acc over Q_l * P
+    std::vector<std::pair<int, int>> order;
+    for (auto &kv : babies) order.push_back(kv.first);
+    std::map<std::pair<int, int>, int> bpos;
+    for (size_t i = 0; i < order.size(); i++) bpos[order[i]] = (int)i;
+    std::vector<int> gs;
+    for (auto &kv : groups) gs.push_back(kv.first);
+    const int tmax = std::min(MAX_SUM_TERMS, c.sum_terms_max_qp);
+    Buf acc(c.pool.get(), qp_words);
+    bool have = false;
+    for (size_t g0 = 0; g0 < gs.size(); g0 += MULTI_SUM_GROUPS) {
+        const int ng = (int)std::min<size_t>(MULTI_SUM_GROUPS, gs.size() - g0);
+        std::vector<Buf> inner;
+        for (int j = 0; j < ng; j++) inner.emplace_back(c.pool.get(), qp_words);
+        for (size_t t0 = 0; t0 < order.size(); t0 += (size_t)tmax) {
+            MultiSumTerms mt{};
+            mt.nt = (int)std::min<size_t>((size_t)tmax, order.size() - t0);
+            mt.ng = ng;
+            for (int t = 0; t < mt.nt; t++) mt.ct[t] = babies.at(order[t0 + t]).get();
+            for (int j = 0; j < ng; j++) {
+                mt.out[j] = inner[j].get();
+                for (const Item &it : groups[gs[g0 + j]]) {
+                    const int pos = bpos.at({it.set, it.b}) - (int)t0;
+                    if (pos >= 0 && pos < mt.nt) {
+                        if (mt.pt[j][pos]) throw Error(MMFHE_ERR_BAD_ARG, "bsgs: two diagonals for one baby and giant step");
+                        mt.pt[j][pos] = it.pt->buf.get();
+                    }
+                }
+            }
+            k_launch_mul_plain_sum_multi(c, mt, B, level, t0 > 0, st, true);
+        }
+        for (int j = 0; j < ng; j++) {
+            const int g = gs[g0 + j];
+            const int32_t r = norm_rot(c, g * n1 * stride);
+            if (r == 0) {
+                k_launch_qp_giant_acc(c, acc.get(), inner[j].get(), nullptr, B, level, 1, have, st);
+            } else {
+                // c1 of the inner sum down to Q, then its key switch over Q_l * P
+                Buf d(c.pool.get(), (size_t)B * nl * c.n);
+                moddown_blocks(c, d.get(), inner[j].get() + (size_t)nre * c.n, (size_t)2 * nre, (size_t)B, level, st);
+                DigitsB dg = modup(c, d.get(), (size_t)nl, B, level, st);
+                Buf w(c.pool.get(), qp_words);
+                const uint32_t gal = galois_elt(c, r);
+                k_launch_keyip(c, w.get(), dg.buf.get(), dg.own, dg.own_stride, 0, galois_key(k, r), B, level, dg.beta,
+                               gal, st);
+                k_launch_qp_giant_acc(c, acc.get(), inner[j].get(), w.get(), B, level, gal, have, st);
+            }
+            have = true;
+            inner[j].release();
+        }
+    }
+    babies.clear();
+    CtB out = ct_new(c, B, level, scale);
+    moddown_blocks(c, out.ptr(), acc.get(), (size_t)nre, (size_t)B * 2, level, st);
+    return out;
 }
 
 }  // namespace mmfhe

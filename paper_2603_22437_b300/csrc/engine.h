@@ -27,8 +27,18 @@ void ct_mul_plain(Context &c, CtB &out, const CtB &a, const PtDev &pt, bool acc,
 void ct_mul_int(Context &c, CtB &out, const CtB &a, long long k, cudaStream_t st);
 // Convert a plaintext (evaluation domain) into Montgomery form, in place.
 void pt_to_mont(Context &c, PtDev &pt, cudaStream_t st);
+// A plaintext over the extended basis Q_level * P from its coefficient-form Q
+// rows (host or device words, uint64[level+1][N]): the integer coefficients
+// (centered residues mod q_0, which must be below q_0 / 2 in magnitude:
+// checked against q_1, BAD_ARG otherwise) reduced mod every p_k; evaluation
+// domain, Montgomery form.
+PtDev pt_qp_from_coeffs(Context &c, const uint64_t *words, int level, double scale, cudaStream_t st);
 CtB ct_copy(Context &c, const CtB &a, cudaStream_t st);
 CtB ct_drop(Context &c, const CtB &a, int level, cudaStream_t st);
+// Ciphertexts b0 .. b0+nb-1 of a batch (a copy), and the reverse: src copied
+// into dst starting at ciphertext b0 (same level).
+CtB ct_slice(Context &c, const CtB &a, int b0, int nb, cudaStream_t st);
+void ct_place(Context &c, CtB &dst, int b0, const CtB &src, cudaStream_t st);
 
 TensorB tensor_new(Context &c, int B, int level);
 // t (+)= coef * (a (x) b); first call with init = true
@@ -78,5 +88,21 @@ struct BsgsTerm {
     std::vector<std::pair<int, const PtDev *>> diags;   // (delta, pre-rotated diagonal)
 };
 CtB bsgs(Context &c, const Keys &k, const std::vector<BsgsTerm> &terms, int n1, int32_t stride, cudaStream_t st);
+
+// One baby set of a double-hoisted BSGS product: baby b is Rot(x, b * stride
+// + offset), kept over the extended basis; diags = (delta, pre-rotated
+// diagonal D'_{g,b} encoded over Q_l * P), delta = g * n1 + b.
+struct BsgsSet {
+    const CtB *x = nullptr;
+    int32_t offset = 0;
+    std::vector<std::pair<int, const PtDev *>> diags;
+};
+// Double-hoisted BSGS product (Bossuat, Mouchet, Troncoso-Pastoriza and
+// Hubaux, Eurocrypt 2021, Sec. 4): one ModUp per distinct input; every baby
+// (P sigma_b(c0) + u0, u1), inner sum and giant-step term over Q_l * P; a
+// giant step brings only the c1 of its inner sum down to Q (ModDown, ModUp,
+// key inner product w) and adds (sigma_g(inner_0) + w_0, w_1); one ModDown of
+// both parts ends the product.  Not rescaled.
+CtB bsgs_dh(Context &c, const Keys &k, const std::vector<BsgsSet> &sets, int n1, int32_t stride, cudaStream_t st);
 
 }  // namespace mmfhe

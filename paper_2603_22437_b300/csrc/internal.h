@@ -181,6 +181,7 @@ struct Context {
     uint64_t *d_dn_phat_mont = nullptr, *d_dn_negp_mont = nullptr;
     std::vector<LevelConsts> lv;     // per level 0..L
     int sum_terms_max = 8;           // products one Montgomery reduction may absorb: n*q_max < 2^64
+    int sum_terms_max_qp = 8;        // the same over every prime of Q * P (extended-basis sums)
     std::unique_ptr<Pool> pool;
     uint64_t launches = 0;
     std::string last_error;
@@ -243,6 +244,7 @@ struct PtDev {
     int level = -1;
     double scale = 0.0;
     bool mont = false;   // words stored as x * 2^64 mod q (Montgomery form)
+    bool qp = false;     // rows over the extended basis: q_0..q_level, then p_0..p_{K-1}
 };
 
 struct Keys {

@@ -102,12 +102,14 @@ __global__ void k_group_sum(uint64_t *out, const uint64_t *in, size_t words, siz
 constexpr int MULTI_X = 64;
 template <int T>
 __global__ void __launch_bounds__(MULTI_X)
-    k_mul_plain_sum_multi(MultiSumTerms a, int B, int logn, int nl, ModTab mt, int accumulate) {
+    k_mul_plain_sum_multi(MultiSumTerms a, int B, int logn, int nl, int nrows, int pid_p0, ModTab mt,
+                          int accumulate) {
     extern __shared__ uint64_t sp[];   // [ng][T][MULTI_X]
     const uint32_t n = 1u << logn;
     const uint32_t tiles = n / MULTI_X;
-    const uint32_t row = blockIdx.x / tiles;          // h * nl + i
-    const int i = (int)(row % (uint32_t)nl);
+    const uint32_t row = blockIdx.x / tiles;          // h * nrows + i
+    const int i = (int)(row % (uint32_t)nrows);       // rows q_0..q_l, then p_0..p_{K-1} (extended basis)
+    const int pid = i < nl ? i : pid_p0 + (i - nl);
     const uint32_t x = (blockIdx.x % tiles) * MULTI_X + threadIdx.x;
     const size_t poff = ((size_t)i << logn) + x;
     const int ng = a.ng, nt = a.nt;
@@ -115,8 +117,8 @@ __global__ void __launch_bounds__(MULTI_X)
 #pragma unroll
         for (int t = 0; t < T; t++)
             sp[(g * T + t) * MULTI_X + threadIdx.x] = (t < nt && a.pt[g][t]) ? __ldg(a.pt[g][t] + poff) : 0;
-    const uint64_t q = mt.q[i], qinv = mt.qinv[i];
-    const size_t wstride = (size_t)2 * nl << logn;
+    const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
+    const size_t wstride = (size_t)2 * nrows << logn;
     const size_t off = ((size_t)row << logn) + x;
     uint64_t v[T], vn[T];
 #pragma unroll
@@ -136,6 +138,102 @@ __global__ void __launch_bounds__(MULTI_X)
         }
 #pragma unroll
         for (int t = 0; t < T; t++) v[t] = vn[t];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Extended-basis (Q_l * P) helpers of the double-hoisted BSGS product.
+// An extended ciphertext batch is [B][2][l+1+K][N]: rows q_0..q_l, then
+// p_0..p_{K-1}, evaluation domain.
+// ---------------------------------------------------------------------------
+
+// (P c0, P c1) over Q_l * P from a ciphertext over Q_l: rows mod q_i times
+// P mod q_i, rows mod p_k zero (P = 0 there).
+__global__ void k_qp_times_p(uint64_t *out, const uint64_t *in, int B, int nl, int K, int logn, ModTab mt,
+                             ModDownConsts dc) {
+    const int nre = nl + K;
+    const size_t total = ((size_t)B * 2 * nre) << logn;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = w >> logn, x = w & ((1u << logn) - 1);
+        const int t = (int)(r % nre);
+        const size_t bh = r / nre;
+        if (t >= nl) {
+            out[w] = 0;
+            continue;
+        }
+        const uint64_t v = in[((bh * nl + t) << logn) + x];
+        out[w] = mm::mul_shoup(v, dc.pmod[t], dc.pmod_sh[t], mt.q[t]);
+    }
+}
+
+// u0 rows mod q_i += P * c0[perm(x)] mod q_i: the baby's c0 term (u = the key
+// inner product of its rotation, [B][2][nre]; c0 of the input, [B][2][nl]).
+__global__ void k_qp_add_pc0(uint64_t *u, const uint64_t *ct, int B, int nl, int K, int logn, uint32_t galois,
+                             ModTab mt, ModDownConsts dc) {
+    const int nre = nl + K;
+    const uint32_t n = 1u << logn;
+    const size_t total = ((size_t)B * nl) << logn;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + threadIdx.x; w < total; w += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(w & (n - 1));
+        const size_t r = w >> logn;
+        const int i = (int)(r % nl);
+        const size_t b = r / nl;
+        const uint32_t px = galois == 1 ? x : mm::galois_perm(x, galois, logn);
+        const uint64_t q = mt.q[i];
+        const uint64_t pc = mm::mul_shoup(ct[((b * 2 * nl + i) << logn) + px], dc.pmod[i], dc.pmod_sh[i], q);
+        uint64_t *U = u + ((b * 2 * nre + i) << logn) + x;
+        *U = mm::add_mod(*U, pc, q);
+    }
+}
+
+// Giant-step term of the double-hoisted product, accumulated over Q_l * P:
+// w != null: acc_0 (+)= in_0[perm(x)] + w_0, acc_1 (+)= w_1 (in = the inner
+// sum, w = the key inner product of its ModDown'd c1); w == null (no
+// rotation): acc (+)= in.  All [B][2][nre][N].
+__global__ void k_qp_giant_acc(uint64_t *acc, const uint64_t *in, const uint64_t *w, int B, int nl, int K, int logn,
+                               uint32_t galois, ModTab mt, int pid_p0, int accumulate) {
+    const int nre = nl + K;
+    const uint32_t n = 1u << logn;
+    const size_t total = ((size_t)B * 2 * nre) << logn;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(e & (n - 1));
+        const size_t r = e >> logn;
+        const int t = (int)(r % nre);
+        const int h = (int)((r / nre) & 1);
+        const int pid = t < nl ? t : pid_p0 + (t - nl);
+        const uint64_t q = mt.q[pid];
+        uint64_t v;
+        if (!w) {
+            v = in[e];
+        } else {
+            v = w[e];
+            if (h == 0) {
+                const uint32_t px = galois == 1 ? x : mm::galois_perm(x, galois, logn);
+                v = mm::add_mod(v, in[((r << logn)) + px], q);
+            }
+        }
+        acc[e] = accumulate ? mm::add_mod(acc[e], v, q) : v;
+    }
+}
+
+// Rows of the special primes of a plan constant from its coefficient-form Q
+// rows ([nl + K][N], rows 0..nl-1 given): the integer coefficient c is the
+// centered residue of row 0, exact while |c| < q_0 / 2 (checked against row
+// 1 when there is one: a mismatch sets *err), reduced mod every p_k.
+__global__ void k_qp_extend(uint64_t *pt, int nl, int K, int logn, ModTab mt, int pid_p0, int *err) {
+    const uint32_t n = 1u << logn;
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        const uint64_t q0 = mt.q[0], r0 = pt[x];
+        const bool neg = r0 > (q0 >> 1);
+        const uint64_t mag = neg ? q0 - r0 : r0;
+        if (nl > 1) {
+            const uint64_t q1 = mt.q[1], m1 = mag % q1;
+            if ((neg ? (m1 ? q1 - m1 : 0) : m1) != pt[n + x]) atomicOr(err, 1);
+        }
+        for (int k = 0; k < K; k++) {
+            const uint64_t pk = mt.q[pid_p0 + k], m = mag % pk;
+            pt[((size_t)(nl + k) << logn) + x] = neg ? (m ? pk - m : 0) : m;
+        }
     }
 }
 
@@ -662,10 +760,10 @@ void k_launch_mul_plain_sum(Context &c, uint64_t *out, const SumTerms &terms, in
 }
 
 void k_launch_mul_plain_sum_multi(Context &c, const MultiSumTerms &terms, int B, int level, bool acc,
-                                  cudaStream_t st) {
-    const int nl = level + 1;
+                                  cudaStream_t st, bool qp) {
+    const int nl = qp ? level + 1 + c.num_p : level + 1;   // rows per part (extended basis: + K)
     if (B <= 0 || terms.ng <= 0 || terms.nt <= 0) return;
-    if (terms.ng > MULTI_SUM_GROUPS || terms.nt > MAX_SUM_TERMS || terms.nt > c.sum_terms_max)
+    if (terms.ng > MULTI_SUM_GROUPS || terms.nt > MAX_SUM_TERMS || terms.nt > (qp ? c.sum_terms_max_qp : c.sum_terms_max))
         throw Error(MMFHE_ERR_BAD_ARG, "mul_plain_sum_multi: too many groups or terms");
     if (c.n % MULTI_X) throw Error(MMFHE_ERR_BAD_ARG, "mul_plain_sum_multi: ring too small");
     const int T = terms.nt <= 8 ? 8 : MAX_SUM_TERMS;
@@ -678,8 +776,8 @@ void k_launch_mul_plain_sum_multi(Context &c, const MultiSumTerms &terms, int B,
     auto go = [&](auto kern) {
         if (smem > 48 * 1024) CK(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         kernel_begin(c, st);
-        kern<<<g, MULTI_X, smem, st>>>(terms, B, c.logn, nl, c.mods, acc ? 1 : 0);
-        kernel_end(c, "mul_plain_sum", g, dim3(MULTI_X), bytes, st);
+        kern<<<g, MULTI_X, smem, st>>>(terms, B, c.logn, level + 1, nl, c.num_q, c.mods, acc ? 1 : 0);
+        kernel_end(c, qp ? "mul_plain_sum_qp" : "mul_plain_sum", g, dim3(MULTI_X), bytes, st);
         CK(cudaGetLastError());
     };
     if (T == 8) go(k_mul_plain_sum_multi<8>);
@@ -695,6 +793,43 @@ void k_launch_lincomb(Context &c, uint64_t *out, const LincombTerms &terms, int 
     dim3 g = grid_for(words);
     LAUNCH(c, "lincomb", W8(words * (terms.n + (acc ? 2 : 1))), g, k_lincomb, out, terms, words, c.logn, nl, c.mods,
            acc ? 1 : 0);
+}
+
+void k_launch_qp_times_p(Context &c, uint64_t *out, const uint64_t *in, int B, int level, const ModDownConsts &dc,
+                         cudaStream_t st) {
+    const int nl = level + 1, K = c.num_p;
+    const size_t work = (size_t)B * 2 * (nl + K) * c.n;
+    if (!work) return;
+    LAUNCH(c, "qp_times_p", W8(work + (size_t)B * 2 * nl * c.n), grid_for(work), k_qp_times_p, out, in, B, nl, K,
+           c.logn, c.mods, dc);
+}
+
+void k_launch_qp_add_pc0(Context &c, uint64_t *u, const uint64_t *ct, int B, int level, uint32_t galois,
+                         const ModDownConsts &dc, cudaStream_t st) {
+    const int nl = level + 1;
+    const size_t work = (size_t)B * nl * c.n;
+    if (!work) return;
+    LAUNCH(c, "qp_add_pc0", W8(3 * work), grid_for(work), k_qp_add_pc0, u, ct, B, nl, c.num_p, c.logn, galois,
+           c.mods, dc);
+}
+
+void k_launch_qp_giant_acc(Context &c, uint64_t *acc, const uint64_t *in, const uint64_t *w, int B, int level,
+                           uint32_t galois, bool accumulate, cudaStream_t st) {
+    const int nl = level + 1;
+    const size_t work = (size_t)B * 2 * (nl + c.num_p) * c.n;
+    if (!work) return;
+    // reads the term's operands (w and the c0 half of in, or all of in), writes acc (and reads it
+    // when accumulating)
+    const size_t operands = w ? work + work / 2 : work;
+    const double bytes = W8(operands + work * (accumulate ? 2 : 1));
+    LAUNCH(c, "qp_giant_acc", bytes, grid_for(work), k_qp_giant_acc, acc, in, w, B, nl, c.num_p, c.logn, galois,
+           c.mods, c.num_q, accumulate ? 1 : 0);
+}
+
+void k_launch_qp_extend(Context &c, uint64_t *pt, int level, int *err, cudaStream_t st) {
+    const int nl = level + 1;
+    LAUNCH(c, "qp_extend", W8((size_t)(2 + c.num_p) * c.n), grid_for(c.n), k_qp_extend, pt, nl, c.num_p, c.logn,
+           c.mods, c.num_q, err);
 }
 
 void k_launch_permute(Context &c, uint64_t *out, const uint64_t *in, size_t rows, uint32_t galois, cudaStream_t st) {

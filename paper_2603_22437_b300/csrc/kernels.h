@@ -90,6 +90,7 @@ struct CombineArgs {
     size_t add_stride;
     uint32_t galois;
     const uint64_t *plus;         // [B][2][level+1][N]
+    size_t u_stride = 0;          // rows between consecutive blocks of u (0: level+1+K)
 };
 
 // Operands of the key inner product when its output words are formed inside
@@ -110,6 +111,11 @@ struct KeyipArgs {
 };
 void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, int B, int level,
                         cudaStream_t st, const KeyipArgs *ka = nullptr);
+// The same over `blocks` single blocks (no window/part structure: add0, add1
+// and the key-inner-product operands unused), block k of u at
+// u + k * u_stride rows, out [blocks][level+1][N].
+void launch_moddown_ntt_blocks(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, size_t blocks,
+                               int level, cudaStream_t st);
 // The P rows of the key inner product, formed in the load of the inverse
 // NTT's contiguous pass, then the strided pass: z[bh][k] =
 // [u_{p_k} Phat_k^-1]_{p_k} in coefficient form ([B*2][K][N]).
@@ -137,8 +143,24 @@ struct MultiSumTerms {
     uint64_t *out[MULTI_SUM_GROUPS];
     int nt, ng;
 };
+// qp: every operand and output is over the extended basis Q_l * P
+// ([B][2][l+1+K][N], constants [l+1+K][N]).
 void k_launch_mul_plain_sum_multi(Context &c, const MultiSumTerms &terms, int B, int level, bool acc,
-                                  cudaStream_t st);
+                                  cudaStream_t st, bool qp = false);
+
+// Extended-basis helpers of the double-hoisted BSGS product (batches
+// [B][2][l+1+K][N], rows q_0..q_l then p_0..p_{K-1}, evaluation domain):
+// out = (P c0, P c1) from a ciphertext over Q_l ([B][2][l+1][N]);
+void k_launch_qp_times_p(Context &c, uint64_t *out, const uint64_t *in, int B, int level, const ModDownConsts &dc,
+                         cudaStream_t st);
+// u_0 rows mod q_i += P * c0[perm(x)] (c0 of ct [B][2][l+1][N], perm = the Galois map);
+void k_launch_qp_add_pc0(Context &c, uint64_t *u, const uint64_t *ct, int B, int level, uint32_t galois,
+                         const ModDownConsts &dc, cudaStream_t st);
+// acc (+)= (in_0[perm(x)] + w_0, w_1), or acc (+)= in when w is null;
+void k_launch_qp_giant_acc(Context &c, uint64_t *acc, const uint64_t *in, const uint64_t *w, int B, int level,
+                           uint32_t galois, bool accumulate, cudaStream_t st);
+// rows l+1.. of pt ([l+1+K][N], coefficient form) from its row 0, checked against row 1 (*err |= 1).
+void k_launch_qp_extend(Context &c, uint64_t *pt, int level, int *err, cudaStream_t st);
 
 // Linear combination with scalar constants: out (+)= sum_k s_k * ct_k over a
 // batch at one level, s_k[i] = the scalar's residue mod q_i in Montgomery

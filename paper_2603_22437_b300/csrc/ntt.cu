@@ -234,16 +234,30 @@ void launch_keyip_p_inv(Context &c, uint64_t *z, const KeyipArgs &ka, int B, int
     CK(cudaGetLastError());
 }
 
+static void moddown_ntt_impl(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, size_t blocks,
+                             int level, cudaStream_t st, const KeyipArgs *ka);
+
+void launch_moddown_ntt_blocks(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, size_t blocks,
+                               int level, cudaStream_t st) {
+    if (a.add0 || a.add1) throw Error(MMFHE_ERR_BAD_ARG, "moddown of single blocks takes no window addends");
+    moddown_ntt_impl(c, vtmp, z, a, blocks, level, st, nullptr);
+}
+
 void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, int B, int level,
                         cudaStream_t st, const KeyipArgs *ka) {
+    moddown_ntt_impl(c, vtmp, z, a, (size_t)B * 2, level, st, ka);
+}
+
+static void moddown_ntt_impl(Context &c, uint64_t *vtmp, const uint64_t *z, const CombineArgs &a, size_t blocks,
+                             int level, cudaStream_t st, const KeyipArgs *ka) {
     const int nl = level + 1, nre = nl + c.num_p, K = c.num_p;
-    if (B == 0) return;
+    if (blocks == 0) return;
+    const size_t ustride = a.u_stride ? a.u_stride : (size_t)nre;
     std::vector<int> pids(nl);
     for (int i = 0; i < nl; i++) pids[i] = i;
     RowMap mv = make_map(nl, nl, pids), ms = mv;
     const uint32_t nact = set_active(ms, mv);
     const RowGroups gr = make_groups(mv, c.tune.conv_rows, 0);
-    const size_t blocks = (size_t)B * 2;
     const size_t chunk = 65535 / nact;
     for (size_t b0 = 0; b0 < blocks; b0 += chunk) {
         // chunks hold whole windows, so the (window, h) parity of a block is kept
@@ -251,7 +265,7 @@ void launch_moddown_ntt(Context &c, uint64_t *vtmp, const uint64_t *z, const Com
         const size_t nr = nb * nact;
         CombineArgs ab = a;
         ab.out = a.out + ((b0 * nl) << c.logn);
-        if (ab.u) ab.u = a.u + ((b0 * nre) << c.logn);
+        if (ab.u) ab.u = a.u + ((b0 * ustride) << c.logn);
         if (ab.add0) ab.add0 += (b0 / 2) * a.add_stride;
         if (ab.add1) ab.add1 += (b0 / 2) * a.add_stride;
         if (ab.plus) ab.plus += (b0 * nl) << c.logn;

@@ -484,7 +484,7 @@ __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16,
     const int hi0 = blockIdx.x * Gm::ROWS;
     const uint64_t q = mt.q[pid];
     const size_t base = (size_t)hi0 * Gm::T1;
-    const uint64_t *U = KB ? nullptr : a.u + (((size_t)blk * nre + p) << LOGN);
+    const uint64_t *U = KB ? nullptr : a.u + (((size_t)blk * (a.u_stride ? a.u_stride : (size_t)nre) + p) << LOGN);
     const uint64_t *A = (blk & 1) ? a.add1 : a.add0;
     if (A) A += (size_t)(blk >> 1) * a.add_stride + ((size_t)p << LOGN);
     const uint64_t *Pl = a.plus ? a.plus + (((size_t)blk * nl + p) << LOGN) : nullptr;

@@ -1,0 +1,184 @@
+"""The gesture chain with a learned feature map, on the GPU.
+
+The paper's gesture chain raises the notched power to p (p^2)^2 (soft power
+gamma = 4 and feature weighting; three levels of Table 1's depth 11).  Here
+a learned degree-2 map a p + b p^2 stands in for it (one level), so the
+chain needs depth 9 and its parameter set two Q primes less.  The map is
+learned with the network: the features are linear in (a, b), so one pass of
+the FP64 pipeline gives the features of every candidate; for each b / a of a
+small grid the library's plaintext CUDA trainer fits the network on 1600
+synthetic windows, the ratio with the best accuracy on 400 more is kept, and
+the plain chain's network is trained on the same windows.
+
+Checked: output ciphertexts word for word against the oracle's learned
+circuit (two windows, split and complex-slot packing); the trained learned
+network's held-out accuracy against the plain chain's on the same 400
+held-out windows; and on three held-out full windows the decrypted logits of
+the encrypted learned chain give the labels of its FP64 network."""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import ckks as ck
+from oracle import circuits as cc
+from oracle import params as pm
+from oracle import plain
+from test_gpu_gesture import (encrypt_pairs, expand_first, flat, gesture_config, install, pooled, random_mats)
+from test_gpu_parity import compare_plan_consts, lib_params, load_keys, window_words
+
+pytestmark = pytest.mark.gpu
+
+KEY_SEED = 67
+COEF = (0.7, 2.5)            # the word-exact test's map (any coefficients)
+BETAS = (0.25, 1.0, 4.0, 16.0, 64.0)   # candidate b / a of the learned map (a = 1)
+
+
+def oracle_setup(cfg):
+    P = pm.gesture_learned_params()
+    circ = cc.GestureCircuit(P, cfg)
+    rots = circ.rotations()
+    kd = synth.KeyDraws(KEY_SEED, P.n, P.q, P.p, P.dnum, rots)
+    sk = ck.SecretKey(P, kd.secret)
+    pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
+    rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
+    gks = {ck.key_id(P, k): ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
+    return P, circ, sk, pk, rlk, gks
+
+
+def small(cplx):
+    return cc.GestureConfig(frames=4, feature_coef=COEF, complex_slots=cplx)
+
+
+def _oracle_window(job):
+    """Worker (spawned process): the oracle's output words of window w."""
+    w, cplx = job
+    cfg = small(cplx)
+    P, circ, sk, pk, rlk, gks = oracle_setup(cfg)
+    zt = plain.gesture_preprocess(synth.gesture_window(400 + w, frames=cfg.frames).z)
+    cts = encrypt_pairs(P, pk, circ, zt, 6000 + 100 * w)
+    out = circ.run(cc.Evaluator(P, rlk, gks), circ.constants(random_mats(cfg, 9)), cts)
+    return window_words(flat(cts)), out.words(), out.scale
+
+
+def _features(seed):
+    """Pooled frame sums of p and p^2 (the learned map's two terms) and of the
+    paper's p (p^2)^2, and the label."""
+    w = synth.gesture_window(seed)
+    zt = plain.gesture_preprocess(w.z)
+    r = plain.gesture_features(zt)
+    p = r["p"]
+    return pooled(p.sum(0)), pooled((p * p).sum(0)), pooled(r["feat"]), w.label
+
+
+@pytest.fixture(scope="module")
+def learned():
+    pool = mp.get_context("spawn").Pool(8)
+    pending = pool.map_async(_oracle_window, [(0, False), (1, False), (0, True), (1, True)])
+    feats = pool.map_async(_features, range(30000, 32400), chunksize=25)
+    import paper_2603_22437_b300 as M
+    P, circ, sk, pk, rlk, gks = oracle_setup(small(False))
+    ctx = M.Context(lib_params(P))
+    keys = load_keys(ctx, P, rlk, gks)
+    _, _, sk_c, pk_c, rlk_c, gks_c = oracle_setup(small(True))
+    keys_c = load_keys(ctx, P, rlk_c, gks_c)
+    yield dict(P=P, sk=sk, pk=pk, ctx=ctx, keys=keys, keys_c=keys_c, pending=pending, feats=feats)
+    pool.close()
+    pool.join()
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_learned_gesture_word_exact_two_windows(learned, cplx):
+    import paper_2603_22437_b300 as M
+    P, ctx = learned["P"], learned["ctx"]
+    cfg = small(cplx)
+    circ = cc.GestureCircuit(P, cfg)
+    plan = ctx.plan(gesture_config(M, cfg))
+    assert plan.rotations() == circ.rotations()
+    assert plan.io()[2] == [0]                  # depth 9 on the 10-prime set
+    install(plan, circ.constants(random_mats(cfg, 9)), cfg.chirps)
+    ref = learned["pending"].get(timeout=1800)[2 * int(cplx): 2 * int(cplx) + 2]
+    outs = [np.empty(2 * P.n, dtype=np.uint64) for _ in ref]
+    ctx.eval(plan, learned["keys_c" if cplx else "keys"], [r[0] for r in ref], outs)
+    for w, (_, want, _) in enumerate(ref):
+        assert np.array_equal(outs[w], want.reshape(-1)), "window %d" % w
+    lib = ctx.plan(gesture_config(M, cfg))
+    lib.encode_consts()
+    for l, W in enumerate(random_mats(cfg, 9)):
+        lib.set_fc_layer(l, W)
+    compare_plan_consts(plan, lib, P)
+
+
+def test_learned_map_network_labels(learned):
+    import paper_2603_22437_b300 as M
+    from test_fc_fold import quad_forward
+    P, ctx = learned["P"], learned["ctx"]
+    data = learned["feats"].get(timeout=1800)
+    F1 = np.array([d[0] for d in data])
+    F2 = np.array([d[1] for d in data])
+    Fp = np.array([d[2] for d in data])
+    y = np.array([d[3] for d in data], dtype=np.int32)
+    n_tr, n_va = 1600, 400
+    tr, va, te = slice(0, n_tr), slice(n_tr, n_tr + n_va), slice(n_tr + n_va, None)
+    cfg0 = cc.GestureConfig()
+    dims = (F1.shape[1],) + tuple(cfg0.fc_dims)
+    alpha = float(np.float32(0.1))
+
+    def fit(X):
+        kappa = 1.0 / X[tr].std(axis=0).max()
+        w, _ = ctx.train_poly_net(X[tr] * kappa, y[tr], dims, alpha=alpha, epochs=40, batch=64, lr=0.005, seed=5)
+
+        def acc(s):
+            pred = np.array([quad_forward(w, dims, alpha, x * kappa).argmax() for x in X[s]])
+            return float((pred == y[s]).mean())
+        return w, kappa, acc
+
+    results = {}
+    for beta in BETAS:
+        w, kappa, acc = fit(F1 + beta * F2)
+        results[beta] = (acc(va), w, kappa, acc)
+    beta = max(results, key=lambda b: results[b][0])
+    va_acc, w, kappa, acc = results[beta]
+    test_learned = acc(te)
+    _, _, acc_p = fit(Fp)
+    test_plain = acc_p(te)
+    print("learned map p + %g p^2: validation %.3f, held-out %.3f; plain p (p^2)^2 held-out %.3f"
+          % (beta, va_acc, test_learned, test_plain))
+    assert test_learned > 0.6 and test_learned >= test_plain - 0.05, (test_learned, test_plain)
+    # the encrypted learned chain with this network: labels of the FP64 network
+    cfg = cc.GestureConfig(feature_coef=(1.0, beta))
+    circ = cc.GestureCircuit(P, cfg)
+    first, tail = M.fold_poly_net_wide(dims, alpha, w, cfg.width)
+    mats = [expand_first(first, cfg, kappa), tail[0], tail[1]]
+    plan = ctx.plan(gesture_config(M, cfg))
+    plan.encode_consts()
+    for l, Wm in enumerate(mats):
+        plan.set_fc_layer(l, Wm)
+    _, _, sk, pk, rlk, gks = oracle_setup(cfg)
+    keys = load_keys(ctx, P, rlk, gks)
+    sel = list(range(30000 + n_tr + n_va, 30000 + n_tr + n_va + 3))
+    zts = [plain.gesture_preprocess(synth.gesture_window(s).z) for s in sel]
+    cts = [encrypt_pairs(P, pk, circ, zt, 9000 + 200 * i) for i, zt in enumerate(zts)]
+    outs = [np.empty(2 * P.n, dtype=np.uint64) for _ in sel]
+    ctx.eval(plan, keys, [window_words(flat(c)) for c in cts], outs)
+    C = cfg.fc_dims[-1]
+    for j, zt in enumerate(zts):
+        feat = plain.gesture_features(zt, cfg)["feat"]
+        want = cc.gesture_forward(mats, feat, cfg)[:C]
+        quad = quad_forward(w, dims, alpha, pooled(feat) * kappa)
+        o = outs[j].reshape(2, 1, P.n)
+        got = ck.decrypt_decode(P, sk, ck.Ciphertext(o[0], o[1], 0, logits_scale(P, circ)))[:C]
+        assert got.argmax() == want.argmax() == quad.argmax()
+        assert np.allclose(got, want, atol=1e-4 * max(1.0, np.abs(want).max()))
+
+
+def logits_scale(P, circ):
+    """Scale of the learned chain's logits: FC1's output scale, then square,
+    FC2, square, FC3 with constants at q_l (features at level L - 4)."""
+    q, L = P.q, P.L
+    s = circ.fc1_out_scale(P.scale)
+    s = s * s / q[L - 5]
+    s = s * q[L - 6] / q[L - 6]
+    s = s * s / q[L - 7]
+    return s * q[L - 8] / q[L - 8]

@@ -83,10 +83,16 @@ def test_block_diagonal_bsgs_in_the_clear():
 
 
 def test_hybrid_fc1_in_the_clear():
+    """FC1's extended diagonals restated on slot vectors give W0 x in slots
+    0..width-2 of every period and 0 in slot width-1, the slot of the
+    constant 1 the later layers' biases read (its bias is added after FC1).
+    Row width-1 of W0 is made nonzero, so a rule that let it into the
+    product would leave (W0 x)[width-1] in the constant's slot and fail."""
     P = tiny_params()
     circ = cc.GestureCircuit(P, TINY)
     mats = random_gesture_net(TINY, 3)
-    W0 = mats[0][:, : TINY.ard]
+    W0 = mats[0][:, : TINY.ard].copy()
+    W0[TINY.width - 1] = np.random.default_rng(5).normal(size=TINY.ard)
     x = np.random.default_rng(4).normal(size=TINY.ard)
     xs = np.zeros(P.slots)
     for j in range(circ.lay.k):
@@ -95,7 +101,10 @@ def test_hybrid_fc1_in_the_clear():
     y = t.copy()
     for i in range(int(np.log2(circ.lay.ard_pad // TINY.width))):
         y = y + cc.rotate_slots(y, TINY.width << i)
-    assert np.allclose(y, np.tile(W0 @ x, P.slots // TINY.width), atol=1e-9)
+    want = W0 @ x
+    assert abs(want[TINY.width - 1]) > 1e-3
+    want[TINY.width - 1] = 0.0
+    assert np.allclose(y, np.tile(want, P.slots // TINY.width), atol=1e-9)
 
 
 def test_depth_and_rotations_full_size():
@@ -205,6 +214,63 @@ def test_complex_slot_gesture_circuit_decrypts_to_fp64(frames):
     feat = circ.features(ev, consts, cts)
     assert feat.level == P.L - 6
     dec = ck.decrypt_decode(P, sk, feat)
+    for j in range(circ.lay.k):
+        got = dec[j * circ.lay.ard_pad: j * circ.lay.ard_pad + cfg.ard]
+        assert np.allclose(got, ref.reshape(-1), atol=1e-9 * max(1.0, np.abs(ref).max()))
+    out = circ.run(ev, consts, cts)
+    assert out.level == 0
+    logits = ck.decrypt_decode(P, sk, out)[: cfg.fc_dims[-1]]
+    want = cc.gesture_forward(mats, ref, cfg)[: cfg.fc_dims[-1]]
+    assert np.allclose(logits, want, rtol=1e-6, atol=1e-6 * np.abs(want).max())
+
+
+def test_learned_feature_map_depth_9_full_size():
+    """The learned map a p + b p^2 takes one level where p (p^2)^2 takes
+    three: the chain ends at level 0 on the 10-prime parameter set."""
+    P = pm.gesture_learned_params()
+    circ = cc.GestureCircuit(P, cc.GestureConfig(feature_coef=(1.0, 2.0)))
+    ev = cc.CountingEvaluator(P)
+
+    class Any(dict):
+        def __missing__(self, k):
+            return cc._Shape(0)
+    pairs = [(cc._Shape(P.L), cc._Shape(P.L)) for _ in range(circ.lay.pairs)]
+    assert P.L == 9 and circ.run(ev, Any(), pairs).level == 0
+    assert circ.rotations() == cc.GestureCircuit(pm.gesture_params()).rotations()
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+def test_learned_feature_map_decrypts_to_fp64(cplx):
+    """The learned feature map in the encrypted chain (test-only ring with the
+    learned chain's 10-prime modulus shape) decrypts to the FP64 features
+    a p + b p^2 summed over frames, and its logits to the FP64 network."""
+    cfg = cc.GestureConfig(antennas=2, bins=4, chirps=8, frames=20, fc_dims=(7, 5, 3), width=16,
+                           feature_coef=(0.7, 2.5), complex_slots=cplx)
+    P = pm.make_params(11, 10, 60, 50, 4, 60, 3, 50)
+    circ = cc.GestureCircuit(P, cfg)
+    rots = circ.rotations()
+    kd = synth.KeyDraws(53, P.n, P.q, P.p, P.dnum, rots)
+    sk = ck.SecretKey(P, kd.secret)
+    pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
+    rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
+    gks = {ck.key_id(P, k): ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
+    mats = random_gesture_net(cfg, 7)
+    consts = circ.constants(mats)
+    zt = tiny_window(8, cfg)
+    if cplx:
+        cts = [ck.encrypt(P, pk, ck.encode(P, v, P.scale, P.L), *synth.encryption_draws(90 + 2 * i, P.n))
+               for i, v in enumerate(circ.lay.pack_complex(zt))]
+    else:
+        cts = [tuple(ck.encrypt(P, pk, ck.encode(P, v, P.scale, P.L), *synth.encryption_draws(90 + 2 * i + h, P.n))
+                     for h, v in enumerate(pair)) for i, pair in enumerate(circ.lay.pack(zt))]
+    ev = cc.Evaluator(P, rlk, gks)
+    r = plain.gesture_features(zt, cfg)
+    a, b = cfg.feature_coef
+    assert np.allclose(r["f"], a * r["p"] + b * r["p"] ** 2)
+    feat = circ.features(ev, consts, cts)
+    assert feat.level == P.L - 4
+    dec = ck.decrypt_decode(P, sk, feat)
+    ref = r["feat"]
     for j in range(circ.lay.k):
         got = dec[j * circ.lay.ard_pad: j * circ.lay.ard_pad + cfg.ard]
         assert np.allclose(got, ref.reshape(-1), atol=1e-9 * max(1.0, np.abs(ref).max()))
