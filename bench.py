@@ -642,8 +642,8 @@ def accuracy_line():
     if not os.path.exists(p):
         return None
     j = json.load(open(p))
-    keys = ("windows", "inside_precision_window", "below_floor", "above_ceiling", "mae_bpm_inside",
-            "max_bpm_inside", "max_err_target_bin")
+    keys = ("windows", "inside_precision_window", "within_1e-3_bpm_both_bands", "below_floor", "above_ceiling",
+            "mae_bpm_inside", "max_bpm_inside", "max_err_target_bin")
     out = {k: j[k] for k in keys if k in j}
     out["source"] = ACCURACY_PROFILE + " (tests/test_gpu_accuracy.py, B = 64, seeds 4000..4063)"
     return out

@@ -108,7 +108,8 @@ def install(plan, consts, D):
 
 def gesture_config(M, cfg):
     return M.gesture_config(antennas=cfg.antennas, bins=cfg.bins, chirps=cfg.chirps, frames=cfg.frames,
-                            fc_dims=cfg.fc_dims, fc_width=cfg.width, complex_slots=cfg.complex_slots)
+                            fc_dims=cfg.fc_dims, fc_width=cfg.width, complex_slots=cfg.complex_slots,
+                            feature_coef=cfg.feature_coef)
 
 
 def test_gesture_word_exact_two_windows(gest):
