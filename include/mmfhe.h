@@ -60,6 +60,7 @@ typedef int32_t mmfhe_status;
 #define MMFHE_ERR_TIMEOUT (-7)        /* bounded wait expired; work is still queued */
 #define MMFHE_ERR_NOT_FOUND (-8)      /* missing Galois key / constant */
 #define MMFHE_ERR_BUSY (-9)           /* object in use */
+#define MMFHE_ERR_CANCELLED (-10)     /* a queued serving request was cancelled */
 
 #define MMFHE_MAX_Q 32
 #define MMFHE_MAX_P 8
@@ -710,6 +711,7 @@ typedef struct mmfhe_server_stats {
     double mean_batch;            /* windows per batch */
     double p50_ms, p99_ms;        /* submit -> output written, completed windows */
     double windows_per_s;         /* completed / (last completion - first submission) */
+    uint64_t cancelled;           /* requests cancelled while queued */
 } mmfhe_server_stats;
 typedef struct mmfhe_server mmfhe_server;
 /* base: the circuit every window runs (one plan per frame count, created on
@@ -743,10 +745,17 @@ mmfhe_status mmfhe_server_set_const(mmfhe_server *s, uint32_t frames, uint32_t i
  * for an unknown user. */
 mmfhe_status mmfhe_server_submit(mmfhe_server *s, uint64_t user_id, uint32_t frames, const uint64_t *in,
                                  uint64_t *out, uint64_t *ticket);
+/* Cancel a window that is still queued: it is never dispatched, its output
+ * is not written, and its wait returns CANCELLED.  A window already running on
+ * the GPU (or complete) is not interrupted: BUSY.  NOT_FOUND for an unknown
+ * ticket. */
+mmfhe_status mmfhe_server_cancel(mmfhe_server *s, uint64_t ticket);
 /* Wait up to timeout_ms for a window: OK (output written; *latency_ms =
- * submit -> completion), TIMEOUT, or the status its batch failed with. */
+ * submit -> completion), TIMEOUT, CANCELLED, or the status its batch failed
+ * with. */
 mmfhe_status mmfhe_server_wait(mmfhe_server *s, uint64_t ticket, uint32_t timeout_ms, double *latency_ms);
-/* Wait up to timeout_ms until every submitted window has completed. */
+/* Wait up to timeout_ms until every submitted window has completed, failed
+ * or been cancelled. */
 mmfhe_status mmfhe_server_drain(mmfhe_server *s, uint32_t timeout_ms);
 mmfhe_status mmfhe_server_stats_get(mmfhe_server *s, mmfhe_server_stats *out);
 /* Stop the worker after the queued windows complete, free everything. */

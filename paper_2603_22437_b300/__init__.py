@@ -624,6 +624,10 @@ class Server:
         self._live[t.value] = (inp, out)
         return t.value
 
+    def cancel(self, ticket):
+        """Cancel a window that is still queued (BUSY once it runs)."""
+        self.ctx._c(_lib.lib().mmfhe_server_cancel(self.h, ticket))
+
     def wait(self, ticket, timeout_ms=600000):
         """Latency (ms) of a completed window; raises on timeout or failure."""
         lat = ctypes.c_double()

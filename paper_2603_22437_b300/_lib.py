@@ -18,7 +18,7 @@ MAX_Q, MAX_P = 32, 8
 OK = 0
 ERRORS = {
     -1: "BAD_ARG", -2: "BAD_BLOB", -3: "PARAM_MISMATCH", -4: "LEVEL_MISMATCH", -5: "OUT_OF_MEMORY",
-    -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "BUSY",
+    -6: "CUDA", -7: "TIMEOUT", -8: "NOT_FOUND", -9: "BUSY", -10: "CANCELLED",
 }
 CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_FC, CIRCUIT_VITAL_PER_FRAME, CIRCUIT_GESTURE = 1, 2, 3, 4, 5
 CONST_TAGS = {1: "idx", 2: "one", 3: "fir", 4: "dre", 5: "dim", 6: "fw", 7: "fone", 8: "dft_c", 9: "dft_s",
@@ -87,7 +87,8 @@ class ServerConfig(ctypes.Structure):
 class ServerStats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "batches", "key_loads",
                                                 "key_evictions", "keys_resident", "key_bytes")] + \
-               [(n, ctypes.c_double) for n in ("mean_batch", "p50_ms", "p99_ms", "windows_per_s")]
+               [(n, ctypes.c_double) for n in ("mean_batch", "p50_ms", "p99_ms", "windows_per_s")] + \
+               [("cancelled", ctypes.c_uint64)]
 
 
 class MemStats(ctypes.Structure):
@@ -154,6 +155,7 @@ _SIGS = {
     "mmfhe_ntt32_destroy": [_VP],
     "mmfhe_server_submit": [_VP, _U64, _U32, _VP, _VP, ctypes.POINTER(_U64)],
     "mmfhe_server_wait": [_VP, _U64, _U32, ctypes.POINTER(ctypes.c_double)],
+    "mmfhe_server_cancel": [_VP, _U64],
     "mmfhe_server_drain": [_VP, _U32],
     "mmfhe_server_stats_get": [_VP, _VP],
     "mmfhe_server_destroy": [_VP],

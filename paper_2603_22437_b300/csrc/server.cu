@@ -74,7 +74,7 @@ struct mmfhe_server {
     std::map<uint32_t, std::map<uint32_t, std::vector<uint64_t>>> const_words;
 
     // statistics (guarded by mu)
-    uint64_t submitted = 0, completed = 0, failed = 0, batches = 0, batch_windows = 0;
+    uint64_t submitted = 0, completed = 0, failed = 0, cancelled = 0, batches = 0, batch_windows = 0;
     uint64_t key_loads = 0, key_evictions = 0;
     std::vector<double> lat_ms;
     Clock::time_point t_first{}, t_last{};
@@ -502,6 +502,26 @@ mmfhe_status mmfhe_server_submit(mmfhe_server *s, uint64_t user_id, uint32_t fra
     return MMFHE_OK;
 }
 
+mmfhe_status mmfhe_server_cancel(mmfhe_server *s, uint64_t ticket) {
+    if (!s) return sfail(nullptr, MMFHE_ERR_BAD_ARG, "null server");
+    {
+        std::lock_guard<std::mutex> g(s->mu);
+        auto it = s->reqs.find(ticket);
+        if (it == s->reqs.end()) return sfail(s->c, MMFHE_ERR_NOT_FOUND, "unknown ticket");
+        mmfhe_server::Req &r = it->second;
+        if (r.state != mmfhe_server::QUEUED) return sfail(s->c, MMFHE_ERR_BUSY, "the window is running or complete");
+        auto q = std::find(s->queue.begin(), s->queue.end(), ticket);
+        if (q == s->queue.end()) return sfail(s->c, MMFHE_ERR_BUSY, "the window is being dispatched");
+        s->queue.erase(q);
+        r.state = mmfhe_server::FAILED;
+        r.status = MMFHE_ERR_CANCELLED;
+        r.t_done = Clock::now();
+        s->cancelled++;
+    }
+    s->cv_done.notify_all();
+    return MMFHE_OK;
+}
+
 mmfhe_status mmfhe_server_wait(mmfhe_server *s, uint64_t ticket, uint32_t timeout_ms, double *latency_ms) {
     if (!s) return sfail(nullptr, MMFHE_ERR_BAD_ARG, "null server");
     std::unique_lock<std::mutex> lk(s->mu);
@@ -520,7 +540,7 @@ mmfhe_status mmfhe_server_drain(mmfhe_server *s, uint32_t timeout_ms) {
     if (!s) return sfail(nullptr, MMFHE_ERR_BAD_ARG, "null server");
     std::unique_lock<std::mutex> lk(s->mu);
     const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
-                                        [&] { return s->completed + s->failed == s->submitted; });
+                                        [&] { return s->completed + s->failed + s->cancelled == s->submitted; });
     return ok ? MMFHE_OK : MMFHE_ERR_TIMEOUT;
 }
 
@@ -531,6 +551,7 @@ mmfhe_status mmfhe_server_stats_get(mmfhe_server *s, mmfhe_server_stats *out) {
     out->submitted = s->submitted;
     out->completed = s->completed;
     out->failed = s->failed;
+    out->cancelled = s->cancelled;
     out->batches = s->batches;
     out->key_loads = s->key_loads;
     out->key_evictions = s->key_evictions;

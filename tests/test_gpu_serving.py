@@ -201,3 +201,48 @@ def test_serving_vital_and_gesture_windows_concurrently(gsmall):
                 ctx.eval(plan, k, [x], [ref])
                 assert np.array_equal(out, ref), "window %d (kind %d, user %d)" % (i, kind, u)
             k.unload()
+
+
+def test_cancelled_request_never_runs(gsmall):
+    """A queued window is cancelled before its batch is dispatched (the
+    server holds its first batch up to 3 s for more windows): its wait
+    returns CANCELLED and its output buffer stays untouched, the windows
+    around it complete with the words they have alone, and a complete
+    window or an unknown ticket cannot be cancelled."""
+    import paper_2603_22437_b300 as M
+    P, ctx = gsmall["P"], gsmall["ctx"]
+    base = M.fir_dft_config(bins=40)
+    plan = ctx.plan(base)
+    plan.encode_consts()
+    relin, gal = user_keys(P, plan.rotations(), 77)
+    n_in, _, lv = plan.io()
+    out_words = sum(2 * (l + 1) * P.n for l in lv)
+    srv = ctx.server(base, max_batch=8, streams=1, batch_wait_us=3_000_000)
+    srv.add_user(5, relin, gal)
+    xs = [np.ascontiguousarray(rand_ct(P, P.L, 700 + i, n_in).reshape(-1)) for i in range(3)]
+    outs = [np.zeros(out_words, dtype=np.uint64) for _ in xs]
+    tickets = [srv.submit(5, 200, x, o) for x, o in zip(xs, outs)]
+    srv.cancel(tickets[1])
+    with pytest.raises(M.MmfheError) as e:
+        srv.wait(tickets[1])
+    assert e.value.name == "CANCELLED"
+    for i in (0, 2):
+        assert srv.wait(tickets[i]) > 0
+    srv.drain()
+    st = srv.stats()
+    assert st["cancelled"] == 1 and st["completed"] == 2 and st["failed"] == 0
+    for name, fn in (("BUSY", lambda: srv.cancel(tickets[0])), ("NOT_FOUND", lambda: srv.cancel(987654))):
+        with pytest.raises(M.MmfheError) as e:
+            fn()
+        assert e.value.name == name
+    srv.close()
+    assert not outs[1].any()
+    k = ctx.keys(55)
+    k.set_relin(relin)
+    for r, w in gal.items():
+        k.set_galois(r, w)
+    for i in (0, 2):
+        ref = np.empty(out_words, dtype=np.uint64)
+        ctx.eval(plan, k, [xs[i]], [ref])
+        assert np.array_equal(outs[i], ref), "window %d" % i
+    k.unload()
