@@ -78,7 +78,8 @@ def parse():
     ap.add_argument("--complex-slots", action="store_true",
                     help="vital and gesture workloads: Re + i Im in one complex slot (half the input ciphertexts)")
     ap.add_argument("--tiles", default=None,
-                    help="cols_width,rows_threads,keyip_windows,conv_rows: set the tile shapes instead of autotuning")
+                    help="cols_width,rows_threads,keyip_windows,conv_rows[,keyip_pipe]: set the tile shapes instead "
+                         "of autotuning")
     ap.add_argument("--keyip-fusion", action="store_true",
                     help="form the key inner product inside the ModDown passes instead of storing it with its "
                          "own kernel (ablation; same words, slower on B300)")
@@ -424,14 +425,48 @@ def ncu_traffic(kernel, batch, workload=None):
     return k.get("dram_bytes_per_launch_full_size") * batch / sec.get("batch", batch)
 
 
+ISSUE_PROFILE = os.path.join("profiles", "ncu_issue_rates.json")
+SM_COUNT = 148
+ISSUE_PER_SM_CLK = 4     # one warp instruction per clock from each of an SM's four schedulers
+
+
+def ncu_issue(kernel, sm_mhz):
+    """The dominant kernel's instruction issue against the hardware: warp
+    instructions per active SM cycle from the committed ncu capture (one
+    kernel, two launches, --clock-control none) of the current kernel
+    sources, against the issue limit of 4 per SM per clock x 148 SMs x the SM
+    clock sampled during the timed region; and each integer pipe's share of
+    its own peak (ncu's pct_of_peak_sustained_active)."""
+    p = os.path.join(ROOT, ISSUE_PROFILE)
+    if not os.path.exists(p):
+        return None
+    j = json.load(open(p))
+    if j.get("csrc_hash") != csrc_hash():
+        return None
+    k = j.get("kernels", {}).get(kernel)
+    if k is None:
+        return None
+    ipc = k["inst_per_active_sm_cycle"]
+    clk = sm_mhz or k["sm_mhz"]
+    return {"inst_per_sm_cycle": ipc, "issue_limit_per_sm_cycle": ISSUE_PER_SM_CLK,
+            "achieved_warp_inst_per_s": ipc * SM_COUNT * clk * 1e6,
+            "peak_warp_inst_per_s": ISSUE_PER_SM_CLK * SM_COUNT * clk * 1e6,
+            "frac": ipc / ISSUE_PER_SM_CLK, "sm_mhz": clk,
+            "pipes_pct_of_peak": k["pipes_pct_of_peak"], "warps_active_pct": k.get("warps_active_pct"),
+            "stalls_per_issue": k.get("stalls_per_issue"),
+            "source": ISSUE_PROFILE + " (" + k.get("capture", "") + ")"}
+
+
 def pick_tiles(ctx, args, batch):
     """Tile shapes: given (--tiles), defaults (--no-autotune) or autotuned."""
     fused = 1 if args.keyip_fusion else 0
     if args.tiles:
-        ctx.set_tuning(*[int(v) for v in args.tiles.split(",")], keyip_fused=fused)
+        v = [int(x) for x in args.tiles.split(",")]
+        ctx.set_tuning(*v[:4], keyip_fused=fused, keyip_pipe=v[4] if len(v) > 4 else 0)
         return ctx.tuning()
     t = ctx.tuning() if args.no_autotune else ctx.autotune(batch)
-    ctx.set_tuning(t["ntt_cols_width"], t["ntt_rows_threads"], t["keyip_windows"], t["conv_rows"], fused)
+    ctx.set_tuning(t["ntt_cols_width"], t["ntt_rows_threads"], t["keyip_windows"], t["conv_rows"], fused,
+                   t["keyip_pipe"])
     return ctx.tuning()
 
 
@@ -600,6 +635,7 @@ def run_mine(args, rank, world, local):
     ctx.profile(False)
     bf64_peak, bf32_peak = ctx.butterfly_peak()
     roofline = roofline_of(prof, bf64_peak, bf32_peak, B, ctx.mac_peak())
+    roofline["issue"] = ncu_issue(roofline["kernel"], clk.get("sm_mhz") if clk else None)
     line = {
         "metric": METRIC, "value": value, "unit": "windows/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
@@ -642,9 +678,13 @@ def accuracy_line():
     if not os.path.exists(p):
         return None
     j = json.load(open(p))
-    keys = ("windows", "inside_precision_window", "within_1e-3_bpm_both_bands", "below_floor", "above_ceiling",
-            "mae_bpm_inside", "max_bpm_inside", "max_err_target_bin")
+    keys = ("windows", "copies", "split_windows", "inside_precision_window", "within_1e-3_bpm_both_bands",
+            "below_floor", "above_ceiling", "mae_bpm", "max_bpm", "max_err_target_bin")
     out = {k: j[k] for k in keys if k in j}
+    if j.get("copies"):
+        # a window whose two bands need separate normalization factors is
+        # encrypted twice: ciphertext windows evaluated per client window
+        out["copies_per_window"] = j["copies"] / j["windows"]
     out["source"] = ACCURACY_PROFILE + " (tests/test_gpu_accuracy.py, B = 64, seeds 4000..4063)"
     return out
 

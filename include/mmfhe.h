@@ -364,8 +364,9 @@ typedef struct mmfhe_circuit_config {
 #define MMFHE_FEATURE_LEARNED 1
 
 /* Constant tags of mmfhe_const_key.tag */
-#define MMFHE_CONST_IDX 1   /* side branch: bin-index vector of group `index` */
-#define MMFHE_CONST_ONE 2   /* side branch: ones vector of group `index` */
+#define MMFHE_CONST_IDX 1   /* VITAL side branch: bin index of group g's bins at the start of its packed
+                               frame block (-g mod G'); VITAL_PER_FRAME: bin r in slot r */
+#define MMFHE_CONST_ONE 2   /* the same positions holding 1 */
 #define MMFHE_CONST_FIR 3   /* FIR diagonal delta=`index` of band `band` (pre-rotated) */
 #define MMFHE_CONST_DRE 4   /* VITAL DFT rows of band `band`, diagonal `index`: Re X_k in row k, Im X_k in
                                row k + F_pad/2 (both bands run in one BSGS product) */
@@ -388,6 +389,9 @@ typedef struct mmfhe_circuit_config {
 #define MMFHE_CONST_NOTCH_B 18 /* GESTURE, learned feature map: b times the notch mask */
 #define MMFHE_CONST_FEAT_A 19  /* GESTURE, learned feature map: a on every active slot, encoded at the
                                   scale of the notched power (one level below the notch) */
+#define MMFHE_CONST_PMASK 20   /* VITAL side branch: 1 on the first F_pad / G' frames of every bin slot
+                                  (G' = groups rounded up to a power of two), the block each group's
+                                  frame sums are kept in before the groups are packed */
 
 typedef struct mmfhe_const_key {
     uint32_t tag, band, index, level;
@@ -566,6 +570,11 @@ typedef struct mmfhe_tuning {
                                     the inverse NTT's load, Q rows in the combine) and never stored, which
                                     measures slower on B300.  Same words either way.  The autotuner leaves
                                     it unchanged. */
+    uint32_t keyip_pipe;         /* 1: the key inner product of a batch sharing one key walks its windows
+                                    with the next group's digit words copied into shared memory while
+                                    the current group's products run (key switches with at most 4
+                                    digits); same words.  Picked by the autotuner. */
+    float keyip_pipe_ms[4];      /* last autotune, ms: pipelined, window groups 1, 2, 4, 8 */
 } mmfhe_tuning;
 mmfhe_status mmfhe_autotune(mmfhe_ctx *ctx, uint32_t batch, uint32_t level, mmfhe_tuning *out);
 mmfhe_status mmfhe_tuning_get(const mmfhe_ctx *ctx, mmfhe_tuning *out);

@@ -596,8 +596,11 @@ class VitalCircuit:
     average, on a window of 2 streams x G groups x (Re, Im) ciphertexts.
 
     Level schedule (Table 1), L0 = top level:
-      side: K1 p (L0-1), rotate-sum over frames; K2 w = E^2 (L0-2);
-            index / one vectors (L0-3), rotate-sum over bins -> num_r, den_r.
+      side: K1 p (L0-1); each group's frame sums halved log2 G' times,
+            the first block masked (L0-2), the groups packed into one
+            ciphertext, rotate-sum over a block; K2 w = E^2 (L0-3); index /
+            one vectors (L0-4), rotate-sum over bins, then over blocks ->
+            num_r, den_r (``side_branch``).
       main: K4 p (L0-1), m = p^2 (L0-2), I, Q = sum m Re, m Im (L0-3),
             rotate-sum over bins (the sums sit in bin slot 0 of every
             frame); K5 FIR of both bands in one BSGS product per part
@@ -620,7 +623,8 @@ class VitalCircuit:
         self.n1_dft, self.n2_dft = bsgs_split(self.lay.f_pad)
         self.bands = [band_bins(cfg.frames, cfg.fs_mhz, b) for b in cfg.bands_mhz]
         L0 = P.L
-        self.lv_side_const = L0 - 2
+        self.lv_side_mask = L0 - 1
+        self.lv_side_const = L0 - 3
         self.lv_fir = L0 - 3
         self.lv_dphi = L0 - 7 if cfg.taylor_order == 3 else L0 - 5
         self.lv_final_const = self.lv_dphi - 3
@@ -697,11 +701,60 @@ class VitalCircuit:
         out = sorted({k % self.P.slots for k in ks} - {0})
         return ([ck.ROT_CONJ] if self.cfg.complex_slots else []) + out
 
+    def side_groups(self):
+        """G rounded up to a power of two: the number of frame blocks."""
+        return next_pow2(self.lay.groups)
+
+    def side_block(self):
+        """Frames per block of the packed side branch: F_pad / G'."""
+        return self.lay.f_pad // self.side_groups()
+
+    def side_block_of(self, c):
+        """Block that group c lands in: packing adds group c + 2^j, rotated
+        by 2^j blocks, onto group c at tree level j, so c moves by -c."""
+        return (-c) % self.side_groups()
+
+    def side_branch(self, ev, consts, ps):
+        """K1 -> K2 on the G groups' energies p_c (frame-major, stride r_c):
+        E_c[r] = sum_t p_c[t, r], w = E^2, num_r = sum gbin w, den_r = sum w.
+
+        Each group's frame sum is halved log2 G' times (G' = G rounded up to
+        a power of two), which leaves the sums over F_pad / G' frame blocks
+        periodic in the block; the mask keeps block 0; the groups are packed
+        into one ciphertext by a rotation tree (group c lands in block -c mod
+        G'); one rotate-and-sum over a block finishes every group's E at its
+        block start.  w = E^2 is squared once, the index / one vectors keep
+        the valid bins, and a rotate-and-sum over the bins and then over the
+        blocks leaves num_r and den_r in slot 0."""
+        lay = self.lay
+        Gp, blk = self.side_groups(), self.side_block()
+        parts = []
+        for p in ps:
+            x = ev.rotsum(p, blk * lay.r_c, Gp)      # sum over the frames t + j F_pad / G'
+            parts.append(ev.rescale(ev.mul_plain(x, consts[("pmask",)])))
+        parts += [None] * (Gp - len(parts))
+        j = 0
+        while len(parts) > 1:
+            nxt = []
+            for a in range(0, len(parts), 2):
+                x, y = parts[a], parts[a + 1]
+                if y is not None:
+                    y = ev.rotate(y, (blk << j) * lay.r_c)
+                    x = y if x is None else ev.add(x, y)
+                nxt.append(x)
+            parts, j = nxt, j + 1
+        E = ev.rotsum(parts[0], lay.r_c, blk)
+        w = ev.rescale(ev.square_sum([E]))
+        out = []
+        for name in ("idx", "one"):
+            t = ev.rescale(ev.mul_plain(w, consts[(name,)]))
+            t = ev.rotsum(t, 1, lay.r_c)
+            out.append(ev.rotsum(t, blk * lay.r_c, Gp))
+        return out
+
     def constant_keys(self):
         """Keys of every constant ``constants()`` encodes, without encoding."""
-        keys = []
-        for c in range(self.lay.groups):
-            keys += [("idx", c), ("one", c)]
+        keys = [("pmask",), ("idx",), ("one",)]
         for b in range(len(self.bands)):
             keys += [("fir", b, k) for k in range(self.cfg.taps)]
         present = set()
@@ -709,22 +762,32 @@ class VitalCircuit:
             rows, cols = np.nonzero(self.dft_time_matrix(b)["support"])
             present |= set(((cols - rows) % self.lay.f_pad).tolist())
         keys += [("dft", int(d)) for d in sorted(present)]
-        keys += [("fw",), ("fone",)]
+        keys += [(t, b) for b in range(len(self.bands)) for t in ("fw", "fone")]
         return keys
 
     def constants(self):
         P, lay, cfg = self.P, self.lay, self.cfg
         out = {}
+        # side branch: the mask of a group's first frame block, and the
+        # target-bin index / one vectors at the packed block starts
+        lv = self.lv_side_mask
+        blk = self.side_block()
+        mask = np.zeros(lay.slots)
+        for t in range(blk):
+            for r in range(lay.r_c):
+                mask[lay.slot(t, r)] = 1.0
+        out[("pmask",)] = ck.encode(P, mask, P.q[lv], lv)
         lv = self.lv_side_const
+        idx, one = np.zeros(lay.slots), np.zeros(lay.slots)
         for c in range(lay.groups):
-            idx, one = np.zeros(lay.slots), np.zeros(lay.slots)
+            t0 = self.side_block_of(c) * blk
             for r in range(lay.r_c):
                 gbin = c * lay.r_c + r
                 if gbin < cfg.bins:
-                    idx[lay.slot(0, r)] = gbin
-                    one[lay.slot(0, r)] = 1.0
-            out[("idx", c)] = ck.encode(P, idx, P.q[lv], lv)
-            out[("one", c)] = ck.encode(P, one, P.q[lv], lv)
+                    idx[lay.slot(t0, r)] = gbin
+                    one[lay.slot(t0, r)] = 1.0
+        out[("idx",)] = ck.encode(P, idx, P.q[lv], lv)
+        out[("one",)] = ck.encode(P, one, P.q[lv], lv)
         # the FIR and DFT diagonals multiply double-hoisted baby steps, which
         # live in the extended basis: encoded over Q_l * P
         lv = self.lv_fir
@@ -741,15 +804,31 @@ class VitalCircuit:
         for delta, v in diags.items():
             v = prerotate(v, delta // self.n1_dft, self.n1_dft, lay.r_c)
             out[("dft", delta)] = ck.encode_qp(P, v, P.q[lv], lv)
+        # one weight pair per band: each band's sums leave in ciphertexts of
+        # their own, so a band far above the other cannot overflow the other's
+        # sums at the last level
         lv = self.lv_final_const
         fs_hz = cfg.fs_mhz / 1000
-        fw, fo = np.zeros(lay.slots), np.zeros(lay.slots)
         for b, ks in enumerate(self.bands):
+            fw, fo = np.zeros(lay.slots), np.zeros(lay.slots)
             for k in ks:
                 fw[lay.slot(k, b)] = k * fs_hz / cfg.frames          # Hz; the client multiplies by 60
                 fo[lay.slot(k, b)] = 1.0
-        out[("fw",)] = ck.encode(P, fw, P.q[lv], lv)
-        out[("fone",)] = ck.encode(P, fo, P.q[lv], lv)
+            out[("fw", b)] = ck.encode(P, fw, P.q[lv], lv)
+            out[("fone", b)] = ck.encode(P, fo, P.q[lv], lv)
+        return out
+
+    def band_sums(self, ev, consts, S):
+        """Weighted frequency average of both bands from the sharpened powers
+        S (band b in bin slot b): num_b = sum_k (k fs / F) S_k and den_b =
+        sum_k S_k over band b's bins, each by its own mask and a
+        rotate-and-sum over band b's span; HR's sums are moved to slot 0.
+        Returns [num_RR, den_RR, num_HR, den_HR]."""
+        out = []
+        for b in range(len(self.bands)):
+            for t in ("fw", "fone"):
+                x = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[(t, b)])), self.lay.r_c, self.span(b))
+                out.append(ev.rotate(x, b) if b else x)
         return out
 
     # -- the chain -----------------------------------------------------------
@@ -762,19 +841,7 @@ class VitalCircuit:
         if cfg.complex_slots:
             return self._run_complex(ev, consts, s1, s2)
         # side branch: K1 energy, K2 soft power attention (gamma = 2)
-        w = []
-        for re, im in s1:
-            p = ev.rescale(ev.square_sum([re, im]))
-            E = ev.rotsum(p, lay.r_c, lay.f_pad)
-            w.append(ev.rescale(ev.square_sum([E])))
-        num = den = None
-        for c in range(G):
-            tn = ev.mul_plain(w[c], consts[("idx", c)])
-            td = ev.mul_plain(w[c], consts[("one", c)])
-            num = tn if num is None else ev.add(num, tn)
-            den = td if den is None else ev.add(den, td)
-        num_r = ev.rotsum(ev.rescale(num), 1, lay.r_c)
-        den_r = ev.rotsum(ev.rescale(den), 1, lay.r_c)
+        num_r, den_r = self.side_branch(ev, consts, [ev.rescale(ev.square_sum([re, im])) for re, im in s1])
 
         # K4 soft I/Q extraction (P_phi = 2)
         m = []
@@ -828,10 +895,7 @@ class VitalCircuit:
 
         # sharpen (gamma = 2), weighted frequency average (RR in slot 0, HR in slot 1)
         S = ev.rescale(ev.square_sum([Mg]))
-        num = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[("fw",)])), lay.r_c, self.span_all())
-        den = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[("fone",)])), lay.r_c, self.span_all())
-        outs = [num_r, den_r, num, den, ev.rotate(num, 1), ev.rotate(den, 1)]
-        return outs
+        return [num_r, den_r] + self.band_sums(ev, consts, S)
 
     def _run_complex(self, ev, consts, s1, s2):
         """The same chain on complex slots z = Re + i Im: |z|^2 = z conj(z);
@@ -846,18 +910,7 @@ class VitalCircuit:
         def abs2(z):
             return ev.rescale(ev.relin(ev.tensor(z, ev.conjugate(z))))
 
-        w = []
-        for z in s1:
-            E = ev.rotsum(abs2(z), lay.r_c, lay.f_pad)
-            w.append(ev.rescale(ev.square_sum([E])))
-        num = den = None
-        for c in range(G):
-            tn = ev.mul_plain(w[c], consts[("idx", c)])
-            td = ev.mul_plain(w[c], consts[("one", c)])
-            num = tn if num is None else ev.add(num, tn)
-            den = td if den is None else ev.add(den, td)
-        num_r = ev.rotsum(ev.rescale(num), 1, lay.r_c)
-        den_r = ev.rotsum(ev.rescale(den), 1, lay.r_c)
+        num_r, den_r = self.side_branch(ev, consts, [abs2(z) for z in s1])
 
         # K4: Z = sum_r m z (I + i Q), P_phi = 2
         m = [ev.rescale(ev.square_sum([abs2(z)])) for z in s2]
@@ -892,9 +945,7 @@ class VitalCircuit:
         pw = ev.rescale(ev.square_sum([X]))
         Mg = ev.add(pw, ev.rotate(pw, (lay.f_pad // 2) * lay.r_c))
         S = ev.rescale(ev.square_sum([Mg]))
-        num = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[("fw",)])), lay.r_c, self.span_all())
-        den = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[("fone",)])), lay.r_c, self.span_all())
-        return [num_r, den_r, num, den, ev.rotate(num, 1), ev.rotate(den, 1)]
+        return [num_r, den_r] + self.band_sums(ev, consts, S)
 
 
 # ---------------------------------------------------------------------------

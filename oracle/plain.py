@@ -30,63 +30,73 @@ def preprocess(z):
 
 
 # Client-side normalization of stream 2 (Sec. "Discussion", end-to-end
-# implementation: the client estimates a stable normalization factor in
-# linear time before encryption, from a calibrated Parseval-based energy
-# estimate).  Every stage of the third-order main chain is homogeneous in the
-# scale s of stream 2 (I, Q grow as s^5, y and x as s^10, dphi as s^30, the
-# band powers S as s^120), so num_b and den_b of both bands grow by s^120 and
-# the rates num_b / den_b are unchanged: s only moves the window into the
-# precision window of the scheme.  The estimate: E_b = (1/F) sum over the
-# FFT bins f of band b of |FFT(zc)_f|^2, the energy of band b of the soft I/Q
-# phasor zc[t] = sum_r |z_r[t]|^4 z_r[t] that K4 forms (Parseval); the band
-# powers scale as E_b^12 (E_b ~ A^2 for a band amplitude A, den_b ~ A^24), so
-# log10 den_b is predicted as 12 log10 E_b + c_b, and s puts the larger
-# prediction at 10^T.  c_b: ``calibrate_stream2`` over seeds 1000..1199 of
-# the synthetic workload (200 frames x 256 bins, rates drawn per seed);
-# T: the level that keeps the most of those windows with both bands in
-# [5e-3, 1e5] (below: the absolute noise of the outputs, ~5e-8, exceeds the
-# 1e-3 bpm budget; above: num nears q_0 / (2 Delta)).
-STREAM2_CAL_LOG10 = (-16.66, -22.65)
-STREAM2_TARGET_LOG10 = 2.25
+# implementation: the client fixes a normalization factor in linear time
+# before encryption, from an energy estimate of its own window).  Every stage
+# of the third-order main chain is homogeneous in the scale s of stream 2
+# (I, Q grow as s^5, y and x as s^10, dphi as s^30, the band powers S as
+# s^120), so num_b and den_b of both bands grow by s^120 and the rates
+# num_b / den_b are unchanged: s only moves a band into the scheme's
+# precision window [5e-3, 1e5] (below: the outputs' absolute noise, ~5e-8,
+# exceeds the 1e-3 bpm budget; above: num nears q_0 / (2 Delta)).
+#
+# The client computes each band's den at s = 1 in the frequency domain
+# (``stream2_band_powers``: the FIR as a zero-padded FFT product, the
+# Hann-windowed band bins from one FFT of dphi), O(F R + F log F), and picks
+# the factor that puts the two log10 den at the window's centre.  The two
+# bands' powers differ by up to ~17 decades over the synthetic workload
+# (their ratio moves with the drawn rates against the FIR band edges and the
+# Taylor arctan's range), the window spans 7.3: a window whose two bands
+# cannot share one factor with NORM_MARGIN decades to spare at either edge
+# is sent twice, each copy with one band at the centre, and the client reads
+# band b from the copy normalized for it.  In the weaker band's copy the
+# stronger band rises far above the window; the circuit keeps each band's
+# final sums in ciphertexts of their own, and the stages the bands share sit
+# at levels with headroom to spare, so only the stronger band's own outputs
+# of that copy (which the client ignores) overflow.
+NORM_WINDOW_LOG10 = (float(np.log10(5e-3)), 5.0)
+NORM_MARGIN = 0.5
 
 
-def stream2_band_energy(s2, cfg=VitalConfig()):
-    """E_b of the soft I/Q phasor of stream 2 for every band (O(F R + F log F))."""
+def stream2_band_powers(s2, cfg=VitalConfig()):
+    """den_b of both bands at s = 1, computed in the frequency domain: the
+    causal FIR with zero initial state as the first F samples of a linear
+    convolution (FFT of length >= F + taps - 1), the phase of the filtered
+    phasor from consecutive samples (Taylor order 3), and the band bins of the
+    Hann-windowed DFT from one FFT.  Equal to the chain's den up to rounding."""
     F = s2.shape[0]
     p = s2.real ** 2 + s2.imag ** 2
-    zc = (p * p * s2).sum(axis=1)
-    Z = np.fft.fft(zc)
-    f = np.fft.fftfreq(F, d=1000.0 / cfg.fs_mhz)
+    z = (p * p * s2).sum(axis=1)             # I + j Q of the soft I/Q stage
+    M = 1 << int(np.ceil(np.log2(F + cfg.taps)))
+    Z = np.fft.fft(z, M)
+    fs = cfg.fs_mhz / 1000
+    w = hann(F)
     out = []
-    for lo, hi in cfg.bands_mhz:
-        band = (np.abs(f) >= lo / 1000) & (np.abs(f) <= hi / 1000)
-        out.append(float((np.abs(Z[band]) ** 2).sum() / F))
+    for b, band in enumerate(cfg.bands_mhz):
+        h = fir_bandpass(cfg.taps, band[0] / 1000, band[1] / 1000, fs)
+        zf = np.fft.ifft(Z * np.fft.fft(h, M))[:F]        # h is real: I and Q filtered alike
+        zf1 = np.concatenate([[0.0], zf[:-1]])
+        u = zf * np.conj(zf1)                               # x + j y of consecutive samples
+        x, y = u.real, u.imag
+        dphi = y * x ** 2 - y ** 3 / 3 if cfg.taylor_order == 3 else y
+        D = np.fft.fft(w * dphi)
+        P = (cfg.gains()[b] * np.abs(D[band_bins(F, cfg.fs_mhz, band)])) ** 2
+        out.append(float((P * P).sum()))
     return out
 
 
-def stream2_scale(s2, cfg=VitalConfig(), cal=STREAM2_CAL_LOG10, target=STREAM2_TARGET_LOG10):
-    """The factor the client multiplies stream 2 by before encryption (third
-    order; the first-order chain is left unscaled)."""
+def stream2_scales(s2, cfg=VitalConfig(), window=NORM_WINDOW_LOG10, margin=NORM_MARGIN):
+    """The client's normalization of stream 2: a list of (factor, bands)
+    copies to encrypt -- one copy [(s, (0, 1))] when both bands fit one
+    factor, else [(s_0, (0,)), (s_1, (1,))].  The first-order chain is left
+    unscaled."""
     if cfg.taylor_order != 3:
-        return 1.0
-    E = stream2_band_energy(s2, cfg)
-    pred = max(12 * np.log10(max(e, 1e-300)) + c for e, c in zip(E, cal))
-    return float(10.0 ** ((target - pred) / 120.0))
-
-
-def calibrate_stream2(seeds, cfg=VitalConfig()):
-    """c_b = mean over seeded synthetic windows of log10 den_b - 12 log10 E_b
-    (FP64 pipeline of this module, unnormalized stream 2)."""
-    from synth import vital_window
-    acc = [[], []]
-    for seed in seeds:
-        win = vital_window(seed, frames=cfg.frames, bins=cfg.bins, randomize_rates=True)
-        _, s2 = preprocess(win.z)
-        E = stream2_band_energy(s2, cfg)
-        mc = main_chain(s2, cfg)
-        for b in range(2):
-            acc[b].append(np.log10(mc["bands"][b]["den"]) - 12 * np.log10(E[b]))
-    return tuple(float(np.mean(a)) for a in acc)
+        return [(1.0, (0, 1))]
+    lo, hi = window
+    c = 0.5 * (lo + hi)
+    ld = [np.log10(max(d, 1e-300)) for d in stream2_band_powers(s2, cfg)]
+    if abs(ld[0] - ld[1]) <= (hi - lo) - 2 * margin:
+        return [(float(10.0 ** ((c - 0.5 * (ld[0] + ld[1])) / 120.0)), (0, 1))]
+    return [(float(10.0 ** ((c - ld[b]) / 120.0)), (b,)) for b in range(2)]
 
 
 def side_branch(s1):

@@ -23,7 +23,7 @@ ERRORS = {
 CIRCUIT_FIR_DFT, CIRCUIT_VITAL, CIRCUIT_FC, CIRCUIT_VITAL_PER_FRAME, CIRCUIT_GESTURE = 1, 2, 3, 4, 5
 CONST_TAGS = {1: "idx", 2: "one", 3: "fir", 4: "dre", 5: "dim", 6: "fw", 7: "fone", 8: "dft_c", 9: "dft_s",
               10: "dft_ms", 11: "fcw", 12: "gdft_c", 13: "gdft_s", 14: "gdft_ms", 15: "notch", 16: "fcb",
-              17: "gdft_w", 18: "notch_b", 19: "feat_a"}
+              17: "gdft_w", 18: "notch_b", 19: "feat_a", 20: "pmask"}
 ROT_CONJ = -(1 << 31)   # key id of the slot-wise complex conjugation
 
 
@@ -65,7 +65,8 @@ class KernelStat(ctypes.Structure):
 class Tuning(ctypes.Structure):
     _fields_ = [("ntt_cols_width", ctypes.c_uint32), ("ntt_rows_threads", ctypes.c_uint32),
                 ("keyip_windows", ctypes.c_uint32), ("conv_rows", ctypes.c_uint32), ("ntt_ms", ctypes.c_float * 4),
-                ("keyip_ms", ctypes.c_float * 4), ("conv_ms", ctypes.c_float * 3), ("keyip_fused", ctypes.c_uint32)]
+                ("keyip_ms", ctypes.c_float * 4), ("conv_ms", ctypes.c_float * 3), ("keyip_fused", ctypes.c_uint32),
+                ("keyip_pipe", ctypes.c_uint32), ("keyip_pipe_ms", ctypes.c_float * 4)]
 
 
 class BatcherConfig(ctypes.Structure):

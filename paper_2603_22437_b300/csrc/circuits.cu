@@ -420,7 +420,7 @@ Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
             p->out_levels.push_back(L - 2);
         }
     } else {
-        const int lv_side = L - 2, lv_fir = L - 3;
+        const int lv_side = L - 3, lv_fir = L - 3;
         const int lv_dphi = cfg.taylor_order == 3 ? L - 7 : L - 5;
         const int lv_final = lv_dphi - 3;
         if (lv_final < 1) throw Error(MMFHE_ERR_BAD_ARG, "not enough levels for the vital chain");
@@ -428,10 +428,10 @@ Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
         p->lv_fir = lv_fir;
         p->lv_dphi = lv_dphi;
         p->lv_final = lv_final;
-        for (int g = 0; g < p->groups; g++) {
-            add(MMFHE_CONST_IDX, 0, g, lv_side);
-            add(MMFHE_CONST_ONE, 0, g, lv_side);
-        }
+        // side branch: the first-block mask at L - 1, index / one vectors at the packed block starts
+        add(MMFHE_CONST_PMASK, 0, 0, L - 1);
+        add(MMFHE_CONST_IDX, 0, 0, lv_side);
+        add(MMFHE_CONST_ONE, 0, 0, lv_side);
         for (int b = 0; b < 2; b++)
             for (uint32_t k = 0; k < cfg.taps; k++) add(MMFHE_CONST_FIR, b, k, lv_fir);
         // from the FIR on, band b lives in bin slot b of every frame
@@ -449,8 +449,10 @@ Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
         }
         p->dft_deltas[0].assign(present.begin(), present.end());
         for (int d : p->dft_deltas[0]) add(MMFHE_CONST_DRE, 0, d, lv_dphi);
-        add(MMFHE_CONST_FW, 0, 0, lv_final);
-        add(MMFHE_CONST_FONE, 0, 0, lv_final);
+        for (uint32_t b = 0; b < 2; b++) {   // one weight pair per band
+            add(MMFHE_CONST_FW, b, 0, lv_final);
+            add(MMFHE_CONST_FONE, b, 0, lv_final);
+        }
         for (int i = 0; (1 << i) < Fp; i++) rot(p->r_c << i);
         for (int i = 0; (1 << i) < p->r_c; i++) rot(1 << i);
         for (int b = 0; b < p->n1_fir; b++) {
@@ -527,11 +529,22 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
             for (int r = 0; r < (int)cfg.bins; r++) v[r] = k.tag == MMFHE_CONST_IDX ? (double)r : 1.0;
             return v;
         }
-        for (int r = 0; r < Rc; r++) {
-            int gb = (int)k.index * Rc + r;
-            if (gb < (int)cfg.bins) v[slot(0, r)] = k.tag == MMFHE_CONST_IDX ? (double)gb : 1.0;
+        {   // group g's bins at the start of its packed block (-g mod G')
+            const int Gp = next_pow2(p.groups), blk = Fp / Gp;
+            for (int g = 0; g < p.groups; g++)
+                for (int r = 0; r < Rc; r++) {
+                    const int gb = g * Rc + r;
+                    if (gb < (int)cfg.bins)
+                        v[slot(((Gp - g) % Gp) * blk, r)] = k.tag == MMFHE_CONST_IDX ? (double)gb : 1.0;
+                }
         }
         return v;
+    case MMFHE_CONST_PMASK: {   // the first F_pad / G' frames of every bin slot
+        const int blk = Fp / next_pow2(p.groups);
+        for (int t = 0; t < blk; t++)
+            for (int r = 0; r < Rc; r++) v[slot(t, r)] = 1.0;
+        return v;
+    }
     case MMFHE_CONST_FIR: {
         int b = (int)k.band, kk = (int)k.index;
         std::vector<double> h = fir_bandpass((int)cfg.taps, cfg.band_lo_mhz[b] / 1000.0, cfg.band_hi_mhz[b] / 1000.0, fs);
@@ -616,9 +629,8 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
     }
     case MMFHE_CONST_FW:
     case MMFHE_CONST_FONE:
-        // both bands: frequency k fs / F (or 1) at (k, band)
-        for (int b = 0; b < 2; b++)
-            for (int kk : p.bands[b]) v[slot(kk, b)] = k.tag == MMFHE_CONST_FW ? kk * fs / F : 1.0;
+        // band k.band only: frequency k fs / F (or 1) at (k, band)
+        for (int kk : p.bands[k.band]) v[slot(kk, (int)k.band)] = k.tag == MMFHE_CONST_FW ? kk * fs / F : 1.0;
         return v;
     }
     throw Error(MMFHE_ERR_BAD_ARG, "unknown constant tag");
@@ -716,9 +728,76 @@ static std::vector<BsgsSet> dft_sets(const Plan &p, const CtB &dphi) {
     return sets;
 }
 
+// K1 -> K2 on the G groups' energies ps (frame-major, stride r_c): each
+// group's frame sums over t + j F_pad / G' (G' = G rounded up to a power of
+// two) by a rotate-and-sum, the first frame block kept by a mask, the groups
+// packed into one ciphertext by a rotation tree (group g lands in block
+// -g mod G'), one rotate-and-sum over a block, w = E^2 once, and
+// rotate-and-sums over the bins and then over the blocks.  Returns
+// {num_r, den_r} (slot 0).
+static std::pair<CtB, CtB> side_branch(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &ps,
+                                       cudaStream_t st) {
+    const int Rc = p.r_c, Gp = next_pow2(p.groups), blk = p.f_pad / Gp;
+    const PtDev &mask = plan_const(p, MMFHE_CONST_PMASK, 0, 0);
+    std::vector<CtB> parts;
+    for (CtB &x : ps) {
+        CtB s = rotsum(c, k, x, blk * Rc, (uint32_t)Gp, st);
+        x = CtB();
+        CtB t = ct_new(c, s.B, s.level, s.scale * mask.scale);
+        ct_mul_plain(c, t, s, mask, false, st);
+        parts.push_back(rescale(c, t, st));
+    }
+    parts.resize(Gp);   // missing groups: empty (level -1)
+    for (int j = 0; parts.size() > 1; j++) {
+        std::vector<CtB> nxt;
+        for (size_t a = 0; a < parts.size(); a += 2) {
+            CtB &x = parts[a], &y = parts[a + 1];
+            if (y.level < 0) {
+                nxt.push_back(std::move(x));
+            } else if (x.level < 0) {
+                nxt.push_back(rotate(c, k, y, (blk << j) * Rc, st));
+            } else {
+                nxt.push_back(rotate_add(c, k, y, (blk << j) * Rc, x, st));
+            }
+        }
+        parts = std::move(nxt);
+    }
+    CtB E = rotsum(c, k, parts[0], Rc, (uint32_t)blk, st);
+    parts.clear();
+    CtB w = rescale(c, square_sum(c, k, {&E}, st), st);
+    CtB sums[2];
+    for (int i = 0; i < 2; i++) {
+        const PtDev &pt = plan_const(p, i == 0 ? MMFHE_CONST_IDX : MMFHE_CONST_ONE, 0, 0);
+        CtB t = ct_new(c, w.B, w.level, w.scale * pt.scale);
+        ct_mul_plain(c, t, w, pt, false, st);
+        CtB r = rotsum(c, k, rescale(c, t, st), 1, (uint32_t)Rc, st);
+        sums[i] = rotsum(c, k, r, blk * Rc, (uint32_t)Gp, st);
+    }
+    return {std::move(sums[0]), std::move(sums[1])};
+}
+
+// Weighted frequency average of both bands from the sharpened powers S (band
+// b in bin slot b): per band, its own weight mask and a rotate-and-sum over
+// its own span, so each band's sums leave in ciphertexts of their own and a
+// band far stronger than the other cannot overflow the other's sums at the
+// last level; HR's sums move to slot 0.  Returns num_RR, den_RR, num_HR, den_HR.
+static std::vector<CtB> band_sums(Context &c, const Plan &p, const Keys &k, const CtB &S, cudaStream_t st) {
+    const int B = S.B;
+    std::vector<CtB> out;
+    for (int b = 0; b < 2; b++)
+        for (uint32_t tag : {(uint32_t)MMFHE_CONST_FW, (uint32_t)MMFHE_CONST_FONE}) {
+            const PtDev &pt = plan_const(p, tag, (uint32_t)b, 0);
+            CtB t = ct_new(c, B, S.level, S.scale * pt.scale);
+            ct_mul_plain(c, t, S, pt, false, st);
+            CtB x = rotsum(c, k, rescale(c, t, st), p.r_c, (uint32_t)p.span[b], st);
+            out.push_back(b ? rotate(c, k, x, 1, st) : std::move(x));
+        }
+    return out;
+}
+
 static std::vector<CtB> run_vital_complex(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in,
                                           cudaStream_t st) {
-    const int G = p.groups, Rc = p.r_c, Fp = p.f_pad;
+    const int G = p.groups, Rc = p.r_c;
     const int B = in[0].B;
     auto abs2 = [&](const CtB &z) {
         CtB zc = rotate(c, k, z, MMFHE_ROT_CONJ, st);
@@ -727,21 +806,9 @@ static std::vector<CtB> run_vital_complex(Context &c, const Plan &p, const Keys 
         return rescale(c, relin(c, k, t, st), st);
     };
     // ---- side branch: K1, K2 ----
-    std::vector<CtB> w;
-    for (int g = 0; g < G; g++) {
-        CtB E = rotsum(c, k, abs2(in[g]), Rc, (uint32_t)Fp, st);
-        w.push_back(rescale(c, square_sum(c, k, {&E}, st), st));
-    }
-    const PtDev &idx0 = plan_const(p, MMFHE_CONST_IDX, 0, 0);
-    CtB num = ct_new(c, B, w[0].level, w[0].scale * idx0.scale);
-    CtB den = ct_new(c, B, w[0].level, w[0].scale * idx0.scale);
-    for (int g = 0; g < G; g++) {
-        ct_mul_plain(c, num, w[g], plan_const(p, MMFHE_CONST_IDX, 0, g), g > 0, st);
-        ct_mul_plain(c, den, w[g], plan_const(p, MMFHE_CONST_ONE, 0, g), g > 0, st);
-    }
-    w.clear();
-    CtB num_r = rotsum(c, k, rescale(c, num, st), 1, (uint32_t)Rc, st);
-    CtB den_r = rotsum(c, k, rescale(c, den, st), 1, (uint32_t)Rc, st);
+    std::vector<CtB> ps;
+    for (int g = 0; g < G; g++) ps.push_back(abs2(in[g]));
+    auto [num_r, den_r] = side_branch(c, p, k, ps, st);
     // ---- K4: Z = sum_r m z ----
     std::vector<CtB> m;
     for (int g = 0; g < G; g++) {
@@ -784,47 +851,21 @@ static std::vector<CtB> run_vital_complex(Context &c, const Plan &p, const Keys 
     CtB pw = rescale(c, square_sum(c, k, {&X}, st), st);
     CtB merged = rotate_add(c, k, pw, (p.f_pad / 2) * Rc, pw, st);
     CtB S = rescale(c, square_sum(c, k, {&merged}, st), st);
-    const uint32_t span = (uint32_t)std::max(p.span[0], p.span[1]);
-    CtB sums[2];
-    for (int i2 = 0; i2 < 2; i2++) {
-        const PtDev &pt = plan_const(p, i2 == 0 ? MMFHE_CONST_FW : MMFHE_CONST_FONE, 0, 0);
-        CtB tt = ct_new(c, B, S.level, S.scale * pt.scale);
-        ct_mul_plain(c, tt, S, pt, false, st);
-        sums[i2] = rotsum(c, k, rescale(c, tt, st), Rc, span, st);
-    }
     std::vector<CtB> out;
     out.push_back(std::move(num_r));
     out.push_back(std::move(den_r));
-    CtB hr_num = rotate(c, k, sums[0], 1, st);
-    CtB hr_den = rotate(c, k, sums[1], 1, st);
-    out.push_back(std::move(sums[0]));
-    out.push_back(std::move(sums[1]));
-    out.push_back(std::move(hr_num));
-    out.push_back(std::move(hr_den));
+    for (CtB &x : band_sums(c, p, k, S, st)) out.push_back(std::move(x));
     return out;
 }
 
 static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &in, cudaStream_t st) {
     if (p.cfg.complex_slots) return run_vital_complex(c, p, k, in, st);
-    const int G = p.groups, Rc = p.r_c, Fp = p.f_pad;
+    const int G = p.groups, Rc = p.r_c;
     const int B = in[0].B;
     // ---- side branch: K1, K2 ----
-    std::vector<CtB> w;
-    for (int g = 0; g < G; g++) {
-        CtB pp = rescale(c, square_sum(c, k, {&in[2 * g], &in[2 * g + 1]}, st), st);
-        CtB E = rotsum(c, k, pp, Rc, (uint32_t)Fp, st);
-        w.push_back(rescale(c, square_sum(c, k, {&E}, st), st));
-    }
-    const PtDev &idx0 = plan_const(p, MMFHE_CONST_IDX, 0, 0);
-    CtB num = ct_new(c, B, w[0].level, w[0].scale * idx0.scale);
-    CtB den = ct_new(c, B, w[0].level, w[0].scale * idx0.scale);
-    for (int g = 0; g < G; g++) {
-        ct_mul_plain(c, num, w[g], plan_const(p, MMFHE_CONST_IDX, 0, g), g > 0, st);
-        ct_mul_plain(c, den, w[g], plan_const(p, MMFHE_CONST_ONE, 0, g), g > 0, st);
-    }
-    w.clear();
-    CtB num_r = rotsum(c, k, rescale(c, num, st), 1, (uint32_t)Rc, st);
-    CtB den_r = rotsum(c, k, rescale(c, den, st), 1, (uint32_t)Rc, st);
+    std::vector<CtB> ps;
+    for (int g = 0; g < G; g++) ps.push_back(rescale(c, square_sum(c, k, {&in[2 * g], &in[2 * g + 1]}, st), st));
+    auto [num_r, den_r] = side_branch(c, p, k, ps, st);
     // ---- K4 soft I/Q ----
     std::vector<CtB> m;
     for (int g = 0; g < G; g++) {
@@ -881,23 +922,10 @@ static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std:
     CtB merged = rotate_add(c, k, pw, (p.f_pad / 2) * Rc, pw, st);
     // ---- sharpen, weighted frequency average (RR in slot 0, HR in slot 1) ----
     CtB S = rescale(c, square_sum(c, k, {&merged}, st), st);
-    const uint32_t span = (uint32_t)std::max(p.span[0], p.span[1]);
-    CtB sums[2];
-    for (int i2 = 0; i2 < 2; i2++) {
-        const PtDev &pt = plan_const(p, i2 == 0 ? MMFHE_CONST_FW : MMFHE_CONST_FONE, 0, 0);
-        CtB t = ct_new(c, B, S.level, S.scale * pt.scale);
-        ct_mul_plain(c, t, S, pt, false, st);
-        sums[i2] = rotsum(c, k, rescale(c, t, st), Rc, span, st);
-    }
     std::vector<CtB> out;
     out.push_back(std::move(num_r));
     out.push_back(std::move(den_r));
-    CtB hr_num = rotate(c, k, sums[0], 1, st);
-    CtB hr_den = rotate(c, k, sums[1], 1, st);
-    out.push_back(std::move(sums[0]));
-    out.push_back(std::move(sums[1]));
-    out.push_back(std::move(hr_num));
-    out.push_back(std::move(hr_den));
+    for (CtB &x : band_sums(c, p, k, S, st)) out.push_back(std::move(x));
     return out;
 }
 

@@ -152,8 +152,10 @@ struct Tune {
     int keyip_wg = 4;    // windows per thread of the key inner product (1, 2, 4 or 8)
     int conv_rows = 1;   // converted rows per CTA of the fused ModUp / ModDown strided passes (1, 2 or 4)
     int keyip_fused = 0; // key inner product stored by its own kernel (0) or formed inside the ModDown passes (1)
+    int keyip_pipe = 0;  // shared-key inner product with the window walk pipelined through shared memory (1)
     float ntt_ms[4] = {};     // last autotune: NTT pair per (cols_w, rows_t) in {8,16} x {128,256}
     float keyip_ms[4] = {};   // last autotune: key inner product per window group 1, 2, 4, 8
+    float keyip_pipe_ms[4] = {};   // the same, pipelined
     float conv_ms[3] = {};    // last autotune: fused ModUp + ModDown per rows per CTA 1, 2, 4
 };
 

@@ -27,6 +27,16 @@ inline dim3 grid_for(size_t work) {
     return dim3((unsigned)std::min<size_t>(b, 148 * 64));
 }
 
+// 128-bit multiply-accumulate, the small-operand form for primes below
+// SMALL_PRIME_LIMIT (S is uniform over a row, so over a warp).
+template <bool S>
+__device__ __forceinline__ void macq(uint64_t &hi, uint64_t &lo, uint64_t a, uint64_t b) {
+    if (S) mm::mac128_small(hi, lo, a, b);
+    else mm::mac128(hi, lo, a, b);
+}
+using SmallT = std::true_type;
+using WideT = std::false_type;
+
 __device__ __forceinline__ uint64_t mulq(uint64_t a, uint64_t b, const ModTab &mt, int pid) {
     return mm::mul_barrett(a, b, mt.q[pid], mt.mu[pid], mt.k[pid]);
 }
@@ -123,22 +133,27 @@ __global__ void __launch_bounds__(MULTI_X)
     uint64_t v[T], vn[T];
 #pragma unroll
     for (int t = 0; t < T; t++) v[t] = t < nt ? __ldg(a.ct[t] + off) : 0;
-    for (int b = 0; b < B; b++) {
-        const size_t wo = (size_t)b * wstride + off;
-        // the next window's baby words load under this window's arithmetic
+    auto walk = [&](auto small) {
+        constexpr bool S = decltype(small)::value;
+        for (int b = 0; b < B; b++) {
+            const size_t wo = (size_t)b * wstride + off;
+            // the next window's baby words load under this window's arithmetic
 #pragma unroll
-        for (int t = 0; t < T; t++) vn[t] = (t < nt && b + 1 < B) ? __ldg(a.ct[t] + wo + wstride) : 0;
-        for (int g = 0; g < ng; g++) {
-            uint64_t hi = 0, lo = 0;
+            for (int t = 0; t < T; t++) vn[t] = (t < nt && b + 1 < B) ? __ldg(a.ct[t] + wo + wstride) : 0;
+            for (int g = 0; g < ng; g++) {
+                uint64_t hi = 0, lo = 0;
 #pragma unroll
-            for (int t = 0; t < T; t++) mm::mac128(hi, lo, v[t], sp[(g * T + t) * MULTI_X + threadIdx.x]);
-            const uint64_t r = mm::redc(hi, lo, q, qinv);
-            uint64_t *o = a.out[g] + wo;
-            *o = accumulate ? mm::add_mod(*o, r, q) : r;
+                for (int t = 0; t < T; t++) macq<S>(hi, lo, v[t], sp[(g * T + t) * MULTI_X + threadIdx.x]);
+                const uint64_t r = mm::redc(hi, lo, q, qinv);
+                uint64_t *o = a.out[g] + wo;
+                *o = accumulate ? mm::add_mod(*o, r, q) : r;
+            }
+#pragma unroll
+            for (int t = 0; t < T; t++) v[t] = vn[t];
         }
-#pragma unroll
-        for (int t = 0; t < T; t++) v[t] = vn[t];
-    }
+    };
+    if (q < mm::SMALL_PRIME_LIMIT) walk(SmallT{});
+    else walk(WideT{});
 }
 
 // ---------------------------------------------------------------------------
@@ -361,31 +376,36 @@ __global__ void __launch_bounds__(EW_THREADS, WG <= 2 ? 4 : (WG == 4 ? 3 : 2))
                 kb[j] = j < beta ? key.k[0][(((size_t)j * 2 + 0) * key_rows + krow) * n + x] : 0;
                 ka[j] = j < beta ? key.k[0][(((size_t)j * 2 + 1) * key_rows + krow) * n + x] : 0;
             }
-            for (int b0 = 0; b0 < B; b0 += WG) {
-                uint64_t h0[WG] = {}, l0[WG] = {}, h1[WG] = {}, l1[WG] = {};
+            auto walk = [&](auto small) {
+                constexpr bool S = decltype(small)::value;
+                for (int b0 = 0; b0 < B; b0 += WG) {
+                    uint64_t h0[WG] = {}, l0[WG] = {}, h1[WG] = {}, l1[WG] = {};
 #pragma unroll
-                for (int j = 0; j < KB; j++) {
-                    if (j >= beta) break;
-                    const uint64_t *src = j == jown ? own + j * own_jstride + (size_t)t * n + px
-                                                    : digits + ((size_t)j * nrows_ext + t) * n + px;
-                    const size_t wstride = j == jown ? own_stride : (size_t)beta * nrows_ext * n;
-                    uint64_t dv[WG];
+                    for (int j = 0; j < KB; j++) {
+                        if (j >= beta) break;
+                        const uint64_t *src = j == jown ? own + j * own_jstride + (size_t)t * n + px
+                                                        : digits + ((size_t)j * nrows_ext + t) * n + px;
+                        const size_t wstride = j == jown ? own_stride : (size_t)beta * nrows_ext * n;
+                        uint64_t dv[WG];
 #pragma unroll
-                    for (int k = 0; k < WG; k++) dv[k] = b0 + k < B ? src[(size_t)(b0 + k) * wstride] : 0;
+                        for (int k = 0; k < WG; k++) dv[k] = b0 + k < B ? src[(size_t)(b0 + k) * wstride] : 0;
+#pragma unroll
+                        for (int k = 0; k < WG; k++) {
+                            macq<S>(h0[k], l0[k], dv[k], kb[j]);
+                            macq<S>(h1[k], l1[k], dv[k], ka[j]);
+                        }
+                    }
 #pragma unroll
                     for (int k = 0; k < WG; k++) {
-                        mm::mac128(h0[k], l0[k], dv[k], kb[j]);
-                        mm::mac128(h1[k], l1[k], dv[k], ka[j]);
+                        if (b0 + k >= B) break;
+                        uint64_t *U = u + ((size_t)(b0 + k) * 2 * nrows_ext) * n;
+                        U[(size_t)t * n + x] = mm::redc(h0[k], l0[k], q, qinv);
+                        U[((size_t)nrows_ext + t) * n + x] = mm::redc(h1[k], l1[k], q, qinv);
                     }
                 }
-#pragma unroll
-                for (int k = 0; k < WG; k++) {
-                    if (b0 + k >= B) break;
-                    uint64_t *U = u + ((size_t)(b0 + k) * 2 * nrows_ext) * n;
-                    U[(size_t)t * n + x] = mm::redc(h0[k], l0[k], q, qinv);
-                    U[((size_t)nrows_ext + t) * n + x] = mm::redc(h1[k], l1[k], q, qinv);
-                }
-            }
+            };
+            if (q < mm::SMALL_PRIME_LIMIT) walk(SmallT{});
+            else walk(WideT{});
         }
         return;
     }
@@ -443,6 +463,95 @@ __global__ void __launch_bounds__(EW_THREADS, WG <= 2 ? 4 : (WG == 4 ? 3 : 2))
             U[(size_t)t * n + x] = mm::redc(h0[k], l0[k], q, qinv);
             U[((size_t)nrows_ext + t) * n + x] = mm::redc(h1[k], l1[k], q, qinv);
         }
+    }
+}
+
+// Asynchronous 8-byte copy global -> shared (completion tracked per thread).
+__device__ __forceinline__ void cpa8(uint64_t *smem_dst, const uint64_t *gsrc) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cpa_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cpa_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int KEYIP_PIPE_THREADS = 128;
+
+// The shared-key inner product of k_keyip with its window walk pipelined:
+// a thread copies the digit words of its next group of WG windows into its
+// own column of shared memory (asynchronous copies; it reads back only what
+// it copied, so no barrier) while the current group's products run, so the
+// loads of one group hide under the arithmetic of the previous one.  Same
+// words as k_keyip.  beta <= KB.
+template <int WG, int KB>
+__global__ void __launch_bounds__(KEYIP_PIPE_THREADS, WG <= 4 ? 4 : 3)
+    k_keyip_pipe(uint64_t *u, const uint64_t *digits, const uint64_t *own, size_t own_stride, size_t own_jstride,
+                 KeyPtrs key, int B, int level, int beta, int alpha, int nrows_ext, int key_rows, int L1, int logn,
+                 uint32_t galois, ModTab mt, int pid_p0) {
+    extern __shared__ uint64_t kbuf[];   // [2][KB][WG][KEYIP_PIPE_THREADS]
+    const int tid = threadIdx.x;
+    auto at = [&](int s, int j, int k) -> uint64_t & {
+        return kbuf[((s * KB + j) * WG + k) * KEYIP_PIPE_THREADS + tid];
+    };
+    const uint32_t n = 1u << logn;
+    const size_t per_group = (size_t)nrows_ext * n;
+    for (size_t w = blockIdx.x * (size_t)blockDim.x + tid; w < per_group; w += (size_t)gridDim.x * blockDim.x) {
+        const uint32_t x = (uint32_t)(w & (n - 1));
+        const int t = (int)(w >> logn);
+        const int pid = t <= level ? t : pid_p0 + (t - level - 1);
+        const int krow = t <= level ? t : L1 + (t - level - 1);
+        const uint32_t px = galois == 1 ? x : mm::galois_perm(x, galois, logn);
+        const uint64_t q = mt.q[pid], qinv = mt.qinv[pid];
+        const int jown = t <= level ? t / alpha : -1;
+        uint64_t kb[KB], ka[KB];
+        const uint64_t *src[KB];
+        size_t ws[KB];
+#pragma unroll
+        for (int j = 0; j < KB; j++) {
+            kb[j] = j < beta ? key.k[0][(((size_t)j * 2 + 0) * key_rows + krow) * n + x] : 0;
+            ka[j] = j < beta ? key.k[0][(((size_t)j * 2 + 1) * key_rows + krow) * n + x] : 0;
+            src[j] = j == jown ? own + j * own_jstride + (size_t)t * n + px : digits + ((size_t)j * nrows_ext + t) * n + px;
+            ws[j] = j == jown ? own_stride : (size_t)beta * nrows_ext * n;
+        }
+        auto issue = [&](int b0, int s) {
+#pragma unroll
+            for (int j = 0; j < KB; j++)
+#pragma unroll
+                for (int k = 0; k < WG; k++)
+                    if (j < beta && b0 + k < B) cpa8(&at(s, j, k), src[j] + (size_t)(b0 + k) * ws[j]);
+            cpa_commit();
+        };
+        auto walk = [&](auto small) {
+            constexpr bool S = decltype(small)::value;
+            issue(0, 0);
+            int s = 0;
+            for (int b0 = 0; b0 < B; b0 += WG, s ^= 1) {
+                if (b0 + WG < B) issue(b0 + WG, s ^ 1);
+                else cpa_commit();   // an empty group keeps one group in flight behind this one
+                cpa_wait<1>();       // this group's words have landed
+                uint64_t h0[WG] = {}, l0[WG] = {}, h1[WG] = {}, l1[WG] = {};
+#pragma unroll
+                for (int j = 0; j < KB; j++) {
+                    if (j >= beta) break;
+#pragma unroll
+                    for (int k = 0; k < WG; k++) {
+                        const uint64_t dv = at(s, j, k);
+                        macq<S>(h0[k], l0[k], dv, kb[j]);
+                        macq<S>(h1[k], l1[k], dv, ka[j]);
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < WG; k++) {
+                    if (b0 + k >= B) break;
+                    uint64_t *U = u + ((size_t)(b0 + k) * 2 * nrows_ext) * n;
+                    U[(size_t)t * n + x] = mm::redc(h0[k], l0[k], q, qinv);
+                    U[((size_t)nrows_ext + t) * n + x] = mm::redc(h1[k], l1[k], q, qinv);
+                }
+            }
+            cpa_wait<0>();
+        };
+        if (q < mm::SMALL_PRIME_LIMIT) walk(SmallT{});
+        else walk(WideT{});
     }
 }
 
@@ -698,6 +807,25 @@ void k_launch_keyip(Context &c, uint64_t *u, const uint64_t *digits, const uint6
     auto go = [&](auto wg_c, auto pw_c) {
         constexpr int WG = decltype(wg_c)::value;
         constexpr bool PW = decltype(pw_c)::value;
+        if (!PW && c.tune.keyip_pipe && beta <= 4) {
+            const size_t smem = (size_t)2 * 4 * WG * KEYIP_PIPE_THREADS * 8;
+            static bool opted = false;
+            if (!opted) {
+                if (smem > 48 * 1024)
+                    CK(cudaFuncSetAttribute(k_keyip_pipe<WG, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)smem));
+                opted = true;
+            }
+            dim3 gp((unsigned)std::min<size_t>((work + KEYIP_PIPE_THREADS - 1) / KEYIP_PIPE_THREADS, 148 * 64));
+            kernel_begin(c, st);
+            k_keyip_pipe<WG, 4><<<gp, KEYIP_PIPE_THREADS, smem, st>>>(u, digits, own, own_stride, own_jstride, key,
+                                                                     B, level, beta, c.alpha, nre,
+                                                                     c.num_q + c.num_p, c.num_q, c.logn, galois,
+                                                                     c.mods, c.num_q);
+            kernel_end(c, "keyip", gp, dim3(KEYIP_PIPE_THREADS), bytes, st);
+            CK(cudaGetLastError());
+            return;
+        }
         kernel_begin(c, st);
         auto kern = beta <= 4 ? k_keyip<WG, PW, 4> : k_keyip<WG, PW, MAX_DNUM>;
         kern<<<g, EW_THREADS, 0, st>>>(u, digits, own, own_stride, own_jstride, key, B, level, beta, c.alpha,

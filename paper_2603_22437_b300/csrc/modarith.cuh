@@ -89,6 +89,29 @@ MM_HD void mac128(uint64_t &hi, uint64_t &lo, uint64_t a, uint64_t b) {
     hi += ph + (lo < pl ? 1 : 0);
 }
 
+// (hi:lo) += a*b for a, b < 2^48 (residues, lazy or not, of primes below
+// 2^47): with a = a1 2^32 + a0 and b = b1 2^32 + b0, a*b = a0 b0 +
+// (a0 b1 + a1 b0) 2^32 + a1 b1 2^64, where the middle sum stays below 2^49
+// and a1 b1 below 2^32, so three 32 x 32 -> 64 products and one 32-bit
+// product replace the two 64 x 64 halves of the general case.
+MM_HD void mac128_small(uint64_t &hi, uint64_t &lo, uint64_t a, uint64_t b) {
+#if defined(__CUDA_ARCH__)
+    const uint32_t a0 = (uint32_t)a, a1 = (uint32_t)(a >> 32), b0 = (uint32_t)b, b1 = (uint32_t)(b >> 32);
+    const uint64_t p0 = (uint64_t)a0 * b0;
+    const uint64_t m = (uint64_t)a0 * b1 + (uint64_t)a1 * b0;
+    const uint64_t top = a1 * b1;
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(p0), "l"(top));
+    asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(m << 32), "l"(m >> 32));
+#else
+    const unsigned __int128 t = (((unsigned __int128)hi << 64) | lo) + (unsigned __int128)a * b;
+    hi = (uint64_t)(t >> 64);
+    lo = (uint64_t)t;
+#endif
+}
+
+// Primes whose residues take mac128_small.
+constexpr uint64_t SMALL_PRIME_LIMIT = 1ull << 47;
+
 // Reduce x in [0, 4q) to [0, q).
 MM_HD uint64_t reduce_4q(uint64_t x, uint64_t q) {
     uint64_t q2 = q << 1;

@@ -109,13 +109,6 @@ struct Geo {
     static constexpr int R2R = LOGT - R1R;
     static constexpr int TPC = H / 16;              // threads per column
     static constexpr int COLS = CW;
-    // Strided tile in shared memory: element (h, c) at h * COLS + c, plus
-    // CPAD words after every 16 rows.  With 8 columns a warp's four column
-    // groups touch rows 16 apart in the second round; the pad puts their
-    // 64-byte segments on alternating halves of the banks.
-    static constexpr int CPAD = CW == 8 ? 8 : 0;
-    static constexpr int TILE = H * CW + (H / 16) * CPAD;
-    __host__ __device__ static constexpr int at(int h, int c) { return h * CW + c + (h >> 4) * CPAD; }
     static constexpr int COLS_THREADS = CW * TPC;
     static constexpr int TPR = T1 / 16;             // threads per block
     static constexpr int ROWS = (RT / TPR) < H ? (RT / TPR) : H;   // blocks per CTA
@@ -136,11 +129,6 @@ __device__ __forceinline__ void cp_async8(uint64_t *smem_dst, const uint64_t *gs
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
-// Closes the group of this thread's copies issued since the last commit.
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-// Waits until at most N of this thread's committed groups are still in flight.
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Bulk prefetch of bytes (multiple of 16, 16-byte aligned start) into L2.
 __device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
@@ -164,7 +152,7 @@ __device__ __forceinline__ void cols_rounds(uint64_t *sm, uint64_t q, uint32_t p
     const int c = threadIdx.x % Gm::COLS, t = threadIdx.x / Gm::COLS;
     const uint64_t *W = (FWD ? tw.fw : tw.iw) + ((size_t)pid << LOGN);
     const uint64_t *Wp = (FWD ? tw.fw_sh : tw.iw_sh) + ((size_t)pid << LOGN);
-    auto addr = [c](int h) { return Gm::at(h, c); };
+    auto addr = [c](int h) { return h * Gm::COLS + c; };
     auto twi = [](int s, int h) { return (1 << s) + (h >> (Gm::S1 - s)); };
     if (FWD) {
         ntt_round<Gm::S1, 0, Gm::R1C, true>(sm, t, q, W, Wp, addr, twi);
@@ -218,7 +206,7 @@ __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::CO
     k_ntt_cols(const uint64_t *__restrict__ src, RowMap ms, uint64_t *dst, RowMap md, ModTab mt, Twiddles tw,
                const uint64_t *__restrict__ oscale, const uint64_t *__restrict__ oscale_sh) {
     using Gm = Geo<LOGN, CW>;
-    __shared__ uint64_t sm[Gm::TILE];
+    __shared__ uint64_t sm[Gm::H * Gm::COLS];
     uint32_t blk, p;
     row_decode(md, blockIdx.y, blk, p);
     const uint32_t pid = md.pid[p];
@@ -226,20 +214,17 @@ __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::CO
     uint64_t *D = dst + row_at(md, blk, p, LOGN);
     const int lo0 = blockIdx.x * Gm::COLS;
     const uint64_t q = mt.q[pid];
-    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS)
-        cp_async8(&sm[Gm::at(e / Gm::COLS, e % Gm::COLS)], &S[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)]);
+    MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) cp_async8(&sm[e], &S[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)]);
     cp_async_wait_all();
     __syncthreads();
     cols_rounds<LOGN, FWD, CW>(sm, q, pid, tw);
     __syncthreads();
     if (FWD) {
-        MMFHE_TILE_LOOP(e, Gm::COLS_THREADS)
-            D[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)] = sm[Gm::at(e / Gm::COLS, e % Gm::COLS)];
+        MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) D[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)] = sm[e];
     } else {
         const uint64_t ni = oscale ? oscale[pid] : tw.ninv[pid], nip = oscale ? oscale_sh[pid] : tw.ninv_sh[pid];
         MMFHE_TILE_LOOP(e, Gm::COLS_THREADS)
-            D[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)] =
-                mm::mul_shoup(sm[Gm::at(e / Gm::COLS, e % Gm::COLS)], ni, nip, q);
+            D[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)] = mm::mul_shoup(sm[e], ni, nip, q);
     }
 }
 
@@ -291,10 +276,9 @@ template <int LOGN, int CW, int RG, int NT, bool CENTERED>
 __device__ __forceinline__ void conv_load(uint64_t *tiles, int nr, const uint64_t *__restrict__ X, int lo0,
                                           const ConvConsts<RG> &cc) {
     using Gm = Geo<LOGN, CW>;
-    constexpr int TILE = Gm::TILE;
+    constexpr int TILE = Gm::H * Gm::COLS;
     MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) {
         const size_t idx = (size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS);
-        const int se = Gm::at(e / Gm::COLS, e % Gm::COLS);
         uint64_t x[NT], neg = 0;
 #pragma unroll
         for (int k = 0; k < NT; k++) {
@@ -308,7 +292,7 @@ __device__ __forceinline__ void conv_load(uint64_t *tiles, int nr, const uint64_
 #pragma unroll
             for (int k = 0; k < NT; k++) mm::mac128(hi, lo, x[k], cc.f[r][k]);
             if (CENTERED) mm::mac128(hi, lo, neg, cc.negp[r]);
-            tiles[r * TILE + se] = mm::redc(hi, lo, cc.q[r], cc.qinv[r]);
+            tiles[r * TILE + e] = mm::redc(hi, lo, cc.q[r], cc.qinv[r]);
         }
     }
 }
@@ -318,10 +302,9 @@ template <int LOGN, int CW, int RG, bool CENTERED>
 __device__ __forceinline__ void conv_load_any(uint64_t *tiles, int nr, const uint64_t *__restrict__ X, int nt,
                                               int lo0, const ConvConsts<RG> &cc) {
     using Gm = Geo<LOGN, CW>;
-    constexpr int TILE = Gm::TILE;
+    constexpr int TILE = Gm::H * Gm::COLS;
     MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) {
         const size_t idx = (size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS);
-        const int se = Gm::at(e / Gm::COLS, e % Gm::COLS);
         uint64_t neg = 0;
         if (CENTERED)
             for (int k = 0; k < nt; k++) neg += X[((size_t)k << LOGN) + idx] > cc.half[k] ? 1u : 0u;
@@ -329,7 +312,7 @@ __device__ __forceinline__ void conv_load_any(uint64_t *tiles, int nr, const uin
             uint64_t hi = 0, lo = 0;
             for (int k = 0; k < nt; k++) mm::mac128(hi, lo, X[((size_t)k << LOGN) + idx], cc.f[r][k]);
             if (CENTERED) mm::mac128(hi, lo, neg, cc.negp[r]);
-            tiles[r * TILE + se] = mm::redc(hi, lo, cc.q[r], cc.qinv[r]);
+            tiles[r * TILE + e] = mm::redc(hi, lo, cc.q[r], cc.qinv[r]);
         }
     }
 }
@@ -352,7 +335,7 @@ __device__ __forceinline__ void cols_finish_group(uint64_t *tiles, int nr, const
                                                   const RowMap &md, const RowGroups &gr, uint32_t g, uint32_t blk,
                                                   int lo0, const Twiddles &tw) {
     using Gm = Geo<LOGN, CW>;
-    constexpr int TILE = Gm::TILE;
+    constexpr int TILE = Gm::H * Gm::COLS;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RG; r++) {
@@ -363,8 +346,7 @@ __device__ __forceinline__ void cols_finish_group(uint64_t *tiles, int nr, const
     for (int r = 0; r < nr; r++) {
         uint64_t *D = dst + row_at(md, blk, md.act[gr.start[g] + r], LOGN);
         const uint64_t *T = tiles + r * TILE;
-        MMFHE_TILE_LOOP(e, Gm::COLS_THREADS)
-            D[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)] = T[Gm::at(e / Gm::COLS, e % Gm::COLS)];
+        MMFHE_TILE_LOOP(e, Gm::COLS_THREADS) D[(size_t)(e / Gm::COLS) * Gm::T1 + lo0 + (e % Gm::COLS)] = T[e];
     }
 }
 
@@ -493,13 +475,7 @@ __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16,
                        const uint64_t *__restrict__ Pinv, const uint64_t *__restrict__ Pinv_sh, ModTab mt,
                        Twiddles tw, KeyipArgs ka) {
     using Gm = Geo<LOGN, 16, RT>;
-    // The u tile (the epilogue's operand, contiguous like the output) is
-    // staged into shared memory by a second group of asynchronous copies
-    // issued with the v tile's, so it arrives while the stages run -- when
-    // both tiles fit the static shared-memory budget.
-    constexpr int SU = (KB == 0 && Gm::ROWS * (Gm::RS + Gm::T1) * 8 <= 40960) ? Gm::ROWS * Gm::T1 : 1;
     __shared__ uint64_t sm[Gm::ROWS * Gm::RS];
-    __shared__ uint64_t su[SU];
     uint32_t blk, p;
     row_decode(mv, blockIdx.y, blk, p);
     const uint32_t pid = mv.pid[p];
@@ -513,9 +489,9 @@ __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16,
     if (A) A += (size_t)(blk >> 1) * a.add_stride + ((size_t)p << LOGN);
     const uint64_t *Pl = a.plus ? a.plus + (((size_t)blk * nl + p) << LOGN) : nullptr;
     if (threadIdx.x == 0) {
-        // the epilogue's other contiguous operands travel to L2 while the stages run
+        // the epilogue's contiguous operands travel to L2 while the stages run
         constexpr uint32_t seg = Gm::ROWS * Gm::T1 * 8;
-        if (!KB && SU == 1) l2_prefetch(U + base, seg);
+        if (!KB) l2_prefetch(U + base, seg);
         if (Pl) l2_prefetch(Pl + base, seg);
         if (A && a.galois == 1) l2_prefetch(A + base, seg);
     }
@@ -523,27 +499,17 @@ __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16,
         int rr = e / Gm::T1, l = e % Gm::T1;
         cp_async8(&sm[rr * Gm::RS + l + (l >> 4)], &S[base + e]);
     }
-    if (SU > 1) {
-        cp_async_commit();
-        // each thread copies the u words its own epilogue iterations read (no barrier needed)
-        MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) cp_async8(&su[e], &U[base + e]);
-        cp_async_commit();
-        cp_async_wait<1>();   // the v tile
-    } else {
-        cp_async_wait_all();
-    }
+    cp_async_wait_all();
     __syncthreads();
     rows_rounds<LOGN, true, RT>(sm, hi0, q, pid, tw);
     __syncthreads();
-    if (SU > 1) cp_async_wait<0>();   // this thread's u words
     const uint64_t pi = Pinv[pid], pis = Pinv_sh[pid], qinv = mt.qinv[pid];
     uint64_t *O = a.out + (((size_t)blk * nl + p) << LOGN);
     MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
         int r2 = e / Gm::T1, l = e % Gm::T1;
         const uint32_t x = (uint32_t)(base + e);
         const uint64_t vv = mm::reduce_4q(sm[r2 * Gm::RS + l + (l >> 4)], q);
-        const uint64_t uu = KB ? keyip_word<KB ? KB : 1>(ka, blk >> 1, (int)(blk & 1), (int)p, x, LOGN, q, qinv)
-                               : (SU > 1 ? su[e] : U[x]);
+        const uint64_t uu = KB ? keyip_word<KB ? KB : 1>(ka, blk >> 1, (int)(blk & 1), (int)p, x, LOGN, q, qinv) : U[x];
         uint64_t res = mm::mul_shoup(mm::sub_mod(uu, vv, q), pi, pis, q);
         if (A) res = mm::add_mod(res, A[a.galois == 1 ? x : mm::galois_perm(x, a.galois, LOGN)], q);
         if (Pl) res = mm::add_mod(res, Pl[x], q);
@@ -606,7 +572,7 @@ void modup_cols_pass(Context &c, uint64_t *digits, const uint64_t *y, const RowM
                      size_t nblk, int nl, int nre, int j0, const uint64_t *m_mont, double bytes, size_t nr,
                      double macs, cudaStream_t st) {
     using Gm = Geo<LOGN, CW>;
-    const size_t smem = (size_t)RG * Gm::TILE * 8;
+    const size_t smem = (size_t)RG * Gm::H * Gm::COLS * 8;
     static bool opted = false;
     if (!opted) {
         smem_opt_in(k_ntt_cols_modup<LOGN, CW, RG>, smem);
@@ -642,7 +608,7 @@ template <int LOGN, int CW, int RG>
 void moddown_cols_pass(Context &c, uint64_t *vtmp, const uint64_t *z, const RowMap &mv, const RowGroups &gr,
                        size_t nblk, double bytes, size_t nr, double macs, cudaStream_t st) {
     using Gm = Geo<LOGN, CW>;
-    const size_t smem = (size_t)RG * Gm::TILE * 8;
+    const size_t smem = (size_t)RG * Gm::H * Gm::COLS * 8;
     static bool opted = false;
     if (!opted) {
         smem_opt_in(k_ntt_cols_moddown<LOGN, CW, RG>, smem);

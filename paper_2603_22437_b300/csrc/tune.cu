@@ -84,17 +84,21 @@ void autotune(Context &c, int batch, int level) {
         kp.n = 1;
         const int wgs[4] = {1, 2, 4, 8};
         float bk = 1e30f;
-        for (int i = 0; i < 4; i++) {
-            c.tune.keyip_wg = wgs[i];
-            const float ms = time_best(st, [&] {
-                k_launch_keyip(c, u.get(), dg.get(), own.get(), (size_t)nl * c.n, 0, kp, batch, level, beta, g, st);
-            });
-            best.keyip_ms[i] = ms;
-            if (ms < bk) {
-                bk = ms;
-                best.keyip_wg = wgs[i];
+        for (int pipe = 0; pipe < 2; pipe++)
+            for (int i = 0; i < 4; i++) {
+                c.tune.keyip_wg = wgs[i];
+                c.tune.keyip_pipe = pipe;
+                const float ms = time_best(st, [&] {
+                    k_launch_keyip(c, u.get(), dg.get(), own.get(), (size_t)nl * c.n, 0, kp, batch, level, beta, g,
+                                   st);
+                });
+                (pipe ? best.keyip_pipe_ms : best.keyip_ms)[i] = ms;
+                if (ms < bk) {
+                    bk = ms;
+                    best.keyip_wg = wgs[i];
+                    best.keyip_pipe = pipe;
+                }
             }
-        }
         dg.release();
         own.release();
         key.release();
@@ -155,6 +159,8 @@ void to_abi(const Tune &t, mmfhe_tuning *out) {
     out->conv_rows = (uint32_t)t.conv_rows;
     std::copy(t.conv_ms, t.conv_ms + 3, out->conv_ms);
     out->keyip_fused = (uint32_t)t.keyip_fused;
+    out->keyip_pipe = (uint32_t)t.keyip_pipe;
+    std::copy(t.keyip_pipe_ms, t.keyip_pipe_ms + 4, out->keyip_pipe_ms);
 }
 
 }  // namespace
@@ -188,9 +194,10 @@ mmfhe_status mmfhe_tuning_set(mmfhe_ctx *ctx, const mmfhe_tuning *in) {
     Context *c = ctx->c;
     const uint32_t w = in->ntt_cols_width, r = in->ntt_rows_threads, k = in->keyip_windows, g = in->conv_rows;
     if ((w != 8 && w != 16) || (r != 128 && r != 256) || (k != 1 && k != 2 && k != 4 && k != 8) ||
-        (g != 1 && g != 2 && g != 4) || in->keyip_fused > 1)
+        (g != 1 && g != 2 && g != 4) || in->keyip_fused > 1 || in->keyip_pipe > 1)
         return tfail(c, MMFHE_ERR_BAD_ARG, "unsupported tile shape");
     c->tune.keyip_fused = (int)in->keyip_fused;
+    c->tune.keyip_pipe = (int)in->keyip_pipe;
     c->tune.conv_rows = (int)g;
     c->tune.cols_w = (int)w;
     c->tune.rows_t = (int)r;

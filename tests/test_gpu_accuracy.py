@@ -2,20 +2,20 @@
 fidelity against the plaintext pipeline, Table 3: below 1e-3 bpm).
 
 64 seeded full-size windows (200 frames x 256 bins, rates drawn per seed;
-seeds 4000..4063, none of them used to calibrate the client's normalizer)
-are preprocessed by the client (clutter removal, stream 1 by the window
+seeds 4000..4063, none of them used by the normalizer's CPU pins) are
+preprocessed by the client (clutter removal, stream 1 by the window
 maximum, stream 2 frame by frame and by the client's normalization factor),
-encrypted, evaluated on the GPU in one batch of 64 (the bench's batch),
-decrypted, and compared with the FP64 pipeline on the same inputs.
+encrypted, evaluated on the GPU in one batch, decrypted, and compared with
+the FP64 pipeline on the same inputs.
 
-A window is inside the scheme's precision window when both bands' powers
-(den, FP64) lie in [5e-3, 1e5]: below, the outputs' absolute noise (~5e-8)
-exceeds the 1e-3 bpm budget; above, num nears q_0 / (2 Delta).  Every
-window inside must be within 1e-3 bpm in both bands; the count of windows
-outside is reported (MMFHE_ACCURACY_OUT names a JSON file for the summary).
-The two fixed public gains cannot hold every synthetic window: the chain
-raises the band amplitude to the 24th power, and one factor per window
-cannot level both bands."""
+The client's factor puts both bands' powers (den) at the centre of the
+scheme's precision window [5e-3, 1e5] (below, the outputs' absolute noise,
+~5e-8, exceeds the 1e-3 bpm budget; above, num nears q_0 / (2 Delta)); a
+window whose two bands cannot share one factor is encrypted twice, each
+copy normalized for one band, and band b is read from its copy.  Checked:
+every band of every window is inside the window in its copy and within
+1e-3 bpm of the FP64 pipeline (MMFHE_ACCURACY_OUT names a JSON file for the
+summary)."""
 import json
 import multiprocessing as mp
 import os
@@ -49,8 +49,8 @@ def _keys(rot_chunk):
 
 
 def _window(args):
-    """Worker: one window preprocessed, normalized and encrypted, with its
-    FP64 pipeline results."""
+    """Worker: one window preprocessed, normalized and encrypted (one or two
+    copies), with the FP64 pipeline results of each copy."""
     seed, pk_words = args
     import synth
     from oracle import ckks as ck
@@ -63,13 +63,15 @@ def _window(args):
     lay = cc.Layout(P.slots, 256, 200)
     win = synth.vital_window(seed, frames=200, bins=256, randomize_rates=True)
     s1, s2 = plain.preprocess(win.z)
-    s = plain.stream2_scale(s2, cfg)
-    s2 = s2 * s
     pk = ck.PublicKey(*pk_words)
-    cts = encrypt_window(P, pk, lay, [s1, s2], 10 * seed)
-    sb, mc = plain.side_branch(s1), plain.main_chain(s2, cfg)
-    return {"seed": seed, "scale": s, "in": window_words(cts), "r": sb["num"] / sb["den"],
-            "bpm": [b["bpm"] for b in mc["bands"]], "den": [b["den"] for b in mc["bands"]]}
+    sb = plain.side_branch(s1)
+    copies = []
+    for k, (s, bands) in enumerate(plain.stream2_scales(s2, cfg)):
+        cts = encrypt_window(P, pk, lay, [s1, s2 * s], 10 * seed + k)
+        mc = plain.main_chain(s2 * s, cfg)
+        copies.append({"scale": s, "bands": bands, "in": window_words(cts),
+                       "bpm": [b["bpm"] for b in mc["bands"]], "den": [b["den"] for b in mc["bands"]]})
+    return {"seed": seed, "r": sb["num"] / sb["den"], "copies": copies}
 
 
 def test_decrypted_rates_over_64_windows():
@@ -100,32 +102,45 @@ def test_decrypted_rates_over_64_windows():
     install_oracle_consts(plan, circ.constants())
     _, _, lv = plan.io()
     out_words = sum(2 * (l + 1) * P.n for l in lv)
-    outs = [np.empty(out_words, dtype=np.uint64) for _ in wins]
-    ctx.eval(plan, keys, [w["in"] for w in wins], outs, vital=True)
+    inputs = [c["in"] for w in wins for c in w["copies"]]
+    outs = [np.empty(out_words, dtype=np.uint64) for _ in inputs]
+    ctx.eval(plan, keys, inputs, outs, vital=True)
     sk = ck.SecretKey(P, base["secret"])
     # output scales follow the oracle's scale arithmetic (a counting run)
     scales = [o.scale for o in circ.run(cc.CountingEvaluator(P), circ.constants(), *_shapes(circ, P))]
-    rows = []
-    for w, o in zip(wins, outs):
+
+    def decrypt(o):
         dv, off = [], 0
         for l, sc in zip(lv, scales):
             n = 2 * (l + 1) * P.n
             c = o[off : off + n].reshape(2, l + 1, P.n)
             dv.append(ck.decrypt_decode(P, sk, ck.Ciphertext(c[0], c[1], l, sc))[0])
             off += n
-        err = [abs(60 * dv[2 + 2 * b] / dv[3 + 2 * b] - w["bpm"][b]) for b in range(2)]
-        inside = all(LO <= d <= HI for d in w["den"])
-        rows.append({"seed": w["seed"], "scale": w["scale"], "den": w["den"], "bpm": w["bpm"], "err_bpm": err,
-                     "err_r": abs(dv[0] / dv[1] - w["r"]), "inside": inside})
-    ins = [r for r in rows if r["inside"]]
+        return dv
+
+    rows, k = [], 0
+    for w in wins:
+        err, den, bpm, scl, err_r = [None, None], [None, None], [None, None], [None, None], 0.0
+        for c in w["copies"]:
+            dv = decrypt(outs[k])
+            k += 1
+            err_r = max(err_r, abs(dv[0] / dv[1] - w["r"]))
+            for b in c["bands"]:
+                err[b] = abs(60 * dv[2 + 2 * b] / dv[3 + 2 * b] - c["bpm"][b])
+                den[b], bpm[b], scl[b] = c["den"][b], c["bpm"][b], c["scale"]
+        rows.append({"seed": w["seed"], "copies": len(w["copies"]), "scale": scl, "den": den, "bpm": bpm,
+                     "err_bpm": err, "err_r": err_r, "inside": all(LO <= d <= HI for d in den)})
     summary = {
         "windows": len(rows),
-        "inside_precision_window": len(ins),
+        "copies": len(inputs),
+        "split_windows": sum(1 for r in rows if r["copies"] == 2),
+        "inside_precision_window": sum(1 for r in rows if r["inside"]),
+        "within_1e-3_bpm_both_bands": sum(1 for r in rows if max(r["err_bpm"]) < 1e-3),
         "below_floor": sum(1 for r in rows if min(r["den"]) < LO),
         "above_ceiling": sum(1 for r in rows if max(r["den"]) > HI),
-        "mae_bpm_inside": {"RR": float(np.mean([r["err_bpm"][0] for r in ins])),
-                           "HR": float(np.mean([r["err_bpm"][1] for r in ins]))},
-        "max_bpm_inside": float(max(max(r["err_bpm"]) for r in ins)),
+        "mae_bpm": {"RR": float(np.mean([r["err_bpm"][0] for r in rows])),
+                    "HR": float(np.mean([r["err_bpm"][1] for r in rows]))},
+        "max_bpm": float(max(max(r["err_bpm"]) for r in rows)),
         "max_err_target_bin": float(max(r["err_r"] for r in rows)),
         "rows": rows,
     }
@@ -133,8 +148,8 @@ def test_decrypted_rates_over_64_windows():
     if path:
         with open(path, "w") as f:
             json.dump(summary, f, indent=1, default=float)
-    assert len(ins) >= 0.7 * len(rows)
-    for r in ins:
+    assert summary["below_floor"] == 0 and summary["above_ceiling"] == 0
+    for r in rows:
         assert max(r["err_bpm"]) < 1e-3, r
     assert summary["max_err_target_bin"] < 1e-6
 

@@ -200,10 +200,10 @@ def oracle_const_words(plan, consts):
     (coefficient-form words, one array per constant)."""
     out = []
     for tag, band, index, level in plan.const_keys():
-        if tag in ("idx", "one"):
-            key = (tag, index)
-        elif tag in ("fw", "fone"):
+        if tag in ("idx", "one", "pmask"):
             key = (tag,)
+        elif tag in ("fw", "fone"):
+            key = (tag, band)
         elif tag == "dre":
             key = ("dft", index)
         elif tag == "fir" and ("fir", band, index) in consts:

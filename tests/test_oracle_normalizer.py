@@ -4,10 +4,11 @@ normalization factor before encryption, Sec. "Discussion").
 * Homogeneity: multiplying stream 2 by s multiplies num and den of both
   bands by exactly s^120 in the FP64 pipeline, so the rates are unchanged
   (the factor only moves a window into the scheme's precision window).
-* The stored calibration constants are what ``calibrate_stream2`` computes
-  on the seeds they were fitted on.
-* On those seeds, the factor puts both bands inside [5e-3, 1e5] for at least
-  four windows in five, against fewer than three in five unnormalized.
+* The frequency-domain band powers the client computes equal the FP64
+  pipeline's den (a direct-form FIR and direct DFT sums) to rounding.
+* On 200 seeds every band lands inside [5e-3, 1e5] in the copy normalized
+  for it; fewer than three windows in five are inside unnormalized, and
+  fewer than one in six needs two copies.
 """
 import numpy as np
 import pytest
@@ -18,6 +19,7 @@ from oracle import plain
 
 CFG = cc.VitalConfig(bins=256, taylor_order=3)
 LO, HI = 5e-3, 1e5
+LO_L, HI_L = plain.NORM_WINDOW_LOG10
 
 
 @pytest.mark.parametrize("seed", [1000, 1017, 1101])
@@ -32,18 +34,32 @@ def test_scaling_stream2_scales_band_powers_by_s_to_the_120(seed):
         assert abs(bb["bpm"] - ba["bpm"]) < 1e-9 * ba["bpm"]
 
 
-def test_calibration_constants_recompute():
-    c = plain.calibrate_stream2(range(1000, 1200), CFG)
-    assert np.allclose(c, plain.STREAM2_CAL_LOG10, atol=0.005)
+@pytest.mark.parametrize("seed", [1000, 1017, 1018, 1070, 1101, 1102, 1165, 1199])
+def test_band_powers_equal_the_fp64_chain(seed):
+    win = synth.vital_window(seed, frames=200, bins=256, randomize_rates=True)
+    _, s2 = plain.preprocess(win.z)
+    got = plain.stream2_band_powers(s2, CFG)
+    want = [b["den"] for b in plain.main_chain(s2, CFG)["bands"]]
+    for g, w in zip(got, want):
+        assert abs(g / w - 1) < 1e-9, (g, w)
 
 
-def test_normalization_brings_most_windows_into_the_precision_window():
-    inside = [0, 0]
+def test_every_band_lands_inside_its_copy():
+    inside_raw, split = 0, 0
     for seed in range(1000, 1200):
         win = synth.vital_window(seed, frames=200, bins=256, randomize_rates=True)
         _, s2 = plain.preprocess(win.z)
-        for k, x in enumerate((s2, s2 * plain.stream2_scale(s2, CFG))):
-            d = [bd["den"] for bd in plain.main_chain(x, CFG)["bands"]]
-            inside[k] += all(LO <= v <= HI for v in d)
-    assert inside[0] < 0.6 * 200
-    assert inside[1] >= 0.8 * 200
+        d = [bd["den"] for bd in plain.main_chain(s2, CFG)["bands"]]
+        inside_raw += all(LO <= v <= HI for v in d)
+        copies = plain.stream2_scales(s2, CFG)
+        assert len(copies) in (1, 2)
+        assert sorted(b for _, bands in copies for b in bands) == [0, 1]
+        split += len(copies) == 2
+        if len(copies) == 2:      # only when one factor cannot hold both bands with the margin
+            assert abs(np.log10(d[0] / d[1])) > (HI_L - LO_L) - 2 * plain.NORM_MARGIN
+        for s, bands in copies:
+            ds = [bd["den"] for bd in plain.main_chain(s2 * s, CFG)["bands"]]
+            for b in bands:
+                assert LO <= ds[b] <= HI, (seed, b, ds[b])
+    assert inside_raw < 0.6 * 200
+    assert split < 200 / 6

@@ -253,4 +253,8 @@ def test_table1_golden_depths():
     st = gold["stages_cumulative"]
     assert P.L - c3.lv_fir == st["phase_extraction"]
     assert P.L - c3.lv_dphi == st["taylor_arctan_third_order"]
-    assert P.L - c3.lv_side_const == st["soft_attention"]
+    # the side branch packs its G groups into one ciphertext behind a block
+    # mask (one of the levels it has to spare, the main chain sets the depth):
+    # K1 at depth 1, the mask at 2, K2's w = E^2 at the paper's depth + 1
+    assert P.L - c3.lv_side_mask == 1
+    assert P.L - c3.lv_side_const == st["soft_attention"] + 1
