@@ -629,6 +629,11 @@ class VitalCircuit:
         self.lv_dphi = L0 - 7 if cfg.taylor_order == 3 else L0 - 5
         self.lv_final_const = self.lv_dphi - 3
         assert self.lv_final_const >= 1, "not enough levels for the chain"
+        self.record = None   # a dict: run() records each kernel's output ciphertexts in it
+
+    def _record(self, name, value):
+        if self.record is not None:
+            self.record[name] = value
 
     # -- public constants ----------------------------------------------------
     def taps(self, b):
@@ -728,6 +733,7 @@ class VitalCircuit:
         blocks leaves num_r and den_r in slot 0."""
         lay = self.lay
         Gp, blk = self.side_groups(), self.side_block()
+        self._record("K1_energy", ps)
         parts = []
         for p in ps:
             x = ev.rotsum(p, blk * lay.r_c, Gp)      # sum over the frames t + j F_pad / G'
@@ -745,6 +751,8 @@ class VitalCircuit:
             parts, j = nxt, j + 1
         E = ev.rotsum(parts[0], lay.r_c, blk)
         w = ev.rescale(ev.square_sum([E]))
+        self._record("K1_integration", E)
+        self._record("K2_soft_attention", w)
         out = []
         for name in ("idx", "one"):
             t = ev.rescale(ev.mul_plain(w, consts[(name,)]))
@@ -858,6 +866,7 @@ class VitalCircuit:
                 t = tc if t is None else ev.tensor_add(t, tc)
             iq.append(ev.rotsum(ev.rescale(ev.relin(t)), 1, lay.r_c))
         I, Q = iq
+        self._record("K4_phase_extraction", (I, Q))
 
         # K5 FIR of both bands in one double-hoisted BSGS product per part:
         # the baby steps of I (and Q) share one ModUp, unshifted for RR
@@ -872,6 +881,7 @@ class VitalCircuit:
             sets = {"s0": (x, 0), "s1": (x, -1)}
             filtered.append(ev.rescale(ev.bsgs_dh(sets, fir, n1, -lay.r_c)))
         If, Qf = filtered
+        self._record("K5_fir", (If, Qf))
         # K7 differential phase, both bands slot by slot
         If1 = ev.rotate(If, -lay.r_c)
         Qf1 = ev.rotate(Qf, -lay.r_c)
@@ -884,6 +894,7 @@ class VitalCircuit:
             dphi = ev.rescale(ev.relin(ev.tensor(yd, u)))
         else:
             dphi = y
+        self._record("K7_taylor_arctan", dphi)
 
         # K3 narrowband DFT (both bands, each in its bin slot), |X|^2
         n1 = self.n1_dft
@@ -892,9 +903,12 @@ class VitalCircuit:
         pw = ev.rescale(ev.square_sum([X]))
         # Re^2 at k, Im^2 at k + F_pad/2: one rotation adds them
         Mg = ev.add(pw, ev.rotate(pw, (lay.f_pad // 2) * lay.r_c))
+        self._record("K3_dft", X)
+        self._record("power", Mg)
 
         # sharpen (gamma = 2), weighted frequency average (RR in slot 0, HR in slot 1)
         S = ev.rescale(ev.square_sum([Mg]))
+        self._record("sharpen", S)
         return [num_r, den_r] + self.band_sums(ev, consts, S)
 
     def _run_complex(self, ev, consts, s1, s2):

@@ -186,38 +186,3 @@ def test_circuit_trace_is_data_oblivious(small_setup):
         ev.hoisted(y, [16, 32])
         traces.append(ev.trace)
     assert traces[0] == traces[1] and len(traces[0]) > 5
-
-
-@pytest.mark.slow
-def test_vital_chain_decrypts_to_fp64():
-    """Full vital chain at N = 2^15 (64 bins, one group) against the FP64
-    plaintext pipeline of the same formulas; decrypted rate error < 1e-3 bpm
-    (Table 3 acceptance bound)."""
-    P = pm.vital_params()
-    cfg = cc.VitalConfig(bins=64)
-    circ = cc.VitalCircuit(P, cfg)
-    rots = circ.rotations()
-    kd = synth.KeyDraws(3, P.n, P.q, P.p, P.dnum, rots)
-    sk = ck.SecretKey(P, kd.secret)
-    pk = ck.gen_public_key(P, sk, kd.pk_a, kd.pk_e)
-    rlk = ck.gen_relin_key(P, sk, kd.rlk_a, kd.rlk_e)
-    gks = {k: ck.gen_galois_key(P, sk, k, *kd.gk[k]) for k in rots}
-    del kd
-    win = synth.vital_window(1003, frames=200, bins=64, randomize_rates=True)
-    s1, s2 = plain.preprocess(win.z)
-    lay = circ.lay
-
-    def stream(x, seed):
-        re, im = lay.pack(x.real), lay.pack(x.imag)
-        return [(ck.encrypt(P, pk, ck.encode(P, re[c], P.scale, P.L), *synth.encryption_draws(seed + 2 * c, P.n)),
-                 ck.encrypt(P, pk, ck.encode(P, im[c], P.scale, P.L), *synth.encryption_draws(seed + 2 * c + 1, P.n)))
-                for c in range(lay.groups)]
-
-    outs = circ.run(cc.Evaluator(P, rlk, gks), circ.constants(), stream(s1, 100), stream(s2, 200))
-    dv = [ck.decrypt_decode(P, sk, o)[0] for o in outs]
-    sb, mc = plain.side_branch(s1), plain.main_chain(s2, cfg)
-    assert abs(dv[0] / dv[1] - sb["num"] / sb["den"]) < 1e-6
-    for b in range(2):
-        bd = mc["bands"][b]
-        if bd["den"] > 1e-4:          # above the precision floor of Delta = 2^40
-            assert abs(60 * dv[2 + 2 * b] / dv[3 + 2 * b] - bd["bpm"]) < 1e-3
