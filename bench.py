@@ -78,8 +78,8 @@ def parse():
     ap.add_argument("--complex-slots", action="store_true",
                     help="vital and gesture workloads: Re + i Im in one complex slot (half the input ciphertexts)")
     ap.add_argument("--tiles", default=None,
-                    help="cols_width,rows_threads,keyip_windows,conv_rows[,keyip_pipe]: set the tile shapes instead "
-                         "of autotuning")
+                    help="cols_width,rows_threads,keyip_windows,conv_rows[,keyip_pipe[,conv_prefetch]]: set the "
+                         "tile shapes instead of autotuning")
     ap.add_argument("--keyip-fusion", action="store_true",
                     help="form the key inner product inside the ModDown passes instead of storing it with its "
                          "own kernel (ablation; same words, slower on B300)")
@@ -462,11 +462,12 @@ def pick_tiles(ctx, args, batch):
     fused = 1 if args.keyip_fusion else 0
     if args.tiles:
         v = [int(x) for x in args.tiles.split(",")]
-        ctx.set_tuning(*v[:4], keyip_fused=fused, keyip_pipe=v[4] if len(v) > 4 else 0)
+        ctx.set_tuning(*v[:4], keyip_fused=fused, keyip_pipe=v[4] if len(v) > 4 else 0,
+                       conv_prefetch=v[5] if len(v) > 5 else 0)
         return ctx.tuning()
     t = ctx.tuning() if args.no_autotune else ctx.autotune(batch)
     ctx.set_tuning(t["ntt_cols_width"], t["ntt_rows_threads"], t["keyip_windows"], t["conv_rows"], fused,
-                   t["keyip_pipe"])
+                   t["keyip_pipe"], t["conv_prefetch"])
     return ctx.tuning()
 
 

@@ -188,20 +188,20 @@ def test_every_tile_variant_gives_the_same_words(gsmall):
     ctx.eval(plan, keys, xs, ref)
     for cw in (8, 16):
         for rt in (128, 256):
-            for wg, rg, fu, pi in ((1, 4, 0, 1), (2, 2, 1, 0), (8, 1, 0, 1), (4, 4, 1, 0), (2, 1, 0, 1),
-                                   (4, 2, 0, 1)):
-                ctx.set_tuning(cw, rt, wg, rg, fu, pi)
+            for wg, rg, fu, pi, pf in ((1, 4, 0, 1, 1), (2, 2, 1, 0, 0), (8, 1, 0, 1, 1), (2, 1, 0, 1, 0),
+                                       (4, 2, 0, 1, 1), (4, 4, 1, 0, 1)):
+                ctx.set_tuning(cw, rt, wg, rg, fu, pi, pf)
                 outs = [np.empty_like(r) for r in ref]
                 ctx.eval(plan, keys, xs, outs)
                 for w in range(3):
-                    assert np.array_equal(outs[w], ref[w]), (cw, rt, wg, rg, fu, pi, w)
+                    assert np.array_equal(outs[w], ref[w]), (cw, rt, wg, rg, fu, pi, pf, w)
     with pytest.raises(M.MmfheError):
         ctx.set_tuning(32, 256, 4)
     t = ctx.autotune(3)
     assert t["ntt_cols_width"] in (8, 16) and t["ntt_rows_threads"] in (128, 256)
     assert t["keyip_windows"] in (1, 2, 4, 8)
     assert min(t["ntt_ms"]) > 0 and min(t["keyip_ms"]) > 0 and min(t["keyip_pipe_ms"]) > 0
-    assert t["keyip_pipe"] in (0, 1)
+    assert t["keyip_pipe"] in (0, 1) and t["conv_prefetch"] in (0, 1) and min(t["conv_prefetch_ms"]) > 0
     assert t["conv_rows"] in (1, 2, 4) and min(t["conv_ms"]) > 0
     assert t["keyip_fused"] == 1   # the last variant's setting: the autotuner leaves it unchanged
     ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"], saved["conv_rows"],
