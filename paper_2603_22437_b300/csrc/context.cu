@@ -348,6 +348,7 @@ Context *create_context(const mmfhe_params &p, int device) {
     Context *c = new Context();
     try {
         c->device = device;
+        CK(cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device));
         c->params = p;
         c->logn = (int)p.log_n;
         c->n = 1u << p.log_n;

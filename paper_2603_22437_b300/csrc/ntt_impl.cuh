@@ -129,6 +129,11 @@ __device__ __forceinline__ void cp_async8(uint64_t *smem_dst, const uint64_t *gs
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
 }
+// Closes the group of this thread's copies issued since the last commit.
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+// Waits until at most N of this thread's committed groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
 // Bulk prefetch of bytes (multiple of 16, 16-byte aligned start) into L2.
 __device__ __forceinline__ void l2_prefetch(const void *p, uint32_t bytes) {
@@ -532,6 +537,81 @@ __global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16,
     }
 }
 
+// The combine of k_ntt_rows_combine (u read from a.u) with its tiles
+// pipelined: a CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... (tile
+// = row * (H / ROWS) + block of ROWS) and copies the v tile of the next one
+// into its second shared buffer (asynchronous copies) while the current
+// tile's stages and epilogue run; the next tile's contiguous epilogue
+// operands go to L2 at the same time.  Same words.
+template <int LOGN, int RT>
+__global__ void __launch_bounds__(Geo<LOGN, 16, RT>::ROWS_THREADS, Geo<LOGN, 16, RT>::ROWS_MINB)
+    k_ntt_rows_combine_pipe(const uint64_t *__restrict__ v, RowMap mv, CombineArgs a, int nre,
+                            const uint64_t *__restrict__ Pinv, const uint64_t *__restrict__ Pinv_sh, ModTab mt,
+                            Twiddles tw, uint32_t ntiles) {
+    using Gm = Geo<LOGN, 16, RT>;
+    constexpr uint32_t XT = Gm::H / Gm::ROWS;           // tiles per row
+    constexpr uint32_t seg = Gm::ROWS * Gm::T1 * 8;     // bytes of a tile's contiguous operand
+    __shared__ uint64_t sm[2][Gm::ROWS * Gm::RS];
+    const int nl = (int)mv.period;
+    struct Tile {
+        uint32_t blk, p;
+        size_t base;
+        const uint64_t *U, *A, *Pl;
+    };
+    auto locate = [&](uint32_t tile) {
+        Tile t;
+        row_decode(mv, tile / XT, t.blk, t.p);
+        t.base = (size_t)(tile % XT) * Gm::ROWS * Gm::T1;
+        t.U = a.u + (((size_t)t.blk * (a.u_stride ? a.u_stride : (size_t)nre) + t.p) << LOGN);
+        t.A = (t.blk & 1) ? a.add1 : a.add0;
+        if (t.A) t.A += (size_t)(t.blk >> 1) * a.add_stride + ((size_t)t.p << LOGN);
+        t.Pl = a.plus ? a.plus + (((size_t)t.blk * nl + t.p) << LOGN) : nullptr;
+        return t;
+    };
+    auto issue = [&](uint32_t tile, int s) {
+        const Tile t = locate(tile);
+        const uint64_t *S = v + row_at(mv, t.blk, t.p, LOGN);
+        MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
+            int rr = e / Gm::T1, l = e % Gm::T1;
+            cp_async8(&sm[s][rr * Gm::RS + l + (l >> 4)], &S[t.base + e]);
+        }
+        if (threadIdx.x == 0) {
+            l2_prefetch(t.U + t.base, seg);
+            if (t.Pl) l2_prefetch(t.Pl + t.base, seg);
+            if (t.A && a.galois == 1) l2_prefetch(t.A + t.base, seg);
+        }
+    };
+    uint32_t tile = blockIdx.x;
+    if (tile >= ntiles) return;
+    issue(tile, 0);
+    cp_async_commit();
+    for (int s = 0; tile < ntiles; tile += gridDim.x, s ^= 1) {
+        if (tile + gridDim.x < ntiles) issue(tile + gridDim.x, s ^ 1);
+        cp_async_commit();      // possibly empty: one group always trails the current tile's
+        cp_async_wait<1>();     // this thread's copies of the current tile have landed
+        __syncthreads();        // ... and everyone's
+        const Tile t = locate(tile);
+        const uint32_t pid = mv.pid[t.p];
+        const uint64_t q = mt.q[pid];
+        const int hi0 = (int)(tile % XT) * Gm::ROWS;
+        rows_rounds<LOGN, true, RT>(sm[s], hi0, q, pid, tw);
+        __syncthreads();
+        const uint64_t pi = Pinv[pid], pis = Pinv_sh[pid];
+        uint64_t *O = a.out + (((size_t)t.blk * nl + t.p) << LOGN);
+        MMFHE_TILE_LOOP(e, Gm::ROWS * Gm::TPR) {
+            int r2 = e / Gm::T1, l = e % Gm::T1;
+            const uint32_t x = (uint32_t)(t.base + e);
+            const uint64_t vv = mm::reduce_4q(sm[s][r2 * Gm::RS + l + (l >> 4)], q);
+            uint64_t res = mm::mul_shoup(mm::sub_mod(t.U[x], vv, q), pi, pis, q);
+            if (t.A) res = mm::add_mod(res, t.A[a.galois == 1 ? x : mm::galois_perm(x, a.galois, LOGN)], q);
+            if (t.Pl) res = mm::add_mod(res, t.Pl[x], q);
+            O[x] = res;
+        }
+        __syncthreads();        // sm[s] is refilled for the tile after next
+    }
+    cp_async_wait<0>();
+}
+
 // Butterflies of one pass over nr rows: N/2 per stage.
 template <int LOGN>
 double bf_cols(size_t nr) { return (double)nr * (double)(1u << (LOGN - 1)) * Geo<LOGN>::S1; }
@@ -650,6 +730,23 @@ void combine_rows_pass(Context &c, uint64_t *vtmp, const RowMap &mv, size_t nr, 
                        double bytes, const KeyipArgs *ka, cudaStream_t st) {
     using Gm = Geo<LOGN, 16, RT>;
     dim3 g(Gm::H / Gm::ROWS, (unsigned)nr), b(Gm::ROWS_THREADS);
+    // the pipelined combine keeps two tile buffers in static shared memory (at most 48 KB)
+    if constexpr (2 * Gm::ROWS * Gm::RS * 8 <= 48 * 1024) {
+        if (!ka && c.tune.combine_pipe) {
+            // persistent CTAs: as many as fit on the GPU at once
+            static int per_sm = 0;
+            if (!per_sm)
+                CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ntt_rows_combine_pipe<LOGN, RT>,
+                                                                  Gm::ROWS_THREADS, 0));
+            const uint32_t ntiles = (uint32_t)(Gm::H / Gm::ROWS) * (uint32_t)nr;
+            dim3 gp((unsigned)std::min<size_t>(ntiles, (size_t)c.sm_count * std::max(per_sm, 1)));
+            kernel_begin(c, st);
+            k_ntt_rows_combine_pipe<LOGN, RT><<<gp, b, 0, st>>>(vtmp, mv, a, nre, c.d_dn_Pinv, c.d_dn_Pinv_sh,
+                                                                 c.mods, c.tw, ntiles);
+            kernel_end(c, "ntt_combine_rows", gp, b, bytes, st, bf_rows<LOGN>(nr));
+            return;
+        }
+    }
     kernel_begin(c, st);
     if (!ka) {
         k_ntt_rows_combine<LOGN, RT, 0><<<g, b, 0, st>>>(vtmp, mv, a, nre, c.d_dn_Pinv, c.d_dn_Pinv_sh, c.mods, c.tw,
