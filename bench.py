@@ -78,8 +78,8 @@ def parse():
     ap.add_argument("--complex-slots", action="store_true",
                     help="vital and gesture workloads: Re + i Im in one complex slot (half the input ciphertexts)")
     ap.add_argument("--tiles", default=None,
-                    help="cols_width,rows_threads,keyip_windows,conv_rows[,keyip_pipe[,conv_prefetch[,combine_pipe]]]: "
-                         "set the tile shapes instead of autotuning")
+                    help="cols_width,rows_threads,keyip_windows,conv_rows[,keyip_pipe[,combine_pipe]]: set the "
+                         "tile shapes instead of autotuning")
     ap.add_argument("--keyip-fusion", action="store_true",
                     help="form the key inner product inside the ModDown passes instead of storing it with its "
                          "own kernel (ablation; same words, slower on B300)")
@@ -463,11 +463,11 @@ def pick_tiles(ctx, args, batch):
     if args.tiles:
         v = [int(x) for x in args.tiles.split(",")]
         ctx.set_tuning(*v[:4], keyip_fused=fused, keyip_pipe=v[4] if len(v) > 4 else 0,
-                       conv_prefetch=v[5] if len(v) > 5 else 0, combine_pipe=v[6] if len(v) > 6 else 0)
+                       combine_pipe=v[5] if len(v) > 5 else 0)
         return ctx.tuning()
     t = ctx.tuning() if args.no_autotune else ctx.autotune(batch)
     ctx.set_tuning(t["ntt_cols_width"], t["ntt_rows_threads"], t["keyip_windows"], t["conv_rows"], fused,
-                   t["keyip_pipe"], t["conv_prefetch"], t["combine_pipe"])
+                   t["keyip_pipe"], t["combine_pipe"])
     return ctx.tuning()
 
 
@@ -1384,7 +1384,8 @@ def run_gesture(args, rank, world, local):
     bf64_peak, bf32_peak = ctx.butterfly_peak()
     roofline = roofline_of(prof, bf64_peak, bf32_peak, B, ctx.mac_peak())
     roofline["traffic"] = ncu_traffic(roofline["kernel"], B, "gesture")
-    roofline["traffic_source"] = "profiles/ncu_traffic.json (gesture capture at B = 4, scaled by B / 4)"
+    if roofline["traffic"] is not None:
+        roofline["traffic_source"] = "profiles/ncu_traffic.json (gesture capture, scaled by the batch)"
     return {
         "metric": "encrypted gesture windows/s", "value": value, "unit": "windows/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)),

@@ -575,15 +575,11 @@ typedef struct mmfhe_tuning {
                                     the current group's products run (key switches with at most 4
                                     digits); same words.  Picked by the autotuner. */
     float keyip_pipe_ms[4];      /* last autotune, ms: pipelined, window groups 1, 2, 4, 8 */
-    uint32_t conv_prefetch;      /* 1: the fused ModUp / ModDown strided passes prefetch their conversion
-                                    sources into L2 before converting; same words.  Picked by the
-                                    autotuner. */
-    float conv_prefetch_ms[3];   /* last autotune, ms: ModUp + ModDown with the prefetch, rows 1, 2, 4 */
     uint32_t combine_pipe;       /* 1: the ModDown combine runs on persistent CTAs that load the next tile
                                     while the current one is transformed and combined; same words.
                                     Picked by the autotuner. */
-    float combine_pipe_ms[6];    /* last autotune, ms: ModUp + ModDown with the pipelined combine, without
-                                    then with the prefetch, rows 1, 2, 4 */
+    float combine_pipe_ms[3];    /* last autotune, ms: ModUp + ModDown with the pipelined combine, rows
+                                    1, 2, 4 */
 } mmfhe_tuning;
 mmfhe_status mmfhe_autotune(mmfhe_ctx *ctx, uint32_t batch, uint32_t level, mmfhe_tuning *out);
 mmfhe_status mmfhe_tuning_get(const mmfhe_ctx *ctx, mmfhe_tuning *out);

@@ -371,11 +371,10 @@ class Context:
         return _tuning_dict(t)
 
     def set_tuning(self, cols_width, rows_threads, keyip_windows, conv_rows=1, keyip_fused=0, keyip_pipe=0,
-                   conv_prefetch=0, combine_pipe=0):
+                   combine_pipe=0):
         t = Tuning(cols_width, rows_threads, keyip_windows, conv_rows)
         t.keyip_fused = keyip_fused
         t.keyip_pipe = keyip_pipe
-        t.conv_prefetch = conv_prefetch
         t.combine_pipe = combine_pipe
         self._c(_lib.lib().mmfhe_tuning_set(self.h, ctypes.byref(t)))
 
@@ -504,7 +503,6 @@ def _tuning_dict(t):
             "keyip_windows": t.keyip_windows, "conv_rows": t.conv_rows, "ntt_ms": list(t.ntt_ms),
             "keyip_ms": list(t.keyip_ms), "conv_ms": list(t.conv_ms), "keyip_fused": t.keyip_fused,
             "keyip_pipe": t.keyip_pipe, "keyip_pipe_ms": list(t.keyip_pipe_ms),
-            "conv_prefetch": t.conv_prefetch, "conv_prefetch_ms": list(t.conv_prefetch_ms),
             "combine_pipe": t.combine_pipe, "combine_pipe_ms": list(t.combine_pipe_ms)}
 
 

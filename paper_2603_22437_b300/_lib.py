@@ -67,8 +67,7 @@ class Tuning(ctypes.Structure):
                 ("keyip_windows", ctypes.c_uint32), ("conv_rows", ctypes.c_uint32), ("ntt_ms", ctypes.c_float * 4),
                 ("keyip_ms", ctypes.c_float * 4), ("conv_ms", ctypes.c_float * 3), ("keyip_fused", ctypes.c_uint32),
                 ("keyip_pipe", ctypes.c_uint32), ("keyip_pipe_ms", ctypes.c_float * 4),
-                ("conv_prefetch", ctypes.c_uint32), ("conv_prefetch_ms", ctypes.c_float * 3),
-                ("combine_pipe", ctypes.c_uint32), ("combine_pipe_ms", ctypes.c_float * 6)]
+                ("combine_pipe", ctypes.c_uint32), ("combine_pipe_ms", ctypes.c_float * 3)]
 
 
 class BatcherConfig(ctypes.Structure):

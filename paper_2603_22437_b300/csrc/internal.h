@@ -156,10 +156,8 @@ struct Tune {
     float ntt_ms[4] = {};     // last autotune: NTT pair per (cols_w, rows_t) in {8,16} x {128,256}
     float keyip_ms[4] = {};   // last autotune: key inner product per window group 1, 2, 4, 8
     float keyip_pipe_ms[4] = {};   // the same, pipelined
-    int conv_prefetch = 0;         // fused ModUp / ModDown strided passes prefetch their sources into L2 (1)
     int combine_pipe = 0;          // the ModDown combine walks its tiles with the next tile's load in flight (1)
-    float conv_prefetch_ms[3] = {};   // last autotune: fused ModUp + ModDown with the prefetch, rows 1, 2, 4
-    float combine_pipe_ms[6] = {};    // the same two sets of three with the pipelined combine
+    float combine_pipe_ms[3] = {};    // last autotune: fused ModUp + ModDown with the pipelined combine, rows 1, 2, 4
     float conv_ms[3] = {};    // last autotune: fused ModUp + ModDown per rows per CTA 1, 2, 4
 };
 

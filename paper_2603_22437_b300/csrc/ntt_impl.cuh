@@ -322,19 +322,6 @@ __device__ __forceinline__ void conv_load_any(uint64_t *tiles, int nr, const uin
     }
 }
 
-// Bulk L2 prefetch of the column strip this CTA converts: H segments of COLS
-// words in each of the nt source rows, spread over the CTA's threads, so
-// that the conversion's loads find their words in L2 when the sources do
-// not fit there (large batches).
-template <int LOGN, int CW>
-__device__ __forceinline__ void conv_prefetch(const uint64_t *X, int nt, int lo0) {
-    using Gm = Geo<LOGN, CW>;
-    for (int s = threadIdx.x; s < nt * Gm::H; s += Gm::COLS_THREADS) {
-        const int k = s / Gm::H, h = s % Gm::H;
-        l2_prefetch(X + ((size_t)k << LOGN) + (size_t)h * Gm::T1 + lo0, Gm::COLS * 8);
-    }
-}
-
 template <int LOGN, int CW, int RG, bool CENTERED>
 __device__ __forceinline__ void conv_dispatch(uint64_t *tiles, int nr, const uint64_t *X, int nt, int lo0,
                                               const ConvConsts<RG> &cc) {
@@ -376,7 +363,7 @@ __device__ __forceinline__ void cols_finish_group(uint64_t *tiles, int nr, const
 template <int LOGN, int CW, int RG>
 __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::COLS_MINB)
     k_ntt_cols_modup(const uint64_t *__restrict__ y, int nl, int nre, int alpha, int j0, uint64_t *dst, RowMap md,
-                     RowGroups gr, const uint64_t *__restrict__ m_mont, ModTab mt, Twiddles tw, int prefetch) {
+                     RowGroups gr, const uint64_t *__restrict__ m_mont, ModTab mt, Twiddles tw) {
     using Gm = Geo<LOGN, CW>;
     extern __shared__ uint64_t tiles[];
     __shared__ ConvConsts<RG> cc;
@@ -396,7 +383,6 @@ __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::CO
     __syncthreads();
     const uint64_t *Y = y + (((size_t)blk * nl + i0) << LOGN);
     const int lo0 = blockIdx.x * Gm::COLS;
-    if (prefetch) conv_prefetch<LOGN, CW>(Y, cnt, lo0);
     conv_dispatch<LOGN, CW, RG, false>(tiles, nr, Y, cnt, lo0, cc);
     cols_finish_group<LOGN, CW, RG>(tiles, nr, cc, dst, md, gr, g, blk, lo0, tw);
 }
@@ -461,7 +447,7 @@ template <int LOGN, int CW, int RG>
 __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::COLS_MINB)
     k_ntt_cols_moddown(const uint64_t *__restrict__ z, int K, int pid_p0, uint64_t *dst, RowMap md, RowGroups gr,
                        const uint64_t *__restrict__ phat_mont, const uint64_t *__restrict__ negp_mont, ModTab mt,
-                       Twiddles tw, int prefetch) {
+                       Twiddles tw) {
     using Gm = Geo<LOGN, CW>;
     extern __shared__ uint64_t tiles[];
     __shared__ ConvConsts<RG> cc;
@@ -480,7 +466,6 @@ __global__ void __launch_bounds__(Geo<LOGN, CW>::COLS_THREADS, Geo<LOGN, CW>::CO
     __syncthreads();
     const uint64_t *Z = z + (((size_t)blk * K) << LOGN);
     const int lo0 = blockIdx.x * Gm::COLS;
-    if (prefetch) conv_prefetch<LOGN, CW>(Z, K, lo0);
     conv_dispatch<LOGN, CW, RG, true>(tiles, nr, Z, K, lo0, cc);
     cols_finish_group<LOGN, CW, RG>(tiles, nr, cc, dst, md, gr, g, blk, lo0, tw);
 }
@@ -675,8 +660,7 @@ void modup_cols_pass(Context &c, uint64_t *digits, const uint64_t *y, const RowM
     }
     dim3 g(Gm::T1 / Gm::COLS, (unsigned)(nblk * gr.n)), b(Gm::COLS_THREADS);
     kernel_begin(c, st);
-    k_ntt_cols_modup<LOGN, CW, RG><<<g, b, smem, st>>>(y, nl, nre, c.alpha, j0, digits, md, gr, m_mont, c.mods, c.tw,
-                                                       c.tune.conv_prefetch);
+    k_ntt_cols_modup<LOGN, CW, RG><<<g, b, smem, st>>>(y, nl, nre, c.alpha, j0, digits, md, gr, m_mont, c.mods, c.tw);
     kernel_end(c, "ntt_modup_cols", g, b, bytes, st, bf_cols<LOGN>(nr), macs);
 }
 
@@ -713,7 +697,7 @@ void moddown_cols_pass(Context &c, uint64_t *vtmp, const uint64_t *z, const RowM
     dim3 g(Gm::T1 / Gm::COLS, (unsigned)(nblk * gr.n)), b(Gm::COLS_THREADS);
     kernel_begin(c, st);
     k_ntt_cols_moddown<LOGN, CW, RG><<<g, b, smem, st>>>(z, c.num_p, c.num_q, vtmp, mv, gr, c.d_dn_phat_mont,
-                                                         c.d_dn_negp_mont, c.mods, c.tw, c.tune.conv_prefetch);
+                                                         c.d_dn_negp_mont, c.mods, c.tw);
     kernel_end(c, "ntt_moddown_cols", g, b, bytes, st, bf_cols<LOGN>(nr), macs);
 }
 

@@ -115,24 +115,20 @@ void autotune(Context &c, int batch, int level) {
         const int rgs[3] = {1, 2, 4};
         float bg = 1e30f;
         for (int cp = 0; cp < 2; cp++)
-            for (int pf = 0; pf < 2; pf++)
-                for (int i = 0; i < 3; i++) {
-                    c.tune.conv_rows = rgs[i];
-                    c.tune.conv_prefetch = pf;
-                    c.tune.combine_pipe = cp;
-                    const float ms = time_best(st, [&] {
-                        launch_modup_ntt(c, dig.get(), y.get(), batch, level, st);
-                        launch_moddown_ntt(c, v.get(), z.get(), ca, batch, level, st);
-                    });
-                    if (!cp) (pf ? best.conv_prefetch_ms : best.conv_ms)[i] = ms;
-                    else best.combine_pipe_ms[pf * 3 + i] = ms;
-                    if (ms < bg) {
-                        bg = ms;
-                        best.conv_rows = rgs[i];
-                        best.conv_prefetch = pf;
-                        best.combine_pipe = cp;
-                    }
+            for (int i = 0; i < 3; i++) {
+                c.tune.conv_rows = rgs[i];
+                c.tune.combine_pipe = cp;
+                const float ms = time_best(st, [&] {
+                    launch_modup_ntt(c, dig.get(), y.get(), batch, level, st);
+                    launch_moddown_ntt(c, v.get(), z.get(), ca, batch, level, st);
+                });
+                (cp ? best.combine_pipe_ms : best.conv_ms)[i] = ms;
+                if (ms < bg) {
+                    bg = ms;
+                    best.conv_rows = rgs[i];
+                    best.combine_pipe = cp;
                 }
+            }
         CK(cudaStreamSynchronize(st));
     } catch (...) {
         cudaStreamDestroy(st);
@@ -168,10 +164,8 @@ void to_abi(const Tune &t, mmfhe_tuning *out) {
     out->keyip_fused = (uint32_t)t.keyip_fused;
     out->keyip_pipe = (uint32_t)t.keyip_pipe;
     std::copy(t.keyip_pipe_ms, t.keyip_pipe_ms + 4, out->keyip_pipe_ms);
-    out->conv_prefetch = (uint32_t)t.conv_prefetch;
-    std::copy(t.conv_prefetch_ms, t.conv_prefetch_ms + 3, out->conv_prefetch_ms);
     out->combine_pipe = (uint32_t)t.combine_pipe;
-    std::copy(t.combine_pipe_ms, t.combine_pipe_ms + 6, out->combine_pipe_ms);
+    std::copy(t.combine_pipe_ms, t.combine_pipe_ms + 3, out->combine_pipe_ms);
 }
 
 }  // namespace
@@ -205,13 +199,11 @@ mmfhe_status mmfhe_tuning_set(mmfhe_ctx *ctx, const mmfhe_tuning *in) {
     Context *c = ctx->c;
     const uint32_t w = in->ntt_cols_width, r = in->ntt_rows_threads, k = in->keyip_windows, g = in->conv_rows;
     if ((w != 8 && w != 16) || (r != 128 && r != 256) || (k != 1 && k != 2 && k != 4 && k != 8) ||
-        (g != 1 && g != 2 && g != 4) || in->keyip_fused > 1 || in->keyip_pipe > 1 || in->conv_prefetch > 1 ||
-        in->combine_pipe > 1)
+        (g != 1 && g != 2 && g != 4) || in->keyip_fused > 1 || in->keyip_pipe > 1 || in->combine_pipe > 1)
         return tfail(c, MMFHE_ERR_BAD_ARG, "unsupported tile shape");
     c->tune.combine_pipe = (int)in->combine_pipe;
     c->tune.keyip_fused = (int)in->keyip_fused;
     c->tune.keyip_pipe = (int)in->keyip_pipe;
-    c->tune.conv_prefetch = (int)in->conv_prefetch;
     c->tune.conv_rows = (int)g;
     c->tune.cols_w = (int)w;
     c->tune.rows_t = (int)r;

@@ -173,8 +173,8 @@ def test_every_tile_variant_gives_the_same_words(gsmall):
     """The autotuner only picks among variants that compute identical words:
     the FIR + DFT circuit (NTTs, fused ModUp / ModDown, key inner products of
     relinearisations and rotations) under every tile shape and conversion
-    row grouping, the conversion sources prefetched into L2 or not, the
-    combine on persistent pipelined CTAs or one tile per CTA, with the key
+    row grouping, the combine on persistent pipelined CTAs or one tile per
+    CTA, with the key
     inner product stored by its own kernel (its window walk plain or
     pipelined through shared memory) or formed inside the ModDown passes,
     equals the default-shape result, which
@@ -190,21 +190,20 @@ def test_every_tile_variant_gives_the_same_words(gsmall):
     ctx.eval(plan, keys, xs, ref)
     for cw in (8, 16):
         for rt in (128, 256):
-            for wg, rg, fu, pi, pf, cp in ((1, 4, 0, 1, 1, 1), (2, 2, 1, 0, 0, 0), (8, 1, 0, 1, 1, 0),
-                                           (2, 1, 0, 1, 0, 1), (4, 2, 0, 1, 1, 1), (4, 4, 1, 0, 1, 1)):
-                ctx.set_tuning(cw, rt, wg, rg, fu, pi, pf, cp)
+            for wg, rg, fu, pi, cp in ((1, 4, 0, 1, 1), (2, 2, 1, 0, 0), (8, 1, 0, 1, 0), (2, 1, 0, 1, 1),
+                                       (4, 2, 0, 1, 1), (4, 4, 1, 0, 1)):
+                ctx.set_tuning(cw, rt, wg, rg, fu, pi, cp)
                 outs = [np.empty_like(r) for r in ref]
                 ctx.eval(plan, keys, xs, outs)
                 for w in range(3):
-                    assert np.array_equal(outs[w], ref[w]), (cw, rt, wg, rg, fu, pi, pf, cp, w)
+                    assert np.array_equal(outs[w], ref[w]), (cw, rt, wg, rg, fu, pi, cp, w)
     with pytest.raises(M.MmfheError):
         ctx.set_tuning(32, 256, 4)
     t = ctx.autotune(3)
     assert t["ntt_cols_width"] in (8, 16) and t["ntt_rows_threads"] in (128, 256)
     assert t["keyip_windows"] in (1, 2, 4, 8)
     assert min(t["ntt_ms"]) > 0 and min(t["keyip_ms"]) > 0 and min(t["keyip_pipe_ms"]) > 0
-    assert t["keyip_pipe"] in (0, 1) and t["conv_prefetch"] in (0, 1) and min(t["conv_prefetch_ms"]) > 0
-    assert t["combine_pipe"] in (0, 1) and min(t["combine_pipe_ms"]) > 0
+    assert t["keyip_pipe"] in (0, 1) and t["combine_pipe"] in (0, 1) and min(t["combine_pipe_ms"]) > 0
     assert t["conv_rows"] in (1, 2, 4) and min(t["conv_ms"]) > 0
     assert t["keyip_fused"] == 1   # the last variant's setting: the autotuner leaves it unchanged
     ctx.set_tuning(saved["ntt_cols_width"], saved["ntt_rows_threads"], saved["keyip_windows"], saved["conv_rows"],
