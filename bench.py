@@ -659,6 +659,7 @@ def run_mine(args, rank, world, local):
         "memory": memory_line(mem, B, "5.3 GB peak cloud GPU memory per batched vital window (paper Table 5, "
                                       "RTX 3090 Ti)"),
         "accuracy": accuracy_line(),
+        "learned_vs_plain": learned_line(),
         "variants": variants,
         "wall_s_timed": wall,
     }
@@ -716,6 +717,23 @@ def memory_line(mem, batch, paper):
 
 
 ACCURACY_PROFILE = os.path.join("profiles", "accuracy_vital_64_windows.json")
+
+
+LEARNED_PROFILE = os.path.join("profiles", "gesture_learned_vs_plain.json")
+
+
+def learned_line():
+    """Batched learned chain against the plain one, from the committed record:
+    the gesture chain with the learned feature map a p + b p^2 (depth 9) and
+    with the paper's p (p^2)^2 (depth 11), windows/s at B = 16 and the
+    held-out accuracy of each chain's network trained by the library on the
+    same windows (tests/test_gpu_gesture_learned.py)."""
+    p = os.path.join(ROOT, LEARNED_PROFILE)
+    if not os.path.exists(p):
+        return None
+    j = json.load(open(p))
+    j["source"] = LEARNED_PROFILE
+    return j
 
 
 def accuracy_line():

@@ -14,8 +14,11 @@ Checked: output ciphertexts word for word against the oracle's learned
 circuit (two windows, split and complex-slot packing); the trained learned
 network's held-out accuracy against the plain chain's on the same 400
 held-out windows; and on three held-out full windows the decrypted logits of
-the encrypted learned chain give the labels of its FP64 network."""
+the encrypted learned chain give the labels of its FP64 network.  With
+MMFHE_LEARNED_OUT set, the accuracies are written there as JSON."""
+import json
 import multiprocessing as mp
+import os
 
 import numpy as np
 import pytest
@@ -145,6 +148,13 @@ def test_learned_map_network_labels(learned):
     test_plain = acc_p(te)
     print("learned map p + %g p^2: validation %.3f, held-out %.3f; plain p (p^2)^2 held-out %.3f"
           % (beta, va_acc, test_learned, test_plain))
+    path = os.environ.get("MMFHE_LEARNED_OUT")
+    if path:
+        with open(path, "w") as f:
+            json.dump({"b_over_a": beta, "validation_accuracy": va_acc, "heldout_accuracy_learned": test_learned,
+                       "heldout_accuracy_plain": test_plain, "candidates": {str(b): results[b][0] for b in BETAS},
+                       "train_windows": n_tr, "validation_windows": n_va, "heldout_windows": len(y) - n_tr - n_va},
+                      f, indent=1)
     assert test_learned > 0.6 and test_learned >= test_plain - 0.05, (test_learned, test_plain)
     # the encrypted learned chain with this network: labels of the FP64 network
     cfg = cc.GestureConfig(feature_coef=(1.0, beta))
