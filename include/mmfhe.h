@@ -437,6 +437,16 @@ mmfhe_status mmfhe_plan_rotations(const mmfhe_plan *plan, int32_t *out, uint32_t
  * uint64[n_in][2][L+1][N]; output: the n_out ciphertexts back to back, each
  * uint64[2][level_i+1][N]. */
 mmfhe_status mmfhe_plan_io(const mmfhe_plan *plan, uint32_t *n_in, uint32_t *n_out, uint32_t *out_levels);
+/* Where the client reads a vital plan's results after decryption: for
+ * num_r, den_r, num_RR, den_RR, num_HR, den_HR (the target bin's weighted
+ * average and each band's, Sec. "Example Pipelines"), the output ciphertext
+ * index and the slot.  The three outputs are the side branch (num_r in slot
+ * 0, den_r in slot r_c) and one ciphertext per band (num_b in slot b, den_b
+ * in slot span_b r_c + b, span_b the band's power-of-two bin span), so each
+ * band's sums stay apart from the other band's.  *count = 6 for VITAL plans,
+ * 0 for the others; BAD_ARG when capacity is below the count. */
+mmfhe_status mmfhe_plan_readout(const mmfhe_plan *plan, uint32_t *out_index, uint32_t *slot, uint32_t capacity,
+                                uint32_t *count);
 
 /* Evaluate the plan's circuit on `batch` windows.  keys[w], in_cts[w] and
  * out_cts[w] belong to window w; windows with the same keys object are
@@ -448,8 +458,10 @@ mmfhe_status mmfhe_eval(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *cons
 /* mmfhe_eval restricted to MMFHE_CIRCUIT_VITAL (and _PER_FRAME) plans (paper Sec. "Example
  * Pipelines", Encrypted Vital Signs; depth per Table 1).  Window inputs:
  * stream 1 (K1) G groups x (Re, Im), then stream 2 (K4) G x (Re, Im), at the
- * top level.  Outputs: num_r, den_r (target bin), num_RR, den_RR, num_HR,
- * den_HR (frequency-weighted sums in Hz; BPM = 60 num/den). */
+ * top level.  VITAL outputs: three ciphertexts holding num_r, den_r (target
+ * bin), num_RR, den_RR, num_HR, den_HR (frequency-weighted sums in Hz; BPM =
+ * 60 num/den) at the slots mmfhe_plan_readout gives; VITAL_PER_FRAME: six
+ * ciphertexts, those values in slot 0 in that order. */
 mmfhe_status mmfhe_eval_vital(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *const *keys,
                               const uint64_t *const *in_cts, size_t batch, uint64_t *const *out_cts, void *stream);
 

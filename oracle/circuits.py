@@ -610,10 +610,10 @@ class VitalCircuit:
             bands at once slot by slot; K3 narrowband DFT (+1): real rows
             at position k, imaginary rows at k + F_pad/2, band b in slot b;
             |X|^2 (+2), the imaginary half added onto the real by one
-            rotation; square (+3); x f_k and x 1 (+4), rotate-sum -> num
-            and den with RR in slot 0, HR in slot 1; one rotation each
-            brings HR to slot 0.
-    Outputs: [num_r, den_r, num_RR, den_RR, num_HR, den_HR].
+            rotation; square (+3); x f_k and x 1 (+4) per band, den's
+            products moved span_b frames on, one rotate-sum per band.
+    Outputs: [side branch, band RR, band HR]; ``readout`` gives where
+    num_r, den_r, num_RR, den_RR, num_HR, den_HR sit.
     """
 
     def __init__(self, P, cfg=VitalConfig()):
@@ -701,6 +701,7 @@ class VitalCircuit:
                 if delta // self.n1_dft:
                     ks.add((delta // self.n1_dft) * self.n1_dft * lay.r_c)
         ks |= {lay.r_c << i for i in range(int(math.log2(self.span_all())))}
+        ks |= {-self.span(b) * lay.r_c for b in range(len(self.bands))}     # den beside num in a band's sums
         ks.add((lay.f_pad // 2) * lay.r_c)
         ks.add(1)
         out = sorted({k % self.P.slots for k in ks} - {0})
@@ -729,8 +730,9 @@ class VitalCircuit:
         into one ciphertext by a rotation tree (group c lands in block -c mod
         G'); one rotate-and-sum over a block finishes every group's E at its
         block start.  w = E^2 is squared once, the index / one vectors keep
-        the valid bins, and a rotate-and-sum over the bins and then over the
-        blocks leaves num_r and den_r in slot 0."""
+        the valid bins, den's products move one frame on, and a rotate-and-
+        sum over the bins and then over the blocks leaves num_r in slot 0 and
+        den_r in slot r_c of one ciphertext."""
         lay = self.lay
         Gp, blk = self.side_groups(), self.side_block()
         self._record("K1_energy", ps)
@@ -753,12 +755,13 @@ class VitalCircuit:
         w = ev.rescale(ev.square_sum([E]))
         self._record("K1_integration", E)
         self._record("K2_soft_attention", w)
-        out = []
-        for name in ("idx", "one"):
-            t = ev.rescale(ev.mul_plain(w, consts[(name,)]))
-            t = ev.rotsum(t, 1, lay.r_c)
-            out.append(ev.rotsum(t, blk * lay.r_c, Gp))
-        return out
+        # num and den share one ciphertext: den's terms moved one frame on
+        # (block starts + 1 frame, never reached by the other's sums)
+        tn = ev.rescale(ev.mul_plain(w, consts[("idx",)]))
+        td = ev.rescale(ev.mul_plain(w, consts[("one",)]))
+        t = ev.add(tn, ev.rotate(td, -lay.r_c))
+        t = ev.rotsum(t, 1, lay.r_c)
+        return ev.rotsum(t, blk * lay.r_c, Gp)
 
     def constant_keys(self):
         """Keys of every constant ``constants()`` encodes, without encoding."""
@@ -829,27 +832,34 @@ class VitalCircuit:
     def band_sums(self, ev, consts, S):
         """Weighted frequency average of both bands from the sharpened powers
         S (band b in bin slot b): num_b = sum_k (k fs / F) S_k and den_b =
-        sum_k S_k over band b's bins, each by its own mask and a
-        rotate-and-sum over band b's span; HR's sums are moved to slot 0.
-        Returns [num_RR, den_RR, num_HR, den_HR]."""
+        sum_k S_k over band b's bins, each band by its own masks in a
+        ciphertext of its own: den's products moved span_b frames on, one
+        rotate-and-sum over band b's span leaves num_b in slot b and den_b in
+        slot span_b r_c + b.  Returns [band RR, band HR]."""
         out = []
         for b in range(len(self.bands)):
-            for t in ("fw", "fone"):
-                x = ev.rotsum(ev.rescale(ev.mul_plain(S, consts[(t, b)])), self.lay.r_c, self.span(b))
-                out.append(ev.rotate(x, b) if b else x)
+            tn = ev.rescale(ev.mul_plain(S, consts[("fw", b)]))
+            td = ev.rescale(ev.mul_plain(S, consts[("fone", b)]))
+            t = ev.add(tn, ev.rotate(td, -self.span(b) * self.lay.r_c))
+            out.append(ev.rotsum(t, self.lay.r_c, self.span(b)))
         return out
+
+    def readout(self):
+        """(output, slot) of num_r, den_r, num_RR, den_RR, num_HR, den_HR."""
+        rc = self.lay.r_c
+        return [(0, 0), (0, rc), (1, 0), (1, self.span(0) * rc), (2, 1), (2, self.span(1) * rc + 1)]
 
     # -- the chain -----------------------------------------------------------
     def run(self, ev, consts, s1, s2):
         """s1, s2: lists of G (re, im) ciphertext pairs (stream 1 feeds K1,
         stream 2 feeds K4), all at the top level; with complex slots lists
-        of G ciphertexts of Re + i Im.  Returns six ciphertexts."""
+        of G ciphertexts of Re + i Im.  Returns three ciphertexts (``readout``)."""
         P, lay, cfg = self.P, self.lay, self.cfg
         G = lay.groups
         if cfg.complex_slots:
             return self._run_complex(ev, consts, s1, s2)
         # side branch: K1 energy, K2 soft power attention (gamma = 2)
-        num_r, den_r = self.side_branch(ev, consts, [ev.rescale(ev.square_sum([re, im])) for re, im in s1])
+        side = self.side_branch(ev, consts, [ev.rescale(ev.square_sum([re, im])) for re, im in s1])
 
         # K4 soft I/Q extraction (P_phi = 2)
         m = []
@@ -909,7 +919,7 @@ class VitalCircuit:
         # sharpen (gamma = 2), weighted frequency average (RR in slot 0, HR in slot 1)
         S = ev.rescale(ev.square_sum([Mg]))
         self._record("sharpen", S)
-        return [num_r, den_r] + self.band_sums(ev, consts, S)
+        return [side] + self.band_sums(ev, consts, S)
 
     def _run_complex(self, ev, consts, s1, s2):
         """The same chain on complex slots z = Re + i Im: |z|^2 = z conj(z);
@@ -924,7 +934,7 @@ class VitalCircuit:
         def abs2(z):
             return ev.rescale(ev.relin(ev.tensor(z, ev.conjugate(z))))
 
-        num_r, den_r = self.side_branch(ev, consts, [abs2(z) for z in s1])
+        side = self.side_branch(ev, consts, [abs2(z) for z in s1])
 
         # K4: Z = sum_r m z (I + i Q), P_phi = 2
         m = [ev.rescale(ev.square_sum([abs2(z)])) for z in s2]
@@ -959,7 +969,7 @@ class VitalCircuit:
         pw = ev.rescale(ev.square_sum([X]))
         Mg = ev.add(pw, ev.rotate(pw, (lay.f_pad // 2) * lay.r_c))
         S = ev.rescale(ev.square_sum([Mg]))
-        return [num_r, den_r] + self.band_sums(ev, consts, S)
+        return [side] + self.band_sums(ev, consts, S)
 
 
 # ---------------------------------------------------------------------------

@@ -761,6 +761,13 @@ class Plan:
         self.ctx._c(_lib.lib().mmfhe_plan_io(self.h, ctypes.byref(ni), ctypes.byref(no), lv))
         return ni.value, no.value, [lv[i] for i in range(no.value)]
 
+    def readout(self):
+        """(output index, slot) of num_r, den_r, num_RR, den_RR, num_HR,
+        den_HR for a vital plan; [] for other circuits."""
+        oi, sl, n = (ctypes.c_uint32 * 6)(), (ctypes.c_uint32 * 6)(), ctypes.c_uint32()
+        self.ctx._c(_lib.lib().mmfhe_plan_readout(self.h, oi, sl, 6, ctypes.byref(n)))
+        return [(oi[i], sl[i]) for i in range(n.value)]
+
     def destroy(self):
         if getattr(self, "h", None) and self.owned:
             _lib.lib().mmfhe_plan_destroy(self.h)

@@ -195,6 +195,7 @@ _SIGS = {
     "mmfhe_plan_encode_consts": [_VP],
     "mmfhe_plan_rotations": [_VP, _VP, _U32, ctypes.POINTER(_U32)],
     "mmfhe_plan_io": [_VP, ctypes.POINTER(_U32), ctypes.POINTER(_U32), _VP],
+    "mmfhe_plan_readout": [_VP, _VP, _VP, _U32, ctypes.POINTER(_U32)],
     "mmfhe_eval": [_VP, _VP, _VP, _VP, _SZ, _VP, _VP],
     "mmfhe_eval_vital": [_VP, _VP, _VP, _VP, _SZ, _VP, _VP],
     "mmfhe_pack_window": [_U32, _U32, _U32, _VP, _VP],

@@ -856,6 +856,26 @@ mmfhe_status mmfhe_plan_io(const mmfhe_plan *plan, uint32_t *n_in, uint32_t *n_o
     return MMFHE_OK;
 }
 
+mmfhe_status mmfhe_plan_readout(const mmfhe_plan *plan, uint32_t *out_index, uint32_t *slot, uint32_t capacity,
+                                uint32_t *count) {
+    if (!plan || !plan->p || !count) return fail(nullptr, MMFHE_ERR_BAD_ARG, "null argument");
+    const Plan &p = *plan->p;
+    if (p.cfg.kind != MMFHE_CIRCUIT_VITAL) {
+        *count = 0;
+        return MMFHE_OK;
+    }
+    const uint32_t rc = (uint32_t)p.r_c;
+    const uint32_t idx[6] = {0, 0, 1, 1, 2, 2};
+    const uint32_t pos[6] = {0, rc, 0, (uint32_t)p.span[0] * rc, 1, (uint32_t)p.span[1] * rc + 1};
+    *count = 6;
+    if (capacity < 6 || !out_index || !slot) return fail(p.ctx, MMFHE_ERR_BAD_ARG, "readout needs room for 6 entries");
+    for (int i = 0; i < 6; i++) {
+        out_index[i] = idx[i];
+        slot[i] = pos[i];
+    }
+    return MMFHE_OK;
+}
+
 mmfhe_status mmfhe_eval(mmfhe_ctx *ctx, const mmfhe_plan *plan, mmfhe_keys *const *keys,
                         const uint64_t *const *in_cts, size_t batch, uint64_t *const *out_cts, void *stream) {
     Context *c = nullptr;

@@ -468,9 +468,11 @@ Plan *create_plan(Context &c, const mmfhe_circuit_config &cfg_in) {
         for (int i = 0; (1 << i) < std::max(p->span[0], p->span[1]); i++) rot(p->r_c << i);
         rot((Fp / 2) * p->r_c);
         rot(1);
+        for (int b = 0; b < 2; b++) rot(-p->span[b] * p->r_c);   // den beside num in a band's sums
         if (cfg.complex_slots) rots.insert(MMFHE_ROT_CONJ);
         p->n_in = (cfg.complex_slots ? 2 : 4) * p->groups;
-        p->out_levels = {lv_side - 1, lv_side - 1, lv_final - 1, lv_final - 1, lv_final - 1, lv_final - 1};
+        // the side branch (num_r, den_r), band RR, band HR
+        p->out_levels = {lv_side - 1, lv_final - 1, lv_final - 1};
     }
     rots.erase(0);
     p->rotations.assign(rots.begin(), rots.end());
@@ -734,9 +736,9 @@ static std::vector<BsgsSet> dft_sets(const Plan &p, const CtB &dphi) {
 // packed into one ciphertext by a rotation tree (group g lands in block
 // -g mod G'), one rotate-and-sum over a block, w = E^2 once, and
 // rotate-and-sums over the bins and then over the blocks.  Returns
-// {num_r, den_r} (slot 0).
-static std::pair<CtB, CtB> side_branch(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &ps,
-                                       cudaStream_t st) {
+// one ciphertext holding num_r in slot 0 and den_r in slot r_c (den's
+// products moved one frame on before the sums).
+static CtB side_branch(Context &c, const Plan &p, const Keys &k, std::vector<CtB> &ps, cudaStream_t st) {
     const int Rc = p.r_c, Gp = next_pow2(p.groups), blk = p.f_pad / Gp;
     const PtDev &mask = plan_const(p, MMFHE_CONST_PMASK, 0, 0);
     std::vector<CtB> parts;
@@ -765,33 +767,39 @@ static std::pair<CtB, CtB> side_branch(Context &c, const Plan &p, const Keys &k,
     CtB E = rotsum(c, k, parts[0], Rc, (uint32_t)blk, st);
     parts.clear();
     CtB w = rescale(c, square_sum(c, k, {&E}, st), st);
-    CtB sums[2];
+    CtB t[2];
     for (int i = 0; i < 2; i++) {
         const PtDev &pt = plan_const(p, i == 0 ? MMFHE_CONST_IDX : MMFHE_CONST_ONE, 0, 0);
-        CtB t = ct_new(c, w.B, w.level, w.scale * pt.scale);
-        ct_mul_plain(c, t, w, pt, false, st);
-        CtB r = rotsum(c, k, rescale(c, t, st), 1, (uint32_t)Rc, st);
-        sums[i] = rotsum(c, k, r, blk * Rc, (uint32_t)Gp, st);
+        CtB x = ct_new(c, w.B, w.level, w.scale * pt.scale);
+        ct_mul_plain(c, x, w, pt, false, st);
+        t[i] = rescale(c, x, st);
     }
-    return {std::move(sums[0]), std::move(sums[1])};
+    // den's terms one frame on, beside num's in one ciphertext
+    CtB r = rotate_add(c, k, t[1], -Rc, t[0], st);
+    r = rotsum(c, k, r, 1, (uint32_t)Rc, st);
+    return rotsum(c, k, r, blk * Rc, (uint32_t)Gp, st);
 }
 
 // Weighted frequency average of both bands from the sharpened powers S (band
-// b in bin slot b): per band, its own weight mask and a rotate-and-sum over
-// its own span, so each band's sums leave in ciphertexts of their own and a
-// band far stronger than the other cannot overflow the other's sums at the
-// last level; HR's sums move to slot 0.  Returns num_RR, den_RR, num_HR, den_HR.
+// b in bin slot b): per band, its own weight and one masks, den's products
+// moved span_b frames on beside num's, and one rotate-and-sum over the span,
+// so each band's sums leave in a ciphertext of their own (a band far stronger
+// than the other cannot overflow the other's sums at the last level): num_b
+// in slot b, den_b in slot span_b r_c + b.  Returns the RR and HR ciphertexts.
 static std::vector<CtB> band_sums(Context &c, const Plan &p, const Keys &k, const CtB &S, cudaStream_t st) {
     const int B = S.B;
     std::vector<CtB> out;
-    for (int b = 0; b < 2; b++)
-        for (uint32_t tag : {(uint32_t)MMFHE_CONST_FW, (uint32_t)MMFHE_CONST_FONE}) {
-            const PtDev &pt = plan_const(p, tag, (uint32_t)b, 0);
-            CtB t = ct_new(c, B, S.level, S.scale * pt.scale);
-            ct_mul_plain(c, t, S, pt, false, st);
-            CtB x = rotsum(c, k, rescale(c, t, st), p.r_c, (uint32_t)p.span[b], st);
-            out.push_back(b ? rotate(c, k, x, 1, st) : std::move(x));
+    for (int b = 0; b < 2; b++) {
+        CtB t[2];
+        for (int i = 0; i < 2; i++) {
+            const PtDev &pt = plan_const(p, i == 0 ? MMFHE_CONST_FW : MMFHE_CONST_FONE, (uint32_t)b, 0);
+            CtB x = ct_new(c, B, S.level, S.scale * pt.scale);
+            ct_mul_plain(c, x, S, pt, false, st);
+            t[i] = rescale(c, x, st);
         }
+        CtB r = rotate_add(c, k, t[1], -p.span[b] * p.r_c, t[0], st);
+        out.push_back(rotsum(c, k, r, p.r_c, (uint32_t)p.span[b], st));
+    }
     return out;
 }
 
@@ -808,7 +816,7 @@ static std::vector<CtB> run_vital_complex(Context &c, const Plan &p, const Keys 
     // ---- side branch: K1, K2 ----
     std::vector<CtB> ps;
     for (int g = 0; g < G; g++) ps.push_back(abs2(in[g]));
-    auto [num_r, den_r] = side_branch(c, p, k, ps, st);
+    CtB side = side_branch(c, p, k, ps, st);
     // ---- K4: Z = sum_r m z ----
     std::vector<CtB> m;
     for (int g = 0; g < G; g++) {
@@ -852,8 +860,7 @@ static std::vector<CtB> run_vital_complex(Context &c, const Plan &p, const Keys 
     CtB merged = rotate_add(c, k, pw, (p.f_pad / 2) * Rc, pw, st);
     CtB S = rescale(c, square_sum(c, k, {&merged}, st), st);
     std::vector<CtB> out;
-    out.push_back(std::move(num_r));
-    out.push_back(std::move(den_r));
+    out.push_back(std::move(side));
     for (CtB &x : band_sums(c, p, k, S, st)) out.push_back(std::move(x));
     return out;
 }
@@ -865,7 +872,7 @@ static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std:
     // ---- side branch: K1, K2 ----
     std::vector<CtB> ps;
     for (int g = 0; g < G; g++) ps.push_back(rescale(c, square_sum(c, k, {&in[2 * g], &in[2 * g + 1]}, st), st));
-    auto [num_r, den_r] = side_branch(c, p, k, ps, st);
+    CtB side = side_branch(c, p, k, ps, st);
     // ---- K4 soft I/Q ----
     std::vector<CtB> m;
     for (int g = 0; g < G; g++) {
@@ -923,8 +930,7 @@ static std::vector<CtB> run_vital(Context &c, const Plan &p, const Keys &k, std:
     // ---- sharpen, weighted frequency average (RR in slot 0, HR in slot 1) ----
     CtB S = rescale(c, square_sum(c, k, {&merged}, st), st);
     std::vector<CtB> out;
-    out.push_back(std::move(num_r));
-    out.push_back(std::move(den_r));
+    out.push_back(std::move(side));
     for (CtB &x : band_sums(c, p, k, S, st)) out.push_back(std::move(x));
     return out;
 }

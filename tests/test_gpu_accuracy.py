@@ -79,7 +79,7 @@ def test_decrypted_rates_over_64_windows():
     from oracle import ckks as ck
     from oracle import circuits as cc
     from oracle import params as pm
-    from test_gpu_parity import install_oracle_consts, lib_params
+    from test_gpu_parity import install_oracle_consts, lib_params, read_values
 
     P = pm.vital_params()
     circ = cc.VitalCircuit(P, cc.VitalConfig(bins=256))
@@ -109,14 +109,17 @@ def test_decrypted_rates_over_64_windows():
     # output scales follow the oracle's scale arithmetic (a counting run)
     scales = [o.scale for o in circ.run(cc.CountingEvaluator(P), circ.constants(), *_shapes(circ, P))]
 
+    readout = plan.readout()
+    assert readout == circ.readout()
+
     def decrypt(o):
-        dv, off = [], 0
+        cts, off = [], 0
         for l, sc in zip(lv, scales):
             n = 2 * (l + 1) * P.n
             c = o[off : off + n].reshape(2, l + 1, P.n)
-            dv.append(ck.decrypt_decode(P, sk, ck.Ciphertext(c[0], c[1], l, sc))[0])
+            cts.append(ck.Ciphertext(c[0], c[1], l, sc))
             off += n
-        return dv
+        return read_values(P, sk, cts, readout)
 
     rows, k = [], 0
     for w in wins:

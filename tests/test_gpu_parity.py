@@ -235,6 +235,18 @@ def encrypt_window(P, pk, lay, arrays, seed):
     return out
 
 
+def read_values(P, sk, cts, readout):
+    """The six values of a vital window (num_r, den_r, num_RR, den_RR,
+    num_HR, den_HR) from its output ciphertexts (oracle Ciphertexts),
+    decrypted and read at the plan's readout positions."""
+    dec, vals = {}, []
+    for o, slot in readout:
+        if o not in dec:
+            dec[o] = ck.decrypt_decode(P, sk, cts[o]).real
+        vals.append(dec[o][slot])
+    return vals
+
+
 def window_words(cts):
     return np.ascontiguousarray(np.stack([c.words() for c in cts]))
 

@@ -11,7 +11,8 @@ from oracle import circuits as cc
 from oracle import params as pm
 from oracle import plain
 
-from test_gpu_parity import compare_plan_consts, encrypt_window, install_oracle_consts, lib_params, load_keys, window_words
+from test_gpu_parity import (compare_plan_consts, encrypt_window, install_oracle_consts, lib_params, load_keys,
+                             read_values, window_words)
 
 pytestmark = pytest.mark.gpu
 
@@ -68,8 +69,9 @@ def split(P, flat, lv):
 def test_plan_matches_oracle_structure(vital):
     assert vital["plan"].rotations() == vital["rots"]
     n_in, n_out, lv = vital["plan"].io()
-    assert n_in == 16 and n_out == 6
-    assert lv == [o.level for o in vital["ref0"]] == [7, 7, 0, 0, 0, 0]
+    assert n_in == 16 and n_out == 3
+    assert lv == [o.level for o in vital["ref0"]] == [7, 0, 0]
+    assert vital["plan"].readout() == vital["circ"].readout()
 
 
 def test_vital_batch_word_exact_and_decrypted(vital):
@@ -83,8 +85,9 @@ def test_vital_batch_word_exact_and_decrypted(vital):
     s1, s2 = vital["wins"][1]
     sb, mc = plain.side_branch(s1), plain.main_chain(s2, vital["cfg"])
     scales = [r.scale for r in vital["ref0"]]
-    dv = [ck.decrypt_decode(P, vital["sk"], ck.Ciphertext(g[0], g[1], l, sc))[0]
-          for g, l, sc in zip(split(P, outs[1], lv), lv, scales)]
+    dv = read_values(P, vital["sk"], [ck.Ciphertext(g[0], g[1], l, sc)
+                                      for g, l, sc in zip(split(P, outs[1], lv), lv, scales)],
+                     vital["circ"].readout())
     assert abs(dv[0] / dv[1] - sb["num"] / sb["den"]) < 1e-6
     for b in range(2):
         bd = mc["bands"][b]
@@ -108,9 +111,11 @@ def test_library_encoded_plan_matches(vital):
     outs, lv = out_buffers(vital, 1)
     ctx.eval(plan2, vital["keys"], [vital["ins"][0]], outs, vital=True)
     got = split(P, outs[0], lv)
-    for g, r in zip(got, vital["ref0"]):
-        a = ck.decrypt_decode(P, vital["sk"], ck.Ciphertext(g[0], g[1], r.level, r.scale))[0]
-        b = ck.decrypt_decode(P, vital["sk"], r)[0]
+    ro = vital["circ"].readout()
+    va = read_values(P, vital["sk"], [ck.Ciphertext(g[0], g[1], r.level, r.scale) for g, r in zip(got, vital["ref0"])],
+                     ro)
+    vb = read_values(P, vital["sk"], vital["ref0"], ro)
+    for a, b in zip(va, vb):
         assert abs(a - b) <= 1e-6 * max(1.0, abs(b))
     plan2.destroy()
 
@@ -184,13 +189,14 @@ def test_complex_slot_vital_word_exact_and_decrypted(vital_complex):
     P, ctx, plan = v["P"], v["ctx"], v["plan"]
     assert plan.rotations() == v["circ"].rotations() and plan.rotations()[0] == M.ROT_CONJ
     n_in, n_out, lv = plan.io()
-    assert n_in == 8 and n_out == 6 and lv == [o.level for o in v["ref"]]
+    assert n_in == 8 and n_out == 3 and lv == [o.level for o in v["ref"]]
+    assert plan.readout() == v["circ"].readout()
     outs, lv = out_buffers(v, 1)
     ctx.eval(plan, v["keys"], v["ins"], outs, vital=True)
     got = split(P, outs[0], lv)
     for o, (g, r) in enumerate(zip(got, v["ref"])):
         assert np.array_equal(g, r.words()), "output %d" % o
-    dv = [ck.decrypt_decode(P, v["sk"], r)[0] for r in v["ref"]]
+    dv = read_values(P, v["sk"], v["ref"], v["circ"].readout())
     sb, mc = plain.side_branch(v["s"][0]), plain.main_chain(v["s"][1], cc.VitalConfig(bins=256, taylor_order=3))
     assert abs(dv[0] / dv[1] - sb["num"] / sb["den"]) < 1e-6
     for b in range(2):

@@ -105,7 +105,9 @@ def test_per_kernel_encryption_noise_and_rates():
             json.dump({"window_seed": 1003, "bins": R, "frames": F, "rows": rows}, f, indent=1)
     for name, r in rows.items():
         assert r["mse"] < 1e-5, (name, r)
-    dv = [ck.decrypt_decode(P, sk, o)[0] for o in outs]
+    assert len(outs) == 3
+    full = [ck.decrypt_decode(P, sk, o).real for o in outs]
+    dv = [full[o][slot] for o, slot in circ.readout()]
     assert abs(dv[0] / dv[1] - sb["num"] / sb["den"]) < 1e-6
     for b in range(2):
         bd = mc["bands"][b]
