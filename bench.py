@@ -831,8 +831,14 @@ def run_batching(args, rank, world, local):
         ms = [a.elapsed_time(b) for a, b in ev]
         res[mode] = {"value": job_throughput(world, len(frames) * args.steps, sum(ms) / 1000.0),
                      "ms_per_step": float(np.mean(ms))}
-    same = all(torch.equal(outs["graph"][w], outs["plain"][w]) and torch.equal(outs["nograph"][w], outs["plain"][w])
-               for w in range(len(frames)))
+    differ = []
+    for w in range(len(frames)):
+        for m in ("graph", "nograph"):
+            if not torch.equal(outs[m][w], outs["plain"][w]):
+                bad = (outs[m][w] != outs["plain"][w]).nonzero().flatten()
+                differ.append({"window": w, "frames": frames[w], "mode": m, "words": int(bad.numel()),
+                               "first_word": int(bad[0]), "out_words": out_words[frames[w]]})
+    same = not differ
     st = bat.stats()
     line = {
         "metric": METRIC, "value": res["graph"]["value"], "unit": "windows/s", "n_gpus": world,
@@ -847,6 +853,7 @@ def run_batching(args, rank, world, local):
         "batched_graphs": res["graph"], "batched_no_graphs": res["nograph"], "plain_one_call_per_window": res["plain"],
         "speedup_vs_plain": res["graph"]["value"] / res["plain"]["value"],
         "identical_words_all_modes": bool(same),
+        "differing_windows": differ[:12],
         "batcher_stats": st,
     }
     return line

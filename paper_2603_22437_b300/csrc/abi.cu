@@ -211,6 +211,10 @@ Buf mmfhe::load_key(Context &c, const uint64_t *words) {
     check_ptr(words, "key words");
     const int rows = c.num_q + c.num_p;
     const size_t total = (size_t)c.dnum * 2 * rows * c.n;
+    // the context pool reuses a freed buffer at once, which is safe only in
+    // stream order; evaluations may run on a caller's stream, so wait for
+    // all device work before this set-up step allocates from the pool
+    CK(cudaDeviceSynchronize());
     Buf b(c.pool.get(), total);
     CK(cudaMemcpy(b.get(), words, total * 8, cudaMemcpyDefault));
     std::vector<int> pids(rows);

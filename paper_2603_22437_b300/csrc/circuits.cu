@@ -498,6 +498,10 @@ static bool const_is_qp(const Plan &p, const mmfhe_const_key &k) {
 void plan_set_const(Plan &p, uint32_t i, const uint64_t *words_host_or_dev, cudaStream_t st) {
     Context &c = *p.ctx;
     if (i >= p.keys.size()) throw Error(MMFHE_ERR_BAD_ARG, "constant index out of range");
+    // the context pool reuses a freed buffer at once, which is safe only in
+    // stream order; evaluations may run on a caller's stream, so wait for
+    // all device work before this set-up step allocates from the pool
+    CK(cudaDeviceSynchronize());
     const int level = (int)p.keys[i].level;
     if (const_is_qp(p, p.keys[i])) {
         p.consts[i] = pt_qp_from_coeffs(c, words_host_or_dev, level, (double)c.primes[level], st);
@@ -640,6 +644,10 @@ static std::vector<double> const_slots(const Plan &p, const mmfhe_const_key &k) 
 
 void plan_encode_consts(Plan &p, cudaStream_t st) {
     Context &c = *p.ctx;
+    // the context pool reuses a freed buffer at once, which is safe only in
+    // stream order; evaluations may run on a caller's stream, so wait for
+    // all device work before this set-up step allocates from the pool
+    CK(cudaDeviceSynchronize());
     if (p.cfg.kind == MMFHE_CIRCUIT_FC)
         throw Error(MMFHE_ERR_BAD_ARG, "FC constants are learned weights: set them with mmfhe_plan_set_fc_layer");
     std::vector<uint64_t> words;
