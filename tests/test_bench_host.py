@@ -57,3 +57,38 @@ def test_traffic_scales_with_the_batch_and_follows_the_source_hash(bench, tmp_pa
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "csrc_hash", lambda: "f" * 16)
     assert bench.ncu_traffic(name, 16) is None
+
+
+def test_issue_block_against_the_hardware_limit(bench, tmp_path, monkeypatch):
+    """roofline.issue: warp instructions per SM cycle from the committed record
+    against 4 per SM per clock x 148 SMs x the sampled clock; unused when the
+    record was taken on other kernel sources."""
+    j = json.load(open(os.path.join(ROOT, "profiles", "ncu_issue_rates.json")))
+    name, k = next(iter(j["kernels"].items()))
+    if j["csrc_hash"] == bench.csrc_hash():
+        r = bench.ncu_issue(name, 2000.0)
+        ipc = k["inst_per_active_sm_cycle"]
+        assert r["frac"] == pytest.approx(ipc / 4)
+        assert r["peak_warp_inst_per_s"] == pytest.approx(4 * 148 * 2000e6)
+        assert r["achieved_warp_inst_per_s"] == pytest.approx(ipc * 148 * 2000e6)
+    assert bench.ncu_issue("no_such_kernel", 2000.0) is None
+    fake = dict(j, csrc_hash="0" * 16)
+    os.makedirs(tmp_path / "profiles")
+    (tmp_path / "profiles" / "ncu_issue_rates.json").write_text(json.dumps(fake))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "csrc_hash", lambda: "f" * 16)
+    assert bench.ncu_issue(name, 2000.0) is None
+
+
+def test_line_carries_the_committed_accuracy_and_learned_records(bench):
+    """The bench line's accuracy and learned-vs-plain blocks come from the
+    committed GPU records, with the fields the line promises."""
+    acc = bench.accuracy_line()
+    assert acc["windows"] == 64 and acc["below_floor"] == 0 and acc["above_ceiling"] == 0
+    assert acc["within_1e-3_bpm_both_bands"] == acc["windows"] and acc["max_bpm"] < 1e-3
+    assert acc["copies_per_window"] == pytest.approx(acc["copies"] / acc["windows"])
+    lv = bench.learned_line()
+    assert lv["learned"]["depth"] < lv["plain"]["depth"]
+    assert lv["learned"]["windows_per_s"] > lv["plain"]["windows_per_s"]
+    assert lv["speedup_learned_over_plain"] == pytest.approx(lv["learned"]["windows_per_s"] /
+                                                              lv["plain"]["windows_per_s"])
